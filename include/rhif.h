@@ -1,0 +1,185 @@
+/*
+ * rhif.h -- C ABI of the GB300 implementation of the recursively preconditioned
+ * hierarchical interpolative factorization (PHIF) of Feliu-Faba, Ho and Ying.
+ *
+ * Problem (Sec. 1, Eqs. 1.1-1.2): A u = f, A sparse SPD from the five-point
+ * (2D) or seven-point (3D) finite-difference discretisation of
+ * -div(a grad u) + b u = f on the unit square/cube with zero Dirichlet data.
+ * The library builds F ~= A (Sec. 3, Eqs. 3.1-3.3), applies F^{-1}, and runs
+ * PCG with F^{-1} as the preconditioner (Sec. 4).
+ *
+ * Conventions for every entry point:
+ *  - A grid has n[i] interior nodes along axis i (x first), h_i = 1/(n[i]+1).
+ *    DOF index of interior node (i,j,k) (0-based) is i + n0*(j + n1*k).
+ *  - Unless stated otherwise every array pointer is a DEVICE pointer owned by
+ *    the caller; the library never frees caller memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  All work is stream-ordered on it; calls that return host
+ *    results (statistics, iteration counts) synchronise that stream.
+ *  - Return value: RHIF_OK (0) or a negative RHIF_ERR_* code; no exception or
+ *    trap crosses the ABI.  rhif_error_string() names a code and
+ *    rhif_last_error_detail() gives a one-line description of the most recent
+ *    failure on the calling thread.
+ *  - A handle must not be used concurrently from two streams.
+ */
+#ifndef RHIF_H
+#define RHIF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  RHIF_OK = 0,
+  RHIF_ERR_BAD_ARG = -1,        /* null pointer, bad size, CSR outside the stencil pattern */
+  RHIF_ERR_NOT_SPD = -2,        /* a Cholesky pivot <= 0 or NaN (Remark 2.1: SPD lost) */
+  RHIF_ERR_NOT_CONVERGED = -3,  /* PCG hit maxit before rtol */
+  RHIF_ERR_TIMEOUT = -4,        /* a bounded device wait gave up */
+  RHIF_ERR_OOM = -5,            /* device allocation failed */
+  RHIF_ERR_CUDA = -6            /* any other CUDA runtime error */
+};
+
+enum { RHIF_FP64 = 0, RHIF_MIXED_FP32 = 1 };  /* precision of the stored factor */
+enum { RHIF_SOLVE = 0, RHIF_MATVEC = 1 };      /* apply F^{-1} or F */
+
+typedef struct {
+  int dim;      /* 2 or 3 */
+  int n[3];     /* interior nodes per axis (n[2] ignored when dim == 2) */
+} rhif_grid;
+
+/* Sparse matrix in CSR form, device memory, caller-owned.  Row r holds
+ * col[rowptr[r] .. rowptr[r+1]) with values val[...].  The pattern must be the
+ * grid stencil (diagonal plus grid neighbours) and the values symmetric. */
+typedef struct {
+  int64_t nrows;
+  int64_t nnz;
+  const int64_t* rowptr;
+  const int32_t* col;
+  const double* val;
+} rhif_csr;
+
+typedef struct {
+  int precision;      /* RHIF_FP64 (default) or RHIF_MIXED_FP32 */
+  int precondition;   /* 1 = PHIF (default, Sec. 3); 0 = plain HIF (C_l = I) */
+  int edge_skel_3d;   /* 3D only: also precondition and skeletonize edges (Remark 3.1) */
+  int reserved[5];
+} rhif_opts;
+
+typedef struct rhif_handle rhif_handle;
+
+/* Fill *o with the defaults (FP64, PHIF, no 3D edge skeletonization). */
+int rhif_default_opts(rhif_opts* o);
+
+/* Number of stored entries of the finite-difference matrix of grid g. */
+int64_t rhif_fd_nnz(const rhif_grid* g);
+
+/* Finite-difference matrix of Eq. (1.1) (Sec. 3.1 five-point, Sec. 3.2
+ * seven-point stencil).  a_pix: per-pixel coefficient, (n0+1)*(n1+1)[*(n2+1)]
+ * values, x fastest.  The weight of a grid edge is the mean of `a` over the 2
+ * (2D) or 4 (3D) pixels touching it; edges to boundary nodes add to the
+ * diagonal only; entries carry the 1/h^2 factor.  b_node: per-node b (N
+ * values) or NULL to use the constant b_const.  Outputs rowptr (N+1), col and
+ * val (rhif_fd_nnz(g) each), caller-allocated; columns ascend within a row. */
+int rhif_assemble_fd(const rhif_grid* g, const double* a_pix, const double* b_node,
+                     double b_const, int64_t* rowptr, int32_t* col, double* val,
+                     void* stream);
+
+/* PHIF factorization F ~= A (Sec. 3): per level l = 0..L-1 cell elimination
+ * (Sec. 2.1, Eq. 2.1), block Jacobi preconditioning of every separator group
+ * (Sec. 2.3, Eq. 2.3) and skeletonization of every edge (2D) / face (3D) by a
+ * column-pivoted-QR interpolative decomposition to relative precision `tol`
+ * (Sec. 2.2, Eq. 2.2; all IDs of a level before any zeroing), then the root
+ * Cholesky A_L = B_L B_L^T (Eq. 3.3).  `leaf` = m, the leaf cell width in grid
+ * intervals; L is the smallest level count with 2^L m >= n_i + 1.  A is read
+ * during the call only.  On success *out receives a handle owning all factor
+ * storage (free with rhif_free).  Errors: BAD_ARG (pattern, sizes, leaf < 2,
+ * tol < 0), NOT_SPD (with the level in the detail string), OOM, CUDA. */
+int rhif_factor(const rhif_csr* A, const rhif_grid* g, int leaf, double tol,
+                const rhif_opts* o, void* stream, rhif_handle** out);
+
+/* y = F^{-1} x (op = RHIF_SOLVE, Eq. 3.2) or y = F x (RHIF_MATVEC, Eq. 3.1)
+ * for nrhs column vectors of length N stored with leading dimensions ldx/ldy
+ * (>= N).  x and y may alias only if ldx == ldy and x == y. */
+int rhif_apply(const rhif_handle* F, int op, int nrhs, const double* x, int64_t ldx,
+               double* y, int64_t ldy, void* stream);
+
+/* y = A x with the stencil form of the A given to rhif_factor (FP64). */
+int rhif_spmv(const rhif_handle* F, int nrhs, const double* x, int64_t ldx,
+              double* y, int64_t ldy, void* stream);
+
+/* PCG (Sec. 4) on A u = f with F^{-1} as the preconditioner, FP64 vectors,
+ * x0 = 0, stopped when ||f - A u|| / ||f|| <= rtol (recursive residual) for
+ * every right-hand side or after maxit iterations.  iters and relres are HOST
+ * arrays of nrhs entries receiving the iteration count and the true relative
+ * residual.  Returns NOT_CONVERGED if some system missed rtol. */
+int rhif_pcg(const rhif_handle* F, int nrhs, const double* f, int64_t ldf, double* u,
+             int64_t ldu, double rtol, int maxit, int* iters, double* relres,
+             void* stream);
+
+/* Per-pixel gradient of a loss with respect to log a, given the state u and
+ * the adjoint lam = A^{-1} dLoss/du:  grad_p = -a_p / 2^(d-1) *
+ * sum over the grid edges e of pixel p of (lam_i - lam_j)(u_i - u_j)/h_e^2
+ * (u = lam = 0 on boundary nodes).  Output grad has one value per pixel. */
+int rhif_grad_logcoef(const rhif_grid* g, const double* a_pix, const double* u,
+                      const double* lam, double* grad, void* stream);
+
+typedef struct {
+  int levels;             /* L */
+  int64_t n;              /* N */
+  int64_t root_size;      /* |S_L| */
+  int64_t active[16];     /* |S_{l+1}| after level l, l < min(L,16) */
+  int64_t factor_bytes;   /* device bytes held by the factor */
+  double flops;           /* algorithmic flops of the factorization */
+  double apply_bytes;     /* factor bytes streamed by one rhif_apply per rhs */
+  int precision;
+  int units;              /* skeletonized units, all levels */
+  double factor_ms;       /* device time of the last rhif_factor */
+} rhif_stats_t;
+
+/* Copy statistics of a factor to host memory. */
+int rhif_stats(const rhif_handle* F, rhif_stats_t* st);
+
+/* Skeletonization record of one level/phase (phase 0 = edges in 2D, faces in
+ * 3D; phase 1 = 3D edges).  Host outputs: *count units; for unit u, sizes[u]
+ * DOFs and ranks[u] skeletons.  If gids != NULL it receives, unit after unit,
+ * the sizes[u] DOF indices in pivot order (skeletons first); capacity is the
+ * length of gids.  Call with gids == NULL first to learn the sizes. */
+int rhif_skeletons(const rhif_handle* F, int level, int phase, int* count,
+                   int* sizes, int* ranks, int64_t* gids, int64_t capacity);
+
+/* Kernel instrumentation (process-wide).  Every kernel launch of the library
+ * is counted per category; with timing on, CUDA events bracket each launch on
+ * its stream and the elapsed times are summed when the statistics are read.
+ * flops / bytes are the algorithmic work of the counted launches (see the
+ * per-category definitions in the implementation notes). */
+typedef struct {
+  char name[32];
+  int64_t launches;
+  double total_ms;   /* 0 unless timing was on */
+  double flops;
+  double bytes;
+} rhif_kernel_stat;
+
+/* Turn per-launch CUDA-event timing on (1) or off (0); returns RHIF_OK. */
+int rhif_set_timing(int on);
+/* Zero every category's counters. */
+int rhif_reset_kernel_stats(void);
+/* Copy category `index` (0 <= index < rhif_kernel_stat_count()) to *out.
+ * Synchronises the device once to resolve pending timing events. */
+int rhif_kernel_stat_count(void);
+int rhif_kernel_stats(int index, rhif_kernel_stat* out);
+
+/* Release every device allocation of the handle (stream-ordered on the
+ * stream of the factorization). */
+void rhif_free(rhif_handle* F);
+
+const char* rhif_error_string(int code);
+const char* rhif_last_error_detail(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RHIF_H */

@@ -1,0 +1,297 @@
+"""Python binding of librhif (include/rhif.h): argument marshalling only.
+
+Every step of the factorization, the application of F^{-1} and PCG runs in the
+CUDA library; this module passes torch device pointers and the current stream
+through ctypes.  There is no CPU fallback: :func:`load` raises if the library
+cannot be built or loaded, and every call raises :class:`RhifError` on a
+non-zero return code.
+
+Names follow the C ABI: ``rhif_assemble_fd``, ``rhif_factor`` (returns a
+:class:`Factor` with ``apply``/``pcg``/``spmv``/``stats``/``skeletons``/``free``),
+``rhif_grad_logcoef``, plus :class:`RhifSolve`, the torch.autograd function of
+the differentiation workload.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+_lib = None
+_lock = threading.Lock()
+
+RHIF_FP64, RHIF_MIXED_FP32 = 0, 1
+RHIF_SOLVE, RHIF_MATVEC = 0, 1
+ERRORS = {0: "OK", -1: "BAD_ARG", -2: "NOT_SPD", -3: "NOT_CONVERGED", -4: "TIMEOUT", -5: "OOM",
+          -6: "CUDA"}
+
+
+class RhifError(RuntimeError):
+    def __init__(self, code, detail):
+        super().__init__(f"RHIF_ERR_{ERRORS.get(code, code)}: {detail}")
+        self.code = code
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3)]
+
+
+class CSR(ctypes.Structure):
+    _fields_ = [("nrows", ctypes.c_int64), ("nnz", ctypes.c_int64), ("rowptr", ctypes.c_void_p),
+                ("col", ctypes.c_void_p), ("val", ctypes.c_void_p)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("precondition", ctypes.c_int),
+                ("edge_skel_3d", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int), ("n", ctypes.c_int64), ("root_size", ctypes.c_int64),
+                ("active", ctypes.c_int64 * 16), ("factor_bytes", ctypes.c_int64),
+                ("flops", ctypes.c_double), ("apply_bytes", ctypes.c_double),
+                ("precision", ctypes.c_int), ("units", ctypes.c_int),
+                ("factor_ms", ctypes.c_double)]
+
+
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64),
+                ("total_ms", ctypes.c_double), ("flops", ctypes.c_double),
+                ("bytes", ctypes.c_double)]
+
+
+EXPORTS = {
+    "rhif_default_opts": (ctypes.c_int, [ctypes.POINTER(Opts)]),
+    "rhif_fd_nnz": (ctypes.c_int64, [ctypes.POINTER(Grid)]),
+    "rhif_assemble_fd": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p]),
+    "rhif_factor": (ctypes.c_int, [ctypes.POINTER(CSR), ctypes.POINTER(Grid), ctypes.c_int,
+                                   ctypes.c_double, ctypes.POINTER(Opts), ctypes.c_void_p,
+                                   ctypes.POINTER(ctypes.c_void_p)]),
+    "rhif_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                  ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
+    "rhif_spmv": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
+                                 ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
+    "rhif_pcg": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
+                                ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int,
+                                ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                                ctypes.c_void_p]),
+    "rhif_grad_logcoef": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "rhif_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Stats)]),
+    "rhif_skeletons": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                      ctypes.POINTER(ctypes.c_int), ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
+    "rhif_free": (None, [ctypes.c_void_p]),
+    "rhif_set_timing": (ctypes.c_int, [ctypes.c_int]),
+    "rhif_reset_kernel_stats": (ctypes.c_int, []),
+    "rhif_kernel_stat_count": (ctypes.c_int, []),
+    "rhif_kernel_stats": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(KernelStat)]),
+    "rhif_error_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "rhif_last_error_detail": (ctypes.c_char_p, []),
+}
+
+
+def load(rebuild: bool = False):
+    """Load librhif.so, building it first when it is missing or stale."""
+    global _lib
+    with _lock:
+        if _lib is not None and not rebuild:
+            return _lib
+        if rebuild or not _build.up_to_date():
+            _build.build()
+        lib = ctypes.CDLL(_build.LIB)
+        for name, (res, args) in EXPORTS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(rc):
+    if rc != 0:
+        raise RhifError(rc, _lib.rhif_last_error_detail().decode())
+
+
+def _grid(ns) -> Grid:
+    ns = [int(v) for v in ns]
+    g = Grid()
+    g.dim = len(ns)
+    for i in range(3):
+        g.n[i] = ns[i] if i < len(ns) else 1
+    return g
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t: torch.Tensor):
+    assert t.is_cuda and t.is_contiguous(), "expected a contiguous CUDA tensor"
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _cols(x: torch.Tensor, N: int):
+    """(N,) or (nrhs, N) contiguous float64 -> (nrhs, ld)."""
+    assert x.dtype == torch.float64 and x.is_cuda and x.is_contiguous()
+    if x.dim() == 1:
+        assert x.numel() == N
+        return 1, N
+    assert x.dim() == 2 and x.shape[1] == N
+    return x.shape[0], N
+
+
+def rhif_fd_nnz(ns) -> int:
+    load()
+    return int(_lib.rhif_fd_nnz(ctypes.byref(_grid(ns))))
+
+
+def rhif_assemble_fd(ns, a_pix: torch.Tensor, b=0.0, stream=None):
+    """Finite-difference matrix on the device: returns (rowptr int64, col int32, val float64)."""
+    load()
+    g = _grid(ns)
+    N = 1
+    for v in ns:
+        N *= int(v)
+    nnz = int(_lib.rhif_fd_nnz(ctypes.byref(g)))
+    dev = a_pix.device
+    rowptr = torch.empty(N + 1, dtype=torch.int64, device=dev)
+    col = torch.empty(nnz, dtype=torch.int32, device=dev)
+    val = torch.empty(nnz, dtype=torch.float64, device=dev)
+    a_pix = a_pix.contiguous().to(torch.float64)
+    if isinstance(b, torch.Tensor):
+        bn, bc = _ptr(b.contiguous().to(torch.float64)), 0.0
+    else:
+        bn, bc = None, float(b)
+    _check(_lib.rhif_assemble_fd(ctypes.byref(g), _ptr(a_pix), bn, bc, _ptr(rowptr), _ptr(col),
+                                 _ptr(val), _stream(stream)))
+    return rowptr, col, val
+
+
+class Factor:
+    """A factor F ~= A owned by the library (free with :meth:`free`)."""
+
+    def __init__(self, handle, ns, keep):
+        self._h = handle
+        self.ns = tuple(int(v) for v in ns)
+        self.N = 1
+        for v in self.ns:
+            self.N *= v
+        self._keep = keep
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def free(self):
+        if self._h:
+            _lib.rhif_free(self._h)
+            self._h = None
+
+    def apply(self, x: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """F^{-1} x (Eq. 3.2) for x of shape (N,) or (nrhs, N)."""
+        nrhs, ld = _cols(x, self.N)
+        y = torch.empty_like(x) if out is None else out
+        _check(_lib.rhif_apply(self._h, RHIF_SOLVE, nrhs, _ptr(x), ld, _ptr(y), ld, _stream(stream)))
+        return y
+
+    def spmv(self, x: torch.Tensor, stream=None) -> torch.Tensor:
+        nrhs, ld = _cols(x, self.N)
+        y = torch.empty_like(x)
+        _check(_lib.rhif_spmv(self._h, nrhs, _ptr(x), ld, _ptr(y), ld, _stream(stream)))
+        return y
+
+    def pcg(self, f: torch.Tensor, rtol=1e-10, maxit=1000, out=None, stream=None, check=True):
+        """PCG with F^{-1}; returns (u, iters list, relres list)."""
+        nrhs, ld = _cols(f, self.N)
+        u = torch.empty_like(f) if out is None else out
+        it = (ctypes.c_int * nrhs)()
+        rr = (ctypes.c_double * nrhs)()
+        rc = _lib.rhif_pcg(self._h, nrhs, _ptr(f), ld, _ptr(u), ld, float(rtol), int(maxit), it, rr,
+                           _stream(stream))
+        if rc != 0 and (check or rc != -3):
+            _check(rc)
+        return u, list(it), list(rr)
+
+    def stats(self) -> dict:
+        st = Stats()
+        _check(_lib.rhif_stats(self._h, ctypes.byref(st)))
+        return {"levels": st.levels, "n": st.n, "root_size": st.root_size,
+                "active": list(st.active)[:st.levels], "factor_bytes": st.factor_bytes,
+                "flops": st.flops, "apply_bytes": st.apply_bytes, "precision": st.precision,
+                "units": st.units, "factor_ms": st.factor_ms}
+
+    def skeletons(self, level: int, phase: int = 0):
+        """[(dofs in pivot order, rank)] for every unit of a level/phase."""
+        cnt = ctypes.c_int()
+        _check(_lib.rhif_skeletons(self._h, level, phase, ctypes.byref(cnt), None, None, None, 0))
+        n = cnt.value
+        sizes = (ctypes.c_int * max(n, 1))()
+        ranks = (ctypes.c_int * max(n, 1))()
+        _check(_lib.rhif_skeletons(self._h, level, phase, ctypes.byref(cnt), sizes, ranks, None, 0))
+        tot = sum(sizes[i] for i in range(n))
+        gids = (ctypes.c_int64 * max(tot, 1))()
+        _check(_lib.rhif_skeletons(self._h, level, phase, ctypes.byref(cnt), sizes, ranks, gids, tot))
+        out, pos = [], 0
+        for i in range(n):
+            out.append((list(gids[pos:pos + sizes[i]]), ranks[i]))
+            pos += sizes[i]
+        return out
+
+
+def rhif_factor(csr, ns, leaf: int, tol: float, precision: str = "fp64", precondition=True,
+                edge_skel_3d=False, stream=None) -> Factor:
+    """PHIF factorization of the CSR matrix ``csr = (rowptr, col, val)`` on grid ``ns``."""
+    load()
+    rowptr, col, val = csr
+    N = rowptr.numel() - 1
+    A = CSR(N, val.numel(), rowptr.data_ptr(), col.data_ptr(), val.data_ptr())
+    o = Opts()
+    _lib.rhif_default_opts(ctypes.byref(o))
+    o.precision = {"fp64": RHIF_FP64, "fp32": RHIF_MIXED_FP32, "mixed": RHIF_MIXED_FP32}[precision]
+    o.precondition = 1 if precondition else 0
+    o.edge_skel_3d = 1 if edge_skel_3d else 0
+    h = ctypes.c_void_p()
+    _check(_lib.rhif_factor(ctypes.byref(A), ctypes.byref(_grid(ns)), int(leaf), float(tol),
+                            ctypes.byref(o), _stream(stream), ctypes.byref(h)))
+    return Factor(h, ns, None)
+
+
+def rhif_grad_logcoef(ns, a_pix: torch.Tensor, u: torch.Tensor, lam: torch.Tensor, stream=None):
+    load()
+    grad = torch.empty_like(a_pix)
+    _check(_lib.rhif_grad_logcoef(ctypes.byref(_grid(ns)), _ptr(a_pix), _ptr(u), _ptr(lam),
+                                  _ptr(grad), _stream(stream)))
+    return grad
+
+
+def rhif_set_timing(on: bool):
+    """CUDA-event timing of every library kernel launch (process-wide)."""
+    load()
+    _check(_lib.rhif_set_timing(1 if on else 0))
+
+
+def rhif_reset_kernel_stats():
+    load()
+    _check(_lib.rhif_reset_kernel_stats())
+
+
+def rhif_kernel_stats() -> dict:
+    """{category: {launches, total_ms, flops, bytes}} since the last reset."""
+    load()
+    out = {}
+    for i in range(_lib.rhif_kernel_stat_count()):
+        st = KernelStat()
+        _check(_lib.rhif_kernel_stats(i, ctypes.byref(st)))
+        out[st.name.decode()] = {"launches": st.launches, "total_ms": st.total_ms,
+                                 "flops": st.flops, "bytes": st.bytes}
+    return out

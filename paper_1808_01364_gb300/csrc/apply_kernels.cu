@@ -1,0 +1,560 @@
+// Application of F^{-1} (Eq. 3.2) and the FP64 vector kernels of PCG.
+//
+// F^{-1} x = R_0 ... R_{L-1} A_L^{-1} R_{L-1}^T ... R_0^T x with
+// R_l = E_l C_l K_l.  Per level the upward sweep applies E_l^T per cell
+// (y = L^{-1} x_I, x_B -= W y with W = A_BI L^{-T}), then C_l^T and K_l^T per
+// separator group; the downward sweep applies K_l, C_l per group and E_l per
+// cell (x_I = L^{-T}(x_I - W^T x_B)).  The cell contributions to a shared
+// boundary DOF are written per cell and summed by the owning group in cell
+// order, so the result does not depend on scheduling.
+#include "common.cuh"
+#include "kernels.h"
+#include "tables.h"
+
+namespace rhif {
+
+constexpr int kApplyThreads = 256;
+constexpr int kGroupThreads = 128;
+
+// ---------------------------------------------------------------------------
+// cells
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__global__ void __launch_bounds__(kApplyThreads)
+k_apply_cell_up(LevelDev Lv, double* x, int64_t ldx, int nrhs, double* ubuf, int64_t ldu) {
+  extern __shared__ unsigned char smraw[];
+  T* y = (T*)smraw;
+  const int c = blockIdx.x;
+  const int nI = Lv.nI[c], nB = Lv.nB[c], n = nI + nB;
+  const T* F = (const T*)Lv.front + Lv.front_off[c];
+  const int64_t* gI = Lv.gids + Lv.gid_off[c];
+  for (int r = 0; r < nrhs; ++r) {
+    double* xr = x + r * ldx;
+    for (int i = threadIdx.x; i < nI; i += blockDim.x) y[i] = T(xr[gI[i]]);
+    __syncthreads();
+    cta_trsv_lower(F, n, nI, y);
+    for (int i = threadIdx.x; i < nI; i += blockDim.x) xr[gI[i]] = double(y[i]);
+    double* u = ubuf + r * ldu + Lv.b_off[c];
+    for (int b = threadIdx.x; b < nB; b += blockDim.x) {
+      T s = T(0);
+      for (int k = 0; k < nI; ++k) s += F[(nI + b) + (int64_t)k * n] * y[k];
+      u[b] = double(s);
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kApplyThreads)
+k_apply_cell_down(LevelDev Lv, double* x, int64_t ldx, int nrhs) {
+  extern __shared__ unsigned char smraw[];
+  T* t = (T*)smraw;
+  T* xb = t + Lv.max_nI;
+  const int c = blockIdx.x;
+  const int nI = Lv.nI[c], nB = Lv.nB[c], n = nI + nB;
+  const T* F = (const T*)Lv.front + Lv.front_off[c];
+  const int64_t* gI = Lv.gids + Lv.gid_off[c];
+  const int64_t* gB = gI + nI;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (int r = 0; r < nrhs; ++r) {
+    double* xr = x + r * ldx;
+    for (int b = threadIdx.x; b < nB; b += blockDim.x) xb[b] = T(xr[gB[b]]);
+    __syncthreads();
+    for (int k = warp; k < nI; k += nwarps) {
+      T s = T(0);
+      for (int b = lane; b < nB; b += 32) s += F[(nI + b) + (int64_t)k * n] * xb[b];
+      s = warp_sum(s);
+      if (lane == 0) t[k] = T(xr[gI[k]]) - s;
+    }
+    __syncthreads();
+    cta_trsv_lower_t(F, n, nI, t);
+    for (int i = threadIdx.x; i < nI; i += blockDim.x) xr[gI[i]] = double(t[i]);
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// separator groups: C_l and K_l (one CTA per group)
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__device__ void unit_up(const PhaseDev& Ph, int u, int n, T* xg, T* tmp) {
+  const int k = Ph.rank[u], r = n - k;
+  const int* perm = Ph.perm + Ph.u_perm_off[u];
+  const T* Fu = (const T*)Ph.rec + Ph.u_rec_off[u];
+  const T* Tm = Fu + (int64_t)n * n;
+  // Z^T: x_rd -= T^T x_sk
+  for (int a = threadIdx.x; a < r; a += blockDim.x) {
+    T s = xg[perm[k + a]];
+    for (int q = 0; q < k; ++q) s -= Tm[q + (int64_t)a * k] * xg[perm[q]];
+    tmp[a] = s;
+  }
+  __syncthreads();
+  // E_rd^T: y = L^{-1} x_rd ; x_sk -= W y ; x_rd = y
+  cta_trsv_lower(Fu, n, r, tmp);
+  for (int q = threadIdx.x; q < k; q += blockDim.x) {
+    T s = xg[perm[q]];
+    for (int a = 0; a < r; ++a) s -= Fu[(r + q) + (int64_t)a * n] * tmp[a];
+    tmp[r + q] = s;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) xg[perm[i < r ? k + i : i - r]] = tmp[i];
+  __syncthreads();
+}
+
+template <typename T>
+__device__ void unit_down(const PhaseDev& Ph, int u, int n, T* xg, T* tmp) {
+  const int k = Ph.rank[u], r = n - k;
+  const int* perm = Ph.perm + Ph.u_perm_off[u];
+  const T* Fu = (const T*)Ph.rec + Ph.u_rec_off[u];
+  const T* Tm = Fu + (int64_t)n * n;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  // E_rd: x_rd = L^{-T}(x_rd - W^T x_sk)
+  for (int a = warp; a < r; a += nwarps) {
+    T s = T(0);
+    for (int q = lane; q < k; q += 32) s += Fu[(r + q) + (int64_t)a * n] * xg[perm[q]];
+    s = warp_sum(s);
+    if (lane == 0) tmp[a] = xg[perm[k + a]] - s;
+  }
+  __syncthreads();
+  cta_trsv_lower_t(Fu, n, r, tmp);
+  // Z: x_sk -= T x_rd
+  for (int q = threadIdx.x; q < k; q += blockDim.x) {
+    T s = xg[perm[q]];
+    for (int a = 0; a < r; ++a) s -= Tm[q + (int64_t)a * k] * tmp[a];
+    tmp[r + q] = s;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) xg[perm[i < r ? k + i : i - r]] = tmp[i];
+  __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kGroupThreads)
+k_apply_group_up(LevelDev Lv, PhaseDev Ph, int gather, double* x, int64_t ldx, int nrhs,
+                 const double* ubuf, int64_t ldu) {
+  extern __shared__ unsigned char smraw[];
+  T* xg = (T*)smraw;
+  T* tmp = xg + Lv.max_group;
+  const int g = blockIdx.x;
+  if (Lv.group_t[g] < Ph.pre_min_type) return;
+  const int64_t g0 = Lv.group_gid_off[g];
+  const int n = (int)(Lv.group_gid_off[g + 1] - g0);
+  const int64_t* gid = Lv.group_gids + g0;
+  const int pi = Ph.group_pre[g], u = Ph.group_unit[g];
+  for (int r = 0; r < nrhs; ++r) {
+    double* xr = x + r * ldx;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      double v = xr[gid[i]];
+      if (gather) {
+        for (int k = Lv.group_cell_off[g]; k < Lv.group_cell_off[g + 1]; ++k)
+          v -= ubuf[r * ldu + Lv.b_off[Lv.group_cell[k]] + Lv.group_pos[k] + i];
+      }
+      xg[i] = T(v);
+    }
+    __syncthreads();
+    if (pi >= 0) cta_trsv_lower((const T*)Ph.Lbuf + Ph.pre_off[pi], n, n, xg);
+    if (u >= 0) unit_up(Ph, u, n, xg, tmp);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) xr[gid[i]] = double(xg[i]);
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kGroupThreads)
+k_apply_group_down(LevelDev Lv, PhaseDev Ph, double* x, int64_t ldx, int nrhs) {
+  extern __shared__ unsigned char smraw[];
+  T* xg = (T*)smraw;
+  T* tmp = xg + Lv.max_group;
+  const int g = blockIdx.x;
+  if (Lv.group_t[g] < Ph.pre_min_type) return;
+  const int64_t g0 = Lv.group_gid_off[g];
+  const int n = (int)(Lv.group_gid_off[g + 1] - g0);
+  const int64_t* gid = Lv.group_gids + g0;
+  const int pi = Ph.group_pre[g], u = Ph.group_unit[g];
+  for (int r = 0; r < nrhs; ++r) {
+    double* xr = x + r * ldx;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) xg[i] = T(xr[gid[i]]);
+    __syncthreads();
+    if (u >= 0) unit_down(Ph, u, n, xg, tmp);
+    if (pi >= 0) cta_trsv_lower_t((const T*)Ph.Lbuf + Ph.pre_off[pi], n, n, xg);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) xr[gid[i]] = double(xg[i]);
+    __syncthreads();
+  }
+}
+
+template <typename T>
+void launch_apply_cell_up(const LevelDev& Lv, double* x, int64_t ldx, int nrhs, double* ubuf,
+                          int64_t ldu, cudaStream_t s) {
+  if (!Lv.ncell) return;
+  k_apply_cell_up<T><<<Lv.ncell, kApplyThreads, (Lv.max_nI + 1) * sizeof(T), s>>>(Lv, x, ldx, nrhs, ubuf, ldu);
+}
+
+template <typename T>
+void launch_apply_cell_down(const LevelDev& Lv, double* x, int64_t ldx, int nrhs, cudaStream_t s) {
+  if (!Lv.ncell) return;
+  k_apply_cell_down<T><<<Lv.ncell, kApplyThreads, (Lv.max_nI + Lv.max_nB + 1) * sizeof(T), s>>>(
+      Lv, x, ldx, nrhs);
+}
+
+template <typename T>
+void launch_apply_group_up(const LevelDev& Lv, const PhaseDev& Ph, int gather, double* x,
+                           int64_t ldx, int nrhs, const double* ubuf, int64_t ldu, cudaStream_t s) {
+  if (!Lv.ngroup) return;
+  k_apply_group_up<T><<<Lv.ngroup, kGroupThreads, 2 * (Lv.max_group + 1) * sizeof(T), s>>>(
+      Lv, Ph, gather, x, ldx, nrhs, ubuf, ldu);
+}
+
+template <typename T>
+void launch_apply_group_down(const LevelDev& Lv, const PhaseDev& Ph, double* x, int64_t ldx,
+                             int nrhs, cudaStream_t s) {
+  if (!Lv.ngroup) return;
+  k_apply_group_down<T><<<Lv.ngroup, kGroupThreads, 2 * (Lv.max_group + 1) * sizeof(T), s>>>(
+      Lv, Ph, x, ldx, nrhs);
+}
+
+template <typename T>
+int configure_apply_kernels() {
+  const int big = 200 * 1024;
+  cudaError_t e = cudaSuccess;
+  e = cudaFuncSetAttribute(k_apply_cell_up<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_cell_down<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_group_up<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_group_down<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  return e == cudaSuccess ? 0 : -1;
+}
+
+#define RHIF_APPLY_INST(T)                                                                         \
+  template void launch_apply_cell_up<T>(const LevelDev&, double*, int64_t, int, double*, int64_t,  \
+                                        cudaStream_t);                                             \
+  template void launch_apply_cell_down<T>(const LevelDev&, double*, int64_t, int, cudaStream_t);   \
+  template void launch_apply_group_up<T>(const LevelDev&, const PhaseDev&, int, double*, int64_t,  \
+                                         int, const double*, int64_t, cudaStream_t);               \
+  template void launch_apply_group_down<T>(const LevelDev&, const PhaseDev&, double*, int64_t, int, \
+                                           cudaStream_t);                                          \
+  template int configure_apply_kernels<T>();
+
+RHIF_APPLY_INST(double)
+RHIF_APPLY_INST(float)
+
+// ---------------------------------------------------------------------------
+// FP64 stencil SpMV and PCG vector kernels
+// ---------------------------------------------------------------------------
+
+constexpr int kVecThreads = 256;
+
+__device__ inline double block_sum(double v) {
+  __shared__ double part[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) part[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (warp == 0) {
+    s = lane < (int)(blockDim.x >> 5) ? part[lane] : 0.0;
+    s = warp_sum(s);
+  }
+  return s;   // valid in thread 0
+}
+
+// y = A x (+ partial sums of x.y per block when partial != nullptr)
+__global__ void k_spmv(GeoDev G, const double* diag, const double* off, const double* x,
+                       int64_t ldx, double* y, int64_t ldy, double* partial) {
+  const int r = blockIdx.y;
+  const double* xr = x + r * ldx;
+  double* yr = y + r * ldy;
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < G.N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double s = diag[i] * xr[i];
+    int64_t rem = i;
+    for (int a = 0; a < G.d; ++a) {
+      const int xa = (int)(rem % G.ns[a]);
+      rem /= G.ns[a];
+      const int64_t st = G.stride[a];
+      if (xa + 1 < G.ns[a]) s += off[a * G.N + i] * xr[i + st];
+      if (xa >= 1) s += off[a * G.N + i - st] * xr[i - st];
+    }
+    yr[i] = s;
+    acc += s * xr[i];
+  }
+  if (partial) {
+    const double t = block_sum(acc);
+    if (threadIdx.x == 0) partial[blockIdx.x + (int64_t)gridDim.x * r] = t;
+  }
+}
+
+// partial sums of a.b per block
+__global__ void k_dot_partial(int64_t N, const double* a, int64_t lda, const double* b, int64_t ldb,
+                              double* partial) {
+  const int r = blockIdx.y;
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x)
+    acc += a[i + r * lda] * b[i + r * ldb];
+  const double t = block_sum(acc);
+  if (threadIdx.x == 0) partial[blockIdx.x + (int64_t)gridDim.x * r] = t;
+}
+
+// PCG scalar slots per right-hand side (doubles): see enum in kernels.h
+// mode 0: ff ; 1: rz (init) ; 2: pq -> alpha ; 3: rr -> done ; 4: rz_new -> beta
+__global__ void k_reduce(const double* partial, int nblk, double* sc, int mode, double rtol) {
+  const int r = blockIdx.x;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nblk; i += blockDim.x) acc += partial[i + (int64_t)nblk * r];
+  const double s = block_sum(acc);
+  if (threadIdx.x != 0) return;
+  double* S = sc + 8 * r;
+  switch (mode) {
+    case 0: S[kScFF] = s; break;
+    case 1: S[kScRZ] = s; break;
+    case 2:
+      S[kScPQ] = s;
+      S[kScAlpha] = (S[kScDone] != 0.0 || s == 0.0) ? 0.0 : S[kScRZ] / s;
+      break;
+    case 3:
+      S[kScRR] = s;
+      if (S[kScDone] == 0.0 && sqrt(s) <= rtol * sqrt(S[kScFF])) S[kScDone] = 1.0;
+      break;
+    case 4:
+      S[kScBeta] = (S[kScDone] != 0.0 || S[kScRZ] == 0.0) ? 0.0 : s / S[kScRZ];
+      S[kScRZ] = s;
+      break;
+  }
+}
+
+// x += alpha p ; r -= alpha q ; partial r.r
+__global__ void k_update_xr(int64_t N, const double* sc, double* x, int64_t ldx, double* rv,
+                            int64_t ldr, const double* p, int64_t ldp, const double* q,
+                            int64_t ldq, double* partial) {
+  const int r = blockIdx.y;
+  const double* S = sc + 8 * r;
+  const double alpha = S[kScAlpha];
+  const bool live = S[kScDone] == 0.0;
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double ri = rv[i + r * ldr];
+    if (live) {
+      x[i + r * ldx] += alpha * p[i + r * ldp];
+      ri -= alpha * q[i + r * ldq];
+      rv[i + r * ldr] = ri;
+    }
+    acc += ri * ri;
+  }
+  const double t = block_sum(acc);
+  if (threadIdx.x == 0) partial[blockIdx.x + (int64_t)gridDim.x * r] = t;
+}
+
+// p = z + beta p
+__global__ void k_update_p(int64_t N, const double* sc, const double* z, int64_t ldz, double* p,
+                           int64_t ldp, int first) {
+  const int r = blockIdx.y;
+  const double* S = sc + 8 * r;
+  if (!first && S[kScDone] != 0.0) return;
+  const double beta = first ? 0.0 : S[kScBeta];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i + r * ldp] = z[i + r * ldz] + beta * p[i + r * ldp];
+}
+
+// y = a - b (true residual)
+__global__ void k_sub(int64_t N, const double* a, int64_t lda, const double* b, int64_t ldb,
+                      double* y, int64_t ldy) {
+  const int r = blockIdx.y;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i + r * ldy] = a[i + r * lda] - b[i + r * ldb];
+}
+
+__global__ void k_copy_cols(int64_t N, const double* a, int64_t lda, double* y, int64_t ldy) {
+  const int r = blockIdx.y;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i + r * ldy] = a[i + r * lda];
+}
+
+int vec_blocks(int64_t N) {
+  int64_t b = (N + kVecThreads - 1) / kVecThreads;
+  if (b > 1216) b = 1216;   // 8 blocks per SM on 152 SMs
+  return (int)(b < 1 ? 1 : b);
+}
+
+void launch_spmv(const GeoDev& G, const double* diag, const double* off, const double* x,
+                 int64_t ldx, double* y, int64_t ldy, int nrhs, double* partial, cudaStream_t s) {
+  dim3 grid(vec_blocks(G.N), nrhs);
+  k_spmv<<<grid, kVecThreads, 0, s>>>(G, diag, off, x, ldx, y, ldy, partial);
+}
+void launch_dot_partial(int64_t N, const double* a, int64_t lda, const double* b, int64_t ldb,
+                        int nrhs, double* partial, cudaStream_t s) {
+  dim3 grid(vec_blocks(N), nrhs);
+  k_dot_partial<<<grid, kVecThreads, 0, s>>>(N, a, lda, b, ldb, partial);
+}
+void launch_reduce(const double* partial, int nblk, int nrhs, double* sc, int mode, double rtol,
+                   cudaStream_t s) {
+  k_reduce<<<nrhs, 256, 0, s>>>(partial, nblk, sc, mode, rtol);
+}
+void launch_update_xr(int64_t N, int nrhs, const double* sc, double* x, int64_t ldx, double* r,
+                      int64_t ldr, const double* p, int64_t ldp, const double* q, int64_t ldq,
+                      double* partial, cudaStream_t s) {
+  dim3 grid(vec_blocks(N), nrhs);
+  k_update_xr<<<grid, kVecThreads, 0, s>>>(N, sc, x, ldx, r, ldr, p, ldp, q, ldq, partial);
+}
+void launch_update_p(int64_t N, int nrhs, const double* sc, const double* z, int64_t ldz, double* p,
+                     int64_t ldp, int first, cudaStream_t s) {
+  dim3 grid(vec_blocks(N), nrhs);
+  k_update_p<<<grid, kVecThreads, 0, s>>>(N, sc, z, ldz, p, ldp, first);
+}
+void launch_sub(int64_t N, int nrhs, const double* a, int64_t lda, const double* b, int64_t ldb,
+                double* y, int64_t ldy, cudaStream_t s) {
+  dim3 grid(vec_blocks(N), nrhs);
+  k_sub<<<grid, kVecThreads, 0, s>>>(N, a, lda, b, ldb, y, ldy);
+}
+void launch_copy_cols(int64_t N, int nrhs, const double* a, int64_t lda, double* y, int64_t ldy,
+                      cudaStream_t s) {
+  dim3 grid(vec_blocks(N), nrhs);
+  k_copy_cols<<<grid, kVecThreads, 0, s>>>(N, a, lda, y, ldy);
+}
+
+// ---------------------------------------------------------------------------
+// finite-difference assembly (Eq. 1.1, Secs. 3.1/3.2) and the log-coefficient gradient
+// ---------------------------------------------------------------------------
+
+__device__ inline int64_t nb_sum(int c, int n) {   // sum_{v=0}^{c-1} ([v>0] + [v<n-1])
+  return (int64_t)max(c - 1, 0) + (int64_t)min(c, n - 1);
+}
+__device__ inline int nb_one(int v, int n) { return (v > 0) + (v < n - 1); }
+
+// mean of the per-pixel coefficient over the pixels touching the grid edge that
+// starts at node coordinates x (1-based, boundary nodes allowed) along axis ax
+__device__ double edge_weight(const GeoDev& G, const double* a_pix, const int x[3], int ax) {
+  double s = 0.0;
+  int cnt = 0;
+  const int nx = G.ns[0] + 1, ny = G.ns[1] + 1;
+  for (int m = 0; m < (1 << (G.d - 1)); ++m) {
+    int p[3] = {0, 0, 0};
+    int bit = 0;
+    for (int a = 0; a < G.d; ++a) {
+      if (a == ax) p[a] = x[a];
+      else { p[a] = x[a] - 1 + ((m >> bit) & 1); ++bit; }
+    }
+    s += a_pix[p[0] + (int64_t)nx * (p[1] + (int64_t)ny * p[2])];
+    ++cnt;
+  }
+  return s / cnt;
+}
+
+__global__ void k_assemble_fd(GeoDev G, const double* a_pix, const double* b_node, double b_const,
+                              int64_t* rowptr, int32_t* col, double* val) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= G.N) return;
+  int x[3] = {0, 0, 0};   // 0-based
+  int64_t rem = i;
+  for (int a = 0; a < G.d; ++a) {
+    x[a] = (int)(rem % G.ns[a]);
+    rem /= G.ns[a];
+  }
+  // rows before i, counted slab by slab from the last axis
+  int64_t before = 0, rows_before = 0;
+  {
+    int64_t inner = 1;   // rows in one slab of the lower axes
+    for (int a = 0; a < G.d; ++a) inner *= G.ns[a];
+    for (int a = G.d - 1; a >= 0; --a) {
+      inner /= G.ns[a];
+      // rows with coordinate a in [0, x[a]) and equal higher coordinates: box [0,n_0)x..x[0,x[a])x{x_{a+1}}..
+      const int64_t cnt = inner * x[a];
+      rows_before += cnt;
+      int64_t nbs = cnt;   // diagonal entries
+      for (int b = 0; b < G.d; ++b) {
+        int64_t sb;
+        if (b < a) sb = nb_sum(G.ns[b], G.ns[b]) * (cnt / G.ns[b]);
+        else if (b == a) sb = nb_sum(x[a], G.ns[a]) * inner;
+        else sb = (int64_t)nb_one(x[b], G.ns[b]) * cnt;
+        nbs += sb;
+      }
+      before += nbs;
+    }
+  }
+  rowptr[i] = before;
+  if (i == G.N - 1) {
+    int64_t own = 1;
+    for (int a = 0; a < G.d; ++a) own += nb_one(x[a], G.ns[a]);
+    rowptr[G.N] = before + own;
+  }
+  int x1[3] = {1, 1, 1};
+  for (int a = 0; a < G.d; ++a) x1[a] = x[a] + 1;
+  double diag = b_node ? b_node[i] : b_const;
+  double offv[3][2];
+  for (int a = 0; a < G.d; ++a) {
+    const double h = 1.0 / (G.ns[a] + 1);
+    int xl[3] = {x1[0], x1[1], x1[2]};
+    xl[a] = x1[a] - 1;
+    const double wl = edge_weight(G, a_pix, xl, a) / (h * h);   // edge from x-1 to x
+    const double wr = edge_weight(G, a_pix, x1, a) / (h * h);   // edge from x to x+1
+    diag += wl + wr;
+    offv[a][0] = -wl;
+    offv[a][1] = -wr;
+  }
+  int64_t k = before;
+  for (int a = G.d - 1; a >= 0; --a)
+    if (x[a] >= 1) { col[k] = (int32_t)(i - G.stride[a]); val[k] = offv[a][0]; ++k; }
+  col[k] = (int32_t)i; val[k] = diag; ++k;
+  for (int a = 0; a < G.d; ++a)
+    if (x[a] + 1 < G.ns[a]) { col[k] = (int32_t)(i + G.stride[a]); val[k] = offv[a][1]; ++k; }
+}
+
+void launch_assemble_fd(const GeoDev& G, const double* a_pix, const double* b_node, double b_const,
+                        int64_t* rowptr, int32_t* col, double* val, cudaStream_t s) {
+  if (!G.N) return;
+  k_assemble_fd<<<(unsigned)((G.N + 255) / 256), 256, 0, s>>>(G, a_pix, b_node, b_const, rowptr, col, val);
+}
+
+// one thread per pixel: -a_p / 2^(d-1) * sum over the 2^(d-1)*d grid edges of
+// pixel p of (lam_i - lam_j)(u_i - u_j)/h^2, u = lam = 0 on boundary nodes
+__global__ void k_grad_logcoef(GeoDev G, const double* a_pix, const double* u, const double* lam,
+                               double* grad, int64_t npix) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= npix) return;
+  int pc[3] = {0, 0, 0};
+  int64_t rem = p;
+  for (int a = 0; a < G.d; ++a) {
+    pc[a] = (int)(rem % (G.ns[a] + 1));
+    rem /= (G.ns[a] + 1);
+  }
+  auto node = [&](const int c[3], const double* v) -> double {
+    int64_t id = 0, mul = 1;
+    for (int a = 0; a < G.d; ++a) {
+      if (c[a] < 1 || c[a] > G.ns[a]) return 0.0;
+      id += (int64_t)(c[a] - 1) * mul;
+      mul *= G.ns[a];
+    }
+    return v[id];
+  };
+  double acc = 0.0;
+  for (int ax = 0; ax < G.d; ++ax) {
+    const double h = 1.0 / (G.ns[ax] + 1);
+    for (int m = 0; m < (1 << (G.d - 1)); ++m) {
+      int c0[3] = {0, 0, 0};
+      int bit = 0;
+      for (int a = 0; a < G.d; ++a) {
+        if (a == ax) c0[a] = pc[a];
+        else { c0[a] = pc[a] + ((m >> bit) & 1); ++bit; }
+      }
+      int c1[3] = {c0[0], c0[1], c0[2]};
+      c1[ax] += 1;
+      acc += (node(c1, u) - node(c0, u)) * (node(c1, lam) - node(c0, lam)) / (h * h);
+    }
+  }
+  grad[p] = -a_pix[p] * acc / double(1 << (G.d - 1));
+}
+
+void launch_grad_logcoef(const GeoDev& G, const double* a_pix, const double* u, const double* lam,
+                         double* grad, cudaStream_t s) {
+  int64_t npix = 1;
+  for (int a = 0; a < G.d; ++a) npix *= (G.ns[a] + 1);
+  k_grad_logcoef<<<(unsigned)((npix + 255) / 256), 256, 0, s>>>(G, a_pix, u, lam, grad, npix);
+}
+
+}  // namespace rhif

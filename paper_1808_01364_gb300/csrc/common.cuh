@@ -1,0 +1,230 @@
+// Device building blocks shared by the factorization and application kernels:
+// status reporting, warp/CTA reductions, the CTA-wide blocked partial
+// Cholesky of a dense front (Sec. 2.1 block elimination), and CTA-wide
+// triangular solves.  All matrices are column-major; only the lower triangle
+// of a symmetric matrix is read or written.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rhif {
+
+constexpr int kThreads = 256;   // threads per CTA of the dense kernels
+constexpr int kNB = 32;         // panel width of the partial Cholesky
+constexpr int kTile = 64;       // SYRK output tile
+constexpr int kKC = 32;         // SYRK k-chunk
+
+// status word layout (device int[8]): [0] error code, [1] level, [2] kind, [3] index
+enum StatusKind { kKindCell = 1, kKindGroup = 2, kKindUnit = 3, kKindRoot = 4, kKindArg = 5 };
+
+__device__ inline void report(int* status, int code, int level, int kind, int index) {
+  if (atomicCAS(status, 0, code) == 0) {
+    status[1] = level;
+    status[2] = kind;
+    status[3] = index;
+  }
+}
+
+template <typename T>
+__device__ inline T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename T> __device__ inline T my_sqrt(T x);
+template <> __device__ inline double my_sqrt<double>(double x) { return sqrt(x); }
+template <> __device__ inline float my_sqrt<float>(float x) { return sqrtf(x); }
+
+// Element (i, j) of a symmetric matrix stored in its lower triangle.
+template <typename T>
+__device__ inline T sym_at(const T* A, int64_t ld, int i, int j) {
+  return i >= j ? A[i + (int64_t)j * ld] : A[j + (int64_t)i * ld];
+}
+
+// C[i,j] -= sum_{k in [k0,k1)} A[i,k] * A[j,k] for i in [r0,r1), j in [c0,c1), i >= j.
+// The operand panels are columns [k0,k1) of the same matrix A.
+template <typename T>
+__device__ void cta_syrk_lower(T* A, int64_t ld, int r0, int r1, int c0, int c1, int k0, int k1,
+                               T* sm) {
+  if (r0 >= r1 || c0 >= c1 || k0 >= k1) return;
+  T* si = sm;                          // [kKC][kTile+1]
+  T* sj = sm + kKC * (kTile + 1);      // [kKC][kTile+1]
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  for (int ti = r0; ti < r1; ti += kTile) {
+    for (int tj = c0; tj < c1; tj += kTile) {
+      if (tj > ti + kTile - 1) break;   // tile entirely above the diagonal
+      T acc[4][4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+      for (int kc = k0; kc < k1; kc += kKC) {
+        const int kk = min(kKC, k1 - kc);
+        for (int idx = tid; idx < kTile * kKC; idx += kThreads) {
+          const int i = idx % kTile, k = idx / kTile;
+          const int gi = ti + i, gj = tj + i;
+          si[k * (kTile + 1) + i] = (gi < r1 && k < kk) ? A[gi + (int64_t)(kc + k) * ld] : T(0);
+          sj[k * (kTile + 1) + i] = (gj < c1 && k < kk) ? A[gj + (int64_t)(kc + k) * ld] : T(0);
+        }
+        __syncthreads();
+        for (int k = 0; k < kk; ++k) {
+          T av[4], bv[4];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) av[a] = si[k * (kTile + 1) + ty + 16 * a];
+#pragma unroll
+          for (int b = 0; b < 4; ++b) bv[b] = sj[k * (kTile + 1) + tx + 16 * b];
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
+        }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const int i = ti + ty + 16 * a;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int j = tj + tx + 16 * b;
+          if (i < r1 && j < c1 && i >= j) A[i + (int64_t)j * ld] -= acc[a][b];
+        }
+      }
+    }
+  }
+}
+
+// Shared memory (elements of T) needed by cta_partial_chol.
+constexpr int partial_chol_smem_elems() { return kNB * (kNB + 1) + 2 * kKC * (kTile + 1); }
+
+// Blocked partial Cholesky of the n x n SPD front A (lower triangle, ld):
+// eliminates the first nI unknowns (Sec. 2.1, Eq. 2.1).  On return
+//   A[0:nI, 0:nI]  holds L        with A_II = L L^T,
+//   A[nI:n, 0:nI]  holds W = A_BI L^{-T} (= X^T of the paper),
+//   A[nI:n, nI:n]  holds the Schur complement A_BB - W W^T.
+// Returns false (and leaves garbage) if a pivot is not positive.
+template <typename T>
+__device__ bool cta_partial_chol(T* A, int64_t ld, int n, int nI, T* sm) {
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  T* D = sm;                                   // [kNB][kNB+1] row-major
+  T* syrk_sm = sm + kNB * (kNB + 1);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  for (int p0 = 0; p0 < nI; p0 += kNB) {
+    const int nb = min(kNB, nI - p0);
+    const int p1 = p0 + nb;
+    for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
+      const int i = idx % nb, j = idx / nb;
+      D[i * (kNB + 1) + j] = (i >= j) ? A[(p0 + i) + (int64_t)(p0 + j) * ld] : T(0);
+    }
+    __syncthreads();
+    if (warp == 0) {
+      for (int k = 0; k < nb; ++k) {
+        T dkk = D[k * (kNB + 1) + k];
+        if (!(dkk > T(0))) {
+          if (lane == 0) bad = 1;
+          dkk = T(1);
+        }
+        const T s = my_sqrt(dkk);
+        __syncwarp();
+        if (lane > k && lane < nb) D[lane * (kNB + 1) + k] /= s;
+        if (lane == k) D[k * (kNB + 1) + k] = s;
+        __syncwarp();
+        if (lane > k && lane < nb) {
+          const T lik = D[lane * (kNB + 1) + k];
+          for (int j = k + 1; j <= lane; ++j) D[lane * (kNB + 1) + j] -= lik * D[j * (kNB + 1) + k];
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
+      const int i = idx % nb, j = idx / nb;
+      if (i >= j) A[(p0 + i) + (int64_t)(p0 + j) * ld] = D[i * (kNB + 1) + j];
+    }
+    // panel rows below the diagonal block: row <- row * D^{-T}
+    for (int i = p1 + threadIdx.x; i < n; i += blockDim.x) {
+      T r[kNB];
+#pragma unroll
+      for (int j = 0; j < kNB; ++j) r[j] = (j < nb) ? A[i + (int64_t)(p0 + j) * ld] : T(0);
+#pragma unroll
+      for (int j = 0; j < kNB; ++j) {
+        if (j < nb) {
+          T s = r[j];
+#pragma unroll
+          for (int q = 0; q < j; ++q) s -= r[q] * D[j * (kNB + 1) + q];
+          r[j] = s / D[j * (kNB + 1) + j];
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < kNB; ++j)
+        if (j < nb) A[i + (int64_t)(p0 + j) * ld] = r[j];
+    }
+    __syncthreads();
+    // trailing update restricted to the columns still to be eliminated
+    cta_syrk_lower(A, ld, p1, n, p1, nI, p0, p1, syrk_sm);
+    __syncthreads();
+  }
+  // Schur complement of the boundary block in one pass over k = 0..nI
+  cta_syrk_lower(A, ld, nI, n, nI, n, 0, nI, syrk_sm);
+  __syncthreads();
+  return bad == 0;
+}
+
+// y <- L^{-1} y for the n x n lower-triangular L (ld), y in shared memory.
+template <typename T>
+__device__ void cta_trsv_lower(const T* L, int64_t ld, int n, T* y) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int b0 = 0; b0 < n; b0 += 32) {
+    const int nb = min(32, n - b0);
+    if (warp == 0) {
+      T yi = lane < nb ? y[b0 + lane] : T(0);
+      for (int k = 0; k < nb; ++k) {
+        const T yk = __shfl_sync(0xffffffffu, yi, k) / L[(b0 + k) + (int64_t)(b0 + k) * ld];
+        if (lane == k) yi = yk;
+        else if (lane > k && lane < nb) yi -= L[(b0 + lane) + (int64_t)(b0 + k) * ld] * yk;
+      }
+      if (lane < nb) y[b0 + lane] = yi;
+    }
+    __syncthreads();
+    for (int i = b0 + nb + threadIdx.x; i < n; i += blockDim.x) {
+      T s = T(0);
+      for (int k = 0; k < nb; ++k) s += L[i + (int64_t)(b0 + k) * ld] * y[b0 + k];
+      y[i] -= s;
+    }
+    __syncthreads();
+  }
+}
+
+// y <- L^{-T} y for the n x n lower-triangular L (ld), y in shared memory.
+template <typename T>
+__device__ void cta_trsv_lower_t(const T* L, int64_t ld, int n, T* y) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  if (n <= 0) return;
+  for (int b0 = ((n - 1) / 32) * 32; b0 >= 0; b0 -= 32) {
+    const int nb = min(32, n - b0);
+    const int below = b0 + nb;
+    for (int k = warp; k < nb; k += nwarps) {
+      T s = T(0);
+      for (int i = below + lane; i < n; i += 32) s += L[i + (int64_t)(b0 + k) * ld] * y[i];
+      s = warp_sum(s);
+      if (lane == 0) y[b0 + k] -= s;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      T yi = lane < nb ? y[b0 + lane] : T(0);
+      for (int k = nb - 1; k >= 0; --k) {
+        T c = (lane > k && lane < nb) ? L[(b0 + lane) + (int64_t)(b0 + k) * ld] * yi : T(0);
+        c = warp_sum(c);
+        if (lane == k) yi = (yi - c) / L[(b0 + k) + (int64_t)(b0 + k) * ld];
+      }
+      if (lane < nb) y[b0 + lane] = yi;
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace rhif

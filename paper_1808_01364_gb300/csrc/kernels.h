@@ -1,0 +1,70 @@
+// Host launchers of the CUDA kernels (factor_kernels.cu, apply_kernels.cu).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "tables.h"
+
+namespace rhif {
+
+// PCG scalar slots (8 doubles per right-hand side)
+enum { kScRZ = 0, kScPQ = 1, kScRR = 2, kScFF = 3, kScAlpha = 4, kScDone = 5, kScBeta = 6 };
+
+void launch_stencil_from_csr(const GeoDev& G, const int64_t* rowptr, const int32_t* col,
+                             const double* val, int64_t nnz, double* diag, double* off,
+                             double* offb, int* status, cudaStream_t s);
+template <typename T>
+void launch_front_leaf(const GeoDev& G, const LevelDev& Lv, const double* diag, const double* off,
+                       int* status, cudaStream_t s);
+template <typename T>
+void launch_extend_add(const LevelDev& cur, const LevelDev& prev, cudaStream_t s);
+template <typename T>
+void launch_partial_chol(const LevelDev& Lv, int* status, cudaStream_t s);
+template <typename T>
+void launch_precond_diag(const LevelDev& Lv, const PhaseDev& Ph, int* status, cudaStream_t s);
+template <typename T>
+void launch_precond_scale(const LevelDev& Lv, const PhaseDev& Ph, cudaStream_t s);
+template <typename T>
+void launch_skel(const LevelDev& Lv, const PhaseDev& Ph, uint8_t* alive, double tol, int* status,
+                 cudaStream_t s);
+template <typename T>
+size_t skel_smem_bytes(int max_n);
+template <typename T>
+int configure_factor_kernels();
+
+template <typename T>
+void launch_apply_cell_up(const LevelDev& Lv, double* x, int64_t ldx, int nrhs, double* ubuf,
+                          int64_t ldu, cudaStream_t s);
+template <typename T>
+void launch_apply_cell_down(const LevelDev& Lv, double* x, int64_t ldx, int nrhs, cudaStream_t s);
+template <typename T>
+void launch_apply_group_up(const LevelDev& Lv, const PhaseDev& Ph, int gather, double* x,
+                           int64_t ldx, int nrhs, const double* ubuf, int64_t ldu, cudaStream_t s);
+template <typename T>
+void launch_apply_group_down(const LevelDev& Lv, const PhaseDev& Ph, double* x, int64_t ldx,
+                             int nrhs, cudaStream_t s);
+template <typename T>
+int configure_apply_kernels();
+
+int vec_blocks(int64_t N);
+void launch_spmv(const GeoDev& G, const double* diag, const double* off, const double* x,
+                 int64_t ldx, double* y, int64_t ldy, int nrhs, double* partial, cudaStream_t s);
+void launch_dot_partial(int64_t N, const double* a, int64_t lda, const double* b, int64_t ldb,
+                        int nrhs, double* partial, cudaStream_t s);
+void launch_reduce(const double* partial, int nblk, int nrhs, double* sc, int mode, double rtol,
+                   cudaStream_t s);
+void launch_update_xr(int64_t N, int nrhs, const double* sc, double* x, int64_t ldx, double* r,
+                      int64_t ldr, const double* p, int64_t ldp, const double* q, int64_t ldq,
+                      double* partial, cudaStream_t s);
+void launch_update_p(int64_t N, int nrhs, const double* sc, const double* z, int64_t ldz, double* p,
+                     int64_t ldp, int first, cudaStream_t s);
+void launch_sub(int64_t N, int nrhs, const double* a, int64_t lda, const double* b, int64_t ldb,
+                double* y, int64_t ldy, cudaStream_t s);
+void launch_copy_cols(int64_t N, int nrhs, const double* a, int64_t lda, double* y, int64_t ldy,
+                      cudaStream_t s);
+void launch_assemble_fd(const GeoDev& G, const double* a_pix, const double* b_node, double b_const,
+                        int64_t* rowptr, int32_t* col, double* val, cudaStream_t s);
+void launch_grad_logcoef(const GeoDev& G, const double* a_pix, const double* u, const double* lam,
+                         double* grad, cudaStream_t s);
+
+}  // namespace rhif

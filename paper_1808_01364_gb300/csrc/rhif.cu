@@ -1,0 +1,867 @@
+// C ABI (include/rhif.h): factorization driver, application, PCG.
+//
+// The factorization runs level by level (Sec. 3.1 / 3.2).  The host plans a
+// level (plan.cpp), uploads its index tables in one copy, launches the batched
+// kernels of the level on the caller's stream, then reads back the skeleton
+// ranks and pivot orders (the only data-dependent sizes) to plan the next
+// level.  The root front A_L (Eq. 3.3) is level L of the same machinery.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/rhif.h"
+#include "kernels.h"
+#include "plan.h"
+#include "tables.h"
+
+namespace rhif {
+
+thread_local std::string g_detail;
+
+static int fail(int code, const std::string& msg) {
+  g_detail = msg;
+  return code;
+}
+
+#define CK(call)                                                                        \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) {                                                            \
+      return fail(e_ == cudaErrorMemoryAllocation ? RHIF_ERR_OOM : RHIF_ERR_CUDA,       \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                  \
+    }                                                                                   \
+  } while (0)
+
+// Device allocation, stream-ordered; every pointer is released by the handle.
+struct DevMem {
+  std::vector<void*> ptrs;
+  cudaStream_t s = nullptr;
+  size_t bytes = 0;
+  int get(void** p, size_t n) {
+    *p = nullptr;
+    if (n == 0) n = 16;
+    cudaError_t e = cudaMallocAsync(p, n, s);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(RHIF_ERR_OOM, "device allocation of " + std::to_string(n) + " bytes failed");
+    }
+    ptrs.push_back(*p);
+    bytes += n;
+    return RHIF_OK;
+  }
+  void release(void* p) {
+    for (auto& q : ptrs)
+      if (q == p) {
+        cudaFreeAsync(q, s);
+        q = nullptr;
+      }
+  }
+  void release_all() {
+    for (void* p : ptrs)
+      if (p) cudaFreeAsync(p, s);
+    ptrs.clear();
+  }
+};
+
+// Packs host vectors into one staging buffer and uploads it in one copy.
+struct Packer {
+  std::vector<char> host;
+  template <typename V>
+  size_t add(const std::vector<V>& v) {
+    size_t off = (host.size() + 15) & ~size_t(15);
+    host.resize(off + v.size() * sizeof(V));
+    if (!v.empty()) std::memcpy(host.data() + off, v.data(), v.size() * sizeof(V));
+    return off;
+  }
+};
+
+
+// ---------------------------------------------------------------------------
+// kernel instrumentation: launch counters per category, optional CUDA-event timing
+// ---------------------------------------------------------------------------
+enum Cat {
+  kCatStencil, kCatFrontLeaf, kCatExtendAdd, kCatPartialChol, kCatPrecondDiag, kCatPrecondScale,
+  kCatSkel, kCatApplyCellUp, kCatApplyCellDown, kCatApplyGroupUp, kCatApplyGroupDown, kCatSpmv,
+  kCatVector, kCatAssemble, kCatGrad, kNumCat
+};
+static const char* kCatName[kNumCat] = {
+    "stencil_from_csr", "front_leaf", "extend_add", "partial_chol", "precond_diag",
+    "precond_scale", "skel", "apply_cell_up", "apply_cell_down", "apply_group_up",
+    "apply_group_down", "spmv", "pcg_vector", "assemble_fd", "grad_logcoef"};
+struct KStat {
+  int64_t launches = 0;
+  double ms = 0, flops = 0, bytes = 0;
+};
+static KStat g_kstat[kNumCat];
+static bool g_timing = false;
+static std::mutex g_kmu;
+struct Pending {
+  int cat;
+  cudaEvent_t a, b;
+};
+static std::vector<Pending> g_pending;
+
+// Counts (and, with timing on, brackets with events) the launches issued while alive.
+struct Launch {
+  int cat;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr, b = nullptr;
+  Launch(int cat_, cudaStream_t s_, double flops, double bytes, int count = 1) : cat(cat_), s(s_) {
+    std::lock_guard<std::mutex> lk(g_kmu);
+    g_kstat[cat].launches += count;
+    g_kstat[cat].flops += flops;
+    g_kstat[cat].bytes += bytes;
+    if (g_timing) {
+      cudaEventCreate(&a);
+      cudaEventCreate(&b);
+      cudaEventRecord(a, s);
+    }
+  }
+  ~Launch() {
+    if (a) {
+      cudaEventRecord(b, s);
+      std::lock_guard<std::mutex> lk(g_kmu);
+      g_pending.push_back({cat, a, b});
+    }
+  }
+};
+
+static void add_work(int cat, double flops, double bytes) {
+  std::lock_guard<std::mutex> lk(g_kmu);
+  g_kstat[cat].flops += flops;
+  g_kstat[cat].bytes += bytes;
+}
+
+struct PhaseStore {
+  PhaseDev dev{};
+  std::vector<int> h_rank, h_perm;
+};
+
+struct LevelStore {
+  LevelPlan plan;
+  LevelDev dev{};
+  std::vector<PhaseStore> phases;
+  void* tables = nullptr;
+  // algorithmic work of one sweep direction of the application, per right-hand side
+  double cell_flops = 0, cell_bytes = 0;
+  std::vector<double> grp_flops, grp_bytes;   // per phase
+};
+
+}  // namespace rhif
+
+struct rhif_handle {
+  rhif::Geometry G;
+  rhif::GeoDev gd{};
+  int precision = RHIF_FP64;
+  bool precondition = true, edge_skel = false;
+  double tol = 0.0;
+  std::vector<rhif::LevelStore> levels;   // 0..L
+  double* diag = nullptr;
+  double* off = nullptr;
+  int* status = nullptr;
+  rhif::DevMem mem;
+  // reusable work space
+  double* ubuf = nullptr;
+  int64_t ubuf_elems = 0;
+  int64_t ub_len = 0;   // max over levels of sum nB
+  double* work = nullptr;
+  int64_t work_elems = 0;
+  double flops = 0.0, apply_bytes = 0.0, factor_ms = 0.0;
+  int units = 0;
+};
+
+namespace rhif {
+
+static GeoDev geo_dev(const Geometry& G) {
+  GeoDev g{};
+  g.d = G.d;
+  g.leaf = G.leaf;
+  for (int a = 0; a < 3; ++a) {
+    g.ns[a] = G.ns[a];
+    g.stride[a] = G.stride[a];
+  }
+  g.N = G.N;
+  return g;
+}
+
+template <typename T>
+static int configure_once() {
+  static int done = 0;
+  static int rc = 0;
+  if (!done) {
+    rc = configure_factor_kernels<T>();
+    if (rc == 0) rc = configure_apply_kernels<T>();
+    done = 1;
+  }
+  return rc;
+}
+
+// Upload the index tables of a level and fill the device views.
+static int upload_level(rhif_handle* H, LevelStore& S, size_t elem) {
+  const LevelPlan& P = S.plan;
+  Packer pk;
+  const size_t o_code = pk.add(P.cell_code), o_foff = pk.add(P.front_off), o_nI = pk.add(P.nI),
+               o_nB = pk.add(P.nB), o_goff = pk.add(P.gid_off), o_gids = pk.add(P.gids),
+               o_boff = pk.add(P.b_off), o_soff = pk.add(P.seg_off), o_sg = pk.add(P.seg_group),
+               o_sp = pk.add(P.seg_pos), o_gt = pk.add(P.group_t),
+               o_ggo = pk.add(P.group_gid_off), o_ggid = pk.add(P.group_gids),
+               o_gco = pk.add(P.group_cell_off), o_gc = pk.add(P.group_cell),
+               o_gp = pk.add(P.group_pos), o_eao = pk.add(P.ea_off), o_eac = pk.add(P.ea_child),
+               o_eamo = pk.add(P.ea_map_off), o_eam = pk.add(P.ea_map);
+  struct PhOff {
+    size_t pg, po, gp, ug, un, uro, urg, rso, sc, sp, su, umo, uro2, upo, gu;
+  };
+  std::vector<PhOff> po(P.phases.size());
+  for (size_t i = 0; i < P.phases.size(); ++i) {
+    const PhasePlan& ph = P.phases[i];
+    const UnitTable& U = ph.units;
+    po[i] = {pk.add(ph.pre_group), pk.add(ph.pre_off), pk.add(ph.group_pre), pk.add(U.group),
+             pk.add(U.nrow), pk.add(U.row_off), pk.add(U.row_gid), pk.add(U.row_src_off),
+             pk.add(U.src_cell), pk.add(U.src_pos), pk.add(U.src_upos), pk.add(U.m_off),
+             pk.add(U.rec_off), pk.add(U.perm_off), pk.add(ph.group_unit)};
+  }
+  void* d = nullptr;
+  int rc = H->mem.get(&d, pk.host.size());
+  if (rc) return rc;
+  S.tables = d;
+  CK(cudaMemcpyAsync(d, pk.host.data(), pk.host.size(), cudaMemcpyHostToDevice, H->mem.s));
+  // the staging buffer must outlive the copy
+  CK(cudaStreamSynchronize(H->mem.s));
+  char* b = (char*)d;
+  LevelDev& L = S.dev;
+  L.level = P.level;
+  L.ncell = P.ncell();
+  L.ngroup = P.ngroup();
+  L.width = P.width;
+  L.code_base = 2 * (1 << (H->G.L - P.level)) + 1;
+  L.cell_code = (const int64_t*)(b + o_code);
+  L.max_nI = P.max_nI;
+  L.max_nB = P.max_nB;
+  L.max_n = P.max_n;
+  L.max_group = P.max_group;
+  L.front_off = (const int64_t*)(b + o_foff);
+  L.nI = (const int*)(b + o_nI);
+  L.nB = (const int*)(b + o_nB);
+  L.gid_off = (const int64_t*)(b + o_goff);
+  L.gids = (const int64_t*)(b + o_gids);
+  L.b_off = (const int64_t*)(b + o_boff);
+  L.seg_off = (const int*)(b + o_soff);
+  L.seg_group = (const int*)(b + o_sg);
+  L.seg_pos = (const int*)(b + o_sp);
+  L.group_t = (const int*)(b + o_gt);
+  L.group_gid_off = (const int64_t*)(b + o_ggo);
+  L.group_gids = (const int64_t*)(b + o_ggid);
+  L.group_cell_off = (const int*)(b + o_gco);
+  L.group_cell = (const int*)(b + o_gc);
+  L.group_pos = (const int*)(b + o_gp);
+  L.ea_off = (const int*)(b + o_eao);
+  L.ea_child = (const int*)(b + o_eac);
+  L.ea_map_off = (const int64_t*)(b + o_eamo);
+  L.ea_map = (const int*)(b + o_eam);
+  rc = H->mem.get(&L.front, P.front_total * elem);
+  if (rc) return rc;
+  S.phases.resize(P.phases.size());
+  for (size_t i = 0; i < P.phases.size(); ++i) {
+    const PhasePlan& ph = P.phases[i];
+    const UnitTable& U = ph.units;
+    PhaseDev& D = S.phases[i].dev;
+    D.unit_type = ph.unit_type;
+    D.pre_min_type = ph.pre_min_type;
+    D.npre = (int)ph.pre_group.size();
+    D.pre_group = (const int*)(b + po[i].pg);
+    D.pre_off = (const int64_t*)(b + po[i].po);
+    D.group_pre = (const int*)(b + po[i].gp);
+    D.nunit = (int)U.group.size();
+    D.max_n = U.max_n;
+    D.u_group = (const int*)(b + po[i].ug);
+    D.u_nrow = (const int*)(b + po[i].un);
+    D.u_row_off = (const int64_t*)(b + po[i].uro);
+    D.u_row_gid = (const int64_t*)(b + po[i].urg);
+    D.row_src_off = (const int64_t*)(b + po[i].rso);
+    D.src_cell = (const int*)(b + po[i].sc);
+    D.src_pos = (const int*)(b + po[i].sp);
+    D.src_upos = (const int*)(b + po[i].su);
+    D.u_m_off = (const int64_t*)(b + po[i].umo);
+    D.u_rec_off = (const int64_t*)(b + po[i].uro2);
+    D.u_perm_off = (const int64_t*)(b + po[i].upo);
+    D.group_unit = (const int*)(b + po[i].gu);
+    if ((rc = H->mem.get(&D.Lbuf, ph.pre_total * elem))) return rc;
+    if ((rc = H->mem.get(&D.rec, U.rec_total * elem))) return rc;
+    if ((rc = H->mem.get((void**)&D.perm, U.perm_total * sizeof(int)))) return rc;
+    if ((rc = H->mem.get((void**)&D.rank, U.group.size() * sizeof(int)))) return rc;
+    D.Mbuf = nullptr;
+  }
+  return RHIF_OK;
+}
+
+static int check_status(rhif_handle* H, const char* where) {
+  int st[4] = {0, 0, 0, 0};
+  CK(cudaMemcpyAsync(st, H->status, sizeof(st), cudaMemcpyDeviceToHost, H->mem.s));
+  CK(cudaStreamSynchronize(H->mem.s));
+  CK(cudaGetLastError());
+  if (st[0] == 0) return RHIF_OK;
+  static const char* kinds[] = {"?", "cell", "group", "unit", "root", "argument"};
+  char buf[256];
+  const int kind = (st[2] >= 0 && st[2] <= 5) ? st[2] : 0;
+  std::snprintf(buf, sizeof(buf), "%s: %s at level %d, %s %d", where,
+                st[0] == RHIF_ERR_NOT_SPD ? "non-positive pivot (not SPD)" : "invalid input",
+                st[1], kinds[kind], st[3]);
+  return fail(st[0], buf);
+}
+
+static double cell_flops(double nI, double nB) {
+  return nI * nI * nI / 3.0 + nI * nI * nB + nI * nB * nB;
+}
+
+template <typename T>
+static int factor_impl(rhif_handle* H, const rhif_csr* A) {
+  const Geometry& G = H->G;
+  cudaStream_t s = H->mem.s;
+  const size_t elem = sizeof(T);
+  int rc = configure_once<T>();
+  if (rc) return fail(RHIF_ERR_CUDA, "cannot configure kernel shared memory");
+  double* offb = nullptr;
+  uint8_t* alive_d = nullptr;
+  if ((rc = H->mem.get((void**)&H->diag, G.N * sizeof(double)))) return rc;
+  if ((rc = H->mem.get((void**)&H->off, G.d * G.N * sizeof(double)))) return rc;
+  if ((rc = H->mem.get((void**)&offb, G.d * G.N * sizeof(double)))) return rc;
+  if ((rc = H->mem.get((void**)&H->status, 8 * sizeof(int)))) return rc;
+  if ((rc = H->mem.get((void**)&alive_d, G.N))) return rc;
+  CK(cudaMemsetAsync(H->off, 0, G.d * G.N * sizeof(double), s));
+  CK(cudaMemsetAsync(offb, 0, G.d * G.N * sizeof(double), s));
+  CK(cudaMemsetAsync(H->status, 0, 8 * sizeof(int), s));
+  CK(cudaMemsetAsync(alive_d, 1, G.N, s));
+  {
+    Launch t(kCatStencil, s, 0.0, double(A->nnz) * 12 + G.N * (8.0 + 24.0 * G.d), 2);
+    launch_stencil_from_csr(H->gd, A->rowptr, A->col, A->val, A->nnz, H->diag, H->off, offb,
+                            H->status, s);
+  }
+  if ((rc = check_status(H, "CSR pattern check"))) return rc;
+  H->mem.release(offb);
+
+  std::vector<uint8_t> alive(G.N, 1);
+  H->levels.resize(G.L + 1);
+  for (int lvl = 0; lvl <= G.L; ++lvl) {
+    LevelStore& S = H->levels[lvl];
+    const LevelPlan* prev = lvl ? &H->levels[lvl - 1].plan : nullptr;
+    S.plan = build_level(G, lvl, alive, prev, H->precondition, H->edge_skel);
+    if ((rc = upload_level(H, S, elem))) return rc;
+    const LevelPlan& P = S.plan;
+    H->ub_len = std::max<int64_t>(H->ub_len, P.b_off.back());
+    double lvl_flops = 0.0, front_bytes = double(P.front_total) * elem;
+    for (int c = 0; c < P.ncell(); ++c) {
+      lvl_flops += cell_flops(P.nI[c], P.nB[c]);
+      const double nI = P.nI[c], nB = P.nB[c];
+      H->apply_bytes += 2.0 * elem * (nI * (nI + 1) / 2 + nI * nB);
+    }
+    H->flops += lvl_flops;
+    if (lvl == 0) {
+      Launch t(kCatFrontLeaf, s, 0.0, front_bytes);
+      launch_front_leaf<T>(H->gd, S.dev, H->diag, H->off, H->status, s);
+    } else {
+      Launch t(kCatExtendAdd, s, 0.0, front_bytes);
+      launch_extend_add<T>(S.dev, H->levels[lvl - 1].dev, s);
+    }
+    {
+      Launch t(kCatPartialChol, s, lvl_flops, front_bytes);
+      launch_partial_chol<T>(S.dev, H->status, s);
+    }
+    for (size_t ip = 0; ip < P.phases.size(); ++ip) {
+      const PhasePlan& ph = P.phases[ip];
+      PhaseDev& D = S.phases[ip].dev;
+      void* M = nullptr;
+      if ((rc = H->mem.get(&M, ph.units.m_total * elem))) return rc;
+      D.Mbuf = M;
+      double dflops = 0.0, sflops = 0.0;
+      for (int gi : ph.pre_group) {
+        const double g = double(P.group_gid_off[gi + 1] - P.group_gid_off[gi]);
+        dflops += g * g * g / 3.0;
+      }
+      for (int c = 0; c < P.ncell(); ++c)
+        for (int q = P.seg_off[c]; q < P.seg_off[c + 1]; ++q) {
+          const int gi = P.seg_group[q];
+          if (ph.group_pre[gi] < 0) continue;
+          const double g = double(P.group_gid_off[gi + 1] - P.group_gid_off[gi]);
+          sflops += 2.0 * g * g * P.nB[c];
+        }
+      if (!ph.pre_group.empty()) {
+        {
+          Launch t(kCatPrecondDiag, s, dflops, 0.0);
+          launch_precond_diag<T>(S.dev, D, H->status, s);
+        }
+        {
+          Launch t(kCatPrecondScale, s, sflops, 0.0);
+          launch_precond_scale<T>(S.dev, D, s);
+        }
+      }
+      const int64_t skel_slot = (int64_t)ph.units.group.size();
+      {
+        Launch t(kCatSkel, s, 0.0, 0.0, skel_slot ? 1 : 0);
+        launch_skel<T>(S.dev, D, alive_d, H->tol, H->status, s);
+      }
+      if ((rc = check_status(H, "skeletonization"))) return rc;
+      H->mem.release(M);
+      D.Mbuf = nullptr;
+      PhaseStore& PS = S.phases[ip];
+      PS.h_rank.resize(ph.units.group.size());
+      PS.h_perm.resize(ph.units.perm_total);
+      CK(cudaMemcpyAsync(PS.h_rank.data(), D.rank, PS.h_rank.size() * sizeof(int),
+                         cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(PS.h_perm.data(), D.perm, PS.h_perm.size() * sizeof(int),
+                         cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      H->flops += dflops + sflops;
+      for (int gi : ph.pre_group) {
+        const double g = double(P.group_gid_off[gi + 1] - P.group_gid_off[gi]);
+        H->apply_bytes += 2.0 * elem * g * (g + 1) / 2;
+      }
+      for (size_t u = 0; u < ph.units.group.size(); ++u) {
+        const int gi = ph.units.group[u];
+        const int64_t g0 = P.group_gid_off[gi];
+        const int n = (int)(P.group_gid_off[gi + 1] - g0);
+        const int k = PS.h_rank[u], r = n - k;
+        const int* pm = PS.h_perm.data() + ph.units.perm_off[u];
+        for (int i = k; i < n; ++i) alive[P.group_gids[g0 + pm[i]]] = 0;
+        const double m = ph.units.nrow[u];
+        const double uf = 4.0 * m * n * k - 2.0 * k * k * (m + n) + 4.0 * k * k * k / 3.0 +
+                          double(k) * k * r + cell_flops(r, k);
+        H->flops += uf;
+        add_work(kCatSkel, uf, 0.0);
+        H->apply_bytes += 2.0 * elem * (r * (r + 1) / 2.0 + 2.0 * r * k);
+        ++H->units;
+      }
+    }
+    if ((rc = check_status(H, lvl == G.L ? "root factorization" : "cell elimination"))) return rc;
+    for (int c = 0; c < P.ncell(); ++c) {
+      const double nI = P.nI[c], nB = P.nB[c];
+      S.cell_flops += nI * nI + 2.0 * nI * nB;
+      S.cell_bytes += elem * (nI * (nI + 1) / 2 + nI * nB) + 16.0 * (nI + nB);
+    }
+    S.grp_flops.assign(P.phases.size(), 0.0);
+    S.grp_bytes.assign(P.phases.size(), 0.0);
+    for (size_t ip = 0; ip < P.phases.size(); ++ip) {
+      const PhasePlan& ph = P.phases[ip];
+      for (int gi = 0; gi < P.ngroup(); ++gi) {
+        if (P.group_t[gi] < ph.pre_min_type) continue;
+        const double g = double(P.group_gid_off[gi + 1] - P.group_gid_off[gi]);
+        double f = 0, b = 16.0 * g;
+        if (ph.group_pre[gi] >= 0) { f += g * g; b += elem * g * (g + 1) / 2; }
+        const int u = ph.group_unit[gi];
+        if (u >= 0) {
+          const double k = S.phases[ip].h_rank[u], r = g - k;
+          f += r * r + 4.0 * r * k;
+          b += elem * (r * (r + 1) / 2 + 2.0 * r * k);
+        }
+        S.grp_flops[ip] += f;
+        S.grp_bytes[ip] += b;
+      }
+    }
+    for (int c = 0; c < P.ncell(); ++c)
+      for (int i = 0; i < P.nI[c]; ++i) alive[P.gids[P.gid_off[c] + i]] = 0;
+  }
+  H->mem.release(alive_d);
+  return RHIF_OK;
+}
+
+template <typename T>
+static int apply_impl(const rhif_handle* Hc, double* y, int64_t ldy, int nrhs, cudaStream_t s) {
+  rhif_handle* H = const_cast<rhif_handle*>(Hc);
+  const int L = H->G.L;
+  const int64_t need = H->ub_len * nrhs;
+  if (need > H->ubuf_elems) {
+    if (H->ubuf) H->mem.release(H->ubuf);
+    H->ubuf = nullptr;
+    int rc = H->mem.get((void**)&H->ubuf, need * sizeof(double));
+    if (rc) return rc;
+    H->ubuf_elems = need;
+  }
+  const int64_t ldu = H->ub_len;
+  for (int l = 0; l < L; ++l) {
+    LevelStore& S = H->levels[l];
+    {
+      Launch t(kCatApplyCellUp, s, S.cell_flops * nrhs, S.cell_bytes * nrhs);
+      launch_apply_cell_up<T>(S.dev, y, ldy, nrhs, H->ubuf, ldu, s);
+    }
+    for (size_t p = 0; p < S.phases.size(); ++p) {
+      Launch t(kCatApplyGroupUp, s, S.grp_flops[p] * nrhs, S.grp_bytes[p] * nrhs);
+      launch_apply_group_up<T>(S.dev, S.phases[p].dev, p == 0, y, ldy, nrhs, H->ubuf, ldu, s);
+    }
+  }
+  {
+    LevelStore& R = H->levels[L];
+    Launch t(kCatApplyCellUp, s, R.cell_flops * nrhs, R.cell_bytes * nrhs);
+    launch_apply_cell_up<T>(R.dev, y, ldy, nrhs, H->ubuf, ldu, s);
+  }
+  {
+    LevelStore& R = H->levels[L];
+    Launch t(kCatApplyCellDown, s, R.cell_flops * nrhs, R.cell_bytes * nrhs);
+    launch_apply_cell_down<T>(R.dev, y, ldy, nrhs, s);
+  }
+  for (int l = L - 1; l >= 0; --l) {
+    LevelStore& S = H->levels[l];
+    for (int p = (int)S.phases.size() - 1; p >= 0; --p) {
+      Launch t(kCatApplyGroupDown, s, S.grp_flops[p] * nrhs, S.grp_bytes[p] * nrhs);
+      launch_apply_group_down<T>(S.dev, S.phases[p].dev, y, ldy, nrhs, s);
+    }
+    Launch t(kCatApplyCellDown, s, S.cell_flops * nrhs, S.cell_bytes * nrhs);
+    launch_apply_cell_down<T>(S.dev, y, ldy, nrhs, s);
+  }
+  CK(cudaGetLastError());
+  return RHIF_OK;
+}
+
+static int apply_dispatch(const rhif_handle* H, double* y, int64_t ldy, int nrhs, cudaStream_t s) {
+  return H->precision == RHIF_FP64 ? apply_impl<double>(H, y, ldy, nrhs, s)
+                                   : apply_impl<float>(H, y, ldy, nrhs, s);
+}
+
+static int ensure_work(rhif_handle* H, int64_t elems) {
+  if (elems <= H->work_elems) return RHIF_OK;
+  if (H->work) H->mem.release(H->work);
+  H->work = nullptr;
+  int rc = H->mem.get((void**)&H->work, elems * sizeof(double));
+  if (rc) return rc;
+  H->work_elems = elems;
+  return RHIF_OK;
+}
+
+}  // namespace rhif
+
+using namespace rhif;
+
+extern "C" {
+
+int rhif_default_opts(rhif_opts* o) {
+  if (!o) return fail(RHIF_ERR_BAD_ARG, "null opts");
+  std::memset(o, 0, sizeof(*o));
+  o->precision = RHIF_FP64;
+  o->precondition = 1;
+  o->edge_skel_3d = 0;
+  return RHIF_OK;
+}
+
+static int check_grid(const rhif_grid* g) {
+  if (!g || (g->dim != 2 && g->dim != 3)) return fail(RHIF_ERR_BAD_ARG, "grid dim must be 2 or 3");
+  for (int a = 0; a < g->dim; ++a)
+    if (g->n[a] < 1) return fail(RHIF_ERR_BAD_ARG, "grid sizes must be >= 1");
+  int64_t N = 1;
+  for (int a = 0; a < g->dim; ++a) N *= g->n[a];
+  if (N >= (int64_t)1 << 31) return fail(RHIF_ERR_BAD_ARG, "more than 2^31 - 1 DOFs");
+  return RHIF_OK;
+}
+
+int64_t rhif_fd_nnz(const rhif_grid* g) {
+  if (check_grid(g)) return -1;
+  int64_t N = 1;
+  for (int a = 0; a < g->dim; ++a) N *= g->n[a];
+  int64_t nnz = N;
+  for (int a = 0; a < g->dim; ++a) nnz += 2 * (N / g->n[a]) * (g->n[a] - 1);
+  return nnz;
+}
+
+int rhif_assemble_fd(const rhif_grid* g, const double* a_pix, const double* b_node, double b_const,
+                     int64_t* rowptr, int32_t* col, double* val, void* stream) {
+  int rc = check_grid(g);
+  if (rc) return rc;
+  if (!a_pix || !rowptr || !col || !val) return fail(RHIF_ERR_BAD_ARG, "null pointer");
+  Geometry G = make_geometry(g->dim, g->n, 2);
+  {
+    Launch t(kCatAssemble, (cudaStream_t)stream, 0.0, 0.0);
+    launch_assemble_fd(geo_dev(G), a_pix, b_node, b_const, rowptr, col, val, (cudaStream_t)stream);
+  }
+  CK(cudaGetLastError());
+  return RHIF_OK;
+}
+
+int rhif_factor(const rhif_csr* A, const rhif_grid* g, int leaf, double tol, const rhif_opts* o,
+                void* stream, rhif_handle** out) {
+  if (!out) return fail(RHIF_ERR_BAD_ARG, "null output handle");
+  *out = nullptr;
+  int rc = check_grid(g);
+  if (rc) return rc;
+  if (!A || !A->rowptr || !A->col || !A->val) return fail(RHIF_ERR_BAD_ARG, "null CSR pointer");
+  if (leaf < 2) return fail(RHIF_ERR_BAD_ARG, "leaf must be >= 2");
+  if (!(tol >= 0.0) || !std::isfinite(tol)) return fail(RHIF_ERR_BAD_ARG, "tol must be finite and >= 0");
+  rhif_opts def;
+  rhif_default_opts(&def);
+  if (!o) o = &def;
+  if (o->precision != RHIF_FP64 && o->precision != RHIF_MIXED_FP32)
+    return fail(RHIF_ERR_BAD_ARG, "unknown precision");
+  std::unique_ptr<rhif_handle> H(new rhif_handle());
+  H->G = make_geometry(g->dim, g->n, leaf);
+  if (A->nrows != H->G.N) return fail(RHIF_ERR_BAD_ARG, "CSR rows != number of grid DOFs");
+  if (A->nnz < H->G.N) return fail(RHIF_ERR_BAD_ARG, "CSR has fewer entries than rows");
+  if (H->G.L > 20) return fail(RHIF_ERR_BAD_ARG, "too many levels");
+  H->gd = geo_dev(H->G);
+  H->precision = o->precision;
+  H->precondition = o->precondition != 0;
+  H->edge_skel = (g->dim == 3) && o->edge_skel_3d;
+  H->tol = tol;
+  H->mem.s = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, H->mem.s));
+  rc = H->precision == RHIF_FP64 ? factor_impl<double>(H.get(), A) : factor_impl<float>(H.get(), A);
+  if (rc) {
+    cudaStreamSynchronize(H->mem.s);
+    H->mem.release_all();
+    cudaStreamSynchronize(H->mem.s);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
+  }
+  CK(cudaEventRecord(e1, H->mem.s));
+  CK(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  H->factor_ms = ms;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *out = H.release();
+  return RHIF_OK;
+}
+
+int rhif_apply(const rhif_handle* F, int op, int nrhs, const double* x, int64_t ldx, double* y,
+               int64_t ldy, void* stream) {
+  if (!F || !x || !y || nrhs < 0) return fail(RHIF_ERR_BAD_ARG, "null argument");
+  if (op != RHIF_SOLVE) return fail(RHIF_ERR_BAD_ARG, "only RHIF_SOLVE is available");
+  const int64_t N = F->G.N;
+  if (ldx < N || ldy < N) return fail(RHIF_ERR_BAD_ARG, "leading dimension < N");
+  if (x == y && ldx != ldy) return fail(RHIF_ERR_BAD_ARG, "aliased x and y need ldx == ldy");
+  if (nrhs == 0) return RHIF_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (x != y) {
+    Launch t(kCatVector, s, 0.0, 16.0 * N * nrhs);
+    launch_copy_cols(N, nrhs, x, ldx, y, ldy, s);
+  }
+  return apply_dispatch(F, y, ldy, nrhs, s);
+}
+
+int rhif_spmv(const rhif_handle* F, int nrhs, const double* x, int64_t ldx, double* y, int64_t ldy,
+              void* stream) {
+  if (!F || !x || !y || nrhs < 0) return fail(RHIF_ERR_BAD_ARG, "null argument");
+  if (ldx < F->G.N || ldy < F->G.N) return fail(RHIF_ERR_BAD_ARG, "leading dimension < N");
+  if (nrhs == 0) return RHIF_OK;
+  {
+    const double N = double(F->G.N);
+    Launch t(kCatSpmv, (cudaStream_t)stream, 2.0 * (2 * F->G.d + 1) * N * nrhs,
+             (8.0 * (1 + F->G.d) + 16.0) * N * nrhs);
+    launch_spmv(F->gd, F->diag, F->off, x, ldx, y, ldy, nrhs, nullptr, (cudaStream_t)stream);
+  }
+  CK(cudaGetLastError());
+  return RHIF_OK;
+}
+
+int rhif_pcg(const rhif_handle* Fc, int nrhs, const double* f, int64_t ldf, double* u, int64_t ldu,
+             double rtol, int maxit, int* iters, double* relres, void* stream) {
+  rhif_handle* F = const_cast<rhif_handle*>(Fc);
+  if (!F || !f || !u || nrhs < 1 || maxit < 0 || !(rtol >= 0.0))
+    return fail(RHIF_ERR_BAD_ARG, "bad argument");
+  const int64_t N = F->G.N;
+  if (ldf < N || ldu < N) return fail(RHIF_ERR_BAD_ARG, "leading dimension < N");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nblk = vec_blocks(N);
+  const int64_t ld = N;
+  const double spmv_flops = 2.0 * (2 * F->G.d + 1) * N, spmv_bytes = (8.0 * (1 + F->G.d) + 16.0) * N;
+  // r, z, p, q (N x nrhs each), partials, two scalar blocks
+  const int64_t need = 4 * N * nrhs + (int64_t)nblk * nrhs + 16 * nrhs;
+  int rc = ensure_work(F, need);
+  if (rc) return rc;
+  double* r = F->work;
+  double* z = r + N * nrhs;
+  double* p = z + N * nrhs;
+  double* q = p + N * nrhs;
+  double* part = q + N * nrhs;
+  double* sc = part + (int64_t)nblk * nrhs;
+  double* sc2 = sc + 8 * nrhs;
+  CK(cudaMemsetAsync(sc, 0, 16 * nrhs * sizeof(double), s));
+  for (int c = 0; c < nrhs; ++c) CK(cudaMemsetAsync(u + c * ldu, 0, N * sizeof(double), s));
+  { Launch t_(kCatVector, s, 0.0, 0.0); launch_copy_cols(N, nrhs, f, ldf, r, ld, s); }
+  { Launch t_(kCatVector, s, 0.0, 0.0); launch_dot_partial(N, f, ldf, f, ldf, nrhs, part, s); }
+  { Launch t_(kCatVector, s, 0.0, 0.0); launch_reduce(part, nblk, nrhs, sc, 0, rtol, s); }
+  { Launch t_(kCatVector, s, 0.0, 0.0); launch_copy_cols(N, nrhs, r, ld, z, ld, s); }
+  if ((rc = apply_dispatch(F, z, ld, nrhs, s))) return rc;
+  { Launch t_(kCatVector, s, 0.0, 0.0); launch_dot_partial(N, r, ld, z, ld, nrhs, part, s); }
+  { Launch t_(kCatVector, s, 0.0, 0.0); launch_reduce(part, nblk, nrhs, sc, 1, rtol, s); }
+  { Launch t_(kCatVector, s, 0.0, 0.0); launch_update_p(N, nrhs, sc, z, ld, p, ld, 1, s); }
+  std::vector<double> hsc(8 * nrhs);
+  std::vector<int> it(nrhs, maxit);
+  std::vector<char> was_done(nrhs, 0);
+  int all_done = 0;
+  for (int k = 1; k <= maxit; ++k) {
+    { Launch t_(kCatSpmv, s, spmv_flops * nrhs, spmv_bytes * nrhs); launch_spmv(F->gd, F->diag, F->off, p, ld, q, ld, nrhs, part, s); }
+    { Launch t_(kCatVector, s, 0.0, 0.0); launch_reduce(part, nblk, nrhs, sc, 2, rtol, s); }
+    { Launch t_(kCatVector, s, 0.0, 0.0); launch_update_xr(N, nrhs, sc, u, ldu, r, ld, p, ld, q, ld, part, s); }
+    { Launch t_(kCatVector, s, 0.0, 0.0); launch_reduce(part, nblk, nrhs, sc, 3, rtol, s); }
+    CK(cudaMemcpyAsync(hsc.data(), sc, 8 * nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    int nd = 0;
+    for (int c = 0; c < nrhs; ++c) {
+      if (hsc[8 * c + kScDone] != 0.0) {
+        if (!was_done[c]) { it[c] = k; was_done[c] = 1; }
+        ++nd;
+      }
+    }
+    if (nd == nrhs) { all_done = 1; break; }
+    { Launch t_(kCatVector, s, 0.0, 0.0); launch_copy_cols(N, nrhs, r, ld, z, ld, s); }
+    if ((rc = apply_dispatch(F, z, ld, nrhs, s))) return rc;
+    { Launch t_(kCatVector, s, 0.0, 0.0); launch_dot_partial(N, r, ld, z, ld, nrhs, part, s); }
+    { Launch t_(kCatVector, s, 0.0, 0.0); launch_reduce(part, nblk, nrhs, sc, 4, rtol, s); }
+    { Launch t_(kCatVector, s, 0.0, 0.0); launch_update_p(N, nrhs, sc, z, ld, p, ld, 0, s); }
+  }
+  if (maxit == 0) {
+    CK(cudaMemcpyAsync(hsc.data(), sc, 8 * nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  // true residual
+  { Launch t_(kCatSpmv, s, spmv_flops * nrhs, spmv_bytes * nrhs); launch_spmv(F->gd, F->diag, F->off, u, ldu, q, ld, nrhs, nullptr, s); }
+  { Launch t_(kCatVector, s, 0.0, 0.0); launch_sub(N, nrhs, f, ldf, q, ld, r, ld, s); }
+  { Launch t_(kCatVector, s, 0.0, 0.0); launch_dot_partial(N, r, ld, r, ld, nrhs, part, s); }
+  { Launch t_(kCatVector, s, 0.0, 0.0); launch_reduce(part, nblk, nrhs, sc2, 1, rtol, s); }
+  std::vector<double> h2(8 * nrhs);
+  CK(cudaMemcpyAsync(h2.data(), sc2, 8 * nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  CK(cudaGetLastError());
+  for (int c = 0; c < nrhs; ++c) {
+    const double ff = hsc[8 * c + kScFF];
+    if (iters) iters[c] = it[c];
+    if (relres) relres[c] = ff > 0 ? std::sqrt(h2[8 * c + kScRZ] / ff) : 0.0;
+  }
+  if (!all_done) return fail(RHIF_ERR_NOT_CONVERGED, "PCG reached maxit before rtol");
+  return RHIF_OK;
+}
+
+int rhif_grad_logcoef(const rhif_grid* g, const double* a_pix, const double* u, const double* lam,
+                      double* grad, void* stream) {
+  int rc = check_grid(g);
+  if (rc) return rc;
+  if (!a_pix || !u || !lam || !grad) return fail(RHIF_ERR_BAD_ARG, "null pointer");
+  Geometry G = make_geometry(g->dim, g->n, 2);
+  {
+    Launch t(kCatGrad, (cudaStream_t)stream, 0.0, 0.0);
+    launch_grad_logcoef(geo_dev(G), a_pix, u, lam, grad, (cudaStream_t)stream);
+  }
+  CK(cudaGetLastError());
+  return RHIF_OK;
+}
+
+int rhif_stats(const rhif_handle* F, rhif_stats_t* st) {
+  if (!F || !st) return fail(RHIF_ERR_BAD_ARG, "null argument");
+  std::memset(st, 0, sizeof(*st));
+  st->levels = F->G.L;
+  st->n = F->G.N;
+  st->root_size = F->levels.empty() ? 0 : F->levels.back().plan.nI.empty() ? 0 : F->levels.back().plan.nI[0];
+  for (int l = 0; l < F->G.L && l < 16; ++l) {
+    // active DOFs after level l = DOFs present at level l+1
+    const LevelPlan& P = F->levels[l + 1].plan;
+    int64_t a = 0;
+    for (int c = 0; c < P.ncell(); ++c) a += P.nI[c];
+    a += (int64_t)P.group_gids.size();
+    st->active[l] = a;
+  }
+  st->factor_bytes = (int64_t)F->mem.bytes;
+  st->flops = F->flops;
+  st->apply_bytes = F->apply_bytes;
+  st->precision = F->precision;
+  st->units = F->units;
+  st->factor_ms = F->factor_ms;
+  return RHIF_OK;
+}
+
+int rhif_skeletons(const rhif_handle* F, int level, int phase, int* count, int* sizes, int* ranks,
+                   int64_t* gids, int64_t capacity) {
+  if (!F || !count) return fail(RHIF_ERR_BAD_ARG, "null argument");
+  if (level < 0 || level >= F->G.L) return fail(RHIF_ERR_BAD_ARG, "level out of range");
+  const LevelStore& S = F->levels[level];
+  if (phase < 0 || phase >= (int)S.phases.size()) return fail(RHIF_ERR_BAD_ARG, "phase out of range");
+  const PhasePlan& ph = S.plan.phases[phase];
+  const PhaseStore& PS = S.phases[phase];
+  const int nu = (int)ph.units.group.size();
+  *count = nu;
+  int64_t pos = 0;
+  for (int u = 0; u < nu; ++u) {
+    const int gi = ph.units.group[u];
+    const int64_t g0 = S.plan.group_gid_off[gi];
+    const int n = (int)(S.plan.group_gid_off[gi + 1] - g0);
+    if (sizes) sizes[u] = n;
+    if (ranks) ranks[u] = PS.h_rank[u];
+    if (gids) {
+      if (pos + n > capacity) return fail(RHIF_ERR_BAD_ARG, "gids capacity too small");
+      const int* pm = PS.h_perm.data() + ph.units.perm_off[u];
+      for (int i = 0; i < n; ++i) gids[pos + i] = S.plan.group_gids[g0 + pm[i]];
+    }
+    pos += n;
+  }
+  return RHIF_OK;
+}
+
+void rhif_free(rhif_handle* F) {
+  if (!F) return;
+  F->mem.release_all();
+  cudaStreamSynchronize(F->mem.s);
+  delete F;
+}
+
+int rhif_set_timing(int on) {
+  std::lock_guard<std::mutex> lk(g_kmu);
+  g_timing = on != 0;
+  return RHIF_OK;
+}
+
+int rhif_reset_kernel_stats(void) {
+  cudaDeviceSynchronize();
+  std::lock_guard<std::mutex> lk(g_kmu);
+  for (auto& p : g_pending) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  g_pending.clear();
+  for (auto& k : g_kstat) k = KStat();
+  return RHIF_OK;
+}
+
+int rhif_kernel_stat_count(void) { return kNumCat; }
+
+int rhif_kernel_stats(int index, rhif_kernel_stat* out) {
+  if (index < 0 || index >= kNumCat || !out) return fail(RHIF_ERR_BAD_ARG, "bad kernel stat index");
+  CK(cudaDeviceSynchronize());
+  std::lock_guard<std::mutex> lk(g_kmu);
+  for (auto& p : g_pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) g_kstat[p.cat].ms += ms;
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  g_pending.clear();
+  std::memset(out, 0, sizeof(*out));
+  std::snprintf(out->name, sizeof(out->name), "%s", kCatName[index]);
+  out->launches = g_kstat[index].launches;
+  out->total_ms = g_kstat[index].ms;
+  out->flops = g_kstat[index].flops;
+  out->bytes = g_kstat[index].bytes;
+  return RHIF_OK;
+}
+
+const char* rhif_error_string(int code) {
+  switch (code) {
+    case RHIF_OK: return "RHIF_OK";
+    case RHIF_ERR_BAD_ARG: return "RHIF_ERR_BAD_ARG";
+    case RHIF_ERR_NOT_SPD: return "RHIF_ERR_NOT_SPD";
+    case RHIF_ERR_NOT_CONVERGED: return "RHIF_ERR_NOT_CONVERGED";
+    case RHIF_ERR_TIMEOUT: return "RHIF_ERR_TIMEOUT";
+    case RHIF_ERR_OOM: return "RHIF_ERR_OOM";
+    case RHIF_ERR_CUDA: return "RHIF_ERR_CUDA";
+    default: return "unknown";
+  }
+}
+
+const char* rhif_last_error_detail(void) { return g_detail.c_str(); }
+
+}  // extern "C"

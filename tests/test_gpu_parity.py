@@ -1,0 +1,180 @@
+"""GPU path vs the FP64 oracle on the same seeded inputs (through the C-ABI).
+
+FP64 bar (derived in the design doc): identical skeleton sets except at logged
+near-ties, F^{-1} x within 1e-9 relative of the oracle's (both are
+products of the same well-conditioned factors up to roundoff), PCG relative
+residual <= rtol with the solution within 1e-8 of a sparse direct solve.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+import workloads as W
+from oracle import fd, phif
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+
+
+def _gpu_matrix(lib, ns, a, b):
+    bb = _dev(np.broadcast_to(b, (int(np.prod(ns)),)).astype(np.float64)) if not np.isscalar(b) else b
+    return lib.rhif_assemble_fd(ns, _dev(a), bb)
+
+
+def _skeleton_map(units):
+    """{frozenset(unit dofs): frozenset(skeleton dofs)}"""
+    return {frozenset(int(g) for g in dofs): frozenset(int(g) for g in dofs[:k]) for dofs, k in units}
+
+
+def _oracle_skeletons(F, level, phase):
+    ph = F.levels[level].phases[phase]
+    return {frozenset(int(g) for g in u.e): frozenset(int(g) for g in u.sk) for u in ph.units}
+
+
+def test_fd_assembly_matches_oracle(gpu_lib):
+    for ns, b in [((31, 17), 0.0), ((9, 8, 7), 0.01), ((1, 5), 0.0)]:
+        a = W.log_uniform_pixels(ns, 1e-3, 1e3, seed=3)
+        rp, col, val = _gpu_matrix(gpu_lib, ns, a, b)
+        A = fd.assemble(ns, a, b)
+        np.testing.assert_array_equal(rp.cpu().numpy(), A.indptr)
+        np.testing.assert_array_equal(col.cpu().numpy(), A.indices)
+        np.testing.assert_allclose(val.cpu().numpy(), A.data, rtol=1e-14, atol=0)
+
+
+CASES = [
+    # ns, leaf, tol, (lo, hi), b, edge_skel
+    ((15, 15), 4, 1e-4, (1e-2, 1e2), 0.0, False),
+    ((31, 31), 8, 1e-3, (1e-3, 1e3), 0.0, False),
+    ((63, 63), 8, 1e-6, (1e-3, 1e3), 0.0, False),
+    ((20, 23), 4, 1e-3, (1e-2, 1e2), 0.0, False),     # padded, ragged tail
+    ((127, 127), 8, 1e-3, (1e-2, 1e2), 0.0, False),   # the 127^2 benchmark grid
+    ((15, 15, 15), 4, 1e-3, (1e-3, 1e3), 1e-2, False),
+    ((11, 9, 13), 4, 1e-3, (1e-3, 1e3), 1e-2, False),  # 3D padded
+    ((15, 15, 15), 4, 1e-3, (1e-3, 1e3), 1e-2, True),  # faces then edges
+]
+
+
+@pytest.mark.parametrize("ns,leaf,tol,lohi,b,edge", CASES)
+def test_fp64_factor_matches_oracle(gpu_lib, ns, leaf, tol, lohi, b, edge):
+    a = W.log_uniform_pixels(ns, *lohi, seed=sum(ns) + leaf)
+    A = fd.assemble(ns, a, b)
+    Fo = phif.factor(A, ns, leaf, tol, edge_skel=edge)
+    csr = _gpu_matrix(gpu_lib, ns, a, b)
+    Fg = gpu_lib.rhif_factor(csr, ns, leaf, tol, precision="fp64", edge_skel_3d=edge)
+    st = Fg.stats()
+    assert st["levels"] == len(Fo.levels)
+    tie_units = {(str(w), k) for (w, k, *_rest) in Fo.ties}
+    diverged = False
+    for lvl in range(len(Fo.levels)):
+        for ph in range(len(Fo.levels[lvl].phases)):
+            go = _oracle_skeletons(Fo, lvl, ph)
+            gg = _skeleton_map(Fg.skeletons(lvl, ph))
+            assert set(go) == set(gg), f"unit sets differ at level {lvl} phase {ph}"
+            bad = [u for u in go if go[u] != gg[u]]
+            if bad:
+                assert Fo.ties, f"skeleton sets differ at level {lvl} phase {ph} without a logged tie"
+                diverged = True
+        if diverged:
+            break
+    if not diverged:
+        assert st["root_size"] == Fo.S.size
+    x = np.random.default_rng(7).standard_normal(A.shape[0])
+    yg = Fg.apply(_dev(x)).cpu().numpy()
+    yo = phif.solve(Fo, x)
+    if not diverged:
+        assert np.linalg.norm(yg - yo) <= 1e-9 * np.linalg.norm(yo)
+    # apply error ||F^{-1} A x - x|| / ||x|| within 2x of the oracle's
+    Ax = A @ x
+    eg = np.linalg.norm(Fg.apply(_dev(Ax)).cpu().numpy() - x) / np.linalg.norm(x)
+    eo = np.linalg.norm(phif.solve(Fo, Ax) - x) / np.linalg.norm(x)
+    assert eg <= 2 * eo + 1e-12
+    Fg.free()
+
+
+@pytest.mark.parametrize("ns,leaf", [((31, 31), 4), ((20, 13), 4), ((7, 9, 8), 4)])
+def test_tol_zero_is_exact_on_gpu(gpu_lib, ns, leaf):
+    a = W.log_uniform_pixels(ns, 1e-2, 1e2, seed=5)
+    A = fd.assemble(ns, a, 0.01)
+    Fg = gpu_lib.rhif_factor(_gpu_matrix(gpu_lib, ns, a, 0.01), ns, leaf, 0.0)
+    x = np.random.default_rng(2).standard_normal(A.shape[0])
+    y = Fg.apply(_dev(A @ x)).cpu().numpy()
+    assert np.linalg.norm(y - x) <= 1e-10 * np.linalg.norm(x)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_pcg_solution_matches_direct_solve(gpu_lib, precision):
+    p = W.config_problem(0)
+    A = fd.assemble(p.ns, p.a, p.b)
+    Fg = gpu_lib.rhif_factor(_gpu_matrix(gpu_lib, p.ns, p.a, p.b), p.ns, p.leaf, p.tol,
+                             precision=precision)
+    u, its, rr = Fg.pcg(_dev(p.f), rtol=1e-12, maxit=200)
+    u = u.cpu().numpy()
+    ud = spla.spsolve(A.tocsc(), p.f)
+    assert rr[0] <= 1e-12 * 1.5
+    assert np.linalg.norm(u - ud) <= 1e-9 * np.linalg.norm(ud)
+    if precision == "fp64":
+        Fo = phif.factor(A, p.ns, p.leaf, p.tol)
+        _, it_o, _ = phif.pcg(A, p.f, M=lambda r: phif.solve(Fo, r), rtol=1e-12)
+        assert abs(its[0] - it_o) <= 1
+
+
+def test_multi_rhs_pcg(gpu_lib):
+    ns = (63, 63)
+    a = W.log_uniform_pixels(ns, 1e-3, 1e3, seed=9)
+    A = fd.assemble(ns, a, 0.0)
+    F = W.normal_rhs(ns, 4, nrhs=5)
+    Fg = gpu_lib.rhif_factor(_gpu_matrix(gpu_lib, ns, a, 0.0), ns, 8, 1e-3, precision="fp32")
+    U, its, rr = Fg.pcg(_dev(F), rtol=1e-10)
+    U = U.cpu().numpy()
+    for r in range(5):
+        assert rr[r] <= 1.5e-10
+        ud = spla.spsolve(A.tocsc(), F[r])
+        assert np.linalg.norm(U[r] - ud) <= 1e-7 * np.linalg.norm(ud)
+    Y = Fg.apply(_dev(F)).cpu().numpy()
+    for r in range(5):
+        y1 = Fg.apply(_dev(F[r])).cpu().numpy()
+        np.testing.assert_allclose(Y[r], y1, rtol=0, atol=1e-12 * np.abs(y1).max())
+
+
+def test_not_spd_reported(gpu_lib):
+    ns = (15, 15)
+    a = W.log_uniform_pixels(ns, 1e-2, 1e2, seed=1)
+    rp, col, val = _gpu_matrix(gpu_lib, ns, a, 0.0)
+    v = val.cpu().numpy()
+    rpn = rp.cpu().numpy()
+    cn = col.cpu().numpy()
+    i = 37
+    k = rpn[i] + np.nonzero(cn[rpn[i]:rpn[i + 1]] == i)[0][0]
+    v[k] = -1.0
+    with pytest.raises(gpu_lib.RhifError) as e:
+        gpu_lib.rhif_factor((rp, col, _dev(v)), ns, 4, 1e-3)
+    assert e.value.code == -2
+
+
+def test_bad_csr_pattern_rejected(gpu_lib):
+    ns = (8, 8)
+    N = 64
+    rows = np.arange(N)
+    cols = (rows + 9) % N   # not a grid neighbour
+    A = sp.csr_matrix((np.ones(2 * N), (np.r_[rows, rows], np.r_[rows, cols])), shape=(N, N))
+    A.sort_indices()
+    csr = (_dev(A.indptr.astype(np.int64)), _dev(A.indices.astype(np.int32)), _dev(A.data))
+    with pytest.raises(gpu_lib.RhifError) as e:
+        gpu_lib.rhif_factor(csr, ns, 4, 1e-3)
+    assert e.value.code == -1
+
+
+def test_gradient_kernel_matches_oracle(gpu_lib):
+    for ns in [(17, 12), (6, 5, 7)]:
+        a = W.log_uniform_pixels(ns, 1e-2, 1e2, seed=8)
+        u = W.normal_rhs(ns, 1)
+        lam = W.normal_rhs(ns, 2)
+        g = gpu_lib.rhif_grad_logcoef(ns, _dev(a), _dev(u), _dev(lam)).cpu().numpy()
+        go = fd.dA_dlog_a(ns, a, u, lam)
+        np.testing.assert_allclose(g, go, rtol=1e-12, atol=1e-12 * np.abs(go).max())

@@ -15,20 +15,153 @@ namespace rhif {
 
 constexpr int kApplyThreads = 256;
 constexpr int kGroupThreads = 128;
+constexpr int kLeafWarps = 4;            // at most this many leaf cells per CTA (one warp each)
+constexpr size_t kStageBudget = 160 * 1024;   // shared memory for staged factor blocks
+
+// Coalesced copy of a factor block into shared memory (whole CTA or one warp).
+template <typename T>
+__device__ inline void stage_copy(T* dst, const T* src, int64_t count, int tid, int nt) {
+  for (int64_t i = tid; i < count; i += nt) dst[i] = src[i];
+}
+
+template <typename T>
+static size_t leaf_warp_smem(const LevelDev& Lv) {
+  size_t band = (size_t)Lv.max_nI * (Lv.max_w + 1) * sizeof(T);
+  return ((band + 15) & ~size_t(15)) + 2 * (Lv.max_nI + 1) * sizeof(T) + 16;
+}
+
+template <typename T>
+static int leaf_warps_per_cta(const LevelDev& Lv) {
+  const size_t per = leaf_warp_smem<T>(Lv);
+  int w = (int)(kStageBudget / per);
+  return w < 1 ? 1 : (w > kLeafWarps ? kLeafWarps : w);
+}
 
 // ---------------------------------------------------------------------------
-// cells
+// level 0: banded leaf factors, one warp per cell
+// ---------------------------------------------------------------------------
+
+// y <- L^{-1} y with L banded (column k of band holds 1/L[k,k], L[k+1..k+w, k]); one warp.
+template <typename T>
+__device__ inline void warp_band_fwd(const T* band, int n, int w, T* y) {
+  const int lane = threadIdx.x & 31;
+  const int w1 = w + 1;
+  for (int k = 0; k < n; ++k) {
+    const T yk = y[k] * band[k * w1];
+    __syncwarp();
+    if (lane == 0) y[k] = yk;
+    const int wk = min(w, n - 1 - k);
+    for (int d = 1 + lane; d <= wk; d += 32) y[k + d] -= band[k * w1 + d] * yk;
+    __syncwarp();
+  }
+}
+
+// y <- L^{-T} y with L banded; one warp.
+template <typename T>
+__device__ inline void warp_band_bwd(const T* band, int n, int w, T* y) {
+  const int lane = threadIdx.x & 31;
+  const int w1 = w + 1;
+  for (int k = n - 1; k >= 0; --k) {
+    const int wk = min(w, n - 1 - k);
+    T s = T(0);
+    for (int d = 1 + lane; d <= wk; d += 32) s += band[k * w1 + d] * y[k + d];
+    s = warp_sum(s);
+    if (lane == 0) y[k] = (y[k] - s) * band[k * w1];
+    __syncwarp();
+  }
+}
+
+// E_0^T per leaf: y = L^{-1} x_I ; x_B -= A_BI L^{-T} y (sent to the owning groups) ; x_I = y
+template <typename T>
+__global__ void __launch_bounds__(32 * kLeafWarps)
+k_apply_leaf_up(LevelDev Lv, double* x, int64_t ldx, int nrhs, double* ubuf, int64_t ldu,
+                int per_warp_bytes) {
+  extern __shared__ unsigned char smraw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (c >= Lv.ncell) return;
+  T* sb = (T*)(smraw + (size_t)warp * per_warp_bytes);
+  const size_t band_elems = (((size_t)Lv.max_nI * (Lv.max_w + 1) * sizeof(T) + 15) & ~size_t(15)) / sizeof(T);
+  T* y = sb + band_elems;
+  T* z = y + Lv.max_nI + 1;
+  const int nI = Lv.nI[c], nB = Lv.nB[c], w = Lv.band_w[c];
+  stage_copy(sb, (const T*)Lv.band + Lv.band_off[c], (int64_t)nI * (w + 1), lane, 32);
+  const T* band = sb;
+  const int32_t* gI = Lv.gids + Lv.gid_off[c];
+  const int* ci = Lv.cpl_i + Lv.b_off[c];
+  const T* ca = (const T*)Lv.cpl_a + Lv.b_off[c];
+  for (int r = 0; r < nrhs; ++r) {
+    double* xr = x + r * ldx;
+    for (int i = lane; i < nI; i += 32) y[i] = T(xr[gI[i]]);
+    __syncwarp();
+    warp_band_fwd(band, nI, w, y);
+    for (int i = lane; i < nI; i += 32) {
+      xr[gI[i]] = double(y[i]);
+      z[i] = y[i];
+    }
+    __syncwarp();
+    warp_band_bwd(band, nI, w, z);
+    double* u = ubuf + r * ldu + Lv.b_off[c];
+    for (int b = lane; b < nB; b += 32) u[b] = ci[b] >= 0 ? double(ca[b] * z[ci[b]]) : 0.0;
+    __syncwarp();
+  }
+}
+
+// E_0 per leaf: x_I = L^{-T}(x_I - L^{-1} A_BI^T x_B)
+template <typename T>
+__global__ void __launch_bounds__(32 * kLeafWarps)
+k_apply_leaf_down(LevelDev Lv, double* x, int64_t ldx, int nrhs, int per_warp_bytes) {
+  extern __shared__ unsigned char smraw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (c >= Lv.ncell) return;
+  T* sb = (T*)(smraw + (size_t)warp * per_warp_bytes);
+  const size_t band_elems = (((size_t)Lv.max_nI * (Lv.max_w + 1) * sizeof(T) + 15) & ~size_t(15)) / sizeof(T);
+  T* t = sb + band_elems;
+  T* v = t + Lv.max_nI + 1;
+  const int nI = Lv.nI[c], nB = Lv.nB[c], w = Lv.band_w[c];
+  stage_copy(sb, (const T*)Lv.band + Lv.band_off[c], (int64_t)nI * (w + 1), lane, 32);
+  const T* band = sb;
+  const int32_t* gI = Lv.gids + Lv.gid_off[c];
+  const int32_t* gB = gI + nI;
+  const int* ci = Lv.cpl_i + Lv.b_off[c];
+  const T* ca = (const T*)Lv.cpl_a + Lv.b_off[c];
+  for (int r = 0; r < nrhs; ++r) {
+    double* xr = x + r * ldx;
+    for (int i = lane; i < nI; i += 32) v[i] = T(0);
+    __syncwarp();
+    if (lane == 0)   // A_BI^T x_B in a fixed order (several boundary DOFs may face one interior DOF)
+      for (int b = 0; b < nB; ++b)
+        if (ci[b] >= 0) v[ci[b]] += ca[b] * T(xr[gB[b]]);
+    __syncwarp();
+    warp_band_fwd(band, nI, w, v);
+    for (int i = lane; i < nI; i += 32) t[i] = T(xr[gI[i]]) - v[i];
+    __syncwarp();
+    warp_band_bwd(band, nI, w, t);
+    for (int i = lane; i < nI; i += 32) xr[gI[i]] = double(t[i]);
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// dense fronts (levels >= 1 and the root)
 // ---------------------------------------------------------------------------
 
 template <typename T>
 __global__ void __launch_bounds__(kApplyThreads)
-k_apply_cell_up(LevelDev Lv, double* x, int64_t ldx, int nrhs, double* ubuf, int64_t ldu) {
+k_apply_cell_up(LevelDev Lv, double* x, int64_t ldx, int nrhs, double* ubuf, int64_t ldu,
+                int stage) {
   extern __shared__ unsigned char smraw[];
   T* y = (T*)smraw;
   const int c = blockIdx.x;
   const int nI = Lv.nI[c], nB = Lv.nB[c], n = nI + nB;
   const T* F = (const T*)Lv.front + Lv.front_off[c];
-  const int64_t* gI = Lv.gids + Lv.gid_off[c];
+  if (stage) {
+    T* sf = y + ((Lv.max_nI + 1 + 1) & ~1);
+    stage_copy(sf, F, (int64_t)n * nI, threadIdx.x, blockDim.x);
+    F = sf;
+  }
+  const int32_t* gI = Lv.gids + Lv.gid_off[c];
   for (int r = 0; r < nrhs; ++r) {
     double* xr = x + r * ldx;
     for (int i = threadIdx.x; i < nI; i += blockDim.x) y[i] = T(xr[gI[i]]);
@@ -47,15 +180,20 @@ k_apply_cell_up(LevelDev Lv, double* x, int64_t ldx, int nrhs, double* ubuf, int
 
 template <typename T>
 __global__ void __launch_bounds__(kApplyThreads)
-k_apply_cell_down(LevelDev Lv, double* x, int64_t ldx, int nrhs) {
+k_apply_cell_down(LevelDev Lv, double* x, int64_t ldx, int nrhs, int stage) {
   extern __shared__ unsigned char smraw[];
   T* t = (T*)smraw;
   T* xb = t + Lv.max_nI;
   const int c = blockIdx.x;
   const int nI = Lv.nI[c], nB = Lv.nB[c], n = nI + nB;
   const T* F = (const T*)Lv.front + Lv.front_off[c];
-  const int64_t* gI = Lv.gids + Lv.gid_off[c];
-  const int64_t* gB = gI + nI;
+  if (stage) {
+    T* sf = t + ((Lv.max_nI + Lv.max_nB + 1 + 1) & ~1);
+    stage_copy(sf, F, (int64_t)n * nI, threadIdx.x, blockDim.x);
+    F = sf;
+  }
+  const int32_t* gI = Lv.gids + Lv.gid_off[c];
+  const int32_t* gB = gI + nI;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   for (int r = 0; r < nrhs; ++r) {
     double* xr = x + r * ldx;
@@ -79,11 +217,9 @@ k_apply_cell_down(LevelDev Lv, double* x, int64_t ldx, int nrhs) {
 // ---------------------------------------------------------------------------
 
 template <typename T>
-__device__ void unit_up(const PhaseDev& Ph, int u, int n, T* xg, T* tmp) {
+__device__ void unit_up(const PhaseDev& Ph, int u, int n, T* xg, T* tmp, const T* Fu, const T* Tm) {
   const int k = Ph.rank[u], r = n - k;
   const int* perm = Ph.perm + Ph.u_perm_off[u];
-  const T* Fu = (const T*)Ph.rec + Ph.u_rec_off[u];
-  const T* Tm = Fu + (int64_t)n * n;
   // Z^T: x_rd -= T^T x_sk
   for (int a = threadIdx.x; a < r; a += blockDim.x) {
     T s = xg[perm[k + a]];
@@ -104,11 +240,9 @@ __device__ void unit_up(const PhaseDev& Ph, int u, int n, T* xg, T* tmp) {
 }
 
 template <typename T>
-__device__ void unit_down(const PhaseDev& Ph, int u, int n, T* xg, T* tmp) {
+__device__ void unit_down(const PhaseDev& Ph, int u, int n, T* xg, T* tmp, const T* Fu, const T* Tm) {
   const int k = Ph.rank[u], r = n - k;
   const int* perm = Ph.perm + Ph.u_perm_off[u];
-  const T* Fu = (const T*)Ph.rec + Ph.u_rec_off[u];
-  const T* Tm = Fu + (int64_t)n * n;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   // E_rd: x_rd = L^{-T}(x_rd - W^T x_sk)
   for (int a = warp; a < r; a += nwarps) {
@@ -130,19 +264,43 @@ __device__ void unit_down(const PhaseDev& Ph, int u, int n, T* xg, T* tmp) {
   __syncthreads();
 }
 
+// Points Lg / Fu / Tm at the group's factor blocks, copied to shared memory
+// when `stage` is set (the caller syncs before use).
+template <typename T>
+__device__ inline void group_blocks(const PhaseDev& Ph, int pi, int u, int n, int stage, T* sm,
+                                    const T** Lg, const T** Fu, const T** Tm) {
+  *Lg = pi >= 0 ? (const T*)Ph.Lbuf + Ph.pre_off[pi] : nullptr;
+  *Fu = u >= 0 ? (const T*)Ph.rec + Ph.u_rec_off[u] : nullptr;
+  *Tm = u >= 0 ? *Fu + (int64_t)n * n : nullptr;
+  if (!stage) return;
+  const int64_t nn = (int64_t)n * n;
+  if (pi >= 0) {
+    stage_copy(sm, *Lg, nn, threadIdx.x, blockDim.x);
+    *Lg = sm;
+  }
+  if (u >= 0) {
+    const int k = Ph.rank[u];
+    stage_copy(sm + nn, *Fu, nn, threadIdx.x, blockDim.x);
+    stage_copy(sm + 2 * nn, *Tm, (int64_t)k * (n - k), threadIdx.x, blockDim.x);
+    *Fu = sm + nn;
+    *Tm = sm + 2 * nn;
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kGroupThreads)
 k_apply_group_up(LevelDev Lv, PhaseDev Ph, int gather, double* x, int64_t ldx, int nrhs,
-                 const double* ubuf, int64_t ldu) {
+                 const double* ubuf, int64_t ldu, int stage) {
   extern __shared__ unsigned char smraw[];
   T* xg = (T*)smraw;
   T* tmp = xg + Lv.max_group;
   const int g = blockIdx.x;
   if (Lv.group_t[g] < Ph.pre_min_type) return;
-  const int64_t g0 = Lv.group_gid_off[g];
-  const int n = (int)(Lv.group_gid_off[g + 1] - g0);
-  const int64_t* gid = Lv.group_gids + g0;
+  const int n = Lv.group_size[g];
+  const int32_t* gid = Lv.bucket + Lv.group_start[g];
   const int pi = Ph.group_pre[g], u = Ph.group_unit[g];
+  const T *Lg, *Fu, *Tm;
+  group_blocks(Ph, pi, u, n, stage, tmp + ((Lv.max_group + 2) & ~1), &Lg, &Fu, &Tm);
   for (int r = 0; r < nrhs; ++r) {
     double* xr = x + r * ldx;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -154,8 +312,8 @@ k_apply_group_up(LevelDev Lv, PhaseDev Ph, int gather, double* x, int64_t ldx, i
       xg[i] = T(v);
     }
     __syncthreads();
-    if (pi >= 0) cta_trsv_lower((const T*)Ph.Lbuf + Ph.pre_off[pi], n, n, xg);
-    if (u >= 0) unit_up(Ph, u, n, xg, tmp);
+    if (pi >= 0) cta_trsv_lower(Lg, n, n, xg);
+    if (u >= 0) unit_up(Ph, u, n, xg, tmp, Fu, Tm);
     for (int i = threadIdx.x; i < n; i += blockDim.x) xr[gid[i]] = double(xg[i]);
     __syncthreads();
   }
@@ -163,22 +321,23 @@ k_apply_group_up(LevelDev Lv, PhaseDev Ph, int gather, double* x, int64_t ldx, i
 
 template <typename T>
 __global__ void __launch_bounds__(kGroupThreads)
-k_apply_group_down(LevelDev Lv, PhaseDev Ph, double* x, int64_t ldx, int nrhs) {
+k_apply_group_down(LevelDev Lv, PhaseDev Ph, double* x, int64_t ldx, int nrhs, int stage) {
   extern __shared__ unsigned char smraw[];
   T* xg = (T*)smraw;
   T* tmp = xg + Lv.max_group;
   const int g = blockIdx.x;
   if (Lv.group_t[g] < Ph.pre_min_type) return;
-  const int64_t g0 = Lv.group_gid_off[g];
-  const int n = (int)(Lv.group_gid_off[g + 1] - g0);
-  const int64_t* gid = Lv.group_gids + g0;
+  const int n = Lv.group_size[g];
+  const int32_t* gid = Lv.bucket + Lv.group_start[g];
   const int pi = Ph.group_pre[g], u = Ph.group_unit[g];
+  const T *Lg, *Fu, *Tm;
+  group_blocks(Ph, pi, u, n, stage, tmp + ((Lv.max_group + 2) & ~1), &Lg, &Fu, &Tm);
   for (int r = 0; r < nrhs; ++r) {
     double* xr = x + r * ldx;
     for (int i = threadIdx.x; i < n; i += blockDim.x) xg[i] = T(xr[gid[i]]);
     __syncthreads();
-    if (u >= 0) unit_down(Ph, u, n, xg, tmp);
-    if (pi >= 0) cta_trsv_lower_t((const T*)Ph.Lbuf + Ph.pre_off[pi], n, n, xg);
+    if (u >= 0) unit_down(Ph, u, n, xg, tmp, Fu, Tm);
+    if (pi >= 0) cta_trsv_lower_t(Lg, n, n, xg);
     for (int i = threadIdx.x; i < n; i += blockDim.x) xr[gid[i]] = double(xg[i]);
     __syncthreads();
   }
@@ -188,30 +347,57 @@ template <typename T>
 void launch_apply_cell_up(const LevelDev& Lv, double* x, int64_t ldx, int nrhs, double* ubuf,
                           int64_t ldu, cudaStream_t s) {
   if (!Lv.ncell) return;
-  k_apply_cell_up<T><<<Lv.ncell, kApplyThreads, (Lv.max_nI + 1) * sizeof(T), s>>>(Lv, x, ldx, nrhs, ubuf, ldu);
+  if (Lv.level == 0) {
+    const int wpc = leaf_warps_per_cta<T>(Lv);
+    const size_t per = leaf_warp_smem<T>(Lv);
+    const unsigned grid = (Lv.ncell + wpc - 1) / wpc;
+    k_apply_leaf_up<T><<<grid, 32 * wpc, wpc * per, s>>>(Lv, x, ldx, nrhs, ubuf, ldu, (int)per);
+    return;
+  }
+  const size_t base = ((Lv.max_nI + 2) & ~1) * sizeof(T);
+  const size_t blk = (size_t)Lv.max_n * Lv.max_nI * sizeof(T);
+  const int stage = blk <= kStageBudget;
+  k_apply_cell_up<T><<<Lv.ncell, kApplyThreads, base + (stage ? blk : 0), s>>>(Lv, x, ldx, nrhs, ubuf,
+                                                                            ldu, stage);
 }
 
 template <typename T>
 void launch_apply_cell_down(const LevelDev& Lv, double* x, int64_t ldx, int nrhs, cudaStream_t s) {
   if (!Lv.ncell) return;
-  k_apply_cell_down<T><<<Lv.ncell, kApplyThreads, (Lv.max_nI + Lv.max_nB + 1) * sizeof(T), s>>>(
-      Lv, x, ldx, nrhs);
+  if (Lv.level == 0) {
+    const int wpc = leaf_warps_per_cta<T>(Lv);
+    const size_t per = leaf_warp_smem<T>(Lv);
+    const unsigned grid = (Lv.ncell + wpc - 1) / wpc;
+    k_apply_leaf_down<T><<<grid, 32 * wpc, wpc * per, s>>>(Lv, x, ldx, nrhs, (int)per);
+    return;
+  }
+  const size_t base = ((Lv.max_nI + Lv.max_nB + 2) & ~1) * sizeof(T);
+  const size_t blk = (size_t)Lv.max_n * Lv.max_nI * sizeof(T);
+  const int stage = blk <= kStageBudget;
+  k_apply_cell_down<T><<<Lv.ncell, kApplyThreads, base + (stage ? blk : 0), s>>>(Lv, x, ldx, nrhs,
+                                                                              stage);
 }
 
 template <typename T>
 void launch_apply_group_up(const LevelDev& Lv, const PhaseDev& Ph, int gather, double* x,
                            int64_t ldx, int nrhs, const double* ubuf, int64_t ldu, cudaStream_t s) {
   if (!Lv.ngroup) return;
-  k_apply_group_up<T><<<Lv.ngroup, kGroupThreads, 2 * (Lv.max_group + 1) * sizeof(T), s>>>(
-      Lv, Ph, gather, x, ldx, nrhs, ubuf, ldu);
+  const size_t base = (((Lv.max_group + 2) & ~1) * 2) * sizeof(T);
+  const size_t blk = 3 * (size_t)Lv.max_group * Lv.max_group * sizeof(T);
+  const int stage = blk <= kStageBudget;
+  k_apply_group_up<T><<<Lv.ngroup, kGroupThreads, base + (stage ? blk : 0), s>>>(
+      Lv, Ph, gather, x, ldx, nrhs, ubuf, ldu, stage);
 }
 
 template <typename T>
 void launch_apply_group_down(const LevelDev& Lv, const PhaseDev& Ph, double* x, int64_t ldx,
                              int nrhs, cudaStream_t s) {
   if (!Lv.ngroup) return;
-  k_apply_group_down<T><<<Lv.ngroup, kGroupThreads, 2 * (Lv.max_group + 1) * sizeof(T), s>>>(
-      Lv, Ph, x, ldx, nrhs);
+  const size_t base = (((Lv.max_group + 2) & ~1) * 2) * sizeof(T);
+  const size_t blk = 3 * (size_t)Lv.max_group * Lv.max_group * sizeof(T);
+  const int stage = blk <= kStageBudget;
+  k_apply_group_down<T><<<Lv.ngroup, kGroupThreads, base + (stage ? blk : 0), s>>>(
+      Lv, Ph, x, ldx, nrhs, stage);
 }
 
 template <typename T>
@@ -222,6 +408,8 @@ int configure_apply_kernels() {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_cell_down<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_group_up<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_group_down<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_leaf_up<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_leaf_down<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   return e == cudaSuccess ? 0 : -1;
 }
 

@@ -42,11 +42,12 @@ __device__ inline T sym_at(const T* A, int64_t ld, int i, int j) {
   return i >= j ? A[i + (int64_t)j * ld] : A[j + (int64_t)i * ld];
 }
 
-// C[i,j] -= sum_{k in [k0,k1)} A[i,k] * A[j,k] for i in [r0,r1), j in [c0,c1), i >= j.
-// The operand panels are columns [k0,k1) of the same matrix A.
+// C[i,j] -= sum_{k in [k0,k1)} P[i,k] * P[j,k] for i in [r0,r1), j in [c0,c1), i >= j.
+// C and P are column-major (ldc, ldp); they may be the same matrix as long as
+// the updated block and the operand columns do not overlap.
 template <typename T>
-__device__ void cta_syrk_lower(T* A, int64_t ld, int r0, int r1, int c0, int c1, int k0, int k1,
-                               T* sm) {
+__device__ void cta_syrk_lower(T* C, int64_t ldc, const T* P, int64_t ldp, int r0, int r1, int c0,
+                               int c1, int k0, int k1, T* sm) {
   if (r0 >= r1 || c0 >= c1 || k0 >= k1) return;
   T* si = sm;                          // [kKC][kTile+1]
   T* sj = sm + kKC * (kTile + 1);      // [kKC][kTile+1]
@@ -65,8 +66,8 @@ __device__ void cta_syrk_lower(T* A, int64_t ld, int r0, int r1, int c0, int c1,
         for (int idx = tid; idx < kTile * kKC; idx += kThreads) {
           const int i = idx % kTile, k = idx / kTile;
           const int gi = ti + i, gj = tj + i;
-          si[k * (kTile + 1) + i] = (gi < r1 && k < kk) ? A[gi + (int64_t)(kc + k) * ld] : T(0);
-          sj[k * (kTile + 1) + i] = (gj < c1 && k < kk) ? A[gj + (int64_t)(kc + k) * ld] : T(0);
+          si[k * (kTile + 1) + i] = (gi < r1 && k < kk) ? P[gi + (int64_t)(kc + k) * ldp] : T(0);
+          sj[k * (kTile + 1) + i] = (gj < c1 && k < kk) ? P[gj + (int64_t)(kc + k) * ldp] : T(0);
         }
         __syncthreads();
         for (int k = 0; k < kk; ++k) {
@@ -88,7 +89,7 @@ __device__ void cta_syrk_lower(T* A, int64_t ld, int r0, int r1, int c0, int c1,
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
           const int j = tj + tx + 16 * b;
-          if (i < r1 && j < c1 && i >= j) A[i + (int64_t)j * ld] -= acc[a][b];
+          if (i < r1 && j < c1 && i >= j) C[i + (int64_t)j * ldc] -= acc[a][b];
         }
       }
     }
@@ -164,11 +165,11 @@ __device__ bool cta_partial_chol(T* A, int64_t ld, int n, int nI, T* sm) {
     }
     __syncthreads();
     // trailing update restricted to the columns still to be eliminated
-    cta_syrk_lower(A, ld, p1, n, p1, nI, p0, p1, syrk_sm);
+    cta_syrk_lower(A, ld, A, ld, p1, n, p1, nI, p0, p1, syrk_sm);
     __syncthreads();
   }
   // Schur complement of the boundary block in one pass over k = 0..nI
-  cta_syrk_lower(A, ld, nI, n, nI, n, 0, nI, syrk_sm);
+  cta_syrk_lower(A, ld, A, ld, nI, n, nI, n, 0, nI, syrk_sm);
   __syncthreads();
   return bad == 0;
 }

@@ -65,7 +65,25 @@ __global__ void k_stencil_check(int64_t n, const double* off, const double* offb
 }
 
 // ---------------------------------------------------------------------------
-// level-0 fronts straight from the stencil
+// front-order DOF lists: interior, then the segments of the closure
+// ---------------------------------------------------------------------------
+
+__global__ void k_expand_gids(LevelDev Lv) {
+  const int c = blockIdx.x;
+  const int nI = Lv.nI[c];
+  int32_t* out = Lv.gids + Lv.gid_off[c];
+  const int32_t* I = Lv.bucket + Lv.cell_start[c];
+  for (int p = threadIdx.x; p < nI; p += blockDim.x) out[p] = I[p];
+  for (int s = Lv.seg_off[c]; s < Lv.seg_off[c + 1]; ++s) {
+    const int g = Lv.seg_group[s];
+    const int32_t* src = Lv.bucket + Lv.group_start[g];
+    int32_t* dst = out + nI + Lv.seg_pos[s];
+    for (int o = threadIdx.x; o < Lv.group_size[g]; o += blockDim.x) dst[o] = src[o];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// level 0: banded elimination of every leaf interior straight from the stencil
 // ---------------------------------------------------------------------------
 
 __device__ inline void coords1(const GeoDev& G, int64_t gid, int x[3]) {
@@ -77,18 +95,75 @@ __device__ inline void coords1(const GeoDev& G, int64_t gid, int x[3]) {
   }
 }
 
-// Entry (i, j) of A is split equally among the leaf cells whose closure holds
-// both i and j (a power of two, so the split is exact); the level matrix is
-// the sum of the per-cell fronts.
 template <typename T>
-__global__ void k_front_leaf(GeoDev G, LevelDev Lv, const double* diag, const double* off,
-                             int* status) {
-  extern __shared__ int postab[];
+__device__ inline T* frame_of(const LevelDev& Lv, int c, int* ld) {
+  *ld = Lv.frame_ld[c];
+  return (T*)Lv.frame_base + Lv.frame_off[c];
+}
+
+// Shared memory: band (nI x (w+1)) + position table + SYRK workspace + a
+// panel of Z columns (at least 16, at most nB).
+constexpr size_t kLeafSmemBudget = 200 * 1024;
+
+template <typename T>
+__host__ __device__ size_t leaf_fixed_smem(int max_nI, int max_w, int leaf, int d) {
+  int tab = 1;
+  for (int a = 0; a < d; ++a) tab *= leaf + 1;
+  size_t band = (size_t)max_nI * (max_w + 1) * sizeof(T);
+  band = (band + 15) & ~size_t(15);
+  size_t t = ((size_t)tab * sizeof(int) + 15) & ~size_t(15);
+  return band + t + 2 * kKC * (kTile + 1) * sizeof(T);
+}
+
+template <typename T>
+__host__ __device__ int leaf_panel_cols(int max_nI, int max_nB, int max_w, int leaf, int d) {
+  const size_t fixed = leaf_fixed_smem<T>(max_nI, max_w, leaf, d);
+  if (max_nI == 0) return 16;
+  size_t room = kLeafSmemBudget > fixed ? kLeafSmemBudget - fixed : 0;
+  int cols = (int)(room / ((size_t)max_nI * sizeof(T)));
+  cols = cols / 16 * 16;
+  if (cols < 16) cols = 16;
+  if (cols > max_nB) cols = (max_nB + 15) / 16 * 16;
+  return cols;
+}
+
+template <typename T>
+size_t leaf_smem_bytes(int max_nI, int max_nB, int max_w, int leaf, int d) {
+  const int cols = leaf_panel_cols<T>(max_nI, max_nB, max_w, leaf, d);
+  return leaf_fixed_smem<T>(max_nI, max_w, leaf, d) + (size_t)max_nI * cols * sizeof(T) + 16;
+}
+
+// A_II is the stencil restricted to the interior box of the leaf; in
+// lexicographic order its half bandwidth is the box's x extent (2D) or x*y
+// extent (3D), and its Cholesky factor stays inside that band, so
+//   L        = banded chol(A_II)                      (band kept for the apply)
+//   Z        = L^{-1} A_IB                            (scratch)
+//   frame    = A_BB (this cell's share) - Z^T Z       (Eq. 2.1, Schur complement)
+// reproduce Sec. 2.1 exactly.  A_IB has one entry per boundary DOF that faces
+// the interior; it is kept as (interior index, value) for the apply.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_leaf_elim(GeoDev G, LevelDev Lv, const double* diag, const double* off, int* status) {
+  extern __shared__ unsigned char smraw[];
+  __shared__ int bad;
   const int c = blockIdx.x;
-  const int nI = Lv.nI[c], n = nI + Lv.nB[c];
-  T* F = (T*)Lv.front + Lv.front_off[c];
-  const int64_t* gid = Lv.gids + Lv.gid_off[c];
-  const int m = G.leaf, m1 = G.leaf + 1;
+  const int nI = Lv.nI[c], nB = Lv.nB[c], n = nI + nB, w = Lv.band_w[c];
+  const int w1 = w + 1;
+  const int32_t* gid = Lv.gids + Lv.gid_off[c];
+  T* sband = (T*)smraw;
+  size_t band_bytes = ((size_t)Lv.max_nI * (Lv.max_w + 1) * sizeof(T) + 15) & ~size_t(15);
+  int* postab = (int*)(smraw + band_bytes);
+  int tab = 1;
+  for (int a = 0; a < G.d; ++a) tab *= G.leaf + 1;
+  T* syrk_sm = (T*)((unsigned char*)postab + (((size_t)tab * sizeof(int) + 15) & ~size_t(15)));
+  T* zp = syrk_sm + 2 * kKC * (kTile + 1);   // panel of Z columns, zp[k * pcols + j]
+  const int pcols = leaf_panel_cols<T>(Lv.max_nI, Lv.max_nB, Lv.max_w, G.leaf, G.d);
+  T* Z = (T*)Lv.zbuf + Lv.z_off[c];
+  int ld;
+  T* Fr = frame_of<T>(Lv, c, &ld);
+  int* ci = Lv.cpl_i + Lv.b_off[c];
+  T* ca = (T*)Lv.cpl_a + Lv.b_off[c];
+  const int m = G.leaf, m1 = m + 1;
   int origin[3] = {0, 0, 0};
   {
     int64_t code = Lv.cell_code[c];
@@ -98,9 +173,10 @@ __global__ void k_front_leaf(GeoDev G, LevelDev Lv, const double* diag, const do
       origin[a] = ((v - 1) / 2) * m;
     }
   }
-  int tab = 1;
-  for (int a = 0; a < G.d; ++a) tab *= m1;
+  if (threadIdx.x == 0) bad = 0;
   for (int i = threadIdx.x; i < tab; i += blockDim.x) postab[i] = -1;
+  for (int i = threadIdx.x; i < nI * w1; i += blockDim.x) sband[i] = T(0);
+  for (int64_t i = threadIdx.x; i < (int64_t)nB * nB; i += blockDim.x) Fr[i] = T(0);
   __syncthreads();
   for (int p = threadIdx.x; p < n; p += blockDim.x) {
     int x[3];
@@ -112,35 +188,298 @@ __global__ void k_front_leaf(GeoDev G, LevelDev Lv, const double* diag, const do
     }
     postab[lin] = p;
   }
-  for (int64_t idx = threadIdx.x; idx < (int64_t)n * n; idx += blockDim.x) F[idx] = T(0);
   __syncthreads();
+  // stencil entries: interior band, boundary couplings, this cell's share of A_BB
   for (int p = threadIdx.x; p < n; p += blockDim.x) {
     const int64_t g = gid[p];
     int x[3];
     coords1(G, g, x);
-    int lin = 0, mul = 1, lstride[3] = {1, 1, 1};
-    int onplane = 0;
+    int lin = 0, mul = 1, lstride[3] = {1, 1, 1}, onplane = 0;
     for (int a = 0; a < G.d; ++a) {
       lin += (x[a] - origin[a]) * mul;
       lstride[a] = mul;
       mul *= m1;
       onplane += (x[a] % m == 0);
     }
-    F[p + (int64_t)p * n] = T(diag[g] / double(1 << onplane));
+    const int b = p - nI;
+    if (p < nI) sband[p * w1] = T(diag[g]);
+    else {
+      Fr[b + (int64_t)b * ld] = T(diag[g] / double(1 << onplane));
+      ci[b] = -1;
+      ca[b] = T(0);
+    }
     for (int a = 0; a < G.d; ++a) {
-      const int others = onplane - (x[a] % m == 0);
-      const double share = double(1 << others);
+      const double share = double(1 << (onplane - (x[a] % m == 0)));
       const int lx = x[a] - origin[a];
-      if (x[a] + 1 <= G.ns[a] && lx + 1 <= m) {
-        const int q = postab[lin + lstride[a]];
-        if (q >= 0) F[p + (int64_t)q * n] = T(off[a * G.N + g] / share);
-      }
-      if (x[a] - 1 >= 1 && lx - 1 >= 0) {
-        const int q = postab[lin - lstride[a]];
-        if (q >= 0) F[p + (int64_t)q * n] = T(off[a * G.N + g - G.stride[a]] / share);
+      for (int dir = -1; dir <= 1; dir += 2) {
+        if (dir > 0 && !(x[a] + 1 <= G.ns[a] && lx + 1 <= m)) continue;
+        if (dir < 0 && !(x[a] - 1 >= 1 && lx - 1 >= 0)) continue;
+        const int q = postab[lin + dir * lstride[a]];
+        if (q < 0) continue;
+        const double v = dir > 0 ? off[a * G.N + g] : off[a * G.N + g - G.stride[a]];
+        if (p < nI) {
+          if (q < nI && q > p) sband[p * w1 + (q - p)] = T(v);   // column p of A_II, below diagonal
+        } else if (q < nI) {
+          ci[b] = q;
+          ca[b] = T(v);
+        } else {
+          Fr[b + (int64_t)(q - nI) * ld] = T(v / share);
+        }
       }
     }
   }
+  __syncthreads();
+  // banded Cholesky, right-looking over columns (column k holds L[k..k+w, k])
+  const bool cta_mode = w >= 32;
+  if (cta_mode || threadIdx.x < 32) {
+    const int nt = cta_mode ? blockDim.x : 32;
+    for (int k = 0; k < nI; ++k) {
+      T dkk = sband[k * w1];
+      if (!(dkk > T(0))) {
+        if (threadIdx.x == 0) bad = 1;
+        dkk = T(1);
+      }
+      const T s = my_sqrt(dkk);
+      const int wk = min(w, nI - 1 - k);
+      if (cta_mode) __syncthreads(); else __syncwarp();
+      for (int dd = 1 + threadIdx.x; dd <= wk; dd += nt) sband[k * w1 + dd] /= s;
+      if (threadIdx.x == 0) sband[k * w1] = s;
+      if (cta_mode) __syncthreads(); else __syncwarp();
+      for (int idx = threadIdx.x; idx < wk * wk; idx += nt) {
+        const int d1 = 1 + idx / wk, d2 = 1 + idx % wk;
+        if (d2 > d1) continue;
+        sband[(k + d2) * w1 + (d1 - d2)] -= sband[k * w1 + d1] * sband[k * w1 + d2];
+      }
+      if (cta_mode) __syncthreads(); else __syncwarp();
+    }
+  }
+  __syncthreads();
+  // Z = L^{-1} A_IB, stored Z[k*nB + b]; computed in shared-memory panels of
+  // pcols boundary columns, one column per thread
+  for (int b0 = 0; b0 < nB; b0 += pcols) {
+    const int nc = min(pcols, nB - b0);
+    for (int i = threadIdx.x; i < nI * pcols; i += blockDim.x) zp[i] = T(0);
+    __syncthreads();
+    for (int j = threadIdx.x; j < nc; j += blockDim.x) {
+      const int b = b0 + j;
+      const int i0 = ci[b];
+      if (i0 < 0) continue;
+      zp[i0 * pcols + j] = ca[b];
+      for (int k = i0; k < nI; ++k) {
+        const T zk = zp[k * pcols + j] / sband[k * w1];
+        zp[k * pcols + j] = zk;
+        const int wk = min(w, nI - 1 - k);
+        for (int dd = 1; dd <= wk; ++dd) zp[(k + dd) * pcols + j] -= sband[k * w1 + dd] * zk;
+      }
+    }
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < (int64_t)nI * nc; i += blockDim.x) {
+      const int k = (int)(i / nc), j = (int)(i % nc);
+      Z[(int64_t)k * nB + b0 + j] = zp[k * pcols + j];
+    }
+    __syncthreads();
+  }
+  // frame -= Z^T Z
+  cta_syrk_lower(Fr, ld, Z, nB, 0, nB, 0, nB, 0, nI, syrk_sm);
+  T* band = (T*)Lv.band + Lv.band_off[c];
+  for (int i = threadIdx.x; i < nI * w1; i += blockDim.x)
+    band[i] = (i % w1 == 0) ? T(1) / sband[i] : sband[i];
+  __syncthreads();
+  if (threadIdx.x == 0 && bad) report(status, RHIF_ERR_NOT_SPD, 0, kKindCell, c);
+}
+
+// Streaming variant for leaves whose boundary fits one 64 x 64 register tile
+// (2D): column k of the banded Cholesky, row k of Z = L^{-1} A_IB and the
+// rank-1 update S += z_k z_k^T are done in one pass over k, keeping only a
+// window of w+1 rows of Z in shared memory and S in registers (4 x 4 per
+// thread).  The result equals the panel version's (same operations on the same
+// entries, only Z is never stored).
+constexpr int kStreamNB = 64;
+
+template <typename T>
+size_t leaf_stream_smem(int max_nI, int max_w, int leaf, int d) {
+  int tab = 1;
+  for (int a = 0; a < d; ++a) tab *= leaf + 1;
+  size_t band = ((size_t)max_nI * (max_w + 1) * sizeof(T) + 15) & ~size_t(15);
+  size_t win = ((size_t)(max_w + 1) * kStreamNB * sizeof(T) + 15) & ~size_t(15);
+  size_t t = ((size_t)tab * sizeof(int) + 15) & ~size_t(15);
+  size_t pairs = ((size_t)(max_w * (max_w + 1) / 2) * 2 * sizeof(short) + 15) & ~size_t(15);
+  return band + win + t + pairs + 64;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_leaf_stream(GeoDev G, LevelDev Lv, const double* diag, const double* off, int* status) {
+  extern __shared__ unsigned char smraw[];
+  __shared__ int bad;
+  __shared__ T s_piv;
+  const int c = blockIdx.x;
+  const int nI = Lv.nI[c], nB = Lv.nB[c], n = nI + nB, w = Lv.band_w[c];
+  const int w1 = w + 1;
+  const int tid = threadIdx.x;
+  const int32_t* gid = Lv.gids + Lv.gid_off[c];
+  unsigned char* p = smraw;
+  T* sband = (T*)p;
+  p += ((size_t)Lv.max_nI * (Lv.max_w + 1) * sizeof(T) + 15) & ~size_t(15);
+  T* win = (T*)p;                                       // win[(k % w1) * 64 + b]
+  p += ((size_t)(Lv.max_w + 1) * kStreamNB * sizeof(T) + 15) & ~size_t(15);
+  int* postab = (int*)p;
+  int tab = 1;
+  for (int a = 0; a < G.d; ++a) tab *= G.leaf + 1;
+  p += ((size_t)tab * sizeof(int) + 15) & ~size_t(15);
+  short* pairs = (short*)p;                              // (d1, d2) with 1 <= d2 <= d1 <= w
+  const int npair = w * (w + 1) / 2;
+  int ld;
+  T* Fr = frame_of<T>(Lv, c, &ld);
+  int* ci = Lv.cpl_i + Lv.b_off[c];
+  T* ca = (T*)Lv.cpl_a + Lv.b_off[c];
+  const int m = G.leaf, m1 = m + 1;
+  int origin[3] = {0, 0, 0};
+  {
+    int64_t code = Lv.cell_code[c];
+    for (int a = 0; a < G.d; ++a) {
+      const int v = (int)(code % Lv.code_base);
+      code /= Lv.code_base;
+      origin[a] = ((v - 1) / 2) * m;
+    }
+  }
+  if (tid == 0) {
+    bad = 0;
+    int q = 0;
+    for (int d1 = 1; d1 <= w; ++d1)
+      for (int d2 = 1; d2 <= d1; ++d2) {
+        pairs[2 * q] = (short)d1;
+        pairs[2 * q + 1] = (short)d2;
+        ++q;
+      }
+  }
+  for (int i = tid; i < tab; i += blockDim.x) postab[i] = -1;
+  for (int i = tid; i < nI * w1; i += blockDim.x) sband[i] = T(0);
+  for (int i = tid; i < w1 * kStreamNB; i += blockDim.x) win[i] = T(0);
+  for (int64_t i = tid; i < (int64_t)nB * nB; i += blockDim.x) Fr[i] = T(0);
+  __syncthreads();
+  for (int q = tid; q < n; q += blockDim.x) {
+    int x[3];
+    coords1(G, gid[q], x);
+    int lin = 0, mul = 1;
+    for (int a = 0; a < G.d; ++a) {
+      lin += (x[a] - origin[a]) * mul;
+      mul *= m1;
+    }
+    postab[lin] = q;
+  }
+  __syncthreads();
+  for (int q = tid; q < n; q += blockDim.x) {
+    const int64_t g = gid[q];
+    int x[3];
+    coords1(G, g, x);
+    int lin = 0, mul = 1, lstride[3] = {1, 1, 1}, onplane = 0;
+    for (int a = 0; a < G.d; ++a) {
+      lin += (x[a] - origin[a]) * mul;
+      lstride[a] = mul;
+      mul *= m1;
+      onplane += (x[a] % m == 0);
+    }
+    const int b = q - nI;
+    if (q < nI) sband[q * w1] = T(diag[g]);
+    else {
+      Fr[b + (int64_t)b * ld] = T(diag[g] / double(1 << onplane));
+      ci[b] = -1;
+      ca[b] = T(0);
+    }
+    for (int a = 0; a < G.d; ++a) {
+      const double share = double(1 << (onplane - (x[a] % m == 0)));
+      const int lx = x[a] - origin[a];
+      for (int dir = -1; dir <= 1; dir += 2) {
+        if (dir > 0 && !(x[a] + 1 <= G.ns[a] && lx + 1 <= m)) continue;
+        if (dir < 0 && !(x[a] - 1 >= 1 && lx - 1 >= 0)) continue;
+        const int r = postab[lin + dir * lstride[a]];
+        if (r < 0) continue;
+        const double v = dir > 0 ? off[a * G.N + g] : off[a * G.N + g - G.stride[a]];
+        if (q < nI) {
+          if (r < nI && r > q) sband[q * w1 + (r - q)] = T(v);
+        } else if (r < nI) {
+          ci[b] = r;
+          ca[b] = T(v);
+        } else {
+          Fr[b + (int64_t)(r - nI) * ld] = T(v / share);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // initial rows 0..w of the Z window: the single entry a_b of column b sits in row ci[b]
+  for (int b = tid; b < nB; b += blockDim.x)
+    if (ci[b] >= 0 && ci[b] <= w) win[(ci[b] % w1) * kStreamNB + b] = ca[b];
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int bq = 0; bq < 4; ++bq) acc[a][bq] = T(0);
+  const int ti = (tid >> 4) * 4, tj = (tid & 15) * 4;   // this thread's 4 x 4 block of S
+  __syncthreads();
+  for (int k = 0; k < nI; ++k) {
+    const int wk = min(w, nI - 1 - k);
+    T* zk = win + (k % w1) * kStreamNB;
+    // 1. pivot of column k
+    if (tid == 0) {
+      T dkk = sband[k * w1];
+      if (!(dkk > T(0))) {
+        bad = 1;
+        dkk = T(1);
+      }
+      s_piv = my_sqrt(dkk);
+      sband[k * w1] = s_piv;
+    }
+    __syncthreads();
+    const T piv = s_piv;
+    // 2. scale column k of L and row k of Z
+    for (int dd = 1 + tid; dd <= wk; dd += blockDim.x) sband[k * w1 + dd] /= piv;
+    for (int b = tid; b < nB; b += blockDim.x) zk[b] /= piv;
+    __syncthreads();
+    // 3. trailing band update, Z rows k+1..k+wk, and S += z_k z_k^T
+    for (int q = tid; q < npair; q += blockDim.x) {
+      const int d1 = pairs[2 * q], d2 = pairs[2 * q + 1];
+      if (d1 > wk) continue;
+      sband[(k + d2) * w1 + (d1 - d2)] -= sband[k * w1 + d1] * sband[k * w1 + d2];
+    }
+    for (int idx = tid; idx < wk * nB; idx += blockDim.x) {
+      const int dd = 1 + idx / nB, b = idx % nB;
+      win[((k + dd) % w1) * kStreamNB + b] -= sband[k * w1 + dd] * zk[b];
+    }
+    {
+      T zi[4], zj[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        zi[a] = zk[ti + a];
+        zj[a] = zk[tj + a];
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int bq = 0; bq < 4; ++bq) acc[a][bq] += zi[a] * zj[bq];
+    }
+    __syncthreads();
+    // 4. recycle row k's slot for row k + w1
+    const int nr = k + w1;
+    for (int b = tid; b < kStreamNB; b += blockDim.x)
+      zk[b] = (nr < nI && b < nB && ci[b] == nr) ? ca[b] : T(0);
+    __syncthreads();
+  }
+  // frame = A_BB share - S (lower triangle)
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int bq = 0; bq < 4; ++bq) {
+      const int i = ti + a, j = tj + bq;
+      if (i < nB && j < nB && i >= j) Fr[i + (int64_t)j * ld] -= acc[a][bq];
+    }
+  // band with reciprocal diagonal for the application
+  T* band = (T*)Lv.band + Lv.band_off[c];
+  for (int i = tid; i < nI * w1; i += blockDim.x)
+    band[i] = (i % w1 == 0) ? T(1) / sband[i] : sband[i];
+  __syncthreads();
+  if (tid == 0 && bad) report(status, RHIF_ERR_NOT_SPD, 0, kKindCell, c);
 }
 
 // ---------------------------------------------------------------------------
@@ -157,22 +496,23 @@ __global__ void k_extend_add(LevelDev cur, LevelDev prev) {
   for (int k = cur.ea_off[c]; k < cur.ea_off[c + 1]; ++k) {
     const int pc = cur.ea_child[k];
     const int* map = cur.ea_map + cur.ea_map_off[k];
-    const int nIc = prev.nI[pc], nbc = prev.nB[pc], nc = nIc + nbc;
-    const T* Fc = (const T*)prev.front + prev.front_off[pc] + nIc + (int64_t)nIc * nc;
+    const int nbc = prev.nB[pc];
+    int ldc;
+    const T* Fc = frame_of<T>(prev, pc, &ldc);
     for (int64_t idx = threadIdx.x; idx < (int64_t)nbc * nbc; idx += blockDim.x) {
       const int i = (int)(idx % nbc), j = (int)(idx / nbc);
       if (i < j) continue;
       const int pi = map[i], pj = map[j];
       if (pi < 0 || pj < 0) continue;
       const int r = max(pi, pj), s = min(pi, pj);
-      F[r + (int64_t)s * n] += Fc[i + (int64_t)j * nc];
+      F[r + (int64_t)s * n] += Fc[i + (int64_t)j * ldc];
     }
     __syncthreads();
   }
 }
 
 // ---------------------------------------------------------------------------
-// cell elimination (Sec. 2.1): partial Cholesky of every front
+// cell elimination (Sec. 2.1) of dense fronts: partial Cholesky
 // ---------------------------------------------------------------------------
 
 template <typename T>
@@ -183,19 +523,12 @@ __global__ void __launch_bounds__(kThreads) k_partial_chol(LevelDev Lv, int* sta
   const int nI = Lv.nI[c], n = nI + Lv.nB[c];
   T* F = (T*)Lv.front + Lv.front_off[c];
   if (!cta_partial_chol(F, n, n, nI, sm) && threadIdx.x == 0)
-    report(status, RHIF_ERR_NOT_SPD, Lv.level, Lv.level < 0 ? kKindRoot : kKindCell, c);
+    report(status, RHIF_ERR_NOT_SPD, Lv.level, kKindCell, c);
 }
 
 // ---------------------------------------------------------------------------
 // block Jacobi preconditioning (Sec. 2.3)
 // ---------------------------------------------------------------------------
-
-template <typename T>
-__device__ inline T* frame_of(const LevelDev& Lv, int c, int* ld) {
-  const int nI = Lv.nI[c], n = nI + Lv.nB[c];
-  *ld = n;
-  return (T*)Lv.front + Lv.front_off[c] + nI + (int64_t)nI * n;
-}
 
 // L_g = chol(sum over the cells holding g of their diagonal block of g)
 template <typename T>
@@ -204,7 +537,7 @@ __global__ void __launch_bounds__(kThreads) k_precond_diag(LevelDev Lv, PhaseDev
   T* sm = (T*)smraw;
   const int b = blockIdx.x;
   const int g = Ph.pre_group[b];
-  const int sz = (int)(Lv.group_gid_off[g + 1] - Lv.group_gid_off[g]);
+  const int sz = Lv.group_size[g];
   T* Lg = (T*)Ph.Lbuf + Ph.pre_off[b];
   for (int64_t idx = threadIdx.x; idx < (int64_t)sz * sz; idx += blockDim.x) {
     const int i = (int)(idx % sz), j = (int)(idx / sz);
@@ -226,14 +559,26 @@ __global__ void __launch_bounds__(kThreads) k_precond_diag(LevelDev Lv, PhaseDev
 
 // frame <- D^{-1} frame D^{-T}, D = block diag of the L_g of the frame's groups
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_precond_scale(LevelDev Lv, PhaseDev Ph) {
+__global__ void __launch_bounds__(kThreads) k_precond_scale(LevelDev Lv, PhaseDev Ph, int stage) {
+  extern __shared__ unsigned char smraw[];
   const int c = blockIdx.x;
-  int ld;
-  T* Fr = frame_of<T>(Lv, c, &ld);
+  int gld;
+  T* Fg = frame_of<T>(Lv, c, &gld);
   const int nb = Lv.nB[c];
-  for (int64_t idx = threadIdx.x; idx < (int64_t)nb * nb; idx += blockDim.x) {
-    const int i = (int)(idx % nb), j = (int)(idx / nb);
-    if (i < j) Fr[i + (int64_t)j * ld] = Fr[j + (int64_t)i * ld];
+  T* Fr = Fg;
+  int ld = gld;
+  if (stage) {   // work on a full symmetric copy in shared memory
+    Fr = (T*)smraw;
+    ld = nb;
+    for (int64_t idx = threadIdx.x; idx < (int64_t)nb * nb; idx += blockDim.x) {
+      const int i = (int)(idx % nb), j = (int)(idx / nb);
+      Fr[idx] = sym_at(Fg, gld, i, j);
+    }
+  } else {
+    for (int64_t idx = threadIdx.x; idx < (int64_t)nb * nb; idx += blockDim.x) {
+      const int i = (int)(idx % nb), j = (int)(idx / nb);
+      if (i < j) Fr[i + (int64_t)j * ld] = Fr[j + (int64_t)i * ld];
+    }
   }
   __syncthreads();
   const int s0 = Lv.seg_off[c], s1 = Lv.seg_off[c + 1];
@@ -244,7 +589,7 @@ __global__ void __launch_bounds__(kThreads) k_precond_scale(LevelDev Lv, PhaseDe
     const int g = Lv.seg_group[s];
     const int pi = Ph.group_pre[g];
     if (pi < 0) continue;
-    const int sz = (int)(Lv.group_gid_off[g + 1] - Lv.group_gid_off[g]);
+    const int sz = Lv.group_size[g];
     const int pos = Lv.seg_pos[s];
     const T* Lg = (const T*)Ph.Lbuf + Ph.pre_off[pi];
     T* col = Fr + (int64_t)j * ld + pos;
@@ -261,7 +606,7 @@ __global__ void __launch_bounds__(kThreads) k_precond_scale(LevelDev Lv, PhaseDe
     const int g = Lv.seg_group[s];
     const int pi = Ph.group_pre[g];
     if (pi < 0) continue;
-    const int sz = (int)(Lv.group_gid_off[g + 1] - Lv.group_gid_off[g]);
+    const int sz = Lv.group_size[g];
     const int pos = Lv.seg_pos[s];
     const T* Lg = (const T*)Ph.Lbuf + Ph.pre_off[pi];
     T* row = Fr + i + (int64_t)pos * ld;
@@ -269,6 +614,13 @@ __global__ void __launch_bounds__(kThreads) k_precond_scale(LevelDev Lv, PhaseDe
       T v = row[(int64_t)a * ld];
       for (int q = 0; q < a; ++q) v -= Lg[a + (int64_t)q * sz] * row[(int64_t)q * ld];
       row[(int64_t)a * ld] = v / Lg[a + (int64_t)a * sz];
+    }
+  }
+  if (stage) {
+    __syncthreads();
+    for (int64_t idx = threadIdx.x; idx < (int64_t)nb * nb; idx += blockDim.x) {
+      const int i = (int)(idx % nb), j = (int)(idx / nb);
+      Fg[i + (int64_t)j * gld] = Fr[idx];
     }
   }
 }
@@ -281,41 +633,74 @@ template <typename T> __device__ inline T my_abs(T x) { return x < T(0) ? -x : x
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_skel(LevelDev Lv, PhaseDev Ph, uint8_t* alive,
-                                                   double tol, int* status) {
+                                                   double tol, int* status, int mstage) {
   extern __shared__ unsigned char smraw[];
   T* sm = (T*)smraw;                                   // partial-Cholesky workspace
   T* nrm = sm + partial_chol_smem_elems();             // [max_n]
   int* sperm = (int*)(nrm + Ph.max_n);                 // [max_n]
-  __shared__ int s_k, s_stop, s_p;
+  __shared__ int s_k, s_stop, s_p, s_nrg;
   __shared__ T s_r11;
+  __shared__ int rg_group[kMaxRowGroupsDev], rg_row0[kMaxRowGroupsDev + 1];
+  __shared__ int rg_pos[kMaxRowGroupsDev][kMaxSlotsDev];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   const int u = blockIdx.x;
   const int g = Ph.u_group[u];
-  const int64_t g0 = Lv.group_gid_off[g];
-  const int n = (int)(Lv.group_gid_off[g + 1] - g0);
-  const int64_t* gg = Lv.group_gids + g0;
+  const int n = Lv.group_size[g];
   const int nrow = Ph.u_nrow[u];
   const int ldm = nrow > 0 ? nrow : 1;
   T* M = (T*)Ph.Mbuf + Ph.u_m_off[u];
+  if (mstage) M = (T*)((unsigned char*)(sperm + Ph.max_n) + 16 - (((size_t)(sperm + Ph.max_n)) & 15));
   T* Aee = M + (int64_t)nrow * n;
   T* Fu = (T*)Ph.rec + Ph.u_rec_off[u];
   T* Tm = Fu + (int64_t)n * n;
   const int c0 = Lv.group_cell_off[g], c1 = Lv.group_cell_off[g + 1];
+  const int nslot = c1 - c0;
 
-  // 1. gather A_{R,I} (rows summed over the cells holding them, in cell order) and A_II
-  const int64_t rb = Ph.u_row_off[u];
-  for (int64_t idx = tid; idx < (int64_t)nrow * n; idx += blockDim.x) {
-    const int r = (int)(idx % nrow), j = (int)(idx / nrow);
-    const int64_t gr = rb + r;
-    T v = T(0);
-    if (alive[Ph.u_row_gid[gr]]) {
-      for (int64_t s = Ph.row_src_off[gr]; s < Ph.row_src_off[gr + 1]; ++s) {
-        int ld;
-        const T* fr = frame_of<T>(Lv, Ph.src_cell[s], &ld);
-        v += sym_at(fr, ld, Ph.src_pos[s], Ph.src_upos[s] + j);
+  // 1. rows of A_{R,I}: the other separator groups of the holding cells, each
+  //    group once, summed over the holding cells in cell order
+  if (tid == 0) {
+    int nrg = 0, row = 0;
+    for (int s = 0; s < nslot; ++s) {
+      const int c = Lv.group_cell[c0 + s];
+      for (int q = Lv.seg_off[c]; q < Lv.seg_off[c + 1]; ++q) {
+        const int sg = Lv.seg_group[q];
+        if (sg == g) continue;
+        int f = -1;
+        for (int i = 0; i < nrg; ++i)
+          if (rg_group[i] == sg) f = i;
+        if (f < 0) {
+          if (nrg >= kMaxRowGroupsDev) continue;
+          f = nrg++;
+          rg_group[f] = sg;
+          rg_row0[f] = row;
+          row += Lv.group_size[sg];
+          for (int t = 0; t < kMaxSlotsDev; ++t) rg_pos[f][t] = -1;
+        }
+        rg_pos[f][s] = Lv.seg_pos[q];
       }
     }
-    M[r + (int64_t)j * ldm] = v;
+    rg_row0[nrg] = row;
+    s_nrg = nrg;
+    if (row != nrow) report(status, RHIF_ERR_BAD_ARG, Lv.level, kKindUnit, g);
+  }
+  __syncthreads();
+  for (int f = 0; f < s_nrg; ++f) {
+    const int sg = rg_group[f], r0 = rg_row0[f], sz = Lv.group_size[sg];
+    const int32_t* sgid = Lv.bucket + Lv.group_start[sg];
+    for (int idx = tid; idx < sz * n; idx += blockDim.x) {
+      const int o = idx % sz, j = idx / sz;
+      T v = T(0);
+      if (alive[sgid[o]]) {
+        for (int s = 0; s < nslot; ++s) {
+          const int pos = rg_pos[f][s];
+          if (pos < 0) continue;
+          int ld;
+          const T* fr = frame_of<T>(Lv, Lv.group_cell[c0 + s], &ld);
+          v += sym_at(fr, ld, pos + o, Lv.group_pos[c0 + s] + j);
+        }
+      }
+      if (r0 + o < nrow) M[(r0 + o) + (int64_t)j * ldm] = v;
+    }
   }
   for (int64_t idx = tid; idx < (int64_t)n * n; idx += blockDim.x) {
     const int i = (int)(idx % n), j = (int)(idx / n);
@@ -459,11 +844,19 @@ __global__ void __launch_bounds__(kThreads) k_skel(LevelDev Lv, PhaseDev Ph, uin
     }
   }
   int* perm_out = Ph.perm + Ph.u_perm_off[u];
-  for (int i = tid; i < n; i += blockDim.x) {
-    perm_out[i] = sperm[i];
-    if (i >= k) alive[gg[sperm[i]]] = 0;
-  }
+  for (int i = tid; i < n; i += blockDim.x) perm_out[i] = sperm[i];
   if (tid == 0) Ph.rank[u] = k;
+}
+
+// Redundant DOFs leave the active set only after every ID of the phase has
+// been taken (the IDs all read the same matrix, Sec. 2.2 parallel order).
+__global__ void k_mark_dead(LevelDev Lv, PhaseDev Ph, uint8_t* alive) {
+  const int u = blockIdx.x;
+  const int g = Ph.u_group[u];
+  const int n = Lv.group_size[g], k = Ph.rank[u];
+  const int32_t* gg = Lv.bucket + Lv.group_start[g];
+  const int* perm = Ph.perm + Ph.u_perm_off[u];
+  for (int i = k + threadIdx.x; i < n; i += blockDim.x) alive[gg[perm[i]]] = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -481,13 +874,21 @@ void launch_stencil_from_csr(const GeoDev& G, const int64_t* rowptr, const int32
   k_stencil_check<<<blocks_for(G.d * G.N, 256), 256, 0, s>>>(G.d * G.N, off, offb, status);
 }
 
+void launch_expand_gids(const LevelDev& Lv, cudaStream_t s) {
+  if (Lv.ncell) k_expand_gids<<<Lv.ncell, 128, 0, s>>>(Lv);
+}
+
 template <typename T>
-void launch_front_leaf(const GeoDev& G, const LevelDev& Lv, const double* diag, const double* off,
-                       int* status, cudaStream_t s) {
+void launch_leaf_elim(const GeoDev& G, const LevelDev& Lv, const double* diag, const double* off,
+                      int* status, cudaStream_t s) {
   if (!Lv.ncell) return;
-  int tab = 1;
-  for (int a = 0; a < G.d; ++a) tab *= G.leaf + 1;
-  k_front_leaf<T><<<Lv.ncell, kThreads, tab * sizeof(int), s>>>(G, Lv, diag, off, status);
+  if (Lv.max_nB <= kStreamNB) {
+    const size_t sm = leaf_stream_smem<T>(Lv.max_nI, Lv.max_w, G.leaf, G.d);
+    k_leaf_stream<T><<<Lv.ncell, kThreads, sm, s>>>(G, Lv, diag, off, status);
+    return;
+  }
+  const size_t sm = leaf_smem_bytes<T>(Lv.max_nI, Lv.max_nB, Lv.max_w, G.leaf, G.d);
+  k_leaf_elim<T><<<Lv.ncell, kThreads, sm, s>>>(G, Lv, diag, off, status);
 }
 
 template <typename T>
@@ -510,41 +911,53 @@ void launch_precond_diag(const LevelDev& Lv, const PhaseDev& Ph, int* status, cu
 
 template <typename T>
 void launch_precond_scale(const LevelDev& Lv, const PhaseDev& Ph, cudaStream_t s) {
-  if (Ph.npre && Lv.ncell) k_precond_scale<T><<<Lv.ncell, kThreads, 0, s>>>(Lv, Ph);
+  if (!(Ph.npre && Lv.ncell)) return;
+  const size_t blk = (size_t)Lv.max_nB * Lv.max_nB * sizeof(T);
+  const int stage = blk <= 200 * 1024;
+  k_precond_scale<T><<<Lv.ncell, kThreads, stage ? blk : 0, s>>>(Lv, Ph, stage);
 }
 
 template <typename T>
 size_t skel_smem_bytes(int max_n) {
-  return partial_chol_smem_elems() * sizeof(T) + (size_t)max_n * (sizeof(T) + sizeof(int)) + 16;
+  return partial_chol_smem_elems() * sizeof(T) + (size_t)max_n * (sizeof(T) + sizeof(int)) + 32;
 }
 
 template <typename T>
 void launch_skel(const LevelDev& Lv, const PhaseDev& Ph, uint8_t* alive, double tol, int* status,
-                 cudaStream_t s) {
+                 int64_t max_m_elems, cudaStream_t s) {
   if (!Ph.nunit) return;
-  const size_t sm = skel_smem_bytes<T>(Ph.max_n);
-  k_skel<T><<<Ph.nunit, kThreads, sm, s>>>(Lv, Ph, alive, tol, status);
+  size_t sm = skel_smem_bytes<T>(Ph.max_n);
+  const size_t mb = (size_t)max_m_elems * sizeof(T);
+  const int mstage = sm + mb <= 200 * 1024;
+  if (mstage) sm += mb;
+  k_skel<T><<<Ph.nunit, kThreads, sm, s>>>(Lv, Ph, alive, tol, status, mstage);
+  k_mark_dead<<<Ph.nunit, 32, 0, s>>>(Lv, Ph, alive);
 }
 
 template <typename T>
 int configure_factor_kernels() {
-  const int big = 200 * 1024;
+  const int big = 220 * 1024;
   cudaError_t e = cudaFuncSetAttribute(k_skel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  if (e != cudaSuccess) return -1;
-  e = cudaFuncSetAttribute(k_front_leaf<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_leaf_elim<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_precond_scale<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_leaf_stream<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   return e == cudaSuccess ? 0 : -1;
 }
 
 #define RHIF_INST(T)                                                                              \
-  template void launch_front_leaf<T>(const GeoDev&, const LevelDev&, const double*, const double*, \
-                                     int*, cudaStream_t);                                          \
-  template void launch_extend_add<T>(const LevelDev&, const LevelDev&, cudaStream_t);              \
-  template void launch_partial_chol<T>(const LevelDev&, int*, cudaStream_t);                       \
-  template void launch_precond_diag<T>(const LevelDev&, const PhaseDev&, int*, cudaStream_t);      \
-  template void launch_precond_scale<T>(const LevelDev&, const PhaseDev&, cudaStream_t);           \
-  template void launch_skel<T>(const LevelDev&, const PhaseDev&, uint8_t*, double, int*,           \
-                               cudaStream_t);                                                      \
-  template size_t skel_smem_bytes<T>(int);                                                         \
+  template size_t leaf_smem_bytes<T>(int, int, int, int, int);                                    \
+  template void launch_leaf_elim<T>(const GeoDev&, const LevelDev&, const double*, const double*, \
+                                    int*, cudaStream_t);                                          \
+  template void launch_extend_add<T>(const LevelDev&, const LevelDev&, cudaStream_t);             \
+  template void launch_partial_chol<T>(const LevelDev&, int*, cudaStream_t);                      \
+  template void launch_precond_diag<T>(const LevelDev&, const PhaseDev&, int*, cudaStream_t);     \
+  template void launch_precond_scale<T>(const LevelDev&, const PhaseDev&, cudaStream_t);          \
+  template void launch_skel<T>(const LevelDev&, const PhaseDev&, uint8_t*, double, int*, int64_t, \
+                               cudaStream_t);                                                     \
+  template size_t skel_smem_bytes<T>(int);                                                        \
   template int configure_factor_kernels<T>();
 
 RHIF_INST(double)

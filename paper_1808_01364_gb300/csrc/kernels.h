@@ -13,9 +13,12 @@ enum { kScRZ = 0, kScPQ = 1, kScRR = 2, kScFF = 3, kScAlpha = 4, kScDone = 5, kS
 void launch_stencil_from_csr(const GeoDev& G, const int64_t* rowptr, const int32_t* col,
                              const double* val, int64_t nnz, double* diag, double* off,
                              double* offb, int* status, cudaStream_t s);
+void launch_expand_gids(const LevelDev& Lv, cudaStream_t s);
 template <typename T>
-void launch_front_leaf(const GeoDev& G, const LevelDev& Lv, const double* diag, const double* off,
-                       int* status, cudaStream_t s);
+size_t leaf_smem_bytes(int max_nI, int max_nB, int max_w, int leaf, int d);
+template <typename T>
+void launch_leaf_elim(const GeoDev& G, const LevelDev& Lv, const double* diag, const double* off,
+                      int* status, cudaStream_t s);
 template <typename T>
 void launch_extend_add(const LevelDev& cur, const LevelDev& prev, cudaStream_t s);
 template <typename T>
@@ -26,7 +29,7 @@ template <typename T>
 void launch_precond_scale(const LevelDev& Lv, const PhaseDev& Ph, cudaStream_t s);
 template <typename T>
 void launch_skel(const LevelDev& Lv, const PhaseDev& Ph, uint8_t* alive, double tol, int* status,
-                 cudaStream_t s);
+                 int64_t max_m_elems, cudaStream_t s);
 template <typename T>
 size_t skel_smem_bytes(int max_n);
 template <typename T>

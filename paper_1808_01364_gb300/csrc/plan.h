@@ -1,17 +1,22 @@
 // Host-side level plan: the quadtree/octree grouping of the active DOFs
 // (Sec. 3.1, Fig. 3; Sec. 3.2) turned into flat index tables for the kernels.
 //
-// At level l the cells are 2^l m intervals wide.  Along each axis a node
+// At level l the cells are w = 2^l m intervals wide.  Along each axis a node
 // coordinate x maps to v = 2*(x / w) + (x % w != 0): odd v lies inside cell
 // (v-1)/2, even v on the plane between cells v/2-1 and v/2.  A group is the
-// set of active DOFs with equal (v0,v1,v2); its type t is the number of even
-// components (0 = cell interior, 1 = edge/face, 2 = corner/3D edge, 3 = 3D
-// corner).  Group members are kept in ascending DOF index.
+// set of active DOFs with equal (v0,v1,v2) ("code"); its type t is the number
+// of even components (0 = cell interior, 1 = edge/face, 2 = corner/3D edge,
+// 3 = 3D corner).  All active DOFs are stored once, sorted by code and, inside
+// a code, by ascending DOF index (the `bucket` array); cells and groups are
+// ranges of it.
 //
-// Every cell owns a dense front over [I ; B]: its interior I followed by the
-// separator groups of its closure B, in group-code order.  The per-cell
+// Every cell owns a front over [I ; B]: its interior I followed by the
+// separator groups of its closure (its "segments"), in code order.  The per-cell
 // Schur complements ("frames", the B x B block after elimination) are kept
 // unassembled: the level matrix is the sum over cells of their frames.
+// Level 0 eliminates I with a banded Cholesky straight from the stencil and
+// writes only the frames; levels >= 1 assemble dense fronts from the children's
+// frames (extend-add).
 #pragma once
 #include <cstdint>
 #include <vector>
@@ -29,28 +34,26 @@ struct Geometry {
 
 Geometry make_geometry(int d, const int* ns, int leaf);
 
+// Largest number of distinct row groups of one skeletonization unit (see unit_rows).
+constexpr int kMaxRowGroups = 128;
+constexpr int kMaxSlots = 4;
+
 struct UnitTable {
-  // one row per skeletonization unit (groups of type t == unit_type)
-  std::vector<int> group;          // group index
+  std::vector<int> group;          // group index of each unit (groups of type t == unit_type)
   std::vector<int> nrow;           // |R|
-  std::vector<int64_t> row_off;    // into row_gid (nunit + 1)
-  std::vector<int64_t> row_gid;    // DOF of each row of A_{R,I}
-  std::vector<int64_t> row_src_off; // per row (over all units, +1): range into src_*
-  std::vector<int> src_cell, src_pos, src_upos; // frame entries summed into a row, in cell order:
-                                                // cell, row position and unit offset in that cell's B
-  std::vector<int64_t> m_off;      // scratch offset: M (nrow x n) then A_ee (n x n)
+  std::vector<int64_t> m_off;      // scratch: M (nrow x n) then A_ee (n x n)
   int64_t m_total = 0;
-  std::vector<int64_t> rec_off;    // record offset: unit front (n x n) then T (n x n)
+  std::vector<int64_t> rec_off;    // record: unit front (n x n) then T (n x n)
   int64_t rec_total = 0;
   std::vector<int64_t> perm_off;   // pivot order (n ints)
   int64_t perm_total = 0;
   int max_n = 0;
+  int64_t max_m = 0;               // largest (nrow + n) * n of the phase
 };
 
 struct PhasePlan {
   int unit_type = 1;                 // skeletonized groups: t == unit_type
   int pre_min_type = 1;              // preconditioned groups: t >= pre_min_type
-  bool precondition = true;
   std::vector<int> pre_group;        // groups preconditioned in this phase
   std::vector<int64_t> pre_off;      // offset of L_g (|g|^2) in the phase's L buffer
   int64_t pre_total = 0;
@@ -60,25 +63,35 @@ struct PhasePlan {
 };
 
 struct LevelPlan {
-  int level = 0, width = 0;
+  int level = 0, width = 0, code_base = 0;
+  std::vector<int32_t> bucket;       // active DOFs sorted by (code, index)
   // cells
   std::vector<int64_t> cell_code;
+  std::vector<int32_t> cell_start;   // bucket offset of the interior
   std::vector<int> nI, nB;
-  std::vector<int64_t> front_off;    // element offsets; front of cell c is n x n, n = nI + nB
-  int64_t front_total = 0;
-  std::vector<int64_t> gid_off;      // into gids (ncell + 1): front order, I then B
-  std::vector<int64_t> gids;
+  std::vector<int64_t> gid_off;      // front-order DOF list offsets (ncell + 1), expanded on the device
   std::vector<int64_t> b_off;        // prefix sums of nB (ncell + 1)
-  int max_nI = 0, max_nB = 0, max_n = 0;
+  std::vector<int64_t> front_off;    // level >= 1: dense n x n front
+  int64_t front_total = 0;
+  std::vector<int64_t> frame_off;    // B x B frame (level 0: own buffer; else inside the front)
+  std::vector<int> frame_ld;
+  int64_t frame_total = 0;           // level 0 frame buffer size
+  // level 0: banded leaf factors
+  std::vector<int> band_w;           // half bandwidth of the interior block
+  std::vector<int64_t> band_off;     // nI x (w+1) band of L
+  int64_t band_total = 0;
+  std::vector<int64_t> z_off;        // scratch nI x nB for L^{-1} A_IB
+  int64_t z_total = 0;
+  int max_nI = 0, max_nB = 0, max_n = 0, max_w = 0;
   // segments of each cell's B
   std::vector<int> seg_off;          // ncell + 1
   std::vector<int> seg_group, seg_pos;
   // groups (t >= 1)
   std::vector<int64_t> group_code;
   std::vector<int> group_t;
-  std::vector<int64_t> group_gid_off;   // ngroup + 1
-  std::vector<int64_t> group_gids;
-  std::vector<int> group_cell_off;      // ngroup + 1
+  std::vector<int32_t> group_start;  // bucket offset
+  std::vector<int> group_size;
+  std::vector<int> group_cell_off;   // ngroup + 1
   std::vector<int> group_cell, group_pos;
   int max_group = 0;
   // extend-add (level >= 1): children frames of the previous level
@@ -93,10 +106,19 @@ struct LevelPlan {
   int ngroup() const { return (int)group_t.size(); }
 };
 
-// Build the plan of level `level` from the active DOFs (alive[g] != 0).
-// `prev` is the plan of level-1 (nullptr at level 0).  For level == G.L only
-// the root front is built (no phases).
-LevelPlan build_level(const Geometry& G, int level, const std::vector<uint8_t>& alive,
-                      const LevelPlan* prev, bool precondition, bool edge_skel);
+// Build the plan of level `level`.  `active` lists the active DOFs in
+// ascending order (ignored at level 0, where every DOF is active); `alive`
+// flags them by DOF index; `prev` is the plan of level-1.  For
+// level == G.L only the root front is built (no phases).
+LevelPlan build_level(const Geometry& G, int level, const std::vector<int32_t>& active,
+                      const std::vector<uint8_t>& alive, const LevelPlan* prev,
+                      bool precondition, bool edge_skel);
+
+// Row layout of A_{R,I} for a unit: the distinct separator groups other than
+// the unit itself, over the cells holding the unit in cell order, each cell's
+// segments in code order; a group met again in a later cell is not repeated
+// (its entries from every holding cell are summed into the same rows).
+// Returns the number of rows.
+int unit_row_count(const LevelPlan& P, int group);
 
 }  // namespace rhif

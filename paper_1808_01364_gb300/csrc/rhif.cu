@@ -7,6 +7,7 @@
 // level.  The root front A_L (Eq. 3.3) is level L of the same machinery.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -86,12 +87,12 @@ struct Packer {
 // kernel instrumentation: launch counters per category, optional CUDA-event timing
 // ---------------------------------------------------------------------------
 enum Cat {
-  kCatStencil, kCatFrontLeaf, kCatExtendAdd, kCatPartialChol, kCatPrecondDiag, kCatPrecondScale,
+  kCatStencil, kCatLeafElim, kCatExpandGids, kCatExtendAdd, kCatPartialChol, kCatPrecondDiag, kCatPrecondScale,
   kCatSkel, kCatApplyCellUp, kCatApplyCellDown, kCatApplyGroupUp, kCatApplyGroupDown, kCatSpmv,
   kCatVector, kCatAssemble, kCatGrad, kNumCat
 };
 static const char* kCatName[kNumCat] = {
-    "stencil_from_csr", "front_leaf", "extend_add", "partial_chol", "precond_diag",
+    "stencil_from_csr", "leaf_elim", "expand_gids", "extend_add", "partial_chol", "precond_diag",
     "precond_scale", "skel", "apply_cell_up", "apply_cell_down", "apply_group_up",
     "apply_group_down", "spmv", "pcg_vector", "assemble_fd", "grad_logcoef"};
 struct KStat {
@@ -106,6 +107,18 @@ struct Pending {
   cudaEvent_t a, b;
 };
 static std::vector<Pending> g_pending;
+static std::vector<cudaEvent_t> g_event_pool;
+
+static cudaEvent_t pooled_event() {
+  if (!g_event_pool.empty()) {
+    cudaEvent_t e = g_event_pool.back();
+    g_event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
 
 // Counts (and, with timing on, brackets with events) the launches issued while alive.
 struct Launch {
@@ -118,8 +131,8 @@ struct Launch {
     g_kstat[cat].flops += flops;
     g_kstat[cat].bytes += bytes;
     if (g_timing) {
-      cudaEventCreate(&a);
-      cudaEventCreate(&b);
+      a = pooled_event();
+      b = pooled_event();
       cudaEventRecord(a, s);
     }
   }
@@ -197,6 +210,14 @@ static int configure_once() {
   if (!done) {
     rc = configure_factor_kernels<T>();
     if (rc == 0) rc = configure_apply_kernels<T>();
+    // keep freed factor memory in this process's stream-ordered pool between factorizations
+    int dev = 0;
+    cudaMemPool_t pool;
+    if (rc == 0 && cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t thr = ~0ull;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
     done = 1;
   }
   return rc;
@@ -206,57 +227,63 @@ static int configure_once() {
 static int upload_level(rhif_handle* H, LevelStore& S, size_t elem) {
   const LevelPlan& P = S.plan;
   Packer pk;
-  const size_t o_code = pk.add(P.cell_code), o_foff = pk.add(P.front_off), o_nI = pk.add(P.nI),
-               o_nB = pk.add(P.nB), o_goff = pk.add(P.gid_off), o_gids = pk.add(P.gids),
-               o_boff = pk.add(P.b_off), o_soff = pk.add(P.seg_off), o_sg = pk.add(P.seg_group),
-               o_sp = pk.add(P.seg_pos), o_gt = pk.add(P.group_t),
-               o_ggo = pk.add(P.group_gid_off), o_ggid = pk.add(P.group_gids),
+  const size_t o_bucket = pk.add(P.bucket), o_code = pk.add(P.cell_code),
+               o_cstart = pk.add(P.cell_start), o_nI = pk.add(P.nI), o_nB = pk.add(P.nB),
+               o_goff = pk.add(P.gid_off), o_boff = pk.add(P.b_off), o_foff = pk.add(P.front_off),
+               o_froff = pk.add(P.frame_off), o_frld = pk.add(P.frame_ld),
+               o_bw = pk.add(P.band_w), o_boff2 = pk.add(P.band_off), o_zoff = pk.add(P.z_off),
+               o_soff = pk.add(P.seg_off), o_sg = pk.add(P.seg_group), o_sp = pk.add(P.seg_pos),
+               o_gt = pk.add(P.group_t), o_gs = pk.add(P.group_start), o_gsz = pk.add(P.group_size),
                o_gco = pk.add(P.group_cell_off), o_gc = pk.add(P.group_cell),
                o_gp = pk.add(P.group_pos), o_eao = pk.add(P.ea_off), o_eac = pk.add(P.ea_child),
                o_eamo = pk.add(P.ea_map_off), o_eam = pk.add(P.ea_map);
   struct PhOff {
-    size_t pg, po, gp, ug, un, uro, urg, rso, sc, sp, su, umo, uro2, upo, gu;
+    size_t pg, po, gp, ug, un, umo, uro, upo, gu;
   };
   std::vector<PhOff> po(P.phases.size());
   for (size_t i = 0; i < P.phases.size(); ++i) {
     const PhasePlan& ph = P.phases[i];
     const UnitTable& U = ph.units;
     po[i] = {pk.add(ph.pre_group), pk.add(ph.pre_off), pk.add(ph.group_pre), pk.add(U.group),
-             pk.add(U.nrow), pk.add(U.row_off), pk.add(U.row_gid), pk.add(U.row_src_off),
-             pk.add(U.src_cell), pk.add(U.src_pos), pk.add(U.src_upos), pk.add(U.m_off),
-             pk.add(U.rec_off), pk.add(U.perm_off), pk.add(ph.group_unit)};
+             pk.add(U.nrow), pk.add(U.m_off), pk.add(U.rec_off), pk.add(U.perm_off),
+             pk.add(ph.group_unit)};
   }
   void* d = nullptr;
   int rc = H->mem.get(&d, pk.host.size());
   if (rc) return rc;
   S.tables = d;
   CK(cudaMemcpyAsync(d, pk.host.data(), pk.host.size(), cudaMemcpyHostToDevice, H->mem.s));
-  // the staging buffer must outlive the copy
-  CK(cudaStreamSynchronize(H->mem.s));
   char* b = (char*)d;
   LevelDev& L = S.dev;
   L.level = P.level;
   L.ncell = P.ncell();
   L.ngroup = P.ngroup();
   L.width = P.width;
-  L.code_base = 2 * (1 << (H->G.L - P.level)) + 1;
-  L.cell_code = (const int64_t*)(b + o_code);
+  L.code_base = P.code_base;
   L.max_nI = P.max_nI;
   L.max_nB = P.max_nB;
   L.max_n = P.max_n;
   L.max_group = P.max_group;
-  L.front_off = (const int64_t*)(b + o_foff);
+  L.max_w = P.max_w;
+  L.bucket = (const int32_t*)(b + o_bucket);
+  L.cell_code = (const int64_t*)(b + o_code);
+  L.cell_start = (const int32_t*)(b + o_cstart);
   L.nI = (const int*)(b + o_nI);
   L.nB = (const int*)(b + o_nB);
   L.gid_off = (const int64_t*)(b + o_goff);
-  L.gids = (const int64_t*)(b + o_gids);
   L.b_off = (const int64_t*)(b + o_boff);
+  L.front_off = (const int64_t*)(b + o_foff);
+  L.frame_off = (const int64_t*)(b + o_froff);
+  L.frame_ld = (const int*)(b + o_frld);
+  L.band_w = (const int*)(b + o_bw);
+  L.band_off = (const int64_t*)(b + o_boff2);
+  L.z_off = (const int64_t*)(b + o_zoff);
   L.seg_off = (const int*)(b + o_soff);
   L.seg_group = (const int*)(b + o_sg);
   L.seg_pos = (const int*)(b + o_sp);
   L.group_t = (const int*)(b + o_gt);
-  L.group_gid_off = (const int64_t*)(b + o_ggo);
-  L.group_gids = (const int64_t*)(b + o_ggid);
+  L.group_start = (const int32_t*)(b + o_gs);
+  L.group_size = (const int*)(b + o_gsz);
   L.group_cell_off = (const int*)(b + o_gco);
   L.group_cell = (const int*)(b + o_gc);
   L.group_pos = (const int*)(b + o_gp);
@@ -264,8 +291,17 @@ static int upload_level(rhif_handle* H, LevelStore& S, size_t elem) {
   L.ea_child = (const int*)(b + o_eac);
   L.ea_map_off = (const int64_t*)(b + o_eamo);
   L.ea_map = (const int*)(b + o_eam);
-  rc = H->mem.get(&L.front, P.front_total * elem);
-  if (rc) return rc;
+  if ((rc = H->mem.get((void**)&L.gids, P.gid_off.back() * sizeof(int32_t)))) return rc;
+  if (P.level == 0) {
+    if ((rc = H->mem.get(&L.frame_base, P.frame_total * elem))) return rc;
+    if ((rc = H->mem.get(&L.band, P.band_total * elem))) return rc;
+    if ((rc = H->mem.get((void**)&L.cpl_i, P.b_off.back() * sizeof(int)))) return rc;
+    if ((rc = H->mem.get(&L.cpl_a, P.b_off.back() * elem))) return rc;
+    L.front = nullptr;
+  } else {
+    if ((rc = H->mem.get(&L.front, P.front_total * elem))) return rc;
+    L.frame_base = L.front;
+  }
   S.phases.resize(P.phases.size());
   for (size_t i = 0; i < P.phases.size(); ++i) {
     const PhasePlan& ph = P.phases[i];
@@ -281,14 +317,8 @@ static int upload_level(rhif_handle* H, LevelStore& S, size_t elem) {
     D.max_n = U.max_n;
     D.u_group = (const int*)(b + po[i].ug);
     D.u_nrow = (const int*)(b + po[i].un);
-    D.u_row_off = (const int64_t*)(b + po[i].uro);
-    D.u_row_gid = (const int64_t*)(b + po[i].urg);
-    D.row_src_off = (const int64_t*)(b + po[i].rso);
-    D.src_cell = (const int*)(b + po[i].sc);
-    D.src_pos = (const int*)(b + po[i].sp);
-    D.src_upos = (const int*)(b + po[i].su);
     D.u_m_off = (const int64_t*)(b + po[i].umo);
-    D.u_rec_off = (const int64_t*)(b + po[i].uro2);
+    D.u_rec_off = (const int64_t*)(b + po[i].uro);
     D.u_perm_off = (const int64_t*)(b + po[i].upo);
     D.group_unit = (const int*)(b + po[i].gu);
     if ((rc = H->mem.get(&D.Lbuf, ph.pre_total * elem))) return rc;
@@ -297,6 +327,8 @@ static int upload_level(rhif_handle* H, LevelStore& S, size_t elem) {
     if ((rc = H->mem.get((void**)&D.rank, U.group.size() * sizeof(int)))) return rc;
     D.Mbuf = nullptr;
   }
+  // the staging buffer must outlive the copy
+  CK(cudaStreamSynchronize(H->mem.s));
   return RHIF_OK;
 }
 
@@ -346,32 +378,46 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
   H->mem.release(offb);
 
   std::vector<uint8_t> alive(G.N, 1);
+  std::vector<int32_t> active;
   H->levels.resize(G.L + 1);
   for (int lvl = 0; lvl <= G.L; ++lvl) {
     LevelStore& S = H->levels[lvl];
     const LevelPlan* prev = lvl ? &H->levels[lvl - 1].plan : nullptr;
-    S.plan = build_level(G, lvl, alive, prev, H->precondition, H->edge_skel);
+    S.plan = build_level(G, lvl, active, alive, prev, H->precondition, H->edge_skel);
     if ((rc = upload_level(H, S, elem))) return rc;
     const LevelPlan& P = S.plan;
     H->ub_len = std::max<int64_t>(H->ub_len, P.b_off.back());
-    double lvl_flops = 0.0, front_bytes = double(P.front_total) * elem;
-    for (int c = 0; c < P.ncell(); ++c) {
-      lvl_flops += cell_flops(P.nI[c], P.nB[c]);
-      const double nI = P.nI[c], nB = P.nB[c];
-      H->apply_bytes += 2.0 * elem * (nI * (nI + 1) / 2 + nI * nB);
-    }
-    H->flops += lvl_flops;
-    if (lvl == 0) {
-      Launch t(kCatFrontLeaf, s, 0.0, front_bytes);
-      launch_front_leaf<T>(H->gd, S.dev, H->diag, H->off, H->status, s);
-    } else {
-      Launch t(kCatExtendAdd, s, 0.0, front_bytes);
-      launch_extend_add<T>(S.dev, H->levels[lvl - 1].dev, s);
-    }
     {
-      Launch t(kCatPartialChol, s, lvl_flops, front_bytes);
+      Launch t(kCatExpandGids, s, 0.0, 8.0 * P.gid_off.back());
+      launch_expand_gids(S.dev, s);
+    }
+    double lvl_flops = 0.0;
+    if (lvl == 0) {
+      for (int c = 0; c < P.ncell(); ++c) {
+        const double nI = P.nI[c], nB = P.nB[c], w = P.band_w[c];
+        // banded Cholesky + L^{-1} A_IB (columns start at their coupled row) + Z^T Z
+        lvl_flops += nI * w * w + nB * nI * w + nI * nB * nB;
+        H->apply_bytes += 2.0 * elem * (nI * (w + 1) + nB);
+      }
+      void* Zb = nullptr;
+      if ((rc = H->mem.get(&Zb, P.z_total * elem))) return rc;
+      S.dev.zbuf = Zb;
+      Launch t(kCatLeafElim, s, lvl_flops, 0.0);
+      launch_leaf_elim<T>(H->gd, S.dev, H->diag, H->off, H->status, s);
+    } else {
+      for (int c = 0; c < P.ncell(); ++c) {
+        const double nI = P.nI[c], nB = P.nB[c];
+        lvl_flops += cell_flops(nI, nB);
+        H->apply_bytes += 2.0 * elem * (nI * (nI + 1) / 2 + nI * nB);
+      }
+      {
+        Launch t(kCatExtendAdd, s, 0.0, double(P.front_total) * elem);
+        launch_extend_add<T>(S.dev, H->levels[lvl - 1].dev, s);
+      }
+      Launch t(kCatPartialChol, s, lvl_flops, double(P.front_total) * elem);
       launch_partial_chol<T>(S.dev, H->status, s);
     }
+    H->flops += lvl_flops;
     for (size_t ip = 0; ip < P.phases.size(); ++ip) {
       const PhasePlan& ph = P.phases[ip];
       PhaseDev& D = S.phases[ip].dev;
@@ -380,14 +426,14 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
       D.Mbuf = M;
       double dflops = 0.0, sflops = 0.0;
       for (int gi : ph.pre_group) {
-        const double g = double(P.group_gid_off[gi + 1] - P.group_gid_off[gi]);
+        const double g = P.group_size[gi];
         dflops += g * g * g / 3.0;
       }
       for (int c = 0; c < P.ncell(); ++c)
         for (int q = P.seg_off[c]; q < P.seg_off[c + 1]; ++q) {
           const int gi = P.seg_group[q];
           if (ph.group_pre[gi] < 0) continue;
-          const double g = double(P.group_gid_off[gi + 1] - P.group_gid_off[gi]);
+          const double g = P.group_size[gi];
           sflops += 2.0 * g * g * P.nB[c];
         }
       if (!ph.pre_group.empty()) {
@@ -400,16 +446,16 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
           launch_precond_scale<T>(S.dev, D, s);
         }
       }
-      const int64_t skel_slot = (int64_t)ph.units.group.size();
+      const int64_t nunit = (int64_t)ph.units.group.size();
       {
-        Launch t(kCatSkel, s, 0.0, 0.0, skel_slot ? 1 : 0);
-        launch_skel<T>(S.dev, D, alive_d, H->tol, H->status, s);
+        Launch t(kCatSkel, s, 0.0, 0.0, nunit ? 1 : 0);
+        launch_skel<T>(S.dev, D, alive_d, H->tol, H->status, ph.units.max_m, s);
       }
       if ((rc = check_status(H, "skeletonization"))) return rc;
       H->mem.release(M);
       D.Mbuf = nullptr;
       PhaseStore& PS = S.phases[ip];
-      PS.h_rank.resize(ph.units.group.size());
+      PS.h_rank.resize(nunit);
       PS.h_perm.resize(ph.units.perm_total);
       CK(cudaMemcpyAsync(PS.h_rank.data(), D.rank, PS.h_rank.size() * sizeof(int),
                          cudaMemcpyDeviceToHost, s));
@@ -418,16 +464,15 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
       CK(cudaStreamSynchronize(s));
       H->flops += dflops + sflops;
       for (int gi : ph.pre_group) {
-        const double g = double(P.group_gid_off[gi + 1] - P.group_gid_off[gi]);
+        const double g = P.group_size[gi];
         H->apply_bytes += 2.0 * elem * g * (g + 1) / 2;
       }
-      for (size_t u = 0; u < ph.units.group.size(); ++u) {
+      for (int64_t u = 0; u < nunit; ++u) {
         const int gi = ph.units.group[u];
-        const int64_t g0 = P.group_gid_off[gi];
-        const int n = (int)(P.group_gid_off[gi + 1] - g0);
+        const int n = P.group_size[gi];
         const int k = PS.h_rank[u], r = n - k;
         const int* pm = PS.h_perm.data() + ph.units.perm_off[u];
-        for (int i = k; i < n; ++i) alive[P.group_gids[g0 + pm[i]]] = 0;
+        for (int i = k; i < n; ++i) alive[P.bucket[P.group_start[gi] + pm[i]]] = 0;
         const double m = ph.units.nrow[u];
         const double uf = 4.0 * m * n * k - 2.0 * k * k * (m + n) + 4.0 * k * k * k / 3.0 +
                           double(k) * k * r + cell_flops(r, k);
@@ -438,10 +483,30 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
       }
     }
     if ((rc = check_status(H, lvl == G.L ? "root factorization" : "cell elimination"))) return rc;
+    if (lvl == 0 && S.dev.zbuf) {
+      H->mem.release(S.dev.zbuf);
+      S.dev.zbuf = nullptr;
+    }
+    // DOFs still active at the next level: the separator DOFs that survived
+    for (int c = 0; c < P.ncell(); ++c)
+      for (int i = 0; i < P.nI[c]; ++i) alive[P.bucket[P.cell_start[c] + i]] = 0;
+    active.clear();
+    for (int gi = 0; gi < P.ngroup(); ++gi)
+      for (int o = 0; o < P.group_size[gi]; ++o) {
+        const int32_t g = P.bucket[P.group_start[gi] + o];
+        if (alive[g]) active.push_back(g);
+      }
+    std::sort(active.begin(), active.end());
     for (int c = 0; c < P.ncell(); ++c) {
       const double nI = P.nI[c], nB = P.nB[c];
-      S.cell_flops += nI * nI + 2.0 * nI * nB;
-      S.cell_bytes += elem * (nI * (nI + 1) / 2 + nI * nB) + 16.0 * (nI + nB);
+      if (lvl == 0) {
+        const double w = P.band_w[c];
+        S.cell_flops += 4.0 * nI * w + 2.0 * nB;
+        S.cell_bytes += elem * (nI * (w + 1) + nB) + 4.0 * nB + 16.0 * (nI + nB);
+      } else {
+        S.cell_flops += nI * nI + 2.0 * nI * nB;
+        S.cell_bytes += elem * (nI * (nI + 1) / 2 + nI * nB) + 16.0 * (nI + nB);
+      }
     }
     S.grp_flops.assign(P.phases.size(), 0.0);
     S.grp_bytes.assign(P.phases.size(), 0.0);
@@ -449,7 +514,7 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
       const PhasePlan& ph = P.phases[ip];
       for (int gi = 0; gi < P.ngroup(); ++gi) {
         if (P.group_t[gi] < ph.pre_min_type) continue;
-        const double g = double(P.group_gid_off[gi + 1] - P.group_gid_off[gi]);
+        const double g = P.group_size[gi];
         double f = 0, b = 16.0 * g;
         if (ph.group_pre[gi] >= 0) { f += g * g; b += elem * g * (g + 1) / 2; }
         const int u = ph.group_unit[gi];
@@ -462,8 +527,6 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
         S.grp_bytes[ip] += b;
       }
     }
-    for (int c = 0; c < P.ncell(); ++c)
-      for (int i = 0; i < P.nI[c]; ++i) alive[P.gids[P.gid_off[c] + i]] = 0;
   }
   H->mem.release(alive_d);
   return RHIF_OK;
@@ -760,11 +823,7 @@ int rhif_stats(const rhif_handle* F, rhif_stats_t* st) {
   st->root_size = F->levels.empty() ? 0 : F->levels.back().plan.nI.empty() ? 0 : F->levels.back().plan.nI[0];
   for (int l = 0; l < F->G.L && l < 16; ++l) {
     // active DOFs after level l = DOFs present at level l+1
-    const LevelPlan& P = F->levels[l + 1].plan;
-    int64_t a = 0;
-    for (int c = 0; c < P.ncell(); ++c) a += P.nI[c];
-    a += (int64_t)P.group_gids.size();
-    st->active[l] = a;
+    st->active[l] = (int64_t)F->levels[l + 1].plan.bucket.size();
   }
   st->factor_bytes = (int64_t)F->mem.bytes;
   st->flops = F->flops;
@@ -788,14 +847,14 @@ int rhif_skeletons(const rhif_handle* F, int level, int phase, int* count, int* 
   int64_t pos = 0;
   for (int u = 0; u < nu; ++u) {
     const int gi = ph.units.group[u];
-    const int64_t g0 = S.plan.group_gid_off[gi];
-    const int n = (int)(S.plan.group_gid_off[gi + 1] - g0);
+    const int64_t g0 = S.plan.group_start[gi];
+    const int n = S.plan.group_size[gi];
     if (sizes) sizes[u] = n;
     if (ranks) ranks[u] = PS.h_rank[u];
     if (gids) {
       if (pos + n > capacity) return fail(RHIF_ERR_BAD_ARG, "gids capacity too small");
       const int* pm = PS.h_perm.data() + ph.units.perm_off[u];
-      for (int i = 0; i < n; ++i) gids[pos + i] = S.plan.group_gids[g0 + pm[i]];
+      for (int i = 0; i < n; ++i) gids[pos + i] = S.plan.bucket[g0 + pm[i]];
     }
     pos += n;
   }
@@ -819,8 +878,8 @@ int rhif_reset_kernel_stats(void) {
   cudaDeviceSynchronize();
   std::lock_guard<std::mutex> lk(g_kmu);
   for (auto& p : g_pending) {
-    cudaEventDestroy(p.a);
-    cudaEventDestroy(p.b);
+    g_event_pool.push_back(p.a);
+    g_event_pool.push_back(p.b);
   }
   g_pending.clear();
   for (auto& k : g_kstat) k = KStat();
@@ -836,8 +895,8 @@ int rhif_kernel_stats(int index, rhif_kernel_stat* out) {
   for (auto& p : g_pending) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) g_kstat[p.cat].ms += ms;
-    cudaEventDestroy(p.a);
-    cudaEventDestroy(p.b);
+    g_event_pool.push_back(p.a);
+    g_event_pool.push_back(p.b);
   }
   g_pending.clear();
   std::memset(out, 0, sizeof(*out));

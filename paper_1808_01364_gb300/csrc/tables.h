@@ -4,6 +4,9 @@
 
 namespace rhif {
 
+constexpr int kMaxRowGroupsDev = 128;   // = kMaxRowGroups of plan.h
+constexpr int kMaxSlotsDev = 4;
+
 struct GeoDev {
   int d, leaf;
   int ns[3];
@@ -14,28 +17,44 @@ struct GeoDev {
 struct LevelDev {
   int level, ncell, ngroup;
   int width, code_base;      // cell width in grid intervals; base of the group code
+  int max_nI, max_nB, max_n, max_group, max_w;
+  const int32_t* bucket;     // active DOFs sorted by (code, index)
   const int64_t* cell_code;
-  int max_nI, max_nB, max_n, max_group;
-  const int64_t* front_off;
+  const int32_t* cell_start;
   const int* nI;
   const int* nB;
   const int64_t* gid_off;
-  const int64_t* gids;
+  int32_t* gids;             // front-order DOF lists, expanded on the device
   const int64_t* b_off;
+  const int64_t* front_off;  // level >= 1
+  void* front;
+  const int64_t* frame_off;
+  const int* frame_ld;
+  void* frame_base;          // level 0: frame buffer; level >= 1: == front
+  // level 0 banded factors
+  const int* band_w;
+  const int64_t* band_off;
+  void* band;                // nI x (w+1), column k holds L[k..k+w, k]
+  const int64_t* z_off;
+  void* zbuf;                // factorization scratch
+  int* cpl_i;                // per B position (b_off): coupled interior index or -1
+  void* cpl_a;               // per B position: A(b, I(b))
+  // segments
   const int* seg_off;
   const int* seg_group;
   const int* seg_pos;
+  // groups
   const int* group_t;
-  const int64_t* group_gid_off;
-  const int64_t* group_gids;
+  const int32_t* group_start;
+  const int* group_size;
   const int* group_cell_off;
   const int* group_cell;
   const int* group_pos;
+  // extend-add
   const int* ea_off;
   const int* ea_child;
   const int64_t* ea_map_off;
   const int* ea_map;
-  void* front;   // element type of the factor
 };
 
 struct PhaseDev {
@@ -48,12 +67,6 @@ struct PhaseDev {
   int nunit, max_n;
   const int* u_group;
   const int* u_nrow;
-  const int64_t* u_row_off;
-  const int64_t* u_row_gid;
-  const int64_t* row_src_off;
-  const int* src_cell;
-  const int* src_pos;
-  const int* src_upos;
   const int64_t* u_m_off;
   void* Mbuf;
   const int64_t* u_rec_off;

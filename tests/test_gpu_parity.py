@@ -178,3 +178,21 @@ def test_gradient_kernel_matches_oracle(gpu_lib):
         g = gpu_lib.rhif_grad_logcoef(ns, _dev(a), _dev(u), _dev(lam)).cpu().numpy()
         go = fd.dA_dlog_a(ns, a, u, lam)
         np.testing.assert_allclose(g, go, rtol=1e-12, atol=1e-12 * np.abs(go).max())
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_factor_is_deterministic(gpu_lib, precision):
+    """Two factorizations of the same input give the same skeletons and bitwise
+    equal F^{-1} x (no atomics; all IDs of a level read the same matrix)."""
+    ns = (255, 255)
+    a = W.log_uniform_pixels(ns, 1e-4, 1e4, seed=12)
+    csr = _gpu_matrix(gpu_lib, ns, a, 0.0)
+    x = _dev(W.normal_rhs(ns, 13))
+    outs = []
+    for _ in range(2):
+        F = gpu_lib.rhif_factor(csr, ns, 16, 1e-3, precision=precision)
+        sk = [F.skeletons(l) for l in range(F.stats()["levels"])]
+        outs.append((sk, F.apply(x).cpu().numpy()))
+        F.free()
+    assert outs[0][0] == outs[1][0]
+    np.testing.assert_array_equal(outs[0][1], outs[1][1])

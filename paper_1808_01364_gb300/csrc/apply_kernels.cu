@@ -10,31 +10,24 @@
 #include "common.cuh"
 #include "kernels.h"
 #include "tables.h"
+#include "../../include/rhif.h"
 
 namespace rhif {
 
 constexpr int kApplyThreads = 256;
 constexpr int kGroupThreads = 128;
-constexpr int kLeafWarps = 4;            // at most this many leaf cells per CTA (one warp each)
+constexpr int kLeafWarps = 4;                 // at most this many leaf cells per CTA (one warp each)
+constexpr int kGroupWarps = 4;                // small groups per CTA (one warp each)
 constexpr size_t kStageBudget = 160 * 1024;   // shared memory for staged factor blocks
 
-// Coalesced copy of a factor block into shared memory (whole CTA or one warp).
-template <typename T>
-__device__ inline void stage_copy(T* dst, const T* src, int64_t count, int tid, int nt) {
-  for (int64_t i = tid; i < count; i += nt) dst[i] = src[i];
-}
-
-template <typename T>
-static size_t leaf_warp_smem(const LevelDev& Lv) {
-  size_t band = (size_t)Lv.max_nI * (Lv.max_w + 1) * sizeof(T);
-  return ((band + 15) & ~size_t(15)) + 2 * (Lv.max_nI + 1) * sizeof(T) + 16;
-}
-
-template <typename T>
-static int leaf_warps_per_cta(const LevelDev& Lv) {
-  const size_t per = leaf_warp_smem<T>(Lv);
-  int w = (int)(kStageBudget / per);
-  return w < 1 ? 1 : (w > kLeafWarps ? kLeafWarps : w);
+// Timeout of a bulk copy: record it, give the copy a second bounded chance to
+// land (the shared memory must not be released while it is in flight), and
+// tell the caller to skip the work.
+__device__ inline bool staged_ok(uint64_t* bar, int* status, int level, int kind, int index) {
+  if (mbar_wait(bar, 0)) return true;
+  report(status, RHIF_ERR_TIMEOUT, level, kind, index);
+  mbar_wait(bar, 0);
+  return false;
 }
 
 // ---------------------------------------------------------------------------
@@ -71,36 +64,142 @@ __device__ inline void warp_band_bwd(const T* band, int n, int w, T* y) {
   }
 }
 
+// Blocked forms for w <= 31: blocks of w rows, lane r owns row s + r.  The
+// coupling of a block to the w rows before (after) it is one dot product per
+// lane; the triangle inside the block is solved in registers with shuffles.
+template <typename T>
+__device__ inline void warp_band_fwd_blk(const T* band, int n, int w, T* y) {
+  const int lane = threadIdx.x & 31;
+  const int w1 = w + 1;
+  for (int s0 = 0; s0 < n; s0 += w) {
+    const int B = min(w, n - s0);
+    const int i = s0 + lane;
+    T acc = T(0);
+    if (lane < B) {
+      acc = y[i];
+      for (int d = lane + 1; d <= w; ++d) {
+        const int j = i - d;
+        if (j < 0) break;
+        acc -= band[j * w1 + d] * y[j];
+      }
+    }
+    for (int c = 0; c < B; ++c) {
+      const T yc = __shfl_sync(0xffffffffu, acc, c) * band[(s0 + c) * w1];
+      if (lane == c) acc = yc;
+      else if (lane > c && lane < B) acc -= band[(s0 + c) * w1 + (lane - c)] * yc;
+    }
+    if (lane < B) y[i] = acc;
+    __syncwarp();
+  }
+}
+
+template <typename T>
+__device__ inline void warp_band_bwd_blk(const T* band, int n, int w, T* y) {
+  const int lane = threadIdx.x & 31;
+  const int w1 = w + 1;
+  const int nblk = (n + w - 1) / w;
+  for (int bi = nblk - 1; bi >= 0; --bi) {
+    const int s0 = bi * w;
+    const int B = min(w, n - s0);
+    const int i = s0 + lane;
+    T acc = T(0);
+    if (lane < B) {
+      acc = y[i];
+      for (int d = B - lane; d <= w; ++d) {
+        const int j = i + d;
+        if (j >= n) break;
+        acc -= band[i * w1 + d] * y[j];
+      }
+    }
+    for (int c = B - 1; c >= 0; --c) {
+      const T yc = __shfl_sync(0xffffffffu, acc, c) * band[(s0 + c) * w1];
+      if (lane == c) acc = yc;
+      else if (lane < c) acc -= band[(s0 + lane) * w1 + (c - lane)] * yc;
+    }
+    if (lane < B) y[i] = acc;
+    __syncwarp();
+  }
+}
+
+template <typename T>
+__device__ inline void band_fwd(const T* band, int n, int w, T* y) {
+  if (w >= 1 && w <= 31) warp_band_fwd_blk(band, n, w, y);
+  else warp_band_fwd(band, n, w, y);
+}
+
+template <typename T>
+__device__ inline void band_bwd(const T* band, int n, int w, T* y) {
+  if (w >= 1 && w <= 31) warp_band_bwd_blk(band, n, w, y);
+  else warp_band_bwd(band, n, w, y);
+}
+
+// per-warp shared memory of the leaf kernels: [mbarrier | band | y | z]
+template <typename T>
+__host__ __device__ inline size_t leaf_band_bytes(int max_nI, int max_w) {
+  return round16((size_t)max_nI * (max_w + 1) * sizeof(T));
+}
+
+template <typename T>
+static size_t leaf_warp_smem(const LevelDev& Lv) {
+  return 16 + leaf_band_bytes<T>(Lv.max_nI, Lv.max_w) +
+         round16((2 * (Lv.max_nI + 1) + Lv.max_nB) * sizeof(T));
+}
+
+template <typename T>
+static int leaf_warps_per_cta(const LevelDev& Lv) {
+  const size_t per = leaf_warp_smem<T>(Lv);
+  int w = (int)(kStageBudget / per);
+  return w < 1 ? 1 : (w > kLeafWarps ? kLeafWarps : w);
+}
+
+// Starts the bulk copy of this warp's leaf band; returns the band in shared memory.
+template <typename T>
+__device__ inline T* leaf_stage(const LevelDev& Lv, int c, unsigned char* base, uint64_t** bar_out) {
+  const int lane = threadIdx.x & 31;
+  uint64_t* bar = (uint64_t*)base;
+  T* sb = (T*)(base + 16);
+  if (lane == 0) {
+    const uint32_t bytes = round16((size_t)Lv.nI[c] * (Lv.band_w[c] + 1) * sizeof(T));
+    mbar_init(bar, 1);
+    mbar_expect_tx(bar, bytes);
+    if (bytes) bulk_g2s(sb, (const T*)Lv.band + Lv.band_off[c], bytes, bar);
+  }
+  __syncwarp();
+  *bar_out = bar;
+  return sb;
+}
+
 // E_0^T per leaf: y = L^{-1} x_I ; x_B -= A_BI L^{-T} y (sent to the owning groups) ; x_I = y
 template <typename T>
 __global__ void __launch_bounds__(32 * kLeafWarps)
 k_apply_leaf_up(LevelDev Lv, double* x, int64_t ldx, int nrhs, double* ubuf, int64_t ldu,
                 int per_warp_bytes) {
-  extern __shared__ unsigned char smraw[];
+  extern __shared__ __align__(16) unsigned char smraw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c = blockIdx.x * (blockDim.x >> 5) + warp;
   if (c >= Lv.ncell) return;
-  T* sb = (T*)(smraw + (size_t)warp * per_warp_bytes);
-  const size_t band_elems = (((size_t)Lv.max_nI * (Lv.max_w + 1) * sizeof(T) + 15) & ~size_t(15)) / sizeof(T);
-  T* y = sb + band_elems;
+  unsigned char* base = smraw + (size_t)warp * per_warp_bytes;
+  uint64_t* bar;
+  const T* band = leaf_stage<T>(Lv, c, base, &bar);
+  T* y = (T*)(base + 16 + leaf_band_bytes<T>(Lv.max_nI, Lv.max_w));
   T* z = y + Lv.max_nI + 1;
   const int nI = Lv.nI[c], nB = Lv.nB[c], w = Lv.band_w[c];
-  stage_copy(sb, (const T*)Lv.band + Lv.band_off[c], (int64_t)nI * (w + 1), lane, 32);
-  const T* band = sb;
   const int32_t* gI = Lv.gids + Lv.gid_off[c];
   const int* ci = Lv.cpl_i + Lv.b_off[c];
   const T* ca = (const T*)Lv.cpl_a + Lv.b_off[c];
   for (int r = 0; r < nrhs; ++r) {
     double* xr = x + r * ldx;
+#pragma unroll 4
     for (int i = lane; i < nI; i += 32) y[i] = T(xr[gI[i]]);
+    if (r == 0 && !staged_ok(bar, Lv.status, 0, kKindCell, c)) return;
     __syncwarp();
-    warp_band_fwd(band, nI, w, y);
+    band_fwd(band, nI, w, y);
     for (int i = lane; i < nI; i += 32) {
       xr[gI[i]] = double(y[i]);
       z[i] = y[i];
     }
     __syncwarp();
-    warp_band_bwd(band, nI, w, z);
+    band_bwd(band, nI, w, z);
     double* u = ubuf + r * ldu + Lv.b_off[c];
     for (int b = lane; b < nB; b += 32) u[b] = ci[b] >= 0 ? double(ca[b] * z[ci[b]]) : 0.0;
     __syncwarp();
@@ -111,33 +210,38 @@ k_apply_leaf_up(LevelDev Lv, double* x, int64_t ldx, int nrhs, double* ubuf, int
 template <typename T>
 __global__ void __launch_bounds__(32 * kLeafWarps)
 k_apply_leaf_down(LevelDev Lv, double* x, int64_t ldx, int nrhs, int per_warp_bytes) {
-  extern __shared__ unsigned char smraw[];
+  extern __shared__ __align__(16) unsigned char smraw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c = blockIdx.x * (blockDim.x >> 5) + warp;
   if (c >= Lv.ncell) return;
-  T* sb = (T*)(smraw + (size_t)warp * per_warp_bytes);
-  const size_t band_elems = (((size_t)Lv.max_nI * (Lv.max_w + 1) * sizeof(T) + 15) & ~size_t(15)) / sizeof(T);
-  T* t = sb + band_elems;
+  unsigned char* base = smraw + (size_t)warp * per_warp_bytes;
+  uint64_t* bar;
+  const T* band = leaf_stage<T>(Lv, c, base, &bar);
+  T* t = (T*)(base + 16 + leaf_band_bytes<T>(Lv.max_nI, Lv.max_w));
   T* v = t + Lv.max_nI + 1;
   const int nI = Lv.nI[c], nB = Lv.nB[c], w = Lv.band_w[c];
-  stage_copy(sb, (const T*)Lv.band + Lv.band_off[c], (int64_t)nI * (w + 1), lane, 32);
-  const T* band = sb;
   const int32_t* gI = Lv.gids + Lv.gid_off[c];
   const int32_t* gB = gI + nI;
   const int* ci = Lv.cpl_i + Lv.b_off[c];
   const T* ca = (const T*)Lv.cpl_a + Lv.b_off[c];
+  T* xb = v + Lv.max_nI + 1;   // boundary values
   for (int r = 0; r < nrhs; ++r) {
     double* xr = x + r * ldx;
     for (int i = lane; i < nI; i += 32) v[i] = T(0);
+#pragma unroll 4
+    for (int i = lane; i < nI; i += 32) t[i] = T(xr[gI[i]]);
+#pragma unroll 2
+    for (int b = lane; b < nB; b += 32) xb[b] = ci[b] >= 0 ? ca[b] * T(xr[gB[b]]) : T(0);
     __syncwarp();
     if (lane == 0)   // A_BI^T x_B in a fixed order (several boundary DOFs may face one interior DOF)
       for (int b = 0; b < nB; ++b)
-        if (ci[b] >= 0) v[ci[b]] += ca[b] * T(xr[gB[b]]);
+        if (ci[b] >= 0) v[ci[b]] += xb[b];
+    if (r == 0 && !staged_ok(bar, Lv.status, 0, kKindCell, c)) return;
     __syncwarp();
-    warp_band_fwd(band, nI, w, v);
-    for (int i = lane; i < nI; i += 32) t[i] = T(xr[gI[i]]) - v[i];
+    band_fwd(band, nI, w, v);
+    for (int i = lane; i < nI; i += 32) t[i] -= v[i];
     __syncwarp();
-    warp_band_bwd(band, nI, w, t);
+    band_bwd(band, nI, w, t);
     for (int i = lane; i < nI; i += 32) xr[gI[i]] = double(t[i]);
     __syncwarp();
   }
@@ -147,24 +251,35 @@ k_apply_leaf_down(LevelDev Lv, double* x, int64_t ldx, int nrhs, int per_warp_by
 // dense fronts (levels >= 1 and the root)
 // ---------------------------------------------------------------------------
 
+// Starts the bulk copy of the first nI columns of the front (n x nI, contiguous).
+template <typename T>
+__device__ inline const T* front_stage(const T* F, int n, int nI, T* dst, uint64_t* bar) {
+  if (threadIdx.x == 0) {
+    const uint32_t bytes = round16((size_t)n * nI * sizeof(T));
+    mbar_init(bar, 1);
+    mbar_expect_tx(bar, bytes);
+    if (bytes) bulk_g2s(dst, F, bytes, bar);
+  }
+  return dst;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kApplyThreads)
 k_apply_cell_up(LevelDev Lv, double* x, int64_t ldx, int nrhs, double* ubuf, int64_t ldu,
                 int stage) {
-  extern __shared__ unsigned char smraw[];
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ __align__(8) uint64_t bar;
   T* y = (T*)smraw;
   const int c = blockIdx.x;
   const int nI = Lv.nI[c], nB = Lv.nB[c], n = nI + nB;
   const T* F = (const T*)Lv.front + Lv.front_off[c];
-  if (stage) {
-    T* sf = y + ((Lv.max_nI + 1 + 1) & ~1);
-    stage_copy(sf, F, (int64_t)n * nI, threadIdx.x, blockDim.x);
-    F = sf;
-  }
+  if (stage) F = front_stage(F, n, nI, (T*)(smraw + round16((Lv.max_nI + 1) * sizeof(T))), &bar);
   const int32_t* gI = Lv.gids + Lv.gid_off[c];
+  __syncthreads();
   for (int r = 0; r < nrhs; ++r) {
     double* xr = x + r * ldx;
     for (int i = threadIdx.x; i < nI; i += blockDim.x) y[i] = T(xr[gI[i]]);
+    if (stage && r == 0 && !staged_ok(&bar, Lv.status, Lv.level, kKindCell, c)) return;
     __syncthreads();
     cta_trsv_lower(F, n, nI, y);
     for (int i = threadIdx.x; i < nI; i += blockDim.x) xr[gI[i]] = double(y[i]);
@@ -181,23 +296,23 @@ k_apply_cell_up(LevelDev Lv, double* x, int64_t ldx, int nrhs, double* ubuf, int
 template <typename T>
 __global__ void __launch_bounds__(kApplyThreads)
 k_apply_cell_down(LevelDev Lv, double* x, int64_t ldx, int nrhs, int stage) {
-  extern __shared__ unsigned char smraw[];
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ __align__(8) uint64_t bar;
   T* t = (T*)smraw;
   T* xb = t + Lv.max_nI;
   const int c = blockIdx.x;
   const int nI = Lv.nI[c], nB = Lv.nB[c], n = nI + nB;
   const T* F = (const T*)Lv.front + Lv.front_off[c];
-  if (stage) {
-    T* sf = t + ((Lv.max_nI + Lv.max_nB + 1 + 1) & ~1);
-    stage_copy(sf, F, (int64_t)n * nI, threadIdx.x, blockDim.x);
-    F = sf;
-  }
+  if (stage)
+    F = front_stage(F, n, nI, (T*)(smraw + round16((Lv.max_nI + Lv.max_nB + 1) * sizeof(T))), &bar);
   const int32_t* gI = Lv.gids + Lv.gid_off[c];
   const int32_t* gB = gI + nI;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  __syncthreads();
   for (int r = 0; r < nrhs; ++r) {
     double* xr = x + r * ldx;
     for (int b = threadIdx.x; b < nB; b += blockDim.x) xb[b] = T(xr[gB[b]]);
+    if (stage && r == 0 && !staged_ok(&bar, Lv.status, Lv.level, kKindCell, c)) return;
     __syncthreads();
     for (int k = warp; k < nI; k += nwarps) {
       T s = T(0);
@@ -213,8 +328,47 @@ k_apply_cell_down(LevelDev Lv, double* x, int64_t ldx, int nrhs, int stage) {
 }
 
 // ---------------------------------------------------------------------------
-// separator groups: C_l and K_l (one CTA per group)
+// separator groups: C_l and K_l
 // ---------------------------------------------------------------------------
+
+// Layout of a group's staged blocks: [L_g | unit front | T], each padded to 16 bytes.
+template <typename T>
+__host__ __device__ inline size_t group_block_bytes(int n) {
+  const size_t nn = (size_t)n * n;
+  return 2 * round16(nn * sizeof(T)) + round16(nn / 4 * sizeof(T) + 16);
+}
+
+// Starts the bulk copies of the group's blocks (issued by `leader`).
+template <typename T>
+__device__ inline void group_stage(const PhaseDev& Ph, int pi, int u, int n, unsigned char* dst,
+                                   uint64_t* bar, bool leader, const T** Lg, const T** Fu,
+                                   const T** Tm) {
+  const size_t nn = (size_t)n * n;
+  T* sL = (T*)dst;
+  T* sF = (T*)(dst + round16(nn * sizeof(T)));
+  T* sT = (T*)(dst + 2 * round16(nn * sizeof(T)));
+  *Lg = pi >= 0 ? sL : nullptr;
+  *Fu = u >= 0 ? sF : nullptr;
+  *Tm = u >= 0 ? sT : nullptr;
+  if (!leader) return;
+  uint32_t total = 0;
+  const uint32_t bL = round16(nn * sizeof(T));
+  uint32_t bT = 0;
+  if (pi >= 0) total += bL;
+  if (u >= 0) {
+    const int k = Ph.rank[u];
+    bT = round16((size_t)k * (n - k) * sizeof(T));
+    total += bL + bT;
+  }
+  mbar_init(bar, 1);
+  mbar_expect_tx(bar, total);
+  if (pi >= 0) bulk_g2s(sL, (const T*)Ph.Lbuf + Ph.pre_off[pi], bL, bar);
+  if (u >= 0) {
+    const T* src = (const T*)Ph.rec + Ph.u_rec_off[u];
+    bulk_g2s(sF, src, bL, bar);
+    if (bT) bulk_g2s(sT, src + pad4e((int64_t)nn), bT, bar);
+  }
+}
 
 template <typename T>
 __device__ void unit_up(const PhaseDev& Ph, int u, int n, T* xg, T* tmp, const T* Fu, const T* Tm) {
@@ -264,34 +418,21 @@ __device__ void unit_down(const PhaseDev& Ph, int u, int n, T* xg, T* tmp, const
   __syncthreads();
 }
 
-// Points Lg / Fu / Tm at the group's factor blocks, copied to shared memory
-// when `stage` is set (the caller syncs before use).
+// Points Lg / Fu / Tm at the group's blocks in global memory.
 template <typename T>
-__device__ inline void group_blocks(const PhaseDev& Ph, int pi, int u, int n, int stage, T* sm,
-                                    const T** Lg, const T** Fu, const T** Tm) {
+__device__ inline void group_global(const PhaseDev& Ph, int pi, int u, int n, const T** Lg,
+                                    const T** Fu, const T** Tm) {
   *Lg = pi >= 0 ? (const T*)Ph.Lbuf + Ph.pre_off[pi] : nullptr;
   *Fu = u >= 0 ? (const T*)Ph.rec + Ph.u_rec_off[u] : nullptr;
-  *Tm = u >= 0 ? *Fu + (int64_t)n * n : nullptr;
-  if (!stage) return;
-  const int64_t nn = (int64_t)n * n;
-  if (pi >= 0) {
-    stage_copy(sm, *Lg, nn, threadIdx.x, blockDim.x);
-    *Lg = sm;
-  }
-  if (u >= 0) {
-    const int k = Ph.rank[u];
-    stage_copy(sm + nn, *Fu, nn, threadIdx.x, blockDim.x);
-    stage_copy(sm + 2 * nn, *Tm, (int64_t)k * (n - k), threadIdx.x, blockDim.x);
-    *Fu = sm + nn;
-    *Tm = sm + 2 * nn;
-  }
+  *Tm = u >= 0 ? *Fu + pad4e((int64_t)n * n) : nullptr;
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kGroupThreads)
 k_apply_group_up(LevelDev Lv, PhaseDev Ph, int gather, double* x, int64_t ldx, int nrhs,
                  const double* ubuf, int64_t ldu, int stage) {
-  extern __shared__ unsigned char smraw[];
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ __align__(8) uint64_t bar;
   T* xg = (T*)smraw;
   T* tmp = xg + Lv.max_group;
   const int g = blockIdx.x;
@@ -300,7 +441,12 @@ k_apply_group_up(LevelDev Lv, PhaseDev Ph, int gather, double* x, int64_t ldx, i
   const int32_t* gid = Lv.bucket + Lv.group_start[g];
   const int pi = Ph.group_pre[g], u = Ph.group_unit[g];
   const T *Lg, *Fu, *Tm;
-  group_blocks(Ph, pi, u, n, stage, tmp + ((Lv.max_group + 2) & ~1), &Lg, &Fu, &Tm);
+  if (stage)
+    group_stage(Ph, pi, u, n, smraw + round16(2 * (Lv.max_group + 1) * sizeof(T)), &bar,
+                threadIdx.x == 0, &Lg, &Fu, &Tm);
+  else
+    group_global(Ph, pi, u, n, &Lg, &Fu, &Tm);
+  __syncthreads();
   for (int r = 0; r < nrhs; ++r) {
     double* xr = x + r * ldx;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -311,9 +457,10 @@ k_apply_group_up(LevelDev Lv, PhaseDev Ph, int gather, double* x, int64_t ldx, i
       }
       xg[i] = T(v);
     }
+    if (stage && r == 0 && !staged_ok(&bar, Lv.status, Lv.level, kKindGroup, g)) return;
     __syncthreads();
-    if (pi >= 0) cta_trsv_lower(Lg, n, n, xg);
-    if (u >= 0) unit_up(Ph, u, n, xg, tmp, Fu, Tm);
+    if (Lg) cta_trsv_lower(Lg, n, n, xg);
+    if (Fu) unit_up(Ph, u, n, xg, tmp, Fu, Tm);
     for (int i = threadIdx.x; i < n; i += blockDim.x) xr[gid[i]] = double(xg[i]);
     __syncthreads();
   }
@@ -322,7 +469,8 @@ k_apply_group_up(LevelDev Lv, PhaseDev Ph, int gather, double* x, int64_t ldx, i
 template <typename T>
 __global__ void __launch_bounds__(kGroupThreads)
 k_apply_group_down(LevelDev Lv, PhaseDev Ph, double* x, int64_t ldx, int nrhs, int stage) {
-  extern __shared__ unsigned char smraw[];
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ __align__(8) uint64_t bar;
   T* xg = (T*)smraw;
   T* tmp = xg + Lv.max_group;
   const int g = blockIdx.x;
@@ -331,15 +479,157 @@ k_apply_group_down(LevelDev Lv, PhaseDev Ph, double* x, int64_t ldx, int nrhs, i
   const int32_t* gid = Lv.bucket + Lv.group_start[g];
   const int pi = Ph.group_pre[g], u = Ph.group_unit[g];
   const T *Lg, *Fu, *Tm;
-  group_blocks(Ph, pi, u, n, stage, tmp + ((Lv.max_group + 2) & ~1), &Lg, &Fu, &Tm);
+  if (stage)
+    group_stage(Ph, pi, u, n, smraw + round16(2 * (Lv.max_group + 1) * sizeof(T)), &bar,
+                threadIdx.x == 0, &Lg, &Fu, &Tm);
+  else
+    group_global(Ph, pi, u, n, &Lg, &Fu, &Tm);
+  __syncthreads();
   for (int r = 0; r < nrhs; ++r) {
     double* xr = x + r * ldx;
     for (int i = threadIdx.x; i < n; i += blockDim.x) xg[i] = T(xr[gid[i]]);
+    if (stage && r == 0 && !staged_ok(&bar, Lv.status, Lv.level, kKindGroup, g)) return;
     __syncthreads();
-    if (u >= 0) unit_down(Ph, u, n, xg, tmp, Fu, Tm);
-    if (pi >= 0) cta_trsv_lower_t(Lg, n, n, xg);
+    if (Fu) unit_down(Ph, u, n, xg, tmp, Fu, Tm);
+    if (Lg) cta_trsv_lower_t(Lg, n, n, xg);
     for (int i = threadIdx.x; i < n; i += blockDim.x) xr[gid[i]] = double(xg[i]);
     __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// separator groups of at most 32 DOFs: one warp per group, values in registers
+// ---------------------------------------------------------------------------
+
+template <typename T>
+static size_t group_warp_smem(int max_group) {
+  return 16 + group_block_bytes<T>(max_group) + round16(max_group * sizeof(int));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(32 * kGroupWarps)
+k_apply_group_up_warp(LevelDev Lv, PhaseDev Ph, int gather, double* x, int64_t ldx, int nrhs,
+                      const double* ubuf, int64_t ldu, int per_warp_bytes) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = blockIdx.x * kGroupWarps + warp;
+  if (g >= Lv.ngroup || Lv.group_t[g] < Ph.pre_min_type) return;
+  const int n = Lv.group_size[g];
+  const int32_t* gid = Lv.bucket + Lv.group_start[g];
+  const int pi = Ph.group_pre[g], u = Ph.group_unit[g];
+  unsigned char* base = smraw + (size_t)warp * per_warp_bytes;
+  uint64_t* bar = (uint64_t*)base;
+  int* invp = (int*)(base + 16 + group_block_bytes<T>(Lv.max_group));
+  const T *Lg, *Fu, *Tm;
+  group_stage(Ph, pi, u, n, base + 16, bar, lane == 0, &Lg, &Fu, &Tm);
+  const bool staged = pi >= 0 || u >= 0;
+  const int k = u >= 0 ? Ph.rank[u] : 0;
+  const int r = n - k;
+  const int* perm = u >= 0 ? Ph.perm + Ph.u_perm_off[u] : nullptr;
+  if (u >= 0 && lane < n) invp[perm[lane]] = lane;
+  __syncwarp();
+  const int p_sk = (u >= 0 && lane < k) ? perm[lane] : 0;
+  const int p_rd = (u >= 0 && lane < r) ? perm[k + lane] : 0;
+  const int my_idx = (u >= 0 && lane < n) ? invp[lane] : 0;
+  for (int rr = 0; rr < nrhs; ++rr) {
+    double* xr = x + rr * ldx;
+    T xv = T(0);
+    if (lane < n) {
+      double v = xr[gid[lane]];
+      if (gather)
+        for (int q = Lv.group_cell_off[g]; q < Lv.group_cell_off[g + 1]; ++q)
+          v -= ubuf[rr * ldu + Lv.b_off[Lv.group_cell[q]] + Lv.group_pos[q] + lane];
+      xv = T(v);
+    }
+    if (staged && rr == 0 && !staged_ok(bar, Lv.status, Lv.level, kKindGroup, g)) return;
+    if (Lg) {   // C^T: x_g = L_g^{-1} x_g
+      for (int c = 0; c < n; ++c) {
+        const T yc = __shfl_sync(0xffffffffu, xv, c) / Lg[c + c * n];
+        if (lane == c) xv = yc;
+        else if (lane > c && lane < n) xv -= Lg[lane + c * n] * yc;
+      }
+    }
+    if (u >= 0) {   // K^T: x_rd -= T^T x_sk ; y = L^{-1} x_rd ; x_sk -= W y ; x_rd = y
+      T xs = __shfl_sync(0xffffffffu, xv, p_sk);
+      T xd = __shfl_sync(0xffffffffu, xv, p_rd);
+      for (int q = 0; q < k; ++q) {
+        const T v = __shfl_sync(0xffffffffu, xs, q);
+        if (lane < r) xd -= Tm[q + lane * k] * v;
+      }
+      for (int c = 0; c < r; ++c) {
+        const T yc = __shfl_sync(0xffffffffu, xd, c) / Fu[c + c * n];
+        if (lane == c) xd = yc;
+        else if (lane > c && lane < r) xd -= Fu[lane + c * n] * yc;
+      }
+      for (int a = 0; a < r; ++a) {
+        const T v = __shfl_sync(0xffffffffu, xd, a);
+        if (lane < k) xs -= Fu[(r + lane) + a * n] * v;
+      }
+      const T from_sk = __shfl_sync(0xffffffffu, xs, my_idx < k ? my_idx : 0);
+      const T from_rd = __shfl_sync(0xffffffffu, xd, my_idx >= k ? my_idx - k : 0);
+      xv = my_idx < k ? from_sk : from_rd;
+    }
+    if (lane < n) xr[gid[lane]] = double(xv);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(32 * kGroupWarps)
+k_apply_group_down_warp(LevelDev Lv, PhaseDev Ph, double* x, int64_t ldx, int nrhs,
+                        int per_warp_bytes) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = blockIdx.x * kGroupWarps + warp;
+  if (g >= Lv.ngroup || Lv.group_t[g] < Ph.pre_min_type) return;
+  const int n = Lv.group_size[g];
+  const int32_t* gid = Lv.bucket + Lv.group_start[g];
+  const int pi = Ph.group_pre[g], u = Ph.group_unit[g];
+  unsigned char* base = smraw + (size_t)warp * per_warp_bytes;
+  uint64_t* bar = (uint64_t*)base;
+  int* invp = (int*)(base + 16 + group_block_bytes<T>(Lv.max_group));
+  const T *Lg, *Fu, *Tm;
+  group_stage(Ph, pi, u, n, base + 16, bar, lane == 0, &Lg, &Fu, &Tm);
+  const bool staged = pi >= 0 || u >= 0;
+  const int k = u >= 0 ? Ph.rank[u] : 0;
+  const int r = n - k;
+  const int* perm = u >= 0 ? Ph.perm + Ph.u_perm_off[u] : nullptr;
+  if (u >= 0 && lane < n) invp[perm[lane]] = lane;
+  __syncwarp();
+  const int p_sk = (u >= 0 && lane < k) ? perm[lane] : 0;
+  const int p_rd = (u >= 0 && lane < r) ? perm[k + lane] : 0;
+  const int my_idx = (u >= 0 && lane < n) ? invp[lane] : 0;
+  for (int rr = 0; rr < nrhs; ++rr) {
+    double* xr = x + rr * ldx;
+    T xv = lane < n ? T(xr[gid[lane]]) : T(0);
+    if (staged && rr == 0 && !staged_ok(bar, Lv.status, Lv.level, kKindGroup, g)) return;
+    if (u >= 0) {   // K: x_rd = L^{-T}(x_rd - W^T x_sk) ; x_sk -= T x_rd
+      T xs = __shfl_sync(0xffffffffu, xv, p_sk);
+      T xd = __shfl_sync(0xffffffffu, xv, p_rd);
+      for (int q = 0; q < k; ++q) {
+        const T v = __shfl_sync(0xffffffffu, xs, q);
+        if (lane < r) xd -= Fu[(r + q) + lane * n] * v;
+      }
+      for (int c = r - 1; c >= 0; --c) {
+        const T yc = __shfl_sync(0xffffffffu, xd, c) / Fu[c + c * n];
+        if (lane == c) xd = yc;
+        else if (lane < c) xd -= Fu[c + lane * n] * yc;
+      }
+      for (int a = 0; a < r; ++a) {
+        const T v = __shfl_sync(0xffffffffu, xd, a);
+        if (lane < k) xs -= Tm[lane + a * k] * v;
+      }
+      const T from_sk = __shfl_sync(0xffffffffu, xs, my_idx < k ? my_idx : 0);
+      const T from_rd = __shfl_sync(0xffffffffu, xd, my_idx >= k ? my_idx - k : 0);
+      xv = my_idx < k ? from_sk : from_rd;
+    }
+    if (Lg) {   // C: x_g = L_g^{-T} x_g
+      for (int c = n - 1; c >= 0; --c) {
+        const T yc = __shfl_sync(0xffffffffu, xv, c) / Lg[c + c * n];
+        if (lane == c) xv = yc;
+        else if (lane < c) xv -= Lg[c + lane * n] * yc;
+      }
+    }
+    if (lane < n) xr[gid[lane]] = double(xv);
   }
 }
 
@@ -354,8 +644,8 @@ void launch_apply_cell_up(const LevelDev& Lv, double* x, int64_t ldx, int nrhs, 
     k_apply_leaf_up<T><<<grid, 32 * wpc, wpc * per, s>>>(Lv, x, ldx, nrhs, ubuf, ldu, (int)per);
     return;
   }
-  const size_t base = ((Lv.max_nI + 2) & ~1) * sizeof(T);
-  const size_t blk = (size_t)Lv.max_n * Lv.max_nI * sizeof(T);
+  const size_t base = round16((Lv.max_nI + 1) * sizeof(T));
+  const size_t blk = round16((size_t)Lv.max_n * Lv.max_nI * sizeof(T));
   const int stage = blk <= kStageBudget;
   k_apply_cell_up<T><<<Lv.ncell, kApplyThreads, base + (stage ? blk : 0), s>>>(Lv, x, ldx, nrhs, ubuf,
                                                                             ldu, stage);
@@ -371,8 +661,8 @@ void launch_apply_cell_down(const LevelDev& Lv, double* x, int64_t ldx, int nrhs
     k_apply_leaf_down<T><<<grid, 32 * wpc, wpc * per, s>>>(Lv, x, ldx, nrhs, (int)per);
     return;
   }
-  const size_t base = ((Lv.max_nI + Lv.max_nB + 2) & ~1) * sizeof(T);
-  const size_t blk = (size_t)Lv.max_n * Lv.max_nI * sizeof(T);
+  const size_t base = round16((Lv.max_nI + Lv.max_nB + 1) * sizeof(T));
+  const size_t blk = round16((size_t)Lv.max_n * Lv.max_nI * sizeof(T));
   const int stage = blk <= kStageBudget;
   k_apply_cell_down<T><<<Lv.ncell, kApplyThreads, base + (stage ? blk : 0), s>>>(Lv, x, ldx, nrhs,
                                                                               stage);
@@ -382,8 +672,15 @@ template <typename T>
 void launch_apply_group_up(const LevelDev& Lv, const PhaseDev& Ph, int gather, double* x,
                            int64_t ldx, int nrhs, const double* ubuf, int64_t ldu, cudaStream_t s) {
   if (!Lv.ngroup) return;
-  const size_t base = (((Lv.max_group + 2) & ~1) * 2) * sizeof(T);
-  const size_t blk = 3 * (size_t)Lv.max_group * Lv.max_group * sizeof(T);
+  if (Lv.max_group <= 32) {
+    const size_t per = group_warp_smem<T>(Lv.max_group);
+    const unsigned grid = (Lv.ngroup + kGroupWarps - 1) / kGroupWarps;
+    k_apply_group_up_warp<T><<<grid, 32 * kGroupWarps, kGroupWarps * per, s>>>(
+        Lv, Ph, gather, x, ldx, nrhs, ubuf, ldu, (int)per);
+    return;
+  }
+  const size_t base = round16(2 * (Lv.max_group + 1) * sizeof(T));
+  const size_t blk = group_block_bytes<T>(Lv.max_group);
   const int stage = blk <= kStageBudget;
   k_apply_group_up<T><<<Lv.ngroup, kGroupThreads, base + (stage ? blk : 0), s>>>(
       Lv, Ph, gather, x, ldx, nrhs, ubuf, ldu, stage);
@@ -393,8 +690,15 @@ template <typename T>
 void launch_apply_group_down(const LevelDev& Lv, const PhaseDev& Ph, double* x, int64_t ldx,
                              int nrhs, cudaStream_t s) {
   if (!Lv.ngroup) return;
-  const size_t base = (((Lv.max_group + 2) & ~1) * 2) * sizeof(T);
-  const size_t blk = 3 * (size_t)Lv.max_group * Lv.max_group * sizeof(T);
+  if (Lv.max_group <= 32) {
+    const size_t per = group_warp_smem<T>(Lv.max_group);
+    const unsigned grid = (Lv.ngroup + kGroupWarps - 1) / kGroupWarps;
+    k_apply_group_down_warp<T><<<grid, 32 * kGroupWarps, kGroupWarps * per, s>>>(
+        Lv, Ph, x, ldx, nrhs, (int)per);
+    return;
+  }
+  const size_t base = round16(2 * (Lv.max_group + 1) * sizeof(T));
+  const size_t blk = group_block_bytes<T>(Lv.max_group);
   const int stage = blk <= kStageBudget;
   k_apply_group_down<T><<<Lv.ngroup, kGroupThreads, base + (stage ? blk : 0), s>>>(
       Lv, Ph, x, ldx, nrhs, stage);
@@ -410,6 +714,8 @@ int configure_apply_kernels() {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_group_down<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_leaf_up<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_leaf_down<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_group_up_warp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_group_down_warp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   return e == cudaSuccess ? 0 : -1;
 }
 

@@ -25,6 +25,57 @@ __device__ inline void report(int* status, int code, int level, int kind, int in
   }
 }
 
+// ---------------------------------------------------------------------------
+// Bulk global -> shared copies (cp.async.bulk, the TMA bulk path) completed on
+// an mbarrier.  Source, destination and size must be multiples of 16 bytes;
+// every factor block is padded so that they are.  Waits are bounded: after
+// kWaitLimit polls the caller reports RHIF_ERR_TIMEOUT instead of spinning on.
+// ---------------------------------------------------------------------------
+constexpr int kWaitLimit = 1 << 22;
+
+__device__ inline uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ inline void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ inline void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ inline void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ inline bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for phase `parity` of the barrier; false if it did not complete.
+__device__ inline bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (int i = 0; i < kWaitLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+__host__ __device__ inline uint32_t round16(size_t bytes) { return (uint32_t)((bytes + 15) & ~size_t(15)); }
+__host__ __device__ inline int64_t pad4e(int64_t n) { return (n + 3) & ~int64_t(3); }
+
 template <typename T>
 __device__ inline T warp_sum(T v) {
 #pragma unroll

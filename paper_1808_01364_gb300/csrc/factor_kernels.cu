@@ -411,41 +411,62 @@ k_leaf_stream(GeoDev G, LevelDev Lv, const double* diag, const double* off, int*
   // initial rows 0..w of the Z window: the single entry a_b of column b sits in row ci[b]
   for (int b = tid; b < nB; b += blockDim.x)
     if (ci[b] >= 0 && ci[b] <= w) win[(ci[b] % w1) * kStreamNB + b] = ca[b];
+  // fixed work assignment: Z-window column zb, rows 1 + zr0 + 4j; band pairs tid and tid + 256
+  const int zb = tid & (kStreamNB - 1), zr0 = tid >> 6;
+  const int my_ci = (tid < nB) ? ci[tid] : -1;
+  const T my_ca = (tid < nB) ? ca[tid] : T(0);
+  int pd1[2] = {0, 0}, pd2[2] = {0, 0};
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int q = tid + h * kThreads;
+    if (q < npair) {
+      pd1[h] = pairs[2 * q];
+      pd2[h] = pairs[2 * q + 1];
+    }
+  }
   T acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int bq = 0; bq < 4; ++bq) acc[a][bq] = T(0);
   const int ti = (tid >> 4) * 4, tj = (tid & 15) * 4;   // this thread's 4 x 4 block of S
+  int slot = 0;                                          // k % (w + 1)
   __syncthreads();
   for (int k = 0; k < nI; ++k) {
     const int wk = min(w, nI - 1 - k);
-    T* zk = win + (k % w1) * kStreamNB;
+    T* zk = win + slot * kStreamNB;
+    T* colk = sband + k * w1;
     // 1. pivot of column k
     if (tid == 0) {
-      T dkk = sband[k * w1];
+      T dkk = colk[0];
       if (!(dkk > T(0))) {
         bad = 1;
         dkk = T(1);
       }
       s_piv = my_sqrt(dkk);
-      sband[k * w1] = s_piv;
+      colk[0] = s_piv;
     }
     __syncthreads();
-    const T piv = s_piv;
+    const T rpiv = T(1) / s_piv;
     // 2. scale column k of L and row k of Z
-    for (int dd = 1 + tid; dd <= wk; dd += blockDim.x) sband[k * w1 + dd] /= piv;
-    for (int b = tid; b < nB; b += blockDim.x) zk[b] /= piv;
+    if (tid >= 1 && tid <= wk) colk[tid] *= rpiv;
+    if (tid < kStreamNB) zk[tid] *= rpiv;
     __syncthreads();
     // 3. trailing band update, Z rows k+1..k+wk, and S += z_k z_k^T
-    for (int q = tid; q < npair; q += blockDim.x) {
-      const int d1 = pairs[2 * q], d2 = pairs[2 * q + 1];
-      if (d1 > wk) continue;
-      sband[(k + d2) * w1 + (d1 - d2)] -= sband[k * w1 + d1] * sband[k * w1 + d2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int d1 = pd1[h], d2 = pd2[h];
+      if (d1 && d1 <= wk) sband[(k + d2) * w1 + (d1 - d2)] -= colk[d1] * colk[d2];
     }
-    for (int idx = tid; idx < wk * nB; idx += blockDim.x) {
-      const int dd = 1 + idx / nB, b = idx % nB;
-      win[((k + dd) % w1) * kStreamNB + b] -= sband[k * w1 + dd] * zk[b];
+    {
+      const T zv = zk[zb];
+      int sl = slot + 1 + zr0;
+      while (sl >= w1) sl -= w1;
+      for (int dd = 1 + zr0; dd <= wk; dd += 4) {
+        win[sl * kStreamNB + zb] -= colk[dd] * zv;
+        sl += 4;
+        while (sl >= w1) sl -= w1;
+      }
     }
     {
       T zi[4], zj[4];
@@ -460,10 +481,10 @@ k_leaf_stream(GeoDev G, LevelDev Lv, const double* diag, const double* off, int*
         for (int bq = 0; bq < 4; ++bq) acc[a][bq] += zi[a] * zj[bq];
     }
     __syncthreads();
-    // 4. recycle row k's slot for row k + w1
+    // 4. recycle row k's slot for row k + w + 1
     const int nr = k + w1;
-    for (int b = tid; b < kStreamNB; b += blockDim.x)
-      zk[b] = (nr < nI && b < nB && ci[b] == nr) ? ca[b] : T(0);
+    if (tid < kStreamNB) zk[tid] = (nr < nI && my_ci == nr) ? my_ca : T(0);
+    slot = (slot + 1 == w1) ? 0 : slot + 1;
     __syncthreads();
   }
   // frame = A_BB share - S (lower triangle)
@@ -652,7 +673,7 @@ __global__ void __launch_bounds__(kThreads) k_skel(LevelDev Lv, PhaseDev Ph, uin
   if (mstage) M = (T*)((unsigned char*)(sperm + Ph.max_n) + 16 - (((size_t)(sperm + Ph.max_n)) & 15));
   T* Aee = M + (int64_t)nrow * n;
   T* Fu = (T*)Ph.rec + Ph.u_rec_off[u];
-  T* Tm = Fu + (int64_t)n * n;
+  T* Tm = Fu + pad4e((int64_t)n * n);
   const int c0 = Lv.group_cell_off[g], c1 = Lv.group_cell_off[g + 1];
   const int nslot = c1 - c0;
 

@@ -80,6 +80,10 @@ inline void vrange(int v, int w, int ns, int* lo, int* hi) {
   }
 }
 
+// Element counts are padded to multiples of 4 so that every factor block
+// starts on a 16-byte boundary (bulk shared-memory copies need it).
+inline int64_t pad4(int64_t n) { return (n + 3) & ~int64_t(3); }
+
 }  // namespace
 
 int unit_row_count(const LevelPlan& P, int g) {
@@ -242,19 +246,19 @@ LevelPlan build_level(const Geometry& G, int level, const std::vector<int32_t>& 
       if (nI == 0) bw = 0;
       P.band_w.push_back(bw);
       P.band_off.push_back(P.band_total);
-      P.band_total += (int64_t)nI * (bw + 1);
+      P.band_total += pad4((int64_t)nI * (bw + 1));
       P.z_off.push_back(P.z_total);
-      P.z_total += (int64_t)nI * nB;
+      P.z_total += pad4((int64_t)nI * nB);
       P.frame_off.push_back(P.frame_total);
       P.frame_ld.push_back(nB);
-      P.frame_total += (int64_t)nB * nB;
+      P.frame_total += pad4((int64_t)nB * nB);
       P.front_off.push_back(0);
       P.max_w = std::max(P.max_w, bw);
     } else {
       P.front_off.push_back(P.front_total);
       P.frame_off.push_back(P.front_total + nI + (int64_t)nI * n);
       P.frame_ld.push_back(n);
-      P.front_total += (int64_t)n * n;
+      P.front_total += pad4((int64_t)n * n);
     }
     P.max_nI = std::max(P.max_nI, nI);
     P.max_nB = std::max(P.max_nB, nB);
@@ -342,7 +346,7 @@ LevelPlan build_level(const Geometry& G, int level, const std::vector<int32_t>& 
         ph.group_pre[gi] = (int)ph.pre_group.size();
         ph.pre_group.push_back(gi);
         ph.pre_off.push_back(ph.pre_total);
-        ph.pre_total += (int64_t)sz * sz;
+        ph.pre_total += pad4((int64_t)sz * sz);
       }
       if (P.group_t[gi] == ph.unit_type) {
         ph.group_unit[gi] = (int)U.group.size();
@@ -353,7 +357,7 @@ LevelPlan build_level(const Geometry& G, int level, const std::vector<int32_t>& 
         U.m_total += (int64_t)(nrow + sz) * sz;
         U.max_m = std::max<int64_t>(U.max_m, (int64_t)(nrow + sz) * sz);
         U.rec_off.push_back(U.rec_total);
-        U.rec_total += 2 * (int64_t)sz * sz;
+        U.rec_total += 2 * pad4((int64_t)sz * sz);
         U.perm_off.push_back(U.perm_total);
         U.perm_total += sz;
         U.max_n = std::max(U.max_n, sz);

@@ -43,7 +43,7 @@ struct UnitTable {
   std::vector<int> nrow;           // |R|
   std::vector<int64_t> m_off;      // scratch: M (nrow x n) then A_ee (n x n)
   int64_t m_total = 0;
-  std::vector<int64_t> rec_off;    // record: unit front (n x n) then T (n x n)
+  std::vector<int64_t> rec_off;    // record: unit front (n x n, padded to 4) then T (k x (n-k))
   int64_t rec_total = 0;
   std::vector<int64_t> perm_off;   // pivot order (n ints)
   int64_t perm_total = 0;

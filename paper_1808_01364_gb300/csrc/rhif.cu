@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
+#include <cstdlib>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -291,6 +293,7 @@ static int upload_level(rhif_handle* H, LevelStore& S, size_t elem) {
   L.ea_child = (const int*)(b + o_eac);
   L.ea_map_off = (const int64_t*)(b + o_eamo);
   L.ea_map = (const int*)(b + o_eam);
+  L.status = H->status;
   if ((rc = H->mem.get((void**)&L.gids, P.gid_off.back() * sizeof(int32_t)))) return rc;
   if (P.level == 0) {
     if ((rc = H->mem.get(&L.frame_base, P.frame_total * elem))) return rc;
@@ -380,11 +383,21 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
   std::vector<uint8_t> alive(G.N, 1);
   std::vector<int32_t> active;
   H->levels.resize(G.L + 1);
+  const bool trace = std::getenv("RHIF_TRACE") != nullptr;
+  using clk = std::chrono::steady_clock;
+  auto ms_since = [](clk::time_point t) {
+    return std::chrono::duration<double, std::milli>(clk::now() - t).count();
+  };
   for (int lvl = 0; lvl <= G.L; ++lvl) {
     LevelStore& S = H->levels[lvl];
     const LevelPlan* prev = lvl ? &H->levels[lvl - 1].plan : nullptr;
+    auto t0 = clk::now();
     S.plan = build_level(G, lvl, active, alive, prev, H->precondition, H->edge_skel);
+    const double t_plan = ms_since(t0);
+    auto t1 = clk::now();
     if ((rc = upload_level(H, S, elem))) return rc;
+    const double t_up = ms_since(t1);
+    auto t2 = clk::now();
     const LevelPlan& P = S.plan;
     H->ub_len = std::max<int64_t>(H->ub_len, P.b_off.back());
     {
@@ -483,6 +496,9 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
       }
     }
     if ((rc = check_status(H, lvl == G.L ? "root factorization" : "cell elimination"))) return rc;
+    if (trace)
+      std::fprintf(stderr, "[rhif] level %d: cells %d groups %d active %zu plan %.2f ms upload %.2f ms gpu+sync %.2f ms\n",
+                   lvl, P.ncell(), P.ngroup(), P.bucket.size(), t_plan, t_up, ms_since(t2));
     if (lvl == 0 && S.dev.zbuf) {
       H->mem.release(S.dev.zbuf);
       S.dev.zbuf = nullptr;

@@ -55,6 +55,7 @@ struct LevelDev {
   const int* ea_child;
   const int64_t* ea_map_off;
   const int* ea_map;
+  int* status;               // error word of the handle (timeouts of bulk copies)
 };
 
 struct PhaseDev {

@@ -1,9 +1,12 @@
 """GPU path vs the FP64 oracle on the same seeded inputs (through the C-ABI).
 
-FP64 bar (derived in the design doc): identical skeleton sets except at logged
-near-ties, F^{-1} x within 1e-9 relative of the oracle's (both are
-products of the same well-conditioned factors up to roundoff), PCG relative
-residual <= rtol with the solution within 1e-8 of a sparse direct solve.
+FP64 bar: identical skeleton sets except at logged near-ties (the pivot
+choices are then the same, so both sides apply the same operators); F^{-1} x
+within 1e-9 relative of the oracle's (the two differ only in summation order,
+about 1e-16 per operation, amplified by the conditioning of the level factors,
+which stays below ~1e6 on these grids); apply error ||F^{-1}Ax - x|| within 2x
+of the oracle's; PCG relative residual <= rtol with the solution within 1e-9 of
+a sparse direct solve.
 """
 import numpy as np
 import pytest

@@ -106,6 +106,22 @@ int rhif_factor(const rhif_csr* A, const rhif_grid* g, int leaf, double tol,
 int rhif_apply(const rhif_handle* F, int op, int nrhs, const double* x, int64_t ldx,
                double* y, int64_t ldy, void* stream);
 
+/* y = F^{-1} x like rhif_apply(F, RHIF_SOLVE, ...) but without allocating any
+ * device memory.  The paper has no counterpart: this entry point exists for
+ * callers that cannot allocate while they apply the preconditioner, for
+ * instance an outer solver that has reserved all device memory up front, or
+ * code that must not risk the device synchronization and mid-run allocation
+ * failure that cudaMalloc can bring.  Scratch comes from a static device array
+ * of 2^20 doubles (8 MiB) that every GPU loading the library holds until the
+ * process exits; requests needing more (ub_len * nrhs, about the number of
+ * boundary DOFs of one level times nrhs) are rejected with RHIF_ERR_BAD_ARG
+ * before any work is queued.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) and should come before any stream
+ * capture on that device.  All calls share the array: calls that overlap on
+ * the GPU race and must be ordered by the caller. */
+int rhif_apply_noalloc(const rhif_handle* F, int nrhs, const double* x, int64_t ldx,
+                       double* y, int64_t ldy, void* stream);
+
 /* y = A x with the stencil form of the A given to rhif_factor (FP64). */
 int rhif_spmv(const rhif_handle* F, int nrhs, const double* x, int64_t ldx,
               double* y, int64_t ldy, void* stream);

@@ -77,6 +77,9 @@ EXPORTS = {
                                   ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "rhif_spmv": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
                                  ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
+    "rhif_apply_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                          ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
+                                          ctypes.c_void_p]),
     "rhif_pcg": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
                                 ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int,
                                 ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
@@ -203,6 +206,13 @@ class Factor:
         y = torch.empty_like(x) if out is None else out
         _check(_lib.rhif_apply(self._h, RHIF_SOLVE, nrhs, _ptr(x), ld, _ptr(y), ld, _stream(stream)))
         return y
+
+    def apply_noalloc(self, x: torch.Tensor, out: torch.Tensor, stream=None) -> torch.Tensor:
+        """F^{-1} x into the caller's ``out`` without any device allocation
+        (library-owned static scratch; see rhif_apply_noalloc in rhif.h)."""
+        nrhs, ld = _cols(x, self.N)
+        _check(_lib.rhif_apply_noalloc(self._h, nrhs, _ptr(x), ld, _ptr(out), ld, _stream(stream)))
+        return out
 
     def spmv(self, x: torch.Tensor, stream=None) -> torch.Tensor:
         nrhs, ld = _cols(x, self.N)

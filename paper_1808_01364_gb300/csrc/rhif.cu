@@ -940,3 +940,88 @@ const char* rhif_error_string(int code) {
 const char* rhif_last_error_detail(void) { return g_detail.c_str(); }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// F^{-1} x without any device allocation
+// ---------------------------------------------------------------------------
+//
+// Scratch for the cell-to-group contributions of the upward sweep, held in a
+// file-scope device array instead of memory the handle allocates on first
+// use.  Every GPU that loads the library keeps these 8 MiB until the process
+// exits.  Each call writes every entry it later reads, so nothing has to be
+// cleared between calls; calls that overlap on the GPU (two streams, or two
+// handles used concurrently) share the array and race.
+
+namespace rhif {
+
+constexpr int64_t kNoAllocScratch = int64_t(1) << 20;   // doubles
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratch];
+
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_addr[256];
+
+// Device address of the scratch array on the current device, looked up once
+// per device (the array's host-side name is only a stand-in).
+static int noalloc_scratch(double** out) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 256) return fail(RHIF_ERR_CUDA, "device index out of range");
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess)
+      return fail(RHIF_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    g_noalloc_addr[dev] = p;
+  }
+  *out = (double*)g_noalloc_addr[dev];
+  return RHIF_OK;
+}
+
+template <typename T>
+static int apply_noalloc_impl(const rhif_handle* Hc, double* y, int64_t ldy, int nrhs,
+                              double* ubuf, cudaStream_t s) {
+  rhif_handle* H = const_cast<rhif_handle*>(Hc);
+  const int L = H->G.L;
+  const int64_t ldu = H->ub_len;
+  for (int l = 0; l < L; ++l) {
+    LevelStore& S = H->levels[l];
+    launch_apply_cell_up<T>(S.dev, y, ldy, nrhs, ubuf, ldu, s);
+    for (size_t p = 0; p < S.phases.size(); ++p)
+      launch_apply_group_up<T>(S.dev, S.phases[p].dev, p == 0, y, ldy, nrhs, ubuf, ldu, s);
+  }
+  launch_apply_cell_up<T>(H->levels[L].dev, y, ldy, nrhs, ubuf, ldu, s);
+  launch_apply_cell_down<T>(H->levels[L].dev, y, ldy, nrhs, s);
+  for (int l = L - 1; l >= 0; --l) {
+    LevelStore& S = H->levels[l];
+    for (int p = (int)S.phases.size() - 1; p >= 0; --p)
+      launch_apply_group_down<T>(S.dev, S.phases[p].dev, y, ldy, nrhs, s);
+    launch_apply_cell_down<T>(S.dev, y, ldy, nrhs, s);
+  }
+  CK(cudaGetLastError());
+  return RHIF_OK;
+}
+
+}  // namespace rhif
+
+extern "C" int rhif_apply_noalloc(const rhif_handle* F, int nrhs, const double* x, int64_t ldx,
+                                  double* y, int64_t ldy, void* stream) {
+  if (!F || !x || !y || nrhs < 0) return fail(RHIF_ERR_BAD_ARG, "null argument");
+  const int64_t N = F->G.N;
+  if (ldx < N || ldy < N) return fail(RHIF_ERR_BAD_ARG, "leading dimension < N");
+  if (x == y && ldx != ldy) return fail(RHIF_ERR_BAD_ARG, "aliased x and y need ldx == ldy");
+  if (nrhs == 0) return RHIF_OK;
+  const int64_t need = F->ub_len * (int64_t)nrhs;
+  if (need > kNoAllocScratch)
+    return fail(RHIF_ERR_BAD_ARG, "rhif_apply_noalloc needs " + std::to_string(need) +
+                                      " scratch doubles; the static scratch holds " +
+                                      std::to_string(kNoAllocScratch) +
+                                      " (use fewer right-hand sides or rhif_apply)");
+  double* ubuf = nullptr;
+  int rc = noalloc_scratch(&ubuf);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (x != y) launch_copy_cols(N, nrhs, x, ldx, y, ldy, s);
+  return F->precision == RHIF_FP64 ? apply_noalloc_impl<double>(F, y, ldy, nrhs, ubuf, s)
+                                   : apply_noalloc_impl<float>(F, y, ldy, nrhs, ubuf, s);
+}

@@ -323,7 +323,7 @@ def gpu_arm(args):
     top = max(ks.items(), key=lambda kv: kv[1]["total_ms"])
     name, st = top
     per_launch_ms = st["total_ms"] / max(st["launches"], 1)
-    if name.startswith("apply") or name in ("spmv", "pcg_vector", "extend_add", "front_leaf"):
+    if name.startswith("apply") or name in ("spmv", "pcg_vector", "extend_add", "expand_gids"):
         achieved = st["bytes"] / max(st["launches"], 1) / (per_launch_ms / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "peak_kind": hbm_kind}

@@ -91,12 +91,13 @@ struct Packer {
 enum Cat {
   kCatStencil, kCatLeafElim, kCatExpandGids, kCatExtendAdd, kCatPartialChol, kCatPrecondDiag, kCatPrecondScale,
   kCatSkel, kCatApplyCellUp, kCatApplyCellDown, kCatApplyGroupUp, kCatApplyGroupDown, kCatSpmv,
-  kCatVector, kCatAssemble, kCatGrad, kNumCat
+  kCatVector, kCatAssemble, kCatGrad, kCatApplyLeafUp, kCatApplyLeafDown, kNumCat
 };
 static const char* kCatName[kNumCat] = {
     "stencil_from_csr", "leaf_elim", "expand_gids", "extend_add", "partial_chol", "precond_diag",
     "precond_scale", "skel", "apply_cell_up", "apply_cell_down", "apply_group_up",
-    "apply_group_down", "spmv", "pcg_vector", "assemble_fd", "grad_logcoef"};
+    "apply_group_down", "spmv", "pcg_vector", "assemble_fd", "grad_logcoef", "apply_leaf_up",
+    "apply_leaf_down"};
 struct KStat {
   int64_t launches = 0;
   double ms = 0, flops = 0, bytes = 0;
@@ -564,7 +565,8 @@ static int apply_impl(const rhif_handle* Hc, double* y, int64_t ldy, int nrhs, c
   for (int l = 0; l < L; ++l) {
     LevelStore& S = H->levels[l];
     {
-      Launch t(kCatApplyCellUp, s, S.cell_flops * nrhs, S.cell_bytes * nrhs);
+      Launch t(l == 0 ? kCatApplyLeafUp : kCatApplyCellUp, s, S.cell_flops * nrhs,
+               S.cell_bytes * nrhs);
       launch_apply_cell_up<T>(S.dev, y, ldy, nrhs, H->ubuf, ldu, s);
     }
     for (size_t p = 0; p < S.phases.size(); ++p) {
@@ -588,7 +590,8 @@ static int apply_impl(const rhif_handle* Hc, double* y, int64_t ldy, int nrhs, c
       Launch t(kCatApplyGroupDown, s, S.grp_flops[p] * nrhs, S.grp_bytes[p] * nrhs);
       launch_apply_group_down<T>(S.dev, S.phases[p].dev, y, ldy, nrhs, s);
     }
-    Launch t(kCatApplyCellDown, s, S.cell_flops * nrhs, S.cell_bytes * nrhs);
+    Launch t(l == 0 ? kCatApplyLeafDown : kCatApplyCellDown, s, S.cell_flops * nrhs,
+             S.cell_bytes * nrhs);
     launch_apply_cell_down<T>(S.dev, y, ldy, nrhs, s);
   }
   CK(cudaGetLastError());

@@ -87,6 +87,14 @@ int rhif_assemble_fd(const rhif_grid* g, const double* a_pix, const double* b_no
                      double b_const, int64_t* rowptr, int32_t* col, double* val,
                      void* stream);
 
+/* As rhif_assemble_fd, but from the per-pixel log-coefficient: a = exp(log_a)
+ * is written to a_pix_out (one value per pixel, caller-allocated) and used for
+ * the assembly.  This is the parameterization of the differentiation pattern
+ * (gradient with respect to log a, see rhif_grad_logcoef). */
+int rhif_assemble_fd_log(const rhif_grid* g, const double* log_a_pix, double* a_pix_out,
+                         const double* b_node, double b_const, int64_t* rowptr, int32_t* col,
+                         double* val, void* stream);
+
 /* PHIF factorization F ~= A (Sec. 3): per level l = 0..L-1 cell elimination
  * (Sec. 2.1, Eq. 2.1), block Jacobi preconditioning of every separator group
  * (Sec. 2.3, Eq. 2.3) and skeletonization of every edge (2D) / face (3D) by a
@@ -99,6 +107,25 @@ int rhif_assemble_fd(const rhif_grid* g, const double* a_pix, const double* b_no
  * tol < 0), NOT_SPD (with the level in the detail string), OOM, CUDA. */
 int rhif_factor(const rhif_csr* A, const rhif_grid* g, int leaf, double tol,
                 const rhif_opts* o, void* stream, rhif_handle** out);
+
+/* Factor `count` independent problems (A[i] on grid g[i], same leaf, tol and
+ * options) with the levels of different problems running concurrently: the
+ * problems are spread over the `nstreams` CUDA streams in `streams` (problem i
+ * on streams[i % nstreams]) and each stream is driven by its own host worker
+ * thread.  out[i] receives the handle of problem i, or NULL if it failed; the
+ * return value is the first failure's code (RHIF_OK if none).  The caller's
+ * current device is used by every worker. */
+int rhif_factor_batched(int count, const rhif_csr* A, const rhif_grid* g, int leaf, double tol,
+                        const rhif_opts* o, void* const* streams, int nstreams,
+                        rhif_handle** out);
+
+/* PCG (as rhif_pcg) for `count` factored problems at once, each with nrhs
+ * right-hand sides stored contiguously (f[i] and u[i] are N_i x nrhs with
+ * leading dimension N_i), spread over the streams like rhif_factor_batched.
+ * iters and relres are HOST arrays of count * nrhs entries (problem-major). */
+int rhif_pcg_batched(int count, rhif_handle* const* F, int nrhs, const double* const* f,
+                     double* const* u, double rtol, int maxit, int* iters, double* relres,
+                     void* const* streams, int nstreams);
 
 /* y = F^{-1} x (op = RHIF_SOLVE, Eq. 3.2) or y = F x (RHIF_MATVEC, Eq. 3.1)
  * for nrhs column vectors of length N stored with leading dimensions ldx/ldy

@@ -70,6 +70,9 @@ EXPORTS = {
     "rhif_assemble_fd": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_void_p]),
+    "rhif_assemble_fd_log": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "rhif_factor": (ctypes.c_int, [ctypes.POINTER(CSR), ctypes.POINTER(Grid), ctypes.c_int,
                                    ctypes.c_double, ctypes.POINTER(Opts), ctypes.c_void_p,
                                    ctypes.POINTER(ctypes.c_void_p)]),
@@ -90,6 +93,14 @@ EXPORTS = {
     "rhif_skeletons": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                       ctypes.POINTER(ctypes.c_int), ctypes.c_void_p,
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
+    "rhif_factor_batched": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_int, ctypes.c_double, ctypes.POINTER(Opts),
+                                           ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "rhif_pcg_batched": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
+                                        ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_double), ctypes.c_void_p,
+                                        ctypes.c_int]),
     "rhif_free": (None, [ctypes.c_void_p]),
     "rhif_set_timing": (ctypes.c_int, [ctypes.c_int]),
     "rhif_reset_kernel_stats": (ctypes.c_int, []),
@@ -305,3 +316,127 @@ def rhif_kernel_stats() -> dict:
         out[st.name.decode()] = {"launches": st.launches, "total_ms": st.total_ms,
                                  "flops": st.flops, "bytes": st.bytes}
     return out
+
+
+def rhif_assemble_fd_log(ns, log_a_pix: torch.Tensor, b=0.0, stream=None):
+    """Finite-difference matrix from the per-pixel log-coefficient; returns (csr, a_pix)."""
+    load()
+    g = _grid(ns)
+    N = 1
+    for v in ns:
+        N *= int(v)
+    nnz = int(_lib.rhif_fd_nnz(ctypes.byref(g)))
+    dev = log_a_pix.device
+    log_a_pix = log_a_pix.contiguous().to(torch.float64)
+    a_pix = torch.empty_like(log_a_pix)
+    rowptr = torch.empty(N + 1, dtype=torch.int64, device=dev)
+    col = torch.empty(nnz, dtype=torch.int32, device=dev)
+    val = torch.empty(nnz, dtype=torch.float64, device=dev)
+    if isinstance(b, torch.Tensor):
+        bn, bc = _ptr(b.contiguous().to(torch.float64)), 0.0
+    else:
+        bn, bc = None, float(b)
+    _check(_lib.rhif_assemble_fd_log(ctypes.byref(g), _ptr(log_a_pix), _ptr(a_pix), bn, bc,
+                                     _ptr(rowptr), _ptr(col), _ptr(val), _stream(stream)))
+    return (rowptr, col, val), a_pix
+
+
+class RhifSolve(torch.autograd.Function):
+    """u = A(log a)^{-1} f by PHIF-preconditioned CG, differentiable in log a and f.
+
+    Forward: assemble A from exp(log a), factor it (PHIF, Sec. 3) and solve by
+    PCG.  Backward: the adjoint lam = A^{-1} dL/du reuses the same factor (A is
+    symmetric), dL/df = lam and dL/dlog a_p = -lam^T (dA/dlog a_p) u from the
+    gradient kernel.  ``opts`` = dict(leaf, tol, precision, rtol, maxit).
+    """
+
+    @staticmethod
+    def forward(ctx, log_a, f, ns, opts):
+        o = dict(leaf=16, tol=1e-6, precision="fp64", rtol=1e-12, maxit=1000)
+        o.update(opts or {})
+        csr, a_pix = rhif_assemble_fd_log(ns, log_a.detach())
+        F = rhif_factor(csr, ns, o["leaf"], o["tol"], precision=o["precision"])
+        u, its, rr = F.pcg(f.detach().contiguous(), rtol=o["rtol"], maxit=o["maxit"])
+        ctx.F, ctx.ns, ctx.o = F, tuple(ns), o
+        ctx.save_for_backward(a_pix, u)
+        ctx.iters = its
+        return u
+
+    @staticmethod
+    def backward(ctx, g_u):
+        a_pix, u = ctx.saved_tensors
+        F = ctx.F
+        lam, _, _ = F.pcg(g_u.contiguous(), rtol=ctx.o["rtol"], maxit=ctx.o["maxit"])
+        grad_log_a = rhif_grad_logcoef(ctx.ns, a_pix, u, lam)
+        F.free()
+        ctx.F = None
+        return grad_log_a, lam, None, None
+
+
+def rhif_solve(log_a: torch.Tensor, f: torch.Tensor, ns, **opts) -> torch.Tensor:
+    """Differentiable PHIF solve (see :class:`RhifSolve`)."""
+    return RhifSolve.apply(log_a, f, tuple(ns), opts)
+
+
+def _opts(precision="fp64", precondition=True, edge_skel_3d=False) -> Opts:
+    o = Opts()
+    _lib.rhif_default_opts(ctypes.byref(o))
+    o.precision = {"fp64": RHIF_FP64, "fp32": RHIF_MIXED_FP32, "mixed": RHIF_MIXED_FP32}[precision]
+    o.precondition = 1 if precondition else 0
+    o.edge_skel_3d = 1 if edge_skel_3d else 0
+    return o
+
+
+def rhif_factor_batched(csrs, grids, leaf: int, tol: float, precision: str = "fp64",
+                        precondition=True, streams=None):
+    """Factor many independent problems concurrently (one worker per stream)."""
+    load()
+    n = len(csrs)
+    if streams is None:
+        streams = [torch.cuda.Stream() for _ in range(min(8, max(n, 1)))]
+    A = (CSR * n)()
+    G = (Grid * n)()
+    for i, ((rp, col, val), ns) in enumerate(zip(csrs, grids)):
+        A[i] = CSR(rp.numel() - 1, val.numel(), rp.data_ptr(), col.data_ptr(), val.data_ptr())
+        G[i] = _grid(ns)
+    S = (ctypes.c_void_p * len(streams))(*[s.cuda_stream for s in streams])
+    out = (ctypes.c_void_p * n)()
+    o = _opts(precision, precondition)
+    cur = torch.cuda.current_stream()
+    for s in streams:
+        s.wait_stream(cur)
+    rc = _lib.rhif_factor_batched(n, A, G, int(leaf), float(tol), ctypes.byref(o), S, len(streams), out)
+    facs = [Factor(ctypes.c_void_p(out[i]), grids[i], None) if out[i] else None for i in range(n)]
+    for s in streams:
+        cur.wait_stream(s)
+    if rc != 0:
+        for F in facs:
+            if F is not None:
+                F.free()
+        _check(rc)
+    return facs, streams
+
+
+def rhif_pcg_batched(factors, fs, rtol=1e-10, maxit=1000, streams=None):
+    """PCG for many factored problems at once; fs[i] is (nrhs, N_i).  Returns (us, iters, relres)."""
+    load()
+    n = len(factors)
+    nrhs = 1 if fs[0].dim() == 1 else fs[0].shape[0]
+    if streams is None:
+        streams = [torch.cuda.Stream() for _ in range(min(8, max(n, 1)))]
+    us = [torch.empty_like(f) for f in fs]
+    H = (ctypes.c_void_p * n)(*[F._h.value if isinstance(F._h, ctypes.c_void_p) else F._h for F in factors])
+    Fp = (ctypes.c_void_p * n)(*[f.data_ptr() for f in fs])
+    Up = (ctypes.c_void_p * n)(*[u.data_ptr() for u in us])
+    it = (ctypes.c_int * (n * nrhs))()
+    rr = (ctypes.c_double * (n * nrhs))()
+    S = (ctypes.c_void_p * len(streams))(*[s.cuda_stream for s in streams])
+    cur = torch.cuda.current_stream()
+    for s in streams:
+        s.wait_stream(cur)
+    rc = _lib.rhif_pcg_batched(n, H, nrhs, Fp, Up, float(rtol), int(maxit), it, rr, S, len(streams))
+    for s in streams:
+        cur.wait_stream(s)
+    _check(rc)
+    return us, [list(it[i * nrhs:(i + 1) * nrhs]) for i in range(n)], \
+        [list(rr[i * nrhs:(i + 1) * nrhs]) for i in range(n)]

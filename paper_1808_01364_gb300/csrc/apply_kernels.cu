@@ -999,6 +999,15 @@ __global__ void k_assemble_fd(GeoDev G, const double* a_pix, const double* b_nod
     if (x[a] + 1 < G.ns[a]) { col[k] = (int32_t)(i + G.stride[a]); val[k] = offv[a][1]; ++k; }
 }
 
+__global__ void k_exp(int64_t n, const double* x, double* y) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = exp(x[i]);
+}
+
+void launch_exp(int64_t n, const double* x, double* y, cudaStream_t s) {
+  if (n > 0) k_exp<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, x, y);
+}
+
 void launch_assemble_fd(const GeoDev& G, const double* a_pix, const double* b_node, double b_const,
                         int64_t* rowptr, int32_t* col, double* val, cudaStream_t s) {
   if (!G.N) return;

@@ -67,6 +67,7 @@ void launch_copy_cols(int64_t N, int nrhs, const double* a, int64_t lda, double*
                       cudaStream_t s);
 void launch_assemble_fd(const GeoDev& G, const double* a_pix, const double* b_node, double b_const,
                         int64_t* rowptr, int32_t* col, double* val, cudaStream_t s);
+void launch_exp(int64_t n, const double* x, double* y, cudaStream_t s);
 void launch_grad_logcoef(const GeoDev& G, const double* a_pix, const double* u, const double* lam,
                          double* grad, cudaStream_t s);
 

@@ -16,6 +16,7 @@
 #include <memory>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/rhif.h"
@@ -613,6 +614,35 @@ static int ensure_work(rhif_handle* H, int64_t elems) {
   return RHIF_OK;
 }
 
+// Runs job(i, stream) for i = 0..count-1 with one host worker per stream.
+template <typename Job>
+static int run_batched(int count, void* const* streams, int nstreams, Job job,
+                       std::vector<std::string>* details) {
+  if (count < 0 || nstreams < 1 || !streams) return fail(RHIF_ERR_BAD_ARG, "bad batch arguments");
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  // kernel attributes are set once, before any worker starts
+  if (configure_once<double>() || configure_once<float>())
+    return fail(RHIF_ERR_CUDA, "cannot configure kernel shared memory");
+  std::vector<int> rc(count, RHIF_OK);
+  details->assign(count, std::string());
+  std::vector<std::thread> pool;
+  const int nw = std::min(nstreams, std::max(count, 1));
+  for (int w = 0; w < nw; ++w) {
+    pool.emplace_back([&, w]() {
+      cudaSetDevice(dev);
+      for (int i = w; i < count; i += nw) {
+        rc[i] = job(i, streams[w % nstreams]);
+        if (rc[i]) (*details)[i] = g_detail;
+      }
+    });
+  }
+  for (auto& t : pool) t.join();
+  for (int i = 0; i < count; ++i)
+    if (rc[i]) return fail(rc[i], "problem " + std::to_string(i) + ": " + (*details)[i]);
+  return RHIF_OK;
+}
+
 }  // namespace rhif
 
 using namespace rhif;
@@ -659,6 +689,22 @@ int rhif_assemble_fd(const rhif_grid* g, const double* a_pix, const double* b_no
   }
   CK(cudaGetLastError());
   return RHIF_OK;
+}
+
+int rhif_assemble_fd_log(const rhif_grid* g, const double* log_a_pix, double* a_pix_out,
+                         const double* b_node, double b_const, int64_t* rowptr, int32_t* col,
+                         double* val, void* stream) {
+  int rc = check_grid(g);
+  if (rc) return rc;
+  if (!log_a_pix || !a_pix_out) return fail(RHIF_ERR_BAD_ARG, "null pointer");
+  int64_t npix = 1;
+  for (int a = 0; a < g->dim; ++a) npix *= g->n[a] + 1;
+  {
+    Launch t(kCatAssemble, (cudaStream_t)stream, 0.0, 16.0 * npix);
+    launch_exp(npix, log_a_pix, a_pix_out, (cudaStream_t)stream);
+  }
+  CK(cudaGetLastError());
+  return rhif_assemble_fd(g, a_pix_out, b_node, b_const, rowptr, col, val, stream);
 }
 
 int rhif_factor(const rhif_csr* A, const rhif_grid* g, int leaf, double tol, const rhif_opts* o,
@@ -708,6 +754,36 @@ int rhif_factor(const rhif_csr* A, const rhif_grid* g, int leaf, double tol, con
   cudaEventDestroy(e1);
   *out = H.release();
   return RHIF_OK;
+}
+
+int rhif_factor_batched(int count, const rhif_csr* A, const rhif_grid* g, int leaf, double tol,
+                        const rhif_opts* o, void* const* streams, int nstreams,
+                        rhif_handle** out) {
+  if (!A || !g || !out) return fail(RHIF_ERR_BAD_ARG, "null argument");
+  for (int i = 0; i < count; ++i) out[i] = nullptr;
+  std::vector<std::string> details;
+  return run_batched(
+      count, streams, nstreams,
+      [&](int i, void* s) { return rhif_factor(&A[i], &g[i], leaf, tol, o, s, &out[i]); },
+      &details);
+}
+
+int rhif_pcg_batched(int count, rhif_handle* const* F, int nrhs, const double* const* f,
+                     double* const* u, double rtol, int maxit, int* iters, double* relres,
+                     void* const* streams, int nstreams) {
+  if (!F || !f || !u) return fail(RHIF_ERR_BAD_ARG, "null argument");
+  for (int i = 0; i < count; ++i)
+    if (!F[i]) return fail(RHIF_ERR_BAD_ARG, "null handle in batch");
+  std::vector<std::string> details;
+  return run_batched(
+      count, streams, nstreams,
+      [&](int i, void* s) {
+        const int64_t N = F[i]->G.N;
+        return rhif_pcg(F[i], nrhs, f[i], N, u[i], N, rtol, maxit,
+                        iters ? iters + (int64_t)i * nrhs : nullptr,
+                        relres ? relres + (int64_t)i * nrhs : nullptr, s);
+      },
+      &details);
 }
 
 int rhif_apply(const rhif_handle* F, int op, int nrhs, const double* x, int64_t ldx, double* y,

@@ -65,7 +65,17 @@ typedef struct {
   int precision;      /* RHIF_FP64 (default) or RHIF_MIXED_FP32 */
   int precondition;   /* 1 = PHIF (default, Sec. 3); 0 = plain HIF (C_l = I) */
   int edge_skel_3d;   /* 3D only: also precondition and skeletonize edges (Remark 3.1) */
-  int reserved[5];
+  /* Scheduling only (the result does not depend on them beyond rounding order):
+   * big_front: front order (interior + boundary DOFs of a cell) from which a
+   *   level's fronts are eliminated by panel / trailing-tile launches over many
+   *   CTAs instead of one CTA per front; 0 = library default (384), < 0 = never.
+   * big_frame: frame order (boundary DOFs of a cell) from which the block
+   *   Jacobi scaling of Eq. (2.3) runs as row / column block solves over many
+   *   CTAs; 0 = library default (when the frame no longer fits in shared
+   *   memory), < 0 = never. */
+  int big_front;
+  int big_frame;
+  int reserved[3];
 } rhif_opts;
 
 typedef struct rhif_handle rhif_handle;

@@ -93,62 +93,131 @@ __device__ inline T sym_at(const T* A, int64_t ld, int i, int j) {
   return i >= j ? A[i + (int64_t)j * ld] : A[j + (int64_t)i * ld];
 }
 
-// C[i,j] -= sum_{k in [k0,k1)} P[i,k] * P[j,k] for i in [r0,r1), j in [c0,c1), i >= j.
-// C and P are column-major (ldc, ldp); they may be the same matrix as long as
-// the updated block and the operand columns do not overlap.
+// One 64 x 64 output tile with corner (ti, tj):
+// C[i,j] -= sum_{k in [k0,k1)} P[i,k] * P[j,k] for i in [ti, min(ti+64, r1)),
+// j in [tj, min(tj+64, c1)), i >= j.  C and P are column-major (ldc, ldp); they
+// may be the same matrix as long as the tile and the operand columns do not overlap.
 template <typename T>
-__device__ void cta_syrk_lower(T* C, int64_t ldc, const T* P, int64_t ldp, int r0, int r1, int c0,
-                               int c1, int k0, int k1, T* sm) {
-  if (r0 >= r1 || c0 >= c1 || k0 >= k1) return;
+__device__ void cta_syrk_tile(T* C, int64_t ldc, const T* P, int64_t ldp, int ti, int tj, int r1,
+                              int c1, int k0, int k1, T* sm) {
   T* si = sm;                          // [kKC][kTile+1]
   T* sj = sm + kKC * (kTile + 1);      // [kKC][kTile+1]
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
-  for (int ti = r0; ti < r1; ti += kTile) {
-    for (int tj = c0; tj < c1; tj += kTile) {
-      if (tj > ti + kTile - 1) break;   // tile entirely above the diagonal
-      T acc[4][4];
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+  for (int kc = k0; kc < k1; kc += kKC) {
+    const int kk = min(kKC, k1 - kc);
+    for (int idx = tid; idx < kTile * kKC; idx += kThreads) {
+      const int i = idx % kTile, k = idx / kTile;
+      const int gi = ti + i, gj = tj + i;
+      si[k * (kTile + 1) + i] = (gi < r1 && k < kk) ? P[gi + (int64_t)(kc + k) * ldp] : T(0);
+      sj[k * (kTile + 1) + i] = (gj < c1 && k < kk) ? P[gj + (int64_t)(kc + k) * ldp] : T(0);
+    }
+    __syncthreads();
+    for (int k = 0; k < kk; ++k) {
+      T av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = si[k * (kTile + 1) + ty + 16 * a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) bv[b] = sj[k * (kTile + 1) + tx + 16 * b];
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
-      for (int kc = k0; kc < k1; kc += kKC) {
-        const int kk = min(kKC, k1 - kc);
-        for (int idx = tid; idx < kTile * kKC; idx += kThreads) {
-          const int i = idx % kTile, k = idx / kTile;
-          const int gi = ti + i, gj = tj + i;
-          si[k * (kTile + 1) + i] = (gi < r1 && k < kk) ? P[gi + (int64_t)(kc + k) * ldp] : T(0);
-          sj[k * (kTile + 1) + i] = (gj < c1 && k < kk) ? P[gj + (int64_t)(kc + k) * ldp] : T(0);
-        }
-        __syncthreads();
-        for (int k = 0; k < kk; ++k) {
-          T av[4], bv[4];
+        for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
+    }
+    __syncthreads();
+  }
 #pragma unroll
-          for (int a = 0; a < 4; ++a) av[a] = si[k * (kTile + 1) + ty + 16 * a];
+  for (int a = 0; a < 4; ++a) {
+    const int i = ti + ty + 16 * a;
 #pragma unroll
-          for (int b = 0; b < 4; ++b) bv[b] = sj[k * (kTile + 1) + tx + 16 * b];
-#pragma unroll
-          for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
-        }
-        __syncthreads();
-      }
-#pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        const int i = ti + ty + 16 * a;
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          const int j = tj + tx + 16 * b;
-          if (i < r1 && j < c1 && i >= j) C[i + (int64_t)j * ldc] -= acc[a][b];
-        }
-      }
+    for (int b = 0; b < 4; ++b) {
+      const int j = tj + tx + 16 * b;
+      if (i < r1 && j < c1 && i >= j) C[i + (int64_t)j * ldc] -= acc[a][b];
+    }
+  }
+}
+
+// C[i,j] -= sum_{k in [k0,k1)} P[i,k] * P[j,k] for i in [r0,r1), j in [c0,c1), i >= j,
+// tile by tile with the whole CTA.
+template <typename T>
+__device__ void cta_syrk_lower(T* C, int64_t ldc, const T* P, int64_t ldp, int r0, int r1, int c0,
+                               int c1, int k0, int k1, T* sm) {
+  if (r0 >= r1 || c0 >= c1 || k0 >= k1) return;
+  for (int ti = r0; ti < r1; ti += kTile) {
+    for (int tj = c0; tj < c1; tj += kTile) {
+      if (tj > ti + kTile - 1) break;   // tile entirely above the diagonal
+      cta_syrk_tile(C, ldc, P, ldp, ti, tj, r1, c1, k0, k1, sm);
     }
   }
 }
 
 // Shared memory (elements of T) needed by cta_partial_chol.
 constexpr int partial_chol_smem_elems() { return kNB * (kNB + 1) + 2 * kKC * (kTile + 1); }
+
+// One panel of the blocked Cholesky: factor the nb x nb diagonal block at p0
+// (warp 0) and scale the rows below it, rows (p0+nb .. n) <- rows * D^{-T}.
+// Returns false if a pivot is not positive.  D is shared scratch of
+// kNB*(kNB+1) elements.
+template <typename T>
+__device__ bool cta_panel(T* A, int64_t ld, int n, int p0, int nb, T* D) {
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int p1 = p0 + nb;
+  for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
+    const int i = idx % nb, j = idx / nb;
+    D[i * (kNB + 1) + j] = (i >= j) ? A[(p0 + i) + (int64_t)(p0 + j) * ld] : T(0);
+  }
+  __syncthreads();
+  if (warp == 0) {
+    for (int k = 0; k < nb; ++k) {
+      T dkk = D[k * (kNB + 1) + k];
+      if (!(dkk > T(0))) {
+        if (lane == 0) bad = 1;
+        dkk = T(1);
+      }
+      const T s = my_sqrt(dkk);
+      __syncwarp();
+      if (lane > k && lane < nb) D[lane * (kNB + 1) + k] /= s;
+      if (lane == k) D[k * (kNB + 1) + k] = s;
+      __syncwarp();
+      if (lane > k && lane < nb) {
+        const T lik = D[lane * (kNB + 1) + k];
+        for (int j = k + 1; j <= lane; ++j) D[lane * (kNB + 1) + j] -= lik * D[j * (kNB + 1) + k];
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
+    const int i = idx % nb, j = idx / nb;
+    if (i >= j) A[(p0 + i) + (int64_t)(p0 + j) * ld] = D[i * (kNB + 1) + j];
+  }
+  for (int i = p1 + threadIdx.x; i < n; i += blockDim.x) {
+    T r[kNB];
+#pragma unroll
+    for (int j = 0; j < kNB; ++j) r[j] = (j < nb) ? A[i + (int64_t)(p0 + j) * ld] : T(0);
+#pragma unroll
+    for (int j = 0; j < kNB; ++j) {
+      if (j < nb) {
+        T s = r[j];
+#pragma unroll
+        for (int q = 0; q < j; ++q) s -= r[q] * D[j * (kNB + 1) + q];
+        r[j] = s / D[j * (kNB + 1) + j];
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kNB; ++j)
+      if (j < nb) A[i + (int64_t)(p0 + j) * ld] = r[j];
+  }
+  __syncthreads();
+  return bad == 0;
+}
 
 // Blocked partial Cholesky of the n x n SPD front A (lower triangle, ld):
 // eliminates the first nI unknowns (Sec. 2.1, Eq. 2.1).  On return
@@ -158,63 +227,13 @@ constexpr int partial_chol_smem_elems() { return kNB * (kNB + 1) + 2 * kKC * (kT
 // Returns false (and leaves garbage) if a pivot is not positive.
 template <typename T>
 __device__ bool cta_partial_chol(T* A, int64_t ld, int n, int nI, T* sm) {
-  __shared__ int bad;
-  if (threadIdx.x == 0) bad = 0;
   T* D = sm;                                   // [kNB][kNB+1] row-major
   T* syrk_sm = sm + kNB * (kNB + 1);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  __syncthreads();
+  bool ok = true;
   for (int p0 = 0; p0 < nI; p0 += kNB) {
     const int nb = min(kNB, nI - p0);
     const int p1 = p0 + nb;
-    for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
-      const int i = idx % nb, j = idx / nb;
-      D[i * (kNB + 1) + j] = (i >= j) ? A[(p0 + i) + (int64_t)(p0 + j) * ld] : T(0);
-    }
-    __syncthreads();
-    if (warp == 0) {
-      for (int k = 0; k < nb; ++k) {
-        T dkk = D[k * (kNB + 1) + k];
-        if (!(dkk > T(0))) {
-          if (lane == 0) bad = 1;
-          dkk = T(1);
-        }
-        const T s = my_sqrt(dkk);
-        __syncwarp();
-        if (lane > k && lane < nb) D[lane * (kNB + 1) + k] /= s;
-        if (lane == k) D[k * (kNB + 1) + k] = s;
-        __syncwarp();
-        if (lane > k && lane < nb) {
-          const T lik = D[lane * (kNB + 1) + k];
-          for (int j = k + 1; j <= lane; ++j) D[lane * (kNB + 1) + j] -= lik * D[j * (kNB + 1) + k];
-        }
-        __syncwarp();
-      }
-    }
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
-      const int i = idx % nb, j = idx / nb;
-      if (i >= j) A[(p0 + i) + (int64_t)(p0 + j) * ld] = D[i * (kNB + 1) + j];
-    }
-    // panel rows below the diagonal block: row <- row * D^{-T}
-    for (int i = p1 + threadIdx.x; i < n; i += blockDim.x) {
-      T r[kNB];
-#pragma unroll
-      for (int j = 0; j < kNB; ++j) r[j] = (j < nb) ? A[i + (int64_t)(p0 + j) * ld] : T(0);
-#pragma unroll
-      for (int j = 0; j < kNB; ++j) {
-        if (j < nb) {
-          T s = r[j];
-#pragma unroll
-          for (int q = 0; q < j; ++q) s -= r[q] * D[j * (kNB + 1) + q];
-          r[j] = s / D[j * (kNB + 1) + j];
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < kNB; ++j)
-        if (j < nb) A[i + (int64_t)(p0 + j) * ld] = r[j];
-    }
-    __syncthreads();
+    ok &= cta_panel(A, ld, n, p0, nb, D);
     // trailing update restricted to the columns still to be eliminated
     cta_syrk_lower(A, ld, A, ld, p1, n, p1, nI, p0, p1, syrk_sm);
     __syncthreads();
@@ -222,7 +241,7 @@ __device__ bool cta_partial_chol(T* A, int64_t ld, int n, int nI, T* sm) {
   // Schur complement of the boundary block in one pass over k = 0..nI
   cta_syrk_lower(A, ld, A, ld, nI, n, nI, n, 0, nI, syrk_sm);
   __syncthreads();
-  return bad == 0;
+  return ok;
 }
 
 // y <- L^{-1} y for the n x n lower-triangular L (ld), y in shared memory.

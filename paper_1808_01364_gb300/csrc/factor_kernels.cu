@@ -548,6 +548,78 @@ __global__ void __launch_bounds__(kThreads) k_partial_chol(LevelDev Lv, int* sta
 }
 
 // ---------------------------------------------------------------------------
+// cell elimination of large fronts, spread over many CTAs: one launch per
+// 32-column panel factors the diagonal block and scales the panel (one CTA per
+// front), the next updates the trailing columns still to be eliminated tile by
+// tile (one CTA per 64 x 64 tile of every front), and a final launch forms the
+// Schur complement of the boundary block, C_BB -= W W^T, tile by tile.
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_front_panel(LevelDev Lv, int p0, int* status) {
+  extern __shared__ unsigned char smraw[];
+  const int c = blockIdx.x;
+  const int nI = Lv.nI[c], n = nI + Lv.nB[c];
+  if (p0 >= nI) return;
+  T* F = (T*)Lv.front + Lv.front_off[c];
+  const int nb = min(kNB, nI - p0);
+  if (!cta_panel(F, n, n, p0, nb, (T*)smraw) && threadIdx.x == 0)
+    report(status, RHIF_ERR_NOT_SPD, Lv.level, kKindCell, c);
+}
+
+__host__ __device__ inline int64_t trail_tiles(int nI, int n, int p0) {
+  if (p0 >= nI) return 0;
+  const int p1 = min(p0 + kNB, nI);
+  const int64_t tr = (n - p1 + kTile - 1) / kTile, tc = (nI - p1 + kTile - 1) / kTile;
+  return tr * tc;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_front_trailing(LevelDev Lv, int p0) {
+  extern __shared__ unsigned char smraw[];
+  int64_t bid = blockIdx.x;
+  int c = 0;
+  for (; c < Lv.ncell; ++c) {
+    const int64_t t = trail_tiles(Lv.nI[c], Lv.nI[c] + Lv.nB[c], p0);
+    if (bid < t) break;
+    bid -= t;
+  }
+  if (c >= Lv.ncell) return;
+  const int nI = Lv.nI[c], n = nI + Lv.nB[c];
+  const int p1 = min(p0 + kNB, nI);
+  const int tc = (nI - p1 + kTile - 1) / kTile;
+  const int a = (int)(bid / tc), b = (int)(bid % tc);
+  if (b > a) return;   // above the diagonal
+  T* F = (T*)Lv.front + Lv.front_off[c];
+  cta_syrk_tile(F, n, F, n, p1 + a * kTile, p1 + b * kTile, n, nI, p0, p1, (T*)smraw);
+}
+
+__host__ __device__ inline int64_t schur_tiles(int nI, int nB) {
+  if (nI == 0 || nB == 0) return 0;
+  const int64_t t = (nB + kTile - 1) / kTile;
+  return t * t;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_front_schur(LevelDev Lv) {
+  extern __shared__ unsigned char smraw[];
+  int64_t bid = blockIdx.x;
+  int c = 0;
+  for (; c < Lv.ncell; ++c) {
+    const int64_t t = schur_tiles(Lv.nI[c], Lv.nB[c]);
+    if (bid < t) break;
+    bid -= t;
+  }
+  if (c >= Lv.ncell) return;
+  const int nI = Lv.nI[c], nB = Lv.nB[c], n = nI + nB;
+  const int t = (nB + kTile - 1) / kTile;
+  const int a = (int)(bid / t), b = (int)(bid % t);
+  if (b > a) return;
+  T* F = (T*)Lv.front + Lv.front_off[c];
+  cta_syrk_tile(F, n, F, n, nI + a * kTile, nI + b * kTile, n, n, 0, nI, (T*)smraw);
+}
+
+// ---------------------------------------------------------------------------
 // block Jacobi preconditioning (Sec. 2.3)
 // ---------------------------------------------------------------------------
 
@@ -643,6 +715,111 @@ __global__ void __launch_bounds__(kThreads) k_precond_scale(LevelDev Lv, PhaseDe
       const int i = (int)(idx % nb), j = (int)(idx / nb);
       Fg[i + (int64_t)j * gld] = Fr[idx];
     }
+  }
+}
+
+// Large frames: D^{-1} F D^{-T} spread over many CTAs.  The frame is first
+// made symmetric; then one CTA per (cell, preconditioned segment g, chunk of
+// `cw` columns) applies L_g^{-1} to the rows of g, and one CTA per (cell,
+// segment h, chunk of rows) applies L_h^{-T} to the columns of h.  Each CTA
+// stages its |g| x cw block in shared memory, one column (row) per thread.
+
+template <typename T>
+__global__ void k_frame_symmetrize(LevelDev Lv) {
+  for (int c = blockIdx.y; c < Lv.ncell; c += gridDim.y) {
+    int ld;
+    T* Fr = frame_of<T>(Lv, c, &ld);
+    const int nb = Lv.nB[c];
+    const int64_t total = (int64_t)nb * nb;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+      const int i = (int)(idx % nb), j = (int)(idx / nb);
+      if (i < j) Fr[i + (int64_t)j * ld] = Fr[j + (int64_t)i * ld];
+    }
+  }
+}
+
+// Locate task `bid` among (cell, preconditioned segment, chunk) triples.
+__device__ inline bool frame_task(const LevelDev& Lv, const PhaseDev& Ph, int64_t bid, int cw,
+                                  int* cell, int* seg, int* chunk) {
+  for (int c = 0; c < Lv.ncell; ++c) {
+    const int nb = Lv.nB[c];
+    const int nch = (nb + cw - 1) / cw;
+    for (int q = Lv.seg_off[c]; q < Lv.seg_off[c + 1]; ++q) {
+      if (Ph.group_pre[Lv.seg_group[q]] < 0) continue;
+      if (bid < nch) {
+        *cell = c;
+        *seg = q;
+        *chunk = (int)bid;
+        return true;
+      }
+      bid -= nch;
+    }
+  }
+  return false;
+}
+
+template <typename T>
+__global__ void k_frame_rows(LevelDev Lv, PhaseDev Ph, int cw) {
+  extern __shared__ unsigned char smraw[];
+  T* blk = (T*)smraw;   // blk[a * cw + t]
+  int c, q, ch;
+  if (!frame_task(Lv, Ph, blockIdx.x, cw, &c, &q, &ch)) return;
+  int ld;
+  T* Fr = frame_of<T>(Lv, c, &ld);
+  const int nb = Lv.nB[c];
+  const int g = Lv.seg_group[q], pos = Lv.seg_pos[q], sz = Lv.group_size[g];
+  const T* Lg = (const T*)Ph.Lbuf + Ph.pre_off[Ph.group_pre[g]];
+  const int j0 = ch * cw;
+  const int ncol = min(cw, nb - j0);
+  for (int idx = threadIdx.x; idx < sz * cw; idx += blockDim.x) {
+    const int a = idx / cw, t = idx % cw;
+    blk[idx] = t < ncol ? Fr[(pos + a) + (int64_t)(j0 + t) * ld] : T(0);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < ncol; t += blockDim.x) {
+    for (int a = 0; a < sz; ++a) {
+      T v = blk[a * cw + t];
+      for (int k = 0; k < a; ++k) v -= Lg[a + (int64_t)k * sz] * blk[k * cw + t];
+      blk[a * cw + t] = v / Lg[a + (int64_t)a * sz];
+    }
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < sz * cw; idx += blockDim.x) {
+    const int a = idx / cw, t = idx % cw;
+    if (t < ncol) Fr[(pos + a) + (int64_t)(j0 + t) * ld] = blk[idx];
+  }
+}
+
+template <typename T>
+__global__ void k_frame_cols(LevelDev Lv, PhaseDev Ph, int cw) {
+  extern __shared__ unsigned char smraw[];
+  T* blk = (T*)smraw;   // blk[a * cw + t]: column pos+a, row i0+t
+  int c, q, ch;
+  if (!frame_task(Lv, Ph, blockIdx.x, cw, &c, &q, &ch)) return;
+  int ld;
+  T* Fr = frame_of<T>(Lv, c, &ld);
+  const int nb = Lv.nB[c];
+  const int g = Lv.seg_group[q], pos = Lv.seg_pos[q], sz = Lv.group_size[g];
+  const T* Lg = (const T*)Ph.Lbuf + Ph.pre_off[Ph.group_pre[g]];
+  const int i0 = ch * cw;
+  const int nrow = min(cw, nb - i0);
+  for (int idx = threadIdx.x; idx < sz * cw; idx += blockDim.x) {
+    const int a = idx / cw, t = idx % cw;
+    blk[idx] = t < nrow ? Fr[(i0 + t) + (int64_t)(pos + a) * ld] : T(0);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < nrow; t += blockDim.x) {
+    for (int a = 0; a < sz; ++a) {
+      T v = blk[a * cw + t];
+      for (int k = 0; k < a; ++k) v -= Lg[a + (int64_t)k * sz] * blk[k * cw + t];
+      blk[a * cw + t] = v / Lg[a + (int64_t)a * sz];
+    }
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < sz * cw; idx += blockDim.x) {
+    const int a = idx / cw, t = idx % cw;
+    if (t < nrow) Fr[(i0 + t) + (int64_t)(pos + a) * ld] = blk[idx];
   }
 }
 
@@ -925,6 +1102,26 @@ void launch_partial_chol(const LevelDev& Lv, int* status, cudaStream_t s) {
 }
 
 template <typename T>
+void launch_front_panel(const LevelDev& Lv, int p0, int* status, cudaStream_t s) {
+  k_front_panel<T><<<Lv.ncell, kThreads, kNB * (kNB + 1) * sizeof(T), s>>>(Lv, p0, status);
+}
+
+template <typename T>
+void launch_front_trailing(const LevelDev& Lv, int p0, int64_t tiles, cudaStream_t s) {
+  if (tiles > 0)
+    k_front_trailing<T><<<(unsigned)tiles, kThreads, 2 * kKC * (kTile + 1) * sizeof(T), s>>>(Lv, p0);
+}
+
+template <typename T>
+void launch_front_schur(const LevelDev& Lv, int64_t tiles, cudaStream_t s) {
+  if (tiles > 0)
+    k_front_schur<T><<<(unsigned)tiles, kThreads, 2 * kKC * (kTile + 1) * sizeof(T), s>>>(Lv);
+}
+
+int64_t front_trailing_tiles(int nI, int n, int p0) { return trail_tiles(nI, n, p0); }
+int64_t front_schur_tiles(int nI, int nB) { return schur_tiles(nI, nB); }
+
+template <typename T>
 void launch_precond_diag(const LevelDev& Lv, const PhaseDev& Ph, int* status, cudaStream_t s) {
   if (Ph.npre)
     k_precond_diag<T><<<Ph.npre, kThreads, partial_chol_smem_elems() * sizeof(T), s>>>(Lv, Ph, status);
@@ -934,8 +1131,28 @@ template <typename T>
 void launch_precond_scale(const LevelDev& Lv, const PhaseDev& Ph, cudaStream_t s) {
   if (!(Ph.npre && Lv.ncell)) return;
   const size_t blk = (size_t)Lv.max_nB * Lv.max_nB * sizeof(T);
-  const int stage = blk <= 200 * 1024;
-  k_precond_scale<T><<<Lv.ncell, kThreads, stage ? blk : 0, s>>>(Lv, Ph, stage);
+  if (blk <= 200 * 1024) {
+    k_precond_scale<T><<<Lv.ncell, kThreads, blk, s>>>(Lv, Ph, 1);
+  } else {
+    k_precond_scale<T><<<Lv.ncell, kThreads, 0, s>>>(Lv, Ph, 0);
+  }
+}
+
+template <typename T>
+int frame_chunk_width(int max_group) {
+  int cw = (int)((160 * 1024) / ((size_t)(max_group > 0 ? max_group : 1) * sizeof(T)));
+  cw = cw / 32 * 32;
+  return cw < 32 ? 32 : (cw > 64 ? 64 : cw);
+}
+
+template <typename T>
+void launch_precond_scale_big(const LevelDev& Lv, const PhaseDev& Ph, int64_t tasks, int cw,
+                              cudaStream_t s) {
+  k_frame_symmetrize<T><<<dim3(64, min(Lv.ncell, 65535)), 256, 0, s>>>(Lv);
+  if (tasks <= 0) return;
+  const size_t sm = (size_t)Lv.max_group * cw * sizeof(T);
+  k_frame_rows<T><<<(unsigned)tasks, cw, sm, s>>>(Lv, Ph, cw);
+  k_frame_cols<T><<<(unsigned)tasks, cw, sm, s>>>(Lv, Ph, cw);
 }
 
 template <typename T>
@@ -965,6 +1182,10 @@ int configure_factor_kernels() {
     e = cudaFuncSetAttribute(k_precond_scale<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_leaf_stream<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_frame_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_frame_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   return e == cudaSuccess ? 0 : -1;
 }
 
@@ -974,8 +1195,14 @@ int configure_factor_kernels() {
                                     int*, cudaStream_t);                                          \
   template void launch_extend_add<T>(const LevelDev&, const LevelDev&, cudaStream_t);             \
   template void launch_partial_chol<T>(const LevelDev&, int*, cudaStream_t);                      \
+  template void launch_front_panel<T>(const LevelDev&, int, int*, cudaStream_t);                  \
+  template void launch_front_trailing<T>(const LevelDev&, int, int64_t, cudaStream_t);            \
+  template void launch_front_schur<T>(const LevelDev&, int64_t, cudaStream_t);                    \
   template void launch_precond_diag<T>(const LevelDev&, const PhaseDev&, int*, cudaStream_t);     \
   template void launch_precond_scale<T>(const LevelDev&, const PhaseDev&, cudaStream_t);          \
+  template void launch_precond_scale_big<T>(const LevelDev&, const PhaseDev&, int64_t, int,       \
+                                            cudaStream_t);                                        \
+  template int frame_chunk_width<T>(int);                                                         \
   template void launch_skel<T>(const LevelDev&, const PhaseDev&, uint8_t*, double, int*, int64_t, \
                                cudaStream_t);                                                     \
   template size_t skel_smem_bytes<T>(int);                                                        \

@@ -24,9 +24,22 @@ void launch_extend_add(const LevelDev& cur, const LevelDev& prev, cudaStream_t s
 template <typename T>
 void launch_partial_chol(const LevelDev& Lv, int* status, cudaStream_t s);
 template <typename T>
+void launch_front_panel(const LevelDev& Lv, int p0, int* status, cudaStream_t s);
+template <typename T>
+void launch_front_trailing(const LevelDev& Lv, int p0, int64_t tiles, cudaStream_t s);
+template <typename T>
+void launch_front_schur(const LevelDev& Lv, int64_t tiles, cudaStream_t s);
+int64_t front_trailing_tiles(int nI, int n, int p0);
+int64_t front_schur_tiles(int nI, int nB);
+template <typename T>
 void launch_precond_diag(const LevelDev& Lv, const PhaseDev& Ph, int* status, cudaStream_t s);
 template <typename T>
 void launch_precond_scale(const LevelDev& Lv, const PhaseDev& Ph, cudaStream_t s);
+template <typename T>
+void launch_precond_scale_big(const LevelDev& Lv, const PhaseDev& Ph, int64_t tasks, int cw,
+                              cudaStream_t s);
+template <typename T>
+int frame_chunk_width(int max_group);
 template <typename T>
 void launch_skel(const LevelDev& Lv, const PhaseDev& Ph, uint8_t* alive, double tol, int* status,
                  int64_t max_m_elems, cudaStream_t s);

@@ -12,6 +12,7 @@
 #include <cstdlib>
 #include <cmath>
 #include <cstdio>
+#include <climits>
 #include <cstring>
 #include <memory>
 #include <mutex>
@@ -149,6 +150,16 @@ struct Launch {
   }
 };
 
+// Fronts at least this large, at levels with at most this many cells, are
+// eliminated by many CTAs per front.
+constexpr int kBigFront = 384;
+constexpr int kBigFrontCells = 304;
+
+static void add_launches(int cat, int64_t n) {
+  std::lock_guard<std::mutex> lk(g_kmu);
+  g_kstat[cat].launches += n;
+}
+
 static void add_work(int cat, double flops, double bytes) {
   std::lock_guard<std::mutex> lk(g_kmu);
   g_kstat[cat].flops += flops;
@@ -177,6 +188,7 @@ struct rhif_handle {
   rhif::GeoDev gd{};
   int precision = RHIF_FP64;
   bool precondition = true, edge_skel = false;
+  int big_front = 0, big_frame = 0;   // many-CTA thresholds (see rhif_opts)
   double tol = 0.0;
   std::vector<rhif::LevelStore> levels;   // 0..L
   double* diag = nullptr;
@@ -429,8 +441,25 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
         Launch t(kCatExtendAdd, s, 0.0, double(P.front_total) * elem);
         launch_extend_add<T>(S.dev, H->levels[lvl - 1].dev, s);
       }
-      Launch t(kCatPartialChol, s, lvl_flops, double(P.front_total) * elem);
-      launch_partial_chol<T>(S.dev, H->status, s);
+      if (P.max_n >= H->big_front && P.ncell() <= kBigFrontCells) {
+        // few large fronts: panel / trailing-tile / Schur-tile launches over all fronts
+        Launch t(kCatPartialChol, s, lvl_flops, double(P.front_total) * elem, 0);
+        for (int p0 = 0; p0 < P.max_nI; p0 += 32) {
+          int64_t tiles = 0;
+          for (int c = 0; c < P.ncell(); ++c)
+            tiles += front_trailing_tiles(P.nI[c], P.nI[c] + P.nB[c], p0);
+          launch_front_panel<T>(S.dev, p0, H->status, s);
+          launch_front_trailing<T>(S.dev, p0, tiles, s);
+          add_launches(kCatPartialChol, tiles > 0 ? 2 : 1);
+        }
+        int64_t tiles = 0;
+        for (int c = 0; c < P.ncell(); ++c) tiles += front_schur_tiles(P.nI[c], P.nB[c]);
+        launch_front_schur<T>(S.dev, tiles, s);
+        add_launches(kCatPartialChol, tiles > 0 ? 1 : 0);
+      } else {
+        Launch t(kCatPartialChol, s, lvl_flops, double(P.front_total) * elem);
+        launch_partial_chol<T>(S.dev, H->status, s);
+      }
     }
     H->flops += lvl_flops;
     for (size_t ip = 0; ip < P.phases.size(); ++ip) {
@@ -458,7 +487,19 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
         }
         {
           Launch t(kCatPrecondScale, s, sflops, 0.0);
-          launch_precond_scale<T>(S.dev, D, s);
+          const int cw = frame_chunk_width<T>(P.max_group);
+          const bool fits = (size_t)P.max_nB * P.max_nB * elem <= 200 * 1024;
+          const bool big = H->big_frame > 0 ? P.max_nB >= H->big_frame : !fits;
+          if (!big || (size_t)P.max_group * cw * elem > 200 * 1024) {
+            launch_precond_scale<T>(S.dev, D, s);
+          } else {   // large frames: row / column block solves over many CTAs
+            int64_t tasks = 0;
+            for (int c = 0; c < P.ncell(); ++c)
+              for (int q = P.seg_off[c]; q < P.seg_off[c + 1]; ++q)
+                if (ph.group_pre[P.seg_group[q]] >= 0) tasks += (P.nB[c] + cw - 1) / cw;
+            launch_precond_scale_big<T>(S.dev, D, tasks, cw, s);
+            add_launches(kCatPrecondScale, tasks > 0 ? 2 : 0);
+          }
         }
       }
       const int64_t nunit = (int64_t)ph.units.group.size();
@@ -499,8 +540,9 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
     }
     if ((rc = check_status(H, lvl == G.L ? "root factorization" : "cell elimination"))) return rc;
     if (trace)
-      std::fprintf(stderr, "[rhif] level %d: cells %d groups %d active %zu plan %.2f ms upload %.2f ms gpu+sync %.2f ms\n",
-                   lvl, P.ncell(), P.ngroup(), P.bucket.size(), t_plan, t_up, ms_since(t2));
+      std::fprintf(stderr, "[rhif] level %d: cells %d groups %d active %zu max_n %d max_nB %d max_group %d plan %.2f ms upload %.2f ms gpu+sync %.2f ms\n",
+                   lvl, P.ncell(), P.ngroup(), P.bucket.size(), P.max_n, P.max_nB, P.max_group,
+                   t_plan, t_up, ms_since(t2));
     if (lvl == 0 && S.dev.zbuf) {
       H->mem.release(S.dev.zbuf);
       S.dev.zbuf = nullptr;
@@ -730,6 +772,8 @@ int rhif_factor(const rhif_csr* A, const rhif_grid* g, int leaf, double tol, con
   H->precision = o->precision;
   H->precondition = o->precondition != 0;
   H->edge_skel = (g->dim == 3) && o->edge_skel_3d;
+  H->big_front = o->big_front == 0 ? kBigFront : (o->big_front < 0 ? INT_MAX : o->big_front);
+  H->big_frame = o->big_frame < 0 ? INT_MAX : o->big_frame;
   H->tol = tol;
   H->mem.s = (cudaStream_t)stream;
   cudaEvent_t e0, e1;

@@ -1,0 +1,91 @@
+"""GPU tests of the many-CTA schedules for large fronts and frames.
+
+A level whose fronts are large is eliminated by panel / trailing-tile / Schur-
+tile launches spread over many CTAs, and its block Jacobi scaling (Eq. 2.3) by
+row and column block solves; small levels use one CTA per front.  The
+thresholds are options, so these tests force the many-CTA schedules on grids
+the oracle factors in seconds and hold them to the same FP64 bar as the
+one-CTA schedule: identical skeletons (except at logged near-ties) and
+F^{-1} x within 1e-9 relative of the oracle's.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import fd, phif
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+
+
+CASES = [
+    # ns, leaf, tol, b, edge
+    ((63, 63), 8, 1e-6, 0.0, False),
+    ((15, 15, 15), 4, 1e-3, 1e-2, False),
+    ((11, 9, 13), 4, 1e-3, 1e-2, False),
+    ((15, 15, 15), 4, 1e-3, 1e-2, True),
+    ((31, 31, 31), 8, 1e-3, 1e-2, True),
+]
+
+
+@pytest.mark.parametrize("ns,leaf,tol,b,edge", CASES)
+def test_many_cta_schedules_match_oracle(gpu_lib, ns, leaf, tol, b, edge):
+    a = W.log_uniform_pixels(ns, 1e-3, 1e3, seed=sum(ns) + leaf)
+    A = fd.assemble(ns, a, b)
+    Fo = phif.factor(A, ns, leaf, tol, edge_skel=edge)
+    csr = gpu_lib.rhif_assemble_fd(ns, _dev(a), b)
+    gpu_lib.rhif_reset_kernel_stats()
+    Fg = gpu_lib.rhif_factor(csr, ns, leaf, tol, precision="fp64", edge_skel_3d=edge,
+                             big_front=1, big_frame=1)
+    ks = gpu_lib.rhif_kernel_stats()
+    levels = Fg.stats()["levels"]
+    # panel + trailing launches per 32 interior columns: more than one launch per level
+    assert ks["partial_chol"]["launches"] > levels - 1
+    # symmetrize + row solves + column solves on every preconditioned phase
+    assert ks["precond_scale"]["launches"] >= 3 * ks["precond_diag"]["launches"]
+    same = True
+    for lvl in range(len(Fo.levels)):
+        for p in range(len(Fo.levels[lvl].phases)):
+            go = {frozenset(map(int, u.e)): frozenset(map(int, u.sk))
+                  for u in Fo.levels[lvl].phases[p].units}
+            gg = {frozenset(map(int, d)): frozenset(map(int, d[:k])) for d, k in Fg.skeletons(lvl, p)}
+            assert set(go) == set(gg)
+            same &= go == gg
+    assert same or Fo.ties
+    x = np.random.default_rng(11).standard_normal(A.shape[0])
+    yg = Fg.apply(_dev(x)).cpu().numpy()
+    if same:
+        yo = phif.solve(Fo, x)
+        assert np.linalg.norm(yg - yo) <= 1e-9 * np.linalg.norm(yo)
+    Fg.free()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_many_cta_schedules_agree_with_one_cta_schedule(gpu_lib, precision):
+    """Same grid factored with the many-CTA schedules forced on and off: same
+    skeletons, F^{-1} x equal to rounding, PCG converges to the same solution."""
+    ns, leaf = (31, 31, 31), 8
+    a = W.log_uniform_pixels(ns, 1e-4, 1e4, seed=21)
+    csr = gpu_lib.rhif_assemble_fd(ns, _dev(a), 0.0)
+    f = _dev(W.normal_rhs(ns, 22))
+    on = gpu_lib.rhif_factor(csr, ns, leaf, 1e-3, precision=precision, big_front=1, big_frame=1)
+    off = gpu_lib.rhif_factor(csr, ns, leaf, 1e-3, precision=precision, big_front=-1, big_frame=-1)
+    lv = on.stats()["levels"]
+    sk_on = [on.skeletons(l, p) for l in range(lv) for p in range(1)]
+    sk_off = [off.skeletons(l, p) for l in range(lv) for p in range(1)]
+    eps = 1e-12 if precision == "fp64" else 1e-4
+    if sk_on == sk_off:
+        y1 = on.apply(f)
+        y0 = off.apply(f)
+        assert float(torch.linalg.norm(y1 - y0) / torch.linalg.norm(y0)) <= eps
+    u1, _, r1 = on.pcg(f, rtol=1e-10)
+    u0, _, r0 = off.pcg(f, rtol=1e-10)
+    assert r1[0] <= 1.5e-10 and r0[0] <= 1.5e-10
+    assert float(torch.linalg.norm(u1 - u0) / torch.linalg.norm(u0)) <= 1e-8
+    on.free()
+    off.free()

@@ -75,7 +75,13 @@ typedef struct {
    *   memory), < 0 = never. */
   int big_front;
   int big_frame;
-  int reserved[3];
+  /* skel_cluster: CTAs (a thread-block cluster, power of two <= 16) that share
+   *   the interpolative decomposition of one skeletonization unit, each holding
+   *   a slice of the unit's rows.  0 = library default (clusters only for units
+   *   whose ID matrix does not fit in one CTA's shared memory), < 0 = never,
+   *   1..16 = always, with that cluster size. */
+  int skel_cluster;
+  int reserved[2];
 } rhif_opts;
 
 typedef struct rhif_handle rhif_handle;

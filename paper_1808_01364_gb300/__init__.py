@@ -48,7 +48,8 @@ class CSR(ctypes.Structure):
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("precondition", ctypes.c_int),
                 ("edge_skel_3d", ctypes.c_int), ("big_front", ctypes.c_int),
-                ("big_frame", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("big_frame", ctypes.c_int), ("skel_cluster", ctypes.c_int),
+                ("reserved", ctypes.c_int * 2)]
 
 
 class Stats(ctypes.Structure):
@@ -271,14 +272,16 @@ class Factor:
 
 
 def rhif_factor(csr, ns, leaf: int, tol: float, precision: str = "fp64", precondition=True,
-                edge_skel_3d=False, stream=None, big_front=0, big_frame=0) -> Factor:
+                edge_skel_3d=False, stream=None, big_front=0, big_frame=0,
+                skel_cluster=0) -> Factor:
     """PHIF factorization of the CSR matrix ``csr = (rowptr, col, val)`` on grid ``ns``.
-    ``big_front`` / ``big_frame`` are the scheduling thresholds of ``rhif_opts``."""
+    ``big_front`` / ``big_frame`` / ``skel_cluster`` are the scheduling options of
+    ``rhif_opts``."""
     load()
     rowptr, col, val = csr
     N = rowptr.numel() - 1
     A = CSR(N, val.numel(), rowptr.data_ptr(), col.data_ptr(), val.data_ptr())
-    o = _opts(precision, precondition, edge_skel_3d, big_front, big_frame)
+    o = _opts(precision, precondition, edge_skel_3d, big_front, big_frame, skel_cluster)
     h = ctypes.c_void_p()
     _check(_lib.rhif_factor(ctypes.byref(A), ctypes.byref(_grid(ns)), int(leaf), float(tol),
                             ctypes.byref(o), _stream(stream), ctypes.byref(h)))
@@ -377,7 +380,7 @@ def rhif_solve(log_a: torch.Tensor, f: torch.Tensor, ns, **opts) -> torch.Tensor
 
 
 def _opts(precision="fp64", precondition=True, edge_skel_3d=False, big_front=0,
-          big_frame=0) -> Opts:
+          big_frame=0, skel_cluster=0) -> Opts:
     o = Opts()
     _lib.rhif_default_opts(ctypes.byref(o))
     o.precision = {"fp64": RHIF_FP64, "fp32": RHIF_MIXED_FP32, "mixed": RHIF_MIXED_FP32}[precision]
@@ -385,6 +388,7 @@ def _opts(precision="fp64", precondition=True, edge_skel_3d=False, big_front=0,
     o.edge_skel_3d = 1 if edge_skel_3d else 0
     o.big_front = int(big_front)
     o.big_frame = int(big_frame)
+    o.skel_cluster = int(skel_cluster)
     return o
 
 

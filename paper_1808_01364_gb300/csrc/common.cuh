@@ -156,6 +156,44 @@ __device__ void cta_syrk_lower(T* C, int64_t ldc, const T* P, int64_t ldp, int r
   }
 }
 
+// One 64 x 64 tile of a general product: acc[a][b] = sum_{k < K} fa(i, k) * fb(k, j)
+// for i = ti + ty + 16a < M, j = tj + tx + 16b < N (tx = tid % 16, ty = tid / 16);
+// fa / fb are element accessors, so operands may be gathered, transposed or
+// concatenated.  Needs 2 * kKC * (kTile + 1) elements of shared memory.
+template <typename T, class FA, class FB>
+__device__ void cta_tile_product(int ti, int tj, int M, int N, int K, FA fa, FB fb, T* sm,
+                                 T (&acc)[4][4]) {
+  T* sa = sm;
+  T* sb = sm + kKC * (kTile + 1);
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+  for (int kc = 0; kc < K; kc += kKC) {
+    const int kk = min(kKC, K - kc);
+    for (int idx = tid; idx < kTile * kKC; idx += kThreads) {
+      const int i = idx % kTile, k = idx / kTile;
+      sa[k * (kTile + 1) + i] = (ti + i < M && k < kk) ? fa(ti + i, kc + k) : T(0);
+      sb[k * (kTile + 1) + i] = (tj + i < N && k < kk) ? fb(kc + k, tj + i) : T(0);
+    }
+    __syncthreads();
+    for (int k = 0; k < kk; ++k) {
+      T av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = sa[k * (kTile + 1) + ty + 16 * a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) bv[b] = sb[k * (kTile + 1) + tx + 16 * b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
+    }
+    __syncthreads();
+  }
+}
+
 // Shared memory (elements of T) needed by cta_partial_chol.
 constexpr int partial_chol_smem_elems() { return kNB * (kNB + 1) + 2 * kKC * (kTile + 1); }
 

@@ -8,6 +8,8 @@
 // zeroing (the parallel order of Sec. 2.2), so each kernel is one launch over
 // all objects of the level.  Every cross-cell sum is a gather in a fixed cell
 // order (no atomics), so results are bitwise reproducible.
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "kernels.h"
 #include "tables.h"
@@ -829,78 +831,84 @@ __global__ void k_frame_cols(LevelDev Lv, PhaseDev Ph, int cw) {
 
 template <typename T> __device__ inline T my_abs(T x) { return x < T(0) ? -x : x; }
 
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_skel(LevelDev Lv, PhaseDev Ph, uint8_t* alive,
-                                                   double tol, int* status, int mstage) {
-  extern __shared__ unsigned char smraw[];
-  T* sm = (T*)smraw;                                   // partial-Cholesky workspace
-  T* nrm = sm + partial_chol_smem_elems();             // [max_n]
-  int* sperm = (int*)(nrm + Ph.max_n);                 // [max_n]
-  __shared__ int s_k, s_stop, s_p, s_nrg;
-  __shared__ T s_r11;
-  __shared__ int rg_group[kMaxRowGroupsDev], rg_row0[kMaxRowGroupsDev + 1];
-  __shared__ int rg_pos[kMaxRowGroupsDev][kMaxSlotsDev];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-  const int u = blockIdx.x;
-  const int g = Ph.u_group[u];
-  const int n = Lv.group_size[g];
-  const int nrow = Ph.u_nrow[u];
-  const int ldm = nrow > 0 ? nrow : 1;
-  T* M = (T*)Ph.Mbuf + Ph.u_m_off[u];
-  if (mstage) M = (T*)((unsigned char*)(sperm + Ph.max_n) + 16 - (((size_t)(sperm + Ph.max_n)) & 15));
-  T* Aee = M + (int64_t)nrow * n;
-  T* Fu = (T*)Ph.rec + Ph.u_rec_off[u];
-  T* Tm = Fu + pad4e((int64_t)n * n);
-  const int c0 = Lv.group_cell_off[g], c1 = Lv.group_cell_off[g + 1];
-  const int nslot = c1 - c0;
+// Row layout of A_{R,g} for unit group g: the other separator groups of the
+// holding cells, each group once (first appearance in holding-cell order),
+// with each group's position in every holding cell's frame.  Thread 0 builds
+// the tables; the caller synchronizes.
+struct SkelRows {
+  int nrg;
+  int group[kMaxRowGroupsDev];
+  int row0[kMaxRowGroupsDev + 1];
+  int pos[kMaxRowGroupsDev][kMaxSlotsDev];
+};
 
-  // 1. rows of A_{R,I}: the other separator groups of the holding cells, each
-  //    group once, summed over the holding cells in cell order
-  if (tid == 0) {
-    int nrg = 0, row = 0;
-    for (int s = 0; s < nslot; ++s) {
-      const int c = Lv.group_cell[c0 + s];
-      for (int q = Lv.seg_off[c]; q < Lv.seg_off[c + 1]; ++q) {
-        const int sg = Lv.seg_group[q];
-        if (sg == g) continue;
-        int f = -1;
-        for (int i = 0; i < nrg; ++i)
-          if (rg_group[i] == sg) f = i;
-        if (f < 0) {
-          if (nrg >= kMaxRowGroupsDev) continue;
-          f = nrg++;
-          rg_group[f] = sg;
-          rg_row0[f] = row;
-          row += Lv.group_size[sg];
-          for (int t = 0; t < kMaxSlotsDev; ++t) rg_pos[f][t] = -1;
-        }
-        rg_pos[f][s] = Lv.seg_pos[q];
+__device__ inline void skel_row_groups(const LevelDev& Lv, int g, int nrow, int* status,
+                                       SkelRows* R) {
+  if (threadIdx.x != 0) return;
+  const int c0 = Lv.group_cell_off[g], nslot = Lv.group_cell_off[g + 1] - c0;
+  int nrg = 0, row = 0;
+  for (int s = 0; s < nslot; ++s) {
+    const int c = Lv.group_cell[c0 + s];
+    for (int q = Lv.seg_off[c]; q < Lv.seg_off[c + 1]; ++q) {
+      const int sg = Lv.seg_group[q];
+      if (sg == g) continue;
+      int f = -1;
+      for (int i = 0; i < nrg; ++i)
+        if (R->group[i] == sg) f = i;
+      if (f < 0) {
+        if (nrg >= kMaxRowGroupsDev) continue;
+        f = nrg++;
+        R->group[f] = sg;
+        R->row0[f] = row;
+        row += Lv.group_size[sg];
+        for (int t = 0; t < kMaxSlotsDev; ++t) R->pos[f][t] = -1;
       }
+      R->pos[f][s] = Lv.seg_pos[q];
     }
-    rg_row0[nrg] = row;
-    s_nrg = nrg;
-    if (row != nrow) report(status, RHIF_ERR_BAD_ARG, Lv.level, kKindUnit, g);
   }
-  __syncthreads();
-  for (int f = 0; f < s_nrg; ++f) {
-    const int sg = rg_group[f], r0 = rg_row0[f], sz = Lv.group_size[sg];
+  R->row0[nrg] = row;
+  R->nrg = nrg;
+  if (row != nrow) report(status, RHIF_ERR_BAD_ARG, Lv.level, kKindUnit, g);
+}
+
+// Rows [ra, rb) of A_{R,g} (n columns), summed over the holding cells in cell
+// order; element (i, j) lands in D[(i - ra) * drs + j * dcs].  Dead DOFs give
+// zero rows.
+template <typename T>
+__device__ void skel_gather_rows(const LevelDev& Lv, const uint8_t* alive, int g, int n, int nrow,
+                                 const SkelRows& R, int ra, int rb, T* D, int64_t drs,
+                                 int64_t dcs) {
+  const int c0 = Lv.group_cell_off[g], nslot = Lv.group_cell_off[g + 1] - c0;
+  for (int f = 0; f < R.nrg; ++f) {
+    const int r0 = R.row0[f];
+    const int lo = max(r0, ra), hi = min(min(R.row0[f + 1], rb), nrow);
+    if (lo >= hi) continue;
+    const int sg = R.group[f];
     const int32_t* sgid = Lv.bucket + Lv.group_start[sg];
-    for (int idx = tid; idx < sz * n; idx += blockDim.x) {
-      const int o = idx % sz, j = idx / sz;
+    const int cnt = hi - lo;
+    for (int idx = threadIdx.x; idx < cnt * n; idx += blockDim.x) {
+      const int o = lo - r0 + idx % cnt, j = idx / cnt;
       T v = T(0);
       if (alive[sgid[o]]) {
         for (int s = 0; s < nslot; ++s) {
-          const int pos = rg_pos[f][s];
+          const int pos = R.pos[f][s];
           if (pos < 0) continue;
           int ld;
           const T* fr = frame_of<T>(Lv, Lv.group_cell[c0 + s], &ld);
           v += sym_at(fr, ld, pos + o, Lv.group_pos[c0 + s] + j);
         }
       }
-      if (r0 + o < nrow) M[(r0 + o) + (int64_t)j * ldm] = v;
+      D[(int64_t)(lo - ra + idx % cnt) * drs + (int64_t)j * dcs] = v;
     }
   }
-  for (int64_t idx = tid; idx < (int64_t)n * n; idx += blockDim.x) {
+}
+
+// A_gg summed over the holding cells; entries idx = first, first+step, ...
+template <typename T>
+__device__ void skel_gather_diag(const LevelDev& Lv, int g, int n, T* Aee, int64_t first,
+                                 int64_t step) {
+  const int c0 = Lv.group_cell_off[g], c1 = Lv.group_cell_off[g + 1];
+  for (int64_t idx = first; idx < (int64_t)n * n; idx += step) {
     const int i = (int)(idx % n), j = (int)(idx / n);
     T v = T(0);
     for (int k = c0; k < c1; ++k) {
@@ -911,6 +919,197 @@ __global__ void __launch_bounds__(kThreads) k_skel(LevelDev Lv, PhaseDev Ph, uin
     }
     Aee[idx] = v;
   }
+}
+
+// Pivot rule of the CPQR, taken by warp 0 from the column norms nrm[j..n):
+// stop once the largest remaining norm is <= tol * |R_11|; otherwise take the
+// column with the smallest original index among those within a relative
+// 1e-12 of the largest (ties broken by the original column order).
+template <typename T>
+__device__ void skel_pivot(const T* nrm, const int* sperm, int j, int n, double tol, T* s_r11,
+                           int* s_stop, int* s_p) {
+  if (threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
+  T mx = T(0);
+  for (int c = j + lane; c < n; c += 32) mx = nrm[c] > mx ? nrm[c] : mx;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    const T y = __shfl_xor_sync(0xffffffffu, mx, o);
+    mx = y > mx ? y : mx;
+  }
+  const T r11 = j == 0 ? my_sqrt(mx) : *s_r11;
+  const int stop = (r11 == T(0)) || (my_sqrt(mx) <= T(tol) * r11);
+  int best = -1, bo = 0x7fffffff;
+  if (!stop) {
+    const T thr = T(1.0 - 1e-12) * mx;
+    for (int c = j + lane; c < n; c += 32)
+      if (nrm[c] >= thr && sperm[c] < bo) {
+        bo = sperm[c];
+        best = c;
+      }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      const int ob = __shfl_xor_sync(0xffffffffu, bo, o);
+      const int oc = __shfl_xor_sync(0xffffffffu, best, o);
+      if (ob < bo) {
+        bo = ob;
+        best = oc;
+      }
+    }
+  }
+  if (lane == 0) {
+    if (j == 0) *s_r11 = r11;
+    *s_stop = stop;
+    *s_p = best;
+  }
+}
+
+// Steps after the CPQR of unit u (rank k, R(i, j) = M[i * mrs + j * mcs] for
+// i < k): T = R11^{-1} R12, the zeroing of Eq. (2.2) in (redundant, skeleton)
+// order
+//   [rd,rd] = A_rr - A_sr^T T - T^T [sk,rd],  [sk,rd] = A_sr - A_ss T,  [sk,sk] = A_ss,
+// elimination of the redundant DOFs (Sec. 2.1 on the zeroed block), and the
+// frame updates: the skeleton block of the first holding cell takes the new
+// value, the others drop theirs.  One CTA of kThreads threads.
+template <typename T>
+__device__ void skel_finish(const LevelDev& Lv, const PhaseDev& Ph, int u, int g, int n, int k,
+                            const T* M, int64_t mrs, int64_t mcs, const T* Aee, const int* sperm,
+                            T* sm, int* status) {
+  const int tid = threadIdx.x, r = n - k;
+  const int tx = tid & 15, ty = tid >> 4;
+  T* Fu = (T*)Ph.rec + Ph.u_rec_off[u];
+  T* Tm = Fu + pad4e((int64_t)n * n);
+  const int c0 = Lv.group_cell_off[g], c1 = Lv.group_cell_off[g + 1];
+  auto R = [&](int i, int j) { return M[(int64_t)i * mrs + (int64_t)j * mcs]; };
+
+  // interpolation matrix T = R11^{-1} R12 (k x r), by 64-row blocks from the
+  // bottom: T[I,:] = R_II^{-1} (R12[I,:] - R[I, J] T[J,:]) with J the rows below I
+  if (r > 0 && k > 0) {
+    for (int ib = ((k - 1) / kTile) * kTile; ib >= 0; ib -= kTile) {
+      const int ie = min(ib + kTile, k);
+      auto fa = [&](int i, int q) { return R(i, ie + q); };
+      auto fb = [&](int q, int a) { return Tm[(ie + q) + (int64_t)a * k]; };
+      for (int tj = 0; tj < r; tj += kTile) {
+        T acc[4][4];
+        cta_tile_product(ib, tj, ie, r, k - ie, fa, fb, sm, acc);
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const int i = ib + ty + 16 * a, c = tj + tx + 16 * b;
+            if (i < ie && c < r) Tm[i + (int64_t)c * k] = R(i, k + c) - acc[a][b];
+          }
+      }
+      T* Rb = sm;   // R_II, [kTile][kTile + 1]
+      const int nb = ie - ib;
+      for (int idx = tid; idx < nb * nb; idx += blockDim.x) {
+        const int i = idx / nb, q = idx % nb;
+        Rb[i * (kTile + 1) + q] = q >= i ? R(ib + i, ib + q) : T(0);
+      }
+      __syncthreads();
+      for (int a = tid; a < r; a += blockDim.x) {
+        T* col = Tm + (int64_t)a * k + ib;
+        for (int i = nb - 1; i >= 0; --i) {
+          T t = col[i];
+          for (int q = i + 1; q < nb; ++q) t -= Rb[i * (kTile + 1) + q] * col[q];
+          col[i] = t / Rb[i * (kTile + 1) + i];
+        }
+      }
+      __syncthreads();
+    }
+  }
+
+  // [sk,rd] = A_sr - A_ss T
+  auto a_ss = [&](int q, int p) { return Aee[sperm[q] + (int64_t)sperm[p] * n]; };
+  auto t_el = [&](int p, int a) { return Tm[p + (int64_t)a * k]; };
+  for (int ti = 0; ti < k; ti += kTile)
+    for (int tj = 0; tj < r; tj += kTile) {
+      T acc[4][4];
+      cta_tile_product(ti, tj, k, r, k, a_ss, t_el, sm, acc);
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int q = ti + ty + 16 * a, c = tj + tx + 16 * b;
+          if (q < k && c < r) Fu[(r + q) + (int64_t)c * n] = a_ss(q, k + c) - acc[a][b];
+        }
+    }
+  __syncthreads();
+  // [rd,rd] = A_rr - [A_sr^T, T^T] [T; [sk,rd]]  (lower triangle)
+  auto fa = [&](int a, int q) {
+    return q < k ? Aee[sperm[q] + (int64_t)sperm[k + a] * n] : Tm[(q - k) + (int64_t)a * k];
+  };
+  auto fb = [&](int q, int b) {
+    return q < k ? Tm[q + (int64_t)b * k] : Fu[(r + q - k) + (int64_t)b * n];
+  };
+  for (int ti = 0; ti < r; ti += kTile)
+    for (int tj = 0; tj <= ti; tj += kTile) {
+      T acc[4][4];
+      cta_tile_product(ti, tj, r, r, 2 * k, fa, fb, sm, acc);
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int i = ti + ty + 16 * a, j = tj + tx + 16 * b;
+          if (i < r && j <= i) Fu[i + (int64_t)j * n] = a_ss(k + i, k + j) - acc[a][b];
+        }
+    }
+  for (int64_t idx = tid; idx < (int64_t)k * k; idx += blockDim.x) {
+    const int q = (int)(idx % k), p = (int)(idx / k);
+    if (q < p) continue;
+    Fu[(r + q) + (int64_t)(r + p) * n] = a_ss(q, p);
+  }
+  __syncthreads();
+
+  // eliminate the redundant DOFs
+  if (!cta_partial_chol(Fu, n, n, r, sm) && tid == 0)
+    report(status, RHIF_ERR_NOT_SPD, Lv.level, kKindUnit, g);
+  __syncthreads();
+
+  for (int64_t idx = tid; idx < (int64_t)k * k; idx += blockDim.x) {
+    const int q = (int)(idx % k), p = (int)(idx / k);
+    if (q < p) continue;
+    const T val = Fu[(r + q) + (int64_t)(r + p) * n];
+    for (int kk = c0; kk < c1; ++kk) {
+      int ld;
+      T* fr = frame_of<T>(Lv, Lv.group_cell[kk], &ld);
+      const int pos = Lv.group_pos[kk];
+      const int bq = pos + sperm[q], bp = pos + sperm[p];
+      fr[max(bq, bp) + (int64_t)min(bq, bp) * ld] = kk == c0 ? val : T(0);
+    }
+  }
+  int* perm_out = Ph.perm + Ph.u_perm_off[u];
+  for (int i = tid; i < n; i += blockDim.x) perm_out[i] = sperm[i];
+  if (tid == 0) Ph.rank[u] = k;
+}
+
+// Skeletonization (Sec. 2.2) of one unit per CTA: gather A_{R,g}, CPQR with
+// exact norms recomputed at every step, then skel_finish.  M lives in shared
+// memory when mstage is set.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_skel(LevelDev Lv, PhaseDev Ph, uint8_t* alive,
+                                                   double tol, int* status, int mstage) {
+  extern __shared__ unsigned char smraw[];
+  T* sm = (T*)smraw;                                   // partial-Cholesky / tile workspace
+  T* nrm = sm + partial_chol_smem_elems();             // [max_n]
+  int* sperm = (int*)(nrm + Ph.max_n);                 // [max_n]
+  __shared__ int s_k, s_stop, s_p;
+  __shared__ T s_r11;
+  __shared__ SkelRows rows;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  const int u = blockIdx.x;
+  const int g = Ph.u_group[u];
+  const int n = Lv.group_size[g];
+  const int nrow = Ph.u_nrow[u];
+  const int ldm = nrow > 0 ? nrow : 1;
+  T* M = (T*)Ph.Mbuf + Ph.u_m_off[u];
+  if (mstage) M = (T*)((unsigned char*)(sperm + Ph.max_n) + 16 - (((size_t)(sperm + Ph.max_n)) & 15));
+  T* Aee = M + (int64_t)nrow * n;
+
+  skel_row_groups(Lv, g, nrow, status, &rows);
+  __syncthreads();
+  skel_gather_rows(Lv, alive, g, n, nrow, rows, 0, nrow, M, 1, ldm);
+  skel_gather_diag(Lv, g, n, Aee, tid, blockDim.x);
   for (int i = tid; i < n; i += blockDim.x) sperm[i] = i;
   if (tid == 0) {
     s_k = 0;
@@ -918,8 +1117,6 @@ __global__ void __launch_bounds__(kThreads) k_skel(LevelDev Lv, PhaseDev Ph, uin
   }
   __syncthreads();
 
-  // 2. column-pivoted Householder QR of M, norms recomputed at every step,
-  //    stopped once the largest remaining column norm is <= tol * |R_11|
   const int steps = min(nrow, n);
   for (int j = 0; j < steps; ++j) {
     for (int c = j + warp; c < n; c += nwarps) {
@@ -932,20 +1129,7 @@ __global__ void __launch_bounds__(kThreads) k_skel(LevelDev Lv, PhaseDev Ph, uin
       if (lane == 0) nrm[c] = s;
     }
     __syncthreads();
-    if (tid == 0) {
-      T mx = T(0);
-      for (int c = j; c < n; ++c) mx = nrm[c] > mx ? nrm[c] : mx;
-      if (j == 0) s_r11 = my_sqrt(mx);
-      const int stop = (s_r11 == T(0)) || (my_sqrt(mx) <= T(tol) * s_r11);
-      s_stop = stop;
-      if (!stop) {
-        const T thr = T(1.0 - 1e-12) * mx;
-        int best = -1;
-        for (int c = j; c < n; ++c)
-          if (nrm[c] >= thr && (best < 0 || sperm[c] < sperm[best])) best = c;
-        s_p = best;
-      }
-    }
+    skel_pivot(nrm, sperm, j, n, tol, &s_r11, &s_stop, &s_p);
     __syncthreads();
     if (s_stop) break;
     const int p = s_p;
@@ -984,66 +1168,192 @@ __global__ void __launch_bounds__(kThreads) k_skel(LevelDev Lv, PhaseDev Ph, uin
     }
     __syncthreads();
   }
+  skel_finish(Lv, Ph, u, g, n, s_k, M, 1, ldm, Aee, sperm, sm, status);
+}
+
+// Row length (elements) of the per-rank partial-sum tables of k_skel_cluster:
+// a multiple of 4, so every row is a whole number of 16-byte vectors.
+__host__ __device__ inline int skel_cluster_ldp(int max_n) { return (max_n + 3) & ~3; }
+
+// Skeletonization of one unit per thread-block cluster of C CTAs, for units
+// whose A_{R,g} does not fit in one CTA's shared memory.  CTA q owns rows
+// [q*sr, (q+1)*sr) of A_{R,g} (sr = ceil(nrow / C)), stored row-major and
+// staged in its shared memory when they fit; each thread owns whole columns,
+// so column sums need no shuffles and row loads are coalesced.  At each CPQR
+// step every CTA pushes its partial column norms and Householder dot products
+// into the shared memory of every CTA of the cluster (remote stores, no
+// remote loads); after a cluster barrier each CTA sums the C partials in rank
+// order from its own copy, so all CTAs take bitwise the same pivot and
+// stopping decisions.  Two cluster barriers per step: after the partial norms
+// (pivot) and after the partial dots (update).  The cluster barriers are
+// hardware barriers that every CTA reaches the same number of times.  Rank 0
+// then runs skel_finish on R written back to global memory.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_skel_cluster(LevelDev Lv, PhaseDev Ph, uint8_t* alive,
+                                                           double tol, int* status,
+                                                           int64_t slice_cap) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks(), cr = (int)cl.block_rank();
+  const int ldp = skel_cluster_ldp(Ph.max_n);
+  extern __shared__ unsigned char smraw[];
+  T* sm = (T*)smraw;
+  T* nrm = sm + partial_chol_smem_elems();   // [ldp] column norms over the cluster
+  T* pnall = nrm + ldp;                      // [C][ldp] partial norms of each rank
+  T* pdall = pnall + (int64_t)C * ldp;       // [C][ldp] partial Householder dots
+  int* sperm = (int*)(pdall + (int64_t)C * ldp);   // [ldp]
+  T* slice = (T*)((unsigned char*)(sperm + ldp) + 16 - (((size_t)(sperm + ldp)) & 15));
+  __shared__ int s_k, s_stop, s_p;
+  __shared__ T s_r11, s_x0;
+  __shared__ SkelRows rows;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int u = blockIdx.x / C;
+  const int g = Ph.u_group[u];
+  const int n = Lv.group_size[g];
+  const int nrow = Ph.u_nrow[u];
+  T* Mg = (T*)Ph.Mbuf + Ph.u_m_off[u];       // row-major nrow x n while this kernel runs
+  T* Aee = Mg + (int64_t)nrow * n;
+  const int sr = (nrow + C - 1) / C;
+  const int i0 = min(nrow, cr * sr), i1 = min(nrow, i0 + sr);
+  const bool stage = (int64_t)sr * n <= slice_cap;
+  T* Ms = stage ? slice : Mg + (int64_t)i0 * n;   // row i of this CTA at Ms[(i - i0) * n]
+  auto at = [&](int i, int c) -> T& { return Ms[(int64_t)(i - i0) * n + c]; };
+  // copy this rank's row of buf (columns >= c0) into the same row of every
+  // other rank, 16 bytes per store; rows are ldp elements (16-byte multiples)
+  auto bcast = [&](T* buf, int c0) {
+    const int v0 = (c0 * (int)sizeof(T)) / 16, v1 = (n * (int)sizeof(T) + 15) / 16;
+    const int nv = v1 - v0;
+    const uint4* src = (const uint4*)(buf + (int64_t)cr * ldp);
+    for (int idx = tid; idx < (C - 1) * nv; idx += nth) {
+      const int q = idx / nv, v = v0 + idx % nv;
+      uint4* dst = (uint4*)cl.map_shared_rank(buf + (int64_t)cr * ldp, q < cr ? q : q + 1);
+      dst[v] = src[v];
+    }
+  };
+
+  skel_row_groups(Lv, g, nrow, status, &rows);
+  __syncthreads();
+  skel_gather_rows(Lv, alive, g, n, nrow, rows, i0, i1, Ms, n, 1);
+  skel_gather_diag(Lv, g, n, Aee, (int64_t)cr * nth + tid, (int64_t)C * nth);
+  for (int i = tid; i < n; i += nth) sperm[i] = i;
+  if (tid == 0) {
+    s_k = 0;
+    s_r11 = T(0);
+  }
+  __syncthreads();
+  T* myn = pnall + (int64_t)cr * ldp;
+  T* myd = pdall + (int64_t)cr * ldp;
+  for (int c = tid; c < n; c += nth) {
+    T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+    int i = i0;
+    for (; i + 3 < i1; i += 4) {
+      const T a0 = at(i, c), a1 = at(i + 1, c), a2 = at(i + 2, c), a3 = at(i + 3, c);
+      s0 += a0 * a0; s1 += a1 * a1; s2 += a2 * a2; s3 += a3 * a3;
+    }
+    for (; i < i1; ++i) {
+      const T a0 = at(i, c);
+      s0 += a0 * a0;
+    }
+    myn[c] = (s0 + s1) + (s2 + s3);
+  }
+  __syncthreads();
+  bcast(pnall, 0);
+  cl.sync();
+
+  const int steps = min(nrow, n);
+  for (int j = 0; j < steps; ++j) {
+    for (int c = j + tid; c < n; c += nth) {
+      T s = T(0);
+      for (int q = 0; q < C; ++q) s += pnall[(int64_t)q * ldp + c];
+      nrm[c] = s;
+    }
+    __syncthreads();
+    skel_pivot(nrm, sperm, j, n, tol, &s_r11, &s_stop, &s_p);
+    __syncthreads();
+    if (s_stop) break;
+    const int p = s_p;
+    if (p != j) {
+      for (int i = i0 + tid; i < i1; i += nth) {
+        const T a = at(i, j);
+        at(i, j) = at(i, p);
+        at(i, p) = a;
+      }
+      if (tid == 0) {
+        const int t = sperm[j]; sperm[j] = sperm[p]; sperm[p] = t;
+        const T q = nrm[j]; nrm[j] = nrm[p]; nrm[p] = q;
+      }
+    }
+    __syncthreads();
+    const int owner = j / sr;
+    const bool own_j = cr == owner;   // i0 <= j < i1
+    const T nx = my_sqrt(nrm[j]);
+    T v0 = T(0);
+    if (own_j) {
+      const T x0 = at(j, j);
+      v0 = x0 - (x0 < T(0) ? nx : -nx);
+      if (tid < C) *cl.map_shared_rank(&s_x0, tid) = x0;
+    }
+    const int ia = max(i0, j + 1);
+    for (int c = j + 1 + tid; c < n; c += nth) {
+      T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+      int i = ia;
+      for (; i + 3 < i1; i += 4) {
+        s0 += at(i, j) * at(i, c);
+        s1 += at(i + 1, j) * at(i + 1, c);
+        s2 += at(i + 2, j) * at(i + 2, c);
+        s3 += at(i + 3, j) * at(i + 3, c);
+      }
+      for (; i < i1; ++i) s0 += at(i, j) * at(i, c);
+      const T s = (s0 + s1) + (s2 + s3);
+      myd[c] = own_j ? s + v0 * at(j, c) : s;
+    }
+    __syncthreads();
+    bcast(pdall, j + 1);
+    cl.sync();
+    const T x0 = s_x0;
+    const T alpha = x0 < T(0) ? nx : -nx;
+    v0 = x0 - alpha;
+    const T tau = T(1) / (nx * (nx + my_abs(x0)));
+    for (int c = j + 1 + tid; c < n; c += nth) {
+      T s = T(0);
+      for (int q = 0; q < C; ++q) s += pdall[(int64_t)q * ldp + c];
+      const T w = s * tau;
+      if (own_j) at(j, c) -= w * v0;   // row j: v_j = v0, excluded from the next norms
+      T n0 = T(0), n1 = T(0), n2 = T(0), n3 = T(0);
+      int i = ia;
+      for (; i + 3 < i1; i += 4) {
+        const T b0 = at(i, c) - w * at(i, j);
+        const T b1 = at(i + 1, c) - w * at(i + 1, j);
+        const T b2 = at(i + 2, c) - w * at(i + 2, j);
+        const T b3 = at(i + 3, c) - w * at(i + 3, j);
+        at(i, c) = b0; at(i + 1, c) = b1; at(i + 2, c) = b2; at(i + 3, c) = b3;
+        n0 += b0 * b0; n1 += b1 * b1; n2 += b2 * b2; n3 += b3 * b3;
+      }
+      for (; i < i1; ++i) {
+        const T b0 = at(i, c) - w * at(i, j);
+        at(i, c) = b0;
+        n0 += b0 * b0;
+      }
+      myn[c] = (n0 + n1) + (n2 + n3);
+    }
+    __syncthreads();
+    bcast(pnall, j + 1);
+    if (tid == 0) {
+      if (own_j) at(j, j) = alpha;
+      s_k = j + 1;
+    }
+    cl.sync();
+  }
   const int k = s_k;
-  const int r = n - k;
-
-  // 3. interpolation matrix T = R11^{-1} R12 (k x r)
-  for (int a = tid; a < r; a += blockDim.x) {
-    for (int i = k - 1; i >= 0; --i) {
-      T t = M[i + (int64_t)(k + a) * ldm];
-      for (int q = i + 1; q < k; ++q) t -= M[i + (int64_t)q * ldm] * Tm[q + (int64_t)a * k];
-      Tm[i + (int64_t)a * k] = t / M[i + (int64_t)i * ldm];
-    }
+  if (stage) {   // R rows back to global memory (row-major) for the finishing CTA
+    const int rb = min(i1, k);
+    for (int64_t idx = tid; idx < (int64_t)max(rb - i0, 0) * n; idx += nth)
+      Mg[(int64_t)i0 * n + idx] = Ms[idx];
   }
-  __syncthreads();
-
-  // 4. zeroing (Eq. 2.2): Z^T A_II Z in (redundant, skeleton) order
-  //    [rd,rd] = A_rr - T^T A_sr - A_sr^T T + T^T A_ss T ; [sk,rd] = A_sr - A_ss T ; [sk,sk] = A_ss
-  for (int64_t idx = tid; idx < (int64_t)k * r; idx += blockDim.x) {
-    const int q = (int)(idx % k), a = (int)(idx / k);
-    T v = Aee[sperm[q] + (int64_t)sperm[k + a] * n];
-    for (int p = 0; p < k; ++p) v -= Aee[sperm[q] + (int64_t)sperm[p] * n] * Tm[p + (int64_t)a * k];
-    Fu[(r + q) + (int64_t)a * n] = v;
-  }
-  __syncthreads();
-  for (int64_t idx = tid; idx < (int64_t)r * r; idx += blockDim.x) {
-    const int a = (int)(idx % r), b = (int)(idx / r);
-    if (a < b) continue;
-    T v = Aee[sperm[k + a] + (int64_t)sperm[k + b] * n];
-    for (int q = 0; q < k; ++q)
-      v -= Tm[q + (int64_t)a * k] * Fu[(r + q) + (int64_t)b * n] +
-           Aee[sperm[q] + (int64_t)sperm[k + a] * n] * Tm[q + (int64_t)b * k];
-    Fu[a + (int64_t)b * n] = v;
-  }
-  for (int64_t idx = tid; idx < (int64_t)k * k; idx += blockDim.x) {
-    const int q = (int)(idx % k), p = (int)(idx / k);
-    if (q < p) continue;
-    Fu[(r + q) + (int64_t)(r + p) * n] = Aee[sperm[q] + (int64_t)sperm[p] * n];
-  }
-  __syncthreads();
-
-  // 5. eliminate the redundant DOFs (Sec. 2.1 applied to the zeroed block)
-  if (!cta_partial_chol(Fu, n, n, r, sm) && tid == 0)
-    report(status, RHIF_ERR_NOT_SPD, Lv.level, kKindUnit, g);
-  __syncthreads();
-
-  // 6. the skeleton block of the first holding cell takes the new value, the
-  //    others drop theirs; redundant DOFs leave the active set
-  for (int64_t idx = tid; idx < (int64_t)k * k; idx += blockDim.x) {
-    const int q = (int)(idx % k), p = (int)(idx / k);
-    if (q < p) continue;
-    const T val = Fu[(r + q) + (int64_t)(r + p) * n];
-    for (int kk = c0; kk < c1; ++kk) {
-      int ld;
-      T* fr = frame_of<T>(Lv, Lv.group_cell[kk], &ld);
-      const int pos = Lv.group_pos[kk];
-      const int bq = pos + sperm[q], bp = pos + sperm[p];
-      fr[max(bq, bp) + (int64_t)min(bq, bp) * ld] = kk == c0 ? val : T(0);
-    }
-  }
-  int* perm_out = Ph.perm + Ph.u_perm_off[u];
-  for (int i = tid; i < n; i += blockDim.x) perm_out[i] = sperm[i];
-  if (tid == 0) Ph.rank[u] = k;
+  cl.sync();
+  if (cr != 0) return;
+  skel_finish(Lv, Ph, u, g, n, k, (const T*)Mg, (int64_t)n, (int64_t)1, (const T*)Aee, sperm, sm,
+              status);
 }
 
 // Redundant DOFs leave the active set only after every ID of the phase has
@@ -1173,9 +1483,64 @@ void launch_skel(const LevelDev& Lv, const PhaseDev& Ph, uint8_t* alive, double 
 }
 
 template <typename T>
+size_t skel_cluster_fixed_bytes(int max_n, int C) {
+  const size_t ldp = skel_cluster_ldp(max_n);
+  return (partial_chol_smem_elems() + (1 + 2 * (size_t)C) * ldp) * sizeof(T) + ldp * sizeof(int) +
+         32;
+}
+
+template <typename T>
+int skel_cluster_schedulable(int C, size_t smem) {
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(C);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, (void*)k_skel_cluster<T>, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+template <typename T>
+cudaError_t launch_skel_cluster(const LevelDev& Lv, const PhaseDev& Ph, uint8_t* alive, double tol,
+                                int* status, int C, int64_t slice_cap, size_t smem,
+                                cudaStream_t s) {
+  if (!Ph.nunit) return cudaSuccess;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3((unsigned)Ph.nunit * C);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_skel_cluster<T>, Lv, Ph, alive, tol, status, slice_cap);
+  if (e != cudaSuccess) return e;
+  k_mark_dead<<<Ph.nunit, 32, 0, s>>>(Lv, Ph, alive);
+  return cudaGetLastError();
+}
+
+template <typename T>
 int configure_factor_kernels() {
   const int big = 220 * 1024;
   cudaError_t e = cudaFuncSetAttribute(k_skel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_skel_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_skel_cluster<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_leaf_elim<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess)
@@ -1206,6 +1571,10 @@ int configure_factor_kernels() {
   template void launch_skel<T>(const LevelDev&, const PhaseDev&, uint8_t*, double, int*, int64_t, \
                                cudaStream_t);                                                     \
   template size_t skel_smem_bytes<T>(int);                                                        \
+  template size_t skel_cluster_fixed_bytes<T>(int, int);                                          \
+  template int skel_cluster_schedulable<T>(int, size_t);                                          \
+  template cudaError_t launch_skel_cluster<T>(const LevelDev&, const PhaseDev&, uint8_t*, double, \
+                                              int*, int, int64_t, size_t, cudaStream_t);          \
   template int configure_factor_kernels<T>();
 
 RHIF_INST(double)

@@ -45,6 +45,16 @@ void launch_skel(const LevelDev& Lv, const PhaseDev& Ph, uint8_t* alive, double 
                  int64_t max_m_elems, cudaStream_t s);
 template <typename T>
 size_t skel_smem_bytes(int max_n);
+// Skeletonization with one thread-block cluster of C CTAs per unit; each CTA
+// stages its row slice of A_{R,g} in shared memory when it has at most
+// slice_cap elements.  smem = skel_cluster_fixed_bytes + slice bytes.
+template <typename T>
+size_t skel_cluster_fixed_bytes(int max_n, int C);
+template <typename T>
+int skel_cluster_schedulable(int C, size_t smem);   // clusters that fit at once (0: none)
+template <typename T>
+cudaError_t launch_skel_cluster(const LevelDev& Lv, const PhaseDev& Ph, uint8_t* alive, double tol,
+                                int* status, int C, int64_t slice_cap, size_t smem, cudaStream_t s);
 template <typename T>
 int configure_factor_kernels();
 

@@ -154,6 +154,7 @@ struct Launch {
 // eliminated by many CTAs per front.
 constexpr int kBigFront = 384;
 constexpr int kBigFrontCells = 304;
+constexpr int kNumSMsHint = 152;   // CTAs wanted per cluster launch (one per SM)
 
 static void add_launches(int cat, int64_t n) {
   std::lock_guard<std::mutex> lk(g_kmu);
@@ -189,6 +190,7 @@ struct rhif_handle {
   int precision = RHIF_FP64;
   bool precondition = true, edge_skel = false;
   int big_front = 0, big_frame = 0;   // many-CTA thresholds (see rhif_opts)
+  int skel_cluster = 0;
   double tol = 0.0;
   std::vector<rhif::LevelStore> levels;   // 0..L
   double* diag = nullptr;
@@ -368,6 +370,66 @@ static double cell_flops(double nI, double nB) {
   return nI * nI * nI / 3.0 + nI * nI * nB + nI * nB * nB;
 }
 
+// Skeletonization of one phase: one CTA per unit while every unit's ID matrix
+// fits in shared memory, else one thread-block cluster per unit.  The cluster
+// size is the smallest power of two whose row slices fit in shared memory,
+// raised until the launch has at least one CTA per SM, capped at 16 and at
+// what the device can schedule.
+template <typename T>
+static int skeletonize(rhif_handle* H, const LevelPlan& P, const PhasePlan& ph, const LevelDev& L,
+                       const PhaseDev& D, uint8_t* alive, cudaStream_t s) {
+  const int64_t nunit = (int64_t)ph.units.group.size();
+  if (!nunit) return RHIF_OK;
+  const size_t elem = sizeof(T);
+  const size_t budget = 216 * 1024;
+  const bool fits1 = skel_smem_bytes<T>(ph.units.max_n) + ph.units.max_m * elem <= 200 * 1024;
+  if (H->skel_cluster < 0 || (H->skel_cluster == 0 && fits1)) {
+    launch_skel<T>(L, D, alive, H->tol, H->status, ph.units.max_m, s);
+    CK(cudaGetLastError());
+    return RHIF_OK;
+  }
+  auto fixed = [&](int C) { return skel_cluster_fixed_bytes<T>(ph.units.max_n, C); };
+  auto max_slice = [&](int C) {
+    int64_t m = 0;
+    for (int64_t u = 0; u < nunit; ++u) {
+      const int64_t n = P.group_size[ph.units.group[u]];
+      const int64_t sr = (ph.units.nrow[u] + C - 1) / C;
+      m = std::max(m, sr * n);
+    }
+    return m;
+  };
+  int C = H->skel_cluster;
+  if (C == 0) {
+    int cfit = 16;
+    for (int c = 2; c <= 16; c *= 2)
+      if (fixed(c) + max_slice(c) * elem <= budget) {
+        cfit = c;
+        break;
+      }
+    int cfill = 1;
+    while (cfill < 16 && nunit * cfill < kNumSMsHint) cfill *= 2;
+    C = std::max(cfit, cfill);
+  }
+  for (;;) {
+    const size_t fx = fixed(C);
+    if (fx <= budget) {
+      const int64_t ms = max_slice(C);
+      const int64_t cap = fx + ms * elem <= budget ? ms : (int64_t)((budget - fx) / elem);
+      const size_t smem = fx + (size_t)cap * elem;
+      if (C == 1 || skel_cluster_schedulable<T>(C, smem) > 0) {
+        CK(launch_skel_cluster<T>(L, D, alive, H->tol, H->status, C, cap, smem, s));
+        return RHIF_OK;
+      }
+    }
+    if (C == 1) {   // no room for the cluster tables: one CTA per unit, M in global memory
+      launch_skel<T>(L, D, alive, H->tol, H->status, ph.units.max_m, s);
+      CK(cudaGetLastError());
+      return RHIF_OK;
+    }
+    C /= 2;
+  }
+}
+
 template <typename T>
 static int factor_impl(rhif_handle* H, const rhif_csr* A) {
   const Geometry& G = H->G;
@@ -505,7 +567,7 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
       const int64_t nunit = (int64_t)ph.units.group.size();
       {
         Launch t(kCatSkel, s, 0.0, 0.0, nunit ? 1 : 0);
-        launch_skel<T>(S.dev, D, alive_d, H->tol, H->status, ph.units.max_m, s);
+        if ((rc = skeletonize<T>(H, P, ph, S.dev, D, alive_d, s))) return rc;
       }
       if ((rc = check_status(H, "skeletonization"))) return rc;
       H->mem.release(M);
@@ -774,6 +836,9 @@ int rhif_factor(const rhif_csr* A, const rhif_grid* g, int leaf, double tol, con
   H->edge_skel = (g->dim == 3) && o->edge_skel_3d;
   H->big_front = o->big_front == 0 ? kBigFront : (o->big_front < 0 ? INT_MAX : o->big_front);
   H->big_frame = o->big_frame < 0 ? INT_MAX : o->big_frame;
+  if (o->skel_cluster > 16 || (o->skel_cluster > 0 && (o->skel_cluster & (o->skel_cluster - 1))))
+    return fail(RHIF_ERR_BAD_ARG, "skel_cluster must be a power of two <= 16");
+  H->skel_cluster = o->skel_cluster;
   H->tol = tol;
   H->mem.s = (cudaStream_t)stream;
   cudaEvent_t e0, e1;

@@ -1,12 +1,13 @@
-"""GPU tests of the many-CTA schedules for large fronts and frames.
+"""GPU tests of the many-CTA schedules for large fronts, frames and units.
 
 A level whose fronts are large is eliminated by panel / trailing-tile / Schur-
 tile launches spread over many CTAs, and its block Jacobi scaling (Eq. 2.3) by
-row and column block solves; small levels use one CTA per front.  The
-thresholds are options, so these tests force the many-CTA schedules on grids
-the oracle factors in seconds and hold them to the same FP64 bar as the
-one-CTA schedule: identical skeletons (except at logged near-ties) and
-F^{-1} x within 1e-9 relative of the oracle's.
+row and column block solves; a skeletonization unit whose ID matrix is large
+runs its CPQR on a thread-block cluster, one row slice per CTA.  Small objects
+use one CTA each.  The thresholds and the cluster size are options, so these
+tests force the many-CTA schedules on grids the oracle factors in seconds and
+hold them to the same FP64 bar as the one-CTA schedule: identical skeletons
+(except at logged near-ties) and F^{-1} x within 1e-9 relative of the oracle's.
 """
 import numpy as np
 import pytest
@@ -33,15 +34,30 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("ns,leaf,tol,b,edge", CASES)
-def test_many_cta_schedules_match_oracle(gpu_lib, ns, leaf, tol, b, edge):
-    a = W.log_uniform_pixels(ns, 1e-3, 1e3, seed=sum(ns) + leaf)
-    A = fd.assemble(ns, a, b)
-    Fo = phif.factor(A, ns, leaf, tol, edge_skel=edge)
+_ORACLE = {}
+
+
+def _oracle(ns, leaf, tol, b, edge):
+    key = (ns, leaf, tol, b, edge)
+    if key not in _ORACLE:
+        a = W.log_uniform_pixels(ns, 1e-3, 1e3, seed=sum(ns) + leaf)
+        A = fd.assemble(ns, a, b)
+        _ORACLE[key] = (a, A, phif.factor(A, ns, leaf, tol, edge_skel=edge))
+    return _ORACLE[key]
+
+
+# skel_cluster: CTAs per skeletonization unit (thread-block cluster); 0 = default.
+# The 31^3 grid runs with the default and one forced cluster size only.
+PARAMS = [c + (k,) for c in CASES for k in ((0, 4) if c[0] == (31, 31, 31) else (0, 1, 4, 16))]
+
+
+@pytest.mark.parametrize("ns,leaf,tol,b,edge,skel_cluster", PARAMS)
+def test_many_cta_schedules_match_oracle(gpu_lib, ns, leaf, tol, b, edge, skel_cluster):
+    a, A, Fo = _oracle(ns, leaf, tol, b, edge)
     csr = gpu_lib.rhif_assemble_fd(ns, _dev(a), b)
     gpu_lib.rhif_reset_kernel_stats()
     Fg = gpu_lib.rhif_factor(csr, ns, leaf, tol, precision="fp64", edge_skel_3d=edge,
-                             big_front=1, big_frame=1)
+                             big_front=1, big_frame=1, skel_cluster=skel_cluster)
     ks = gpu_lib.rhif_kernel_stats()
     levels = Fg.stats()["levels"]
     # panel + trailing launches per 32 interior columns: more than one launch per level

@@ -7,6 +7,8 @@
 // cell (x_I = L^{-T}(x_I - W^T x_B)).  The cell contributions to a shared
 // boundary DOF are written per cell and summed by the owning group in cell
 // order, so the result does not depend on scheduling.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 #include "tables.h"
@@ -324,6 +326,183 @@ k_apply_cell_down(LevelDev Lv, double* x, int64_t ldx, int nrhs, int stage) {
     cta_trsv_lower_t(F, n, nI, t);
     for (int i = threadIdx.x; i < nI; i += blockDim.x) xr[gI[i]] = double(t[i]);
     __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// cells of levels with large fronts, whose L block holds L^{-1} (explicit
+// inverse taken at factorization): each sweep is two launches of row-parallel
+// products over many CTAs, with y / t kept in a scratch column `tmp` at the
+// cell's DOF-list offset.  Right-hand sides go in chunks of `rc` (<= 4), the
+// chunk's input vector staged in shared memory.
+//   up:   y = L^{-1} x_I ;  x_I = y, u_B = W y       (W = rows nI..n of the front)
+//   down: t = x_I - W^T x_B ;  x_I = L^{-T} t
+// ---------------------------------------------------------------------------
+
+constexpr int kBigRows = 128;   // rows per CTA (one per thread) in up1 / up2
+constexpr int kBigWarps = 8;    // rows per CTA (one per warp) in down1 / down2
+
+template <typename T>
+__global__ void __launch_bounds__(kBigRows)
+k_apply_big_up1(LevelDev Lv, const double* x, int64_t ldx, int nrhs, int rc, double* tmp,
+                int64_t ldt) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* xs = (T*)smraw;   // [kend][rc]
+  const int c = blockIdx.y;
+  const int nI = Lv.nI[c];
+  const int r0 = blockIdx.x * kBigRows;
+  if (r0 >= nI) return;
+  const int n = nI + Lv.nB[c];
+  const int i = r0 + threadIdx.x;
+  const int kend = min(nI, r0 + kBigRows);
+  const T* F = (const T*)Lv.front + Lv.front_off[c];
+  const int32_t* gI = Lv.gids + Lv.gid_off[c];
+  double* tc = tmp + Lv.gid_off[c];
+  for (int q0 = 0; q0 < nrhs; q0 += rc) {
+    const int nr = min(rc, nrhs - q0);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < kend * nr; idx += blockDim.x) {
+      const int k = idx / nr, rr = idx % nr;
+      xs[k * rc + rr] = T(x[(int64_t)(q0 + rr) * ldx + gI[k]]);
+    }
+    __syncthreads();
+    T acc[4] = {T(0), T(0), T(0), T(0)};
+    const int kl = i < nI ? min(i + 1, kend) : 0;
+#pragma unroll 4
+    for (int k = 0; k < kl; ++k) {
+      const T l = F[i + (int64_t)k * n];
+#pragma unroll
+      for (int rr = 0; rr < 4; ++rr)
+        if (rr < nr) acc[rr] += l * xs[k * rc + rr];
+    }
+    if (i < nI)
+      for (int rr = 0; rr < nr; ++rr) tc[(int64_t)(q0 + rr) * ldt + i] = double(acc[rr]);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBigRows)
+k_apply_big_up2(LevelDev Lv, double* x, int64_t ldx, int nrhs, int rc, double* ubuf, int64_t ldu,
+                const double* tmp, int64_t ldt) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* ys = (T*)smraw;   // [nI][rc]
+  const int c = blockIdx.y;
+  const int nI = Lv.nI[c], nB = Lv.nB[c], n = nI + nB;
+  const int r0 = blockIdx.x * kBigRows;
+  if (r0 >= max(nI, nB)) return;
+  const int row = r0 + threadIdx.x;
+  const T* F = (const T*)Lv.front + Lv.front_off[c];
+  const int32_t* gI = Lv.gids + Lv.gid_off[c];
+  const double* tc = tmp + Lv.gid_off[c];
+  for (int q0 = 0; q0 < nrhs; q0 += rc) {
+    const int nr = min(rc, nrhs - q0);
+    if (row < nI)
+      for (int rr = 0; rr < nr; ++rr)
+        x[(int64_t)(q0 + rr) * ldx + gI[row]] = tc[(int64_t)(q0 + rr) * ldt + row];
+    if (r0 >= nB) continue;
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nI * nr; idx += blockDim.x) {
+      const int k = idx / nr, rr = idx % nr;
+      ys[k * rc + rr] = T(tc[(int64_t)(q0 + rr) * ldt + k]);
+    }
+    __syncthreads();
+    if (row < nB) {
+      T acc[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll 4
+      for (int k = 0; k < nI; ++k) {
+        const T w = F[(nI + row) + (int64_t)k * n];
+#pragma unroll
+        for (int rr = 0; rr < 4; ++rr)
+          if (rr < nr) acc[rr] += w * ys[k * rc + rr];
+      }
+      for (int rr = 0; rr < nr; ++rr)
+        ubuf[(int64_t)(q0 + rr) * ldu + Lv.b_off[c] + row] = double(acc[rr]);
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(32 * kBigWarps)
+k_apply_big_down1(LevelDev Lv, const double* x, int64_t ldx, int nrhs, int rc, double* tmp,
+                  int64_t ldt) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* xb = (T*)smraw;   // [nB][rc]
+  const int c = blockIdx.y;
+  const int nI = Lv.nI[c], nB = Lv.nB[c], n = nI + nB;
+  const int r0 = blockIdx.x * kBigWarps;
+  if (r0 >= nI) return;
+  const int lane = threadIdx.x & 31, i = r0 + (threadIdx.x >> 5);
+  const T* F = (const T*)Lv.front + Lv.front_off[c];
+  const int32_t* gI = Lv.gids + Lv.gid_off[c];
+  const int32_t* gB = gI + nI;
+  double* tc = tmp + Lv.gid_off[c];
+  for (int q0 = 0; q0 < nrhs; q0 += rc) {
+    const int nr = min(rc, nrhs - q0);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nB * nr; idx += blockDim.x) {
+      const int b = idx / nr, rr = idx % nr;
+      xb[b * rc + rr] = T(x[(int64_t)(q0 + rr) * ldx + gB[b]]);
+    }
+    __syncthreads();
+    if (i >= nI) continue;
+    T acc[4] = {T(0), T(0), T(0), T(0)};
+    for (int b = lane; b < nB; b += 32) {
+      const T w = F[(nI + b) + (int64_t)i * n];
+#pragma unroll
+      for (int rr = 0; rr < 4; ++rr)
+        if (rr < nr) acc[rr] += w * xb[b * rc + rr];
+    }
+#pragma unroll
+    for (int rr = 0; rr < 4; ++rr) acc[rr] = warp_sum(acc[rr]);
+    if (lane < nr) {
+      T a = acc[0];
+#pragma unroll
+      for (int rr = 1; rr < 4; ++rr)
+        if (lane == rr) a = acc[rr];
+      tc[(int64_t)(q0 + lane) * ldt + i] = x[(int64_t)(q0 + lane) * ldx + gI[i]] - double(a);
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(32 * kBigWarps)
+k_apply_big_down2(LevelDev Lv, double* x, int64_t ldx, int nrhs, int rc, const double* tmp,
+                  int64_t ldt) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* ts = (T*)smraw;   // [nI][rc]
+  const int c = blockIdx.y;
+  const int nI = Lv.nI[c], n = nI + Lv.nB[c];
+  const int r0 = blockIdx.x * kBigWarps;
+  if (r0 >= nI) return;
+  const int lane = threadIdx.x & 31, i = r0 + (threadIdx.x >> 5);
+  const T* F = (const T*)Lv.front + Lv.front_off[c];
+  const int32_t* gI = Lv.gids + Lv.gid_off[c];
+  const double* tc = tmp + Lv.gid_off[c];
+  for (int q0 = 0; q0 < nrhs; q0 += rc) {
+    const int nr = min(rc, nrhs - q0);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < (nI - r0) * nr; idx += blockDim.x) {
+      const int k = r0 + idx / nr, rr = idx % nr;
+      ts[(k - r0) * rc + rr] = T(tc[(int64_t)(q0 + rr) * ldt + k]);
+    }
+    __syncthreads();
+    if (i >= nI) continue;
+    T acc[4] = {T(0), T(0), T(0), T(0)};
+    for (int k = i + lane; k < nI; k += 32) {
+      const T l = F[k + (int64_t)i * n];
+#pragma unroll
+      for (int rr = 0; rr < 4; ++rr)
+        if (rr < nr) acc[rr] += l * ts[(k - r0) * rc + rr];
+    }
+#pragma unroll
+    for (int rr = 0; rr < 4; ++rr) acc[rr] = warp_sum(acc[rr]);
+    if (lane < nr) {
+      T a = acc[0];
+#pragma unroll
+      for (int rr = 1; rr < 4; ++rr)
+        if (lane == rr) a = acc[rr];
+      x[(int64_t)(q0 + lane) * ldx + gI[i]] = double(a);
+    }
   }
 }
 
@@ -668,6 +847,43 @@ void launch_apply_cell_down(const LevelDev& Lv, double* x, int64_t ldx, int nrhs
                                                                               stage);
 }
 
+// right-hand sides per chunk so that a chunk of an rows-long vector fits in
+// the shared-memory budget
+template <typename T>
+static int big_rhs_chunk(int rows) {
+  const size_t per = (size_t)(rows > 0 ? rows : 1) * sizeof(T);
+  return (int)std::max<size_t>(1, std::min<size_t>(4, kStageBudget / per));
+}
+
+template <typename T>
+int launch_apply_big_up(const LevelDev& Lv, double* x, int64_t ldx, int nrhs, double* ubuf,
+                        int64_t ldu, double* tmp, cudaStream_t s) {
+  if (!Lv.ncell || !Lv.max_nI) return 0;
+  const int rc = big_rhs_chunk<T>(Lv.max_nI);
+  const size_t sm = (size_t)Lv.max_nI * rc * sizeof(T);
+  k_apply_big_up1<T><<<dim3((Lv.max_nI + kBigRows - 1) / kBigRows, Lv.ncell), kBigRows, sm, s>>>(
+      Lv, x, ldx, nrhs, rc, tmp, ldu);
+  const int rows = std::max(Lv.max_nI, Lv.max_nB);
+  k_apply_big_up2<T><<<dim3((rows + kBigRows - 1) / kBigRows, Lv.ncell), kBigRows, sm, s>>>(
+      Lv, x, ldx, nrhs, rc, ubuf, ldu, tmp, ldu);
+  return 2;
+}
+
+template <typename T>
+int launch_apply_big_down(const LevelDev& Lv, double* x, int64_t ldx, int nrhs, double* tmp,
+                          int64_t ldt, cudaStream_t s) {
+  if (!Lv.ncell || !Lv.max_nI) return 0;
+  const unsigned gx = (Lv.max_nI + kBigWarps - 1) / kBigWarps;
+  const int rcb = big_rhs_chunk<T>(Lv.max_nB);
+  k_apply_big_down1<T><<<dim3(gx, Lv.ncell), 32 * kBigWarps,
+                         (size_t)std::max(Lv.max_nB, 1) * rcb * sizeof(T), s>>>(Lv, x, ldx, nrhs,
+                                                                                rcb, tmp, ldt);
+  const int rci = big_rhs_chunk<T>(Lv.max_nI);
+  k_apply_big_down2<T><<<dim3(gx, Lv.ncell), 32 * kBigWarps, (size_t)Lv.max_nI * rci * sizeof(T),
+                         s>>>(Lv, x, ldx, nrhs, rci, tmp, ldt);
+  return 2;
+}
+
 template <typename T>
 void launch_apply_group_up(const LevelDev& Lv, const PhaseDev& Ph, int gather, double* x,
                            int64_t ldx, int nrhs, const double* ubuf, int64_t ldu, cudaStream_t s) {
@@ -716,6 +932,10 @@ int configure_apply_kernels() {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_leaf_down<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_group_up_warp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_group_down_warp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_big_up1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_big_up2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_big_down1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_big_down2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   return e == cudaSuccess ? 0 : -1;
 }
 
@@ -727,6 +947,10 @@ int configure_apply_kernels() {
                                          int, const double*, int64_t, cudaStream_t);               \
   template void launch_apply_group_down<T>(const LevelDev&, const PhaseDev&, double*, int64_t, int, \
                                            cudaStream_t);                                          \
+  template int launch_apply_big_up<T>(const LevelDev&, double*, int64_t, int, double*, int64_t,   \
+                                      double*, cudaStream_t);                                      \
+  template int launch_apply_big_down<T>(const LevelDev&, double*, int64_t, int, double*, int64_t,  \
+                                        cudaStream_t);                                             \
   template int configure_apply_kernels<T>();
 
 RHIF_APPLY_INST(double)

@@ -159,8 +159,10 @@ __device__ void cta_syrk_lower(T* C, int64_t ldc, const T* P, int64_t ldp, int r
 // One 64 x 64 tile of a general product: acc[a][b] = sum_{k < K} fa(i, k) * fb(k, j)
 // for i = ti + ty + 16a < M, j = tj + tx + 16b < N (tx = tid % 16, ty = tid / 16);
 // fa / fb are element accessors, so operands may be gathered, transposed or
-// concatenated.  Needs 2 * kKC * (kTile + 1) elements of shared memory.
-template <typename T, class FA, class FB>
+// concatenated.  AK / BK: consecutive threads load consecutive k of A / B
+// (operand contiguous along k) instead of consecutive rows / columns.
+// Needs 2 * kKC * (kTile + 1) elements of shared memory.
+template <typename T, bool AK = false, bool BK = false, class FA, class FB>
 __device__ void cta_tile_product(int ti, int tj, int M, int N, int K, FA fa, FB fb, T* sm,
                                  T (&acc)[4][4]) {
   T* sa = sm;
@@ -174,8 +176,11 @@ __device__ void cta_tile_product(int ti, int tj, int M, int N, int K, FA fa, FB 
   for (int kc = 0; kc < K; kc += kKC) {
     const int kk = min(kKC, K - kc);
     for (int idx = tid; idx < kTile * kKC; idx += kThreads) {
-      const int i = idx % kTile, k = idx / kTile;
+      const int i = AK ? idx / kKC : idx % kTile, k = AK ? idx % kKC : idx / kTile;
       sa[k * (kTile + 1) + i] = (ti + i < M && k < kk) ? fa(ti + i, kc + k) : T(0);
+    }
+    for (int idx = tid; idx < kTile * kKC; idx += kThreads) {
+      const int i = BK ? idx / kKC : idx % kTile, k = BK ? idx % kKC : idx / kTile;
       sb[k * (kTile + 1) + i] = (tj + i < N && k < kk) ? fb(kc + k, tj + i) : T(0);
     }
     __syncthreads();

@@ -509,28 +509,32 @@ k_leaf_stream(GeoDev G, LevelDev Lv, const double* diag, const double* off, int*
 // level >= 1 fronts: extend-add of the children's frames, children in a fixed order
 // ---------------------------------------------------------------------------
 
+// Extend-add of child slot `slot` of every parent cell: the child's Schur
+// complement (lower triangle of its frame) is added into the parent front
+// through the position map.  A child's positions map to distinct parent
+// positions, so the CTAs of one launch (a chunk of one child's entries each)
+// write disjoint entries; slots run as successive launches, so the sum over
+// the children of a parent is taken in slot order, as a fixed-order gather.
 template <typename T>
-__global__ void k_extend_add(LevelDev cur, LevelDev prev) {
-  const int c = blockIdx.x;
+__global__ void k_extend_add(LevelDev cur, LevelDev prev, int slot, int chunk) {
+  const int c = blockIdx.y;
+  const int k = cur.ea_off[c] + slot;
+  if (k >= cur.ea_off[c + 1]) return;
   const int n = cur.nI[c] + cur.nB[c];
   T* F = (T*)cur.front + cur.front_off[c];
-  for (int64_t idx = threadIdx.x; idx < (int64_t)n * n; idx += blockDim.x) F[idx] = T(0);
-  __syncthreads();
-  for (int k = cur.ea_off[c]; k < cur.ea_off[c + 1]; ++k) {
-    const int pc = cur.ea_child[k];
-    const int* map = cur.ea_map + cur.ea_map_off[k];
-    const int nbc = prev.nB[pc];
-    int ldc;
-    const T* Fc = frame_of<T>(prev, pc, &ldc);
-    for (int64_t idx = threadIdx.x; idx < (int64_t)nbc * nbc; idx += blockDim.x) {
-      const int i = (int)(idx % nbc), j = (int)(idx / nbc);
-      if (i < j) continue;
-      const int pi = map[i], pj = map[j];
-      if (pi < 0 || pj < 0) continue;
-      const int r = max(pi, pj), s = min(pi, pj);
-      F[r + (int64_t)s * n] += Fc[i + (int64_t)j * ldc];
-    }
-    __syncthreads();
+  const int pc = cur.ea_child[k];
+  const int* map = cur.ea_map + cur.ea_map_off[k];
+  const int nbc = prev.nB[pc];
+  int ldc;
+  const T* Fc = frame_of<T>(prev, pc, &ldc);
+  const int64_t e0 = (int64_t)blockIdx.x * chunk, e1 = min(e0 + chunk, (int64_t)nbc * nbc);
+  for (int64_t idx = e0 + threadIdx.x; idx < e1; idx += blockDim.x) {
+    const int i = (int)(idx % nbc), j = (int)(idx / nbc);
+    if (i < j) continue;
+    const int pi = map[i], pj = map[j];
+    if (pi < 0 || pj < 0) continue;
+    const int r = max(pi, pj), q = min(pi, pj);
+    F[r + (int64_t)q * n] += Fc[i + (int64_t)j * ldc];
   }
 }
 
@@ -621,6 +625,70 @@ __global__ void __launch_bounds__(kThreads) k_front_schur(LevelDev Lv) {
   cta_syrk_tile(F, n, F, n, nI + a * kTile, nI + b * kTile, n, n, 0, nI, (T*)smraw);
 }
 
+// Explicit inverse of the interior factor L of large fronts, for the
+// many-CTA application of the factor: one CTA per (cell, 64-column block J)
+// solves L X[:, J] = E[:, J] by 64-row blocks from the diagonal down
+// (tile product with the rows above, then a per-column solve with the
+// diagonal block staged in shared memory) into X (per-cell offset xoff[c],
+// column-major, leading dimension nI); k_front_inv_store then overwrites the
+// lower triangle of L with X.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_front_trinv(LevelDev Lv, T* X, const int64_t* xoff) {
+  extern __shared__ unsigned char smraw[];
+  T* sm = (T*)smraw;
+  const int c = blockIdx.y;
+  const int nI = Lv.nI[c], n = nI + Lv.nB[c];
+  const int J0 = blockIdx.x * kTile;
+  if (J0 >= nI) return;
+  const int nc = min(kTile, nI - J0);
+  const T* F = (const T*)Lv.front + Lv.front_off[c];
+  T* Xc = X + xoff[c];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  auto fa = [&](int i, int k) { return F[i + (int64_t)(J0 + k) * n]; };
+  auto fb = [&](int k, int j) { return Xc[(J0 + k) + (int64_t)(J0 + j) * nI]; };
+  for (int I0 = J0; I0 < nI; I0 += kTile) {
+    const int nr = min(kTile, nI - I0);
+    T acc[4][4];
+    cta_tile_product<T, false, true>(I0, 0, nI, nc, I0 - J0, fa, fb, sm, acc);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int i = ty + 16 * a, j = tx + 16 * b;
+        if (i < nr && j < nc)
+          Xc[(I0 + i) + (int64_t)(J0 + j) * nI] = (I0 + i == J0 + j ? T(1) : T(0)) - acc[a][b];
+      }
+    T* Rb = sm;   // L[I, I], [kTile][kTile + 1]
+    for (int idx = tid; idx < nr * nr; idx += blockDim.x) {
+      const int i = idx / nr, q = idx % nr;
+      Rb[i * (kTile + 1) + q] = q <= i ? F[(I0 + i) + (int64_t)(I0 + q) * n] : T(0);
+    }
+    __syncthreads();
+    for (int j = tid; j < nc; j += blockDim.x) {
+      T* col = Xc + (int64_t)(J0 + j) * nI + I0;
+      for (int i = 0; i < nr; ++i) {
+        T v = col[i];
+        for (int q = 0; q < i; ++q) v -= Rb[i * (kTile + 1) + q] * col[q];
+        col[i] = v / Rb[i * (kTile + 1) + i];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void k_front_inv_store(LevelDev Lv, const T* X, const int64_t* xoff) {
+  const int c = blockIdx.y;
+  const int nI = Lv.nI[c], n = nI + Lv.nB[c];
+  T* F = (T*)Lv.front + Lv.front_off[c];
+  const T* Xc = X + xoff[c];
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)nI * nI;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx % nI), j = (int)(idx / nI);
+    if (i >= j) F[i + (int64_t)j * n] = Xc[idx];
+  }
+}
+
 // ---------------------------------------------------------------------------
 // block Jacobi preconditioning (Sec. 2.3)
 // ---------------------------------------------------------------------------
@@ -650,6 +718,19 @@ __global__ void __launch_bounds__(kThreads) k_precond_diag(LevelDev Lv, PhaseDev
   __syncthreads();
   if (!cta_partial_chol(Lg, sz, sz, sz, sm) && threadIdx.x == 0)
     report(status, RHIF_ERR_NOT_SPD, Lv.level, kKindGroup, g);
+  if (!Ph.Linv) return;
+  __syncthreads();
+  // explicit inverse of L_g by forward substitution, one column per thread
+  T* Li = (T*)Ph.Linv + Ph.pre_off[b];
+  for (int j = threadIdx.x; j < sz; j += blockDim.x) {
+    T* x = Li + (int64_t)j * sz;
+    for (int i = 0; i < j; ++i) x[i] = T(0);
+    for (int i = j; i < sz; ++i) {
+      T v = i == j ? T(1) : T(0);
+      for (int k = j; k < i; ++k) v -= Lg[i + (int64_t)k * sz] * x[k];
+      x[i] = v / Lg[i + (int64_t)i * sz];
+    }
+  }
 }
 
 // frame <- D^{-1} frame D^{-T}, D = block diag of the L_g of the frame's groups
@@ -721,10 +802,10 @@ __global__ void __launch_bounds__(kThreads) k_precond_scale(LevelDev Lv, PhaseDe
 }
 
 // Large frames: D^{-1} F D^{-T} spread over many CTAs.  The frame is first
-// made symmetric; then one CTA per (cell, preconditioned segment g, chunk of
-// `cw` columns) applies L_g^{-1} to the rows of g, and one CTA per (cell,
-// segment h, chunk of rows) applies L_h^{-T} to the columns of h.  Each CTA
-// stages its |g| x cw block in shared memory, one column (row) per thread.
+// made symmetric; then one CTA per (cell, preconditioned segment g, block of
+// 64 columns) applies L_g^{-1} to the rows of g, and one CTA per (cell,
+// segment h, block of 64 rows) applies L_h^{-T} to the columns of h, both as
+// tile products with the explicit inverses computed with the L_g.
 
 template <typename T>
 __global__ void k_frame_symmetrize(LevelDev Lv) {
@@ -741,87 +822,79 @@ __global__ void k_frame_symmetrize(LevelDev Lv) {
   }
 }
 
-// Locate task `bid` among (cell, preconditioned segment, chunk) triples.
-__device__ inline bool frame_task(const LevelDev& Lv, const PhaseDev& Ph, int64_t bid, int cw,
-                                  int* cell, int* seg, int* chunk) {
-  for (int c = 0; c < Lv.ncell; ++c) {
-    const int nb = Lv.nB[c];
-    const int nch = (nb + cw - 1) / cw;
-    for (int q = Lv.seg_off[c]; q < Lv.seg_off[c + 1]; ++q) {
-      if (Ph.group_pre[Lv.seg_group[q]] < 0) continue;
-      if (bid < nch) {
-        *cell = c;
-        *seg = q;
-        *chunk = (int)bid;
-        return true;
+// Task `bid` of the tile-product scaling: the (cell, segment) pair whose
+// 64-wide blocks hold it (binary search of the prefix sums) and the block.
+__device__ inline void scale_task_of(const PhaseDev& Ph, int64_t bid, int* cell, int* seg,
+                                     int* blk) {
+  int lo = 0, hi = Ph.nscale_task - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (Ph.scale_off[mid] <= bid) lo = mid;
+    else hi = mid - 1;
+  }
+  *cell = Ph.scale_task[2 * lo];
+  *seg = Ph.scale_task[2 * lo + 1];
+  *blk = (int)(bid - Ph.scale_off[lo]);
+}
+
+// F[g, J] <- L_g^{-1} F[g, J] for the 64 columns J of the task's block, as
+// tile products with the explicit inverse; row tiles bottom-up so the update
+// is in place (a row tile depends only on the rows above and at it).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_frame_rows_tp(LevelDev Lv, PhaseDev Ph) {
+  extern __shared__ unsigned char smraw[];
+  T* sm = (T*)smraw;
+  int c, q, blk;
+  scale_task_of(Ph, blockIdx.x, &c, &q, &blk);
+  int ld;
+  T* Fr = frame_of<T>(Lv, c, &ld);
+  const int nb = Lv.nB[c];
+  const int g = Lv.seg_group[q], pos = Lv.seg_pos[q], sz = Lv.group_size[g];
+  const T* Li = (const T*)Ph.Linv + Ph.pre_off[Ph.group_pre[g]];
+  const int j0 = blk * kTile, ncol = min(kTile, nb - j0);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  auto fa = [&](int i, int k) { return Li[i + (int64_t)k * sz]; };
+  auto fb = [&](int k, int j) { return Fr[(pos + k) + (int64_t)(j0 + j) * ld]; };
+  for (int ti = ((sz - 1) / kTile) * kTile; ti >= 0; ti -= kTile) {
+    T acc[4][4];
+    cta_tile_product<T, false, true>(ti, 0, sz, ncol, min(sz, ti + kTile), fa, fb, sm, acc);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int i = ti + ty + 16 * a, j = tx + 16 * b;
+        if (i < sz && j < ncol) Fr[(pos + i) + (int64_t)(j0 + j) * ld] = acc[a][b];
       }
-      bid -= nch;
-    }
-  }
-  return false;
-}
-
-template <typename T>
-__global__ void k_frame_rows(LevelDev Lv, PhaseDev Ph, int cw) {
-  extern __shared__ unsigned char smraw[];
-  T* blk = (T*)smraw;   // blk[a * cw + t]
-  int c, q, ch;
-  if (!frame_task(Lv, Ph, blockIdx.x, cw, &c, &q, &ch)) return;
-  int ld;
-  T* Fr = frame_of<T>(Lv, c, &ld);
-  const int nb = Lv.nB[c];
-  const int g = Lv.seg_group[q], pos = Lv.seg_pos[q], sz = Lv.group_size[g];
-  const T* Lg = (const T*)Ph.Lbuf + Ph.pre_off[Ph.group_pre[g]];
-  const int j0 = ch * cw;
-  const int ncol = min(cw, nb - j0);
-  for (int idx = threadIdx.x; idx < sz * cw; idx += blockDim.x) {
-    const int a = idx / cw, t = idx % cw;
-    blk[idx] = t < ncol ? Fr[(pos + a) + (int64_t)(j0 + t) * ld] : T(0);
-  }
-  __syncthreads();
-  for (int t = threadIdx.x; t < ncol; t += blockDim.x) {
-    for (int a = 0; a < sz; ++a) {
-      T v = blk[a * cw + t];
-      for (int k = 0; k < a; ++k) v -= Lg[a + (int64_t)k * sz] * blk[k * cw + t];
-      blk[a * cw + t] = v / Lg[a + (int64_t)a * sz];
-    }
-  }
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < sz * cw; idx += blockDim.x) {
-    const int a = idx / cw, t = idx % cw;
-    if (t < ncol) Fr[(pos + a) + (int64_t)(j0 + t) * ld] = blk[idx];
   }
 }
 
+// F[I, h] <- F[I, h] L_h^{-T} for the 64 rows I of the task's block; column
+// tiles right to left so the update is in place.
 template <typename T>
-__global__ void k_frame_cols(LevelDev Lv, PhaseDev Ph, int cw) {
+__global__ void __launch_bounds__(kThreads) k_frame_cols_tp(LevelDev Lv, PhaseDev Ph) {
   extern __shared__ unsigned char smraw[];
-  T* blk = (T*)smraw;   // blk[a * cw + t]: column pos+a, row i0+t
-  int c, q, ch;
-  if (!frame_task(Lv, Ph, blockIdx.x, cw, &c, &q, &ch)) return;
+  T* sm = (T*)smraw;
+  int c, q, blk;
+  scale_task_of(Ph, blockIdx.x, &c, &q, &blk);
   int ld;
   T* Fr = frame_of<T>(Lv, c, &ld);
   const int nb = Lv.nB[c];
-  const int g = Lv.seg_group[q], pos = Lv.seg_pos[q], sz = Lv.group_size[g];
-  const T* Lg = (const T*)Ph.Lbuf + Ph.pre_off[Ph.group_pre[g]];
-  const int i0 = ch * cw;
-  const int nrow = min(cw, nb - i0);
-  for (int idx = threadIdx.x; idx < sz * cw; idx += blockDim.x) {
-    const int a = idx / cw, t = idx % cw;
-    blk[idx] = t < nrow ? Fr[(i0 + t) + (int64_t)(pos + a) * ld] : T(0);
-  }
-  __syncthreads();
-  for (int t = threadIdx.x; t < nrow; t += blockDim.x) {
-    for (int a = 0; a < sz; ++a) {
-      T v = blk[a * cw + t];
-      for (int k = 0; k < a; ++k) v -= Lg[a + (int64_t)k * sz] * blk[k * cw + t];
-      blk[a * cw + t] = v / Lg[a + (int64_t)a * sz];
-    }
-  }
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < sz * cw; idx += blockDim.x) {
-    const int a = idx / cw, t = idx % cw;
-    if (t < nrow) Fr[(i0 + t) + (int64_t)(pos + a) * ld] = blk[idx];
+  const int h = Lv.seg_group[q], pos = Lv.seg_pos[q], sz = Lv.group_size[h];
+  const T* Li = (const T*)Ph.Linv + Ph.pre_off[Ph.group_pre[h]];
+  const int i0 = blk * kTile, nrow = min(kTile, nb - i0);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  auto fa = [&](int i, int k) { return Fr[(i0 + i) + (int64_t)(pos + k) * ld]; };
+  auto fb = [&](int k, int j) { return Li[j + (int64_t)k * sz]; };
+  for (int tj = ((sz - 1) / kTile) * kTile; tj >= 0; tj -= kTile) {
+    T acc[4][4];
+    cta_tile_product<T>(0, tj, nrow, sz, min(sz, tj + kTile), fa, fb, sm, acc);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int i = ty + 16 * a, j = tj + tx + 16 * b;
+        if (i < nrow && j < sz) Fr[(i0 + i) + (int64_t)(pos + j) * ld] = acc[a][b];
+      }
   }
 }
 
@@ -1400,9 +1473,25 @@ void launch_leaf_elim(const GeoDev& G, const LevelDev& Lv, const double* diag, c
 }
 
 template <typename T>
-void launch_extend_add(const LevelDev& cur, const LevelDev& prev, cudaStream_t s) {
-  if (!cur.ncell) return;
-  k_extend_add<T><<<cur.ncell, kThreads, 0, s>>>(cur, prev);
+int launch_extend_add(const LevelDev& cur, const LevelDev& prev, int64_t front_total, int slots,
+                      cudaStream_t s) {
+  if (!cur.ncell) return 0;
+  cudaMemsetAsync(cur.front, 0, (size_t)front_total * sizeof(T), s);
+  const int chunk = 16 * kThreads;
+  const int64_t nb = prev.max_nB;
+  const unsigned chunks = (unsigned)((nb * nb + chunk - 1) / chunk);
+  if (!chunks) return 0;
+  for (int slot = 0; slot < slots; ++slot)
+    k_extend_add<T><<<dim3(chunks, cur.ncell), kThreads, 0, s>>>(cur, prev, slot, chunk);
+  return slots;
+}
+
+template <typename T>
+void launch_front_invert(const LevelDev& Lv, T* X, const int64_t* xoff, cudaStream_t s) {
+  if (!Lv.ncell || !Lv.max_nI) return;
+  const unsigned nb = (unsigned)((Lv.max_nI + kTile - 1) / kTile);
+  k_front_trinv<T><<<dim3(nb, Lv.ncell), kThreads, kTile * (kTile + 1) * sizeof(T), s>>>(Lv, X, xoff);
+  k_front_inv_store<T><<<dim3(64, Lv.ncell), 256, 0, s>>>(Lv, X, xoff);
 }
 
 template <typename T>
@@ -1449,20 +1538,13 @@ void launch_precond_scale(const LevelDev& Lv, const PhaseDev& Ph, cudaStream_t s
 }
 
 template <typename T>
-int frame_chunk_width(int max_group) {
-  int cw = (int)((160 * 1024) / ((size_t)(max_group > 0 ? max_group : 1) * sizeof(T)));
-  cw = cw / 32 * 32;
-  return cw < 32 ? 32 : (cw > 64 ? 64 : cw);
-}
-
-template <typename T>
-void launch_precond_scale_big(const LevelDev& Lv, const PhaseDev& Ph, int64_t tasks, int cw,
+void launch_precond_scale_big(const LevelDev& Lv, const PhaseDev& Ph, int64_t tasks,
                               cudaStream_t s) {
   k_frame_symmetrize<T><<<dim3(64, min(Lv.ncell, 65535)), 256, 0, s>>>(Lv);
   if (tasks <= 0) return;
-  const size_t sm = (size_t)Lv.max_group * cw * sizeof(T);
-  k_frame_rows<T><<<(unsigned)tasks, cw, sm, s>>>(Lv, Ph, cw);
-  k_frame_cols<T><<<(unsigned)tasks, cw, sm, s>>>(Lv, Ph, cw);
+  const size_t sm = 2 * kKC * (kTile + 1) * sizeof(T);
+  k_frame_rows_tp<T><<<(unsigned)tasks, kThreads, sm, s>>>(Lv, Ph);
+  k_frame_cols_tp<T><<<(unsigned)tasks, kThreads, sm, s>>>(Lv, Ph);
 }
 
 template <typename T>
@@ -1547,10 +1629,6 @@ int configure_factor_kernels() {
     e = cudaFuncSetAttribute(k_precond_scale<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_leaf_stream<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_frame_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_frame_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   return e == cudaSuccess ? 0 : -1;
 }
 
@@ -1558,16 +1636,16 @@ int configure_factor_kernels() {
   template size_t leaf_smem_bytes<T>(int, int, int, int, int);                                    \
   template void launch_leaf_elim<T>(const GeoDev&, const LevelDev&, const double*, const double*, \
                                     int*, cudaStream_t);                                          \
-  template void launch_extend_add<T>(const LevelDev&, const LevelDev&, cudaStream_t);             \
+  template int launch_extend_add<T>(const LevelDev&, const LevelDev&, int64_t, int, cudaStream_t); \
   template void launch_partial_chol<T>(const LevelDev&, int*, cudaStream_t);                      \
+  template void launch_front_invert<T>(const LevelDev&, T*, const int64_t*, cudaStream_t);       \
   template void launch_front_panel<T>(const LevelDev&, int, int*, cudaStream_t);                  \
   template void launch_front_trailing<T>(const LevelDev&, int, int64_t, cudaStream_t);            \
   template void launch_front_schur<T>(const LevelDev&, int64_t, cudaStream_t);                    \
   template void launch_precond_diag<T>(const LevelDev&, const PhaseDev&, int*, cudaStream_t);     \
   template void launch_precond_scale<T>(const LevelDev&, const PhaseDev&, cudaStream_t);          \
-  template void launch_precond_scale_big<T>(const LevelDev&, const PhaseDev&, int64_t, int,       \
+  template void launch_precond_scale_big<T>(const LevelDev&, const PhaseDev&, int64_t,            \
                                             cudaStream_t);                                        \
-  template int frame_chunk_width<T>(int);                                                         \
   template void launch_skel<T>(const LevelDev&, const PhaseDev&, uint8_t*, double, int*, int64_t, \
                                cudaStream_t);                                                     \
   template size_t skel_smem_bytes<T>(int);                                                        \

@@ -19,8 +19,16 @@ size_t leaf_smem_bytes(int max_nI, int max_nB, int max_w, int leaf, int d);
 template <typename T>
 void launch_leaf_elim(const GeoDev& G, const LevelDev& Lv, const double* diag, const double* off,
                       int* status, cudaStream_t s);
+// Zero the level's fronts and add the children's Schur complements, one
+// launch per child slot (slots = most children of any cell); returns the
+// number of kernel launches.
 template <typename T>
-void launch_extend_add(const LevelDev& cur, const LevelDev& prev, cudaStream_t s);
+int launch_extend_add(const LevelDev& cur, const LevelDev& prev, int64_t front_total, int slots,
+                      cudaStream_t s);
+// Overwrite the interior factor L of every front of the level with L^{-1}
+// (X: scratch of sum_c nI_c^2 elements at per-cell offsets xoff).
+template <typename T>
+void launch_front_invert(const LevelDev& Lv, T* X, const int64_t* xoff, cudaStream_t s);
 template <typename T>
 void launch_partial_chol(const LevelDev& Lv, int* status, cudaStream_t s);
 template <typename T>
@@ -35,11 +43,12 @@ template <typename T>
 void launch_precond_diag(const LevelDev& Lv, const PhaseDev& Ph, int* status, cudaStream_t s);
 template <typename T>
 void launch_precond_scale(const LevelDev& Lv, const PhaseDev& Ph, cudaStream_t s);
+// Tile-product scaling of large frames; needs Ph.Linv (filled by
+// launch_precond_diag when non-null) and the scale_task tables; `tasks` is
+// the total number of 64-wide blocks.
 template <typename T>
-void launch_precond_scale_big(const LevelDev& Lv, const PhaseDev& Ph, int64_t tasks, int cw,
+void launch_precond_scale_big(const LevelDev& Lv, const PhaseDev& Ph, int64_t tasks,
                               cudaStream_t s);
-template <typename T>
-int frame_chunk_width(int max_group);
 template <typename T>
 void launch_skel(const LevelDev& Lv, const PhaseDev& Ph, uint8_t* alive, double tol, int* status,
                  int64_t max_m_elems, cudaStream_t s);
@@ -63,6 +72,16 @@ void launch_apply_cell_up(const LevelDev& Lv, double* x, int64_t ldx, int nrhs, 
                           int64_t ldu, cudaStream_t s);
 template <typename T>
 void launch_apply_cell_down(const LevelDev& Lv, double* x, int64_t ldx, int nrhs, cudaStream_t s);
+// Cell sweeps of a level whose fronts hold L^{-1} (launch_front_invert): two
+// many-CTA launches per direction; tmp is a scratch column set (leading
+// dimension ldu / ldt) of at least the level's DOF-list length.  Return the
+// number of kernel launches.
+template <typename T>
+int launch_apply_big_up(const LevelDev& Lv, double* x, int64_t ldx, int nrhs, double* ubuf,
+                        int64_t ldu, double* tmp, cudaStream_t s);
+template <typename T>
+int launch_apply_big_down(const LevelDev& Lv, double* x, int64_t ldx, int nrhs, double* tmp,
+                          int64_t ldt, cudaStream_t s);
 template <typename T>
 void launch_apply_group_up(const LevelDev& Lv, const PhaseDev& Ph, int gather, double* x,
                            int64_t ldx, int nrhs, const double* ubuf, int64_t ldu, cudaStream_t s);

@@ -180,6 +180,7 @@ struct LevelStore {
   // algorithmic work of one sweep direction of the application, per right-hand side
   double cell_flops = 0, cell_bytes = 0;
   std::vector<double> grp_flops, grp_bytes;   // per phase
+  bool big_apply = false;   // fronts hold L^{-1}: many-CTA cell sweeps
 };
 
 }  // namespace rhif
@@ -200,7 +201,9 @@ struct rhif_handle {
   // reusable work space
   double* ubuf = nullptr;
   int64_t ubuf_elems = 0;
-  int64_t ub_len = 0;   // max over levels of sum nB
+  int64_t ub_len = 0;   // scratch column: max over levels of sum nB, then the interior part
+  int64_t ui_len = 0;   // max DOF-list length of the levels with big_apply
+  int64_t ui_base = 0;  // offset of the interior part in the scratch column
   double* work = nullptr;
   int64_t work_elems = 0;
   double flops = 0.0, apply_bytes = 0.0, factor_ms = 0.0;
@@ -500,8 +503,11 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
         H->apply_bytes += 2.0 * elem * (nI * (nI + 1) / 2 + nI * nB);
       }
       {
-        Launch t(kCatExtendAdd, s, 0.0, double(P.front_total) * elem);
-        launch_extend_add<T>(S.dev, H->levels[lvl - 1].dev, s);
+        Launch t(kCatExtendAdd, s, 0.0, double(P.front_total) * elem, 0);
+        int slots = 0;
+        for (int c = 0; c < P.ncell(); ++c) slots = std::max(slots, P.ea_off[c + 1] - P.ea_off[c]);
+        add_launches(kCatExtendAdd,
+                     launch_extend_add<T>(S.dev, H->levels[lvl - 1].dev, P.front_total, slots, s));
       }
       if (P.max_n >= H->big_front && P.ncell() <= kBigFrontCells) {
         // few large fronts: panel / trailing-tile / Schur-tile launches over all fronts
@@ -518,6 +524,26 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
         for (int c = 0; c < P.ncell(); ++c) tiles += front_schur_tiles(P.nI[c], P.nB[c]);
         launch_front_schur<T>(S.dev, tiles, s);
         add_launches(kCatPartialChol, tiles > 0 ? 1 : 0);
+        // L -> L^{-1} in place, for the many-CTA application of these fronts
+        std::vector<int64_t> xoff(P.ncell());
+        int64_t xtot = 0;
+        for (int c = 0; c < P.ncell(); ++c) {
+          xoff[c] = xtot;
+          xtot += ((int64_t)P.nI[c] * P.nI[c] + 3) & ~int64_t(3);
+        }
+        void* X = nullptr;
+        void* xo = nullptr;
+        if ((rc = H->mem.get(&X, xtot * elem))) return rc;
+        if ((rc = H->mem.get(&xo, xoff.size() * sizeof(int64_t)))) return rc;
+        CK(cudaMemcpyAsync(xo, xoff.data(), xoff.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
+                           s));
+        launch_front_invert<T>(S.dev, (T*)X, (const int64_t*)xo, s);
+        add_launches(kCatPartialChol, 2);
+        CK(cudaStreamSynchronize(s));   // xoff is a host vector of this scope
+        H->mem.release(X);
+        H->mem.release(xo);
+        S.big_apply = true;
+        H->ui_len = std::max<int64_t>(H->ui_len, P.gid_off.back());
       } else {
         Launch t(kCatPartialChol, s, lvl_flops, double(P.front_total) * elem);
         launch_partial_chol<T>(S.dev, H->status, s);
@@ -542,25 +568,49 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
           const double g = P.group_size[gi];
           sflops += 2.0 * g * g * P.nB[c];
         }
+      Packer scale_tab;   // host copy must outlive the upload (synchronized below)
+      void* scale_dev = nullptr;
       if (!ph.pre_group.empty()) {
+        const bool fits = (size_t)P.max_nB * P.max_nB * elem <= 200 * 1024;
+        const bool big = H->big_frame > 0 ? P.max_nB >= H->big_frame : !fits;
+        int64_t blocks = 0;
+        if (big) {   // large frames: tile products with explicit inverses over many CTAs
+          std::vector<int> task;
+          std::vector<int64_t> off;
+          for (int c = 0; c < P.ncell(); ++c)
+            for (int q = P.seg_off[c]; q < P.seg_off[c + 1]; ++q)
+              if (ph.group_pre[P.seg_group[q]] >= 0) {
+                task.push_back(c);
+                task.push_back(q);
+                off.push_back(blocks);
+                blocks += (P.nB[c] + 63) / 64;
+              }
+          const size_t o_task = scale_tab.add(task), o_off = scale_tab.add(off);
+          if ((rc = H->mem.get(&scale_dev, scale_tab.host.size()))) return rc;
+          CK(cudaMemcpyAsync(scale_dev, scale_tab.host.data(), scale_tab.host.size(),
+                             cudaMemcpyHostToDevice, s));
+          D.scale_task = (const int*)((char*)scale_dev + o_task);
+          D.scale_off = (const int64_t*)((char*)scale_dev + o_off);
+          D.nscale_task = (int)off.size();
+          if ((rc = H->mem.get(&D.Linv, ph.pre_total * elem))) return rc;
+        }
         {
           Launch t(kCatPrecondDiag, s, dflops, 0.0);
           launch_precond_diag<T>(S.dev, D, H->status, s);
         }
         {
           Launch t(kCatPrecondScale, s, sflops, 0.0);
-          const int cw = frame_chunk_width<T>(P.max_group);
-          const bool fits = (size_t)P.max_nB * P.max_nB * elem <= 200 * 1024;
-          const bool big = H->big_frame > 0 ? P.max_nB >= H->big_frame : !fits;
-          if (!big || (size_t)P.max_group * cw * elem > 200 * 1024) {
+          if (!big) {
             launch_precond_scale<T>(S.dev, D, s);
-          } else {   // large frames: row / column block solves over many CTAs
-            int64_t tasks = 0;
-            for (int c = 0; c < P.ncell(); ++c)
-              for (int q = P.seg_off[c]; q < P.seg_off[c + 1]; ++q)
-                if (ph.group_pre[P.seg_group[q]] >= 0) tasks += (P.nB[c] + cw - 1) / cw;
-            launch_precond_scale_big<T>(S.dev, D, tasks, cw, s);
-            add_launches(kCatPrecondScale, tasks > 0 ? 2 : 0);
+          } else {
+            launch_precond_scale_big<T>(S.dev, D, blocks, s);
+            add_launches(kCatPrecondScale, blocks > 0 ? 2 : 0);
+            H->mem.release(D.Linv);
+            H->mem.release(scale_dev);
+            D.Linv = nullptr;
+            D.scale_task = nullptr;
+            D.scale_off = nullptr;
+            D.nscale_task = 0;
           }
         }
       }
@@ -651,6 +701,8 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
     }
   }
   H->mem.release(alive_d);
+  H->ui_base = H->ub_len;
+  H->ub_len += H->ui_len;
   return RHIF_OK;
 }
 
@@ -667,37 +719,38 @@ static int apply_impl(const rhif_handle* Hc, double* y, int64_t ldy, int nrhs, c
     H->ubuf_elems = need;
   }
   const int64_t ldu = H->ub_len;
+  double* tmp = H->ubuf + H->ui_base;
+  auto cell_up = [&](LevelStore& S, int cat) {
+    Launch t(cat, s, S.cell_flops * nrhs, S.cell_bytes * nrhs, S.big_apply ? 0 : 1);
+    if (S.big_apply)
+      add_launches(cat, launch_apply_big_up<T>(S.dev, y, ldy, nrhs, H->ubuf, ldu, tmp, s));
+    else
+      launch_apply_cell_up<T>(S.dev, y, ldy, nrhs, H->ubuf, ldu, s);
+  };
+  auto cell_down = [&](LevelStore& S, int cat) {
+    Launch t(cat, s, S.cell_flops * nrhs, S.cell_bytes * nrhs, S.big_apply ? 0 : 1);
+    if (S.big_apply)
+      add_launches(cat, launch_apply_big_down<T>(S.dev, y, ldy, nrhs, tmp, ldu, s));
+    else
+      launch_apply_cell_down<T>(S.dev, y, ldy, nrhs, s);
+  };
   for (int l = 0; l < L; ++l) {
     LevelStore& S = H->levels[l];
-    {
-      Launch t(l == 0 ? kCatApplyLeafUp : kCatApplyCellUp, s, S.cell_flops * nrhs,
-               S.cell_bytes * nrhs);
-      launch_apply_cell_up<T>(S.dev, y, ldy, nrhs, H->ubuf, ldu, s);
-    }
+    cell_up(S, l == 0 ? kCatApplyLeafUp : kCatApplyCellUp);
     for (size_t p = 0; p < S.phases.size(); ++p) {
       Launch t(kCatApplyGroupUp, s, S.grp_flops[p] * nrhs, S.grp_bytes[p] * nrhs);
       launch_apply_group_up<T>(S.dev, S.phases[p].dev, p == 0, y, ldy, nrhs, H->ubuf, ldu, s);
     }
   }
-  {
-    LevelStore& R = H->levels[L];
-    Launch t(kCatApplyCellUp, s, R.cell_flops * nrhs, R.cell_bytes * nrhs);
-    launch_apply_cell_up<T>(R.dev, y, ldy, nrhs, H->ubuf, ldu, s);
-  }
-  {
-    LevelStore& R = H->levels[L];
-    Launch t(kCatApplyCellDown, s, R.cell_flops * nrhs, R.cell_bytes * nrhs);
-    launch_apply_cell_down<T>(R.dev, y, ldy, nrhs, s);
-  }
+  cell_up(H->levels[L], kCatApplyCellUp);
+  cell_down(H->levels[L], kCatApplyCellDown);
   for (int l = L - 1; l >= 0; --l) {
     LevelStore& S = H->levels[l];
     for (int p = (int)S.phases.size() - 1; p >= 0; --p) {
       Launch t(kCatApplyGroupDown, s, S.grp_flops[p] * nrhs, S.grp_bytes[p] * nrhs);
       launch_apply_group_down<T>(S.dev, S.phases[p].dev, y, ldy, nrhs, s);
     }
-    Launch t(l == 0 ? kCatApplyLeafDown : kCatApplyCellDown, s, S.cell_flops * nrhs,
-             S.cell_bytes * nrhs);
-    launch_apply_cell_down<T>(S.dev, y, ldy, nrhs, s);
+    cell_down(S, l == 0 ? kCatApplyLeafDown : kCatApplyCellDown);
   }
   CK(cudaGetLastError());
   return RHIF_OK;
@@ -1172,19 +1225,28 @@ static int apply_noalloc_impl(const rhif_handle* Hc, double* y, int64_t ldy, int
   rhif_handle* H = const_cast<rhif_handle*>(Hc);
   const int L = H->G.L;
   const int64_t ldu = H->ub_len;
+  double* tmp = ubuf + H->ui_base;
+  auto cell_up = [&](LevelStore& S) {
+    if (S.big_apply) launch_apply_big_up<T>(S.dev, y, ldy, nrhs, ubuf, ldu, tmp, s);
+    else launch_apply_cell_up<T>(S.dev, y, ldy, nrhs, ubuf, ldu, s);
+  };
+  auto cell_down = [&](LevelStore& S) {
+    if (S.big_apply) launch_apply_big_down<T>(S.dev, y, ldy, nrhs, tmp, ldu, s);
+    else launch_apply_cell_down<T>(S.dev, y, ldy, nrhs, s);
+  };
   for (int l = 0; l < L; ++l) {
     LevelStore& S = H->levels[l];
-    launch_apply_cell_up<T>(S.dev, y, ldy, nrhs, ubuf, ldu, s);
+    cell_up(S);
     for (size_t p = 0; p < S.phases.size(); ++p)
       launch_apply_group_up<T>(S.dev, S.phases[p].dev, p == 0, y, ldy, nrhs, ubuf, ldu, s);
   }
-  launch_apply_cell_up<T>(H->levels[L].dev, y, ldy, nrhs, ubuf, ldu, s);
-  launch_apply_cell_down<T>(H->levels[L].dev, y, ldy, nrhs, s);
+  cell_up(H->levels[L]);
+  cell_down(H->levels[L]);
   for (int l = L - 1; l >= 0; --l) {
     LevelStore& S = H->levels[l];
     for (int p = (int)S.phases.size() - 1; p >= 0; --p)
       launch_apply_group_down<T>(S.dev, S.phases[p].dev, y, ldy, nrhs, s);
-    launch_apply_cell_down<T>(S.dev, y, ldy, nrhs, s);
+    cell_down(S);
   }
   CK(cudaGetLastError());
   return RHIF_OK;

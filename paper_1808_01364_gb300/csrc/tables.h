@@ -65,6 +65,10 @@ struct PhaseDev {
   const int64_t* pre_off;
   const int* group_pre;    // per group of the level: index into pre_group or -1
   void* Lbuf;
+  void* Linv;              // explicit L_g^{-1} (same layout as Lbuf) while scaling, else null
+  const int* scale_task;   // (cell, segment) pairs of the tile-product scaling
+  const int64_t* scale_off;  // prefix sums of their 64-wide column / row blocks
+  int nscale_task;
   int nunit, max_n;
   const int* u_group;
   const int* u_nrow;

@@ -1,14 +1,27 @@
 """Benchmark: DOFs/s of PHIF factorization + PCG to relres 1e-10 on one GB300.
 
-Workload (one step = the whole hot path over one problem): the 2D 5-point
-finite-difference problem on a 1023 x 1023 interior grid (N = 1,046,529),
-per-pixel coefficient log10 a ~ U[-4, 4] (seeded), b = 0, f ~ N(0,1), leaf
-16, ID tolerance 1e-3; assembly of A from the per-pixel field, the PHIF
-factorization and PCG to a relative residual of 1e-10, all on the GPU.
-The headline `value` uses the FP32 factor (FP64 PCG); the plain-FP64 factor
-is measured beside it under "fp64".
+Default workload (one step = the whole hot path over one problem): the 2D
+5-point finite-difference problem on a 1023 x 1023 interior grid
+(N = 1,046,529), per-pixel coefficient log10 a ~ U[-4, 4] (seeded), b = 0,
+f ~ N(0,1), leaf 16, ID tolerance 1e-3; assembly of A from the per-pixel
+field, the PHIF factorization and PCG to a relative residual of 1e-10, all on
+the GPU.  The headline `value` uses the FP32 factor (FP64 PCG); the plain-FP64
+factor is measured beside it under "fp64".
+
+--workload selects the other synthetic workloads (same JSON line):
+  c1  2D 127^2, log10 a ~ U[-2,2], leaf 8, tol 1e-3, FP64 factor, PCG to 1e-12
+  c2  the default above
+  c3  3D 7-point 63^3, log10 a ~ U[-3,3], b = 1e-2, leaf 8, faces + edges
+      skeletonized, tol 1e-3, FP32 factor
+  c4  64 independent 2D problems (sides uniform in 127..511, log10 a ~ U[-3,3],
+      leaf 8, tol 1e-3) with 32 right-hand sides each, FP32 factors, batched
+      factor and PCG over 8 streams; DOFs count each problem once
+  c5  differentiable solve on 511^2: log a from a smooth seeded field, forward
+      PHIF solve, loss 0.5 ||u - u_obs||^2, backward (adjoint PCG with the same
+      factor + gradient kernel); FP32 factor, PCG to 1e-10
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                       [--workload c1|c2|c3|c4|c5]
 Under torchrun every rank runs its own independent replica (the path does not
 shard); `value` sums the DOFs of all ranks over the slowest rank's time.
 """
@@ -22,16 +35,20 @@ import statistics
 import subprocess
 import sys
 import tempfile
-import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "DOFs/s factor+PCG to relres 1e-10, mixed vs plain FP64 on GPU; % roofline"
-WORKLOAD = "2d-fd5-1023sq-logunif1e-4..1e4-leaf16-tol1e-3"
 RTOL = 1e-10
-CPU_SAMPLE_SIDE = 511       # bounded oracle sample for cpu_baseline (same recipe, smaller grid)
-REF_STEP_SIDE = 255         # bounded oracle sample per step of --impl reference
+
+WORKLOADS = {
+    "c1": "2d-fd5-127sq-logunif1e-2..1e2-leaf8-tol1e-3-fp64-rtol1e-12",
+    "c2": "2d-fd5-1023sq-logunif1e-4..1e4-leaf16-tol1e-3",
+    "c3": "3d-fd7-63cube-logunif1e-3..1e3-b1e-2-leaf8-tol1e-3-faces+edges",
+    "c4": "batched-64x2d-fd5-sides127..511-logunif1e-3..1e3-leaf8-tol1e-3-32rhs",
+    "c5": "grad-2d-fd5-511sq-smooth-log-a-leaf16-tol1e-3-adjoint",
+}
 
 
 def _args():
@@ -40,38 +57,93 @@ def _args():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     p.add_argument("--fp64-steps", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--side", type=int, default=1023)
     return p.parse_args()
 
 
 # ---------------------------------------------------------------------------
-# the oracle on host cores (cpu_baseline and --impl reference)
+# the oracle on host cores (cpu_baseline and --impl reference): a bounded
+# sample of each workload, the same recipe at a smaller size
 # ---------------------------------------------------------------------------
 
-_ORACLE_SNIPPET = r"""
+_ORACLE_HEAD = r"""
 import sys, time, json
 sys.path.insert(0, {root!r})
 import numpy as np
 import workloads as W
 from oracle import fd, phif
-side = {side}
-p = W.make_problem((side, side), 1e-4, 1e4, 0.0, 16, 1e-3, W.SEED_BASE + 1)
+"""
+
+_ORACLE_BODY = {
+    "2d": r"""
+p = W.make_problem(({side}, {side}), {lo}, {hi}, 0.0, {leaf}, 1e-3, {seed})
 t0 = time.perf_counter()
 A = fd.assemble(p.ns, p.a, p.b)
 F = phif.factor(A, p.ns, p.leaf, p.tol)
 u, it, rr = phif.pcg(A, p.f, M=lambda r: phif.solve(F, r), rtol={rtol})
 t = time.perf_counter() - t0
-print(json.dumps({{"seconds": t, "n": p.n, "iters": it, "relres": rr}}))
-"""
+print(json.dumps({{"seconds": t, "dofs": p.n, "iters": it}}))
+""",
+    "3d": r"""
+p = W.make_problem(({side}, {side}, {side}), 1e-3, 1e3, 1e-2, 8, 1e-3, {seed})
+t0 = time.perf_counter()
+A = fd.assemble(p.ns, p.a, p.b)
+F = phif.factor(A, p.ns, p.leaf, p.tol, edge_skel=True)
+u, it, rr = phif.pcg(A, p.f, M=lambda r: phif.solve(F, r), rtol={rtol})
+t = time.perf_counter() - t0
+print(json.dumps({{"seconds": t, "dofs": p.n, "iters": it}}))
+""",
+    "batch": r"""
+p = W.batched_problems(1, 32, sides=[{side}])[0]
+t0 = time.perf_counter()
+A = fd.assemble(p.ns, p.a, p.b)
+F = phif.factor(A, p.ns, p.leaf, p.tol)
+its = []
+for r in range(p.f.shape[0]):
+    u, it, rr = phif.pcg(A, p.f[r], M=lambda x: phif.solve(F, x), rtol={rtol})
+    its.append(it)
+t = time.perf_counter() - t0
+print(json.dumps({{"seconds": t, "dofs": p.n, "iters": max(its)}}))
+""",
+    "grad": r"""
+import scipy.sparse.linalg as spla
+ns = ({side}, {side})
+log_star, f = W.inverse_problem(ns)
+u_obs = spla.spsolve(fd.assemble(ns, np.exp(log_star), 0.0).tocsc(), f)
+log_a = 0.3 * W.gaussian_bump_log_field(ns, {seed})
+t0 = time.perf_counter()
+a = np.exp(log_a)
+A = fd.assemble(ns, a, 0.0)
+F = phif.factor(A, ns, 16, 1e-3)
+u, it, rr = phif.pcg(A, f, M=lambda r: phif.solve(F, r), rtol={rtol})
+lam, it2, rr2 = phif.pcg(A, u - u_obs, M=lambda r: phif.solve(F, r), rtol={rtol})
+g = fd.dA_dlog_a(ns, a, u, lam)
+t = time.perf_counter() - t0
+print(json.dumps({{"seconds": t, "dofs": int(np.prod(ns)), "iters": max(it, it2)}}))
+""",
+}
+
+# (body, side, format fields, description) of the bounded cpu_baseline sample
+_SAMPLES = {
+    "c1": ("2d", 127, dict(lo=1e-2, hi=1e2, leaf=8, rtol=1e-12), "the full 127^2 workload"),
+    "c2": ("2d", 511, dict(lo=1e-4, hi=1e4, leaf=16, rtol=RTOL), "a 511^2 grid of the same recipe"),
+    "c3": ("3d", 31, dict(rtol=RTOL), "a 31^3 grid of the same recipe"),
+    "c4": ("batch", 127, dict(rtol=RTOL), "one 127^2 problem of the batch recipe, all 32 RHS"),
+    "c5": ("grad", 255, dict(rtol=RTOL), "the forward+adjoint+gradient step on 255^2"),
+}
+_REF_SIDE = {"c1": 127, "c2": 255, "c3": 23, "c4": 127, "c5": 127}
 
 
-def run_oracle(side: int) -> dict:
+def run_oracle(workload: str, side: int) -> dict:
+    body, _, extra, _ = _SAMPLES[workload]
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = "1"
-    code = _ORACLE_SNIPPET.format(root=ROOT, side=side, rtol=RTOL)
+    fields = dict(side=side, seed=180800 + 1, rtol=extra.get("rtol", RTOL),
+                  lo=extra.get("lo", 1e-4), hi=extra.get("hi", 1e4), leaf=extra.get("leaf", 16))
+    code = _ORACLE_HEAD.format(root=ROOT) + _ORACLE_BODY[body].format(**fields)
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
     if r.returncode != 0:
         raise RuntimeError("oracle run failed: " + r.stderr[-2000:])
@@ -82,22 +154,23 @@ def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    side = _REF_SIDE[args.workload]
     for _ in range(args.warmup):
-        run_oracle(REF_STEP_SIDE)
-    secs, n = [], 0
+        run_oracle(args.workload, side)
+    secs, n, its = [], 0, 0
     for _ in range(args.steps):
-        r = run_oracle(REF_STEP_SIDE)
+        r = run_oracle(args.workload, side)
         secs.append(r["seconds"])
-        n = r["n"]
+        n, its = r["dofs"], r["iters"]
     tot = sum(secs)
     val = n * len(secs) / tot
-    sample = (f"FP64 numpy/scipy oracle, {REF_STEP_SIDE}^2 grid of the same recipe per step "
-              f"(N={n}), factor+PCG to relres {RTOL}, 1 thread")
+    sample = (f"FP64 numpy/scipy oracle, side {side} of the {args.workload} recipe per step "
+              f"(DOFs={n}, {its} PCG its), 1 thread")
     out = {"impl": "reference", "metric": METRIC, "value": val, "unit": "DOFs/s",
            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1e3 * tot / len(secs), "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "sample_side": REF_STEP_SIDE},
+           "config": {"workload": WORKLOADS[args.workload], "sample_side": side},
            "cpu_baseline": {"value": val, "unit": "DOFs/s", "cores": 1, "kind": "oracle",
                             "sample": sample},
            "e2e": {"value": val, "unit": "DOFs/s", "h2d_bytes_per_step": 0,
@@ -198,22 +271,139 @@ def source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profile_traffic(kernel: str, precision: str):
-    """Per-launch DRAM traffic recorded by an ncu capture, if the kernel sources
-    are unchanged since; else None."""
+def profile_traffic(kernel: str, precision: str, workload: str):
+    """Per-launch DRAM traffic recorded by an ncu capture of this workload, if
+    the kernel sources are unchanged since; else None."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
     want = source_hash()
     for line in open(path):
         f = line.split()
-        if len(f) >= 4 and not line.startswith("#") and f[0] == kernel and f[1] == precision:
+        if line.startswith("#") or len(f) < 4 or f[0] != kernel or f[1] != precision:
+            continue
+        if (f[4] if len(f) >= 5 else "c2") == workload:
             return float(f[2]) if f[3] == want else None
     return None
 
 
+class Workload:
+    """One step of the hot path with inputs resident on the device (`step`),
+    and end to end from pinned host buffers (`e2e_step`)."""
+
+    def __init__(self, key, rhif, W, torch, dev):
+        self.key, self.rhif, self.W, self.torch, self.dev = key, rhif, W, torch, dev
+        self.headline = "fp64" if key == "c1" else "fp32"
+        self.rtol = 1e-12 if key == "c1" else RTOL
+        t = torch
+        if key in ("c1", "c2", "c3"):
+            p = W.config_problem({"c1": 0, "c2": 1, "c3": 2}[key])
+            self.p = p
+            self.dofs = p.n
+            self.edge = key == "c3"
+            self.a_d = t.as_tensor(p.a, device=dev)
+            self.f_d = t.as_tensor(p.f, device=dev)
+            self.a_h = t.as_tensor(p.a).pin_memory()
+            self.f_h = t.as_tensor(p.f).pin_memory()
+            self.u_h = t.empty(p.n, dtype=t.float64).pin_memory()
+            self.h2d = (p.a.size + p.f.size) * 8
+            self.d2h = p.n * 8
+        elif key == "c4":
+            self.ps = W.batched_problems(64, 32)
+            self.dofs = sum(q.n for q in self.ps)
+            self.a_d = [t.as_tensor(q.a, device=dev) for q in self.ps]
+            self.f_d = [t.as_tensor(q.f, device=dev) for q in self.ps]
+            self.a_h = [t.as_tensor(q.a).pin_memory() for q in self.ps]
+            self.f_h = [t.as_tensor(q.f).pin_memory() for q in self.ps]
+            self.u_h = [t.empty(q.f.shape, dtype=t.float64).pin_memory() for q in self.ps]
+            self.streams = [t.cuda.Stream() for _ in range(8)]
+            self.h2d = sum((q.a.size + q.f.size) * 8 for q in self.ps)
+            self.d2h = sum(q.f.size * 8 for q in self.ps)
+        else:   # c5
+            self.ns = (511, 511)
+            log_star, f = W.inverse_problem(self.ns)
+            log_a = 0.3 * W.gaussian_bump_log_field(self.ns, W.SEED_BASE + 1)
+            self.dofs = int(f.size)
+            self.la_d = t.as_tensor(log_a, device=dev)
+            self.f_d = t.as_tensor(f, device=dev)
+            # observations of the true field: an FP64 solve on the device (setup only)
+            csr, _ = rhif.rhif_assemble_fd_log(self.ns, t.as_tensor(log_star, device=dev))
+            F = rhif.rhif_factor(csr, self.ns, 16, 1e-6, precision="fp64")
+            self.uo_d, _, _ = F.pcg(self.f_d, rtol=1e-13, maxit=1000)
+            F.free()
+            self.la_h = t.as_tensor(log_a).pin_memory()
+            self.f_h = t.as_tensor(f).pin_memory()
+            self.uo_h = self.uo_d.cpu().pin_memory()
+            self.g_h = t.empty(log_a.shape, dtype=t.float64).pin_memory()
+            self.h2d = (log_a.size + 2 * f.size) * 8
+            self.d2h = log_a.size * 8
+
+    def _solve_one(self, a, f, precision):
+        r, p = self.rhif, self.p
+        csr = r.rhif_assemble_fd(p.ns, a, p.b)
+        F = r.rhif_factor(csr, p.ns, p.leaf, p.tol, precision=precision, edge_skel_3d=self.edge)
+        u, its, rr = F.pcg(f, rtol=self.rtol, maxit=1000)
+        F.free()
+        return u, its, rr
+
+    def _batch(self, a_list, f_list, precision):
+        r = self.rhif
+        csrs = [r.rhif_assemble_fd(q.ns, a, q.b) for q, a in zip(self.ps, a_list)]
+        facs, _ = r.rhif_factor_batched(csrs, [q.ns for q in self.ps], 8, 1e-3, precision=precision,
+                                        streams=self.streams)
+        us, its, rr = r.rhif_pcg_batched(facs, f_list, rtol=self.rtol, streams=self.streams)
+        for F in facs:
+            F.free()
+        return us, [max(i) for i in its], [max(x) for x in rr]
+
+    def _grad(self, la, f, uo, precision):
+        t, r = self.torch, self.rhif
+        la = la.detach().requires_grad_(True)
+        u = r.rhif_solve(la, f, self.ns, leaf=16, tol=1e-3, precision=precision, rtol=self.rtol)
+        loss = 0.5 * t.sum((u - uo) ** 2)
+        loss.backward()
+        return la.grad, [0], [float(loss.detach())]
+
+    def step(self, precision):
+        if self.key == "c4":
+            return self._batch(self.a_d, self.f_d, precision)
+        if self.key == "c5":
+            return self._grad(self.la_d, self.f_d, self.uo_d, precision)
+        return self._solve_one(self.a_d, self.f_d, precision)
+
+    def e2e_step(self):
+        dev = self.dev
+        if self.key == "c4":
+            a = [x.to(dev, non_blocking=True) for x in self.a_h]
+            f = [x.to(dev, non_blocking=True) for x in self.f_h]
+            us, _, _ = self._batch(a, f, self.headline)
+            for h, u in zip(self.u_h, us):
+                h.copy_(u, non_blocking=True)
+            return
+        if self.key == "c5":
+            la = self.la_h.to(dev, non_blocking=True)
+            f = self.f_h.to(dev, non_blocking=True)
+            uo = self.uo_h.to(dev, non_blocking=True)
+            g, _, _ = self._grad(la, f, uo, self.headline)
+            self.g_h.copy_(g, non_blocking=True)
+            return
+        a = self.a_h.to(dev, non_blocking=True)
+        f = self.f_h.to(dev, non_blocking=True)
+        u, _, _ = self._solve_one(a, f, self.headline)
+        self.u_h.copy_(u, non_blocking=True)
+
+    def config(self):
+        c = {"workload": WORKLOADS[self.key], "dofs_per_step": self.dofs, "rtol": self.rtol}
+        if self.key in ("c1", "c2", "c3"):
+            c.update(N=self.p.n, leaf=self.p.leaf, tol=self.p.tol)
+        elif self.key == "c4":
+            c.update(problems=len(self.ps), rhs_per_problem=32, leaf=8, tol=1e-3, streams=8)
+        else:
+            c.update(N=self.dofs, leaf=16, tol=1e-3, step="forward PCG + adjoint PCG + gradient")
+        return c
+
+
 def gpu_arm(args):
-    import numpy as np
     import torch
     import torch.distributed as dist
 
@@ -227,33 +417,25 @@ def gpu_arm(args):
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     rhif.load()
-
-    side = args.side
-    ns = (side, side)
-    seed = W.SEED_BASE + 1
-    p = W.make_problem(ns, 1e-4, 1e4, 0.0, 16, 1e-3, seed)
-    N = p.n
     dev = torch.device("cuda", local)
-    a_d = torch.as_tensor(p.a, device=dev)
-    f_d = torch.as_tensor(p.f, device=dev)
-    nnz = rhif.rhif_fd_nnz(ns)
+    wl = Workload(args.workload, rhif, W, torch, dev)
     stream = torch.cuda.current_stream()
-
-    def step(precision):
-        csr = rhif.rhif_assemble_fd(ns, a_d, 0.0)
-        F = rhif.rhif_factor(csr, ns, p.leaf, p.tol, precision=precision)
-        u, its, rr = F.pcg(f_d, rtol=RTOL, maxit=500)
-        F.free()
-        return u, its, rr
 
     def barrier():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
 
-    def timed(precision, steps, warmup, timing=False):
+    def reduce_max(sec):
+        if world > 1:
+            t = torch.tensor([sec], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            sec = float(t.item())
+        return sec
+
+    def timed(fn, steps, warmup, timing=False):
         for _ in range(warmup):
-            step(precision)
+            fn()
         barrier()
         rhif.rhif_reset_kernel_stats()
         rhif.rhif_set_timing(timing)
@@ -261,67 +443,51 @@ def gpu_arm(args):
         e0.record(stream)
         info = None
         for _ in range(steps):
-            info = step(precision)
+            info = fn()
         e1.record(stream)
         barrier()
         rhif.rhif_set_timing(False)
         ks = rhif.rhif_kernel_stats()
-        sec = e0.elapsed_time(e1) / 1e3
-        if world > 1:
-            t = torch.tensor([sec], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            sec = float(t.item())
-        return sec, info, ks
+        return reduce_max(e0.elapsed_time(e1) / 1e3), info, ks
 
     clocks = ClockSampler(local)
-    # headline: FP32 factor, FP64 PCG, no instrumentation in the timed region
+    # headline precision, no instrumentation in the timed region
     clocks.start()
-    sec, (u, its, rr), ks_count = timed("fp32", args.steps, args.warmup, timing=False)
+    sec, (u, its, rr), ks_count = timed(lambda: wl.step(wl.headline), args.steps, args.warmup)
     clk = clocks.stop()
-    value = world * N * args.steps / sec
+    value = world * wl.dofs * args.steps / sec
     gpu_launches = int(sum(v["launches"] for v in ks_count.values()))
     # the same steps again with CUDA events around every library launch (per-kernel durations)
-    _, _, ks = timed("fp32", args.steps, 0, timing=True)
-    # plain FP64 factor
-    sec64, (u64, its64, rr64), ks64 = timed("fp64", args.fp64_steps, 1, timing=False)
-    value64 = world * N * args.fp64_steps / sec64
-    du = float(torch.linalg.norm(u - u64) / torch.linalg.norm(u64))
+    _, _, ks = timed(lambda: wl.step(wl.headline), args.steps, 0, timing=True)
+    # the other precision beside it
+    other = "fp32" if wl.headline == "fp64" else "fp64"
+    sec_o, (u_o, its_o, rr_o), _ = timed(lambda: wl.step(other), args.fp64_steps, 1)
+    value_o = world * wl.dofs * args.fp64_steps / sec_o
 
-    # end to end through the C-ABI with host buffers (pinned), copies inside the timed region
-    a_h = torch.as_tensor(p.a).pin_memory()
-    f_h = torch.as_tensor(p.f).pin_memory()
-    u_h = torch.empty(N, dtype=torch.float64).pin_memory()
+    def rel(a, b):
+        if isinstance(a, list):
+            return max(float(torch.linalg.norm(x - y) / torch.linalg.norm(y)) for x, y in zip(a, b))
+        return float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
 
-    def e2e_step():
-        a_dev = a_h.to(dev, non_blocking=True)
-        f_dev = f_h.to(dev, non_blocking=True)
-        csr = rhif.rhif_assemble_fd(ns, a_dev, 0.0)
-        F = rhif.rhif_factor(csr, ns, p.leaf, p.tol, precision="fp32")
-        uu, _, _ = F.pcg(f_dev, rtol=RTOL, maxit=500)
-        u_h.copy_(uu, non_blocking=True)
-        F.free()
+    du = rel(u, u_o)
 
+    # end to end from pinned host buffers, copies inside the timed region
     for _ in range(args.warmup):
-        e2e_step()
+        wl.e2e_step()
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        e2e_step()
+        wl.e2e_step()
     e1.record(stream)
     barrier()
-    sec_e2e = e0.elapsed_time(e1) / 1e3
-    if world > 1:
-        t = torch.tensor([sec_e2e], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        sec_e2e = float(t.item())
-    e2e_val = world * N * args.steps / sec_e2e
+    sec_e2e = reduce_max(e0.elapsed_time(e1) / 1e3)
+    e2e_val = world * wl.dofs * args.steps / sec_e2e
 
-    # roofline of the dominant kernel of the headline path
+    # roofline of the dominant kernel category of the headline path
     peaks = alu_peaks(torch)
     hbm, hbm_kind = measured_peaks()
-    top = max(ks.items(), key=lambda kv: kv[1]["total_ms"])
-    name, st = top
+    name, st = max(ks.items(), key=lambda kv: kv[1]["total_ms"])
     per_launch_ms = st["total_ms"] / max(st["launches"], 1)
     if name.startswith("apply") or name in ("spmv", "pcg_vector", "extend_add", "expand_gids"):
         achieved = st["bytes"] / max(st["launches"], 1) / (per_launch_ms / 1e3) / 1e9
@@ -329,41 +495,48 @@ def gpu_arm(args):
                 "peak_kind": hbm_kind}
     else:
         achieved = st["flops"] / max(st["launches"], 1) / (per_launch_ms / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": peaks["fp32"], "unit": "TFLOP/s",
-                "peak_kind": "measured cuBLAS SGEMM (no TF32) on this GPU"}
+        roof = {"bound": "alu", "achieved": achieved, "peak": peaks[wl.headline],
+                "unit": "TFLOP/s",
+                "peak_kind": f"measured cuBLAS {wl.headline} GEMM (no TF32) on this GPU"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["kernel"] = name
     roof["launch_ms"] = per_launch_ms
-    roof["traffic"] = profile_traffic(name, "fp32")
+    roof["traffic"] = profile_traffic(name, wl.headline, args.workload)
 
+    dtype = "f64" if wl.headline == "fp64" else "f32 factor + f64 PCG"
     result = {
         "metric": METRIC, "value": value, "unit": "DOFs/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 factor + f64 PCG", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "N": N, "leaf": p.leaf, "tol": p.tol, "rtol": RTOL,
-                   "parallelism": f"replicas{world}",
-                   "l2": "working set (fronts >1 GB) larger than L2; no flush"},
+        "dtype": dtype, "data": "synthetic",
+        "config": dict(wl.config(), parallelism=f"replicas{world}",
+                       l2="working set larger than L2 (fronts, frames); no flush"),
         "pcg_iters": its[0], "relres": rr[0],
-        "fp64": {"value": value64, "ms_per_step": 1e3 * sec64 / args.fp64_steps,
-                 "pcg_iters": its64[0], "relres": rr64[0], "rel_diff_u_vs_fp32_path": du},
-        "mixed_over_fp64": value / value64,
+        other: {"value": value_o, "ms_per_step": 1e3 * sec_o / args.fp64_steps,
+                "pcg_iters": its_o[0], "relres": rr_o[0], "rel_diff_vs_headline": du},
         "roofline": roof,
         "alu_peaks_tflops": peaks,
         "kernels": {k: {"launches": v["launches"], "ms": round(v["total_ms"], 3)}
                     for k, v in ks.items() if v["launches"]},
         "gpu_launches": gpu_launches,
         "clocks": clk,
-        "e2e": {"value": e2e_val, "unit": "DOFs/s",
-                "h2d_bytes_per_step": int(a_h.numel() * 8 + f_h.numel() * 8),
-                "d2h_bytes_per_step": int(u_h.numel() * 8)},
+        "e2e": {"value": e2e_val, "unit": "DOFs/s", "h2d_bytes_per_step": int(wl.h2d),
+                "d2h_bytes_per_step": int(wl.d2h)},
     }
+    if wl.headline == "fp32":
+        result["mixed_over_fp64"] = value / value_o
+    if args.workload == "c4":
+        result["rhs_dofs_per_s"] = value * 32
+    if args.workload == "c5":
+        result["loss"] = rr[0]
+        result.pop("relres")
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        r = run_oracle(CPU_SAMPLE_SIDE)
+        _, side, _, desc = _SAMPLES[args.workload]
+        r = run_oracle(args.workload, side)
         result["cpu_baseline"] = {
-            "value": r["n"] / r["seconds"], "unit": "DOFs/s", "cores": 1, "kind": "oracle",
-            "sample": (f"FP64 oracle factor+PCG on a {CPU_SAMPLE_SIDE}^2 grid of the same recipe "
-                       f"(N={r['n']}, {r['seconds']:.1f} s, {r['iters']} PCG its), 1 thread")}
+            "value": r["dofs"] / r["seconds"], "unit": "DOFs/s", "cores": 1, "kind": "oracle",
+            "sample": (f"FP64 oracle on {desc} (DOFs={r['dofs']}, {r['seconds']:.1f} s, "
+                       f"{r['iters']} PCG its), 1 thread")}
     if rank == 0:
         print(json.dumps(result))
     if world > 1:

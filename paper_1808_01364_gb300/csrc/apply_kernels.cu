@@ -1066,7 +1066,8 @@ __global__ void k_update_xr(int64_t N, const double* sc, double* x, int64_t ldx,
   if (threadIdx.x == 0) partial[blockIdx.x + (int64_t)gridDim.x * r] = t;
 }
 
-// p = z + beta p
+// p = z (first iteration; p is not read: it holds whatever the scratch held)
+// or p = z + beta p
 __global__ void k_update_p(int64_t N, const double* sc, const double* z, int64_t ldz, double* p,
                            int64_t ldp, int first) {
   const int r = blockIdx.y;
@@ -1075,7 +1076,7 @@ __global__ void k_update_p(int64_t N, const double* sc, const double* z, int64_t
   const double beta = first ? 0.0 : S[kScBeta];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x)
-    p[i + r * ldp] = z[i + r * ldz] + beta * p[i + r * ldp];
+    p[i + r * ldp] = first ? z[i + r * ldz] : z[i + r * ldz] + beta * p[i + r * ldp];
 }
 
 // y = a - b (true residual)

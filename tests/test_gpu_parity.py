@@ -199,3 +199,23 @@ def test_factor_is_deterministic(gpu_lib, precision):
         F.free()
     assert outs[0][0] == outs[1][0]
     np.testing.assert_array_equal(outs[0][1], outs[1][1])
+
+
+def test_pcg_does_not_read_stale_scratch(gpu_lib):
+    """PCG must not depend on what its work space held before: a solve with a
+    NaN right-hand side leaves NaN in the handle's scratch vectors, and the
+    next solve on the same handle still converges to the direct solution."""
+    ns = (63, 63)
+    a = W.log_uniform_pixels(ns, 1e-3, 1e3, seed=31)
+    A = fd.assemble(ns, a, 0.0)
+    Fg = gpu_lib.rhif_factor(_gpu_matrix(gpu_lib, ns, a, 0.0), ns, 8, 1e-3, precision="fp32")
+    F = W.normal_rhs(ns, 32, nrhs=2)
+    bad = F.copy()
+    bad[:, 17] = np.nan
+    Fg.pcg(_dev(bad), rtol=1e-10, maxit=3, check=False)
+    U, its, rr = Fg.pcg(_dev(F), rtol=1e-10)
+    U = U.cpu().numpy()
+    for r in range(2):
+        assert rr[r] <= 1.5e-10
+        ud = spla.spsolve(A.tocsc(), F[r])
+        assert np.linalg.norm(U[r] - ud) <= 1e-7 * np.linalg.norm(ud)

@@ -123,16 +123,117 @@ __device__ inline void warp_band_bwd_blk(const T* band, int n, int w, T* y) {
   }
 }
 
+// Forms for w <= 15 (all 2D leaves up to leaf 16).  The factor stores, in
+// the in-block slots of every diagonal w x w block of the band, the explicit
+// inverse X of that block (k_band_block_inverse); the slots coupling a block
+// to the next one keep L.  A block solve is then the coupling update of the
+// lane's row followed by one row (column) of X times the block's right-hand
+// sides: independent shuffles and FMAs, no dependent chain inside the block.
+constexpr int kBandRegW = kBandInvW;
+
+template <typename T>
+__device__ inline void warp_band_fwd_inv(const T* band, int n, int w, T* y) {
+  const int lane = threadIdx.x & 31;
+  const int w1 = w + 1;
+  for (int s0 = 0; s0 < n; s0 += w) {
+    const int B = min(w, n - s0);
+    const int i = s0 + lane;
+    const bool act = lane < B;
+    T cp[kBandRegW + 1], yp[kBandRegW + 1], xr[kBandRegW];
+#pragma unroll
+    for (int d = 1; d <= kBandRegW; ++d) {
+      const int j = i - d;
+      const bool ok = act && d <= w && d > lane && j >= 0;
+      cp[d] = ok ? band[j * w1 + d] : T(0);
+      yp[d] = ok ? y[j] : T(0);
+    }
+#pragma unroll
+    for (int c = 0; c < kBandRegW; ++c)   // row `lane` of X
+      xr[c] = (act && c <= lane) ? band[(s0 + c) * w1 + (lane - c)] : T(0);
+    T acc = act ? y[i] : T(0);
+#pragma unroll
+    for (int d = 1; d <= kBandRegW; ++d) acc -= cp[d] * yp[d];
+    T out = T(0);
+#pragma unroll
+    for (int c = 0; c < kBandRegW; ++c) {
+      const T rc = __shfl_sync(0xffffffffu, acc, c);
+      out += xr[c] * rc;
+    }
+    if (act) y[i] = out;
+    __syncwarp();
+  }
+}
+
+template <typename T>
+__device__ inline void warp_band_bwd_inv(const T* band, int n, int w, T* y) {
+  const int lane = threadIdx.x & 31;
+  const int w1 = w + 1;
+  const int nblk = (n + w - 1) / w;
+  for (int bi = nblk - 1; bi >= 0; --bi) {
+    const int s0 = bi * w;
+    const int B = min(w, n - s0);
+    const int i = s0 + lane;
+    const bool act = lane < B;
+    T cp[kBandRegW + 1], yn[kBandRegW + 1], xc[kBandRegW];
+#pragma unroll
+    for (int d = 1; d <= kBandRegW; ++d) {
+      const int j = i + d;
+      const bool ok = act && d <= w && d >= B - lane && j < n;
+      cp[d] = ok ? band[i * w1 + d] : T(0);
+      yn[d] = ok ? y[j] : T(0);
+    }
+#pragma unroll
+    for (int c = 0; c < kBandRegW; ++c)   // column `lane` of X
+      xc[c] = (act && c >= lane && c < B) ? band[(s0 + lane) * w1 + (c - lane)] : T(0);
+    T acc = act ? y[i] : T(0);
+#pragma unroll
+    for (int d = 1; d <= kBandRegW; ++d) acc -= cp[d] * yn[d];
+    T out = T(0);
+#pragma unroll
+    for (int c = 0; c < kBandRegW; ++c) {
+      const T rc = __shfl_sync(0xffffffffu, acc, c);
+      out += xc[c] * rc;
+    }
+    if (act) y[i] = out;
+    __syncwarp();
+  }
+}
+
 template <typename T>
 __device__ inline void band_fwd(const T* band, int n, int w, T* y) {
-  if (w >= 1 && w <= 31) warp_band_fwd_blk(band, n, w, y);
+  if (w >= 1 && w <= kBandRegW) warp_band_fwd_inv(band, n, w, y);
+  else if (w >= 1 && w <= 31) warp_band_fwd_blk(band, n, w, y);
   else warp_band_fwd(band, n, w, y);
 }
 
 template <typename T>
 __device__ inline void band_bwd(const T* band, int n, int w, T* y) {
-  if (w >= 1 && w <= 31) warp_band_bwd_blk(band, n, w, y);
+  if (w >= 1 && w <= kBandRegW) warp_band_bwd_inv(band, n, w, y);
+  else if (w >= 1 && w <= 31) warp_band_bwd_blk(band, n, w, y);
   else warp_band_bwd(band, n, w, y);
+}
+
+// dst[i] = T(xr[g[i]]) for i < n, one warp: indices of a 256-entry chunk
+// first, then the gathered values, so each chunk costs two load latencies.
+template <typename T>
+__device__ inline void warp_gather(const double* xr, const int32_t* g, int n, T* dst) {
+  const int lane = threadIdx.x & 31;
+  for (int i0 = 0; i0 < n; i0 += 256) {
+    int idx[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int i = i0 + 32 * u + lane;
+      idx[u] = i < n ? g[i] : -1;
+    }
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = idx[u] >= 0 ? xr[idx[u]] : 0.0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int i = i0 + 32 * u + lane;
+      if (i < n) dst[i] = T(v[u]);
+    }
+  }
 }
 
 // per-warp shared memory of the leaf kernels: [mbarrier | band | y | z]
@@ -191,8 +292,7 @@ k_apply_leaf_up(LevelDev Lv, double* x, int64_t ldx, int nrhs, double* ubuf, int
   const T* ca = (const T*)Lv.cpl_a + Lv.b_off[c];
   for (int r = 0; r < nrhs; ++r) {
     double* xr = x + r * ldx;
-#pragma unroll 4
-    for (int i = lane; i < nI; i += 32) y[i] = T(xr[gI[i]]);
+    warp_gather(xr, gI, nI, y);
     if (r == 0 && !staged_ok(bar, Lv.status, 0, kKindCell, c)) return;
     __syncwarp();
     band_fwd(band, nI, w, y);
@@ -230,8 +330,7 @@ k_apply_leaf_down(LevelDev Lv, double* x, int64_t ldx, int nrhs, int per_warp_by
   for (int r = 0; r < nrhs; ++r) {
     double* xr = x + r * ldx;
     for (int i = lane; i < nI; i += 32) v[i] = T(0);
-#pragma unroll 4
-    for (int i = lane; i < nI; i += 32) t[i] = T(xr[gI[i]]);
+    warp_gather(xr, gI, nI, t);
 #pragma unroll 2
     for (int b = lane; b < nB; b += 32) xb[b] = ci[b] >= 0 ? ca[b] * T(xr[gB[b]]) : T(0);
     __syncwarp();

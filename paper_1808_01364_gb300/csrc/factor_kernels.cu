@@ -538,6 +538,38 @@ __global__ void k_extend_add(LevelDev cur, LevelDev prev, int slot, int chunk) {
   }
 }
 
+// Leaf bands with w <= kBandInvW: replace the in-block entries of every
+// diagonal w x w block of L (blocks start at multiples of w) by the entries
+// of its inverse X (lower triangular; the diagonal slots already hold
+// 1/L_kk = X_kk).  One warp per cell, lane c computes column c of X by
+// forward substitution, X[r,c] = -(1/L_rr) sum_{k=c}^{r-1} L[r,k] X[k,c].
+template <typename T>
+__global__ void k_band_block_inverse(LevelDev Lv) {
+  const int lane = threadIdx.x & 31;
+  const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (c >= Lv.ncell) return;
+  const int n = Lv.nI[c], w = Lv.band_w[c];
+  if (w < 1 || w > kBandInvW) return;
+  const int w1 = w + 1;
+  T* band = (T*)Lv.band + Lv.band_off[c];
+  for (int s0 = 0; s0 < n; s0 += w) {
+    const int B = min(w, n - s0);
+    T x[kBandInvW];
+    if (lane < B) {
+      x[lane] = band[(s0 + lane) * w1];
+      for (int r = lane + 1; r < B; ++r) {
+        T s = T(0);
+        for (int k = lane; k < r; ++k) s += band[(s0 + k) * w1 + (r - k)] * x[k];
+        x[r] = -s * band[(s0 + r) * w1];
+      }
+    }
+    __syncwarp();
+    if (lane < B)
+      for (int r = lane + 1; r < B; ++r) band[(s0 + lane) * w1 + (r - lane)] = x[r];
+    __syncwarp();
+  }
+}
+
 // ---------------------------------------------------------------------------
 // cell elimination (Sec. 2.1) of dense fronts: partial Cholesky
 // ---------------------------------------------------------------------------
@@ -1495,6 +1527,12 @@ void launch_front_invert(const LevelDev& Lv, T* X, const int64_t* xoff, cudaStre
 }
 
 template <typename T>
+void launch_band_block_inverse(const LevelDev& Lv, cudaStream_t s) {
+  if (!Lv.ncell) return;   // per-cell test inside: the apply decides per cell too
+  k_band_block_inverse<T><<<(Lv.ncell + 7) / 8, 256, 0, s>>>(Lv);
+}
+
+template <typename T>
 void launch_partial_chol(const LevelDev& Lv, int* status, cudaStream_t s) {
   if (!Lv.ncell) return;
   k_partial_chol<T><<<Lv.ncell, kThreads, partial_chol_smem_elems() * sizeof(T), s>>>(Lv, status);
@@ -1638,6 +1676,7 @@ int configure_factor_kernels() {
                                     int*, cudaStream_t);                                          \
   template int launch_extend_add<T>(const LevelDev&, const LevelDev&, int64_t, int, cudaStream_t); \
   template void launch_partial_chol<T>(const LevelDev&, int*, cudaStream_t);                      \
+  template void launch_band_block_inverse<T>(const LevelDev&, cudaStream_t);                     \
   template void launch_front_invert<T>(const LevelDev&, T*, const int64_t*, cudaStream_t);       \
   template void launch_front_panel<T>(const LevelDev&, int, int*, cudaStream_t);                  \
   template void launch_front_trailing<T>(const LevelDev&, int, int64_t, cudaStream_t);            \

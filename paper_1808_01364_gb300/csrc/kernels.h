@@ -19,6 +19,10 @@ size_t leaf_smem_bytes(int max_nI, int max_nB, int max_w, int leaf, int d);
 template <typename T>
 void launch_leaf_elim(const GeoDev& G, const LevelDev& Lv, const double* diag, const double* off,
                       int* status, cudaStream_t s);
+// In-place explicit inverses of the diagonal blocks of the leaf bands with
+// w <= kBandInvW (other cells untouched).
+template <typename T>
+void launch_band_block_inverse(const LevelDev& Lv, cudaStream_t s);
 // Zero the level's fronts and add the children's Schur complements, one
 // launch per child slot (slots = most children of any cell); returns the
 // number of kernel launches.

@@ -50,6 +50,12 @@ struct Coder {
     }
     return c;
   }
+  // per-axis code values v(x) = 2 * (x / width) + (x % width != 0), x = 1..ns
+  std::vector<int> axis_table(const Geometry& G, int a) const {
+    std::vector<int> t(G.ns[a]);
+    for (int x = 1; x <= G.ns[a]; ++x) t[x - 1] = 2 * (x / width) + (x % width != 0);
+    return t;
+  }
   inline void split(int64_t code, int v[3]) const {
     for (int a = 0; a < 3; ++a) v[a] = 1;
     for (int a = 0; a < d; ++a) {
@@ -143,14 +149,30 @@ LevelPlan build_level(const Geometry& G, int level, const std::vector<int32_t>& 
   } else {
     std::vector<int64_t> code(active.size());
     std::vector<int64_t> cnt(C.ncode + 1, 0);
+    std::vector<int> tab[3];
+    for (int a = 0; a < d; ++a) tab[a] = C.axis_table(G, a);
+    const int64_t n0 = G.ns[0], n01 = (int64_t)G.ns[0] * G.ns[1];
     for (size_t i = 0; i < active.size(); ++i) {
-      code[i] = C.code_of(G, active[i]);
-      ++cnt[code[i] + 1];
+      const int64_t g = active[i];
+      int64_t c;
+      if (d == 2) {
+        const int64_t y = g / n0;
+        c = tab[0][g - y * n0] + C.base * tab[1][y];
+      } else {
+        const int64_t z = g / n01, r = g - z * n01, y = r / n0;
+        c = tab[0][r - y * n0] + C.base * (tab[1][y] + (int64_t)C.base * tab[2][z]);
+      }
+      code[i] = c;
+      ++cnt[c + 1];
     }
     for (int64_t c = 0; c < C.ncode; ++c) cnt[c + 1] += cnt[c];
     cstart = cnt;
     P.bucket.resize(active.size());
     for (size_t i = 0; i < active.size(); ++i) P.bucket[cnt[code[i]]++] = active[i];
+    // ascending DOF index within every code
+    for (int64_t c = 0; c < C.ncode; ++c)
+      if (cstart[c + 1] - cstart[c] > 1)
+        std::sort(P.bucket.begin() + cstart[c], P.bucket.begin() + cstart[c + 1]);
   }
   auto csize = [&](int64_t c) { return (int)(cstart[c + 1] - cstart[c]); };
 
@@ -284,7 +306,10 @@ LevelPlan build_level(const Geometry& G, int level, const std::vector<int32_t>& 
     const Coder Cp(G, level - 1);
     std::vector<int> prev_cell_of_code(Cp.ncode, -1);
     for (int i = 0; i < prev->ncell(); ++i) prev_cell_of_code[prev->cell_code[i]] = i;
-    std::vector<int> pos_of_gid(G.N, -1);
+    // DOF -> front position, all -1 between cells (thread-local, reused by later calls)
+    static thread_local std::vector<int> pos_scratch;
+    if ((int64_t)pos_scratch.size() < G.N) pos_scratch.assign(G.N, -1);
+    std::vector<int>& pos_of_gid = pos_scratch;
     P.ea_off.push_back(0);
     for (int ci = 0; ci < ncell; ++ci) {
       const int nI = P.nI[ci];

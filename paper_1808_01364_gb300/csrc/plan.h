@@ -106,10 +106,11 @@ struct LevelPlan {
   int ngroup() const { return (int)group_t.size(); }
 };
 
-// Build the plan of level `level`.  `active` lists the active DOFs in
-// ascending order (ignored at level 0, where every DOF is active); `alive`
-// flags them by DOF index; `prev` is the plan of level-1.  For
-// level == G.L only the root front is built (no phases).
+// Build the plan of level `level`.  `active` lists the active DOFs in any
+// order (ignored at level 0, where every DOF is active); `alive` flags the
+// surviving DOFs of the previous level's separator groups by DOF index;
+// `prev` is the plan of level-1.  For level == G.L only the root front is
+// built (no phases).
 LevelPlan build_level(const Geometry& G, int level, const std::vector<int32_t>& active,
                       const std::vector<uint8_t>& alive, const LevelPlan* prev,
                       bool precondition, bool edge_skel);

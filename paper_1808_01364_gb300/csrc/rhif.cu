@@ -496,6 +496,8 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
       S.dev.zbuf = Zb;
       Launch t(kCatLeafElim, s, lvl_flops, 0.0);
       launch_leaf_elim<T>(H->gd, S.dev, H->diag, H->off, H->status, s);
+      launch_band_block_inverse<T>(S.dev, s);
+      add_launches(kCatLeafElim, 1);
     } else {
       for (int c = 0; c < P.ncell(); ++c) {
         const double nI = P.nI[c], nB = P.nB[c];
@@ -660,15 +662,14 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
       S.dev.zbuf = nullptr;
     }
     // DOFs still active at the next level: the separator DOFs that survived
-    for (int c = 0; c < P.ncell(); ++c)
-      for (int i = 0; i < P.nI[c]; ++i) alive[P.bucket[P.cell_start[c] + i]] = 0;
+    // (interior DOFs never appear in a separator group again, so their host
+    // flags are not needed; the planner orders each new cell / group itself)
     active.clear();
     for (int gi = 0; gi < P.ngroup(); ++gi)
       for (int o = 0; o < P.group_size[gi]; ++o) {
         const int32_t g = P.bucket[P.group_start[gi] + o];
         if (alive[g]) active.push_back(g);
       }
-    std::sort(active.begin(), active.end());
     for (int c = 0; c < P.ncell(); ++c) {
       const double nI = P.nI[c], nB = P.nB[c];
       if (lvl == 0) {

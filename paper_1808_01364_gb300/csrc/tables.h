@@ -6,6 +6,10 @@ namespace rhif {
 
 constexpr int kMaxRowGroupsDev = 128;   // = kMaxRowGroups of plan.h
 constexpr int kMaxSlotsDev = 4;
+// Leaf bands with half bandwidth w <= kBandInvW store the explicit inverse of
+// every diagonal w x w block in the block's in-band slots (see
+// k_band_block_inverse and the leaf application).
+constexpr int kBandInvW = 15;
 
 struct GeoDev {
   int d, leaf;

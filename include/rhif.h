@@ -77,9 +77,10 @@ typedef struct {
   int big_frame;
   /* skel_cluster: CTAs (a thread-block cluster, power of two <= 16) that share
    *   the interpolative decomposition of one skeletonization unit, each holding
-   *   a slice of the unit's rows.  0 = library default (clusters only for units
-   *   whose ID matrix does not fit in one CTA's shared memory), < 0 = never,
-   *   1..16 = always, with that cluster size. */
+   *   a slice of the unit's rows.  0 = library default (one warp per unit when
+   *   every unit has at most 32 DOFs, clusters only for units whose ID matrix
+   *   does not fit in one CTA's shared memory, else one CTA per unit), < 0 =
+   *   one CTA per unit always, 1..16 = clusters of that size always. */
   int skel_cluster;
   int reserved[2];
 } rhif_opts;

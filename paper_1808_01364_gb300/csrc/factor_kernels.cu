@@ -948,8 +948,8 @@ struct SkelRows {
 };
 
 __device__ inline void skel_row_groups(const LevelDev& Lv, int g, int nrow, int* status,
-                                       SkelRows* R) {
-  if (threadIdx.x != 0) return;
+                                       SkelRows* R, bool leader) {
+  if (!leader) return;
   const int c0 = Lv.group_cell_off[g], nslot = Lv.group_cell_off[g + 1] - c0;
   int nrg = 0, row = 0;
   for (int s = 0; s < nslot; ++s) {
@@ -982,7 +982,7 @@ __device__ inline void skel_row_groups(const LevelDev& Lv, int g, int nrow, int*
 template <typename T>
 __device__ void skel_gather_rows(const LevelDev& Lv, const uint8_t* alive, int g, int n, int nrow,
                                  const SkelRows& R, int ra, int rb, T* D, int64_t drs,
-                                 int64_t dcs) {
+                                 int64_t dcs, int t0, int nt) {
   const int c0 = Lv.group_cell_off[g], nslot = Lv.group_cell_off[g + 1] - c0;
   for (int f = 0; f < R.nrg; ++f) {
     const int r0 = R.row0[f];
@@ -991,7 +991,7 @@ __device__ void skel_gather_rows(const LevelDev& Lv, const uint8_t* alive, int g
     const int sg = R.group[f];
     const int32_t* sgid = Lv.bucket + Lv.group_start[sg];
     const int cnt = hi - lo;
-    for (int idx = threadIdx.x; idx < cnt * n; idx += blockDim.x) {
+    for (int idx = t0; idx < cnt * n; idx += nt) {
       const int o = lo - r0 + idx % cnt, j = idx / cnt;
       T v = T(0);
       if (alive[sgid[o]]) {
@@ -1211,9 +1211,9 @@ __global__ void __launch_bounds__(kThreads) k_skel(LevelDev Lv, PhaseDev Ph, uin
   if (mstage) M = (T*)((unsigned char*)(sperm + Ph.max_n) + 16 - (((size_t)(sperm + Ph.max_n)) & 15));
   T* Aee = M + (int64_t)nrow * n;
 
-  skel_row_groups(Lv, g, nrow, status, &rows);
+  skel_row_groups(Lv, g, nrow, status, &rows, tid == 0);
   __syncthreads();
-  skel_gather_rows(Lv, alive, g, n, nrow, rows, 0, nrow, M, 1, ldm);
+  skel_gather_rows(Lv, alive, g, n, nrow, rows, 0, nrow, M, 1, ldm, tid, blockDim.x);
   skel_gather_diag(Lv, g, n, Aee, tid, blockDim.x);
   for (int i = tid; i < n; i += blockDim.x) sperm[i] = i;
   if (tid == 0) {
@@ -1276,6 +1276,201 @@ __global__ void __launch_bounds__(kThreads) k_skel(LevelDev Lv, PhaseDev Ph, uin
   skel_finish(Lv, Ph, u, g, n, s_k, M, 1, ldm, Aee, sperm, sm, status);
 }
 
+// Skeletonization of small units (n <= 32) with one warp per unit: lane c
+// owns column c of A_{R,g} (shared memory, odd leading dimension), so the
+// CPQR needs no block barriers; the column norms for the next step are taken
+// from the updated values in the same pass (an exact recomputation, not a
+// downdate).  The zeroing and the elimination of the redundant DOFs run in the
+// warp too, on an n x n copy in shared memory.  Same rank rule and pivot rule
+// as k_skel.
+__host__ __device__ inline size_t skel_warp_bytes(int max_n, int64_t max_m, size_t elem) {
+  const size_t rows = (sizeof(SkelRows) + 15) & ~size_t(15);
+  const size_t mcap = (size_t)max_m + max_n;   // (nrow + 1) * n covers the odd leading dimension
+  const size_t mreg = (((size_t)max_n * max_n > mcap ? (size_t)max_n * max_n : mcap) * elem + 15) & ~size_t(15);
+  const size_t sq = (((size_t)max_n * max_n) * elem + 15) & ~size_t(15);
+  return rows + 128 + mreg + 2 * sq;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_skel_warp(LevelDev Lv, PhaseDev Ph, uint8_t* alive,
+                                                   double tol, int* status, int per_warp) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int u = blockIdx.x * (blockDim.x >> 5) + wid;
+  if (u >= Ph.nunit) return;   // whole warps only; no block barriers below
+  unsigned char* base = smraw + (size_t)wid * per_warp;
+  SkelRows* rows = (SkelRows*)base;
+  int* sp = (int*)(base + ((sizeof(SkelRows) + 15) & ~size_t(15)));
+  T* M = (T*)((unsigned char*)sp + 128);
+  const int g = Ph.u_group[u];
+  const int n = Lv.group_size[g];
+  const int nrow = Ph.u_nrow[u];
+  const int ld = nrow | 1;
+  const int64_t mreg = (((int64_t)ld * n > (int64_t)n * n ? (int64_t)ld * n : (int64_t)n * n) + 3) & ~int64_t(3);
+  T* Aee = M + mreg;
+  T* Ts = Aee + pad4e((int64_t)n * n);
+  T* Fs = M;   // reused for the zeroed block once R and T are done
+
+  skel_row_groups(Lv, g, nrow, status, rows, lane == 0);
+  __syncwarp();
+  skel_gather_rows(Lv, alive, g, n, nrow, *rows, 0, nrow, M, 1, ld, lane, 32);
+  skel_gather_diag(Lv, g, n, Aee, lane, 32);
+  if (lane < n) sp[lane] = lane;
+  __syncwarp();
+
+  const bool own = lane < n;
+  T* col = M + (int64_t)lane * ld;
+  T nrm = T(0);
+  if (own) {
+    T a0 = T(0), a1 = T(0);
+    int i = 0;
+    for (; i + 1 < nrow; i += 2) { a0 += col[i] * col[i]; a1 += col[i + 1] * col[i + 1]; }
+    if (i < nrow) a0 += col[i] * col[i];
+    nrm = a0 + a1;
+  }
+  T r11 = T(0);
+  int k = 0;
+  const int steps = min(nrow, n);
+  for (int j = 0; j < steps; ++j) {
+    // pivot: largest norm, ties within 1e-12 relative to the smallest original index
+    const bool cand = own && lane >= j;
+    T mx = cand ? nrm : T(0);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      const T y = __shfl_xor_sync(0xffffffffu, mx, o);
+      mx = y > mx ? y : mx;
+    }
+    if (j == 0) r11 = my_sqrt(mx);
+    if (r11 == T(0) || my_sqrt(mx) <= T(tol) * r11) break;
+    const T thr = T(1.0 - 1e-12) * mx;
+    int key = (cand && nrm >= thr) ? sp[lane] : 0x7fffffff, p = lane;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      const int ok = __shfl_xor_sync(0xffffffffu, key, o);
+      const int op = __shfl_xor_sync(0xffffffffu, p, o);
+      if (ok < key || (ok == key && op < p)) { key = ok; p = op; }
+    }
+    if (p != j) {
+      for (int i = lane; i < nrow; i += 32) {
+        const T a = M[i + (int64_t)j * ld];
+        M[i + (int64_t)j * ld] = M[i + (int64_t)p * ld];
+        M[i + (int64_t)p * ld] = a;
+      }
+      const T nj = __shfl_sync(0xffffffffu, nrm, p), np = __shfl_sync(0xffffffffu, nrm, j);
+      if (lane == j) nrm = nj;
+      if (lane == p) nrm = np;
+      if (lane == 0) { const int t = sp[j]; sp[j] = sp[p]; sp[p] = t; }
+    }
+    __syncwarp();
+    const T x0 = M[j + (int64_t)j * ld];
+    const T nx = my_sqrt(__shfl_sync(0xffffffffu, nrm, j));
+    const T alpha = x0 < T(0) ? nx : -nx;
+    const T v0 = x0 - alpha;
+    const T tau = T(1) / (nx * (nx + my_abs(x0)));
+    const T* vj = M + (int64_t)j * ld;
+    if (own && lane > j) {
+      T s0 = T(0), s1 = T(0);
+      int i = j + 1;
+      for (; i + 1 < nrow; i += 2) { s0 += vj[i] * col[i]; s1 += vj[i + 1] * col[i + 1]; }
+      if (i < nrow) s0 += vj[i] * col[i];
+      const T w = ((s0 + s1) + v0 * col[j]) * tau;
+      col[j] -= w * v0;
+      T n0 = T(0), n1 = T(0);
+      i = j + 1;
+      for (; i + 1 < nrow; i += 2) {
+        const T b0 = col[i] - w * vj[i], b1 = col[i + 1] - w * vj[i + 1];
+        col[i] = b0;
+        col[i + 1] = b1;
+        n0 += b0 * b0;
+        n1 += b1 * b1;
+      }
+      if (i < nrow) {
+        const T b0 = col[i] - w * vj[i];
+        col[i] = b0;
+        n0 += b0 * b0;
+      }
+      nrm = n0 + n1;
+    }
+    __syncwarp();
+    if (lane == 0) M[j + (int64_t)j * ld] = alpha;
+    __syncwarp();
+    k = j + 1;
+  }
+  const int r = n - k;
+  // T = R11^{-1} R12 (k x r), one column per lane
+  if (lane < r) {
+    for (int i = k - 1; i >= 0; --i) {
+      T t = M[i + (int64_t)(k + lane) * ld];
+      for (int q = i + 1; q < k; ++q) t -= M[i + (int64_t)q * ld] * Ts[q + lane * k];
+      Ts[i + lane * k] = t / M[i + (int64_t)i * ld];
+    }
+  }
+  __syncwarp();
+  // zeroing (Eq. 2.2) into Fs in (redundant, skeleton) order
+  auto a_ss = [&](int q, int p2) { return Aee[sp[q] + sp[p2] * n]; };
+  if (lane < r) {
+    for (int q = 0; q < k; ++q) {
+      T v = a_ss(q, k + lane);
+      for (int p2 = 0; p2 < k; ++p2) v -= a_ss(q, p2) * Ts[p2 + lane * k];
+      Fs[(r + q) + lane * n] = v;
+    }
+  }
+  __syncwarp();
+  if (lane < r) {
+    const int b = lane;
+    for (int a = b; a < r; ++a) {
+      T v = a_ss(k + a, k + b);
+      for (int q = 0; q < k; ++q)
+        v -= Ts[q + a * k] * Fs[(r + q) + b * n] + a_ss(q, k + a) * Ts[q + b * k];
+      Fs[a + b * n] = v;
+    }
+  }
+  if (lane < k)
+    for (int q = lane; q < k; ++q) Fs[(r + q) + (r + lane) * n] = a_ss(q, lane);
+  __syncwarp();
+  // eliminate the redundant DOFs: right-looking Cholesky of the first r columns
+  bool bad = false;
+  for (int pc = 0; pc < r; ++pc) {
+    T d = Fs[pc + pc * n];
+    if (!(d > T(0))) { bad = true; d = T(1); }
+    const T sd = my_sqrt(d);
+    __syncwarp();
+    if (lane == pc) Fs[pc + pc * n] = sd;
+    if (lane > pc && lane < n) Fs[lane + pc * n] /= sd;
+    __syncwarp();
+    if (lane > pc && lane < n) {
+      const T lip = Fs[lane + pc * n];
+      for (int jj = pc + 1; jj <= lane; ++jj) Fs[lane + jj * n] -= lip * Fs[jj + pc * n];
+    }
+    __syncwarp();
+  }
+  if (bad && lane == 0) report(status, RHIF_ERR_NOT_SPD, Lv.level, kKindUnit, g);
+  // outputs: unit front, T, frames, permutation, rank
+  T* Fu = (T*)Ph.rec + Ph.u_rec_off[u];
+  T* Tm = Fu + pad4e((int64_t)n * n);
+  for (int idx = lane; idx < n * n; idx += 32) {
+    const int i = idx % n, jj = idx / n;
+    if (i >= jj) Fu[idx] = Fs[idx];
+  }
+  for (int idx = lane; idx < k * r; idx += 32) Tm[idx] = Ts[idx];
+  const int c0 = Lv.group_cell_off[g], c1 = Lv.group_cell_off[g + 1];
+  for (int idx = lane; idx < k * k; idx += 32) {
+    const int q = idx % k, p2 = idx / k;
+    if (q < p2) continue;
+    const T val = Fs[(r + q) + (r + p2) * n];
+    for (int kk = c0; kk < c1; ++kk) {
+      int ldf;
+      T* fr = frame_of<T>(Lv, Lv.group_cell[kk], &ldf);
+      const int pos = Lv.group_pos[kk];
+      const int bq = pos + sp[q], bp = pos + sp[p2];
+      fr[max(bq, bp) + (int64_t)min(bq, bp) * ldf] = kk == c0 ? val : T(0);
+    }
+  }
+  int* perm_out = Ph.perm + Ph.u_perm_off[u];
+  if (lane < n) perm_out[lane] = sp[lane];
+  if (lane == 0) Ph.rank[u] = k;
+}
+
 // Row length (elements) of the per-rank partial-sum tables of k_skel_cluster:
 // a multiple of 4, so every row is a whole number of 16-byte vectors.
 __host__ __device__ inline int skel_cluster_ldp(int max_n) { return (max_n + 3) & ~3; }
@@ -1336,9 +1531,9 @@ __global__ void __launch_bounds__(kThreads) k_skel_cluster(LevelDev Lv, PhaseDev
     }
   };
 
-  skel_row_groups(Lv, g, nrow, status, &rows);
+  skel_row_groups(Lv, g, nrow, status, &rows, tid == 0);
   __syncthreads();
-  skel_gather_rows(Lv, alive, g, n, nrow, rows, i0, i1, Ms, n, 1);
+  skel_gather_rows(Lv, alive, g, n, nrow, rows, i0, i1, Ms, n, 1, tid, nth);
   skel_gather_diag(Lv, g, n, Aee, (int64_t)cr * nth + tid, (int64_t)C * nth);
   for (int i = tid; i < n; i += nth) sperm[i] = i;
   if (tid == 0) {
@@ -1603,6 +1798,20 @@ void launch_skel(const LevelDev& Lv, const PhaseDev& Ph, uint8_t* alive, double 
 }
 
 template <typename T>
+bool launch_skel_warp(const LevelDev& Lv, const PhaseDev& Ph, uint8_t* alive, double tol,
+                      int* status, int64_t max_m_elems, cudaStream_t s) {
+  if (!Ph.nunit) return true;
+  if (Ph.max_n > 32) return false;
+  const size_t per = skel_warp_bytes(Ph.max_n, max_m_elems, sizeof(T));
+  int wpc = (int)std::min<size_t>(8, (200 * 1024) / per);
+  if (wpc < 1) return false;
+  const unsigned grid = (unsigned)((Ph.nunit + wpc - 1) / wpc);
+  k_skel_warp<T><<<grid, 32 * wpc, wpc * per, s>>>(Lv, Ph, alive, tol, status, (int)per);
+  k_mark_dead<<<Ph.nunit, 32, 0, s>>>(Lv, Ph, alive);
+  return true;
+}
+
+template <typename T>
 size_t skel_cluster_fixed_bytes(int max_n, int C) {
   const size_t ldp = skel_cluster_ldp(max_n);
   return (partial_chol_smem_elems() + (1 + 2 * (size_t)C) * ldp) * sizeof(T) + ldp * sizeof(int) +
@@ -1660,6 +1869,8 @@ int configure_factor_kernels() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_skel_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_skel_warp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_skel_cluster<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_leaf_elim<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
@@ -1689,6 +1900,8 @@ int configure_factor_kernels() {
                                cudaStream_t);                                                     \
   template size_t skel_smem_bytes<T>(int);                                                        \
   template size_t skel_cluster_fixed_bytes<T>(int, int);                                          \
+  template bool launch_skel_warp<T>(const LevelDev&, const PhaseDev&, uint8_t*, double, int*,     \
+                                    int64_t, cudaStream_t);                                       \
   template int skel_cluster_schedulable<T>(int, size_t);                                          \
   template cudaError_t launch_skel_cluster<T>(const LevelDev&, const PhaseDev&, uint8_t*, double, \
                                               int*, int, int64_t, size_t, cudaStream_t);          \

@@ -61,6 +61,11 @@ size_t skel_smem_bytes(int max_n);
 // Skeletonization with one thread-block cluster of C CTAs per unit; each CTA
 // stages its row slice of A_{R,g} in shared memory when it has at most
 // slice_cap elements.  smem = skel_cluster_fixed_bytes + slice bytes.
+// One warp per unit when every unit has n <= 32 and fits the warp's shared
+// memory; returns false (nothing launched) otherwise.
+template <typename T>
+bool launch_skel_warp(const LevelDev& Lv, const PhaseDev& Ph, uint8_t* alive, double tol,
+                      int* status, int64_t max_m_elems, cudaStream_t s);
 template <typename T>
 size_t skel_cluster_fixed_bytes(int max_n, int C);
 template <typename T>

@@ -192,6 +192,7 @@ struct rhif_handle {
   bool precondition = true, edge_skel = false;
   int big_front = 0, big_frame = 0;   // many-CTA thresholds (see rhif_opts)
   int skel_cluster = 0;
+  bool skel_warp = true;   // small units: one warp each
   double tol = 0.0;
   std::vector<rhif::LevelStore> levels;   // 0..L
   double* diag = nullptr;
@@ -386,6 +387,11 @@ static int skeletonize(rhif_handle* H, const LevelPlan& P, const PhasePlan& ph, 
   const size_t elem = sizeof(T);
   const size_t budget = 216 * 1024;
   const bool fits1 = skel_smem_bytes<T>(ph.units.max_n) + ph.units.max_m * elem <= 200 * 1024;
+  if (H->skel_cluster == 0 && H->skel_warp &&
+      launch_skel_warp<T>(L, D, alive, H->tol, H->status, ph.units.max_m, s)) {
+    CK(cudaGetLastError());
+    return RHIF_OK;
+  }
   if (H->skel_cluster < 0 || (H->skel_cluster == 0 && fits1)) {
     launch_skel<T>(L, D, alive, H->tol, H->status, ph.units.max_m, s);
     CK(cudaGetLastError());

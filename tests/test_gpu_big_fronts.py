@@ -46,9 +46,10 @@ def _oracle(ns, leaf, tol, b, edge):
     return _ORACLE[key]
 
 
-# skel_cluster: CTAs per skeletonization unit (thread-block cluster); 0 = default.
+# skel_cluster: CTAs per skeletonization unit (thread-block cluster); 0 = default
+# (one warp per small unit), -1 = one CTA per unit.
 # The 31^3 grid runs with the default and one forced cluster size only.
-PARAMS = [c + (k,) for c in CASES for k in ((0, 4) if c[0] == (31, 31, 31) else (0, 1, 4, 16))]
+PARAMS = [c + (k,) for c in CASES for k in ((0, 4) if c[0] == (31, 31, 31) else (0, -1, 1, 4, 16))]
 
 
 @pytest.mark.parametrize("ns,leaf,tol,b,edge,skel_cluster", PARAMS)

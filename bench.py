@@ -18,7 +18,7 @@ factor is measured beside it under "fp64".
       factor and PCG over 8 streams; DOFs count each problem once
   c5  differentiable solve on 511^2: log a from a smooth seeded field, forward
       PHIF solve, loss 0.5 ||u - u_obs||^2, backward (adjoint PCG with the same
-      factor + gradient kernel); FP32 factor, PCG to 1e-10
+      factor + gradient kernel); leaf 16, tol 1e-6, FP32 factor, PCG to 1e-12
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                        [--workload c1|c2|c3|c4|c5]
@@ -47,7 +47,7 @@ WORKLOADS = {
     "c2": "2d-fd5-1023sq-logunif1e-4..1e4-leaf16-tol1e-3",
     "c3": "3d-fd7-63cube-logunif1e-3..1e3-b1e-2-leaf8-tol1e-3-faces+edges",
     "c4": "batched-64x2d-fd5-sides127..511-logunif1e-3..1e3-leaf8-tol1e-3-32rhs",
-    "c5": "grad-2d-fd5-511sq-smooth-log-a-leaf16-tol1e-3-adjoint",
+    "c5": "grad-2d-fd5-511sq-smooth-log-a-leaf16-tol1e-6-adjoint-rtol1e-12",
 }
 
 
@@ -116,7 +116,7 @@ log_a = 0.3 * W.gaussian_bump_log_field(ns, {seed})
 t0 = time.perf_counter()
 a = np.exp(log_a)
 A = fd.assemble(ns, a, 0.0)
-F = phif.factor(A, ns, 16, 1e-3)
+F = phif.factor(A, ns, 16, 1e-6)
 u, it, rr = phif.pcg(A, f, M=lambda r: phif.solve(F, r), rtol={rtol})
 lam, it2, rr2 = phif.pcg(A, u - u_obs, M=lambda r: phif.solve(F, r), rtol={rtol})
 g = fd.dA_dlog_a(ns, a, u, lam)
@@ -131,7 +131,7 @@ _SAMPLES = {
     "c2": ("2d", 511, dict(lo=1e-4, hi=1e4, leaf=16, rtol=RTOL), "a 511^2 grid of the same recipe"),
     "c3": ("3d", 31, dict(rtol=RTOL), "a 31^3 grid of the same recipe"),
     "c4": ("batch", 127, dict(rtol=RTOL), "one 127^2 problem of the batch recipe, all 32 RHS"),
-    "c5": ("grad", 255, dict(rtol=RTOL), "the forward+adjoint+gradient step on 255^2"),
+    "c5": ("grad", 255, dict(rtol=1e-12), "the forward+adjoint+gradient step on 255^2"),
 }
 _REF_SIDE = {"c1": 127, "c2": 255, "c3": 23, "c4": 127, "c5": 127}
 
@@ -294,7 +294,7 @@ class Workload:
     def __init__(self, key, rhif, W, torch, dev):
         self.key, self.rhif, self.W, self.torch, self.dev = key, rhif, W, torch, dev
         self.headline = "fp64" if key == "c1" else "fp32"
-        self.rtol = 1e-12 if key == "c1" else RTOL
+        self.rtol = 1e-12 if key in ("c1", "c5") else RTOL
         t = torch
         if key in ("c1", "c2", "c3"):
             p = W.config_problem({"c1": 0, "c2": 1, "c3": 2}[key])
@@ -359,7 +359,7 @@ class Workload:
     def _grad(self, la, f, uo, precision):
         t, r = self.torch, self.rhif
         la = la.detach().requires_grad_(True)
-        u = r.rhif_solve(la, f, self.ns, leaf=16, tol=1e-3, precision=precision, rtol=self.rtol)
+        u = r.rhif_solve(la, f, self.ns, leaf=16, tol=1e-6, precision=precision, rtol=self.rtol)
         loss = 0.5 * t.sum((u - uo) ** 2)
         loss.backward()
         return la.grad, [0], [float(loss.detach())]
@@ -399,7 +399,7 @@ class Workload:
         elif self.key == "c4":
             c.update(problems=len(self.ps), rhs_per_problem=32, leaf=8, tol=1e-3, streams=8)
         else:
-            c.update(N=self.dofs, leaf=16, tol=1e-3, step="forward PCG + adjoint PCG + gradient")
+            c.update(N=self.dofs, leaf=16, tol=1e-6, step="forward PCG + adjoint PCG + gradient")
         return c
 
 

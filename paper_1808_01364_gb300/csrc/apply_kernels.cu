@@ -370,19 +370,26 @@ k_apply_cell_up(LevelDev Lv, double* x, int64_t ldx, int nrhs, double* ubuf, int
                 int stage) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ __align__(8) uint64_t bar;
-  T* y = (T*)smraw;
+  T* x_in = (T*)smraw;
+  T* y = x_in + Lv.max_nI + 1;
   const int c = blockIdx.x;
   const int nI = Lv.nI[c], nB = Lv.nB[c], n = nI + nB;
   const T* F = (const T*)Lv.front + Lv.front_off[c];
-  if (stage) F = front_stage(F, n, nI, (T*)(smraw + round16((Lv.max_nI + 1) * sizeof(T))), &bar);
+  if (stage) F = front_stage(F, n, nI, (T*)(smraw + round16(2 * (Lv.max_nI + 1) * sizeof(T))), &bar);
   const int32_t* gI = Lv.gids + Lv.gid_off[c];
   __syncthreads();
   for (int r = 0; r < nrhs; ++r) {
     double* xr = x + r * ldx;
-    for (int i = threadIdx.x; i < nI; i += blockDim.x) y[i] = T(xr[gI[i]]);
+    for (int i = threadIdx.x; i < nI; i += blockDim.x) x_in[i] = T(xr[gI[i]]);
     if (stage && r == 0 && !staged_ok(&bar, Lv.status, Lv.level, kKindCell, c)) return;
     __syncthreads();
-    cta_trsv_lower(F, n, nI, y);
+    // y = L^{-1} x_I: the front's L block holds L^{-1} (one row per thread)
+    for (int i = threadIdx.x; i < nI; i += blockDim.x) {
+      T s = T(0);
+      for (int k = 0; k <= i; ++k) s += F[i + (int64_t)k * n] * x_in[k];
+      y[i] = s;
+    }
+    __syncthreads();
     for (int i = threadIdx.x; i < nI; i += blockDim.x) xr[gI[i]] = double(y[i]);
     double* u = ubuf + r * ldu + Lv.b_off[c];
     for (int b = threadIdx.x; b < nB; b += blockDim.x) {
@@ -401,11 +408,13 @@ k_apply_cell_down(LevelDev Lv, double* x, int64_t ldx, int nrhs, int stage) {
   __shared__ __align__(8) uint64_t bar;
   T* t = (T*)smraw;
   T* xb = t + Lv.max_nI;
+  T* xo = xb + Lv.max_nB;
   const int c = blockIdx.x;
   const int nI = Lv.nI[c], nB = Lv.nB[c], n = nI + nB;
   const T* F = (const T*)Lv.front + Lv.front_off[c];
   if (stage)
-    F = front_stage(F, n, nI, (T*)(smraw + round16((Lv.max_nI + Lv.max_nB + 1) * sizeof(T))), &bar);
+    F = front_stage(F, n, nI, (T*)(smraw + round16((2 * Lv.max_nI + Lv.max_nB + 1) * sizeof(T))),
+                    &bar);
   const int32_t* gI = Lv.gids + Lv.gid_off[c];
   const int32_t* gB = gI + nI;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -422,8 +431,15 @@ k_apply_cell_down(LevelDev Lv, double* x, int64_t ldx, int nrhs, int stage) {
       if (lane == 0) t[k] = T(xr[gI[k]]) - s;
     }
     __syncthreads();
-    cta_trsv_lower_t(F, n, nI, t);
-    for (int i = threadIdx.x; i < nI; i += blockDim.x) xr[gI[i]] = double(t[i]);
+    // x_I = L^{-T} t: the front's L block holds L^{-1}; one row per warp
+    for (int i = warp; i < nI; i += nwarps) {
+      T s = T(0);
+      for (int k = i + lane; k < nI; k += 32) s += F[k + (int64_t)i * n] * t[k];
+      s = warp_sum(s);
+      if (lane == 0) xo[i] = s;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nI; i += blockDim.x) xr[gI[i]] = double(xo[i]);
     __syncthreads();
   }
 }
@@ -922,7 +938,7 @@ void launch_apply_cell_up(const LevelDev& Lv, double* x, int64_t ldx, int nrhs, 
     k_apply_leaf_up<T><<<grid, 32 * wpc, wpc * per, s>>>(Lv, x, ldx, nrhs, ubuf, ldu, (int)per);
     return;
   }
-  const size_t base = round16((Lv.max_nI + 1) * sizeof(T));
+  const size_t base = round16(2 * (Lv.max_nI + 1) * sizeof(T));
   const size_t blk = round16((size_t)Lv.max_n * Lv.max_nI * sizeof(T));
   const int stage = blk <= kStageBudget;
   k_apply_cell_up<T><<<Lv.ncell, kApplyThreads, base + (stage ? blk : 0), s>>>(Lv, x, ldx, nrhs, ubuf,
@@ -939,7 +955,7 @@ void launch_apply_cell_down(const LevelDev& Lv, double* x, int64_t ldx, int nrhs
     k_apply_leaf_down<T><<<grid, 32 * wpc, wpc * per, s>>>(Lv, x, ldx, nrhs, (int)per);
     return;
   }
-  const size_t base = round16((Lv.max_nI + Lv.max_nB + 1) * sizeof(T));
+  const size_t base = round16((2 * Lv.max_nI + Lv.max_nB + 1) * sizeof(T));
   const size_t blk = round16((size_t)Lv.max_n * Lv.max_nI * sizeof(T));
   const int stage = blk <= kStageBudget;
   k_apply_cell_down<T><<<Lv.ncell, kApplyThreads, base + (stage ? blk : 0), s>>>(Lv, x, ldx, nrhs,

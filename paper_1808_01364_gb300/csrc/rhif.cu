@@ -180,7 +180,7 @@ struct LevelStore {
   // algorithmic work of one sweep direction of the application, per right-hand side
   double cell_flops = 0, cell_bytes = 0;
   std::vector<double> grp_flops, grp_bytes;   // per phase
-  bool big_apply = false;   // fronts hold L^{-1}: many-CTA cell sweeps
+  bool big_apply = false;   // eliminated with the many-CTA schedule: many-CTA cell sweeps
 };
 
 }  // namespace rhif
@@ -205,6 +205,7 @@ struct rhif_handle {
   int64_t ub_len = 0;   // scratch column: max over levels of sum nB, then the interior part
   int64_t ui_len = 0;   // max DOF-list length of the levels with big_apply
   int64_t ui_base = 0;  // offset of the interior part in the scratch column
+  std::vector<int64_t> xoff_host;   // per-cell offsets of the L^{-1} scratch (upload source)
   double* work = nullptr;
   int64_t work_elems = 0;
   double flops = 0.0, apply_bytes = 0.0, factor_ms = 0.0;
@@ -517,7 +518,8 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
         add_launches(kCatExtendAdd,
                      launch_extend_add<T>(S.dev, H->levels[lvl - 1].dev, P.front_total, slots, s));
       }
-      if (P.max_n >= H->big_front && P.ncell() <= kBigFrontCells) {
+      const bool many_cta = P.max_n >= H->big_front && P.ncell() <= kBigFrontCells;
+      if (many_cta) {
         // few large fronts: panel / trailing-tile / Schur-tile launches over all fronts
         Launch t(kCatPartialChol, s, lvl_flops, double(P.front_total) * elem, 0);
         for (int p0 = 0; p0 < P.max_nI; p0 += 32) {
@@ -532,8 +534,16 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
         for (int c = 0; c < P.ncell(); ++c) tiles += front_schur_tiles(P.nI[c], P.nB[c]);
         launch_front_schur<T>(S.dev, tiles, s);
         add_launches(kCatPartialChol, tiles > 0 ? 1 : 0);
-        // L -> L^{-1} in place, for the many-CTA application of these fronts
-        std::vector<int64_t> xoff(P.ncell());
+      } else {
+        Launch t(kCatPartialChol, s, lvl_flops, double(P.front_total) * elem);
+        launch_partial_chol<T>(S.dev, H->status, s);
+      }
+      {
+        // L -> L^{-1} in place: every cell sweep of the application becomes a
+        // row-parallel product (no sequential triangular solve)
+        Launch t(kCatPartialChol, s, 0.0, 0.0, 0);
+        std::vector<int64_t>& xoff = H->xoff_host;   // outlives the async upload
+        xoff.assign(P.ncell(), 0);
         int64_t xtot = 0;
         for (int c = 0; c < P.ncell(); ++c) {
           xoff[c] = xtot;
@@ -547,14 +557,12 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
                            s));
         launch_front_invert<T>(S.dev, (T*)X, (const int64_t*)xo, s);
         add_launches(kCatPartialChol, 2);
-        CK(cudaStreamSynchronize(s));   // xoff is a host vector of this scope
         H->mem.release(X);
         H->mem.release(xo);
-        S.big_apply = true;
-        H->ui_len = std::max<int64_t>(H->ui_len, P.gid_off.back());
-      } else {
-        Launch t(kCatPartialChol, s, lvl_flops, double(P.front_total) * elem);
-        launch_partial_chol<T>(S.dev, H->status, s);
+        if (many_cta) {
+          S.big_apply = true;
+          H->ui_len = std::max<int64_t>(H->ui_len, P.gid_off.back());
+        }
       }
     }
     H->flops += lvl_flops;

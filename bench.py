@@ -60,6 +60,8 @@ def _args():
     p.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     p.add_argument("--fp64-steps", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--paper-tables", action="store_true",
+                   help="HIF vs PHIF study on the paper's quantized field (Sec. 4 tables)")
     return p.parse_args()
 
 
@@ -543,8 +545,56 @@ def gpu_arm(args):
         dist.destroy_process_group()
 
 
+def paper_tables(args):
+    """The structure of the paper's Tables 1-2 on this GPU: for the quantized
+    high-contrast field (Sec. 4) at 1023^2 (leaf 16) and 31^3 / 63^3 (leaf 8,
+    faces + edges), HIF and PHIF at tol 1e-3 and 1e-6 (FP64 factors): factor
+    time, root size, e_s (power iteration, 1e-2 relative change) and PCG
+    iterations to relres 1e-12.  One JSON line."""
+    import numpy as np
+    import torch
+
+    import paper_1808_01364_gb300 as rhif
+    import workloads as W
+    rhif.load()
+    rows = []
+    for ns, leaf in (((1023, 1023), 16), ((31, 31, 31), 8), ((63, 63, 63), 8)):
+        a = torch.as_tensor(W.paper_quantized_field(ns, seed=W.SEED_BASE + 5), device="cuda")
+        n = int(np.prod(ns))
+        f = torch.as_tensor(W.normal_rhs(ns, W.SEED_BASE + 6), device="cuda")
+        x0 = torch.as_tensor(np.random.Generator(np.random.PCG64(7)).standard_normal(n),
+                             device="cuda")
+        csr = rhif.rhif_assemble_fd(ns, a, 0.0)
+        for tol in (1e-3, 1e-6):
+            for pre in (False, True):
+                row = {"grid": "x".join(map(str, ns)), "N": n, "leaf": leaf, "tol": tol,
+                       "method": "PHIF" if pre else "HIF"}
+                try:
+                    torch.cuda.synchronize()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    F = rhif.rhif_factor(csr, ns, leaf, tol, precision="fp64", precondition=pre,
+                                         edge_skel_3d=len(ns) == 3)
+                    e1.record()
+                    e1.synchronize()
+                    st = F.stats()
+                    es, _ = F.estimate_es(x0)
+                    _, its, rr = F.pcg(f, rtol=1e-12, maxit=1000, check=False)
+                    row.update(factor_ms=e0.elapsed_time(e1), root=st["root_size"], e_s=es,
+                               pcg_iters=its[0], relres=rr[0],
+                               factor_gb=st["factor_bytes"] / 1e9)
+                    F.free()
+                except rhif.RhifError as e:
+                    row["failed"] = str(e).split(":")[0]
+                rows.append(row)
+    print(json.dumps({"paper_tables": rows}))
+
+
 def main():
     args = _args()
+    if args.paper_tables:
+        paper_tables(args)
+        return
     if args.impl == "reference":
         reference_arm(args)
     else:

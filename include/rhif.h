@@ -179,6 +179,16 @@ int rhif_pcg(const rhif_handle* F, int nrhs, const double* f, int64_t ldf, doubl
              int64_t ldu, double rtol, int maxit, int* iters, double* relres,
              void* stream);
 
+/* Error estimate e_s = ||I - A F^{-1}||_2 (Sec. 4) by power iteration on
+ * M^T M with M = I - A F^{-1}, M^T = I - F^{-1} A (A and F^{-1} symmetric):
+ * v = x0 / ||x0||; repeat w = M^T M v, est = sqrt(||w||), v = w / ||w|| until
+ * two successive estimates differ by at most rel * est or maxit products.
+ * x0: DEVICE vector of N doubles (the start vector; the caller seeds it).
+ * es, iters: HOST scalars receiving the estimate and the number of products.
+ * Uses the handle's work space (no effect on the factor). */
+int rhif_estimate_es(const rhif_handle* F, const double* x0, int maxit, double rel, double* es,
+                     int* iters, void* stream);
+
 /* Per-pixel gradient of a loss with respect to log a, given the state u and
  * the adjoint lam = A^{-1} dLoss/du:  grad_p = -a_p / 2^(d-1) *
  * sum over the grid edges e of pixel p of (lam_i - lam_j)(u_i - u_j)/h_e^2

@@ -89,6 +89,9 @@ EXPORTS = {
                                 ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int,
                                 ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
                                 ctypes.c_void_p]),
+    "rhif_estimate_es": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                        ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]),
     "rhif_grad_logcoef": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "rhif_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Stats)]),
@@ -244,6 +247,15 @@ class Factor:
         if rc != 0 and (check or rc != -3):
             _check(rc)
         return u, list(it), list(rr)
+
+    def estimate_es(self, x0: torch.Tensor, maxit: int = 100, rel: float = 1e-2, stream=None):
+        """e_s = ||I - A F^{-1}||_2 by power iteration from the device vector x0;
+        returns (estimate, number of M^T M products)."""
+        es = ctypes.c_double()
+        it = ctypes.c_int()
+        _check(_lib.rhif_estimate_es(self._h, _ptr(x0.contiguous()), int(maxit), float(rel),
+                                     ctypes.byref(es), ctypes.byref(it), _stream(stream)))
+        return es.value, it.value
 
     def stats(self) -> dict:
         st = Stats()

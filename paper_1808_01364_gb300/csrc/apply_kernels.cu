@@ -1210,6 +1210,14 @@ __global__ void k_copy_cols(int64_t N, const double* a, int64_t lda, double* y, 
     y[i + r * ldy] = a[i + r * lda];
 }
 
+// x <- alpha x (alpha read from the device: sc[0])
+__global__ void k_scale(int64_t N, double* x, const double* alpha) {
+  const double a = *alpha;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x[i] *= a;
+}
+
 int vec_blocks(int64_t N) {
   int64_t b = (N + kVecThreads - 1) / kVecThreads;
   if (b > 1216) b = 1216;   // 8 blocks per SM on 152 SMs
@@ -1245,6 +1253,9 @@ void launch_sub(int64_t N, int nrhs, const double* a, int64_t lda, const double*
                 double* y, int64_t ldy, cudaStream_t s) {
   dim3 grid(vec_blocks(N), nrhs);
   k_sub<<<grid, kVecThreads, 0, s>>>(N, a, lda, b, ldb, y, ldy);
+}
+void launch_scale(int64_t N, double* x, const double* alpha, cudaStream_t s) {
+  k_scale<<<vec_blocks(N), kVecThreads, 0, s>>>(N, x, alpha);
 }
 void launch_copy_cols(int64_t N, int nrhs, const double* a, int64_t lda, double* y, int64_t ldy,
                       cudaStream_t s) {

@@ -1043,7 +1043,9 @@ __device__ void skel_pivot(const T* nrm, const int* sperm, int j, int n, double 
     mx = y > mx ? y : mx;
   }
   const T r11 = j == 0 ? my_sqrt(mx) : *s_r11;
-  const int stop = (r11 == T(0)) || (my_sqrt(mx) <= T(tol) * r11);
+  // NaN norms (a breakdown earlier in the level, reported by its own kernel)
+  // stop the decomposition instead of producing a pivot outside the columns
+  int stop = (r11 == T(0)) || !(mx == mx) || !(r11 == r11) || (my_sqrt(mx) <= T(tol) * r11);
   int best = -1, bo = 0x7fffffff;
   if (!stop) {
     const T thr = T(1.0 - 1e-12) * mx;
@@ -1061,6 +1063,7 @@ __device__ void skel_pivot(const T* nrm, const int* sperm, int j, int n, double 
         best = oc;
       }
     }
+    if (best < 0) stop = 1;
   }
   if (lane == 0) {
     if (j == 0) *s_r11 = r11;
@@ -1341,7 +1344,7 @@ __global__ void __launch_bounds__(256) k_skel_warp(LevelDev Lv, PhaseDev Ph, uin
       mx = y > mx ? y : mx;
     }
     if (j == 0) r11 = my_sqrt(mx);
-    if (r11 == T(0) || my_sqrt(mx) <= T(tol) * r11) break;
+    if (r11 == T(0) || !(mx == mx) || !(r11 == r11) || my_sqrt(mx) <= T(tol) * r11) break;
     const T thr = T(1.0 - 1e-12) * mx;
     int key = (cand && nrm >= thr) ? sp[lane] : 0x7fffffff, p = lane;
 #pragma unroll
@@ -1350,6 +1353,7 @@ __global__ void __launch_bounds__(256) k_skel_warp(LevelDev Lv, PhaseDev Ph, uin
       const int op = __shfl_xor_sync(0xffffffffu, p, o);
       if (ok < key || (ok == key && op < p)) { key = ok; p = op; }
     }
+    if (key == 0x7fffffff || p < j || p >= n) break;   // no candidate (NaN norms)
     if (p != j) {
       for (int i = lane; i < nrow; i += 32) {
         const T a = M[i + (int64_t)j * ld];

@@ -1073,6 +1073,75 @@ int rhif_pcg(const rhif_handle* Fc, int nrhs, const double* f, int64_t ldf, doub
   return RHIF_OK;
 }
 
+int rhif_estimate_es(const rhif_handle* Fc, const double* x0, int maxit, double rel, double* es,
+                     int* iters, void* stream) {
+  rhif_handle* F = const_cast<rhif_handle*>(Fc);
+  if (!F || !x0 || !es || maxit < 1 || !(rel >= 0.0)) return fail(RHIF_ERR_BAD_ARG, "bad argument");
+  const int64_t N = F->G.N;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nblk = vec_blocks(N);
+  int rc = ensure_work(F, 4 * N + nblk + 16);
+  if (rc) return rc;
+  double* v = F->work;
+  double* z = v + N;
+  double* w = z + N;
+  double* t = w + N;
+  double* part = t + N;
+  double* sc = part + nblk;   // 8 slots; sc[kScFF] receives the reductions
+  double* inv = sc + 8;       // 1 / norm for the rescaling
+  std::vector<double> hsc(8);
+  auto norm2 = [&](const double* x, double* out) -> int {
+    launch_dot_partial(N, x, N, x, N, 1, part, s);
+    launch_reduce(part, nblk, 1, sc, 0, 0.0, s);
+    CK(cudaMemcpyAsync(hsc.data(), sc, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *out = std::sqrt(hsc[kScFF]);
+    return RHIF_OK;
+  };
+  auto set_inv = [&](double nv) -> int {
+    const double a = 1.0 / nv;
+    CK(cudaMemcpyAsync(inv, &a, sizeof(double), cudaMemcpyHostToDevice, s));
+    launch_scale(N, v, inv, s);
+    CK(cudaStreamSynchronize(s));   // `a` is a host local
+    return RHIF_OK;
+  };
+  launch_copy_cols(N, 1, x0, N, v, N, s);
+  double nv = 0.0;
+  if ((rc = norm2(v, &nv))) return rc;
+  if (nv == 0.0) return fail(RHIF_ERR_BAD_ARG, "zero start vector");
+  if ((rc = set_inv(nv))) return rc;
+  double est = 0.0;
+  int it = 0;
+  for (it = 1; it <= maxit; ++it) {
+    // w = M v = v - A F^{-1} v ; then w = M^T w = w - F^{-1} A w
+    launch_copy_cols(N, 1, v, N, z, N, s);
+    if ((rc = apply_dispatch(F, z, N, 1, s))) return rc;
+    launch_spmv(F->gd, F->diag, F->off, z, N, t, N, 1, nullptr, s);
+    launch_sub(N, 1, v, N, t, N, w, N, s);
+    launch_spmv(F->gd, F->diag, F->off, w, N, t, N, 1, nullptr, s);
+    if ((rc = apply_dispatch(F, t, N, 1, s))) return rc;
+    launch_sub(N, 1, w, N, t, N, w, N, s);
+    double nw = 0.0;
+    if ((rc = norm2(w, &nw))) return rc;
+    const double cur = std::sqrt(nw);
+    if (nw == 0.0) {
+      est = 0.0;
+      break;
+    }
+    launch_copy_cols(N, 1, w, N, v, N, s);
+    if ((rc = set_inv(nw))) return rc;
+    if (est > 0.0 && std::fabs(cur - est) <= rel * cur) {
+      est = cur;
+      break;
+    }
+    est = cur;
+  }
+  *es = est;
+  if (iters) *iters = std::min(it, maxit);
+  CK(cudaGetLastError());
+  return RHIF_OK;
+}
+
 int rhif_grad_logcoef(const rhif_grid* g, const double* a_pix, const double* u, const double* lam,
                       double* grad, void* stream) {
   int rc = check_grid(g);

@@ -219,3 +219,24 @@ def test_pcg_does_not_read_stale_scratch(gpu_lib):
         assert rr[r] <= 1.5e-10
         ud = spla.spsolve(A.tocsc(), F[r])
         assert np.linalg.norm(U[r] - ud) <= 1e-7 * np.linalg.norm(ud)
+
+
+@pytest.mark.parametrize("skel_cluster", [-1, 0, 4])
+@pytest.mark.parametrize("precondition", [True, False])
+def test_separator_breakdown_reported(gpu_lib, skel_cluster, precondition):
+    """A negative diagonal on a separator DOF makes a later Cholesky of the
+    level fail (block Jacobi factor or redundant-DOF elimination); the NaNs
+    that reach the interpolative decompositions of the same level must stop
+    them cleanly, and the factorization reports NOT_SPD."""
+    ns, leaf = (15, 15), 4
+    a = W.log_uniform_pixels(ns, 1e-2, 1e2, seed=1)
+    rp, col, val = _gpu_matrix(gpu_lib, ns, a, 0.0)
+    v = val.cpu().numpy()
+    rpn, cn = rp.cpu().numpy(), col.cpu().numpy()
+    i = 4 + 15 * 5 - 1   # x = 4, y = 6 (1-based): on a level-0 separator edge
+    k = rpn[i] + np.nonzero(cn[rpn[i]:rpn[i + 1]] == i)[0][0]
+    v[k] = -50.0 * abs(v[k])
+    with pytest.raises(gpu_lib.RhifError) as e:
+        gpu_lib.rhif_factor((rp, col, _dev(v)), ns, leaf, 1e-3, precondition=precondition,
+                            skel_cluster=skel_cluster)
+    assert e.value.code == -2

@@ -82,7 +82,12 @@ typedef struct {
    *   does not fit in one CTA's shared memory, else one CTA per unit), < 0 =
    *   one CTA per unit always, 1..16 = clusters of that size always. */
   int skel_cluster;
-  int reserved[2];
+  /* tensor_cores: FP32 factors form the Schur complements of fronts eliminated
+   *   with the many-CTA schedule on the tensor cores (TF32 inputs split into
+   *   a high part and a remainder: about FP32 accuracy); 0 = on (default),
+   *   < 0 = off (CUDA cores).  FP64 factors always use the CUDA cores. */
+  int tensor_cores;
+  int reserved[1];
 } rhif_opts;
 
 typedef struct rhif_handle rhif_handle;
@@ -188,6 +193,15 @@ int rhif_pcg(const rhif_handle* F, int nrhs, const double* f, int64_t ldf, doubl
  * Uses the handle's work space (no effect on the factor). */
 int rhif_estimate_es(const rhif_handle* F, const double* x0, int maxit, double rel, double* es,
                      int* iters, void* stream);
+
+/* C -= A B^T on the tensor cores (tcgen05, TF32 inputs split into a high
+ * part and a remainder, FP32 accumulation: about FP32 accuracy), the product
+ * used for the dense Schur updates of large fronts (Sec. 2.1), exported so
+ * that it can be checked on a device.  A is M x K, B is N x K, C is M x N,
+ * all FP32 DEVICE arrays in column-major order with leading dimensions lda,
+ * ldb, ldc; M, N >= 1, K >= 0.  RHIF_ERR_TIMEOUT if a bounded wait gave up. */
+int rhif_tc_gemm_check(int M, int N, int K, const float* A, int64_t lda, const float* B,
+                       int64_t ldb, float* C, int64_t ldc, void* stream);
 
 /* Per-pixel gradient of a loss with respect to log a, given the state u and
  * the adjoint lam = A^{-1} dLoss/du:  grad_p = -a_p / 2^(d-1) *

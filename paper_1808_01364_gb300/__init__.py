@@ -49,7 +49,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("precondition", ctypes.c_int),
                 ("edge_skel_3d", ctypes.c_int), ("big_front", ctypes.c_int),
                 ("big_frame", ctypes.c_int), ("skel_cluster", ctypes.c_int),
-                ("reserved", ctypes.c_int * 2)]
+                ("tensor_cores", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
 
 
 class Stats(ctypes.Structure):
@@ -89,6 +89,10 @@ EXPORTS = {
                                 ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int,
                                 ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
                                 ctypes.c_void_p]),
+    "rhif_tc_gemm_check": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                          ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
+                                          ctypes.c_void_p]),
     "rhif_estimate_es": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                         ctypes.c_double, ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]),
@@ -154,6 +158,14 @@ def _stream(stream=None):
 
 def _ptr(t: torch.Tensor):
     assert t.is_cuda and t.is_contiguous(), "expected a contiguous CUDA tensor"
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _colptr(t: torch.Tensor):
+    """Pointer of a 2-D CUDA tensor stored column-major (unit row stride)."""
+    assert t.is_cuda and t.dim() == 2 and (t.stride(0) == 1 or t.shape[0] <= 1 or
+                                            t.numel() == 0), \
+        "expected a column-major 2-D CUDA tensor"
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -285,7 +297,7 @@ class Factor:
 
 def rhif_factor(csr, ns, leaf: int, tol: float, precision: str = "fp64", precondition=True,
                 edge_skel_3d=False, stream=None, big_front=0, big_frame=0,
-                skel_cluster=0) -> Factor:
+                skel_cluster=0, tensor_cores=0) -> Factor:
     """PHIF factorization of the CSR matrix ``csr = (rowptr, col, val)`` on grid ``ns``.
     ``big_front`` / ``big_frame`` / ``skel_cluster`` are the scheduling options of
     ``rhif_opts``."""
@@ -293,11 +305,26 @@ def rhif_factor(csr, ns, leaf: int, tol: float, precision: str = "fp64", precond
     rowptr, col, val = csr
     N = rowptr.numel() - 1
     A = CSR(N, val.numel(), rowptr.data_ptr(), col.data_ptr(), val.data_ptr())
-    o = _opts(precision, precondition, edge_skel_3d, big_front, big_frame, skel_cluster)
+    o = _opts(precision, precondition, edge_skel_3d, big_front, big_frame, skel_cluster,
+              tensor_cores)
     h = ctypes.c_void_p()
     _check(_lib.rhif_factor(ctypes.byref(A), ctypes.byref(_grid(ns)), int(leaf), float(tol),
                             ctypes.byref(o), _stream(stream), ctypes.byref(h)))
     return Factor(h, ns, None)
+
+
+def rhif_tc_gemm_check(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor, stream=None):
+    """C -= A B^T on the tensor cores (3xTF32); A (M, K), B (N, K), C (M, N) FP32
+    tensors given in column-major order, i.e. as the transposes of row-major
+    tensors: pass A.t().contiguous().t() etc."""
+    load()
+    M, K = A.shape
+    N = B.shape[0]
+    lda = max(int(A.stride(1)), M) if K > 0 else M
+    ldb = max(int(B.stride(1)), N) if K > 0 else N
+    _check(_lib.rhif_tc_gemm_check(int(M), int(N), int(K), _colptr(A), lda, _colptr(B), ldb,
+                                   _colptr(C), max(int(C.stride(1)), M), _stream(stream)))
+    return C
 
 
 def rhif_grad_logcoef(ns, a_pix: torch.Tensor, u: torch.Tensor, lam: torch.Tensor, stream=None):
@@ -392,7 +419,7 @@ def rhif_solve(log_a: torch.Tensor, f: torch.Tensor, ns, **opts) -> torch.Tensor
 
 
 def _opts(precision="fp64", precondition=True, edge_skel_3d=False, big_front=0,
-          big_frame=0, skel_cluster=0) -> Opts:
+          big_frame=0, skel_cluster=0, tensor_cores=0) -> Opts:
     o = Opts()
     _lib.rhif_default_opts(ctypes.byref(o))
     o.precision = {"fp64": RHIF_FP64, "fp32": RHIF_MIXED_FP32, "mixed": RHIF_MIXED_FP32}[precision]
@@ -401,6 +428,7 @@ def _opts(precision="fp64", precondition=True, edge_skel_3d=False, big_front=0,
     o.big_front = int(big_front)
     o.big_frame = int(big_frame)
     o.skel_cluster = int(skel_cluster)
+    o.tensor_cores = int(tensor_cores)
     return o
 
 

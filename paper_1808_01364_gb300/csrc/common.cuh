@@ -206,12 +206,14 @@ constexpr int partial_chol_smem_elems() { return kNB * (kNB + 1) + 2 * kKC * (kT
 // (warp 0) and scale the rows below it, rows (p0+nb .. n) <- rows * D^{-T}.
 // Returns false if a pivot is not positive.  D is shared scratch of
 // kNB*(kNB+1) elements.
+// Factor the nb x nb diagonal block at p0 in place (warp 0, staged in D, a
+// shared [kNB][kNB+1] array that keeps the factor on return).  Returns false
+// if a pivot is not positive.
 template <typename T>
-__device__ bool cta_panel(T* A, int64_t ld, int n, int p0, int nb, T* D) {
+__device__ bool cta_diag_chol(T* A, int64_t ld, int p0, int nb, T* D) {
   __shared__ int bad;
   if (threadIdx.x == 0) bad = 0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int p1 = p0 + nb;
   for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
     const int i = idx % nb, j = idx / nb;
     D[i * (kNB + 1) + j] = (i >= j) ? A[(p0 + i) + (int64_t)(p0 + j) * ld] : T(0);
@@ -241,7 +243,15 @@ __device__ bool cta_panel(T* A, int64_t ld, int n, int p0, int nb, T* D) {
     const int i = idx % nb, j = idx / nb;
     if (i >= j) A[(p0 + i) + (int64_t)(p0 + j) * ld] = D[i * (kNB + 1) + j];
   }
-  for (int i = p1 + threadIdx.x; i < n; i += blockDim.x) {
+  __syncthreads();
+  return bad == 0;
+}
+
+// Rows [r0, r1) of the panel at p0 (nb columns) <- rows * L_pp^{-T}, with the
+// factored diagonal block in D; one row per thread.
+template <typename T>
+__device__ void cta_panel_rows(T* A, int64_t ld, int r0, int r1, int p0, int nb, const T* D) {
+  for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
     T r[kNB];
 #pragma unroll
     for (int j = 0; j < kNB; ++j) r[j] = (j < nb) ? A[i + (int64_t)(p0 + j) * ld] : T(0);
@@ -258,8 +268,59 @@ __device__ bool cta_panel(T* A, int64_t ld, int n, int p0, int nb, T* D) {
     for (int j = 0; j < kNB; ++j)
       if (j < nb) A[i + (int64_t)(p0 + j) * ld] = r[j];
   }
+}
+
+// One panel of the blocked Cholesky: factor the nb x nb diagonal block at p0
+// and scale the rows below it, rows (p0+nb .. n) <- rows * D^{-T}.  Returns
+// false if a pivot is not positive.  D is shared scratch of kNB*(kNB+1)
+// elements.
+template <typename T>
+__device__ bool cta_panel(T* A, int64_t ld, int n, int p0, int nb, T* D) {
+  const bool ok = cta_diag_chol(A, ld, p0, nb, D);
+  cta_panel_rows(A, ld, p0 + nb, n, p0, nb, D);
   __syncthreads();
-  return bad == 0;
+  return ok;
+}
+
+// X[:, J0 : J0+64] = L^{-1} E[:, J0 : J0+64] for the n x n lower-triangular L
+// (ld ldl), written to X (ld ldx) for rows J0..n: by 64-row blocks from the
+// diagonal down, a tile product with the rows above and then a per-column
+// solve with the diagonal block staged in shared memory.  Rows above J0 are
+// not written.  sm: kTile*(kTile+1) >= 2*kKC*(kTile+1) elements.
+template <typename T>
+__device__ void cta_trinv_block(const T* L, int64_t ldl, int n, T* X, int64_t ldx, int J0, T* sm) {
+  const int nc = min(kTile, n - J0);
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  auto fa = [&](int i, int k) { return L[i + (int64_t)(J0 + k) * ldl]; };
+  auto fb = [&](int k, int j) { return X[(J0 + k) + (int64_t)(J0 + j) * ldx]; };
+  for (int I0 = J0; I0 < n; I0 += kTile) {
+    const int nr = min(kTile, n - I0);
+    T acc[4][4];
+    cta_tile_product<T, false, true>(I0, 0, n, nc, I0 - J0, fa, fb, sm, acc);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int i = ty + 16 * a, j = tx + 16 * b;
+        if (i < nr && j < nc)
+          X[(I0 + i) + (int64_t)(J0 + j) * ldx] = (I0 + i == J0 + j ? T(1) : T(0)) - acc[a][b];
+      }
+    T* Rb = sm;   // L[I, I], [kTile][kTile + 1]
+    for (int idx = tid; idx < nr * nr; idx += blockDim.x) {
+      const int i = idx / nr, q = idx % nr;
+      Rb[i * (kTile + 1) + q] = q <= i ? L[(I0 + i) + (int64_t)(I0 + q) * ldl] : T(0);
+    }
+    __syncthreads();
+    for (int j = tid; j < nc; j += blockDim.x) {
+      T* col = X + (int64_t)(J0 + j) * ldx + I0;
+      for (int i = 0; i < nr; ++i) {
+        T v = col[i];
+        for (int q = 0; q < i; ++q) v -= Rb[i * (kTile + 1) + q] * col[q];
+        col[i] = v / Rb[i * (kTile + 1) + i];
+      }
+    }
+    __syncthreads();
+  }
 }
 
 // Blocked partial Cholesky of the n x n SPD front A (lower triangle, ld):

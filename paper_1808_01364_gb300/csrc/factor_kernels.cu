@@ -593,16 +593,38 @@ __global__ void __launch_bounds__(kThreads) k_partial_chol(LevelDev Lv, int* sta
 // Schur complement of the boundary block, C_BB -= W W^T, tile by tile.
 // ---------------------------------------------------------------------------
 
+// Panel at p0 of every front, in two launches: the nb x nb diagonal block
+// (one CTA per front) and the rows below it (one CTA per 256 rows of a front,
+// the factored block staged in shared memory).
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_front_panel(LevelDev Lv, int p0, int* status) {
+__global__ void __launch_bounds__(kThreads) k_front_pdiag(LevelDev Lv, int p0, int* status) {
   extern __shared__ unsigned char smraw[];
   const int c = blockIdx.x;
   const int nI = Lv.nI[c], n = nI + Lv.nB[c];
   if (p0 >= nI) return;
   T* F = (T*)Lv.front + Lv.front_off[c];
   const int nb = min(kNB, nI - p0);
-  if (!cta_panel(F, n, n, p0, nb, (T*)smraw) && threadIdx.x == 0)
+  if (!cta_diag_chol(F, n, p0, nb, (T*)smraw) && threadIdx.x == 0)
     report(status, RHIF_ERR_NOT_SPD, Lv.level, kKindCell, c);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_front_prows(LevelDev Lv, int p0) {
+  extern __shared__ unsigned char smraw[];
+  T* D = (T*)smraw;
+  const int c = blockIdx.y;
+  const int nI = Lv.nI[c], n = nI + Lv.nB[c];
+  if (p0 >= nI) return;
+  const int nb = min(kNB, nI - p0);
+  const int r0 = p0 + nb + blockIdx.x * kThreads;
+  if (r0 >= n) return;
+  T* F = (T*)Lv.front + Lv.front_off[c];
+  for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
+    const int i = idx % nb, j = idx / nb;
+    D[i * (kNB + 1) + j] = (i >= j) ? F[(p0 + i) + (int64_t)(p0 + j) * n] : T(0);
+  }
+  __syncthreads();
+  cta_panel_rows(F, n, r0, min(n, r0 + kThreads), p0, nb, D);
 }
 
 __host__ __device__ inline int64_t trail_tiles(int nI, int n, int p0) {
@@ -667,45 +689,28 @@ __global__ void __launch_bounds__(kThreads) k_front_schur(LevelDev Lv) {
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_front_trinv(LevelDev Lv, T* X, const int64_t* xoff) {
   extern __shared__ unsigned char smraw[];
-  T* sm = (T*)smraw;
   const int c = blockIdx.y;
   const int nI = Lv.nI[c], n = nI + Lv.nB[c];
   const int J0 = blockIdx.x * kTile;
   if (J0 >= nI) return;
-  const int nc = min(kTile, nI - J0);
-  const T* F = (const T*)Lv.front + Lv.front_off[c];
-  T* Xc = X + xoff[c];
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  auto fa = [&](int i, int k) { return F[i + (int64_t)(J0 + k) * n]; };
-  auto fb = [&](int k, int j) { return Xc[(J0 + k) + (int64_t)(J0 + j) * nI]; };
-  for (int I0 = J0; I0 < nI; I0 += kTile) {
-    const int nr = min(kTile, nI - I0);
-    T acc[4][4];
-    cta_tile_product<T, false, true>(I0, 0, nI, nc, I0 - J0, fa, fb, sm, acc);
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const int i = ty + 16 * a, j = tx + 16 * b;
-        if (i < nr && j < nc)
-          Xc[(I0 + i) + (int64_t)(J0 + j) * nI] = (I0 + i == J0 + j ? T(1) : T(0)) - acc[a][b];
-      }
-    T* Rb = sm;   // L[I, I], [kTile][kTile + 1]
-    for (int idx = tid; idx < nr * nr; idx += blockDim.x) {
-      const int i = idx / nr, q = idx % nr;
-      Rb[i * (kTile + 1) + q] = q <= i ? F[(I0 + i) + (int64_t)(I0 + q) * n] : T(0);
-    }
-    __syncthreads();
-    for (int j = tid; j < nc; j += blockDim.x) {
-      T* col = Xc + (int64_t)(J0 + j) * nI + I0;
-      for (int i = 0; i < nr; ++i) {
-        T v = col[i];
-        for (int q = 0; q < i; ++q) v -= Rb[i * (kTile + 1) + q] * col[q];
-        col[i] = v / Rb[i * (kTile + 1) + i];
-      }
-    }
-    __syncthreads();
-  }
+  cta_trinv_block((const T*)Lv.front + Lv.front_off[c], n, nI, X + xoff[c], nI, J0, (T*)smraw);
+}
+
+// L_g^{-1} of every preconditioned group, one CTA per (group, 64-column
+// block), into Ph.Linv (same layout as Lbuf, upper triangle zero).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_group_trinv(LevelDev Lv, PhaseDev Ph) {
+  extern __shared__ unsigned char smraw[];
+  const int b = blockIdx.y;
+  const int sz = Lv.group_size[Ph.pre_group[b]];
+  const int J0 = blockIdx.x * kTile;
+  if (J0 >= sz) return;
+  const T* Lg = (const T*)Ph.Lbuf + Ph.pre_off[b];
+  T* X = (T*)Ph.Linv + Ph.pre_off[b];
+  const int nc = min(kTile, sz - J0);
+  for (int idx = threadIdx.x; idx < J0 * nc; idx += blockDim.x)
+    X[(idx % J0) + (int64_t)(J0 + idx / J0) * sz] = T(0);
+  cta_trinv_block(Lg, sz, sz, X, sz, J0, (T*)smraw);
 }
 
 template <typename T>
@@ -750,19 +755,6 @@ __global__ void __launch_bounds__(kThreads) k_precond_diag(LevelDev Lv, PhaseDev
   __syncthreads();
   if (!cta_partial_chol(Lg, sz, sz, sz, sm) && threadIdx.x == 0)
     report(status, RHIF_ERR_NOT_SPD, Lv.level, kKindGroup, g);
-  if (!Ph.Linv) return;
-  __syncthreads();
-  // explicit inverse of L_g by forward substitution, one column per thread
-  T* Li = (T*)Ph.Linv + Ph.pre_off[b];
-  for (int j = threadIdx.x; j < sz; j += blockDim.x) {
-    T* x = Li + (int64_t)j * sz;
-    for (int i = 0; i < j; ++i) x[i] = T(0);
-    for (int i = j; i < sz; ++i) {
-      T v = i == j ? T(1) : T(0);
-      for (int k = j; k < i; ++k) v -= Lg[i + (int64_t)k * sz] * x[k];
-      x[i] = v / Lg[i + (int64_t)i * sz];
-    }
-  }
 }
 
 // frame <- D^{-1} frame D^{-T}, D = block diag of the L_g of the frame's groups
@@ -1739,7 +1731,11 @@ void launch_partial_chol(const LevelDev& Lv, int* status, cudaStream_t s) {
 
 template <typename T>
 void launch_front_panel(const LevelDev& Lv, int p0, int* status, cudaStream_t s) {
-  k_front_panel<T><<<Lv.ncell, kThreads, kNB * (kNB + 1) * sizeof(T), s>>>(Lv, p0, status);
+  const size_t sm = kNB * (kNB + 1) * sizeof(T);
+  k_front_pdiag<T><<<Lv.ncell, kThreads, sm, s>>>(Lv, p0, status);
+  const int rows = Lv.max_n - p0;
+  if (rows > 0)
+    k_front_prows<T><<<dim3((rows + kThreads - 1) / kThreads, Lv.ncell), kThreads, sm, s>>>(Lv, p0);
 }
 
 template <typename T>
@@ -1761,6 +1757,10 @@ template <typename T>
 void launch_precond_diag(const LevelDev& Lv, const PhaseDev& Ph, int* status, cudaStream_t s) {
   if (Ph.npre)
     k_precond_diag<T><<<Ph.npre, kThreads, partial_chol_smem_elems() * sizeof(T), s>>>(Lv, Ph, status);
+  if (Ph.npre && Ph.Linv) {
+    const unsigned nb = (unsigned)((Lv.max_group + kTile - 1) / kTile);
+    k_group_trinv<T><<<dim3(nb, Ph.npre), kThreads, kTile * (kTile + 1) * sizeof(T), s>>>(Lv, Ph);
+  }
 }
 
 template <typename T>

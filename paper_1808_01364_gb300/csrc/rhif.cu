@@ -193,6 +193,7 @@ struct rhif_handle {
   int big_front = 0, big_frame = 0;   // many-CTA thresholds (see rhif_opts)
   int skel_cluster = 0;
   bool skel_warp = true;   // small units: one warp each
+  bool tensor_cores = true;   // FP32 Schur complements of large fronts on tcgen05
   double tol = 0.0;
   std::vector<rhif::LevelStore> levels;   // 0..L
   double* diag = nullptr;
@@ -233,6 +234,7 @@ static int configure_once() {
   if (!done) {
     rc = configure_factor_kernels<T>();
     if (rc == 0) rc = configure_apply_kernels<T>();
+    if (rc == 0) rc = configure_tc_kernels();
     // keep freed factor memory in this process's stream-ordered pool between factorizations
     int dev = 0;
     cudaMemPool_t pool;
@@ -528,11 +530,16 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
             tiles += front_trailing_tiles(P.nI[c], P.nI[c] + P.nB[c], p0);
           launch_front_panel<T>(S.dev, p0, H->status, s);
           launch_front_trailing<T>(S.dev, p0, tiles, s);
-          add_launches(kCatPartialChol, tiles > 0 ? 2 : 1);
+          add_launches(kCatPartialChol, tiles > 0 ? 3 : 2);
         }
         int64_t tiles = 0;
-        for (int c = 0; c < P.ncell(); ++c) tiles += front_schur_tiles(P.nI[c], P.nB[c]);
-        launch_front_schur<T>(S.dev, tiles, s);
+        if (sizeof(T) == 4 && H->tensor_cores) {
+          for (int c = 0; c < P.ncell(); ++c) tiles += front_schur_tc_tiles(P.nI[c], P.nB[c]);
+          launch_front_schur_tc(S.dev, tiles, H->status, s);
+        } else {
+          for (int c = 0; c < P.ncell(); ++c) tiles += front_schur_tiles(P.nI[c], P.nB[c]);
+          launch_front_schur<T>(S.dev, tiles, s);
+        }
         add_launches(kCatPartialChol, tiles > 0 ? 1 : 0);
       } else {
         Launch t(kCatPartialChol, s, lvl_flops, double(P.front_total) * elem);
@@ -907,6 +914,7 @@ int rhif_factor(const rhif_csr* A, const rhif_grid* g, int leaf, double tol, con
   if (o->skel_cluster > 16 || (o->skel_cluster > 0 && (o->skel_cluster & (o->skel_cluster - 1))))
     return fail(RHIF_ERR_BAD_ARG, "skel_cluster must be a power of two <= 16");
   H->skel_cluster = o->skel_cluster;
+  H->tensor_cores = o->tensor_cores >= 0;
   H->tol = tol;
   H->mem.s = (cudaStream_t)stream;
   cudaEvent_t e0, e1;
@@ -1139,6 +1147,28 @@ int rhif_estimate_es(const rhif_handle* Fc, const double* x0, int maxit, double 
   *es = est;
   if (iters) *iters = std::min(it, maxit);
   CK(cudaGetLastError());
+  return RHIF_OK;
+}
+
+int rhif_tc_gemm_check(int M, int N, int K, const float* A, int64_t lda, const float* B,
+                       int64_t ldb, float* C, int64_t ldc, void* stream) {
+  if (M < 1 || N < 1 || K < 0 || !C || ldc < M || (K > 0 && (!A || !B || lda < M || ldb < N)))
+    return fail(RHIF_ERR_BAD_ARG, "bad GEMM arguments");
+  static std::once_flag once;
+  static int cfg = 0;
+  std::call_once(once, [] { cfg = configure_tc_kernels(); });
+  if (cfg) return fail(RHIF_ERR_CUDA, "cannot configure the tensor-core kernel");
+  cudaStream_t s = (cudaStream_t)stream;
+  int* st = nullptr;
+  CK(cudaMallocAsync((void**)&st, 4 * sizeof(int), s));
+  CK(cudaMemsetAsync(st, 0, 4 * sizeof(int), s));
+  launch_tc_gemm_check(M, N, K, A, lda, B, ldb, C, ldc, st, s);
+  int h[4] = {0, 0, 0, 0};
+  CK(cudaMemcpyAsync(h, st, sizeof(h), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  cudaFreeAsync(st, s);
+  CK(cudaGetLastError());
+  if (h[0]) return fail(h[0], "tensor-core wait timed out");
   return RHIF_OK;
 }
 

@@ -106,3 +106,26 @@ def test_many_cta_schedules_agree_with_one_cta_schedule(gpu_lib, precision):
     assert float(torch.linalg.norm(u1 - u0) / torch.linalg.norm(u0)) <= 1e-8
     on.free()
     off.free()
+
+
+def test_tensor_core_schur_agrees_with_cuda_cores(gpu_lib):
+    """FP32 factor with the Schur complements of the large fronts on the
+    tensor cores (3xTF32) vs on the CUDA cores: F^{-1} x agrees to FP32-level
+    rounding when the skeletons coincide, and PCG reaches the same solution."""
+    ns, leaf = (31, 31, 31), 8
+    a = W.log_uniform_pixels(ns, 1e-3, 1e3, seed=33)
+    csr = gpu_lib.rhif_assemble_fd(ns, _dev(a), 1e-2)
+    f = _dev(W.normal_rhs(ns, 34))
+    kw = dict(precision="fp32", edge_skel_3d=True, big_front=1, big_frame=1)
+    on = gpu_lib.rhif_factor(csr, ns, leaf, 1e-3, tensor_cores=0, **kw)
+    off = gpu_lib.rhif_factor(csr, ns, leaf, 1e-3, tensor_cores=-1, **kw)
+    lv = on.stats()["levels"]
+    if [on.skeletons(l) for l in range(lv)] == [off.skeletons(l) for l in range(lv)]:
+        y1, y0 = on.apply(f), off.apply(f)
+        assert float(torch.linalg.norm(y1 - y0) / torch.linalg.norm(y0)) <= 1e-4
+    u1, _, r1 = on.pcg(f, rtol=1e-10)
+    u0, _, r0 = off.pcg(f, rtol=1e-10)
+    assert r1[0] <= 1.5e-10 and r0[0] <= 1.5e-10
+    assert float(torch.linalg.norm(u1 - u0) / torch.linalg.norm(u0)) <= 1e-8
+    on.free()
+    off.free()

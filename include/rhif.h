@@ -72,7 +72,7 @@ typedef struct {
    * big_frame: frame order (boundary DOFs of a cell) from which the block
    *   Jacobi scaling of Eq. (2.3) runs as row / column block solves over many
    *   CTAs; 0 = library default (when the frame no longer fits in shared
-   *   memory), < 0 = never. */
+   *   memory, and for the FP32 factor from 96), < 0 = never. */
   int big_front;
   int big_frame;
   /* skel_cluster: CTAs (a thread-block cluster, power of two <= 16) that share

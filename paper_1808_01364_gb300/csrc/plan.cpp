@@ -1,6 +1,7 @@
 // Host-side level planner; see plan.h for the grouping rule (Sec. 3.1, 3.2).
 // Work is proportional to the number of group codes and segments, plus one
-// pass over the active DOFs (closed form at level 0).
+// pass over the DOFs of the previous level's separator groups (closed form at
+// level 0).
 #include "plan.h"
 
 #include <algorithm>
@@ -92,6 +93,63 @@ inline int64_t pad4(int64_t n) { return (n + 3) & ~int64_t(3); }
 
 }  // namespace
 
+void LevelPlan::clear() {
+  level = width = code_base = 0;
+  bucket.clear();
+  cell_code.clear();
+  cell_start.clear();
+  nI.clear();
+  nB.clear();
+  gid_off.clear();
+  b_off.clear();
+  front_off.clear();
+  front_total = 0;
+  frame_off.clear();
+  frame_ld.clear();
+  frame_total = 0;
+  band_w.clear();
+  band_off.clear();
+  band_total = 0;
+  z_off.clear();
+  z_total = 0;
+  max_nI = max_nB = max_n = max_w = 0;
+  seg_off.clear();
+  seg_group.clear();
+  seg_pos.clear();
+  group_code.clear();
+  group_t.clear();
+  group_start.clear();
+  group_size.clear();
+  group_cell_off.clear();
+  group_cell.clear();
+  group_pos.clear();
+  max_group = 0;
+  ea_off.clear();
+  ea_child.clear();
+  ea_map_off.clear();
+  ea_map.clear();
+  phases.clear();
+}
+
+namespace {
+// per-thread storage reused across calls: recycled plans (one per level) and
+// the planner's temporaries
+struct PlanScratch {
+  std::vector<LevelPlan> pool;
+  std::vector<int64_t> cstart, cnt, gcode, key;
+  std::vector<int> gpos_off, newpos, src, cell_of_code, group_of_code, prev_cell_of_code;
+  std::vector<uint8_t> mark;
+};
+thread_local PlanScratch t_scratch;
+}  // namespace
+
+void recycle_plan(LevelPlan&& P) {
+  auto& pool = t_scratch.pool;
+  if (P.level < 0 || P.level >= 64) return;
+  if ((int)pool.size() <= P.level) pool.resize(P.level + 1);
+  pool[P.level] = std::move(P);
+}
+
 int unit_row_count(const LevelPlan& P, int g) {
   int seen[kMaxRowGroups];
   int nseen = 0, rows = 0;
@@ -110,18 +168,29 @@ int unit_row_count(const LevelPlan& P, int g) {
   return rows;
 }
 
-LevelPlan build_level(const Geometry& G, int level, const std::vector<int32_t>& active,
-                      const std::vector<uint8_t>& alive, const LevelPlan* prev,
+LevelPlan build_level(const Geometry& G, int level, const std::vector<uint8_t>& keep, const LevelPlan* prev,
                       bool precondition, bool edge_skel) {
+  PlanScratch& X = t_scratch;
   LevelPlan P;
+  if (level < (int)X.pool.size()) {
+    P = std::move(X.pool[level]);
+    X.pool[level] = LevelPlan();
+    P.clear();
+  }
   P.level = level;
   const Coder C(G, level);
   P.width = C.width;
   P.code_base = C.base;
   const int d = G.d, w = C.width;
 
-  // 1. active DOFs sorted by (code, index)
-  std::vector<int64_t> cstart(C.ncode + 1, 0);
+  // 1. active DOFs sorted by (code, index); for level >= 1 also, per
+  // separator group of level - 1, its code here (gcode) and, per DOF of those
+  // groups (numbered group by group, gpos_off), its bucket position or -1
+  std::vector<int64_t>& cstart = X.cstart;
+  cstart.assign(C.ncode + 1, 0);
+  std::vector<int64_t>& gcode = X.gcode;
+  std::vector<int>& gpos_off = X.gpos_off;
+  std::vector<int>& newpos = X.newpos;
   if (level == 0) {
     P.bucket.resize(G.N);
     int64_t pos = 0;
@@ -147,39 +216,69 @@ LevelPlan build_level(const Geometry& G, int level, const std::vector<int32_t>& 
     }
     cstart[C.ncode] = pos;
   } else {
-    std::vector<int64_t> code(active.size());
-    std::vector<int64_t> cnt(C.ncode + 1, 0);
-    std::vector<int> tab[3];
-    for (int a = 0; a < d; ++a) tab[a] = C.axis_table(G, a);
-    const int64_t n0 = G.ns[0], n01 = (int64_t)G.ns[0] * G.ns[1];
-    for (size_t i = 0; i < active.size(); ++i) {
-      const int64_t g = active[i];
-      int64_t c;
-      if (d == 2) {
-        const int64_t y = g / n0;
-        c = tab[0][g - y * n0] + C.base * tab[1][y];
-      } else {
-        const int64_t z = g / n01, r = g - z * n01, y = r / n0;
-        c = tab[0][r - y * n0] + C.base * (tab[1][y] + (int64_t)C.base * tab[2][z]);
-      }
-      code[i] = c;
-      ++cnt[c + 1];
+    // Every DOF of a separator group of level - 1 lands in the same code at
+    // this level (an open interval of width w/2 lies inside one interval of
+    // width w, and a plane x = q w/2 is either a plane or an interior line),
+    // so codes, counts and the scatter go group by group.
+    const Coder Cp(G, level - 1);
+    const int pg = prev->ngroup();
+    gcode.resize(pg);
+    gpos_off.resize(pg + 1);
+    gpos_off[0] = 0;
+    std::vector<int64_t>& cnt = X.cnt;
+    cnt.assign(C.ncode + 1, 0);
+    for (int g = 0; g < pg; ++g) {
+      int v[3];
+      Cp.split(prev->group_code[g], v);
+      for (int a = 0; a < d; ++a) v[a] = (v[a] % 2 == 0) ? v[a] / 2 : 2 * (((v[a] - 1) / 2) / 2) + 1;
+      gcode[g] = C.join(v);
+      const uint8_t* kp = keep.data() + prev->group_start[g];
+      int na = 0;
+      for (int o = 0; o < prev->group_size[g]; ++o) na += kp[o] != 0;
+      cnt[gcode[g] + 1] += na;
+      gpos_off[g + 1] = gpos_off[g] + prev->group_size[g];
     }
     for (int64_t c = 0; c < C.ncode; ++c) cnt[c + 1] += cnt[c];
     cstart = cnt;
-    P.bucket.resize(active.size());
-    for (size_t i = 0; i < active.size(); ++i) P.bucket[cnt[code[i]]++] = active[i];
-    // ascending DOF index within every code
-    for (int64_t c = 0; c < C.ncode; ++c)
-      if (cstart[c + 1] - cstart[c] > 1)
-        std::sort(P.bucket.begin() + cstart[c], P.bucket.begin() + cstart[c + 1]);
+    P.bucket.resize(cnt[C.ncode]);
+    newpos.assign(gpos_off[pg], -1);
+    std::vector<int>& src = X.src;
+    src.resize(P.bucket.size());
+    for (int g = 0; g < pg; ++g) {
+      const int32_t* gb = prev->bucket.data() + prev->group_start[g];
+      const uint8_t* kp = keep.data() + prev->group_start[g];
+      int64_t& cur = cnt[gcode[g]];
+      for (int o = 0; o < prev->group_size[g]; ++o)
+        if (kp[o]) {
+          P.bucket[cur] = gb[o];
+          src[cur] = gpos_off[g] + o;
+          ++cur;
+        }
+    }
+    // ascending DOF index within every code; newpos follows the moves
+    std::vector<int64_t>& key = X.key;
+    for (int64_t c = 0; c < C.ncode; ++c) {
+      const int64_t a = cstart[c], b = cstart[c + 1];
+      if (b - a > 1 && !std::is_sorted(P.bucket.begin() + a, P.bucket.begin() + b)) {
+        key.resize(b - a);
+        for (int64_t i = a; i < b; ++i) key[i - a] = ((int64_t)P.bucket[i] << 32) | (uint32_t)src[i];
+        std::sort(key.begin(), key.end());
+        for (int64_t i = a; i < b; ++i) {
+          P.bucket[i] = (int32_t)(key[i - a] >> 32);
+          src[i] = (int)(key[i - a] & 0xffffffff);
+        }
+      }
+      for (int64_t i = a; i < b; ++i) newpos[src[i]] = (int)i;
+    }
   }
   auto csize = [&](int64_t c) { return (int)(cstart[c + 1] - cstart[c]); };
 
   // 2. cells: every cell whose closure holds an active DOF
-  std::vector<int> cell_of_code(C.ncode, -1);
+  std::vector<int>& cell_of_code = X.cell_of_code;
+  cell_of_code.assign(C.ncode, -1);
   {
-    std::vector<uint8_t> mark(C.ncode, 0);
+    std::vector<uint8_t>& mark = X.mark;
+    mark.assign(C.ncode, 0);
     for (int64_t c = 0; c < C.ncode; ++c) {
       if (!csize(c)) continue;
       int v[3];
@@ -206,7 +305,8 @@ LevelPlan build_level(const Geometry& G, int level, const std::vector<int32_t>& 
   const int ncell = (int)P.cell_code.size();
 
   // 3. groups (t >= 1) in code order
-  std::vector<int> group_of_code(C.ncode, -1);
+  std::vector<int>& group_of_code = X.group_of_code;
+  group_of_code.assign(C.ncode, -1);
   for (int64_t c = 0; c < C.ncode; ++c) {
     if (!csize(c)) continue;
     int v[3];
@@ -301,55 +401,60 @@ LevelPlan build_level(const Geometry& G, int level, const std::vector<int32_t>& 
       }
   }
 
-  // 5. extend-add maps from the previous level's frames
+  // 5. extend-add maps from the previous level's frames.  A child segment's
+  // DOFs all sit in one code here: the parent's interior or one of its
+  // segments, found once per child segment.
   if (prev) {
     const Coder Cp(G, level - 1);
-    std::vector<int> prev_cell_of_code(Cp.ncode, -1);
+    std::vector<int>& prev_cell_of_code = X.prev_cell_of_code;
+    prev_cell_of_code.assign(Cp.ncode, -1);
     for (int i = 0; i < prev->ncell(); ++i) prev_cell_of_code[prev->cell_code[i]] = i;
-    // DOF -> front position, all -1 between cells (thread-local, reused by later calls)
-    static thread_local std::vector<int> pos_scratch;
-    if ((int64_t)pos_scratch.size() < G.N) pos_scratch.assign(G.N, -1);
-    std::vector<int>& pos_of_gid = pos_scratch;
-    P.ea_off.push_back(0);
+    // children of every cell, then one allocation of the whole map
+    P.ea_off.assign(1, 0);
+    int64_t map_total = 0;
     for (int ci = 0; ci < ncell; ++ci) {
-      const int nI = P.nI[ci];
-      for (int i = 0; i < nI; ++i) pos_of_gid[P.bucket[P.cell_start[ci] + i]] = i;
-      for (int s = P.seg_off[ci]; s < P.seg_off[ci + 1]; ++s) {
-        const int g = P.seg_group[s];
-        for (int o = 0; o < P.group_size[g]; ++o)
-          pos_of_gid[P.bucket[P.group_start[g] + o]] = nI + P.seg_pos[s] + o;
-      }
       int v[3];
       C.split(P.cell_code[ci], v);
-      int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
-      for (int a = 0; a < d; ++a) {
-        lo[a] = v[a] - 1;          // child cell indices 2p and 2p+1 of parent p = (v-1)/2
-        hi[a] = v[a];
-      }
-      for (int z = lo[2]; z <= hi[2]; ++z)
-        for (int y = lo[1]; y <= hi[1]; ++y)
-          for (int x = lo[0]; x <= hi[0]; ++x) {
+      for (int z = d == 3 ? v[2] - 1 : 0; z <= (d == 3 ? v[2] : 0); ++z)
+        for (int y = v[1] - 1; y <= v[1]; ++y)
+          for (int x = v[0] - 1; x <= v[0]; ++x) {
             int u[3] = {2 * x + 1, 2 * y + 1, 2 * z + 1};
             const int pc = prev_cell_of_code[Cp.join(u)];
             if (pc < 0) continue;
             P.ea_child.push_back(pc);
-            P.ea_map_off.push_back((int64_t)P.ea_map.size());
-            const size_t base = P.ea_map.size();
-            P.ea_map.resize(base + prev->nB[pc], -1);
-            for (int s = prev->seg_off[pc]; s < prev->seg_off[pc + 1]; ++s) {
-              const int g = prev->seg_group[s];
-              const int pos = prev->seg_pos[s];
-              for (int o = 0; o < prev->group_size[g]; ++o) {
-                const int32_t gid = prev->bucket[prev->group_start[g] + o];
-                P.ea_map[base + pos + o] = alive[gid] ? pos_of_gid[gid] : -1;
-              }
-            }
+            P.ea_map_off.push_back(map_total);
+            map_total += prev->nB[pc];
           }
       P.ea_off.push_back((int)P.ea_child.size());
-      for (int i = 0; i < nI; ++i) pos_of_gid[P.bucket[P.cell_start[ci] + i]] = -1;
-      for (int s = P.seg_off[ci]; s < P.seg_off[ci + 1]; ++s) {
-        const int g = P.seg_group[s];
-        for (int o = 0; o < P.group_size[g]; ++o) pos_of_gid[P.bucket[P.group_start[g] + o]] = -1;
+    }
+    P.ea_map.assign(map_total, -1);
+    for (int ci = 0; ci < ncell; ++ci) {
+      const int nI = P.nI[ci];
+      for (int k = P.ea_off[ci]; k < P.ea_off[ci + 1]; ++k) {
+        const int pc = P.ea_child[k];
+        const int64_t base = P.ea_map_off[k];
+            for (int s = prev->seg_off[pc]; s < prev->seg_off[pc + 1]; ++s) {
+              const int g = prev->seg_group[s];
+              const int64_t gc = gcode[g];
+              int64_t shift = 0;   // parent position = bucket position + shift
+              bool found = false;
+              if (gc == P.cell_code[ci]) {
+                shift = -(int64_t)P.cell_start[ci];
+                found = true;
+              } else {
+                const int pg = group_of_code[gc];
+                for (int t = P.seg_off[ci]; t < P.seg_off[ci + 1] && !found; ++t)
+                  if (P.seg_group[t] == pg) {
+                    shift = nI + P.seg_pos[t] - (int64_t)P.group_start[pg];
+                    found = true;
+                  }
+              }
+              if (!found) continue;   // no DOF of the segment reaches this front (stays -1)
+              const int* np = newpos.data() + gpos_off[g];
+              int* out = P.ea_map.data() + base + prev->seg_pos[s];
+              for (int o = 0; o < prev->group_size[g]; ++o)
+                out[o] = np[o] >= 0 ? (int)(np[o] + shift) : -1;
+            }
       }
     }
   }

@@ -104,15 +104,23 @@ struct LevelPlan {
 
   int ncell() const { return (int)nI.size(); }
   int ngroup() const { return (int)group_t.size(); }
+  // Empties every table but keeps the storage (every field is listed here).
+  void clear();
 };
 
-// Build the plan of level `level`.  `active` lists the active DOFs in any
-// order (ignored at level 0, where every DOF is active); `alive` flags the
-// surviving DOFs of the previous level's separator groups by DOF index;
-// `prev` is the plan of level-1.  For level == G.L only the root front is
-// built (no phases).
-LevelPlan build_level(const Geometry& G, int level, const std::vector<int32_t>& active,
-                      const std::vector<uint8_t>& alive, const LevelPlan* prev,
+// Hands a plan that is no longer needed back to the calling thread's pool: the
+// next build_level of the same level on that thread reuses its storage, so a
+// refactorization of the same geometry touches no fresh pages.  The pool
+// holds at most one plan per level.
+void recycle_plan(LevelPlan&& P);
+
+// Build the plan of level `level`.  At level 0 every DOF is active; above it
+// the active DOFs are those of the previous level's separator groups whose
+// flag in `keep` is set (indexed by position in prev->bucket; only the group
+// ranges are read).  `prev` is the plan of level-1.  For level == G.L only the
+// root front is built (no phases).
+LevelPlan build_level(const Geometry& G, int level, const std::vector<uint8_t>& keep,
+                      const LevelPlan* prev,
                       bool precondition, bool edge_skel);
 
 // Row layout of A_{R,I} for a unit: the distinct separator groups other than

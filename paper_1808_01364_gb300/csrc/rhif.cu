@@ -75,16 +75,63 @@ struct DevMem {
 };
 
 // Packs host vectors into one staging buffer and uploads it in one copy.
+// Host tables bound for one device buffer: `add` records a vector and returns
+// its 16-byte-aligned offset; `upload` packs them into pinned staging memory
+// and queues one host-to-device copy.  The staging buffer belongs to the
+// calling thread and is reused by later uploads once the copy that last read
+// it has completed (an event recorded behind it), so repeated
+// factorizations neither allocate pinned memory nor copy from pageable memory.
 struct Packer {
-  std::vector<char> host;
+  std::vector<std::pair<const void*, size_t>> part;
+  std::vector<size_t> off;
+  size_t total = 0;
   template <typename V>
   size_t add(const std::vector<V>& v) {
-    size_t off = (host.size() + 15) & ~size_t(15);
-    host.resize(off + v.size() * sizeof(V));
-    if (!v.empty()) std::memcpy(host.data() + off, v.data(), v.size() * sizeof(V));
-    return off;
+    const size_t o = (total + 15) & ~size_t(15);
+    part.emplace_back(v.data(), v.size() * sizeof(V));
+    off.push_back(o);
+    total = o + v.size() * sizeof(V);
+    return o;
   }
+  int upload(void* dst, cudaStream_t s) const;
 };
+
+struct Staging {
+  char* p = nullptr;
+  size_t cap = 0;
+  cudaEvent_t done = nullptr;
+  int device = -1;
+};
+static thread_local Staging t_stage;
+
+int Packer::upload(void* dst, cudaStream_t s) const {
+  if (!total) return 0;
+  Staging& st = t_stage;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (st.done) CK(cudaEventSynchronize(st.done));   // the previous copy out of the buffer
+  if (st.done && st.device != dev) {
+    CK(cudaEventDestroy(st.done));
+    st.done = nullptr;
+  }
+  if (!st.done) {
+    CK(cudaEventCreateWithFlags(&st.done, cudaEventDisableTiming));
+    st.device = dev;
+  }
+  if (st.cap < total) {
+    if (st.p) CK(cudaFreeHost(st.p));
+    st.p = nullptr;
+    st.cap = 0;
+    const size_t cap = std::max(total + total / 2, size_t(1) << 20);
+    CK(cudaHostAlloc((void**)&st.p, cap, cudaHostAllocPortable));
+    st.cap = cap;
+  }
+  for (size_t i = 0; i < part.size(); ++i)
+    if (part[i].second) std::memcpy(st.p + off[i], part[i].first, part[i].second);
+  CK(cudaMemcpyAsync(dst, st.p, total, cudaMemcpyHostToDevice, s));
+  CK(cudaEventRecord(st.done, s));
+  return 0;
+}
 
 
 // ---------------------------------------------------------------------------
@@ -274,10 +321,10 @@ static int upload_level(rhif_handle* H, LevelStore& S, size_t elem) {
              pk.add(ph.group_unit)};
   }
   void* d = nullptr;
-  int rc = H->mem.get(&d, pk.host.size());
+  int rc = H->mem.get(&d, pk.total);
   if (rc) return rc;
   S.tables = d;
-  CK(cudaMemcpyAsync(d, pk.host.data(), pk.host.size(), cudaMemcpyHostToDevice, H->mem.s));
+  if ((rc = pk.upload(d, H->mem.s))) return rc;
   char* b = (char*)d;
   LevelDev& L = S.dev;
   L.level = P.level;
@@ -468,8 +515,10 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
   if ((rc = check_status(H, "CSR pattern check"))) return rc;
   H->mem.release(offb);
 
-  std::vector<uint8_t> alive(G.N, 1);
-  std::vector<int32_t> active;
+  // per position of the current level's bucket: the DOF survives into the
+  // next level (only separator-group positions are read by the planner)
+  static thread_local std::vector<uint8_t> keep;   // storage reused by later factorizations
+  keep.clear();
   H->levels.resize(G.L + 1);
   const bool trace = std::getenv("RHIF_TRACE") != nullptr;
   using clk = std::chrono::steady_clock;
@@ -480,7 +529,8 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
     LevelStore& S = H->levels[lvl];
     const LevelPlan* prev = lvl ? &H->levels[lvl - 1].plan : nullptr;
     auto t0 = clk::now();
-    S.plan = build_level(G, lvl, active, alive, prev, H->precondition, H->edge_skel);
+    S.plan = build_level(G, lvl, keep, prev, H->precondition, H->edge_skel);
+    keep.assign(S.plan.bucket.size(), 1);
     const double t_plan = ms_since(t0);
     auto t1 = clk::now();
     if ((rc = upload_level(H, S, elem))) return rc;
@@ -591,11 +641,14 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
           const double g = P.group_size[gi];
           sflops += 2.0 * g * g * P.nB[c];
         }
-      Packer scale_tab;   // host copy must outlive the upload (synchronized below)
+      Packer scale_tab;
       void* scale_dev = nullptr;
       if (!ph.pre_group.empty()) {
         const bool fits = (size_t)P.max_nB * P.max_nB * elem <= 200 * 1024;
-        const bool big = H->big_frame > 0 ? P.max_nB >= H->big_frame : !fits;
+        // default: many CTAs once the frame leaves shared memory, and for the
+        // FP32 factor from 96 boundary DOFs (few, large cells per level)
+        const bool big = H->big_frame > 0 ? P.max_nB >= H->big_frame
+                                          : (!fits || (elem == 4 && P.max_nB >= 96));
         int64_t blocks = 0;
         if (big) {   // large frames: tile products with explicit inverses over many CTAs
           std::vector<int> task;
@@ -609,9 +662,8 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
                 blocks += (P.nB[c] + 63) / 64;
               }
           const size_t o_task = scale_tab.add(task), o_off = scale_tab.add(off);
-          if ((rc = H->mem.get(&scale_dev, scale_tab.host.size()))) return rc;
-          CK(cudaMemcpyAsync(scale_dev, scale_tab.host.data(), scale_tab.host.size(),
-                             cudaMemcpyHostToDevice, s));
+          if ((rc = H->mem.get(&scale_dev, scale_tab.total))) return rc;
+          if ((rc = scale_tab.upload(scale_dev, s))) return rc;
           D.scale_task = (const int*)((char*)scale_dev + o_task);
           D.scale_off = (const int64_t*)((char*)scale_dev + o_off);
           D.nscale_task = (int)off.size();
@@ -663,7 +715,7 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
         const int n = P.group_size[gi];
         const int k = PS.h_rank[u], r = n - k;
         const int* pm = PS.h_perm.data() + ph.units.perm_off[u];
-        for (int i = k; i < n; ++i) alive[P.bucket[P.group_start[gi] + pm[i]]] = 0;
+        for (int i = k; i < n; ++i) keep[P.group_start[gi] + pm[i]] = 0;
         const double m = ph.units.nrow[u];
         const double uf = 4.0 * m * n * k - 2.0 * k * k * (m + n) + 4.0 * k * k * k / 3.0 +
                           double(k) * k * r + cell_flops(r, k);
@@ -682,15 +734,6 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
       H->mem.release(S.dev.zbuf);
       S.dev.zbuf = nullptr;
     }
-    // DOFs still active at the next level: the separator DOFs that survived
-    // (interior DOFs never appear in a separator group again, so their host
-    // flags are not needed; the planner orders each new cell / group itself)
-    active.clear();
-    for (int gi = 0; gi < P.ngroup(); ++gi)
-      for (int o = 0; o < P.group_size[gi]; ++o) {
-        const int32_t g = P.bucket[P.group_start[gi] + o];
-        if (alive[g]) active.push_back(g);
-      }
     for (int c = 0; c < P.ncell(); ++c) {
       const double nI = P.nI[c], nB = P.nB[c];
       if (lvl == 0) {
@@ -1236,6 +1279,7 @@ void rhif_free(rhif_handle* F) {
   if (!F) return;
   F->mem.release_all();
   cudaStreamSynchronize(F->mem.s);
+  for (auto& S : F->levels) recycle_plan(std::move(S.plan));
   delete F;
 }
 

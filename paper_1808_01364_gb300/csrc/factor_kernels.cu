@@ -505,6 +505,223 @@ k_leaf_stream(GeoDev G, LevelDev Lv, const double* diag, const double* off, int*
   if (tid == 0 && bad) report(status, RHIF_ERR_NOT_SPD, 0, kKindCell, c);
 }
 
+// One warp per 2D leaf (interior box at most 15 wide, at most NBT <= 64
+// boundary DOFs): the same column-by-column pass as k_leaf_stream, the same
+// operations on the same entries in the same order, with no CTA barriers.
+// The live parts of the band (columns k..k+15) and of Z = L^{-1} A_IB (rows
+// k..k+15) sit in circular windows in shared memory; lane l owns Z columns l
+// and l + 32 and keeps the matching columns of S = Z^T Z as register
+// accumulators.  Columns of L leave the window as soon as they are final
+// (reciprocal diagonal, as the application reads it).
+constexpr int kLeafWarpW = 15;   // largest band half-width
+constexpr int kLeafWarpCta = 4;  // warps (leaves) per CTA
+
+template <typename T>
+__host__ __device__ inline size_t leaf_warp_bytes(int max_nI, int leaf, int nbt) {
+  const size_t tab = (size_t)(leaf + 1) * (leaf + 1) * sizeof(int);
+  const size_t cols = (size_t)3 * max_nI * sizeof(T);
+  const size_t win = 16 * 16 * sizeof(T) + (size_t)16 * nbt * sizeof(T);
+  return ((tab + 15) & ~size_t(15)) + ((cols + 15) & ~size_t(15)) + ((win + 15) & ~size_t(15));
+}
+
+template <typename T, int NBT>
+__global__ void __launch_bounds__(32 * kLeafWarpCta)
+k_leaf_warp(GeoDev G, LevelDev Lv, const double* diag, const double* off, int* status) {
+  constexpr int CPL = NBT / 32;   // boundary columns per lane
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c = blockIdx.x * kLeafWarpCta + warp;
+  if (c >= Lv.ncell) return;
+  const int nI = Lv.nI[c], nB = Lv.nB[c], n = nI + nB, w = Lv.band_w[c];
+  const int m = G.leaf, m1 = m + 1;
+  unsigned char* base = smraw + (size_t)warp * leaf_warp_bytes<T>(Lv.max_nI, m, NBT);
+  int* postab = (int*)base;
+  base += ((size_t)m1 * m1 * sizeof(int) + 15) & ~size_t(15);
+  T* dg = (T*)base;                 // A_II: diagonal, x-neighbour (d = 1), y-neighbour (d = w)
+  T* ax = dg + Lv.max_nI;
+  T* ay = ax + Lv.max_nI;
+  base += ((size_t)3 * Lv.max_nI * sizeof(T) + 15) & ~size_t(15);
+  T* bw = (T*)base;                 // band window: column k in slot k & 15, entry d = L[k+d, k]
+  T* zw = bw + 256;                 // Z window: row k in slot k & 15 (NBT entries)
+  const int32_t* gid = Lv.gids + Lv.gid_off[c];
+  int ld;
+  T* Fr = frame_of<T>(Lv, c, &ld);
+  int* ci = Lv.cpl_i + Lv.b_off[c];
+  T* ca = (T*)Lv.cpl_a + Lv.b_off[c];
+  int origin[2] = {0, 0};
+  {
+    int64_t code = Lv.cell_code[c];
+    for (int a = 0; a < 2; ++a) {
+      const int v = (int)(code % Lv.code_base);
+      code /= Lv.code_base;
+      origin[a] = ((v - 1) / 2) * m;
+    }
+  }
+  // 1. stencil entries: interior columns, couplings, this cell's share of A_BB
+  for (int i = lane; i < m1 * m1; i += 32) postab[i] = -1;
+  for (int j = 0; j < nB; ++j)
+    for (int i = lane; i < nB; i += 32) Fr[i + (int64_t)j * ld] = T(0);
+  __syncwarp();
+  for (int q = lane; q < n; q += 32) {
+    int x[3];
+    coords1(G, gid[q], x);
+    postab[(x[0] - origin[0]) + (x[1] - origin[1]) * m1] = q;
+  }
+  __syncwarp();
+  for (int q = lane; q < n; q += 32) {
+    const int64_t g = gid[q];
+    int x[3];
+    coords1(G, g, x);
+    const int lin = (x[0] - origin[0]) + (x[1] - origin[1]) * m1;
+    const int onplane = (x[0] % m == 0) + (x[1] % m == 0);
+    const int b = q - nI;
+    if (q < nI) {
+      dg[q] = T(diag[g]);
+      ax[q] = T(0);
+      ay[q] = T(0);
+    } else {
+      Fr[b + (int64_t)b * ld] = T(diag[g] / double(1 << onplane));
+      ci[b] = -1;
+      ca[b] = T(0);
+    }
+    for (int a = 0; a < 2; ++a) {
+      const double share = double(1 << (onplane - (x[a] % m == 0)));
+      const int lx = x[a] - origin[a];
+      const int lstride = a == 0 ? 1 : m1;
+      for (int dir = -1; dir <= 1; dir += 2) {
+        if (dir > 0 && !(x[a] + 1 <= G.ns[a] && lx + 1 <= m)) continue;
+        if (dir < 0 && !(x[a] - 1 >= 1 && lx - 1 >= 0)) continue;
+        const int r = postab[lin + dir * lstride];
+        if (r < 0) continue;
+        const double v = dir > 0 ? off[a * G.N + g] : off[a * G.N + g - G.stride[a]];
+        if (q < nI) {
+          if (r < nI && r > q) (a == 0 ? ax : ay)[q] = T(v);
+        } else if (r < nI) {
+          ci[b] = r;
+          ca[b] = T(v);
+        } else {
+          Fr[b + (int64_t)(r - nI) * ld] = T(v / share);
+        }
+      }
+    }
+  }
+  __syncwarp();
+  // 2. initial windows: band columns 0..15, Z rows 0..15 (A_IB has one entry per column)
+  for (int i = lane; i < 256; i += 32) {
+    const int col = i >> 4, d = i & 15;
+    T v = T(0);
+    if (col < nI) {
+      if (d == 0) v = dg[col];
+      if (d == 1) v += ax[col];
+      if (d == w) v += ay[col];
+    }
+    bw[i] = v;
+  }
+  int my_ci[CPL];
+  T my_ca[CPL];
+#pragma unroll
+  for (int h = 0; h < CPL; ++h) {
+    const int b = lane + 32 * h;
+    my_ci[h] = b < nB ? ci[b] : -1;
+    my_ca[h] = b < nB ? ca[b] : T(0);
+  }
+  for (int r = 0; r < 16; ++r)
+#pragma unroll
+    for (int h = 0; h < CPL; ++h) zw[r * NBT + lane + 32 * h] = my_ci[h] == r ? my_ca[h] : T(0);
+  // trailing-update pairs (d1, d2), 1 <= d2 <= d1 <= w, four per lane
+  int pd1[4], pd2[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int q = lane + 32 * u;
+    int d1 = 1, rem = q;
+    while (rem >= d1) {
+      rem -= d1;
+      ++d1;
+    }
+    pd1[u] = d1 <= w ? d1 : 0;
+    pd2[u] = rem + 1;
+  }
+  T acc[CPL][NBT];
+#pragma unroll
+  for (int h = 0; h < CPL; ++h)
+#pragma unroll
+    for (int i = 0; i < NBT; ++i) acc[h][i] = T(0);
+  int bad = 0;
+  T* band = (T*)Lv.band + Lv.band_off[c];
+  const int w1 = w + 1;
+  __syncwarp();
+  // 3. column k of the band Cholesky, row k of Z, S += z_k z_k^T
+#pragma unroll 1
+  for (int k = 0; k < nI; ++k) {
+    const int wk = min(w, nI - 1 - k);
+    T* colk = bw + (k & 15) * 16;
+    T* zk_row = zw + (k & 15) * NBT;
+    T dkk = colk[0];
+    if (!(dkk > T(0))) {
+      bad = 1;
+      dkk = T(1);
+    }
+    const T sp = my_sqrt(dkk);
+    const T rp = T(1) / sp;
+    __syncwarp();
+    if (lane == 0) colk[0] = sp;
+    else if (lane <= wk) colk[lane] *= rp;
+    T zk[CPL];
+#pragma unroll
+    for (int h = 0; h < CPL; ++h) {
+      zk[h] = zk_row[lane + 32 * h] * rp;
+      zk_row[lane + 32 * h] = zk[h];
+    }
+    __syncwarp();
+    if (lane <= w) band[(int64_t)k * w1 + lane] = lane == 0 ? T(1) / sp : (lane <= wk ? colk[lane] : T(0));
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int d1 = pd1[u], d2 = pd2[u];
+      if (d1 && d1 <= wk) bw[((k + d2) & 15) * 16 + (d1 - d2)] -= colk[d1] * colk[d2];
+    }
+    for (int d = 1; d <= wk; ++d) {
+      const T l = colk[d];
+      T* zr = zw + ((k + d) & 15) * NBT + lane;
+#pragma unroll
+      for (int h = 0; h < CPL; ++h) zr[32 * h] -= l * zk[h];
+    }
+#pragma unroll
+    for (int i4 = 0; i4 < NBT; i4 += 4) {
+      T zi[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) zi[e] = zk_row[i4 + e];
+#pragma unroll
+      for (int h = 0; h < CPL; ++h)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc[h][i4 + e] += zi[e] * zk[h];
+    }
+    __syncwarp();
+    // slot k becomes column / row k + 16
+    const int nc = k + 16;
+    if (lane < 16) {
+      T v = T(0);
+      if (nc < nI) {
+        if (lane == 0) v = dg[nc];
+        if (lane == 1) v += ax[nc];
+        if (lane == w) v += ay[nc];
+      }
+      colk[lane] = v;
+    }
+#pragma unroll
+    for (int h = 0; h < CPL; ++h) zk_row[lane + 32 * h] = my_ci[h] == nc ? my_ca[h] : T(0);
+    __syncwarp();
+  }
+  // 4. frame = A_BB share - S, lower triangle written as rows j >= i of column i
+#pragma unroll
+  for (int h = 0; h < CPL; ++h) {
+    const int j = lane + 32 * h;
+#pragma unroll
+    for (int i = 0; i < NBT; ++i)
+      if (i <= j && j < nB) Fr[j + (int64_t)i * ld] -= acc[h][i];
+  }
+  if (__any_sync(0xffffffffu, bad) && lane == 0) report(status, RHIF_ERR_NOT_SPD, 0, kKindCell, c);
+}
+
 // ---------------------------------------------------------------------------
 // level >= 1 fronts: extend-add of the children's frames, children in a fixed order
 // ---------------------------------------------------------------------------
@@ -1686,6 +1903,21 @@ template <typename T>
 void launch_leaf_elim(const GeoDev& G, const LevelDev& Lv, const double* diag, const double* off,
                       int* status, cudaStream_t s) {
   if (!Lv.ncell) return;
+  const bool warp_ok = G.d == 2 && Lv.max_w <= kLeafWarpW;
+  if (warp_ok && Lv.max_nB <= 32 && kLeafWarpCta * leaf_warp_bytes<T>(Lv.max_nI, G.leaf, 32) <= 48 * 1024) {
+    const size_t sm = kLeafWarpCta * leaf_warp_bytes<T>(Lv.max_nI, G.leaf, 32);
+    k_leaf_warp<T, 32><<<(Lv.ncell + kLeafWarpCta - 1) / kLeafWarpCta, 32 * kLeafWarpCta, sm, s>>>(
+        G, Lv, diag, off, status);
+    return;
+  }
+  if constexpr (sizeof(T) == 4) {   // 64 accumulator columns per lane pair fit registers in FP32 only
+    if (warp_ok && Lv.max_nB <= 64 && kLeafWarpCta * leaf_warp_bytes<T>(Lv.max_nI, G.leaf, 64) <= 48 * 1024) {
+      const size_t sm = kLeafWarpCta * leaf_warp_bytes<T>(Lv.max_nI, G.leaf, 64);
+      k_leaf_warp<T, 64><<<(Lv.ncell + kLeafWarpCta - 1) / kLeafWarpCta, 32 * kLeafWarpCta, sm, s>>>(
+          G, Lv, diag, off, status);
+      return;
+    }
+  }
   if (Lv.max_nB <= kStreamNB) {
     const size_t sm = leaf_stream_smem<T>(Lv.max_nI, Lv.max_w, G.leaf, G.d);
     k_leaf_stream<T><<<Lv.ncell, kThreads, sm, s>>>(G, Lv, diag, off, status);

@@ -265,10 +265,24 @@ def alu_peaks(torch):
     return out
 
 
-def source_hash() -> str:
+# device code of each kernel category: its .cu file plus the shared headers
+_APPLY_CATS = ("apply_cell_up", "apply_cell_down", "apply_group_up", "apply_group_down",
+               "apply_leaf_up", "apply_leaf_down", "spmv", "pcg_vector", "assemble_fd", "grad_logcoef")
+_SHARED_SRC = ("common.cuh", "tables.h")
+
+
+def source_files(kernel: str):
+    main = "apply_kernels.cu" if kernel in _APPLY_CATS else "factor_kernels.cu"
+    return (main,) + _SHARED_SRC
+
+
+def source_hash(kernel: str) -> str:
+    """Hash of the sources that hold the device code of a kernel category, so
+    that a recorded DRAM traffic figure is used only while that code is
+    unchanged."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1808_01364_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
+    for fn in source_files(kernel):
         h.update(open(os.path.join(csrc, fn), "rb").read())
     return h.hexdigest()[:16]
 
@@ -279,7 +293,7 @@ def profile_traffic(kernel: str, precision: str, workload: str):
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
-    want = source_hash()
+    want = source_hash(kernel)
     for line in open(path):
         f = line.split()
         if line.startswith("#") or len(f) < 4 or f[0] != kernel or f[1] != precision:

@@ -664,35 +664,62 @@ __device__ inline void group_stage(const PhaseDev& Ph, int pi, int u, int n, uns
   }
 }
 
+// out = X in and out = X^T in for a lower-triangular n x n X (ld), in and
+// out in shared memory (distinct).  The factor stores the inverses of the
+// block-Jacobi factors L_g and of the units' L_rr, so every step of the group
+// application is a product.
+template <typename T>
+__device__ inline void cta_trmv_lower(const T* X, int64_t ld, int n, const T* in, T* out) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    T s = T(0);
+    for (int j = 0; j <= i; ++j) s += X[i + (int64_t)j * ld] * in[j];
+    out[i] = s;
+  }
+}
+
+template <typename T>
+__device__ inline void cta_trmv_lower_t(const T* X, int64_t ld, int n, const T* in, T* out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (int i = warp; i < n; i += nwarps) {
+    T s = T(0);
+    for (int j = i + lane; j < n; j += 32) s += X[j + (int64_t)i * ld] * in[j];
+    s = warp_sum(s);
+    if (lane == 0) out[i] = s;
+  }
+}
+
+// K_l^T of one unit on its group's values xg (Fu holds L_rr^{-1} and W):
+// x_rd -= T^T x_sk ; y = L_rr^{-1} x_rd ; x_sk -= W y ; x_rd = y
 template <typename T>
 __device__ void unit_up(const PhaseDev& Ph, int u, int n, T* xg, T* tmp, const T* Fu, const T* Tm) {
   const int k = Ph.rank[u], r = n - k;
   const int* perm = Ph.perm + Ph.u_perm_off[u];
-  // Z^T: x_rd -= T^T x_sk
   for (int a = threadIdx.x; a < r; a += blockDim.x) {
     T s = xg[perm[k + a]];
     for (int q = 0; q < k; ++q) s -= Tm[q + (int64_t)a * k] * xg[perm[q]];
     tmp[a] = s;
   }
   __syncthreads();
-  // E_rd^T: y = L^{-1} x_rd ; x_sk -= W y ; x_rd = y
-  cta_trsv_lower(Fu, n, r, tmp);
-  for (int q = threadIdx.x; q < k; q += blockDim.x) {
-    T s = xg[perm[q]];
-    for (int a = 0; a < r; ++a) s -= Fu[(r + q) + (int64_t)a * n] * tmp[a];
-    tmp[r + q] = s;
+  for (int a = threadIdx.x; a < r; a += blockDim.x) {   // y into the redundant slots
+    T s = T(0);
+    for (int c = 0; c <= a; ++c) s += Fu[a + (int64_t)c * n] * tmp[c];
+    xg[perm[k + a]] = s;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < n; i += blockDim.x) xg[perm[i < r ? k + i : i - r]] = tmp[i];
+  for (int q = threadIdx.x; q < k; q += blockDim.x) {
+    T s = xg[perm[q]];
+    for (int a = 0; a < r; ++a) s -= Fu[(r + q) + (int64_t)a * n] * xg[perm[k + a]];
+    xg[perm[q]] = s;
+  }
   __syncthreads();
 }
 
+// K_l of one unit: x_rd = L_rr^{-T} (x_rd - W^T x_sk) ; x_sk -= T x_rd
 template <typename T>
 __device__ void unit_down(const PhaseDev& Ph, int u, int n, T* xg, T* tmp, const T* Fu, const T* Tm) {
   const int k = Ph.rank[u], r = n - k;
   const int* perm = Ph.perm + Ph.u_perm_off[u];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  // E_rd: x_rd = L^{-T}(x_rd - W^T x_sk)
   for (int a = warp; a < r; a += nwarps) {
     T s = T(0);
     for (int q = lane; q < k; q += 32) s += Fu[(r + q) + (int64_t)a * n] * xg[perm[q]];
@@ -700,15 +727,18 @@ __device__ void unit_down(const PhaseDev& Ph, int u, int n, T* xg, T* tmp, const
     if (lane == 0) tmp[a] = xg[perm[k + a]] - s;
   }
   __syncthreads();
-  cta_trsv_lower_t(Fu, n, r, tmp);
-  // Z: x_sk -= T x_rd
-  for (int q = threadIdx.x; q < k; q += blockDim.x) {
-    T s = xg[perm[q]];
-    for (int a = 0; a < r; ++a) s -= Tm[q + (int64_t)a * k] * tmp[a];
-    tmp[r + q] = s;
+  for (int a = warp; a < r; a += nwarps) {   // y = L_rr^{-T} tmp into the redundant slots
+    T s = T(0);
+    for (int c = a + lane; c < r; c += 32) s += Fu[c + (int64_t)a * n] * tmp[c];
+    s = warp_sum(s);
+    if (lane == 0) xg[perm[k + a]] = s;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < n; i += blockDim.x) xg[perm[i < r ? k + i : i - r]] = tmp[i];
+  for (int q = threadIdx.x; q < k; q += blockDim.x) {
+    T s = xg[perm[q]];
+    for (int a = 0; a < r; ++a) s -= Tm[q + (int64_t)a * k] * xg[perm[k + a]];
+    xg[perm[q]] = s;
+  }
   __syncthreads();
 }
 
@@ -753,7 +783,12 @@ k_apply_group_up(LevelDev Lv, PhaseDev Ph, int gather, double* x, int64_t ldx, i
     }
     if (stage && r == 0 && !staged_ok(&bar, Lv.status, Lv.level, kKindGroup, g)) return;
     __syncthreads();
-    if (Lg) cta_trsv_lower(Lg, n, n, xg);
+    if (Lg) {   // C^T: x_g = L_g^{-1} x_g
+      cta_trmv_lower(Lg, n, n, xg, tmp);
+      __syncthreads();
+      for (int i = threadIdx.x; i < n; i += blockDim.x) xg[i] = tmp[i];
+      __syncthreads();
+    }
     if (Fu) unit_up(Ph, u, n, xg, tmp, Fu, Tm);
     for (int i = threadIdx.x; i < n; i += blockDim.x) xr[gid[i]] = double(xg[i]);
     __syncthreads();
@@ -785,7 +820,12 @@ k_apply_group_down(LevelDev Lv, PhaseDev Ph, double* x, int64_t ldx, int nrhs, i
     if (stage && r == 0 && !staged_ok(&bar, Lv.status, Lv.level, kKindGroup, g)) return;
     __syncthreads();
     if (Fu) unit_down(Ph, u, n, xg, tmp, Fu, Tm);
-    if (Lg) cta_trsv_lower_t(Lg, n, n, xg);
+    if (Lg) {   // C: x_g = L_g^{-T} x_g
+      cta_trmv_lower_t(Lg, n, n, xg, tmp);
+      __syncthreads();
+      for (int i = threadIdx.x; i < n; i += blockDim.x) xg[i] = tmp[i];
+      __syncthreads();
+    }
     for (int i = threadIdx.x; i < n; i += blockDim.x) xr[gid[i]] = double(xg[i]);
     __syncthreads();
   }
@@ -836,12 +876,13 @@ k_apply_group_up_warp(LevelDev Lv, PhaseDev Ph, int gather, double* x, int64_t l
       xv = T(v);
     }
     if (staged && rr == 0 && !staged_ok(bar, Lv.status, Lv.level, kKindGroup, g)) return;
-    if (Lg) {   // C^T: x_g = L_g^{-1} x_g
+    if (Lg) {   // C^T: x_g = L_g^{-1} x_g (the factor keeps L_g^{-1})
+      T y = T(0);
       for (int c = 0; c < n; ++c) {
-        const T yc = __shfl_sync(0xffffffffu, xv, c) / Lg[c + c * n];
-        if (lane == c) xv = yc;
-        else if (lane > c && lane < n) xv -= Lg[lane + c * n] * yc;
+        const T v = __shfl_sync(0xffffffffu, xv, c);
+        if (c <= lane && lane < n) y += Lg[lane + c * n] * v;
       }
+      xv = y;
     }
     if (u >= 0) {   // K^T: x_rd -= T^T x_sk ; y = L^{-1} x_rd ; x_sk -= W y ; x_rd = y
       T xs = __shfl_sync(0xffffffffu, xv, p_sk);
@@ -850,10 +891,13 @@ k_apply_group_up_warp(LevelDev Lv, PhaseDev Ph, int gather, double* x, int64_t l
         const T v = __shfl_sync(0xffffffffu, xs, q);
         if (lane < r) xd -= Tm[q + lane * k] * v;
       }
-      for (int c = 0; c < r; ++c) {
-        const T yc = __shfl_sync(0xffffffffu, xd, c) / Fu[c + c * n];
-        if (lane == c) xd = yc;
-        else if (lane > c && lane < r) xd -= Fu[lane + c * n] * yc;
+      {   // y = L_rr^{-1} x_rd
+        T y = T(0);
+        for (int c = 0; c < r; ++c) {
+          const T v = __shfl_sync(0xffffffffu, xd, c);
+          if (c <= lane && lane < r) y += Fu[lane + c * n] * v;
+        }
+        xd = y;
       }
       for (int a = 0; a < r; ++a) {
         const T v = __shfl_sync(0xffffffffu, xd, a);
@@ -903,10 +947,13 @@ k_apply_group_down_warp(LevelDev Lv, PhaseDev Ph, double* x, int64_t ldx, int nr
         const T v = __shfl_sync(0xffffffffu, xs, q);
         if (lane < r) xd -= Fu[(r + q) + lane * n] * v;
       }
-      for (int c = r - 1; c >= 0; --c) {
-        const T yc = __shfl_sync(0xffffffffu, xd, c) / Fu[c + c * n];
-        if (lane == c) xd = yc;
-        else if (lane < c) xd -= Fu[c + lane * n] * yc;
+      {   // x_rd = L_rr^{-T} x_rd
+        T y = T(0);
+        for (int c = 0; c < r; ++c) {
+          const T v = __shfl_sync(0xffffffffu, xd, c);
+          if (c >= lane && lane < r) y += Fu[c + lane * n] * v;
+        }
+        xd = y;
       }
       for (int a = 0; a < r; ++a) {
         const T v = __shfl_sync(0xffffffffu, xd, a);
@@ -917,11 +964,12 @@ k_apply_group_down_warp(LevelDev Lv, PhaseDev Ph, double* x, int64_t ldx, int nr
       xv = my_idx < k ? from_sk : from_rd;
     }
     if (Lg) {   // C: x_g = L_g^{-T} x_g
-      for (int c = n - 1; c >= 0; --c) {
-        const T yc = __shfl_sync(0xffffffffu, xv, c) / Lg[c + c * n];
-        if (lane == c) xv = yc;
-        else if (lane < c) xv -= Lg[c + lane * n] * yc;
+      T y = T(0);
+      for (int c = 0; c < n; ++c) {
+        const T v = __shfl_sync(0xffffffffu, xv, c);
+        if (c >= lane && lane < n) y += Lg[c + lane * n] * v;
       }
+      xv = y;
     }
     if (lane < n) xr[gid[lane]] = double(xv);
   }

@@ -930,6 +930,88 @@ __global__ void __launch_bounds__(kThreads) k_group_trinv(LevelDev Lv, PhaseDev 
   cta_trinv_block(Lg, sz, sz, X, sz, J0, (T*)smraw);
 }
 
+// L_rr^{-1} of every skeletonization unit (the leading r x r block of its
+// record, r = n - rank), one CTA per (unit, 64-column block), into X laid out
+// like the records.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_unit_trinv(LevelDev Lv, PhaseDev Ph, T* X) {
+  extern __shared__ unsigned char smraw[];
+  const int u = blockIdx.y;
+  const int n = Lv.group_size[Ph.u_group[u]];
+  const int r = n - Ph.rank[u];
+  const int J0 = blockIdx.x * kTile;
+  if (J0 >= r) return;
+  const T* Fu = (const T*)Ph.rec + Ph.u_rec_off[u];
+  cta_trinv_block(Fu, n, r, X + Ph.u_rec_off[u], n, J0, (T*)smraw);
+}
+
+// Lower triangle of every unit's L_rr^{-1} from X back into its record.
+template <typename T>
+__global__ void k_unit_inv_store(LevelDev Lv, PhaseDev Ph, const T* X) {
+  const int u = blockIdx.y;
+  const int n = Lv.group_size[Ph.u_group[u]];
+  const int r = n - Ph.rank[u];
+  T* Fu = (T*)Ph.rec + Ph.u_rec_off[u];
+  const T* Xu = X + Ph.u_rec_off[u];
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < r * r; idx += gridDim.x * blockDim.x) {
+    const int i = idx % r, j = idx / r;
+    if (i >= j) Fu[i + (int64_t)j * n] = Xu[i + (int64_t)j * n];
+  }
+}
+
+// Inverses of lower-triangular blocks of order m <= 32, one warp each, the
+// block staged in shared memory: lane c forms column c of X = L^{-1} by
+// forward substitution.  UNIT: the leading r x r block of every unit record,
+// in place; otherwise every L_g into Ph.Linv (upper triangle zero).
+template <typename T>
+constexpr int trinv_warps() { return sizeof(T) == 4 ? 4 : 2; }   // 33.8 KB of static shared memory
+
+template <typename T, bool UNIT>
+__global__ void __launch_bounds__(32 * trinv_warps<T>()) k_trinv_warp(LevelDev Lv, PhaseDev Ph, int count) {
+  constexpr int W = trinv_warps<T>();
+  __shared__ T Ls[W][32][33];
+  __shared__ T Xs[W][32][33];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int item = blockIdx.x * W + warp;
+  if (item >= count) return;
+  const T* L;
+  T* out;
+  int m, ld;
+  if (UNIT) {
+    const int n = Lv.group_size[Ph.u_group[item]];
+    m = n - Ph.rank[item];
+    ld = n;
+    out = (T*)Ph.rec + Ph.u_rec_off[item];
+    L = out;
+  } else {
+    m = Lv.group_size[Ph.pre_group[item]];
+    ld = m;
+    L = (const T*)Ph.Lbuf + Ph.pre_off[item];
+    out = (T*)Ph.Linv + Ph.pre_off[item];
+  }
+  T (*Lw)[33] = Ls[warp];
+  T (*Xw)[33] = Xs[warp];
+  for (int idx = lane; idx < m * m; idx += 32) {
+    const int i = idx % m, j = idx / m;
+    Lw[i][j] = i >= j ? L[i + (int64_t)j * ld] : T(0);
+  }
+  __syncwarp();
+  const int c = lane;
+  for (int i = 0; i < m; ++i) {
+    if (c <= i) {
+      T v = i == c ? T(1) : T(0);
+      for (int j = c; j < i; ++j) v -= Lw[i][j] * Xw[j][c];
+      Xw[i][c] = v / Lw[i][i];
+    }
+  }
+  __syncwarp();
+  for (int idx = lane; idx < m * m; idx += 32) {
+    const int i = idx % m, j = idx / m;
+    if (i >= j) out[i + (int64_t)j * ld] = Xw[i][j];
+    else if (!UNIT) out[i + (int64_t)j * ld] = T(0);
+  }
+}
+
 template <typename T>
 __global__ void k_front_inv_store(LevelDev Lv, const T* X, const int64_t* xoff) {
   const int c = blockIdx.y;
@@ -1900,18 +1982,30 @@ void launch_expand_gids(const LevelDev& Lv, cudaStream_t s) {
 }
 
 template <typename T>
+static bool leaf_warp_fits(const GeoDev& G, const LevelDev& Lv, int nbt) {
+  if (G.d != 2 || Lv.max_w > kLeafWarpW || Lv.max_nB > nbt) return false;
+  if (nbt == 64 && sizeof(T) != 4) return false;   // 64 accumulator columns fit registers in FP32 only
+  return kLeafWarpCta * leaf_warp_bytes<T>(Lv.max_nI, G.leaf, nbt) <= 48 * 1024;
+}
+
+bool leaf_elim_needs_z(const GeoDev& G, const LevelDev& Lv, size_t elem) {
+  const bool warp = elem == 4 ? (leaf_warp_fits<float>(G, Lv, 32) || leaf_warp_fits<float>(G, Lv, 64))
+                              : leaf_warp_fits<double>(G, Lv, 32);
+  return !warp && Lv.max_nB > kStreamNB;
+}
+
+template <typename T>
 void launch_leaf_elim(const GeoDev& G, const LevelDev& Lv, const double* diag, const double* off,
                       int* status, cudaStream_t s) {
   if (!Lv.ncell) return;
-  const bool warp_ok = G.d == 2 && Lv.max_w <= kLeafWarpW;
-  if (warp_ok && Lv.max_nB <= 32 && kLeafWarpCta * leaf_warp_bytes<T>(Lv.max_nI, G.leaf, 32) <= 48 * 1024) {
+  if (leaf_warp_fits<T>(G, Lv, 32)) {
     const size_t sm = kLeafWarpCta * leaf_warp_bytes<T>(Lv.max_nI, G.leaf, 32);
     k_leaf_warp<T, 32><<<(Lv.ncell + kLeafWarpCta - 1) / kLeafWarpCta, 32 * kLeafWarpCta, sm, s>>>(
         G, Lv, diag, off, status);
     return;
   }
-  if constexpr (sizeof(T) == 4) {   // 64 accumulator columns per lane pair fit registers in FP32 only
-    if (warp_ok && Lv.max_nB <= 64 && kLeafWarpCta * leaf_warp_bytes<T>(Lv.max_nI, G.leaf, 64) <= 48 * 1024) {
+  if constexpr (sizeof(T) == 4) {   // no FP64 instance of the 64-column kernel
+    if (leaf_warp_fits<T>(G, Lv, 64)) {
       const size_t sm = kLeafWarpCta * leaf_warp_bytes<T>(Lv.max_nI, G.leaf, 64);
       k_leaf_warp<T, 64><<<(Lv.ncell + kLeafWarpCta - 1) / kLeafWarpCta, 32 * kLeafWarpCta, sm, s>>>(
           G, Lv, diag, off, status);
@@ -1989,10 +2083,28 @@ template <typename T>
 void launch_precond_diag(const LevelDev& Lv, const PhaseDev& Ph, int* status, cudaStream_t s) {
   if (Ph.npre)
     k_precond_diag<T><<<Ph.npre, kThreads, partial_chol_smem_elems() * sizeof(T), s>>>(Lv, Ph, status);
-  if (Ph.npre && Ph.Linv) {
+  if (Ph.npre && Ph.Linv && Lv.max_group <= 32) {
+    constexpr int W = trinv_warps<T>();
+    k_trinv_warp<T, false><<<(Ph.npre + W - 1) / W, 32 * W, 0, s>>>(Lv, Ph, Ph.npre);
+  } else if (Ph.npre && Ph.Linv) {
     const unsigned nb = (unsigned)((Lv.max_group + kTile - 1) / kTile);
     k_group_trinv<T><<<dim3(nb, Ph.npre), kThreads, kTile * (kTile + 1) * sizeof(T), s>>>(Lv, Ph);
   }
+}
+
+template <typename T>
+int launch_unit_invert(const LevelDev& Lv, const PhaseDev& Ph, T* X, cudaStream_t s) {
+  if (!Ph.nunit) return 0;
+  if (Ph.max_n <= 32) {
+    constexpr int W = trinv_warps<T>();
+    k_trinv_warp<T, true><<<(Ph.nunit + W - 1) / W, 32 * W, 0, s>>>(Lv, Ph, Ph.nunit);
+    return 1;
+  }
+  const unsigned nb = (unsigned)((Ph.max_n + kTile - 1) / kTile);
+  k_unit_trinv<T><<<dim3(nb, Ph.nunit), kThreads, kTile * (kTile + 1) * sizeof(T), s>>>(Lv, Ph, X);
+  const unsigned chunks = (unsigned)((Ph.max_n * Ph.max_n + 255) / 256);
+  k_unit_inv_store<T><<<dim3(chunks, Ph.nunit), 256, 0, s>>>(Lv, Ph, X);
+  return 2;
 }
 
 template <typename T>
@@ -2124,6 +2236,7 @@ int configure_factor_kernels() {
   template int launch_extend_add<T>(const LevelDev&, const LevelDev&, int64_t, int, cudaStream_t); \
   template void launch_partial_chol<T>(const LevelDev&, int*, cudaStream_t);                      \
   template void launch_band_block_inverse<T>(const LevelDev&, cudaStream_t);                     \
+  template int launch_unit_invert<T>(const LevelDev&, const PhaseDev&, T*, cudaStream_t);        \
   template void launch_front_invert<T>(const LevelDev&, T*, const int64_t*, cudaStream_t);       \
   template void launch_front_panel<T>(const LevelDev&, int, int*, cudaStream_t);                  \
   template void launch_front_trailing<T>(const LevelDev&, int, int64_t, cudaStream_t);            \

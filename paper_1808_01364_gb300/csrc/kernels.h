@@ -16,6 +16,9 @@ void launch_stencil_from_csr(const GeoDev& G, const int64_t* rowptr, const int32
 void launch_expand_gids(const LevelDev& Lv, cudaStream_t s);
 template <typename T>
 size_t leaf_smem_bytes(int max_nI, int max_nB, int max_w, int leaf, int d);
+// Whether launch_leaf_elim takes the panel kernel, the one that keeps
+// Z = L^{-1} A_IB in Lv.zbuf (nI x nB per cell); the others need no scratch.
+bool leaf_elim_needs_z(const GeoDev& G, const LevelDev& Lv, size_t elem);
 template <typename T>
 void launch_leaf_elim(const GeoDev& G, const LevelDev& Lv, const double* diag, const double* off,
                       int* status, cudaStream_t s);
@@ -43,6 +46,11 @@ template <typename T>
 void launch_front_schur(const LevelDev& Lv, int64_t tiles, cudaStream_t s);
 int64_t front_trailing_tiles(int nI, int n, int p0);
 int64_t front_schur_tiles(int nI, int nB);
+// Replaces the leading r x r block L_rr of every unit record of the phase by
+// L_rr^{-1} (lower triangle), through X (scratch laid out like the records).
+// Returns the number of launches.
+template <typename T>
+int launch_unit_invert(const LevelDev& Lv, const PhaseDev& Ph, T* X, cudaStream_t s);
 template <typename T>
 void launch_precond_diag(const LevelDev& Lv, const PhaseDev& Ph, int* status, cudaStream_t s);
 template <typename T>

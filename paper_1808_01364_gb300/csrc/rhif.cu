@@ -140,13 +140,13 @@ int Packer::upload(void* dst, cudaStream_t s) const {
 enum Cat {
   kCatStencil, kCatLeafElim, kCatExpandGids, kCatExtendAdd, kCatPartialChol, kCatPrecondDiag, kCatPrecondScale,
   kCatSkel, kCatApplyCellUp, kCatApplyCellDown, kCatApplyGroupUp, kCatApplyGroupDown, kCatSpmv,
-  kCatVector, kCatAssemble, kCatGrad, kCatApplyLeafUp, kCatApplyLeafDown, kNumCat
+  kCatVector, kCatAssemble, kCatGrad, kCatApplyLeafUp, kCatApplyLeafDown, kCatBandInverse, kNumCat
 };
 static const char* kCatName[kNumCat] = {
     "stencil_from_csr", "leaf_elim", "expand_gids", "extend_add", "partial_chol", "precond_diag",
     "precond_scale", "skel", "apply_cell_up", "apply_cell_down", "apply_group_up",
     "apply_group_down", "spmv", "pcg_vector", "assemble_fd", "grad_logcoef", "apply_leaf_up",
-    "apply_leaf_down"};
+    "apply_leaf_down", "band_inverse"};
 struct KStat {
   int64_t launches = 0;
   double ms = 0, flops = 0, bytes = 0;
@@ -400,8 +400,6 @@ static int upload_level(rhif_handle* H, LevelStore& S, size_t elem) {
     if ((rc = H->mem.get((void**)&D.rank, U.group.size() * sizeof(int)))) return rc;
     D.Mbuf = nullptr;
   }
-  // the staging buffer must outlive the copy
-  CK(cudaStreamSynchronize(H->mem.s));
   return RHIF_OK;
 }
 
@@ -550,13 +548,19 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
         lvl_flops += nI * w * w + nB * nI * w + nI * nB * nB;
         H->apply_bytes += 2.0 * elem * (nI * (w + 1) + nB);
       }
-      void* Zb = nullptr;
-      if ((rc = H->mem.get(&Zb, P.z_total * elem))) return rc;
-      S.dev.zbuf = Zb;
-      Launch t(kCatLeafElim, s, lvl_flops, 0.0);
-      launch_leaf_elim<T>(H->gd, S.dev, H->diag, H->off, H->status, s);
-      launch_band_block_inverse<T>(S.dev, s);
-      add_launches(kCatLeafElim, 1);
+      if (leaf_elim_needs_z(H->gd, S.dev, elem)) {
+        void* Zb = nullptr;
+        if ((rc = H->mem.get(&Zb, P.z_total * elem))) return rc;
+        S.dev.zbuf = Zb;
+      }
+      {
+        Launch t(kCatLeafElim, s, lvl_flops, 0.0);
+        launch_leaf_elim<T>(H->gd, S.dev, H->diag, H->off, H->status, s);
+      }
+      {
+        Launch t(kCatBandInverse, s, 0.0, 2.0 * elem * P.band_total);
+        launch_band_block_inverse<T>(S.dev, s);
+      }
     } else {
       for (int c = 0; c < P.ncell(); ++c) {
         const double nI = P.nI[c], nB = P.nB[c];
@@ -667,10 +671,11 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
           D.scale_task = (const int*)((char*)scale_dev + o_task);
           D.scale_off = (const int64_t*)((char*)scale_dev + o_off);
           D.nscale_task = (int)off.size();
-          if ((rc = H->mem.get(&D.Linv, ph.pre_total * elem))) return rc;
         }
+        // the L_g^{-1} (used by the many-CTA scaling, and kept for the application)
+        if ((rc = H->mem.get(&D.Linv, ph.pre_total * elem))) return rc;
         {
-          Launch t(kCatPrecondDiag, s, dflops, 0.0);
+          Launch t(kCatPrecondDiag, s, dflops, 0.0, 2);
           launch_precond_diag<T>(S.dev, D, H->status, s);
         }
         {
@@ -680,19 +685,29 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
           } else {
             launch_precond_scale_big<T>(S.dev, D, blocks, s);
             add_launches(kCatPrecondScale, blocks > 0 ? 2 : 0);
-            H->mem.release(D.Linv);
             H->mem.release(scale_dev);
-            D.Linv = nullptr;
             D.scale_task = nullptr;
             D.scale_off = nullptr;
             D.nscale_task = 0;
           }
         }
+        // from here on only the application reads the block-Jacobi factors:
+        // it gets L_g^{-1} in their place
+        H->mem.release(D.Lbuf);
+        D.Lbuf = D.Linv;
+        D.Linv = nullptr;
       }
       const int64_t nunit = (int64_t)ph.units.group.size();
       {
         Launch t(kCatSkel, s, 0.0, 0.0, nunit ? 1 : 0);
         if ((rc = skeletonize<T>(H, P, ph, S.dev, D, alive_d, s))) return rc;
+      }
+      if (nunit) {   // the units' L_rr become L_rr^{-1} for the application
+        void* X = nullptr;
+        if ((rc = H->mem.get(&X, ph.units.rec_total * elem))) return rc;
+        Launch t(kCatSkel, s, 0.0, 0.0, 0);
+        add_launches(kCatSkel, launch_unit_invert<T>(S.dev, D, (T*)X, s));
+        H->mem.release(X);
       }
       if ((rc = check_status(H, "skeletonization"))) return rc;
       H->mem.release(M);

@@ -64,7 +64,8 @@ def test_many_cta_schedules_match_oracle(gpu_lib, ns, leaf, tol, b, edge, skel_c
     # panel + trailing launches per 32 interior columns: more than one launch per level
     assert ks["partial_chol"]["launches"] > levels - 1
     # symmetrize + row solves + column solves on every preconditioned phase
-    assert ks["precond_scale"]["launches"] >= 3 * ks["precond_diag"]["launches"]
+    # (precond_diag launches the Cholesky and the inverse of the L_g per phase)
+    assert ks["precond_scale"]["launches"] >= 3 * (ks["precond_diag"]["launches"] // 2)
     same = True
     for lvl in range(len(Fo.levels)):
         for p in range(len(Fo.levels[lvl].phases)):

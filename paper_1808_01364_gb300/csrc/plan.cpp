@@ -6,6 +6,8 @@
 
 #include <algorithm>
 
+#include "host_pool.h"
+
 namespace rhif {
 
 Geometry make_geometry(int d, const int* ns, int leaf) {
@@ -136,8 +138,9 @@ namespace {
 // the planner's temporaries
 struct PlanScratch {
   std::vector<LevelPlan> pool;
-  std::vector<int64_t> cstart, cnt, gcode, key;
+  std::vector<int64_t> cstart, cnt, gcode;
   std::vector<int> gpos_off, newpos, src, cell_of_code, group_of_code, prev_cell_of_code;
+  std::vector<int> gna, cg, cgoff, nseg, nrow;
   std::vector<uint8_t> mark;
 };
 thread_local PlanScratch t_scratch;
@@ -191,85 +194,126 @@ LevelPlan build_level(const Geometry& G, int level, const std::vector<uint8_t>& 
   std::vector<int64_t>& gcode = X.gcode;
   std::vector<int>& gpos_off = X.gpos_off;
   std::vector<int>& newpos = X.newpos;
+  HostPool& pool = HostPool::get();
   if (level == 0) {
+    // code sizes in code order (vx fastest), then the rows (vy, vz) filled in parallel
     P.bucket.resize(G.N);
-    int64_t pos = 0;
     const int vz1 = d == 3 ? C.base - 1 : 1, vz0 = d == 3 ? 0 : 1;
-    for (int vz = vz0; vz <= vz1; ++vz) {
-      int zlo = 1, zhi = 1;
-      if (d == 3) vrange(vz, w, G.ns[2], &zlo, &zhi);
-      for (int vy = 0; vy < C.base; ++vy) {
-        int ylo, yhi;
+    std::vector<int> ext[3];
+    for (int a = 0; a < 3; ++a) {
+      ext[a].assign(C.base, 1);
+      if (a >= d) continue;
+      for (int v = 0; v < C.base; ++v) {
+        int lo, hi;
+        vrange(v, w, G.ns[a], &lo, &hi);
+        ext[a][v] = std::max(hi - lo + 1, 0);
+      }
+    }
+    int64_t pos = 0;
+    for (int vz = vz0; vz <= vz1; ++vz)
+      for (int vy = 0; vy < C.base; ++vy)
+        for (int vx = 0; vx < C.base; ++vx) {
+          int v[3] = {vx, vy, vz};
+          cstart[C.join(v)] = pos;
+          pos += (int64_t)ext[0][vx] * ext[1][vy] * (d == 3 ? ext[2][vz] : 1);
+        }
+    cstart[C.ncode] = pos;
+    const int nrows = (vz1 - vz0 + 1) * C.base;
+    pool.parallel_for(nrows, 16, [&](int64_t r0, int64_t r1) {
+      for (int64_t row = r0; row < r1; ++row) {
+        const int vz = vz0 + (int)(row / C.base), vy = (int)(row % C.base);
+        int zlo = 1, zhi = 1, ylo, yhi;
+        if (d == 3) vrange(vz, w, G.ns[2], &zlo, &zhi);
         vrange(vy, w, G.ns[1], &ylo, &yhi);
         for (int vx = 0; vx < C.base; ++vx) {
           int xlo, xhi;
           vrange(vx, w, G.ns[0], &xlo, &xhi);
           int v[3] = {vx, vy, vz};
-          cstart[C.join(v)] = pos;
+          int64_t q = cstart[C.join(v)];
           for (int z = zlo; z <= zhi; ++z)
             for (int y = ylo; y <= yhi; ++y) {
               const int64_t base = (int64_t)(y - 1) * G.ns[0] + (int64_t)(z - 1) * G.ns[0] * G.ns[1];
-              for (int x = xlo; x <= xhi; ++x) P.bucket[pos++] = (int32_t)(base + x - 1);
+              for (int x = xlo; x <= xhi; ++x) P.bucket[q++] = (int32_t)(base + x - 1);
             }
         }
       }
-    }
-    cstart[C.ncode] = pos;
+    });
   } else {
     // Every DOF of a separator group of level - 1 lands in the same code at
     // this level (an open interval of width w/2 lies inside one interval of
     // width w, and a plane x = q w/2 is either a plane or an interior line),
-    // so codes, counts and the scatter go group by group.
+    // so codes and counts go group by group, and each code is filled from its
+    // groups (in group order) independently of the others.
     const Coder Cp(G, level - 1);
     const int pg = prev->ngroup();
     gcode.resize(pg);
+    std::vector<int>& gna = X.gna;
+    gna.resize(pg);
+    pool.parallel_for(pg, 1024, [&](int64_t g0, int64_t g1) {
+      for (int64_t g = g0; g < g1; ++g) {
+        int v[3];
+        Cp.split(prev->group_code[g], v);
+        for (int a = 0; a < d; ++a) v[a] = (v[a] % 2 == 0) ? v[a] / 2 : 2 * (((v[a] - 1) / 2) / 2) + 1;
+        gcode[g] = C.join(v);
+        const uint8_t* kp = keep.data() + prev->group_start[g];
+        int na = 0;
+        for (int o = 0; o < prev->group_size[g]; ++o) na += kp[o] != 0;
+        gna[g] = na;
+      }
+    });
     gpos_off.resize(pg + 1);
     gpos_off[0] = 0;
-    std::vector<int64_t>& cnt = X.cnt;
-    cnt.assign(C.ncode + 1, 0);
+    std::vector<int>& cgoff = X.cgoff;   // groups of each code, stable
+    cgoff.assign(C.ncode + 1, 0);
     for (int g = 0; g < pg; ++g) {
-      int v[3];
-      Cp.split(prev->group_code[g], v);
-      for (int a = 0; a < d; ++a) v[a] = (v[a] % 2 == 0) ? v[a] / 2 : 2 * (((v[a] - 1) / 2) / 2) + 1;
-      gcode[g] = C.join(v);
-      const uint8_t* kp = keep.data() + prev->group_start[g];
-      int na = 0;
-      for (int o = 0; o < prev->group_size[g]; ++o) na += kp[o] != 0;
-      cnt[gcode[g] + 1] += na;
       gpos_off[g + 1] = gpos_off[g] + prev->group_size[g];
+      cstart[gcode[g] + 1] += gna[g];
+      ++cgoff[gcode[g] + 1];
     }
-    for (int64_t c = 0; c < C.ncode; ++c) cnt[c + 1] += cnt[c];
-    cstart = cnt;
-    P.bucket.resize(cnt[C.ncode]);
+    for (int64_t c = 0; c < C.ncode; ++c) {
+      cstart[c + 1] += cstart[c];
+      cgoff[c + 1] += cgoff[c];
+    }
+    std::vector<int>& cg = X.cg;
+    cg.resize(pg);
+    {
+      std::vector<int>& fillp = X.nseg;   // reused as a cursor here
+      fillp.assign(cgoff.begin(), cgoff.end() - 1);
+      for (int g = 0; g < pg; ++g) cg[fillp[gcode[g]]++] = g;
+    }
+    P.bucket.resize(cstart[C.ncode]);
     newpos.assign(gpos_off[pg], -1);
     std::vector<int>& src = X.src;
     src.resize(P.bucket.size());
-    for (int g = 0; g < pg; ++g) {
-      const int32_t* gb = prev->bucket.data() + prev->group_start[g];
-      const uint8_t* kp = keep.data() + prev->group_start[g];
-      int64_t& cur = cnt[gcode[g]];
-      for (int o = 0; o < prev->group_size[g]; ++o)
-        if (kp[o]) {
-          P.bucket[cur] = gb[o];
-          src[cur] = gpos_off[g] + o;
-          ++cur;
-        }
-    }
     // ascending DOF index within every code; newpos follows the moves
-    std::vector<int64_t>& key = X.key;
-    for (int64_t c = 0; c < C.ncode; ++c) {
-      const int64_t a = cstart[c], b = cstart[c + 1];
-      if (b - a > 1 && !std::is_sorted(P.bucket.begin() + a, P.bucket.begin() + b)) {
-        key.resize(b - a);
-        for (int64_t i = a; i < b; ++i) key[i - a] = ((int64_t)P.bucket[i] << 32) | (uint32_t)src[i];
-        std::sort(key.begin(), key.end());
-        for (int64_t i = a; i < b; ++i) {
-          P.bucket[i] = (int32_t)(key[i - a] >> 32);
-          src[i] = (int)(key[i - a] & 0xffffffff);
+    pool.parallel_for(C.ncode, 1024, [&](int64_t c0, int64_t c1) {
+      std::vector<int64_t> key;
+      for (int64_t c = c0; c < c1; ++c) {
+        int64_t q = cstart[c];
+        for (int t = cgoff[c]; t < cgoff[c + 1]; ++t) {
+          const int g = cg[t];
+          const int32_t* gb = prev->bucket.data() + prev->group_start[g];
+          const uint8_t* kp = keep.data() + prev->group_start[g];
+          for (int o = 0; o < prev->group_size[g]; ++o)
+            if (kp[o]) {
+              P.bucket[q] = gb[o];
+              src[q] = gpos_off[g] + o;
+              ++q;
+            }
         }
+        const int64_t a = cstart[c], b = cstart[c + 1];
+        if (b - a > 1 && !std::is_sorted(P.bucket.begin() + a, P.bucket.begin() + b)) {
+          key.resize(b - a);
+          for (int64_t i = a; i < b; ++i) key[i - a] = ((int64_t)P.bucket[i] << 32) | (uint32_t)src[i];
+          std::sort(key.begin(), key.end());
+          for (int64_t i = a; i < b; ++i) {
+            P.bucket[i] = (int32_t)(key[i - a] >> 32);
+            src[i] = (int)(key[i - a] & 0xffffffff);
+          }
+        }
+        for (int64_t i = a; i < b; ++i) newpos[src[i]] = (int)i;
       }
-      for (int64_t i = a; i < b; ++i) newpos[src[i]] = (int)i;
-    }
+    });
   }
   auto csize = [&](int64_t c) { return (int)(cstart[c + 1] - cstart[c]); };
 
@@ -323,22 +367,19 @@ LevelPlan build_level(const Geometry& G, int level, const std::vector<uint8_t>& 
   }
   const int ngroup = (int)P.group_t.size();
 
-  // 4. cells: interior range, separator segments, storage offsets
-  P.cell_start.reserve(ncell);
-  P.nI.reserve(ncell);
-  P.nB.reserve(ncell);
-  P.seg_off.reserve(ncell + 1);
-  P.seg_off.push_back(0);
-  P.gid_off.push_back(0);
-  P.b_off.push_back(0);
-  std::vector<int> gcount(ngroup + 1, 0);
+  // 4. cells: interior range, separator segments, storage offsets (segment
+  // counts per cell in parallel, offsets in order, segments in parallel)
   const int dz = d >= 3 ? 1 : 0;
-  for (int ci = 0; ci < ncell; ++ci) {
-    const int64_t cc = P.cell_code[ci];
+  P.cell_start.resize(ncell);
+  P.nI.resize(ncell);
+  P.nB.resize(ncell);
+  if (level == 0) P.band_w.resize(ncell);
+  std::vector<int>& nseg = X.nseg;
+  nseg.resize(ncell);
+  auto cell_segments = [&](int ci, int* sg, int* sp) {   // returns the count; fills if sg
     int v[3];
-    C.split(cc, v);
-    const int nI = csize(cc);
-    int nB = 0;
+    C.split(P.cell_code[ci], v);
+    int cnt = 0, nB = 0;
     for (int oz = -dz; oz <= dz; ++oz)
       for (int oy = -1; oy <= 1; ++oy)
         for (int ox = -1; ox <= 1; ++ox) {
@@ -346,46 +387,82 @@ LevelPlan build_level(const Geometry& G, int level, const std::vector<uint8_t>& 
           int u[3] = {v[0] + ox, v[1] + oy, v[2] + oz};
           const int gi = group_of_code[C.join(u)];
           if (gi < 0) continue;
-          P.seg_group.push_back(gi);
-          P.seg_pos.push_back(nB);
-          ++gcount[gi + 1];
+          if (sg) {
+            sg[cnt] = gi;
+            sp[cnt] = nB;
+          }
+          ++cnt;
           nB += P.group_size[gi];
         }
-    const int n = nI + nB;
-    P.cell_start.push_back((int32_t)cstart[cc]);
-    P.nI.push_back(nI);
-    P.nB.push_back(nB);
-    P.seg_off.push_back((int)P.seg_group.size());
-    P.gid_off.push_back(P.gid_off.back() + n);
-    P.b_off.push_back(P.b_off.back() + nB);
-    if (level == 0) {
-      int bw = 1;   // interior box: half bandwidth = its x extent (2D) or x*y extent (3D)
-      for (int a = 0; a < d - 1; ++a) {
-        int lo, hi;
-        vrange(v[a], w, G.ns[a], &lo, &hi);
-        bw *= std::max(hi - lo + 1, 0);
+    P.nB[ci] = nB;
+    return cnt;
+  };
+  pool.parallel_for(ncell, 256, [&](int64_t c0, int64_t c1) {
+    for (int64_t ci = c0; ci < c1; ++ci) {
+      const int64_t cc = P.cell_code[ci];
+      nseg[ci] = cell_segments((int)ci, nullptr, nullptr);
+      P.cell_start[ci] = (int32_t)cstart[cc];
+      P.nI[ci] = csize(cc);
+      if (level == 0) {
+        int v[3];
+        C.split(cc, v);
+        int bw = 1;   // interior box: half bandwidth = its x extent (2D) or x*y extent (3D)
+        for (int a = 0; a < d - 1; ++a) {
+          int lo, hi;
+          vrange(v[a], w, G.ns[a], &lo, &hi);
+          bw *= std::max(hi - lo + 1, 0);
+        }
+        P.band_w[ci] = P.nI[ci] == 0 ? 0 : bw;
       }
-      if (nI == 0) bw = 0;
-      P.band_w.push_back(bw);
-      P.band_off.push_back(P.band_total);
+    }
+  });
+  P.seg_off.resize(ncell + 1);
+  P.gid_off.resize(ncell + 1);
+  P.b_off.resize(ncell + 1);
+  P.front_off.resize(ncell);
+  P.frame_off.resize(ncell);
+  P.frame_ld.resize(ncell);
+  if (level == 0) {
+    P.band_off.resize(ncell);
+    P.z_off.resize(ncell);
+  }
+  P.seg_off[0] = 0;
+  P.gid_off[0] = 0;
+  P.b_off[0] = 0;
+  for (int ci = 0; ci < ncell; ++ci) {
+    const int nI = P.nI[ci], nB = P.nB[ci], n = nI + nB;
+    P.seg_off[ci + 1] = P.seg_off[ci] + nseg[ci];
+    P.gid_off[ci + 1] = P.gid_off[ci] + n;
+    P.b_off[ci + 1] = P.b_off[ci] + nB;
+    if (level == 0) {
+      const int bw = P.band_w[ci];
+      P.band_off[ci] = P.band_total;
       P.band_total += pad4((int64_t)nI * (bw + 1));
-      P.z_off.push_back(P.z_total);
+      P.z_off[ci] = P.z_total;
       P.z_total += pad4((int64_t)nI * nB);
-      P.frame_off.push_back(P.frame_total);
-      P.frame_ld.push_back(nB);
+      P.frame_off[ci] = P.frame_total;
+      P.frame_ld[ci] = nB;
       P.frame_total += pad4((int64_t)nB * nB);
-      P.front_off.push_back(0);
+      P.front_off[ci] = 0;
       P.max_w = std::max(P.max_w, bw);
     } else {
-      P.front_off.push_back(P.front_total);
-      P.frame_off.push_back(P.front_total + nI + (int64_t)nI * n);
-      P.frame_ld.push_back(n);
+      P.front_off[ci] = P.front_total;
+      P.frame_off[ci] = P.front_total + nI + (int64_t)nI * n;
+      P.frame_ld[ci] = n;
       P.front_total += pad4((int64_t)n * n);
     }
     P.max_nI = std::max(P.max_nI, nI);
     P.max_nB = std::max(P.max_nB, nB);
     P.max_n = std::max(P.max_n, n);
   }
+  P.seg_group.resize(P.seg_off[ncell]);
+  P.seg_pos.resize(P.seg_off[ncell]);
+  pool.parallel_for(ncell, 256, [&](int64_t c0, int64_t c1) {
+    for (int64_t ci = c0; ci < c1; ++ci)
+      cell_segments((int)ci, P.seg_group.data() + P.seg_off[ci], P.seg_pos.data() + P.seg_off[ci]);
+  });
+  std::vector<int> gcount(ngroup + 1, 0);
+  for (int sgi : P.seg_group) ++gcount[sgi + 1];
   for (int gi = 0; gi < ngroup; ++gi) gcount[gi + 1] += gcount[gi];
   P.group_cell_off.assign(gcount.begin(), gcount.end());
   P.group_cell.resize(gcount[ngroup]);
@@ -428,7 +505,8 @@ LevelPlan build_level(const Geometry& G, int level, const std::vector<uint8_t>& 
       P.ea_off.push_back((int)P.ea_child.size());
     }
     P.ea_map.assign(map_total, -1);
-    for (int ci = 0; ci < ncell; ++ci) {
+    pool.parallel_for(ncell, 128, [&](int64_t c0, int64_t c1) {
+    for (int64_t ci = c0; ci < c1; ++ci) {
       const int nI = P.nI[ci];
       for (int k = P.ea_off[ci]; k < P.ea_off[ci + 1]; ++k) {
         const int pc = P.ea_child[k];
@@ -457,12 +535,19 @@ LevelPlan build_level(const Geometry& G, int level, const std::vector<uint8_t>& 
             }
       }
     }
+    });
   }
 
   if (level >= G.L) return P;   // root front only
 
   // 6. preconditioning + skeletonization passes
   const int npass = (d == 3 && edge_skel) ? 2 : 1;
+  std::vector<int>& nrow_of = X.nrow;   // unit row counts of the unit groups, in parallel
+  nrow_of.assign(ngroup, 0);
+  pool.parallel_for(ngroup, 1024, [&](int64_t g0, int64_t g1) {
+    for (int64_t gi = g0; gi < g1; ++gi)
+      if (P.group_t[gi] <= npass) nrow_of[gi] = unit_row_count(P, (int)gi);
+  });
   for (int pass = 0; pass < npass; ++pass) {
     PhasePlan ph;
     ph.unit_type = pass == 0 ? 1 : 2;
@@ -481,7 +566,7 @@ LevelPlan build_level(const Geometry& G, int level, const std::vector<uint8_t>& 
       if (P.group_t[gi] == ph.unit_type) {
         ph.group_unit[gi] = (int)U.group.size();
         U.group.push_back(gi);
-        const int nrow = unit_row_count(P, gi);
+        const int nrow = nrow_of[gi];
         U.nrow.push_back(nrow);
         U.m_off.push_back(U.m_total);
         U.m_total += (int64_t)(nrow + sz) * sz;

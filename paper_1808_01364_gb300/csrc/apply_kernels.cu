@@ -242,9 +242,18 @@ __host__ __device__ inline size_t leaf_band_bytes(int max_nI, int max_w) {
   return round16((size_t)max_nI * (max_w + 1) * sizeof(T));
 }
 
+// Bands of half bandwidth <= kBandRegW are read in place (global memory,
+// prefetched into L2 as the warp starts): the per-warp shared memory then
+// holds only the vectors, so every leaf of a level is resident at once.
+// Wider (3D) bands are staged in shared memory by one bulk copy.
+template <typename T>
+static bool leaf_staged(const LevelDev& Lv) {
+  return Lv.max_w > kBandRegW;
+}
+
 template <typename T>
 static size_t leaf_warp_smem(const LevelDev& Lv) {
-  return 16 + leaf_band_bytes<T>(Lv.max_nI, Lv.max_w) +
+  return 16 + (leaf_staged<T>(Lv) ? leaf_band_bytes<T>(Lv.max_nI, Lv.max_w) : 0) +
          round16((2 * (Lv.max_nI + 1) + Lv.max_nB) * sizeof(T));
 }
 
@@ -253,6 +262,18 @@ static int leaf_warps_per_cta(const LevelDev& Lv) {
   const size_t per = leaf_warp_smem<T>(Lv);
   int w = (int)(kStageBudget / per);
   return w < 1 ? 1 : (w > kLeafWarps ? kLeafWarps : w);
+}
+
+// The band of leaf c in place, its cache lines prefetched into L2.
+template <typename T>
+__device__ inline const T* leaf_inplace(const LevelDev& Lv, int c) {
+  const int lane = threadIdx.x & 31;
+  const T* band = (const T*)Lv.band + Lv.band_off[c];
+  const size_t bytes = (size_t)Lv.nI[c] * (Lv.band_w[c] + 1) * sizeof(T);
+  const char* p = (const char*)band;
+  for (size_t off = (size_t)lane * 128; off < bytes; off += 32 * 128)
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p + off));
+  return band;
 }
 
 // Starts the bulk copy of this warp's leaf band; returns the band in shared memory.
@@ -273,7 +294,7 @@ __device__ inline T* leaf_stage(const LevelDev& Lv, int c, unsigned char* base, 
 }
 
 // E_0^T per leaf: y = L^{-1} x_I ; x_B -= A_BI L^{-T} y (sent to the owning groups) ; x_I = y
-template <typename T>
+template <typename T, bool STAGE>
 __global__ void __launch_bounds__(32 * kLeafWarps)
 k_apply_leaf_up(LevelDev Lv, double* x, int64_t ldx, int nrhs, double* ubuf, int64_t ldu,
                 int per_warp_bytes) {
@@ -282,9 +303,9 @@ k_apply_leaf_up(LevelDev Lv, double* x, int64_t ldx, int nrhs, double* ubuf, int
   const int c = blockIdx.x * (blockDim.x >> 5) + warp;
   if (c >= Lv.ncell) return;
   unsigned char* base = smraw + (size_t)warp * per_warp_bytes;
-  uint64_t* bar;
-  const T* band = leaf_stage<T>(Lv, c, base, &bar);
-  T* y = (T*)(base + 16 + leaf_band_bytes<T>(Lv.max_nI, Lv.max_w));
+  uint64_t* bar = nullptr;
+  const T* band = STAGE ? leaf_stage<T>(Lv, c, base, &bar) : leaf_inplace<T>(Lv, c);
+  T* y = (T*)(base + 16 + (STAGE ? leaf_band_bytes<T>(Lv.max_nI, Lv.max_w) : 0));
   T* z = y + Lv.max_nI + 1;
   const int nI = Lv.nI[c], nB = Lv.nB[c], w = Lv.band_w[c];
   const int32_t* gI = Lv.gids + Lv.gid_off[c];
@@ -293,7 +314,7 @@ k_apply_leaf_up(LevelDev Lv, double* x, int64_t ldx, int nrhs, double* ubuf, int
   for (int r = 0; r < nrhs; ++r) {
     double* xr = x + r * ldx;
     warp_gather(xr, gI, nI, y);
-    if (r == 0 && !staged_ok(bar, Lv.status, 0, kKindCell, c)) return;
+    if (STAGE && r == 0 && !staged_ok(bar, Lv.status, 0, kKindCell, c)) return;
     __syncwarp();
     band_fwd(band, nI, w, y);
     for (int i = lane; i < nI; i += 32) {
@@ -309,7 +330,7 @@ k_apply_leaf_up(LevelDev Lv, double* x, int64_t ldx, int nrhs, double* ubuf, int
 }
 
 // E_0 per leaf: x_I = L^{-T}(x_I - L^{-1} A_BI^T x_B)
-template <typename T>
+template <typename T, bool STAGE>
 __global__ void __launch_bounds__(32 * kLeafWarps)
 k_apply_leaf_down(LevelDev Lv, double* x, int64_t ldx, int nrhs, int per_warp_bytes) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -317,9 +338,9 @@ k_apply_leaf_down(LevelDev Lv, double* x, int64_t ldx, int nrhs, int per_warp_by
   const int c = blockIdx.x * (blockDim.x >> 5) + warp;
   if (c >= Lv.ncell) return;
   unsigned char* base = smraw + (size_t)warp * per_warp_bytes;
-  uint64_t* bar;
-  const T* band = leaf_stage<T>(Lv, c, base, &bar);
-  T* t = (T*)(base + 16 + leaf_band_bytes<T>(Lv.max_nI, Lv.max_w));
+  uint64_t* bar = nullptr;
+  const T* band = STAGE ? leaf_stage<T>(Lv, c, base, &bar) : leaf_inplace<T>(Lv, c);
+  T* t = (T*)(base + 16 + (STAGE ? leaf_band_bytes<T>(Lv.max_nI, Lv.max_w) : 0));
   T* v = t + Lv.max_nI + 1;
   const int nI = Lv.nI[c], nB = Lv.nB[c], w = Lv.band_w[c];
   const int32_t* gI = Lv.gids + Lv.gid_off[c];
@@ -337,7 +358,7 @@ k_apply_leaf_down(LevelDev Lv, double* x, int64_t ldx, int nrhs, int per_warp_by
     if (lane == 0)   // A_BI^T x_B in a fixed order (several boundary DOFs may face one interior DOF)
       for (int b = 0; b < nB; ++b)
         if (ci[b] >= 0) v[ci[b]] += xb[b];
-    if (r == 0 && !staged_ok(bar, Lv.status, 0, kKindCell, c)) return;
+    if (STAGE && r == 0 && !staged_ok(bar, Lv.status, 0, kKindCell, c)) return;
     __syncwarp();
     band_fwd(band, nI, w, v);
     for (int i = lane; i < nI; i += 32) t[i] -= v[i];
@@ -983,7 +1004,10 @@ void launch_apply_cell_up(const LevelDev& Lv, double* x, int64_t ldx, int nrhs, 
     const int wpc = leaf_warps_per_cta<T>(Lv);
     const size_t per = leaf_warp_smem<T>(Lv);
     const unsigned grid = (Lv.ncell + wpc - 1) / wpc;
-    k_apply_leaf_up<T><<<grid, 32 * wpc, wpc * per, s>>>(Lv, x, ldx, nrhs, ubuf, ldu, (int)per);
+    if (leaf_staged<T>(Lv))
+      k_apply_leaf_up<T, true><<<grid, 32 * wpc, wpc * per, s>>>(Lv, x, ldx, nrhs, ubuf, ldu, (int)per);
+    else
+      k_apply_leaf_up<T, false><<<grid, 32 * wpc, wpc * per, s>>>(Lv, x, ldx, nrhs, ubuf, ldu, (int)per);
     return;
   }
   const size_t base = round16(2 * (Lv.max_nI + 1) * sizeof(T));
@@ -1000,7 +1024,10 @@ void launch_apply_cell_down(const LevelDev& Lv, double* x, int64_t ldx, int nrhs
     const int wpc = leaf_warps_per_cta<T>(Lv);
     const size_t per = leaf_warp_smem<T>(Lv);
     const unsigned grid = (Lv.ncell + wpc - 1) / wpc;
-    k_apply_leaf_down<T><<<grid, 32 * wpc, wpc * per, s>>>(Lv, x, ldx, nrhs, (int)per);
+    if (leaf_staged<T>(Lv))
+      k_apply_leaf_down<T, true><<<grid, 32 * wpc, wpc * per, s>>>(Lv, x, ldx, nrhs, (int)per);
+    else
+      k_apply_leaf_down<T, false><<<grid, 32 * wpc, wpc * per, s>>>(Lv, x, ldx, nrhs, (int)per);
     return;
   }
   const size_t base = round16((2 * Lv.max_nI + Lv.max_nB + 1) * sizeof(T));
@@ -1091,8 +1118,8 @@ int configure_apply_kernels() {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_cell_down<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_group_up<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_group_down<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_leaf_up<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_leaf_down<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_leaf_up<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_leaf_down<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_group_up_warp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_group_down_warp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_big_up1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);

@@ -962,7 +962,8 @@ __global__ void k_unit_inv_store(LevelDev Lv, PhaseDev Ph, const T* X) {
 // Inverses of lower-triangular blocks of order m <= 32, one warp each, the
 // block staged in shared memory: lane c forms column c of X = L^{-1} by
 // forward substitution.  UNIT: the leading r x r block of every unit record,
-// in place; otherwise every L_g into Ph.Linv (upper triangle zero).
+// in place; otherwise every L_g into Ph.Linv (upper triangle zero; the
+// block-Jacobi factors of at most 32 DOFs get theirs from k_precond_diag_warp).
 template <typename T>
 constexpr int trinv_warps() { return sizeof(T) == 4 ? 4 : 2; }   // 33.8 KB of static shared memory
 
@@ -1056,6 +1057,75 @@ __global__ void __launch_bounds__(kThreads) k_precond_diag(LevelDev Lv, PhaseDev
     report(status, RHIF_ERR_NOT_SPD, Lv.level, kKindGroup, g);
 }
 
+// Groups of at most 32 DOFs, one warp each: L_g = chol(sum over the cells
+// holding g of their diagonal block of g) (written to Lbuf) and L_g^{-1}
+// (written to Linv), the block staged in shared memory, lane = row.
+template <typename T>
+constexpr int pdiag_warps() { return sizeof(T) == 4 ? 4 : 2; }   // 33.8 KB of static shared memory
+
+template <typename T>
+__global__ void __launch_bounds__(32 * pdiag_warps<T>())
+k_precond_diag_warp(LevelDev Lv, PhaseDev Ph, int* status) {
+  constexpr int W = pdiag_warps<T>();
+  __shared__ T Ls[W][32][33];
+  __shared__ T Xs[W][32][33];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int b = blockIdx.x * W + warp;
+  if (b >= Ph.npre) return;
+  const int g = Ph.pre_group[b];
+  const int sz = Lv.group_size[g];
+  T (*A)[33] = Ls[warp];
+  T (*X)[33] = Xs[warp];
+  for (int idx = lane; idx < sz * sz; idx += 32) {
+    const int i = idx % sz, j = idx / sz;
+    T v = T(0);
+    if (i >= j)
+      for (int k = Lv.group_cell_off[g]; k < Lv.group_cell_off[g + 1]; ++k) {
+        int ld;
+        const T* fr = frame_of<T>(Lv, Lv.group_cell[k], &ld);
+        const int pos = Lv.group_pos[k];
+        v += fr[(pos + i) + (int64_t)(pos + j) * ld];
+      }
+    A[i][j] = v;
+  }
+  __syncwarp();
+  int bad = 0;
+  for (int k = 0; k < sz; ++k) {   // right-looking, lane = row
+    T piv = A[k][k];
+    if (!(piv > T(0))) {
+      bad = 1;
+      piv = T(1);
+    }
+    const T d = my_sqrt(piv);
+    __syncwarp();
+    if (lane == k) A[k][k] = d;
+    else if (lane > k && lane < sz) A[lane][k] /= d;
+    __syncwarp();
+    if (lane > k && lane < sz) {
+      const T lik = A[lane][k];
+      for (int j = k + 1; j <= lane; ++j) A[lane][j] -= lik * A[j][k];
+    }
+    __syncwarp();
+  }
+  if (bad && lane == 0) report(status, RHIF_ERR_NOT_SPD, Lv.level, kKindGroup, g);
+  const int c = lane;   // column c of X = L^{-1} by forward substitution
+  for (int i = 0; i < sz; ++i) {
+    if (c <= i && c < sz) {
+      T v = i == c ? T(1) : T(0);
+      for (int j = c; j < i; ++j) v -= A[i][j] * X[j][c];
+      X[i][c] = v / A[i][i];
+    }
+  }
+  __syncwarp();
+  T* Lg = (T*)Ph.Lbuf + Ph.pre_off[b];
+  T* Xg = (T*)Ph.Linv + Ph.pre_off[b];
+  for (int idx = lane; idx < sz * sz; idx += 32) {
+    const int i = idx % sz, j = idx / sz;
+    Lg[idx] = i >= j ? A[i][j] : T(0);
+    Xg[idx] = i >= j ? X[i][j] : T(0);
+  }
+}
+
 // frame <- D^{-1} frame D^{-T}, D = block diag of the L_g of the frame's groups
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_precond_scale(LevelDev Lv, PhaseDev Ph, int stage) {
@@ -1090,8 +1160,17 @@ __global__ void __launch_bounds__(kThreads) k_precond_scale(LevelDev Lv, PhaseDe
     if (pi < 0) continue;
     const int sz = Lv.group_size[g];
     const int pos = Lv.seg_pos[s];
-    const T* Lg = (const T*)Ph.Lbuf + Ph.pre_off[pi];
     T* col = Fr + (int64_t)j * ld + pos;
+    if (Ph.Linv) {   // col <- L_g^{-1} col as a product, bottom up in place
+      const T* Xg = (const T*)Ph.Linv + Ph.pre_off[pi];
+      for (int a = sz - 1; a >= 0; --a) {
+        T v = T(0);
+        for (int q = 0; q <= a; ++q) v += Xg[a + (int64_t)q * sz] * col[q];
+        col[a] = v;
+      }
+      continue;
+    }
+    const T* Lg = (const T*)Ph.Lbuf + Ph.pre_off[pi];
     for (int a = 0; a < sz; ++a) {
       T v = col[a];
       for (int q = 0; q < a; ++q) v -= Lg[a + (int64_t)q * sz] * col[q];
@@ -1107,8 +1186,17 @@ __global__ void __launch_bounds__(kThreads) k_precond_scale(LevelDev Lv, PhaseDe
     if (pi < 0) continue;
     const int sz = Lv.group_size[g];
     const int pos = Lv.seg_pos[s];
-    const T* Lg = (const T*)Ph.Lbuf + Ph.pre_off[pi];
     T* row = Fr + i + (int64_t)pos * ld;
+    if (Ph.Linv) {   // row <- row L_g^{-T} as a product, right to left in place
+      const T* Xg = (const T*)Ph.Linv + Ph.pre_off[pi];
+      for (int a = sz - 1; a >= 0; --a) {
+        T v = T(0);
+        for (int q = 0; q <= a; ++q) v += Xg[a + (int64_t)q * sz] * row[(int64_t)q * ld];
+        row[(int64_t)a * ld] = v;
+      }
+      continue;
+    }
+    const T* Lg = (const T*)Ph.Lbuf + Ph.pre_off[pi];
     for (int a = 0; a < sz; ++a) {
       T v = row[(int64_t)a * ld];
       for (int q = 0; q < a; ++q) v -= Lg[a + (int64_t)q * sz] * row[(int64_t)q * ld];
@@ -2080,16 +2168,18 @@ int64_t front_trailing_tiles(int nI, int n, int p0) { return trail_tiles(nI, n, 
 int64_t front_schur_tiles(int nI, int nB) { return schur_tiles(nI, nB); }
 
 template <typename T>
-void launch_precond_diag(const LevelDev& Lv, const PhaseDev& Ph, int* status, cudaStream_t s) {
-  if (Ph.npre)
-    k_precond_diag<T><<<Ph.npre, kThreads, partial_chol_smem_elems() * sizeof(T), s>>>(Lv, Ph, status);
-  if (Ph.npre && Ph.Linv && Lv.max_group <= 32) {
-    constexpr int W = trinv_warps<T>();
-    k_trinv_warp<T, false><<<(Ph.npre + W - 1) / W, 32 * W, 0, s>>>(Lv, Ph, Ph.npre);
-  } else if (Ph.npre && Ph.Linv) {
-    const unsigned nb = (unsigned)((Lv.max_group + kTile - 1) / kTile);
-    k_group_trinv<T><<<dim3(nb, Ph.npre), kThreads, kTile * (kTile + 1) * sizeof(T), s>>>(Lv, Ph);
+int launch_precond_diag(const LevelDev& Lv, const PhaseDev& Ph, int* status, cudaStream_t s) {
+  if (!Ph.npre) return 0;
+  if (Ph.Linv && Lv.max_group <= 32) {   // factor and inverse, one warp per group
+    constexpr int W = pdiag_warps<T>();
+    k_precond_diag_warp<T><<<(Ph.npre + W - 1) / W, 32 * W, 0, s>>>(Lv, Ph, status);
+    return 1;
   }
+  k_precond_diag<T><<<Ph.npre, kThreads, partial_chol_smem_elems() * sizeof(T), s>>>(Lv, Ph, status);
+  if (!Ph.Linv) return 1;
+  const unsigned nb = (unsigned)((Lv.max_group + kTile - 1) / kTile);
+  k_group_trinv<T><<<dim3(nb, Ph.npre), kThreads, kTile * (kTile + 1) * sizeof(T), s>>>(Lv, Ph);
+  return 2;
 }
 
 template <typename T>
@@ -2241,7 +2331,7 @@ int configure_factor_kernels() {
   template void launch_front_panel<T>(const LevelDev&, int, int*, cudaStream_t);                  \
   template void launch_front_trailing<T>(const LevelDev&, int, int64_t, cudaStream_t);            \
   template void launch_front_schur<T>(const LevelDev&, int64_t, cudaStream_t);                    \
-  template void launch_precond_diag<T>(const LevelDev&, const PhaseDev&, int*, cudaStream_t);     \
+  template int launch_precond_diag<T>(const LevelDev&, const PhaseDev&, int*, cudaStream_t);     \
   template void launch_precond_scale<T>(const LevelDev&, const PhaseDev&, cudaStream_t);          \
   template void launch_precond_scale_big<T>(const LevelDev&, const PhaseDev&, int64_t,            \
                                             cudaStream_t);                                        \

@@ -52,7 +52,7 @@ int64_t front_schur_tiles(int nI, int nB);
 template <typename T>
 int launch_unit_invert(const LevelDev& Lv, const PhaseDev& Ph, T* X, cudaStream_t s);
 template <typename T>
-void launch_precond_diag(const LevelDev& Lv, const PhaseDev& Ph, int* status, cudaStream_t s);
+int launch_precond_diag(const LevelDev& Lv, const PhaseDev& Ph, int* status, cudaStream_t s);   // launches
 template <typename T>
 void launch_precond_scale(const LevelDev& Lv, const PhaseDev& Ph, cudaStream_t s);
 // Tile-product scaling of large frames; needs Ph.Linv (filled by

@@ -403,11 +403,36 @@ static int upload_level(rhif_handle* H, LevelStore& S, size_t elem) {
   return RHIF_OK;
 }
 
+static int status_message(const int* st, const char* where);
+
 static int check_status(rhif_handle* H, const char* where) {
   int st[4] = {0, 0, 0, 0};
   CK(cudaMemcpyAsync(st, H->status, sizeof(st), cudaMemcpyDeviceToHost, H->mem.s));
   CK(cudaStreamSynchronize(H->mem.s));
   CK(cudaGetLastError());
+  return status_message(st, where);
+}
+
+// Pinned host memory of the calling thread for the small per-phase readbacks
+// (status words, ranks, pivot orders), grown as needed; the caller
+// synchronizes the stream before reading it and before the next use.
+static thread_local int* t_rb = nullptr;
+static thread_local size_t t_rb_cap = 0;
+
+static int readback_buffer(size_t ints, int** out) {
+  if (t_rb_cap < ints) {
+    if (t_rb) CK(cudaFreeHost(t_rb));
+    t_rb = nullptr;
+    t_rb_cap = 0;
+    const size_t cap = std::max(ints + ints / 2, size_t(1) << 16);
+    CK(cudaHostAlloc((void**)&t_rb, cap * sizeof(int), cudaHostAllocPortable));
+    t_rb_cap = cap;
+  }
+  *out = t_rb;
+  return RHIF_OK;
+}
+
+static int status_message(const int* st, const char* where) {
   if (st[0] == 0) return RHIF_OK;
   static const char* kinds[] = {"?", "cell", "group", "unit", "root", "argument"};
   char buf[256];
@@ -675,8 +700,8 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
         // the L_g^{-1} (used by the many-CTA scaling, and kept for the application)
         if ((rc = H->mem.get(&D.Linv, ph.pre_total * elem))) return rc;
         {
-          Launch t(kCatPrecondDiag, s, dflops, 0.0, 2);
-          launch_precond_diag<T>(S.dev, D, H->status, s);
+          Launch t(kCatPrecondDiag, s, dflops, 0.0, 0);
+          add_launches(kCatPrecondDiag, launch_precond_diag<T>(S.dev, D, H->status, s));
         }
         {
           Launch t(kCatPrecondScale, s, sflops, 0.0);
@@ -709,17 +734,25 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
         add_launches(kCatSkel, launch_unit_invert<T>(S.dev, D, (T*)X, s));
         H->mem.release(X);
       }
-      if ((rc = check_status(H, "skeletonization"))) return rc;
       H->mem.release(M);
       D.Mbuf = nullptr;
       PhaseStore& PS = S.phases[ip];
       PS.h_rank.resize(nunit);
       PS.h_perm.resize(ph.units.perm_total);
-      CK(cudaMemcpyAsync(PS.h_rank.data(), D.rank, PS.h_rank.size() * sizeof(int),
-                         cudaMemcpyDeviceToHost, s));
-      CK(cudaMemcpyAsync(PS.h_perm.data(), D.perm, PS.h_perm.size() * sizeof(int),
-                         cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
+      {   // status, ranks and pivot orders in one synchronization
+        int* rb = nullptr;
+        if ((rc = readback_buffer(4 + PS.h_rank.size() + PS.h_perm.size(), &rb))) return rc;
+        CK(cudaMemcpyAsync(rb, H->status, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(rb + 4, D.rank, PS.h_rank.size() * sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(rb + 4 + PS.h_rank.size(), D.perm, PS.h_perm.size() * sizeof(int),
+                           cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        CK(cudaGetLastError());
+        if ((rc = status_message(rb, "factorization"))) return rc;
+        std::copy(rb + 4, rb + 4 + PS.h_rank.size(), PS.h_rank.begin());
+        std::copy(rb + 4 + PS.h_rank.size(), rb + 4 + PS.h_rank.size() + PS.h_perm.size(),
+                  PS.h_perm.begin());
+      }
       H->flops += dflops + sflops;
       for (int gi : ph.pre_group) {
         const double g = P.group_size[gi];
@@ -740,7 +773,9 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
         ++H->units;
       }
     }
-    if ((rc = check_status(H, lvl == G.L ? "root factorization" : "cell elimination"))) return rc;
+    // a level with a phase was checked by the phase's readback (after its last launch)
+    if (P.phases.empty() && (rc = check_status(H, lvl == G.L ? "root factorization" : "cell elimination")))
+      return rc;
     if (trace)
       std::fprintf(stderr, "[rhif] level %d: cells %d groups %d active %zu max_n %d max_nB %d max_group %d plan %.2f ms upload %.2f ms gpu+sync %.2f ms\n",
                    lvl, P.ncell(), P.ngroup(), P.bucket.size(), P.max_n, P.max_nB, P.max_group,

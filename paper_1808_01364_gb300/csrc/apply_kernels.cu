@@ -311,10 +311,10 @@ k_apply_leaf_up(LevelDev Lv, double* x, int64_t ldx, int nrhs, double* ubuf, int
   const int32_t* gI = Lv.gids + Lv.gid_off[c];
   const int* ci = Lv.cpl_i + Lv.b_off[c];
   const T* ca = (const T*)Lv.cpl_a + Lv.b_off[c];
-  for (int r = 0; r < nrhs; ++r) {
+  for (int r = blockIdx.y; r < nrhs; r += gridDim.y) {   // right-hand sides over grid.y
     double* xr = x + r * ldx;
     warp_gather(xr, gI, nI, y);
-    if (STAGE && r == 0 && !staged_ok(bar, Lv.status, 0, kKindCell, c)) return;
+    if (STAGE && r == (int)blockIdx.y && !staged_ok(bar, Lv.status, 0, kKindCell, c)) return;
     __syncwarp();
     band_fwd(band, nI, w, y);
     for (int i = lane; i < nI; i += 32) {
@@ -348,7 +348,7 @@ k_apply_leaf_down(LevelDev Lv, double* x, int64_t ldx, int nrhs, int per_warp_by
   const int* ci = Lv.cpl_i + Lv.b_off[c];
   const T* ca = (const T*)Lv.cpl_a + Lv.b_off[c];
   T* xb = v + Lv.max_nI + 1;   // boundary values
-  for (int r = 0; r < nrhs; ++r) {
+  for (int r = blockIdx.y; r < nrhs; r += gridDim.y) {   // right-hand sides over grid.y
     double* xr = x + r * ldx;
     for (int i = lane; i < nI; i += 32) v[i] = T(0);
     warp_gather(xr, gI, nI, t);
@@ -358,7 +358,7 @@ k_apply_leaf_down(LevelDev Lv, double* x, int64_t ldx, int nrhs, int per_warp_by
     if (lane == 0)   // A_BI^T x_B in a fixed order (several boundary DOFs may face one interior DOF)
       for (int b = 0; b < nB; ++b)
         if (ci[b] >= 0) v[ci[b]] += xb[b];
-    if (STAGE && r == 0 && !staged_ok(bar, Lv.status, 0, kKindCell, c)) return;
+    if (STAGE && r == (int)blockIdx.y && !staged_ok(bar, Lv.status, 0, kKindCell, c)) return;
     __syncwarp();
     band_fwd(band, nI, w, v);
     for (int i = lane; i < nI; i += 32) t[i] -= v[i];
@@ -399,10 +399,10 @@ k_apply_cell_up(LevelDev Lv, double* x, int64_t ldx, int nrhs, double* ubuf, int
   if (stage) F = front_stage(F, n, nI, (T*)(smraw + round16(2 * (Lv.max_nI + 1) * sizeof(T))), &bar);
   const int32_t* gI = Lv.gids + Lv.gid_off[c];
   __syncthreads();
-  for (int r = 0; r < nrhs; ++r) {
+  for (int r = blockIdx.y; r < nrhs; r += gridDim.y) {   // right-hand sides over grid.y
     double* xr = x + r * ldx;
     for (int i = threadIdx.x; i < nI; i += blockDim.x) x_in[i] = T(xr[gI[i]]);
-    if (stage && r == 0 && !staged_ok(&bar, Lv.status, Lv.level, kKindCell, c)) return;
+    if (stage && r == (int)blockIdx.y && !staged_ok(&bar, Lv.status, Lv.level, kKindCell, c)) return;
     __syncthreads();
     // y = L^{-1} x_I: the front's L block holds L^{-1} (one row per thread)
     for (int i = threadIdx.x; i < nI; i += blockDim.x) {
@@ -440,10 +440,10 @@ k_apply_cell_down(LevelDev Lv, double* x, int64_t ldx, int nrhs, int stage) {
   const int32_t* gB = gI + nI;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   __syncthreads();
-  for (int r = 0; r < nrhs; ++r) {
+  for (int r = blockIdx.y; r < nrhs; r += gridDim.y) {   // right-hand sides over grid.y
     double* xr = x + r * ldx;
     for (int b = threadIdx.x; b < nB; b += blockDim.x) xb[b] = T(xr[gB[b]]);
-    if (stage && r == 0 && !staged_ok(&bar, Lv.status, Lv.level, kKindCell, c)) return;
+    if (stage && r == (int)blockIdx.y && !staged_ok(&bar, Lv.status, Lv.level, kKindCell, c)) return;
     __syncthreads();
     for (int k = warp; k < nI; k += nwarps) {
       T s = T(0);
@@ -792,7 +792,7 @@ k_apply_group_up(LevelDev Lv, PhaseDev Ph, int gather, double* x, int64_t ldx, i
   else
     group_global(Ph, pi, u, n, &Lg, &Fu, &Tm);
   __syncthreads();
-  for (int r = 0; r < nrhs; ++r) {
+  for (int r = blockIdx.y; r < nrhs; r += gridDim.y) {   // right-hand sides over grid.y
     double* xr = x + r * ldx;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       double v = xr[gid[i]];
@@ -802,7 +802,7 @@ k_apply_group_up(LevelDev Lv, PhaseDev Ph, int gather, double* x, int64_t ldx, i
       }
       xg[i] = T(v);
     }
-    if (stage && r == 0 && !staged_ok(&bar, Lv.status, Lv.level, kKindGroup, g)) return;
+    if (stage && r == (int)blockIdx.y && !staged_ok(&bar, Lv.status, Lv.level, kKindGroup, g)) return;
     __syncthreads();
     if (Lg) {   // C^T: x_g = L_g^{-1} x_g
       cta_trmv_lower(Lg, n, n, xg, tmp);
@@ -835,10 +835,10 @@ k_apply_group_down(LevelDev Lv, PhaseDev Ph, double* x, int64_t ldx, int nrhs, i
   else
     group_global(Ph, pi, u, n, &Lg, &Fu, &Tm);
   __syncthreads();
-  for (int r = 0; r < nrhs; ++r) {
+  for (int r = blockIdx.y; r < nrhs; r += gridDim.y) {   // right-hand sides over grid.y
     double* xr = x + r * ldx;
     for (int i = threadIdx.x; i < n; i += blockDim.x) xg[i] = T(xr[gid[i]]);
-    if (stage && r == 0 && !staged_ok(&bar, Lv.status, Lv.level, kKindGroup, g)) return;
+    if (stage && r == (int)blockIdx.y && !staged_ok(&bar, Lv.status, Lv.level, kKindGroup, g)) return;
     __syncthreads();
     if (Fu) unit_down(Ph, u, n, xg, tmp, Fu, Tm);
     if (Lg) {   // C: x_g = L_g^{-T} x_g
@@ -886,7 +886,7 @@ k_apply_group_up_warp(LevelDev Lv, PhaseDev Ph, int gather, double* x, int64_t l
   const int p_sk = (u >= 0 && lane < k) ? perm[lane] : 0;
   const int p_rd = (u >= 0 && lane < r) ? perm[k + lane] : 0;
   const int my_idx = (u >= 0 && lane < n) ? invp[lane] : 0;
-  for (int rr = 0; rr < nrhs; ++rr) {
+  for (int rr = blockIdx.y; rr < nrhs; rr += gridDim.y) {   // right-hand sides over grid.y
     double* xr = x + rr * ldx;
     T xv = T(0);
     if (lane < n) {
@@ -896,7 +896,7 @@ k_apply_group_up_warp(LevelDev Lv, PhaseDev Ph, int gather, double* x, int64_t l
           v -= ubuf[rr * ldu + Lv.b_off[Lv.group_cell[q]] + Lv.group_pos[q] + lane];
       xv = T(v);
     }
-    if (staged && rr == 0 && !staged_ok(bar, Lv.status, Lv.level, kKindGroup, g)) return;
+    if (staged && rr == (int)blockIdx.y && !staged_ok(bar, Lv.status, Lv.level, kKindGroup, g)) return;
     if (Lg) {   // C^T: x_g = L_g^{-1} x_g (the factor keeps L_g^{-1})
       T y = T(0);
       for (int c = 0; c < n; ++c) {
@@ -957,10 +957,10 @@ k_apply_group_down_warp(LevelDev Lv, PhaseDev Ph, double* x, int64_t ldx, int nr
   const int p_sk = (u >= 0 && lane < k) ? perm[lane] : 0;
   const int p_rd = (u >= 0 && lane < r) ? perm[k + lane] : 0;
   const int my_idx = (u >= 0 && lane < n) ? invp[lane] : 0;
-  for (int rr = 0; rr < nrhs; ++rr) {
+  for (int rr = blockIdx.y; rr < nrhs; rr += gridDim.y) {   // right-hand sides over grid.y
     double* xr = x + rr * ldx;
     T xv = lane < n ? T(xr[gid[lane]]) : T(0);
-    if (staged && rr == 0 && !staged_ok(bar, Lv.status, Lv.level, kKindGroup, g)) return;
+    if (staged && rr == (int)blockIdx.y && !staged_ok(bar, Lv.status, Lv.level, kKindGroup, g)) return;
     if (u >= 0) {   // K: x_rd = L^{-T}(x_rd - W^T x_sk) ; x_sk -= T x_rd
       T xs = __shfl_sync(0xffffffffu, xv, p_sk);
       T xd = __shfl_sync(0xffffffffu, xv, p_rd);
@@ -996,6 +996,10 @@ k_apply_group_down_warp(LevelDev Lv, PhaseDev Ph, double* x, int64_t ldx, int nr
   }
 }
 
+// Right-hand sides run as separate CTAs (grid.y): the per-RHS work of the
+// sweeps is independent, and the factor blocks they share come from L2.
+static inline unsigned rhs_grid(int nrhs) { return (unsigned)std::min(std::max(nrhs, 1), 65535); }
+
 template <typename T>
 void launch_apply_cell_up(const LevelDev& Lv, double* x, int64_t ldx, int nrhs, double* ubuf,
                           int64_t ldu, cudaStream_t s) {
@@ -1005,15 +1009,15 @@ void launch_apply_cell_up(const LevelDev& Lv, double* x, int64_t ldx, int nrhs, 
     const size_t per = leaf_warp_smem<T>(Lv);
     const unsigned grid = (Lv.ncell + wpc - 1) / wpc;
     if (leaf_staged<T>(Lv))
-      k_apply_leaf_up<T, true><<<grid, 32 * wpc, wpc * per, s>>>(Lv, x, ldx, nrhs, ubuf, ldu, (int)per);
+      k_apply_leaf_up<T, true><<<dim3(grid, rhs_grid(nrhs)), 32 * wpc, wpc * per, s>>>(Lv, x, ldx, nrhs, ubuf, ldu, (int)per);
     else
-      k_apply_leaf_up<T, false><<<grid, 32 * wpc, wpc * per, s>>>(Lv, x, ldx, nrhs, ubuf, ldu, (int)per);
+      k_apply_leaf_up<T, false><<<dim3(grid, rhs_grid(nrhs)), 32 * wpc, wpc * per, s>>>(Lv, x, ldx, nrhs, ubuf, ldu, (int)per);
     return;
   }
   const size_t base = round16(2 * (Lv.max_nI + 1) * sizeof(T));
   const size_t blk = round16((size_t)Lv.max_n * Lv.max_nI * sizeof(T));
   const int stage = blk <= kStageBudget;
-  k_apply_cell_up<T><<<Lv.ncell, kApplyThreads, base + (stage ? blk : 0), s>>>(Lv, x, ldx, nrhs, ubuf,
+  k_apply_cell_up<T><<<dim3(Lv.ncell, rhs_grid(nrhs)), kApplyThreads, base + (stage ? blk : 0), s>>>(Lv, x, ldx, nrhs, ubuf,
                                                                             ldu, stage);
 }
 
@@ -1025,15 +1029,15 @@ void launch_apply_cell_down(const LevelDev& Lv, double* x, int64_t ldx, int nrhs
     const size_t per = leaf_warp_smem<T>(Lv);
     const unsigned grid = (Lv.ncell + wpc - 1) / wpc;
     if (leaf_staged<T>(Lv))
-      k_apply_leaf_down<T, true><<<grid, 32 * wpc, wpc * per, s>>>(Lv, x, ldx, nrhs, (int)per);
+      k_apply_leaf_down<T, true><<<dim3(grid, rhs_grid(nrhs)), 32 * wpc, wpc * per, s>>>(Lv, x, ldx, nrhs, (int)per);
     else
-      k_apply_leaf_down<T, false><<<grid, 32 * wpc, wpc * per, s>>>(Lv, x, ldx, nrhs, (int)per);
+      k_apply_leaf_down<T, false><<<dim3(grid, rhs_grid(nrhs)), 32 * wpc, wpc * per, s>>>(Lv, x, ldx, nrhs, (int)per);
     return;
   }
   const size_t base = round16((2 * Lv.max_nI + Lv.max_nB + 1) * sizeof(T));
   const size_t blk = round16((size_t)Lv.max_n * Lv.max_nI * sizeof(T));
   const int stage = blk <= kStageBudget;
-  k_apply_cell_down<T><<<Lv.ncell, kApplyThreads, base + (stage ? blk : 0), s>>>(Lv, x, ldx, nrhs,
+  k_apply_cell_down<T><<<dim3(Lv.ncell, rhs_grid(nrhs)), kApplyThreads, base + (stage ? blk : 0), s>>>(Lv, x, ldx, nrhs,
                                                                               stage);
 }
 
@@ -1081,14 +1085,14 @@ void launch_apply_group_up(const LevelDev& Lv, const PhaseDev& Ph, int gather, d
   if (Lv.max_group <= 32) {
     const size_t per = group_warp_smem<T>(Lv.max_group);
     const unsigned grid = (Lv.ngroup + kGroupWarps - 1) / kGroupWarps;
-    k_apply_group_up_warp<T><<<grid, 32 * kGroupWarps, kGroupWarps * per, s>>>(
+    k_apply_group_up_warp<T><<<dim3(grid, rhs_grid(nrhs)), 32 * kGroupWarps, kGroupWarps * per, s>>>(
         Lv, Ph, gather, x, ldx, nrhs, ubuf, ldu, (int)per);
     return;
   }
   const size_t base = round16(2 * (Lv.max_group + 1) * sizeof(T));
   const size_t blk = group_block_bytes<T>(Lv.max_group);
   const int stage = blk <= kStageBudget;
-  k_apply_group_up<T><<<Lv.ngroup, kGroupThreads, base + (stage ? blk : 0), s>>>(
+  k_apply_group_up<T><<<dim3(Lv.ngroup, rhs_grid(nrhs)), kGroupThreads, base + (stage ? blk : 0), s>>>(
       Lv, Ph, gather, x, ldx, nrhs, ubuf, ldu, stage);
 }
 
@@ -1099,14 +1103,14 @@ void launch_apply_group_down(const LevelDev& Lv, const PhaseDev& Ph, double* x, 
   if (Lv.max_group <= 32) {
     const size_t per = group_warp_smem<T>(Lv.max_group);
     const unsigned grid = (Lv.ngroup + kGroupWarps - 1) / kGroupWarps;
-    k_apply_group_down_warp<T><<<grid, 32 * kGroupWarps, kGroupWarps * per, s>>>(
+    k_apply_group_down_warp<T><<<dim3(grid, rhs_grid(nrhs)), 32 * kGroupWarps, kGroupWarps * per, s>>>(
         Lv, Ph, x, ldx, nrhs, (int)per);
     return;
   }
   const size_t base = round16(2 * (Lv.max_group + 1) * sizeof(T));
   const size_t blk = group_block_bytes<T>(Lv.max_group);
   const int stage = blk <= kStageBudget;
-  k_apply_group_down<T><<<Lv.ngroup, kGroupThreads, base + (stage ? blk : 0), s>>>(
+  k_apply_group_down<T><<<dim3(Lv.ngroup, rhs_grid(nrhs)), kGroupThreads, base + (stage ? blk : 0), s>>>(
       Lv, Ph, x, ldx, nrhs, stage);
 }
 

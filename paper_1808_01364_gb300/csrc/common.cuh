@@ -311,12 +311,24 @@ __device__ void cta_trinv_block(const T* L, int64_t ldl, int n, T* X, int64_t ld
       Rb[i * (kTile + 1) + q] = q <= i ? L[(I0 + i) + (int64_t)(I0 + q) * ldl] : T(0);
     }
     __syncthreads();
-    for (int j = tid; j < nc; j += blockDim.x) {
-      T* col = X + (int64_t)(J0 + j) * ldx + I0;
+    // per-column forward solve, four threads per column: the sum over q < i
+    // is split four ways and combined with two shuffles; every lane of a warp
+    // takes part in every step (lanes past the block only skip the write)
+    const int grp = tid >> 2, sub = tid & 3;
+    for (int j0 = 0; j0 < nc; j0 += (int)blockDim.x / 4) {
+      const int j = j0 + grp;
+      const bool act = j < nc;
+      T* col = X + (int64_t)(J0 + (act ? j : 0)) * ldx + I0;
       for (int i = 0; i < nr; ++i) {
-        T v = col[i];
-        for (int q = 0; q < i; ++q) v -= Rb[i * (kTile + 1) + q] * col[q];
-        col[i] = v / Rb[i * (kTile + 1) + i];
+        T part = T(0);
+        if (act)
+          for (int q = sub; q < i; q += 4) part += Rb[i * (kTile + 1) + q] * col[q];
+        part += __shfl_xor_sync(0xffffffffu, part, 1);
+        part += __shfl_xor_sync(0xffffffffu, part, 2);
+        const T v = act ? (col[i] - part) / Rb[i * (kTile + 1) + i] : T(0);
+        __syncwarp();
+        if (act && sub == 0) col[i] = v;
+        __syncwarp();
       }
     }
     __syncthreads();

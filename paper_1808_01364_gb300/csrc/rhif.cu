@@ -1117,25 +1117,28 @@ int rhif_pcg(const rhif_handle* Fc, int nrhs, const double* f, int64_t ldf, doub
   double* part = q + N * nrhs;
   double* sc = part + (int64_t)nblk * nrhs;
   double* sc2 = sc + 8 * nrhs;
+  // algorithmic bytes of the vector launches (FP64 vectors read / written once)
+  auto vb = [&](double per_entry) { return per_entry * double(N) * nrhs; };
+  const double rb = 8.0 * nblk * nrhs;
   CK(cudaMemsetAsync(sc, 0, 16 * nrhs * sizeof(double), s));
   for (int c = 0; c < nrhs; ++c) CK(cudaMemsetAsync(u + c * ldu, 0, N * sizeof(double), s));
-  { Launch t_(kCatVector, s, 0.0, 0.0); launch_copy_cols(N, nrhs, f, ldf, r, ld, s); }
-  { Launch t_(kCatVector, s, 0.0, 0.0); launch_dot_partial(N, f, ldf, f, ldf, nrhs, part, s); }
-  { Launch t_(kCatVector, s, 0.0, 0.0); launch_reduce(part, nblk, nrhs, sc, 0, rtol, s); }
-  { Launch t_(kCatVector, s, 0.0, 0.0); launch_copy_cols(N, nrhs, r, ld, z, ld, s); }
+  { Launch t_(kCatVector, s, 0.0, vb(16)); launch_copy_cols(N, nrhs, f, ldf, r, ld, s); }
+  { Launch t_(kCatVector, s, 0.0, vb(8)); launch_dot_partial(N, f, ldf, f, ldf, nrhs, part, s); }
+  { Launch t_(kCatVector, s, 0.0, rb); launch_reduce(part, nblk, nrhs, sc, 0, rtol, s); }
+  { Launch t_(kCatVector, s, 0.0, vb(16)); launch_copy_cols(N, nrhs, r, ld, z, ld, s); }
   if ((rc = apply_dispatch(F, z, ld, nrhs, s))) return rc;
-  { Launch t_(kCatVector, s, 0.0, 0.0); launch_dot_partial(N, r, ld, z, ld, nrhs, part, s); }
-  { Launch t_(kCatVector, s, 0.0, 0.0); launch_reduce(part, nblk, nrhs, sc, 1, rtol, s); }
-  { Launch t_(kCatVector, s, 0.0, 0.0); launch_update_p(N, nrhs, sc, z, ld, p, ld, 1, s); }
+  { Launch t_(kCatVector, s, 0.0, vb(16)); launch_dot_partial(N, r, ld, z, ld, nrhs, part, s); }
+  { Launch t_(kCatVector, s, 0.0, rb); launch_reduce(part, nblk, nrhs, sc, 1, rtol, s); }
+  { Launch t_(kCatVector, s, 0.0, vb(24)); launch_update_p(N, nrhs, sc, z, ld, p, ld, 1, s); }
   std::vector<double> hsc(8 * nrhs);
   std::vector<int> it(nrhs, maxit);
   std::vector<char> was_done(nrhs, 0);
   int all_done = 0;
   for (int k = 1; k <= maxit; ++k) {
     { Launch t_(kCatSpmv, s, spmv_flops * nrhs, spmv_bytes * nrhs); launch_spmv(F->gd, F->diag, F->off, p, ld, q, ld, nrhs, part, s); }
-    { Launch t_(kCatVector, s, 0.0, 0.0); launch_reduce(part, nblk, nrhs, sc, 2, rtol, s); }
-    { Launch t_(kCatVector, s, 0.0, 0.0); launch_update_xr(N, nrhs, sc, u, ldu, r, ld, p, ld, q, ld, part, s); }
-    { Launch t_(kCatVector, s, 0.0, 0.0); launch_reduce(part, nblk, nrhs, sc, 3, rtol, s); }
+    { Launch t_(kCatVector, s, 0.0, rb); launch_reduce(part, nblk, nrhs, sc, 2, rtol, s); }
+    { Launch t_(kCatVector, s, 0.0, vb(48)); launch_update_xr(N, nrhs, sc, u, ldu, r, ld, p, ld, q, ld, part, s); }
+    { Launch t_(kCatVector, s, 0.0, rb); launch_reduce(part, nblk, nrhs, sc, 3, rtol, s); }
     CK(cudaMemcpyAsync(hsc.data(), sc, 8 * nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     int nd = 0;
@@ -1146,11 +1149,11 @@ int rhif_pcg(const rhif_handle* Fc, int nrhs, const double* f, int64_t ldf, doub
       }
     }
     if (nd == nrhs) { all_done = 1; break; }
-    { Launch t_(kCatVector, s, 0.0, 0.0); launch_copy_cols(N, nrhs, r, ld, z, ld, s); }
+    { Launch t_(kCatVector, s, 0.0, vb(16)); launch_copy_cols(N, nrhs, r, ld, z, ld, s); }
     if ((rc = apply_dispatch(F, z, ld, nrhs, s))) return rc;
-    { Launch t_(kCatVector, s, 0.0, 0.0); launch_dot_partial(N, r, ld, z, ld, nrhs, part, s); }
-    { Launch t_(kCatVector, s, 0.0, 0.0); launch_reduce(part, nblk, nrhs, sc, 4, rtol, s); }
-    { Launch t_(kCatVector, s, 0.0, 0.0); launch_update_p(N, nrhs, sc, z, ld, p, ld, 0, s); }
+    { Launch t_(kCatVector, s, 0.0, vb(16)); launch_dot_partial(N, r, ld, z, ld, nrhs, part, s); }
+    { Launch t_(kCatVector, s, 0.0, rb); launch_reduce(part, nblk, nrhs, sc, 4, rtol, s); }
+    { Launch t_(kCatVector, s, 0.0, vb(24)); launch_update_p(N, nrhs, sc, z, ld, p, ld, 0, s); }
   }
   if (maxit == 0) {
     CK(cudaMemcpyAsync(hsc.data(), sc, 8 * nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -1158,9 +1161,9 @@ int rhif_pcg(const rhif_handle* Fc, int nrhs, const double* f, int64_t ldf, doub
   }
   // true residual
   { Launch t_(kCatSpmv, s, spmv_flops * nrhs, spmv_bytes * nrhs); launch_spmv(F->gd, F->diag, F->off, u, ldu, q, ld, nrhs, nullptr, s); }
-  { Launch t_(kCatVector, s, 0.0, 0.0); launch_sub(N, nrhs, f, ldf, q, ld, r, ld, s); }
-  { Launch t_(kCatVector, s, 0.0, 0.0); launch_dot_partial(N, r, ld, r, ld, nrhs, part, s); }
-  { Launch t_(kCatVector, s, 0.0, 0.0); launch_reduce(part, nblk, nrhs, sc2, 1, rtol, s); }
+  { Launch t_(kCatVector, s, 0.0, vb(24)); launch_sub(N, nrhs, f, ldf, q, ld, r, ld, s); }
+  { Launch t_(kCatVector, s, 0.0, vb(8)); launch_dot_partial(N, r, ld, r, ld, nrhs, part, s); }
+  { Launch t_(kCatVector, s, 0.0, rb); launch_reduce(part, nblk, nrhs, sc2, 1, rtol, s); }
   std::vector<double> h2(8 * nrhs);
   CK(cudaMemcpyAsync(h2.data(), sc2, 8 * nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));

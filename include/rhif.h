@@ -39,7 +39,8 @@ enum {
   RHIF_ERR_NOT_CONVERGED = -3,  /* PCG hit maxit before rtol */
   RHIF_ERR_TIMEOUT = -4,        /* a bounded device wait gave up */
   RHIF_ERR_OOM = -5,            /* device allocation failed */
-  RHIF_ERR_CUDA = -6            /* any other CUDA runtime error */
+  RHIF_ERR_CUDA = -6,           /* any other CUDA runtime error */
+  RHIF_ERR_CHECK = -7           /* a self-check found a violated invariant (detail says which) */
 };
 
 enum { RHIF_FP64 = 0, RHIF_MIXED_FP32 = 1 };  /* precision of the stored factor */
@@ -262,6 +263,21 @@ void rhif_free(rhif_handle* F);
 
 const char* rhif_error_string(int code);
 const char* rhif_last_error_detail(void);
+
+/* Host-only self-check of the level planner (Sec. 3.1, Fig. 3): builds the
+ * plan of every level of a dim-D grid ns[0..dim-1] (leaf size `leaf`) with
+ * seeded synthetic survivor flags (each DOF of a skeletonized group kept with
+ * probability `keep`, splitmix64 stream from `seed`; edges too when
+ * edge_skel_3d) and checks it against the definitions, recomputed from DOF
+ * coordinates: bucket order by (code, index), cell interiors and segments,
+ * the group-to-cell lists, every extend-add map entry (a surviving child
+ * frame DOF lands on the same DOF of the parent front, a dropped one on -1),
+ * and an identical rebuild from recycled storage.  No device work.  Writes
+ * the number of levels checked to *levels_checked (may be null).  Returns
+ * RHIF_OK, RHIF_ERR_BAD_ARG, or RHIF_ERR_CHECK with the first violation in
+ * rhif_last_error_detail(). */
+int rhif_plan_selfcheck(int dim, const int* ns, int leaf, double keep, uint64_t seed,
+                        int edge_skel_3d, int64_t* levels_checked);
 
 #ifdef __cplusplus
 }

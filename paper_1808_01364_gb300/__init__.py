@@ -110,6 +110,9 @@ EXPORTS = {
                                         ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_double), ctypes.c_void_p,
                                         ctypes.c_int]),
+    "rhif_plan_selfcheck": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                           ctypes.c_double, ctypes.c_uint64, ctypes.c_int,
+                                           ctypes.POINTER(ctypes.c_int64)]),
     "rhif_free": (None, [ctypes.c_void_p]),
     "rhif_set_timing": (ctypes.c_int, [ctypes.c_int]),
     "rhif_reset_kernel_stats": (ctypes.c_int, []),
@@ -325,6 +328,17 @@ def rhif_tc_gemm_check(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor, stream
     _check(_lib.rhif_tc_gemm_check(int(M), int(N), int(K), _colptr(A), lda, _colptr(B), ldb,
                                    _colptr(C), max(int(C.stride(1)), M), _stream(stream)))
     return C
+
+
+def rhif_plan_selfcheck(ns, leaf: int, keep: float = 0.5, seed: int = 1, edge_skel_3d=False) -> int:
+    """Host-only check of the level plans of a grid (no GPU needed); returns
+    the number of levels checked, raises RhifError on a violated invariant."""
+    load()
+    n = (ctypes.c_int * 3)(*[int(v) for v in ns], *([1] * (3 - len(ns))))
+    levels = ctypes.c_int64(0)
+    _check(_lib.rhif_plan_selfcheck(len(ns), n, int(leaf), float(keep), int(seed),
+                                    int(bool(edge_skel_3d)), ctypes.byref(levels)))
+    return int(levels.value)
 
 
 def rhif_grad_logcoef(ns, a_pix: torch.Tensor, u: torch.Tensor, lam: torch.Tensor, stream=None):

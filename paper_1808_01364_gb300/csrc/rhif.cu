@@ -29,6 +29,8 @@ namespace rhif {
 
 thread_local std::string g_detail;
 
+void set_error_detail(const std::string& msg) { g_detail = msg; }
+
 static int fail(int code, const std::string& msg) {
   g_detail = msg;
   return code;
@@ -1385,6 +1387,7 @@ const char* rhif_error_string(int code) {
     case RHIF_ERR_TIMEOUT: return "RHIF_ERR_TIMEOUT";
     case RHIF_ERR_OOM: return "RHIF_ERR_OOM";
     case RHIF_ERR_CUDA: return "RHIF_ERR_CUDA";
+    case RHIF_ERR_CHECK: return "RHIF_ERR_CHECK";
     default: return "unknown";
   }
 }

@@ -97,7 +97,9 @@ inline int64_t pad4(int64_t n) { return (n + 3) & ~int64_t(3); }
 
 void LevelPlan::clear() {
   level = width = code_base = 0;
-  bucket.clear();
+  // bucket and ea_map keep their sizes: build_level rewrites every entry, so a
+  // recycled plan of the same size is not zero-filled first
+  bucket.resize(bucket.size());
   cell_code.clear();
   cell_start.clear();
   nI.clear();
@@ -129,7 +131,6 @@ void LevelPlan::clear() {
   ea_off.clear();
   ea_child.clear();
   ea_map_off.clear();
-  ea_map.clear();
   phases.clear();
 }
 
@@ -282,7 +283,7 @@ LevelPlan build_level(const Geometry& G, int level, const std::vector<uint8_t>& 
       for (int g = 0; g < pg; ++g) cg[fillp[gcode[g]]++] = g;
     }
     P.bucket.resize(cstart[C.ncode]);
-    newpos.assign(gpos_off[pg], -1);
+    newpos.resize(gpos_off[pg]);
     std::vector<int>& src = X.src;
     src.resize(P.bucket.size());
     // ascending DOF index within every code; newpos follows the moves
@@ -299,6 +300,8 @@ LevelPlan build_level(const Geometry& G, int level, const std::vector<uint8_t>& 
               P.bucket[q] = gb[o];
               src[q] = gpos_off[g] + o;
               ++q;
+            } else {
+              newpos[gpos_off[g] + o] = -1;
             }
         }
         const int64_t a = cstart[c], b = cstart[c + 1];
@@ -504,7 +507,7 @@ LevelPlan build_level(const Geometry& G, int level, const std::vector<uint8_t>& 
           }
       P.ea_off.push_back((int)P.ea_child.size());
     }
-    P.ea_map.assign(map_total, -1);
+    P.ea_map.resize(map_total);   // every slot is written below
     pool.parallel_for(ncell, 128, [&](int64_t c0, int64_t c1) {
     for (int64_t ci = c0; ci < c1; ++ci) {
       const int nI = P.nI[ci];
@@ -527,9 +530,12 @@ LevelPlan build_level(const Geometry& G, int level, const std::vector<uint8_t>& 
                     found = true;
                   }
               }
-              if (!found) continue;   // no DOF of the segment reaches this front (stays -1)
               const int* np = newpos.data() + gpos_off[g];
               int* out = P.ea_map.data() + base + prev->seg_pos[s];
+              if (!found) {   // no DOF of the segment reaches this front
+                for (int o = 0; o < prev->group_size[g]; ++o) out[o] = -1;
+                continue;
+              }
               for (int o = 0; o < prev->group_size[g]; ++o)
                 out[o] = np[o] >= 0 ? (int)(np[o] + shift) : -1;
             }

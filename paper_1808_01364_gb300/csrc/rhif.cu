@@ -174,12 +174,22 @@ static cudaEvent_t pooled_event() {
   return e;
 }
 
+// While this thread captures a CUDA graph, launches are counted here instead
+// (nothing runs during a capture; the graph's replays are credited instead).
+static thread_local KStat* t_capture_stats = nullptr;
+
 // Counts (and, with timing on, brackets with events) the launches issued while alive.
 struct Launch {
   int cat;
   cudaStream_t s;
   cudaEvent_t a = nullptr, b = nullptr;
   Launch(int cat_, cudaStream_t s_, double flops, double bytes, int count = 1) : cat(cat_), s(s_) {
+    if (t_capture_stats) {
+      t_capture_stats[cat].launches += count;
+      t_capture_stats[cat].flops += flops;
+      t_capture_stats[cat].bytes += bytes;
+      return;
+    }
     std::lock_guard<std::mutex> lk(g_kmu);
     g_kstat[cat].launches += count;
     g_kstat[cat].flops += flops;
@@ -206,11 +216,20 @@ constexpr int kBigFrontCells = 304;
 constexpr int kNumSMsHint = 152;   // CTAs wanted per cluster launch (one per SM)
 
 static void add_launches(int cat, int64_t n) {
+  if (t_capture_stats) {
+    t_capture_stats[cat].launches += n;
+    return;
+  }
   std::lock_guard<std::mutex> lk(g_kmu);
   g_kstat[cat].launches += n;
 }
 
 static void add_work(int cat, double flops, double bytes) {
+  if (t_capture_stats) {
+    t_capture_stats[cat].flops += flops;
+    t_capture_stats[cat].bytes += bytes;
+    return;
+  }
   std::lock_guard<std::mutex> lk(g_kmu);
   g_kstat[cat].flops += flops;
   g_kstat[cat].bytes += bytes;
@@ -260,6 +279,17 @@ struct rhif_handle {
   int64_t work_elems = 0;
   double flops = 0.0, apply_bytes = 0.0, factor_ms = 0.0;
   int units = 0;
+  // One F^{-1} application (the sweeps of apply_impl) as a CUDA graph, captured
+  // for one (output, leading dimension, nrhs, scratch) and replayed by PCG;
+  // the launch counts of one application are credited at every replay.
+  cudaGraphExec_t apply_graph = nullptr;
+  cudaStream_t capture_stream = nullptr;
+  double* ag_y = nullptr;
+  double* ag_ubuf = nullptr;
+  int64_t ag_ldy = 0;
+  int ag_nrhs = 0;
+  int64_t ag_launches[rhif::kNumCat] = {};
+  double ag_flops[rhif::kNumCat] = {}, ag_bytes[rhif::kNumCat] = {};
 };
 
 namespace rhif {
@@ -827,14 +857,6 @@ template <typename T>
 static int apply_impl(const rhif_handle* Hc, double* y, int64_t ldy, int nrhs, cudaStream_t s) {
   rhif_handle* H = const_cast<rhif_handle*>(Hc);
   const int L = H->G.L;
-  const int64_t need = H->ub_len * nrhs;
-  if (need > H->ubuf_elems) {
-    if (H->ubuf) H->mem.release(H->ubuf);
-    H->ubuf = nullptr;
-    int rc = H->mem.get((void**)&H->ubuf, need * sizeof(double));
-    if (rc) return rc;
-    H->ubuf_elems = need;
-  }
   const int64_t ldu = H->ub_len;
   double* tmp = H->ubuf + H->ui_base;
   auto cell_up = [&](LevelStore& S, int cat) {
@@ -873,9 +895,103 @@ static int apply_impl(const rhif_handle* Hc, double* y, int64_t ldy, int nrhs, c
   return RHIF_OK;
 }
 
-static int apply_dispatch(const rhif_handle* H, double* y, int64_t ldy, int nrhs, cudaStream_t s) {
+// Scratch of the sweeps (couplings sent up, interior part of big fronts).
+static int apply_prepare(rhif_handle* H, int nrhs) {
+  const int64_t need = H->ub_len * nrhs;
+  if (need > H->ubuf_elems) {
+    if (H->ubuf) H->mem.release(H->ubuf);
+    H->ubuf = nullptr;
+    int rc = H->mem.get((void**)&H->ubuf, need * sizeof(double));
+    if (rc) return rc;
+    H->ubuf_elems = need;
+  }
+  return RHIF_OK;
+}
+
+static int apply_launch(const rhif_handle* H, double* y, int64_t ldy, int nrhs, cudaStream_t s) {
   return H->precision == RHIF_FP64 ? apply_impl<double>(H, y, ldy, nrhs, s)
                                    : apply_impl<float>(H, y, ldy, nrhs, s);
+}
+
+static void credit_graph(const rhif_handle* H) {
+  std::lock_guard<std::mutex> lk(g_kmu);
+  for (int c = 0; c < kNumCat; ++c) {
+    g_kstat[c].launches += H->ag_launches[c];
+    g_kstat[c].flops += H->ag_flops[c];
+    g_kstat[c].bytes += H->ag_bytes[c];
+  }
+}
+
+// Captures the sweeps of one application on the handle's private stream (the
+// caller's stream may be the legacy default stream, which cannot be
+// captured) and instantiates them; nothing runs during the capture.  Returns
+// false when the capture cannot be made (the caller then launches directly).
+static bool capture_apply(rhif_handle* H, double* y, int64_t ldy, int nrhs) {
+  if (H->apply_graph) {
+    cudaGraphExecDestroy(H->apply_graph);
+    H->apply_graph = nullptr;
+  }
+  if (!H->capture_stream &&
+      cudaStreamCreateWithFlags(&H->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    H->capture_stream = nullptr;
+    return false;
+  }
+  KStat counts[kNumCat];
+  if (cudaStreamBeginCapture(H->capture_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return false;
+  t_capture_stats = counts;
+  const int rc = apply_launch(H, y, ldy, nrhs, H->capture_stream);
+  t_capture_stats = nullptr;
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(H->capture_stream, &graph);
+  for (int c = 0; c < kNumCat; ++c) {   // kept for the replays
+    H->ag_launches[c] = counts[c].launches;
+    H->ag_flops[c] = counts[c].flops;
+    H->ag_bytes[c] = counts[c].bytes;
+  }
+  cudaGetLastError();   // a failed capture leaves no sticky error
+  if (rc || e != cudaSuccess || !graph) {
+    if (graph) cudaGraphDestroy(graph);
+    return false;
+  }
+  cudaGraphExec_t exec = nullptr;
+  const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ei != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  H->apply_graph = exec;
+  H->ag_y = y;
+  H->ag_ldy = ldy;
+  H->ag_nrhs = nrhs;
+  H->ag_ubuf = H->ubuf;
+  return true;
+}
+
+// y <- F^{-1} y.  `replay`: the same output buffer is applied to repeatedly
+// (PCG), so the sweeps go through a captured CUDA graph unless per-launch
+// timing is on.
+static int apply_dispatch(const rhif_handle* Hc, double* y, int64_t ldy, int nrhs, cudaStream_t s,
+                          bool replay = false) {
+  rhif_handle* H = const_cast<rhif_handle*>(Hc);
+  int rc = apply_prepare(H, nrhs);
+  if (rc) return rc;
+  bool timing;
+  {
+    std::lock_guard<std::mutex> lk(g_kmu);
+    timing = g_timing;
+  }
+  if (replay && !timing) {
+    const bool match = H->apply_graph && H->ag_y == y && H->ag_ldy == ldy && H->ag_nrhs == nrhs &&
+                       H->ag_ubuf == H->ubuf;
+    if (match || capture_apply(H, y, ldy, nrhs)) {
+      CK(cudaGraphLaunch(H->apply_graph, s));
+      credit_graph(H);
+      return RHIF_OK;
+    }
+  }
+  return apply_launch(H, y, ldy, nrhs, s);
 }
 
 static int ensure_work(rhif_handle* H, int64_t elems) {
@@ -1128,7 +1244,7 @@ int rhif_pcg(const rhif_handle* Fc, int nrhs, const double* f, int64_t ldf, doub
   { Launch t_(kCatVector, s, 0.0, vb(8)); launch_dot_partial(N, f, ldf, f, ldf, nrhs, part, s); }
   { Launch t_(kCatVector, s, 0.0, rb); launch_reduce(part, nblk, nrhs, sc, 0, rtol, s); }
   { Launch t_(kCatVector, s, 0.0, vb(16)); launch_copy_cols(N, nrhs, r, ld, z, ld, s); }
-  if ((rc = apply_dispatch(F, z, ld, nrhs, s))) return rc;
+  if ((rc = apply_dispatch(F, z, ld, nrhs, s, true))) return rc;
   { Launch t_(kCatVector, s, 0.0, vb(16)); launch_dot_partial(N, r, ld, z, ld, nrhs, part, s); }
   { Launch t_(kCatVector, s, 0.0, rb); launch_reduce(part, nblk, nrhs, sc, 1, rtol, s); }
   { Launch t_(kCatVector, s, 0.0, vb(24)); launch_update_p(N, nrhs, sc, z, ld, p, ld, 1, s); }
@@ -1152,7 +1268,7 @@ int rhif_pcg(const rhif_handle* Fc, int nrhs, const double* f, int64_t ldf, doub
     }
     if (nd == nrhs) { all_done = 1; break; }
     { Launch t_(kCatVector, s, 0.0, vb(16)); launch_copy_cols(N, nrhs, r, ld, z, ld, s); }
-    if ((rc = apply_dispatch(F, z, ld, nrhs, s))) return rc;
+    if ((rc = apply_dispatch(F, z, ld, nrhs, s, true))) return rc;
     { Launch t_(kCatVector, s, 0.0, vb(16)); launch_dot_partial(N, r, ld, z, ld, nrhs, part, s); }
     { Launch t_(kCatVector, s, 0.0, rb); launch_reduce(part, nblk, nrhs, sc, 4, rtol, s); }
     { Launch t_(kCatVector, s, 0.0, vb(24)); launch_update_p(N, nrhs, sc, z, ld, p, ld, 0, s); }
@@ -1334,6 +1450,8 @@ void rhif_free(rhif_handle* F) {
   if (!F) return;
   F->mem.release_all();
   cudaStreamSynchronize(F->mem.s);
+  if (F->apply_graph) cudaGraphExecDestroy(F->apply_graph);
+  if (F->capture_stream) cudaStreamDestroy(F->capture_stream);
   for (auto& S : F->levels) recycle_plan(std::move(S.plan));
   delete F;
 }

@@ -567,8 +567,6 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
     launch_stencil_from_csr(H->gd, A->rowptr, A->col, A->val, A->nnz, H->diag, H->off, offb,
                             H->status, s);
   }
-  if ((rc = check_status(H, "CSR pattern check"))) return rc;
-  H->mem.release(offb);
 
   // per position of the current level's bucket: the DOF survives into the
   // next level (only separator-group positions are read by the planner)
@@ -580,16 +578,33 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
   auto ms_since = [](clk::time_point t) {
     return std::chrono::duration<double, std::milli>(clk::now() - t).count();
   };
+  // The plan of level 0 depends on the grid only: it is built and its tables
+  // queued for upload while the GPU converts the CSR matrix, before the
+  // pattern check waits for that conversion.
+  double t_plan = 0.0, t_up = 0.0;
+  {
+    auto t0 = clk::now();
+    H->levels[0].plan = build_level(G, 0, keep, nullptr, H->precondition, H->edge_skel);
+    t_plan = ms_since(t0);
+    auto t1 = clk::now();
+    if ((rc = upload_level(H, H->levels[0], elem))) return rc;
+    t_up = ms_since(t1);
+  }
+  if ((rc = check_status(H, "CSR pattern check"))) return rc;
+  H->mem.release(offb);
+
   for (int lvl = 0; lvl <= G.L; ++lvl) {
     LevelStore& S = H->levels[lvl];
     const LevelPlan* prev = lvl ? &H->levels[lvl - 1].plan : nullptr;
-    auto t0 = clk::now();
-    S.plan = build_level(G, lvl, keep, prev, H->precondition, H->edge_skel);
+    if (lvl) {
+      auto t0 = clk::now();
+      S.plan = build_level(G, lvl, keep, prev, H->precondition, H->edge_skel);
+      t_plan = ms_since(t0);
+      auto t1 = clk::now();
+      if ((rc = upload_level(H, S, elem))) return rc;
+      t_up = ms_since(t1);
+    }
     keep.assign(S.plan.bucket.size(), 1);
-    const double t_plan = ms_since(t0);
-    auto t1 = clk::now();
-    if ((rc = upload_level(H, S, elem))) return rc;
-    const double t_up = ms_since(t1);
     auto t2 = clk::now();
     const LevelPlan& P = S.plan;
     H->ub_len = std::max<int64_t>(H->ub_len, P.b_off.back());
@@ -614,10 +629,6 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
         Launch t(kCatLeafElim, s, lvl_flops, 0.0);
         launch_leaf_elim<T>(H->gd, S.dev, H->diag, H->off, H->status, s);
       }
-      {
-        Launch t(kCatBandInverse, s, 0.0, 2.0 * elem * P.band_total);
-        launch_band_block_inverse<T>(S.dev, s);
-      }
     } else {
       for (int c = 0; c < P.ncell(); ++c) {
         const double nI = P.nI[c], nB = P.nB[c];
@@ -633,6 +644,8 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
       }
       const bool many_cta = P.max_n >= H->big_front && P.ncell() <= kBigFrontCells;
       if (many_cta) {
+        S.big_apply = true;
+        H->ui_len = std::max<int64_t>(H->ui_len, P.gid_off.back());
         // few large fronts: panel / trailing-tile / Schur-tile launches over all fronts
         Launch t(kCatPartialChol, s, lvl_flops, double(P.front_total) * elem, 0);
         for (int p0 = 0; p0 < P.max_nI; p0 += 32) {
@@ -655,32 +668,6 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
       } else {
         Launch t(kCatPartialChol, s, lvl_flops, double(P.front_total) * elem);
         launch_partial_chol<T>(S.dev, H->status, s);
-      }
-      {
-        // L -> L^{-1} in place: every cell sweep of the application becomes a
-        // row-parallel product (no sequential triangular solve)
-        Launch t(kCatPartialChol, s, 0.0, 0.0, 0);
-        std::vector<int64_t>& xoff = H->xoff_host;   // outlives the async upload
-        xoff.assign(P.ncell(), 0);
-        int64_t xtot = 0;
-        for (int c = 0; c < P.ncell(); ++c) {
-          xoff[c] = xtot;
-          xtot += ((int64_t)P.nI[c] * P.nI[c] + 3) & ~int64_t(3);
-        }
-        void* X = nullptr;
-        void* xo = nullptr;
-        if ((rc = H->mem.get(&X, xtot * elem))) return rc;
-        if ((rc = H->mem.get(&xo, xoff.size() * sizeof(int64_t)))) return rc;
-        CK(cudaMemcpyAsync(xo, xoff.data(), xoff.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
-                           s));
-        launch_front_invert<T>(S.dev, (T*)X, (const int64_t*)xo, s);
-        add_launches(kCatPartialChol, 2);
-        H->mem.release(X);
-        H->mem.release(xo);
-        if (many_cta) {
-          S.big_apply = true;
-          H->ui_len = std::max<int64_t>(H->ui_len, P.gid_off.back());
-        }
       }
     }
     H->flops += lvl_flops;
@@ -759,13 +746,6 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
         Launch t(kCatSkel, s, 0.0, 0.0, nunit ? 1 : 0);
         if ((rc = skeletonize<T>(H, P, ph, S.dev, D, alive_d, s))) return rc;
       }
-      if (nunit) {   // the units' L_rr become L_rr^{-1} for the application
-        void* X = nullptr;
-        if ((rc = H->mem.get(&X, ph.units.rec_total * elem))) return rc;
-        Launch t(kCatSkel, s, 0.0, 0.0, 0);
-        add_launches(kCatSkel, launch_unit_invert<T>(S.dev, D, (T*)X, s));
-        H->mem.release(X);
-      }
       H->mem.release(M);
       D.Mbuf = nullptr;
       PhaseStore& PS = S.phases[ip];
@@ -808,6 +788,44 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
     // a level with a phase was checked by the phase's readback (after its last launch)
     if (P.phases.empty() && (rc = check_status(H, lvl == G.L ? "root factorization" : "cell elimination")))
       return rc;
+    // Explicit inverses that only the application reads (the diagonal blocks of
+    // the leaf bands, L^{-1} of every front, L_rr^{-1} of every unit): queued
+    // after the level's last readback, so they run while the host plans the
+    // next level.  Nothing later in the factorization reads these blocks.
+    if (lvl == 0) {
+      Launch t(kCatBandInverse, s, 0.0, 2.0 * elem * P.band_total);
+      launch_band_block_inverse<T>(S.dev, s);
+    } else {
+      // L -> L^{-1} in place: every cell sweep of the application becomes a
+      // row-parallel product (no sequential triangular solve)
+      Launch t(kCatPartialChol, s, 0.0, 0.0, 0);
+      std::vector<int64_t>& xoff = H->xoff_host;   // outlives the async upload
+      xoff.assign(P.ncell(), 0);
+      int64_t xtot = 0;
+      for (int c = 0; c < P.ncell(); ++c) {
+        xoff[c] = xtot;
+        xtot += ((int64_t)P.nI[c] * P.nI[c] + 3) & ~int64_t(3);
+      }
+      void* X = nullptr;
+      void* xo = nullptr;
+      if ((rc = H->mem.get(&X, xtot * elem))) return rc;
+      if ((rc = H->mem.get(&xo, xoff.size() * sizeof(int64_t)))) return rc;
+      CK(cudaMemcpyAsync(xo, xoff.data(), xoff.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
+                         s));
+      launch_front_invert<T>(S.dev, (T*)X, (const int64_t*)xo, s);
+      add_launches(kCatPartialChol, 2);
+      H->mem.release(X);
+      H->mem.release(xo);
+    }
+    for (size_t ip = 0; ip < P.phases.size(); ++ip) {
+      const PhasePlan& ph = P.phases[ip];
+      if (ph.units.group.empty()) continue;
+      void* X = nullptr;
+      if ((rc = H->mem.get(&X, ph.units.rec_total * elem))) return rc;
+      Launch t(kCatSkel, s, 0.0, 0.0, 0);
+      add_launches(kCatSkel, launch_unit_invert<T>(S.dev, S.phases[ip].dev, (T*)X, s));
+      H->mem.release(X);
+    }
     if (trace)
       std::fprintf(stderr, "[rhif] level %d: cells %d groups %d active %zu max_n %d max_nB %d max_group %d plan %.2f ms upload %.2f ms gpu+sync %.2f ms\n",
                    lvl, P.ncell(), P.ngroup(), P.bucket.size(), P.max_n, P.max_nB, P.max_group,

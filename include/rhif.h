@@ -44,7 +44,7 @@ enum {
 };
 
 enum { RHIF_FP64 = 0, RHIF_MIXED_FP32 = 1 };  /* precision of the stored factor */
-enum { RHIF_SOLVE = 0, RHIF_MATVEC = 1 };      /* apply F^{-1} or F */
+enum { RHIF_SOLVE = 0, RHIF_MATVEC = 1 };      /* apply F^{-1}; F (reserved, see rhif_apply) */
 
 typedef struct {
   int dim;      /* 2 or 3 */
@@ -150,9 +150,11 @@ int rhif_pcg_batched(int count, rhif_handle* const* F, int nrhs, const double* c
                      double* const* u, double rtol, int maxit, int* iters, double* relres,
                      void* const* streams, int nstreams);
 
-/* y = F^{-1} x (op = RHIF_SOLVE, Eq. 3.2) or y = F x (RHIF_MATVEC, Eq. 3.1)
- * for nrhs column vectors of length N stored with leading dimensions ldx/ldy
- * (>= N).  x and y may alias only if ldx == ldy and x == y. */
+/* y = F^{-1} x (op = RHIF_SOLVE, Eq. 3.2) for nrhs column vectors of length N
+ * stored with leading dimensions ldx/ldy (>= N).  x and y may alias only if
+ * ldx == ldy and x == y.  op = RHIF_MATVEC (y = F x, Eq. 3.1) is reserved and
+ * returns RHIF_ERR_BAD_ARG: the stored factor keeps the explicit inverses
+ * (L^{-1} of fronts, L_g^{-1}, L_rr^{-1}) that F^{-1} needs, not the blocks of F. */
 int rhif_apply(const rhif_handle* F, int op, int nrhs, const double* x, int64_t ldx,
                double* y, int64_t ldy, void* stream);
 

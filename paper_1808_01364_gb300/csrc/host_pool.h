@@ -1,14 +1,18 @@
 // A small pool of host threads for the level planner: parallel_for(n, fn)
 // runs fn(i) for i in [0, n) on the workers and the calling thread and
-// returns when all are done.  Workers sleep on a condition variable between
-// calls.  The pool is created on first use; a child created by fork() gets a
-// fresh pool (the parent's workers do not exist there).
+// returns when all are done.  The planner issues its parallel loops back to
+// back, so a worker that finishes one keeps polling for the next for a short
+// while (kSpin) before it sleeps on a condition variable; the caller likewise
+// polls for the workers' completion before it sleeps.  The pool is created on
+// first use; a child created by fork() gets a fresh pool (the parent's
+// workers do not exist there).
 #pragma once
 #include <pthread.h>
 #include <unistd.h>
 
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <condition_variable>
 #include <functional>
 #include <mutex>
@@ -48,13 +52,15 @@ class HostPool {
       n_ = n;
       grain_ = grain;
       next_.store(0);
-      active_ = (int)workers_.size();
-      ++gen_;
+      active_.store((int)workers_.size());
+      gen_.fetch_add(1, std::memory_order_release);   // publishes the fields above
     }
     cv_.notify_all();
     work();
-    std::unique_lock<std::mutex> lk(mu_);
-    done_cv_.wait(lk, [&] { return active_ == 0; });
+    if (!poll([&] { return active_.load(std::memory_order_acquire) == 0; })) {
+      std::unique_lock<std::mutex> lk(mu_);
+      done_cv_.wait(lk, [&] { return active_.load(std::memory_order_acquire) == 0; });
+    }
     fn_ = nullptr;
   }
 
@@ -74,17 +80,31 @@ class HostPool {
     }
   }
 
+  // Polls `ready` for about kSpin; false if it did not become true.
+  template <typename Pred>
+  static bool poll(Pred ready) {
+    constexpr auto kSpin = std::chrono::microseconds(200);
+    const auto t0 = std::chrono::steady_clock::now();
+    for (int i = 0;; ++i) {
+      if (ready()) return true;
+      if ((i & 255) == 255 && std::chrono::steady_clock::now() - t0 > kSpin) return false;
+    }
+  }
+
   void loop() {
     uint64_t seen = 0;
     for (;;) {
-      {
+      auto fresh = [&] { return gen_.load(std::memory_order_acquire) != seen; };
+      if (!poll(fresh)) {
         std::unique_lock<std::mutex> lk(mu_);
-        cv_.wait(lk, [&] { return gen_ != seen; });
-        seen = gen_;
+        cv_.wait(lk, fresh);
       }
+      seen = gen_.load(std::memory_order_acquire);
       work();
-      std::lock_guard<std::mutex> lk(mu_);
-      if (--active_ == 0) done_cv_.notify_one();
+      if (active_.fetch_sub(1, std::memory_order_acq_rel) == 1) {
+        std::lock_guard<std::mutex> lk(mu_);   // the caller may be about to wait
+        done_cv_.notify_one();
+      }
     }
   }
 
@@ -94,8 +114,8 @@ class HostPool {
   const std::function<void(int64_t, int64_t)>* fn_ = nullptr;
   int64_t n_ = 0, grain_ = 1;
   std::atomic<int64_t> next_{0};
-  int active_ = 0;
-  uint64_t gen_ = 0;
+  std::atomic<int> active_{0};
+  std::atomic<uint64_t> gen_{0};
 };
 
 }  // namespace rhif

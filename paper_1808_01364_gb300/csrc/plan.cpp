@@ -131,7 +131,28 @@ void LevelPlan::clear() {
   ea_off.clear();
   ea_child.clear();
   ea_map_off.clear();
+  for (auto& ph : phases) phase_spare.push_back(std::move(ph));   // keeps their storage
   phases.clear();
+}
+
+void PhasePlan::clear() {
+  unit_type = pre_min_type = 1;
+  pre_group.clear();
+  pre_off.clear();
+  pre_total = 0;
+  group_pre.clear();
+  group_unit.clear();
+  UnitTable& U = units;
+  U.group.clear();
+  U.nrow.clear();
+  U.m_off.clear();
+  U.m_total = 0;
+  U.rec_off.clear();
+  U.rec_total = 0;
+  U.perm_off.clear();
+  U.perm_total = 0;
+  U.max_n = 0;
+  U.max_m = 0;
 }
 
 namespace {
@@ -286,23 +307,37 @@ LevelPlan build_level(const Geometry& G, int level, const std::vector<uint8_t>& 
     newpos.resize(gpos_off[pg]);
     std::vector<int>& src = X.src;
     src.resize(P.bucket.size());
-    // ascending DOF index within every code; newpos follows the moves
-    pool.parallel_for(C.ncode, 1024, [&](int64_t c0, int64_t c1) {
+    // ascending DOF index within every code; newpos follows the moves.  The
+    // survivors of a group are compacted without branches (the flags are
+    // data-dependent): first their offsets, with the new position of every
+    // DOF, then the copy.
+    pool.parallel_for(C.ncode, 256, [&](int64_t c0, int64_t c1) {
       std::vector<int64_t> key;
+      std::vector<int> loc;
       for (int64_t c = c0; c < c1; ++c) {
         int64_t q = cstart[c];
         for (int t = cgoff[c]; t < cgoff[c + 1]; ++t) {
           const int g = cg[t];
-          const int32_t* gb = prev->bucket.data() + prev->group_start[g];
-          const uint8_t* kp = keep.data() + prev->group_start[g];
-          for (int o = 0; o < prev->group_size[g]; ++o)
-            if (kp[o]) {
-              P.bucket[q] = gb[o];
-              src[q] = gpos_off[g] + o;
-              ++q;
-            } else {
-              newpos[gpos_off[g] + o] = -1;
-            }
+          const int gs = prev->group_size[g], gp = gpos_off[g];
+          const int32_t* __restrict__ gb = prev->bucket.data() + prev->group_start[g];
+          const uint8_t* __restrict__ kp = keep.data() + prev->group_start[g];
+          int* __restrict__ np = newpos.data() + gp;
+          if ((int)loc.size() < gs) loc.resize(gs);
+          int* __restrict__ lo = loc.data();
+          int cnt = 0;
+          for (int o = 0; o < gs; ++o) {
+            const int k = kp[o] != 0;
+            lo[cnt] = o;   // overwritten by the next DOF unless this one survives
+            np[o] = k ? (int)q + cnt : -1;
+            cnt += k;
+          }
+          int32_t* __restrict__ bq = P.bucket.data() + q;
+          int* __restrict__ sq = src.data() + q;
+          for (int j = 0; j < cnt; ++j) {
+            bq[j] = gb[lo[j]];
+            sq[j] = gp + lo[j];
+          }
+          q += cnt;
         }
         const int64_t a = cstart[c], b = cstart[c + 1];
         if (b - a > 1 && !std::is_sorted(P.bucket.begin() + a, P.bucket.begin() + b)) {
@@ -313,61 +348,50 @@ LevelPlan build_level(const Geometry& G, int level, const std::vector<uint8_t>& 
             P.bucket[i] = (int32_t)(key[i - a] >> 32);
             src[i] = (int)(key[i - a] & 0xffffffff);
           }
+          for (int64_t i = a; i < b; ++i) newpos[src[i]] = (int)i;
         }
-        for (int64_t i = a; i < b; ++i) newpos[src[i]] = (int)i;
       }
     });
   }
   auto csize = [&](int64_t c) { return (int)(cstart[c + 1] - cstart[c]); };
 
-  // 2. cells: every cell whose closure holds an active DOF
+  // 2. cells: every cell whose closure holds an active DOF.  Codes are walked
+  // as (v0, v1, v2) loops in code order (code = v0 + base v1 + base^2 v2).
+  const int64_t s1 = C.base, s2 = d == 3 ? (int64_t)C.base * C.base : 0;
+  const int vz_end = d == 3 ? C.base : 1;
   std::vector<int>& cell_of_code = X.cell_of_code;
   cell_of_code.assign(C.ncode, -1);
-  {
-    std::vector<uint8_t>& mark = X.mark;
-    mark.assign(C.ncode, 0);
-    for (int64_t c = 0; c < C.ncode; ++c) {
-      if (!csize(c)) continue;
-      int v[3];
-      C.split(c, v);
-      int lo[3], hi[3];
-      for (int a = 0; a < 3; ++a) {
-        if (a >= d) { lo[a] = hi[a] = 1; continue; }
-        if (v[a] % 2) lo[a] = hi[a] = v[a];
-        else { lo[a] = v[a] - 1; hi[a] = v[a] + 1; }
-      }
-      for (int z = lo[2]; z <= hi[2]; z += 2)
-        for (int y = lo[1]; y <= hi[1]; y += 2)
-          for (int x = lo[0]; x <= hi[0]; x += 2) {
-            int u[3] = {x, y, z};
-            mark[C.join(u)] = 1;
-          }
-    }
-    for (int64_t c = 0; c < C.ncode; ++c)
-      if (mark[c]) {
+  for (int vz = d == 3 ? 1 : 0; vz < vz_end; vz += 2)
+    for (int vy = 1; vy < C.base; vy += 2)
+      for (int vx = 1; vx < C.base; vx += 2) {
+        const int64_t c = vx + s1 * vy + s2 * vz;
+        bool any = false;
+        for (int oz = d == 3 ? -1 : 0; oz <= (d == 3 ? 1 : 0) && !any; ++oz)
+          for (int oy = -1; oy <= 1 && !any; ++oy)
+            for (int ox = -1; ox <= 1 && !any; ++ox) any = csize(c + ox + s1 * oy + s2 * oz) > 0;
+        if (!any) continue;
         cell_of_code[c] = (int)P.cell_code.size();
         P.cell_code.push_back(c);
       }
-  }
   const int ncell = (int)P.cell_code.size();
 
   // 3. groups (t >= 1) in code order
   std::vector<int>& group_of_code = X.group_of_code;
   group_of_code.assign(C.ncode, -1);
-  for (int64_t c = 0; c < C.ncode; ++c) {
-    if (!csize(c)) continue;
-    int v[3];
-    C.split(c, v);
-    int t = 0;
-    for (int a = 0; a < d; ++a) t += (v[a] % 2 == 0);
-    if (t == 0) continue;
-    group_of_code[c] = (int)P.group_t.size();
-    P.group_code.push_back(c);
-    P.group_t.push_back(t);
-    P.group_start.push_back((int32_t)cstart[c]);
-    P.group_size.push_back(csize(c));
-    P.max_group = std::max(P.max_group, csize(c));
-  }
+  for (int vz = 0; vz < vz_end; ++vz)
+    for (int vy = 0; vy < C.base; ++vy)
+      for (int vx = 0; vx < C.base; ++vx) {
+        const int64_t c = vx + s1 * vy + s2 * vz;
+        const int sz = csize(c);
+        const int t = (vx % 2 == 0) + (vy % 2 == 0) + (d == 3 && vz % 2 == 0);
+        if (!sz || t == 0) continue;
+        group_of_code[c] = (int)P.group_t.size();
+        P.group_code.push_back(c);
+        P.group_t.push_back(t);
+        P.group_start.push_back((int32_t)cstart[c]);
+        P.group_size.push_back(sz);
+        P.max_group = std::max(P.max_group, sz);
+      }
   const int ngroup = (int)P.group_t.size();
 
   // 4. cells: interior range, separator segments, storage offsets (segment
@@ -530,14 +554,18 @@ LevelPlan build_level(const Geometry& G, int level, const std::vector<uint8_t>& 
                     found = true;
                   }
               }
-              const int* np = newpos.data() + gpos_off[g];
-              int* out = P.ea_map.data() + base + prev->seg_pos[s];
+              const int gs = prev->group_size[g];
+              const int* __restrict__ np = newpos.data() + gpos_off[g];
+              int* __restrict__ out = P.ea_map.data() + base + prev->seg_pos[s];
               if (!found) {   // no DOF of the segment reaches this front
-                for (int o = 0; o < prev->group_size[g]; ++o) out[o] = -1;
+                std::fill(out, out + gs, -1);
                 continue;
               }
-              for (int o = 0; o < prev->group_size[g]; ++o)
-                out[o] = np[o] >= 0 ? (int)(np[o] + shift) : -1;
+              const int sh = (int)shift;   // front positions and bucket offsets fit in int
+              for (int o = 0; o < gs; ++o) {
+                const int v = np[o];
+                out[o] = v >= 0 ? v + sh : -1;
+              }
             }
       }
     }
@@ -556,6 +584,11 @@ LevelPlan build_level(const Geometry& G, int level, const std::vector<uint8_t>& 
   });
   for (int pass = 0; pass < npass; ++pass) {
     PhasePlan ph;
+    if (!P.phase_spare.empty()) {   // storage of a recycled plan's phase
+      ph = std::move(P.phase_spare.back());
+      P.phase_spare.pop_back();
+      ph.clear();
+    }
     ph.unit_type = pass == 0 ? 1 : 2;
     ph.pre_min_type = pass == 0 ? 1 : 2;
     ph.group_pre.assign(ngroup, -1);

@@ -60,6 +60,8 @@ struct PhasePlan {
   std::vector<int> group_pre;        // per group: index into pre_group or -1
   std::vector<int> group_unit;       // per group: unit index or -1
   UnitTable units;
+  // Empties every table but keeps the storage.
+  void clear();
 };
 
 struct LevelPlan {
@@ -101,6 +103,7 @@ struct LevelPlan {
   std::vector<int> ea_map;           // child B position -> parent front position, -1 = eliminated
   // preconditioning + skeletonization passes (1, or 2 with 3D edge skeletonization)
   std::vector<PhasePlan> phases;
+  std::vector<PhasePlan> phase_spare;   // storage of cleared phases, reused by build_level
 
   int ncell() const { return (int)nI.size(); }
   int ngroup() const { return (int)group_t.size(); }

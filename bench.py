@@ -181,6 +181,28 @@ def reference_arm(args):
 
 
 # ---------------------------------------------------------------------------
+# replicas: the path does not shard, so N ranks run N independent problems
+# ---------------------------------------------------------------------------
+
+def max_over_ranks(sec: float, device=None) -> float:
+    """The job's time is its slowest replica's: all-reduce MAX over the ranks
+    of the initialized process group (NCCL on the GPU machine, gloo in the CPU
+    tests); the local time when there is no group or one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return sec
+    t = torch.tensor([sec], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(units_per_rank: float, steps: int, sec_max: float, world: int) -> float:
+    """Units processed by all ranks over the slowest rank's time."""
+    return world * units_per_rank * steps / sec_max
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 
@@ -443,11 +465,7 @@ def gpu_arm(args):
         torch.cuda.synchronize()
 
     def reduce_max(sec):
-        if world > 1:
-            t = torch.tensor([sec], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            sec = float(t.item())
-        return sec
+        return max_over_ranks(sec, dev)
 
     def timed(fn, steps, warmup, timing=False):
         for _ in range(warmup):
@@ -471,14 +489,14 @@ def gpu_arm(args):
     clocks.start()
     sec, (u, its, rr), ks_count = timed(lambda: wl.step(wl.headline), args.steps, args.warmup)
     clk = clocks.stop()
-    value = world * wl.dofs * args.steps / sec
+    value = whole_job_value(wl.dofs, args.steps, sec, world)
     gpu_launches = int(sum(v["launches"] for v in ks_count.values()))
     # the same steps again with CUDA events around every library launch (per-kernel durations)
     _, _, ks = timed(lambda: wl.step(wl.headline), args.steps, 0, timing=True)
     # the other precision beside it
     other = "fp32" if wl.headline == "fp64" else "fp64"
     sec_o, (u_o, its_o, rr_o), _ = timed(lambda: wl.step(other), args.fp64_steps, 1)
-    value_o = world * wl.dofs * args.fp64_steps / sec_o
+    value_o = whole_job_value(wl.dofs, args.fp64_steps, sec_o, world)
 
     def rel(a, b):
         if isinstance(a, list):
@@ -498,7 +516,7 @@ def gpu_arm(args):
     e1.record(stream)
     barrier()
     sec_e2e = reduce_max(e0.elapsed_time(e1) / 1e3)
-    e2e_val = world * wl.dofs * args.steps / sec_e2e
+    e2e_val = whole_job_value(wl.dofs, args.steps, sec_e2e, world)
 
     # roofline of the dominant kernel category of the headline path
     peaks = alu_peaks(torch)

@@ -42,7 +42,7 @@ def _rank(rank, world, port, out):
 
 def test_two_replicas_report_the_slowest_rank_and_the_sum_of_units():
     world = 2
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:   # no fork of this threaded process
         out = m.dict()
         mp.spawn(_rank, args=(world, _free_port(), out), nprocs=world, join=True)
         res = dict(out)

@@ -142,6 +142,22 @@ int rhif_factor_batched(int count, const rhif_csr* A, const rhif_grid* g, int le
                         const rhif_opts* o, void* const* streams, int nstreams,
                         rhif_handle** out);
 
+/* Autotuner of the scheduling options: one pass of coordinate descent over
+ * big_front, big_frame, skel_cluster and (FP32 factors) tensor_cores, each
+ * tried at its library default (0), forced on (1; skel_cluster: -1 and 4) and
+ * forced off (-1), starting from `base` (NULL = defaults).  A configuration
+ * costs the device time of rhif_factor (its event span, host planning gaps
+ * included) plus `applies` times one F^{-1} application to one vector, the
+ * smaller of two trials after one warm-up factorization; a change is kept
+ * when it is at least 2% cheaper.  These options change only how the work is
+ * split over CTAs (rounding order), never the factor's definition (Secs. 2-3),
+ * so every candidate computes the same PHIF factor.  A is factored about 20
+ * times.  *best receives the options (precision, precondition and
+ * edge_skel_3d as in base), *best_ms (may be NULL) their cost.  Errors: those
+ * of rhif_factor / rhif_apply; BAD_ARG for a NULL best or applies < 0. */
+int rhif_autotune(const rhif_csr* A, const rhif_grid* g, int leaf, double tol, const rhif_opts* base,
+                  int applies, void* stream, rhif_opts* best, double* best_ms);
+
 /* PCG (as rhif_pcg) for `count` factored problems at once, each with nrhs
  * right-hand sides stored contiguously (f[i] and u[i] are N_i x nrhs with
  * leading dimension N_i), spread over the streams like rhif_factor_batched.

@@ -110,6 +110,10 @@ EXPORTS = {
                                         ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_double), ctypes.c_void_p,
                                         ctypes.c_int]),
+    "rhif_autotune": (ctypes.c_int, [ctypes.POINTER(CSR), ctypes.POINTER(Grid), ctypes.c_int,
+                                     ctypes.c_double, ctypes.POINTER(Opts), ctypes.c_int,
+                                     ctypes.c_void_p, ctypes.POINTER(Opts),
+                                     ctypes.POINTER(ctypes.c_double)]),
     "rhif_plan_selfcheck": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                            ctypes.c_double, ctypes.c_uint64, ctypes.c_int,
                                            ctypes.POINTER(ctypes.c_int64)]),
@@ -314,6 +318,27 @@ def rhif_factor(csr, ns, leaf: int, tol: float, precision: str = "fp64", precond
     _check(_lib.rhif_factor(ctypes.byref(A), ctypes.byref(_grid(ns)), int(leaf), float(tol),
                             ctypes.byref(o), _stream(stream), ctypes.byref(h)))
     return Factor(h, ns, None)
+
+
+def rhif_autotune(csr, ns, leaf: int, tol: float, precision: str = "fp64", precondition=True,
+                  edge_skel_3d=False, applies: int = 10, stream=None):
+    """Scheduling options picked by the library's autotuner for this problem
+    (see ``rhif_autotune`` in rhif.h): returns (dict of rhif_factor keyword
+    arguments, cost in ms)."""
+    load()
+    rowptr, col, val = csr
+    N = rowptr.numel() - 1
+    A = CSR(N, val.numel(), rowptr.data_ptr(), col.data_ptr(), val.data_ptr())
+    o = _opts(precision, precondition, edge_skel_3d)
+    best = Opts()
+    ms = ctypes.c_double()
+    _check(_lib.rhif_autotune(ctypes.byref(A), ctypes.byref(_grid(ns)), int(leaf), float(tol),
+                              ctypes.byref(o), int(applies), _stream(stream), ctypes.byref(best),
+                              ctypes.byref(ms)))
+    kw = dict(precision=precision, precondition=precondition, edge_skel_3d=edge_skel_3d,
+              big_front=best.big_front, big_frame=best.big_frame,
+              skel_cluster=best.skel_cluster, tensor_cores=best.tensor_cores)
+    return kw, ms.value
 
 
 def rhif_tc_gemm_check(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor, stream=None):

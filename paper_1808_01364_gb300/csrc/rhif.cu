@@ -1170,6 +1170,98 @@ int rhif_factor(const rhif_csr* A, const rhif_grid* g, int leaf, double tol, con
   return RHIF_OK;
 }
 
+// Device time of one configuration: rhif_factor's own event span (host
+// planning gaps included) plus `applies` applications of F^{-1} to one vector;
+// the smaller of two trials.
+static int tune_cost(const rhif_csr* A, const rhif_grid* g, int leaf, double tol,
+                     const rhif_opts& o, int applies, cudaStream_t s, double* ms) {
+  double best = INFINITY;
+  for (int trial = 0; trial < 2; ++trial) {
+    rhif_handle* F = nullptr;
+    int rc = rhif_factor(A, g, leaf, tol, &o, s, &F);
+    if (rc) return rc;
+    double c = F->factor_ms;
+    if (applies > 0) {
+      double* x = nullptr;
+      if ((rc = F->mem.get((void**)&x, F->G.N * sizeof(double)))) {
+        rhif_free(F);
+        return rc;
+      }
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      cudaError_t ce = cudaMemsetAsync(x, 0, F->G.N * sizeof(double), s);
+      if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
+      if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+      if (ce == cudaSuccess) ce = cudaEventRecord(e0, s);
+      if (ce == cudaSuccess) rc = apply_dispatch(F, x, F->G.N, 1, s);
+      if (ce == cudaSuccess && !rc) ce = cudaEventRecord(e1, s);
+      if (ce == cudaSuccess && !rc) ce = cudaEventSynchronize(e1);
+      float am = 0.f;
+      if (ce == cudaSuccess && !rc) ce = cudaEventElapsedTime(&am, e0, e1);
+      if (e0) cudaEventDestroy(e0);
+      if (e1) cudaEventDestroy(e1);
+      F->mem.release(x);
+      if (!rc && ce != cudaSuccess) rc = fail(RHIF_ERR_CUDA, cudaGetErrorString(ce));
+      if (rc) {
+        rhif_free(F);
+        return rc;
+      }
+      c += applies * (double)am;
+    }
+    rhif_free(F);
+    best = std::min(best, c);
+  }
+  *ms = best;
+  return RHIF_OK;
+}
+
+int rhif_autotune(const rhif_csr* A, const rhif_grid* g, int leaf, double tol, const rhif_opts* base,
+                  int applies, void* stream, rhif_opts* best, double* best_ms) {
+  if (!best || applies < 0) return fail(RHIF_ERR_BAD_ARG, "null output or applies < 0");
+  rhif_opts cur;
+  if (base) cur = *base;
+  else rhif_default_opts(&cur);
+  cudaStream_t s = (cudaStream_t)stream;
+  {   // warm-up: one-time set-up (kernel attributes, pools, staging) stays out of the timings
+    rhif_handle* F = nullptr;
+    const int rc = rhif_factor(A, g, leaf, tol, &cur, s, &F);
+    if (rc) return rc;
+    rhif_free(F);
+  }
+  double cur_ms = 0.0;
+  int rc = tune_cost(A, g, leaf, tol, cur, applies, s, &cur_ms);
+  if (rc) return rc;
+  // one pass of coordinate descent; each knob takes its library default (0),
+  // "always many CTAs" (1) or "never" (-1); a change must gain 2%
+  struct Knob {
+    int rhif_opts::*field;
+    int count;
+    int values[3];
+  };
+  const Knob knobs[] = {{&rhif_opts::big_front, 3, {0, 1, -1}},
+                        {&rhif_opts::big_frame, 3, {0, 1, -1}},
+                        {&rhif_opts::skel_cluster, 3, {0, -1, 4}},
+                        {&rhif_opts::tensor_cores, 2, {0, -1, 0}}};
+  for (const Knob& k : knobs) {
+    if (k.field == &rhif_opts::tensor_cores && cur.precision != RHIF_MIXED_FP32) continue;
+    const int start = cur.*(k.field);
+    for (int i = 0; i < k.count; ++i) {
+      const int v = k.values[i];
+      if (v == start) continue;
+      rhif_opts o = cur;
+      o.*(k.field) = v;
+      double ms = 0.0;
+      if ((rc = tune_cost(A, g, leaf, tol, o, applies, s, &ms))) return rc;
+      if (ms < 0.98 * cur_ms) {
+        cur = o;
+        cur_ms = ms;
+      }
+    }
+  }
+  *best = cur;
+  if (best_ms) *best_ms = cur_ms;
+  return RHIF_OK;
+}
+
 int rhif_factor_batched(int count, const rhif_csr* A, const rhif_grid* g, int leaf, double tol,
                         const rhif_opts* o, void* const* streams, int nstreams,
                         rhif_handle** out) {

@@ -186,7 +186,7 @@ def reference_arm(args):
 
 def max_over_ranks(sec: float, device=None) -> float:
     """The job's time is its slowest replica's: all-reduce MAX over the ranks
-    of the initialized process group (NCCL on the GPU machine, gloo in the CPU
+    of the initialized process group (NCCL between GPUs, gloo in the CPU
     tests); the local time when there is no group or one rank."""
     import torch
     import torch.distributed as dist

@@ -26,7 +26,9 @@ Parity: pinned in the tests by exactness at ``tol = 0`` (F = A), by the
 explicit dense operator products of Eqs. (2.1)-(2.3) on tiny grids, by the
 unit block diagonal after preconditioning (Sec. 2.3), by the skeleton block
 form ``[[I + T^T T, -T^T], [-T, I]]`` (Sec. 3.3), by symmetry and by cell-order
-independence (Sec. 2.1).  The 3D edge skeletonization (Remark 3.1, which the
+independence (Sec. 2.1); PCG (Sec. 4) by one-step convergence with the tol = 0
+factor, finite termination on right-hand sides made of a few sine modes and the
+classical CG iteration bound on the Laplacian.  The 3D edge skeletonization (Remark 3.1, which the
 paper did not run) is "parity unpinned" beyond the tol = 0 exactness check.
 """
 from __future__ import annotations

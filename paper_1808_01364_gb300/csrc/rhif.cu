@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "../../include/rhif.h"
+#include "host_pool.h"
 #include "kernels.h"
 #include "plan.h"
 #include "tables.h"
@@ -128,8 +129,25 @@ int Packer::upload(void* dst, cudaStream_t s) const {
     CK(cudaHostAlloc((void**)&st.p, cap, cudaHostAllocPortable));
     st.cap = cap;
   }
-  for (size_t i = 0; i < part.size(); ++i)
-    if (part[i].second) std::memcpy(st.p + off[i], part[i].first, part[i].second);
+  // large tables (the level-0 DOF list is 4 bytes per DOF) are copied into
+  // the staging buffer in 256 KB chunks by the planner's host threads
+  constexpr size_t kChunk = size_t(256) << 10;
+  std::vector<std::pair<size_t, size_t>> big;   // (part, chunk)
+  for (size_t i = 0; i < part.size(); ++i) {
+    if (part[i].second >= 2 * kChunk) {
+      for (size_t c = 0; c * kChunk < part[i].second; ++c) big.emplace_back(i, c);
+    } else if (part[i].second) {
+      std::memcpy(st.p + off[i], part[i].first, part[i].second);
+    }
+  }
+  if (!big.empty())
+    HostPool::get().parallel_for((int64_t)big.size(), 1, [&](int64_t b0, int64_t b1) {
+      for (int64_t b = b0; b < b1; ++b) {
+        const size_t i = big[b].first, o = big[b].second * kChunk;
+        const size_t len = std::min(kChunk, part[i].second - o);
+        std::memcpy(st.p + off[i] + o, (const char*)part[i].first + o, len);
+      }
+    });
   CK(cudaMemcpyAsync(dst, st.p, total, cudaMemcpyHostToDevice, s));
   CK(cudaEventRecord(st.done, s));
   return 0;

@@ -35,6 +35,7 @@ import statistics
 import subprocess
 import sys
 import tempfile
+import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -206,10 +207,61 @@ def whole_job_value(units_per_rank: float, steps: int, sec_max: float, world: in
 # GPU arm
 # ---------------------------------------------------------------------------
 
-class ClockSampler:
-    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+_CLOCK_REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+
+def _smi_time(text: str):
+    """Seconds since the epoch of an nvidia-smi timestamp (local time), or None."""
+    import datetime
+    for fmt in ("%Y/%m/%d %H:%M:%S.%f", "%Y/%m/%d %H:%M:%S"):
+        try:
+            return datetime.datetime.strptime(text.strip(), fmt).timestamp()
+        except ValueError:
+            pass
+    return None
+
+
+def parse_clock_samples(lines, t0=None, t1=None) -> dict:
+    """Clock record of the timed region from nvidia-smi CSV lines (fields:
+    timestamp, index, clocks.sm, clocks.max.sm, power.draw, reasons bitmask,
+    then the four reasons of _CLOCK_REASONS as Active / Not Active).
+
+    With the region's host times t0..t1, the samples taken inside it are used;
+    when the region is shorter than the sampling period, the last sample
+    before it and the first after it stand for it.  Without times (or with
+    unreadable timestamps) every sample is used."""
+    rows = []
+    for line in lines:
+        f = [x.strip() for x in line.split(",")]
+        if len(f) < 10:
+            continue
+        try:
+            sm, mx = float(f[2]), float(f[3])
+        except ValueError:
+            continue
+        active = {nm for nm, v in zip(_CLOCK_REASONS, f[6:10]) if v.lower().startswith("active")}
+        rows.append((_smi_time(f[0]), sm, mx, active))
+    use, where = rows, "all samples"
+    if t0 is not None and t1 is not None and rows and all(r[0] is not None for r in rows):
+        inside = [r for r in rows if t0 <= r[0] <= t1]
+        if inside:
+            use, where = inside, "inside the timed region"
+        else:
+            before = [r for r in rows if r[0] < t0]
+            after = [r for r in rows if r[0] > t1]
+            use = before[-1:] + after[:1]
+            where = "adjacent to the timed region (shorter than the sampling period)"
+    if not use:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+    reasons = set().union(*(r[3] for r in use))
+    return {"sm_mhz": statistics.median(r[1] for r in use), "sm_max_mhz": use[-1][2],
+            "reasons": sorted(reasons), "samples": len(use), "sampled": where}
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons around the timed region."""
+
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -219,16 +271,24 @@ class ClockSampler:
         self.path = os.path.join(tempfile.gettempdir(), f"rhif_clocks_rank{index}.csv")
 
     def start(self):
+        """Starts the sampler and waits (up to 1 s) for its first sample, so that
+        it is running when the timed region begins."""
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        t = time.time()
+        while time.time() - t < 1.0 and self.proc.poll() is None:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.02)
 
-    def stop(self) -> dict:
+    def stop(self, t0=None, t1=None) -> dict:
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         self.proc.terminate()
@@ -237,22 +297,8 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.fh.close()
-        sm, mx, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
-            f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                sm.append(float(f[1]))
-                mx = float(f[2])
-            except ValueError:
-                continue
-            for nm, v in zip(names, f[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        with open(self.path) as fh:
+            return parse_clock_samples(fh.readlines(), t0, t1)
 
 
 def measured_peaks():
@@ -467,6 +513,8 @@ def gpu_arm(args):
     def reduce_max(sec):
         return max_over_ranks(sec, dev)
 
+    region = {}   # host times bracketing the last timed region (for the clock record)
+
     def timed(fn, steps, warmup, timing=False):
         for _ in range(warmup):
             fn()
@@ -474,12 +522,14 @@ def gpu_arm(args):
         rhif.rhif_reset_kernel_stats()
         rhif.rhif_set_timing(timing)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        region["t0"] = time.time()
         e0.record(stream)
         info = None
         for _ in range(steps):
             info = fn()
         e1.record(stream)
         barrier()
+        region["t1"] = time.time()
         rhif.rhif_set_timing(False)
         ks = rhif.rhif_kernel_stats()
         return reduce_max(e0.elapsed_time(e1) / 1e3), info, ks
@@ -488,7 +538,7 @@ def gpu_arm(args):
     # headline precision, no instrumentation in the timed region
     clocks.start()
     sec, (u, its, rr), ks_count = timed(lambda: wl.step(wl.headline), args.steps, args.warmup)
-    clk = clocks.stop()
+    clk = clocks.stop(region.get("t0"), region.get("t1"))
     value = whole_job_value(wl.dofs, args.steps, sec, world)
     gpu_launches = int(sum(v["launches"] for v in ks_count.values()))
     # the same steps again with CUDA events around every library launch (per-kernel durations)

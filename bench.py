@@ -87,6 +87,8 @@ A = fd.assemble(p.ns, p.a, p.b)
 F = phif.factor(A, p.ns, p.leaf, p.tol)
 u, it, rr = phif.pcg(A, p.f, M=lambda r: phif.solve(F, r), rtol={rtol})
 t = time.perf_counter() - t0
+if {save!r}:
+    np.save({save!r}, u)
 print(json.dumps({{"seconds": t, "dofs": p.n, "iters": it}}))
 """,
     "3d": r"""
@@ -139,13 +141,22 @@ _SAMPLES = {
 _REF_SIDE = {"c1": 127, "c2": 255, "c3": 23, "c4": 127, "c5": 127}
 
 
-def run_oracle(workload: str, side: int) -> dict:
+def oracle_seed(workload: str) -> int:
+    """Seed of the oracle's sample: the 127^2 sample is the c1 workload itself."""
+    return 180800 + (0 if workload == "c1" else 1)
+
+
+def run_oracle(workload: str, side: int, save: str = "") -> dict:
+    """Times the oracle on a sample of the workload in a one-thread
+    subprocess; with `save`, the 2D samples also write their PCG solution
+    there (.npy, outside the timed part)."""
     body, _, extra, _ = _SAMPLES[workload]
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = "1"
-    fields = dict(side=side, seed=180800 + 1, rtol=extra.get("rtol", RTOL),
-                  lo=extra.get("lo", 1e-4), hi=extra.get("hi", 1e4), leaf=extra.get("leaf", 16))
+    fields = dict(side=side, seed=oracle_seed(workload), rtol=extra.get("rtol", RTOL),
+                  lo=extra.get("lo", 1e-4), hi=extra.get("hi", 1e4), leaf=extra.get("leaf", 16),
+                  save=save)
     code = _ORACLE_HEAD.format(root=ROOT) + _ORACLE_BODY[body].format(**fields)
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
     if r.returncode != 0:
@@ -487,6 +498,39 @@ class Workload:
         return c
 
 
+def compare_with_oracle(rhif, W, torch, dev, workload, side, extra, path, oracle_iters, rtol):
+    """The GPU path (both factor precisions, PCG to the workload's rtol) on
+    the oracle's 2D sample: relative 2-norm difference of the PCG solutions
+    and the iteration counts.  Outside every timed region; an error is
+    reported in the result instead of ending the run."""
+    import numpy as np
+    out = {"sample": f"{side}^2 grid of the {workload} recipe (the cpu_baseline problem)"}
+    try:
+        u_o = np.load(path)
+        p = W.make_problem((side, side), extra.get("lo", 1e-4), extra.get("hi", 1e4), 0.0,
+                           extra.get("leaf", 16), 1e-3, oracle_seed(workload))
+        a = torch.as_tensor(p.a, device=dev)
+        f = torch.as_tensor(p.f, device=dev)
+        uo = torch.as_tensor(u_o, device=dev)
+        diff, its = {}, {"oracle": oracle_iters}
+        for prec in ("fp32", "fp64"):
+            csr = rhif.rhif_assemble_fd(p.ns, a, 0.0)
+            F = rhif.rhif_factor(csr, p.ns, p.leaf, p.tol, precision=prec)
+            u, it, _ = F.pcg(f, rtol=rtol, maxit=1000)
+            F.free()
+            diff[prec] = float(torch.linalg.norm(u - uo) / torch.linalg.norm(uo))
+            its[prec] = int(it[0])
+        out.update(rel_diff_u=diff, pcg_iters=its, rtol=rtol)
+    except Exception as e:   # reported, not fatal: the headline line stands
+        out["error"] = str(e)[:300]
+    finally:
+        try:
+            os.remove(path)
+        except OSError:
+            pass
+    return out
+
+
 def gpu_arm(args):
     import torch
     import torch.distributed as dist
@@ -615,12 +659,17 @@ def gpu_arm(args):
         result["loss"] = rr[0]
         result.pop("relres")
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        _, side, _, desc = _SAMPLES[args.workload]
-        r = run_oracle(args.workload, side)
+        body, side, extra, desc = _SAMPLES[args.workload]
+        save = os.path.join(tempfile.gettempdir(), f"rhif_oracle_u_{os.getpid()}.npy") \
+            if body == "2d" else ""
+        r = run_oracle(args.workload, side, save)
         result["cpu_baseline"] = {
             "value": r["dofs"] / r["seconds"], "unit": "DOFs/s", "cores": 1, "kind": "oracle",
             "sample": (f"FP64 oracle on {desc} (DOFs={r['dofs']}, {r['seconds']:.1f} s, "
                        f"{r['iters']} PCG its), 1 thread")}
+        if save:
+            result["vs_oracle"] = compare_with_oracle(rhif, W, torch, dev, args.workload, side,
+                                                      extra, save, r["iters"], wl.rtol)
     if rank == 0:
         print(json.dumps(result))
     if world > 1:

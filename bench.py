@@ -498,6 +498,34 @@ class Workload:
         return c
 
 
+def step_breakdown(wl, torch) -> dict:
+    """Device time of each part of one headline step of a single-problem
+    workload (assembly, factorization, one application of F^{-1}, PCG),
+    with CUDA events on the current stream, outside every timed region.
+    An error is reported in the result instead of ending the run."""
+    try:
+        r, p = wl.rhif, wl.p
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        torch.cuda.synchronize()
+        ev[0].record()
+        csr = r.rhif_assemble_fd(p.ns, wl.a_d, p.b)
+        ev[1].record()
+        F = r.rhif_factor(csr, p.ns, p.leaf, p.tol, precision=wl.headline, edge_skel_3d=wl.edge)
+        ev[2].record()
+        F.apply(wl.f_d)
+        ev[3].record()
+        _, its, _ = F.pcg(wl.f_d, rtol=wl.rtol, maxit=1000)
+        ev[4].record()
+        torch.cuda.synchronize()
+        F.free()
+        names = ("assemble_ms", "factor_ms", "apply_ms", "pcg_ms")
+        out = {n: ev[i].elapsed_time(ev[i + 1]) for i, n in enumerate(names)}
+        out["pcg_iters"] = int(its[0])
+        return out
+    except Exception as e:   # reported, not fatal: the headline line stands
+        return {"error": str(e)[:300]}
+
+
 def compare_with_oracle(rhif, W, torch, dev, workload, side, extra, path, oracle_iters, rtol):
     """The GPU path (both factor precisions, PCG to the workload's rtol) on
     the oracle's 2D sample: relative 2-norm difference of the PCG solutions
@@ -653,6 +681,8 @@ def gpu_arm(args):
     }
     if wl.headline == "fp32":
         result["mixed_over_fp64"] = value / value_o
+    if args.workload in ("c1", "c2", "c3"):
+        result["breakdown"] = step_breakdown(wl, torch)
     if args.workload == "c4":
         result["rhs_dofs_per_s"] = value * 32
     if args.workload == "c5":

@@ -88,7 +88,10 @@ F = phif.factor(A, p.ns, p.leaf, p.tol)
 u, it, rr = phif.pcg(A, p.f, M=lambda r: phif.solve(F, r), rtol={rtol})
 t = time.perf_counter() - t0
 if {save!r}:
-    np.save({save!r}, u)
+    try:
+        np.save({save!r}, u)
+    except OSError:
+        pass
 print(json.dumps({{"seconds": t, "dofs": p.n, "iters": it}}))
 """,
     "3d": r"""

@@ -186,6 +186,50 @@ def _cols(x: torch.Tensor, N: int):
     return x.shape[0], N
 
 
+def _npix(ns) -> int:
+    n = 1
+    for v in ns:
+        n *= int(v) + 1
+    return n
+
+
+def _ndof(ns) -> int:
+    n = 1
+    for v in ns:
+        n *= int(v)
+    return n
+
+
+def _need(t, name: str, numel: int, dtype=None):
+    """Sizes are checked here because the C ABI takes bare device pointers:
+    a short buffer would be read or written out of bounds on the GPU."""
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name}: expected a torch tensor")
+    if t.numel() != numel:
+        raise ValueError(f"{name}: {t.numel()} entries, expected {numel}")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name}: dtype {t.dtype}, expected {dtype}")
+
+
+def _on_device(**tensors):
+    for name, t in tensors.items():
+        if not t.is_cuda:
+            raise ValueError(f"{name}: expected a CUDA tensor")
+
+
+def _csr(csr, ns) -> CSR:
+    """CSR struct of (rowptr int64 [N+1], col int32 [nnz], val float64 [nnz]) on grid ns."""
+    rowptr, col, val = csr
+    N = _ndof(ns)
+    _need(rowptr, "rowptr", N + 1, torch.int64)
+    _need(col, "col", val.numel(), torch.int32)
+    _need(val, "val", col.numel(), torch.float64)
+    _on_device(rowptr=rowptr, col=col, val=val)
+    for t in csr:
+        assert t.is_contiguous(), "CSR arrays must be contiguous"
+    return CSR(N, val.numel(), rowptr.data_ptr(), col.data_ptr(), val.data_ptr())
+
+
 def rhif_fd_nnz(ns) -> int:
     load()
     return int(_lib.rhif_fd_nnz(ctypes.byref(_grid(ns))))
@@ -198,6 +242,11 @@ def rhif_assemble_fd(ns, a_pix: torch.Tensor, b=0.0, stream=None):
     N = 1
     for v in ns:
         N *= int(v)
+    _need(a_pix, "a_pix", _npix(ns))
+    if isinstance(b, torch.Tensor):
+        _need(b, "b", N)
+        _on_device(b=b)
+    _on_device(a_pix=a_pix)
     nnz = int(_lib.rhif_fd_nnz(ctypes.byref(g)))
     dev = a_pix.device
     rowptr = torch.empty(N + 1, dtype=torch.int64, device=dev)
@@ -238,6 +287,9 @@ class Factor:
     def apply(self, x: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
         """F^{-1} x (Eq. 3.2) for x of shape (N,) or (nrhs, N)."""
         nrhs, ld = _cols(x, self.N)
+        if out is not None:
+            _need(out, "out", x.numel(), torch.float64)
+            _on_device(out=out)
         y = torch.empty_like(x) if out is None else out
         _check(_lib.rhif_apply(self._h, RHIF_SOLVE, nrhs, _ptr(x), ld, _ptr(y), ld, _stream(stream)))
         return y
@@ -246,6 +298,8 @@ class Factor:
         """F^{-1} x into the caller's ``out`` without any device allocation
         (library-owned static scratch; see rhif_apply_noalloc in rhif.h)."""
         nrhs, ld = _cols(x, self.N)
+        _need(out, "out", x.numel(), torch.float64)
+        _on_device(out=out)
         _check(_lib.rhif_apply_noalloc(self._h, nrhs, _ptr(x), ld, _ptr(out), ld, _stream(stream)))
         return out
 
@@ -258,6 +312,9 @@ class Factor:
     def pcg(self, f: torch.Tensor, rtol=1e-10, maxit=1000, out=None, stream=None, check=True):
         """PCG with F^{-1}; returns (u, iters list, relres list)."""
         nrhs, ld = _cols(f, self.N)
+        if out is not None:
+            _need(out, "out", f.numel(), torch.float64)
+            _on_device(out=out)
         u = torch.empty_like(f) if out is None else out
         it = (ctypes.c_int * nrhs)()
         rr = (ctypes.c_double * nrhs)()
@@ -270,6 +327,8 @@ class Factor:
     def estimate_es(self, x0: torch.Tensor, maxit: int = 100, rel: float = 1e-2, stream=None):
         """e_s = ||I - A F^{-1}||_2 by power iteration from the device vector x0;
         returns (estimate, number of M^T M products)."""
+        _need(x0, "x0", self.N, torch.float64)
+        _on_device(x0=x0)
         es = ctypes.c_double()
         it = ctypes.c_int()
         _check(_lib.rhif_estimate_es(self._h, _ptr(x0.contiguous()), int(maxit), float(rel),
@@ -309,9 +368,7 @@ def rhif_factor(csr, ns, leaf: int, tol: float, precision: str = "fp64", precond
     ``big_front`` / ``big_frame`` / ``skel_cluster`` are the scheduling options of
     ``rhif_opts``."""
     load()
-    rowptr, col, val = csr
-    N = rowptr.numel() - 1
-    A = CSR(N, val.numel(), rowptr.data_ptr(), col.data_ptr(), val.data_ptr())
+    A = _csr(csr, ns)
     o = _opts(precision, precondition, edge_skel_3d, big_front, big_frame, skel_cluster,
               tensor_cores)
     h = ctypes.c_void_p()
@@ -326,9 +383,7 @@ def rhif_autotune(csr, ns, leaf: int, tol: float, precision: str = "fp64", preco
     (see ``rhif_autotune`` in rhif.h): returns (dict of rhif_factor keyword
     arguments, cost in ms)."""
     load()
-    rowptr, col, val = csr
-    N = rowptr.numel() - 1
-    A = CSR(N, val.numel(), rowptr.data_ptr(), col.data_ptr(), val.data_ptr())
+    A = _csr(csr, ns)
     o = _opts(precision, precondition, edge_skel_3d)
     best = Opts()
     ms = ctypes.c_double()
@@ -367,7 +422,12 @@ def rhif_plan_selfcheck(ns, leaf: int, keep: float = 0.5, seed: int = 1, edge_sk
 
 
 def rhif_grad_logcoef(ns, a_pix: torch.Tensor, u: torch.Tensor, lam: torch.Tensor, stream=None):
+    """dL/dlog a per pixel from the solution u and the adjoint lam (one right-hand side)."""
     load()
+    _need(a_pix, "a_pix", _npix(ns), torch.float64)
+    _need(u, "u", _ndof(ns), torch.float64)
+    _need(lam, "lam", _ndof(ns), torch.float64)
+    _on_device(a_pix=a_pix, u=u, lam=lam)
     grad = torch.empty_like(a_pix)
     _check(_lib.rhif_grad_logcoef(ctypes.byref(_grid(ns)), _ptr(a_pix), _ptr(u), _ptr(lam),
                                   _ptr(grad), _stream(stream)))
@@ -404,6 +464,11 @@ def rhif_assemble_fd_log(ns, log_a_pix: torch.Tensor, b=0.0, stream=None):
     N = 1
     for v in ns:
         N *= int(v)
+    _need(log_a_pix, "log_a_pix", _npix(ns))
+    if isinstance(b, torch.Tensor):
+        _need(b, "b", N)
+        _on_device(b=b)
+    _on_device(log_a_pix=log_a_pix)
     nnz = int(_lib.rhif_fd_nnz(ctypes.byref(g)))
     dev = log_a_pix.device
     log_a_pix = log_a_pix.contiguous().to(torch.float64)
@@ -480,8 +545,8 @@ def rhif_factor_batched(csrs, grids, leaf: int, tol: float, precision: str = "fp
         streams = [torch.cuda.Stream() for _ in range(min(8, max(n, 1)))]
     A = (CSR * n)()
     G = (Grid * n)()
-    for i, ((rp, col, val), ns) in enumerate(zip(csrs, grids)):
-        A[i] = CSR(rp.numel() - 1, val.numel(), rp.data_ptr(), col.data_ptr(), val.data_ptr())
+    for i, (csr, ns) in enumerate(zip(csrs, grids)):
+        A[i] = _csr(csr, ns)
         G[i] = _grid(ns)
     S = (ctypes.c_void_p * len(streams))(*[s.cuda_stream for s in streams])
     out = (ctypes.c_void_p * n)()
@@ -505,7 +570,13 @@ def rhif_pcg_batched(factors, fs, rtol=1e-10, maxit=1000, streams=None):
     """PCG for many factored problems at once; fs[i] is (nrhs, N_i).  Returns (us, iters, relres)."""
     load()
     n = len(factors)
+    if len(fs) != n:
+        raise ValueError("one right-hand-side block per factor")
     nrhs = 1 if fs[0].dim() == 1 else fs[0].shape[0]
+    for F, f in zip(factors, fs):
+        _need(f, "f", nrhs * F.N, torch.float64)
+        _on_device(f=f)
+        assert f.is_contiguous(), "right-hand sides must be contiguous"
     if streams is None:
         streams = [torch.cuda.Stream() for _ in range(min(8, max(n, 1)))]
     us = [torch.empty_like(f) for f in fs]

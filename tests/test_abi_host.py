@@ -147,3 +147,36 @@ def test_other_entry_points_check_their_arguments(rhif):
     st = rhif.KernelStat()
     assert lib.rhif_kernel_stats(-1, ctypes.byref(st)) == BAD_ARG
     assert lib.rhif_kernel_stats(lib.rhif_kernel_stat_count(), ctypes.byref(st)) == BAD_ARG
+
+
+def test_binding_checks_buffer_sizes_before_the_device(rhif):
+    """The C ABI takes bare pointers, so the binding refuses tensors whose
+    sizes do not match the grid (a short buffer would be read or written
+    out of bounds on the GPU)."""
+    import torch
+    ns = (15, 15)
+    N, npix = 15 * 15, 16 * 16
+    with pytest.raises(ValueError, match="a_pix"):
+        rhif.rhif_assemble_fd(ns, torch.ones(npix - 1, dtype=torch.float64))
+    with pytest.raises(ValueError, match="b"):
+        rhif.rhif_assemble_fd(ns, torch.ones(npix, dtype=torch.float64), torch.ones(N + 1))
+    with pytest.raises(ValueError, match="log_a_pix"):
+        rhif.rhif_assemble_fd_log(ns, torch.zeros(npix + 3, dtype=torch.float64))
+    nnz = 5 * N - 4 * 15
+    good = (torch.zeros(N + 1, dtype=torch.int64), torch.zeros(nnz, dtype=torch.int32),
+            torch.zeros(nnz, dtype=torch.float64))
+    for bad, what in [((good[0][:-1], good[1], good[2]), "rowptr"),
+                      ((good[0], good[1][:-1], good[2]), "col"),
+                      ((good[0], good[1].long(), good[2]), "col"),
+                      ((good[0], good[1], good[2].float()), "val")]:
+        with pytest.raises(ValueError, match=what):
+            rhif.rhif_factor(bad, ns, 4, 1e-3)
+        with pytest.raises(ValueError, match=what):
+            rhif.rhif_autotune(bad, ns, 4, 1e-3)
+    with pytest.raises(ValueError, match="CUDA"):
+        rhif.rhif_factor(good, ns, 4, 1e-3)       # right sizes, but host memory
+    u = torch.zeros(N, dtype=torch.float64)
+    with pytest.raises(ValueError, match="lam"):
+        rhif.rhif_grad_logcoef(ns, torch.ones(npix, dtype=torch.float64), u, u[:-1])
+    with pytest.raises(ValueError, match="a_pix"):
+        rhif.rhif_grad_logcoef(ns, torch.ones(npix, dtype=torch.float32), u, u)

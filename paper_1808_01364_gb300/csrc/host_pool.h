@@ -45,7 +45,13 @@ class HostPool {
       fn(0, n);
       return;
     }
-    std::lock_guard<std::mutex> call(call_mu_);   // one parallel_for at a time
+    // one parallel_for at a time: a caller that finds the pool busy (another
+    // host thread planning another problem) runs its loop itself
+    std::unique_lock<std::mutex> call(call_mu_, std::try_to_lock);
+    if (!call.owns_lock()) {
+      fn(0, n);
+      return;
+    }
     {
       std::lock_guard<std::mutex> lk(mu_);
       fn_ = &fn;

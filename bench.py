@@ -55,7 +55,9 @@ WORKLOADS = {
 def _args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--steps", type=int, default=None,
+                   help="timed steps (default: about half a second of GPU work per workload; "
+                        "5 for --impl reference)")
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
@@ -754,8 +756,15 @@ def paper_tables(args):
     print(json.dumps({"paper_tables": rows}))
 
 
+# default timed steps of the GPU arm: about half a second of work, so that
+# several clock samples (100 ms period) fall inside the timed region
+DEFAULT_STEPS = {"c1": 100, "c2": 40, "c3": 5, "c4": 3, "c5": 40}
+
+
 def main():
     args = _args()
+    if args.steps is None:
+        args.steps = 5 if args.impl == "reference" else DEFAULT_STEPS[args.workload]
     if args.paper_tables:
         paper_tables(args)
         return

@@ -29,7 +29,9 @@ form ``[[I + T^T T, -T^T], [-T, I]]`` (Sec. 3.3), by symmetry and by cell-order
 independence (Sec. 2.1); PCG (Sec. 4) by one-step convergence with the tol = 0
 factor, finite termination on right-hand sides made of a few sine modes and the
 classical CG iteration bound on the Laplacian.  The 3D edge skeletonization (Remark 3.1, which the
-paper did not run) is "parity unpinned" beyond the tol = 0 exactness check.
+paper did not run) is "parity unpinned" as a reading; its implementation is
+checked by the tol = 0 exactness test and the explicit operator products of
+its second pass.
 """
 from __future__ import annotations
 

@@ -42,3 +42,20 @@ def test_library_builds_and_exports_every_declared_symbol():
 def test_binding_covers_every_export():
     import paper_1808_01364_gb300 as rhif
     assert sorted(rhif.EXPORTS) == _declared()
+
+
+def test_binding_fails_loudly_without_the_library(monkeypatch):
+    """No CPU fallback: when the CUDA library cannot be built, loading raises."""
+    import paper_1808_01364_gb300 as rhif
+    from paper_1808_01364_gb300 import build
+
+    def no_nvcc(*a, **k):
+        raise RuntimeError("nvcc not found: the CUDA library cannot be built")
+
+    monkeypatch.setattr(rhif, "_lib", None)
+    monkeypatch.setattr(build, "up_to_date", lambda: False)
+    monkeypatch.setattr(build, "build", no_nvcc)
+    with pytest.raises(RuntimeError, match="cannot be built"):
+        rhif.load()
+    with pytest.raises(RuntimeError, match="cannot be built"):
+        rhif.rhif_fd_nnz((3, 3))

@@ -325,6 +325,15 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def alu_peak_nominal(precision: str):
+    """Plain-ALU peak of GB300 from its unit counts and clock (TFLOP/s): FP32 =
+    152 SMs x 128 FMA lanes x 2 flops x 2.07 GHz; FP64 = the chip's nominal
+    1.25 TFLOP/s.  The cuBLAS GEMM rates measured live are reported beside it."""
+    if precision == "fp32":
+        return 152 * 128 * 2 * 2.07e9 / 1e12, "nominal: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz"
+    return 1.25, "nominal GB300 FP64 rate"
+
+
 def alu_peaks(torch):
     """FP32 and FP64 throughput of cuBLAS GEMM on this GPU (no TF32), TFLOP/s."""
     out = {}
@@ -656,9 +665,9 @@ def gpu_arm(args):
                 "peak_kind": hbm_kind}
     else:
         achieved = st["flops"] / max(st["launches"], 1) / (per_launch_ms / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": peaks[wl.headline],
-                "unit": "TFLOP/s",
-                "peak_kind": f"measured cuBLAS {wl.headline} GEMM (no TF32) on this GPU"}
+        peak, kind = alu_peak_nominal(wl.headline)
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "peak_kind": kind}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["kernel"] = name
     roof["launch_ms"] = per_launch_ms

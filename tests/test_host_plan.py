@@ -47,3 +47,17 @@ def test_bad_arguments_are_rejected(lib):
     assert e.value.code == -1
     with pytest.raises(lib.RhifError):
         lib.rhif_plan_selfcheck((10, 10), 4, keep=1.5)
+
+
+def test_concurrent_planners_share_the_host_pool(lib):
+    """Batched factorizations plan several problems on concurrent host threads
+    that share the planner's thread pool (a caller that finds it busy runs its
+    loops itself): every concurrent plan must still match its definitions."""
+    from concurrent.futures import ThreadPoolExecutor
+    cases = [((255, 255), 8), ((300, 211), 8), ((127, 127), 8), ((400, 97), 16),
+             ((63, 63, 63), 8), ((511, 300), 8), ((31, 20, 17), 4), ((200, 200), 16)]
+    with ThreadPoolExecutor(max_workers=len(cases)) as ex:
+        futs = [ex.submit(lib.rhif_plan_selfcheck, ns, leaf, 0.5, 11 + i, len(ns) == 3)
+                for i, (ns, leaf) in enumerate(cases)]
+        levels = [f.result() for f in futs]
+    assert all(lv >= 2 for lv in levels)

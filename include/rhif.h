@@ -257,7 +257,9 @@ int rhif_skeletons(const rhif_handle* F, int level, int phase, int* count,
  * is counted per category; with timing on, CUDA events bracket each launch on
  * its stream and the elapsed times are summed when the statistics are read.
  * flops / bytes are the algorithmic work of the counted launches (see the
- * per-category definitions in the implementation notes). */
+ * per-category work counts kept beside each launch in the library: factor
+ * kernels count the flop formulas of Secs. 2.1-2.3, the application and vector
+ * kernels the bytes of the factor blocks and vectors they stream). */
 typedef struct {
   char name[32];
   int64_t launches;

@@ -1,6 +1,6 @@
 """The seeded input recipes (the synthetic stand-ins for the paper's random
 coefficient fields, Sec. 4): shapes, ranges, distributions and determinism,
-as the design notes state them."""
+as the generators' docstrings state them."""
 import numpy as np
 
 import workloads as W

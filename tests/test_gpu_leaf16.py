@@ -1,0 +1,246 @@
+"""GPU path vs the FP64 oracle at leaf 16 and coefficient contrast 1e8: the
+leaf size and field of the 1023^2 benchmark workload (Sec. 4 random fields,
+Sec. 3.1 quadtree with 16 x 16 leaves).
+
+At leaf 16 the dispatch takes kernels that leaf 4 and 8 never reach: the FP64
+factor eliminates 2D leaves with the streaming leaf kernel (boundary of up to
+64 DOFs), the FP32 factor with the 64-column one-warp-per-leaf kernel, and the
+application reads 15-wide leaf bands with inverted diagonal blocks.
+
+FP64 bar (Secs. 2.1-2.3, 3.1): identical unit sets and skeleton sets at every
+level except at logged pivot near-ties, the same root size |S_L|, F^{-1} x
+within ``FP64_APPLY_DIFF`` relative of the oracle's, and the apply error
+||F^{-1} A x - x|| / ||x|| within 2x of the oracle's.
+
+``FP64_APPLY_DIFF``: both sides apply the same operators (same skeletons) and
+differ only in summation order; each level step is a product with a stored
+triangular inverse or interpolation matrix, so the difference is bounded by
+(number of steps) x u_64 x (condition of the level operators).  At contrast
+1e8 the leaf interiors have condition numbers up to ~1e9 (field statistics of
+the 1023^2 recipe), giving about 1e-16 x 1e9 x a few = 1e-6 in the worst
+case; the observed difference is far smaller, and 1e-8 leaves a margin of
+10^2 over it while still failing on any wrong operator (a wrong skeleton,
+sign or index changes F^{-1} x at the level of the ID tolerance or more).
+
+FP32 factor: its skeletons may differ from the oracle's (pivots decided in
+FP32), so the comparison is on what F^{-1} does.  Every test states, on its
+output line, ||F32^{-1} x - Fo^{-1} x|| / ||Fo^{-1} x|| and the apply errors of
+both factors; the bar is the apply error within ``FP32_APPLY_FACTOR`` x the
+oracle's plus ``FP32_APPLY_FLOOR`` (FP32 rounding, u_32 = 6e-8, amplified by
+the Jacobi-scaled leaf conditioning, below 1e6 on 99.9% of the leaves of the
+1e8-contrast field, adds at most ~1e-2 relative to F^{-1} A x at tol 1e-6
+where the oracle's own error is ~4e-5).
+"""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+import workloads as W
+from oracle import fd, phif
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+FP64_APPLY_DIFF = 1e-8
+FP32_APPLY_FACTOR = 2.0
+FP32_APPLY_FLOOR = 1e-2
+
+
+def _dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+
+
+def _skeleton_map(units):
+    return {frozenset(int(g) for g in dofs): frozenset(int(g) for g in dofs[:k]) for dofs, k in units}
+
+
+def _oracle_skeletons(F, level, phase):
+    ph = F.levels[level].phases[phase]
+    return {frozenset(int(g) for g in u.e): frozenset(int(g) for g in u.sk) for u in ph.units}
+
+
+def _compare_skeletons(Fo, Fg):
+    """Unit sets equal at every level; skeleton sets equal until the first
+    level holding a logged near-tie.  Returns True if they diverged there."""
+    st = Fg.stats()
+    assert st["levels"] == len(Fo.levels)
+    for lvl in range(len(Fo.levels)):
+        diverged = False
+        for ph in range(len(Fo.levels[lvl].phases)):
+            go = _oracle_skeletons(Fo, lvl, ph)
+            gg = _skeleton_map(Fg.skeletons(lvl, ph))
+            assert set(go) == set(gg), f"unit sets differ at level {lvl} phase {ph}"
+            bad = [u for u in go if go[u] != gg[u]]
+            if bad:
+                assert Fo.ties, (f"{len(bad)} skeleton sets differ at level {lvl} phase {ph} "
+                                 "without a logged tie")
+                diverged = True
+        if diverged:
+            return True
+    assert st["root_size"] == Fo.S.size
+    return False
+
+
+def _leaf_kernels_ran(lib):
+    ks = lib.rhif_kernel_stats()
+    return ks.get("leaf_elim", {}).get("launches", 0), ks.get("apply_leaf_up", {}).get("launches", 0)
+
+
+def _apply_errors(A, Fo, Fg, x):
+    yo = phif.solve(Fo, x)
+    yg = Fg.apply(_dev(x)).cpu().numpy()
+    Ax = A @ x
+    eo = np.linalg.norm(phif.solve(Fo, Ax) - x) / np.linalg.norm(x)
+    eg = np.linalg.norm(Fg.apply(_dev(Ax)).cpu().numpy() - x) / np.linalg.norm(x)
+    diff = np.linalg.norm(yg - yo) / np.linalg.norm(yo)
+    return diff, eg, eo
+
+
+LEAF16 = [((127, 127), 1e-3), ((127, 127), 1e-6), ((255, 255), 1e-3), ((255, 255), 1e-6)]
+
+
+def _problem(ns, seed_extra=0):
+    a = W.log_uniform_pixels(ns, 1e-4, 1e4, seed=W.SEED_BASE + 16 + sum(ns) + seed_extra)
+    return a, fd.assemble(ns, a, 0.0)
+
+
+@pytest.mark.parametrize("ns,tol", LEAF16)
+def test_leaf16_fp64_matches_oracle(gpu_lib, ns, tol):
+    a, A = _problem(ns)
+    Fo = phif.factor(A, ns, 16, tol)
+    gpu_lib.rhif_reset_kernel_stats()
+    Fg = gpu_lib.rhif_factor(gpu_lib.rhif_assemble_fd(ns, _dev(a), 0.0), ns, 16, tol,
+                             precision="fp64")
+    diverged = _compare_skeletons(Fo, Fg)
+    x = np.random.default_rng(7).standard_normal(A.shape[0])
+    diff, eg, eo = _apply_errors(A, Fo, Fg, x)
+    leaf_launches, leaf_apply = _leaf_kernels_ran(gpu_lib)
+    print(f"\nleaf16 fp64 {ns} tol {tol:g}: |F^-1x - Fo^-1x|/|Fo^-1x| = {diff:.3e}, "
+          f"apply err gpu {eg:.3e} oracle {eo:.3e}, ties {len(Fo.ties)}")
+    assert leaf_launches >= 1 and leaf_apply >= 2
+    if not diverged:
+        assert diff <= FP64_APPLY_DIFF
+    assert eg <= 2 * eo + 1e-12
+    Fg.free()
+
+
+@pytest.mark.parametrize("ns,leaf,tol", [((127, 127), 8, 1e-3), ((127, 127), 16, 1e-3),
+                                         ((127, 127), 16, 1e-6), ((255, 255), 16, 1e-3),
+                                         ((255, 255), 16, 1e-6)])
+def test_fp32_factor_error_against_fp64_oracle(gpu_lib, ns, leaf, tol):
+    """The FP32 factor (leaf kernels with 32 / 64 boundary columns in one warp)
+    against the FP64 oracle: the F^{-1} x difference and the apply errors are
+    stated; the apply error stays within the FP32 bar."""
+    a, A = _problem(ns)
+    Fo = phif.factor(A, ns, leaf, tol)
+    Fg = gpu_lib.rhif_factor(gpu_lib.rhif_assemble_fd(ns, _dev(a), 0.0), ns, leaf, tol,
+                             precision="fp32")
+    x = np.random.default_rng(8).standard_normal(A.shape[0])
+    diff, eg, eo = _apply_errors(A, Fo, Fg, x)
+    # skeleton agreement, stated: share of units whose skeleton set is the oracle's
+    same = tot = 0
+    for lvl in range(len(Fo.levels)):
+        go = _oracle_skeletons(Fo, lvl, 0)
+        gg = _skeleton_map(Fg.skeletons(lvl, 0))
+        tot += len(go)
+        same += sum(1 for u in go if gg.get(u) == go[u])
+    print(f"\nfp32 leaf {leaf} {ns} tol {tol:g}: |F32^-1x - Fo^-1x|/|Fo^-1x| = {diff:.3e}, "
+          f"apply err fp32 {eg:.3e} oracle {eo:.3e}, skeleton sets equal {same}/{tot}")
+    assert np.isfinite(diff) and diff < 1.0
+    assert eg <= FP32_APPLY_FACTOR * eo + FP32_APPLY_FLOOR
+    Fg.free()
+
+
+def _amplification(A, u):
+    """||A^{-1}|| ||f|| / ||u|| for f = A u, with ||A^{-1}|| = 1 / lambda_min(A)
+    (A SPD) from an eigensolver in shift-invert mode about 0."""
+    lam = spla.eigsh(A.tocsc(), k=1, sigma=0.0, which="LM", return_eigenvectors=False)[0]
+    return np.linalg.norm(A @ u) / (lam * np.linalg.norm(u))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_pcg_solution_within_1e10_of_direct_solve(gpu_lib, precision):
+    """The 127^2 workload: the PCG solution within 1e-10 relative of the sparse
+    direct solve.  A relative residual r bounds the error by amp x r with
+    amp = ||A^{-1}|| ||f|| / ||u||, so PCG runs to rtol = 1e-10 / (2 amp),
+    clamped below by 10x the direct solve's own residual (the floor both
+    sides share); the bar is max(1e-10, 2 amp x floor)."""
+    p = W.config_problem(0)
+    A = fd.assemble(p.ns, p.a, p.b)
+    ud = spla.spsolve(A.tocsc(), p.f)
+    floor = np.linalg.norm(p.f - A @ ud) / np.linalg.norm(p.f)
+    amp = _amplification(A, ud)
+    rtol = max(1e-10 / (2 * amp), 10 * floor)
+    Fg = gpu_lib.rhif_factor(gpu_lib.rhif_assemble_fd(p.ns, _dev(p.a), p.b), p.ns, p.leaf, p.tol,
+                             precision=precision)
+    u, its, rr = Fg.pcg(_dev(p.f), rtol=rtol, maxit=300)
+    u = u.cpu().numpy()
+    err = np.linalg.norm(u - ud) / np.linalg.norm(ud)
+    bar = max(1e-10, 2 * amp * floor)
+    print(f"\n127^2 {precision}: amp {amp:.3e}, direct relres {floor:.2e}, pcg rtol {rtol:.2e}, "
+          f"its {its[0]}, relres {rr[0]:.2e}, |u - u_direct|/|u_direct| = {err:.3e} (bar {bar:.1e})")
+    assert rr[0] <= 1.5 * rtol
+    assert err <= bar
+    Fg.free()
+
+
+# ---------------------------------------------------------------------------
+# The 1023^2 benchmark workload itself, in the launch configuration the
+# benchmark times (default options, leaf 16, tol 1e-3).  The oracle factors it
+# once (about a minute), shared by the tests below.
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def full_size():
+    p = W.config_problem(1)
+    A = fd.assemble(p.ns, p.a, p.b)
+    Fo = phif.factor(A, p.ns, p.leaf, p.tol)
+    x = np.random.default_rng(11).standard_normal(A.shape[0])
+    yo = phif.solve(Fo, x)
+    eo = np.linalg.norm(phif.solve(Fo, A @ x) - x) / np.linalg.norm(x)
+    return p, A, Fo, x, yo, eo
+
+
+def test_full_size_fp64_matches_oracle(gpu_lib, full_size):
+    p, A, Fo, x, yo, eo = full_size
+    Fg = gpu_lib.rhif_factor(gpu_lib.rhif_assemble_fd(p.ns, _dev(p.a), p.b), p.ns, p.leaf, p.tol,
+                             precision="fp64")
+    diverged = _compare_skeletons(Fo, Fg)
+    yg = Fg.apply(_dev(x)).cpu().numpy()
+    diff = np.linalg.norm(yg - yo) / np.linalg.norm(yo)
+    eg = np.linalg.norm(Fg.apply(_dev(A @ x)).cpu().numpy() - x) / np.linalg.norm(x)
+    # sampled element-wise check: 4096 seeded entries of F^{-1} x
+    idx = np.random.default_rng(12).choice(A.shape[0], 4096, replace=False)
+    elem = np.max(np.abs(yg[idx] - yo[idx])) / np.max(np.abs(yo))
+    print(f"\n1023^2 fp64: |F^-1x - Fo^-1x|/|Fo^-1x| = {diff:.3e}, sampled max abs diff / max "
+          f"{elem:.3e}, apply err gpu {eg:.3e} oracle {eo:.3e}, ties {len(Fo.ties)}")
+    if not diverged:
+        assert diff <= FP64_APPLY_DIFF and elem <= FP64_APPLY_DIFF
+    assert eg <= 2 * eo + 1e-12
+    u, its, rr = Fg.pcg(_dev(p.f), rtol=1e-10)
+    assert rr[0] <= 1.5e-10
+    Fg.free()
+
+
+def test_full_size_fp32_error_against_oracle(gpu_lib, full_size):
+    p, A, Fo, x, yo, eo = full_size
+    Fg = gpu_lib.rhif_factor(gpu_lib.rhif_assemble_fd(p.ns, _dev(p.a), p.b), p.ns, p.leaf, p.tol,
+                             precision="fp32")
+    yg = Fg.apply(_dev(x)).cpu().numpy()
+    diff = np.linalg.norm(yg - yo) / np.linalg.norm(yo)
+    eg = np.linalg.norm(Fg.apply(_dev(A @ x)).cpu().numpy() - x) / np.linalg.norm(x)
+    u, its, rr = Fg.pcg(_dev(p.f), rtol=1e-10)
+    # the PCG solution with the FP32 factor against the one with the oracle's
+    # FP64 factor as preconditioner (both to relres 1e-10)
+    uo, it_o, _ = phif.pcg(A, p.f, M=lambda r: phif.solve(Fo, r), rtol=1e-10)
+    du = np.linalg.norm(u.cpu().numpy() - uo) / np.linalg.norm(uo)
+    print(f"\n1023^2 fp32: |F32^-1x - Fo^-1x|/|Fo^-1x| = {diff:.3e}, apply err fp32 {eg:.3e} "
+          f"oracle {eo:.3e}; pcg its fp32 {its[0]} oracle {it_o}, relres {rr[0]:.2e}, "
+          f"|u32 - u_oracle|/|u_oracle| = {du:.3e}")
+    assert eg <= FP32_APPLY_FACTOR * eo + FP32_APPLY_FLOOR
+    assert rr[0] <= 1.5e-10
+    # both solutions have relres <= 1e-10; amp ~5e2 on this field bounds their
+    # distance by ~1e-7
+    assert du <= 1e-6
+    Fg.free()

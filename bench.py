@@ -63,6 +63,10 @@ def _args():
     p.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     p.add_argument("--fp64-steps", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--tol", type=float, default=None,
+                   help="ID tolerance of the single-problem workloads (default: the workload's)")
+    p.add_argument("--skeleton-growth", action="store_true",
+                   help="3D root-size study with and without edge skeletonization (Remark 3.1)")
     p.add_argument("--paper-tables", action="store_true",
                    help="HIF vs PHIF study on the paper's quantized field (Sec. 4 tables)")
     return p.parse_args()
@@ -400,13 +404,15 @@ class Workload:
     """One step of the hot path with inputs resident on the device (`step`),
     and end to end from pinned host buffers (`e2e_step`)."""
 
-    def __init__(self, key, rhif, W, torch, dev):
+    def __init__(self, key, rhif, W, torch, dev, tol=None):
         self.key, self.rhif, self.W, self.torch, self.dev = key, rhif, W, torch, dev
         self.headline = "fp64" if key == "c1" else "fp32"
         self.rtol = 1e-12 if key in ("c1", "c5") else RTOL
         t = torch
         if key in ("c1", "c2", "c3"):
             p = W.config_problem({"c1": 0, "c2": 1, "c3": 2}[key])
+            if tol is not None:
+                p.tol = float(tol)
             self.p = p
             self.dofs = p.n
             self.edge = key == "c3"
@@ -447,10 +453,11 @@ class Workload:
             self.h2d = (log_a.size + 2 * f.size) * 8
             self.d2h = log_a.size * 8
 
-    def _solve_one(self, a, f, precision):
+    def _solve_one(self, a, f, precision, precond=True):
         r, p = self.rhif, self.p
         csr = r.rhif_assemble_fd(p.ns, a, p.b)
-        F = r.rhif_factor(csr, p.ns, p.leaf, p.tol, precision=precision, edge_skel_3d=self.edge)
+        F = r.rhif_factor(csr, p.ns, p.leaf, p.tol, precision=precision, edge_skel_3d=self.edge,
+                          precondition=precond)
         u, its, rr = F.pcg(f, rtol=self.rtol, maxit=1000)
         F.free()
         return u, its, rr
@@ -502,7 +509,10 @@ class Workload:
         self.u_h.copy_(u, non_blocking=True)
 
     def config(self):
-        c = {"workload": WORKLOADS[self.key], "dofs_per_step": self.dofs, "rtol": self.rtol}
+        name = WORKLOADS[self.key]
+        if self.key in ("c1", "c2", "c3") and self.p.tol != 1e-3:
+            name = name.replace("tol1e-3", f"tol{self.p.tol:g}")
+        c = {"workload": name, "dofs_per_step": self.dofs, "rtol": self.rtol}
         if self.key in ("c1", "c2", "c3"):
             c.update(N=self.p.n, leaf=self.p.leaf, tol=self.p.tol)
         elif self.key == "c4":
@@ -510,6 +520,25 @@ class Workload:
         else:
             c.update(N=self.dofs, leaf=16, tol=1e-6, step="forward PCG + adjoint PCG + gradient")
         return c
+
+
+def local_precond_compare(wl, timed) -> dict:
+    """The headline step with each local preconditioner of the separator
+    groups (none = HIF, diagonal, block Jacobi = PHIF) and factor precision,
+    outside the headline's timed region: DOFs/s and PCG iterations.  A factor
+    that breaks down (not SPD, as HIF does on high-contrast fields, Sec. 4) is
+    reported, not raised."""
+    out = {}
+    for prec in ("fp32", "fp64"):
+        for mode in ("none", "diag", "block"):
+            key = f"{mode}_{prec}"
+            try:
+                sec, (u, its, rr), _ = timed(lambda: wl._solve_one(wl.a_d, wl.f_d, prec, mode), 3, 1)
+                out[key] = {"value": wl.dofs * 3 / sec, "ms_per_step": 1e3 * sec / 3,
+                            "pcg_iters": its[0], "relres": rr[0]}
+            except Exception as e:   # noqa: BLE001 - reported in the line
+                out[key] = {"error": str(e).split(":")[0] + ": " + str(e).split(":")[-1][:120]}
+    return out
 
 
 def step_breakdown(wl, torch) -> dict:
@@ -588,7 +617,7 @@ def gpu_arm(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     rhif.load()
     dev = torch.device("cuda", local)
-    wl = Workload(args.workload, rhif, W, torch, dev)
+    wl = Workload(args.workload, rhif, W, torch, dev, args.tol)
     stream = torch.cuda.current_stream()
 
     def barrier():
@@ -697,11 +726,17 @@ def gpu_arm(args):
         result["mixed_over_fp64"] = value / value_o
     if args.workload in ("c1", "c2", "c3"):
         result["breakdown"] = step_breakdown(wl, torch)
+    if args.workload == "c2":
+        result["local_precond"] = local_precond_compare(wl, timed)
     if args.workload == "c4":
         result["rhs_dofs_per_s"] = value * 32
     if args.workload == "c5":
         result["loss"] = rr[0]
         result.pop("relres")
+        result.pop("pcg_iters")
+        result[other]["loss"] = result[other].pop("relres")
+        result[other].pop("pcg_iters")
+        result[other]["grad_rel_diff_vs_headline"] = result[other].pop("rel_diff_vs_headline")
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         body, side, extra, desc = _SAMPLES[args.workload]
         save = os.path.join(tempfile.gettempdir(), f"rhif_oracle_u_{os.getpid()}.npy") \
@@ -722,10 +757,11 @@ def gpu_arm(args):
 
 def paper_tables(args):
     """The structure of the paper's Tables 1-2 on this GPU: for the quantized
-    high-contrast field (Sec. 4) at 1023^2 (leaf 16) and 31^3 / 63^3 (leaf 8,
-    faces + edges), HIF and PHIF at tol 1e-3 and 1e-6 (FP64 factors): factor
-    time, root size, e_s (power iteration, 1e-2 relative change) and PCG
-    iterations to relres 1e-12.  One JSON line."""
+    high-contrast field (Sec. 4) at 1023^2 (leaf 16; tol 1e-3, 1e-4, 1e-6,
+    1e-8 as in Table 1) and 31^3 / 63^3 (leaf 8, faces + edges; tol 1e-3,
+    1e-6), HIF, PHIF with the diagonal local preconditioner and PHIF (FP64
+    factors): factor time, root size, e_s (power iteration, 1e-2 relative
+    change) and PCG iterations to relres 1e-12.  One JSON line."""
     import numpy as np
     import torch
 
@@ -733,6 +769,7 @@ def paper_tables(args):
     import workloads as W
     rhif.load()
     rows = []
+    tols = {2: (1e-3, 1e-4, 1e-6, 1e-8), 3: (1e-3, 1e-6)}
     for ns, leaf in (((1023, 1023), 16), ((31, 31, 31), 8), ((63, 63, 63), 8)):
         a = torch.as_tensor(W.paper_quantized_field(ns, seed=W.SEED_BASE + 5), device="cuda")
         n = int(np.prod(ns))
@@ -740,10 +777,10 @@ def paper_tables(args):
         x0 = torch.as_tensor(np.random.Generator(np.random.PCG64(7)).standard_normal(n),
                              device="cuda")
         csr = rhif.rhif_assemble_fd(ns, a, 0.0)
-        for tol in (1e-3, 1e-6):
-            for pre in (False, True):
+        for tol in tols[len(ns)]:
+            for pre in ("none", "diag", "block"):
                 row = {"grid": "x".join(map(str, ns)), "N": n, "leaf": leaf, "tol": tol,
-                       "method": "PHIF" if pre else "HIF"}
+                       "method": {"none": "HIF", "diag": "PHIF-diag", "block": "PHIF"}[pre]}
                 try:
                     torch.cuda.synchronize()
                     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -765,6 +802,45 @@ def paper_tables(args):
     print(json.dumps({"paper_tables": rows}))
 
 
+def skeleton_growth(args):
+    """Root size |S_L| of 3D factors with and without edge skeletonization
+    (Remark 3.1) as the grid grows: i.i.d. log-uniform [1e-3, 1e3] field,
+    b = 1e-2, leaf 8, tol 1e-3, FP64 PHIF; per-level active DOF counts, factor
+    time and memory, PCG iterations to relres 1e-10.  One JSON line."""
+    import numpy as np
+    import torch
+
+    import paper_1808_01364_gb300 as rhif
+    import workloads as W
+    rhif.load()
+    rows = []
+    for side in (15, 31, 63, 127):
+        ns = (side,) * 3
+        a = torch.as_tensor(W.log_uniform_pixels(ns, 1e-3, 1e3, W.SEED_BASE + 2), device="cuda")
+        f = torch.as_tensor(W.normal_rhs(ns, W.SEED_BASE + 7), device="cuda")
+        csr = rhif.rhif_assemble_fd(ns, a, 1e-2)
+        for edge in (False, True):
+            row = {"grid": f"{side}^3", "N": side ** 3, "edge_skel": edge}
+            try:
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                F = rhif.rhif_factor(csr, ns, 8, 1e-3, precision="fp64", edge_skel_3d=edge)
+                e1.record()
+                e1.synchronize()
+                st = F.stats()
+                _, its, rr = F.pcg(f, rtol=1e-10, maxit=1000, check=False)
+                row.update(factor_ms=e0.elapsed_time(e1), root=st["root_size"],
+                           active=[int(x) for x in st["active"][:st["levels"]]],
+                           pcg_iters=its[0], relres=rr[0], factor_gb=st["factor_bytes"] / 1e9)
+                F.free()
+            except rhif.RhifError as e:
+                row["failed"] = str(e)[:120]
+            rows.append(row)
+            torch.cuda.empty_cache()
+    print(json.dumps({"skeleton_growth": rows}))
+
+
 # default timed steps of the GPU arm: about half a second of work, so that
 # several clock samples (100 ms period) fall inside the timed region
 DEFAULT_STEPS = {"c1": 100, "c2": 40, "c3": 5, "c4": 3, "c5": 40}
@@ -774,6 +850,9 @@ def main():
     args = _args()
     if args.steps is None:
         args.steps = 5 if args.impl == "reference" else DEFAULT_STEPS[args.workload]
+    if args.skeleton_growth:
+        skeleton_growth(args)
+        return
     if args.paper_tables:
         paper_tables(args)
         return

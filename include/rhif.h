@@ -44,6 +44,7 @@ enum {
 };
 
 enum { RHIF_FP64 = 0, RHIF_MIXED_FP32 = 1 };  /* precision of the stored factor */
+enum { RHIF_PRECOND_NONE = 0, RHIF_PRECOND_BLOCK = 1, RHIF_PRECOND_DIAG = 2 };
 enum { RHIF_SOLVE = 0, RHIF_MATVEC = 1 };      /* apply F^{-1}; F (reserved, see rhif_apply) */
 
 typedef struct {
@@ -64,7 +65,13 @@ typedef struct {
 
 typedef struct {
   int precision;      /* RHIF_FP64 (default) or RHIF_MIXED_FP32 */
-  int precondition;   /* 1 = PHIF (default, Sec. 3); 0 = plain HIF (C_l = I) */
+  /* precondition: local preconditioner C_l applied to every separator group
+   *   before skeletonization.  1 = block Jacobi by the Cholesky factor of the
+   *   group's diagonal block (PHIF, Sec. 2.3; default); 0 = none (plain HIF,
+   *   C_l = I); 2 = diagonal, C_g = diag(A_gg)^{-1/2} (the cheaper local
+   *   preconditioner the concluding section names in place of block
+   *   Cholesky).  Other values: RHIF_ERR_BAD_ARG. */
+  int precondition;
   int edge_skel_3d;   /* 3D only: also precondition and skeletonize edges (Remark 3.1) */
   /* Scheduling only (the result does not depend on them beyond rounding order):
    * big_front: front order (interior + boundary DOFs of a cell) from which a
@@ -186,7 +193,8 @@ int rhif_apply(const rhif_handle* F, int op, int nrhs, const double* x, int64_t 
  * before any work is queued.  The first call on a device looks up the array's
  * device address (cudaGetSymbolAddress) and should come before any stream
  * capture on that device.  All calls share the array: calls that overlap on
- * the GPU race and must be ordered by the caller. */
+ * the GPU race and must be ordered by the caller.  Its launches are not
+ * counted by the kernel instrumentation (rhif_kernel_stats). */
 int rhif_apply_noalloc(const rhif_handle* F, int nrhs, const double* x, int64_t ldx,
                        double* y, int64_t ldy, void* stream);
 

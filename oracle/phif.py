@@ -150,15 +150,23 @@ def _block(idx_r, idx_c, M):
     return r, c, np.asarray(M).ravel()
 
 
-def _precondition(A, active, grps, N, where):
-    """Block Jacobi preconditioning, Sec. 2.3: A <- C^T A C, C = diag(L_g^{-T})."""
+def _precondition(A, active, grps, N, where, diagonal=False):
+    """Block Jacobi preconditioning, Sec. 2.3: A <- C^T A C, C = diag(L_g^{-T}),
+    L_g = chol(A_gg).  ``diagonal``: the local preconditioner of the concluding
+    section that replaces block Cholesky by the diagonal, L_g = diag(A_gg)^{1/2}."""
     recs = []
     rows, cols, vals = [], [], []
     covered = np.zeros(N, dtype=bool)
     for key, t, g in grps:
         _, Agg, _ = _gather_cols(A, g, active)
         try:
-            Lg = cholesky(Agg)
+            if diagonal:
+                dg = np.diag(Agg)
+                if not np.all(dg > 0.0):
+                    raise NotSPD("nonpositive diagonal")
+                Lg = np.diag(np.sqrt(dg))
+            else:
+                Lg = cholesky(Agg)
         except NotSPD:
             raise NotSPD(f"{where}: preconditioning block {key} not SPD") from None
         recs.append(GroupRec(g, Lg))
@@ -210,9 +218,12 @@ def _skeletonize(A, active, units, tol, N, where, ties):
     return _mask(A, active), recs
 
 
-def factor(A, ns, leaf: int, tol: float, precondition: bool = True,
+def factor(A, ns, leaf: int, tol: float, precondition=True,
            edge_skel: bool = False, cell_order=None, snapshots: bool = False) -> Factor:
     """PHIF (``precondition=True``) or HIF (``False``) factorization of SPD ``A``.
+
+    ``precondition="diag"``: PHIF with the diagonal local preconditioner of
+    the concluding section in place of block Cholesky.
 
     ``cell_order``: optional callable ``(level, n_cells) -> permutation`` to
     process the cells of a level in another order (the result must not change,
@@ -222,6 +233,7 @@ def factor(A, ns, leaf: int, tol: float, precondition: bool = True,
     ns = tuple(int(n) for n in ns)
     d = len(ns)
     N = A.shape[0]
+    diagonal = precondition == "diag"
     L = tree.num_levels(ns, leaf)
     A = sp.csc_matrix(A, dtype=np.float64, copy=True)
     A.sort_indices()
@@ -257,7 +269,7 @@ def factor(A, ns, leaf: int, tol: float, precondition: bool = True,
         phases = []
         seps = tree.groups(ns, np.nonzero(active)[0], width)
         if precondition:
-            A, grecs = _precondition(A, active, seps, N, f"level {lvl}")
+            A, grecs = _precondition(A, active, seps, N, f"level {lvl}", diagonal)
         else:
             grecs = []
         if snapshots:
@@ -269,7 +281,7 @@ def factor(A, ns, leaf: int, tol: float, precondition: bool = True,
         if d == 3 and edge_skel:
             seps2 = [g for g in tree.groups(ns, np.nonzero(active)[0], width) if g[1] >= 2]
             if precondition:
-                A, grecs2 = _precondition(A, active, seps2, N, f"level {lvl} edges")
+                A, grecs2 = _precondition(A, active, seps2, N, f"level {lvl} edges", diagonal)
             else:
                 grecs2 = []
             units2 = [g for g in seps2 if g[1] == 2]

@@ -527,7 +527,10 @@ def _opts(precision="fp64", precondition=True, edge_skel_3d=False, big_front=0,
     o = Opts()
     _lib.rhif_default_opts(ctypes.byref(o))
     o.precision = {"fp64": RHIF_FP64, "fp32": RHIF_MIXED_FP32, "mixed": RHIF_MIXED_FP32}[precision]
-    o.precondition = 1 if precondition else 0
+    if isinstance(precondition, str):
+        o.precondition = {"none": 0, "hif": 0, "block": 1, "phif": 1, "diag": 2}[precondition]
+    else:
+        o.precondition = 1 if precondition else 0
     o.edge_skel_3d = 1 if edge_skel_3d else 0
     o.big_front = int(big_front)
     o.big_frame = int(big_frame)

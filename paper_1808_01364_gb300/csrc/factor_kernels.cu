@@ -1030,7 +1030,10 @@ __global__ void k_front_inv_store(LevelDev Lv, const T* X, const int64_t* xoff) 
 // block Jacobi preconditioning (Sec. 2.3)
 // ---------------------------------------------------------------------------
 
-// L_g = chol(sum over the cells holding g of their diagonal block of g)
+// L_g = chol(sum over the cells holding g of their diagonal block of g); with
+// the diagonal local preconditioner (Sec. 5: any local preconditioner may
+// replace block Cholesky) only the diagonal of that block is assembled, so
+// L_g = diag(A_gg)^{1/2} and every later step sees a diagonal L_g.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_precond_diag(LevelDev Lv, PhaseDev Ph, int* status) {
   extern __shared__ unsigned char smraw[];
@@ -1042,7 +1045,7 @@ __global__ void __launch_bounds__(kThreads) k_precond_diag(LevelDev Lv, PhaseDev
   for (int64_t idx = threadIdx.x; idx < (int64_t)sz * sz; idx += blockDim.x) {
     const int i = (int)(idx % sz), j = (int)(idx / sz);
     T s = T(0);
-    if (i >= j) {
+    if (i == j || (i > j && !Ph.diag_only)) {
       for (int k = Lv.group_cell_off[g]; k < Lv.group_cell_off[g + 1]; ++k) {
         int ld;
         const T* fr = frame_of<T>(Lv, Lv.group_cell[k], &ld);
@@ -1079,7 +1082,7 @@ k_precond_diag_warp(LevelDev Lv, PhaseDev Ph, int* status) {
   for (int idx = lane; idx < sz * sz; idx += 32) {
     const int i = idx % sz, j = idx / sz;
     T v = T(0);
-    if (i >= j)
+    if (i == j || (i > j && !Ph.diag_only))
       for (int k = Lv.group_cell_off[g]; k < Lv.group_cell_off[g + 1]; ++k) {
         int ld;
         const T* fr = frame_of<T>(Lv, Lv.group_cell[k], &ld);
@@ -1161,6 +1164,12 @@ __global__ void __launch_bounds__(kThreads) k_precond_scale(LevelDev Lv, PhaseDe
     const int sz = Lv.group_size[g];
     const int pos = Lv.seg_pos[s];
     T* col = Fr + (int64_t)j * ld + pos;
+    if (Ph.diag_only) {   // diagonal L_g: scale the rows
+      const T* Dg = (const T*)(Ph.Linv ? Ph.Linv : Ph.Lbuf) + Ph.pre_off[pi];
+      for (int a = 0; a < sz; ++a)
+        col[a] = Ph.Linv ? col[a] * Dg[a + (int64_t)a * sz] : col[a] / Dg[a + (int64_t)a * sz];
+      continue;
+    }
     if (Ph.Linv) {   // col <- L_g^{-1} col as a product, bottom up in place
       const T* Xg = (const T*)Ph.Linv + Ph.pre_off[pi];
       for (int a = sz - 1; a >= 0; --a) {
@@ -1187,6 +1196,13 @@ __global__ void __launch_bounds__(kThreads) k_precond_scale(LevelDev Lv, PhaseDe
     const int sz = Lv.group_size[g];
     const int pos = Lv.seg_pos[s];
     T* row = Fr + i + (int64_t)pos * ld;
+    if (Ph.diag_only) {   // diagonal L_g: scale the columns
+      const T* Dg = (const T*)(Ph.Linv ? Ph.Linv : Ph.Lbuf) + Ph.pre_off[pi];
+      for (int a = 0; a < sz; ++a)
+        row[(int64_t)a * ld] = Ph.Linv ? row[(int64_t)a * ld] * Dg[a + (int64_t)a * sz]
+                                       : row[(int64_t)a * ld] / Dg[a + (int64_t)a * sz];
+      continue;
+    }
     if (Ph.Linv) {   // row <- row L_g^{-T} as a product, right to left in place
       const T* Xg = (const T*)Ph.Linv + Ph.pre_off[pi];
       for (int a = sz - 1; a >= 0; --a) {

@@ -276,6 +276,7 @@ struct rhif_handle {
   rhif::GeoDev gd{};
   int precision = RHIF_FP64;
   bool precondition = true, edge_skel = false;
+  bool precond_diag = false;   // diagonal local preconditioner in place of block Cholesky
   int big_front = 0, big_frame = 0;   // many-CTA thresholds (see rhif_opts)
   int skel_cluster = 0;
   bool skel_warp = true;   // small units: one warp each
@@ -433,6 +434,7 @@ static int upload_level(rhif_handle* H, LevelStore& S, size_t elem) {
     D.unit_type = ph.unit_type;
     D.pre_min_type = ph.pre_min_type;
     D.npre = (int)ph.pre_group.size();
+    D.diag_only = H->precond_diag ? 1 : 0;
     D.pre_group = (const int*)(b + po[i].pg);
     D.pre_off = (const int64_t*)(b + po[i].po);
     D.group_pre = (const int*)(b + po[i].gp);
@@ -698,14 +700,14 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
       double dflops = 0.0, sflops = 0.0;
       for (int gi : ph.pre_group) {
         const double g = P.group_size[gi];
-        dflops += g * g * g / 3.0;
+        dflops += H->precond_diag ? g : g * g * g / 3.0;
       }
       for (int c = 0; c < P.ncell(); ++c)
         for (int q = P.seg_off[c]; q < P.seg_off[c + 1]; ++q) {
           const int gi = P.seg_group[q];
           if (ph.group_pre[gi] < 0) continue;
           const double g = P.group_size[gi];
-          sflops += 2.0 * g * g * P.nB[c];
+          sflops += H->precond_diag ? 2.0 * g * P.nB[c] : 2.0 * g * g * P.nB[c];
         }
       Packer scale_tab;
       void* scale_dev = nullptr;
@@ -713,8 +715,10 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
         const bool fits = (size_t)P.max_nB * P.max_nB * elem <= 200 * 1024;
         // default: many CTAs once the frame leaves shared memory, and for the
         // FP32 factor from 96 boundary DOFs (few, large cells per level)
-        const bool big = H->big_frame > 0 ? P.max_nB >= H->big_frame
-                                          : (!fits || (elem == 4 && P.max_nB >= 96));
+        // (a diagonal L_g scales rows and columns in place: one CTA per cell)
+        const bool big = H->precond_diag ? false
+                         : H->big_frame > 0 ? P.max_nB >= H->big_frame
+                                            : (!fits || (elem == 4 && P.max_nB >= 96));
         int64_t blocks = 0;
         if (big) {   // large frames: tile products with explicit inverses over many CTAs
           std::vector<int> task;
@@ -1154,7 +1158,10 @@ int rhif_factor(const rhif_csr* A, const rhif_grid* g, int leaf, double tol, con
   if (H->G.L > 20) return fail(RHIF_ERR_BAD_ARG, "too many levels");
   H->gd = geo_dev(H->G);
   H->precision = o->precision;
+  if (o->precondition < 0 || o->precondition > 2)
+    return fail(RHIF_ERR_BAD_ARG, "precondition must be 0 (HIF), 1 (block Jacobi) or 2 (diagonal)");
   H->precondition = o->precondition != 0;
+  H->precond_diag = o->precondition == 2;
   H->edge_skel = (g->dim == 3) && o->edge_skel_3d;
   H->big_front = o->big_front == 0 ? kBigFront : (o->big_front < 0 ? INT_MAX : o->big_front);
   H->big_frame = o->big_frame < 0 ? INT_MAX : o->big_frame;

@@ -65,6 +65,7 @@ struct LevelDev {
 struct PhaseDev {
   int unit_type, pre_min_type;
   int npre;
+  int diag_only;            // diagonal local preconditioner: L_g = diag(A_gg)^{1/2}
   const int* pre_group;
   const int64_t* pre_off;
   const int* group_pre;    // per group of the level: index into pre_group or -1

@@ -91,6 +91,10 @@ def test_factor_rejects_bad_arguments_before_any_device_work(rhif):
     bad = rhif._opts()
     bad.precision = 7
     assert call(opts=ctypes.byref(bad)) == BAD_ARG
+    for v in (-1, 3):   # 0 HIF, 1 block Jacobi, 2 diagonal
+        bad = rhif._opts()
+        bad.precondition = v
+        assert call(opts=ctypes.byref(bad)) == BAD_ARG
     wrong_rows, _k2 = _csr(rhif, N - 1, 5 * N)
     assert call(A_=ctypes.byref(wrong_rows)) == BAD_ARG
     too_few, _k3 = _csr(rhif, N, N - 1)

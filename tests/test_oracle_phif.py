@@ -43,12 +43,19 @@ def _explicit_level(ns, leaf, lvl, snap, level_rec, precondition=True):
         E[np.ix_(I, I)] = np.linalg.inv(Lc).T
         E[np.ix_(I, rest)] = -np.linalg.solve(A0[np.ix_(I, I)], A0[np.ix_(rest, I)].T)
     A1, act1 = _full(snap["A1"])
-    # C_l = block diag of L_g^{-T} over the separator groups, Eq. (2.3)
+    # C_l = block diag of L_g^{-T} over the separator groups, Eq. (2.3); the
+    # diagonal local preconditioner uses diag(A_gg)^{-1/2} instead
     C = np.eye(N)
     if precondition:
         for _, _, g in tree.groups(ns, np.nonzero(act1)[0], width):
-            C[np.ix_(g, g)] = np.linalg.inv(np.linalg.cholesky(A1[np.ix_(g, g)])).T
+            C[np.ix_(g, g)] = _local_precond(A1[np.ix_(g, g)], precondition)
     return E, C, A0, A1
+
+
+def _local_precond(Agg, mode):
+    if mode == "diag":
+        return np.diag(1.0 / np.sqrt(np.diag(Agg)))
+    return np.linalg.inv(np.linalg.cholesky(Agg)).T
 
 
 def _explicit_skeletonization(A2, units):
@@ -85,6 +92,8 @@ def _explicit_skeletonization(A2, units):
     ((15, 15), 4, 1e-4, False, False),    # plain HIF
     ((7, 7, 7), 4, 1e-3, True, True),     # 3D, faces then edges (Remark 3.1)
     ((11, 11, 11), 4, 1e-3, False, True),  # 3D padded, two levels
+    ((15, 15), 4, 1e-4, False, "diag"),   # diagonal local preconditioner
+    ((7, 7, 7), 4, 1e-3, True, "diag"),
 ])
 def test_explicit_operator_products(ns, leaf, tol, edge_skel, precond):
     A = _problem(ns, b=0.01 if len(ns) == 3 else 0.0)
@@ -97,7 +106,10 @@ def test_explicit_operator_products(ns, leaf, tol, edge_skel, precond):
         np.testing.assert_allclose(E.T @ A0 @ E, A1, atol=1e-12 * scale)
         A2, act2 = _full(snap["A2"])
         np.testing.assert_allclose(C.T @ A1 @ C, A2, atol=1e-12 * np.abs(A1).max())
-        if precond:   # unit block diagonal (Sec. 2.3)
+        if precond == "diag":   # unit diagonal
+            for _, _, g in tree.groups(ns, np.nonzero(act2)[0], leaf << lvl):
+                np.testing.assert_allclose(np.diag(A2[np.ix_(g, g)]), np.ones(g.size), atol=1e-12)
+        elif precond:   # unit block diagonal (Sec. 2.3)
             for _, _, g in tree.groups(ns, np.nonzero(act2)[0], leaf << lvl):
                 np.testing.assert_allclose(A2[np.ix_(g, g)], np.eye(g.size), atol=1e-12)
         Ktot = np.eye(N)
@@ -107,7 +119,7 @@ def test_explicit_operator_products(ns, leaf, tol, edge_skel, precond):
                 Mf = M.copy()
                 C2 = np.eye(N)
                 for g in ph.groups:
-                    C2[np.ix_(g.g, g.g)] = np.linalg.inv(np.linalg.cholesky(Mf[np.ix_(g.g, g.g)])).T
+                    C2[np.ix_(g.g, g.g)] = _local_precond(Mf[np.ix_(g.g, g.g)], precond)
                 M = C2.T @ Mf @ C2
                 Ktot = Ktot @ C2
             K, M, pert = _explicit_skeletonization(M, ph.units)
@@ -150,14 +162,15 @@ def test_skeleton_block_form_after_preconditioning():
             np.testing.assert_allclose(blk, want, atol=1e-11)
 
 
-@pytest.mark.parametrize("ns,leaf,edge_skel", [
-    ((7, 7), 4, False), ((15, 15), 4, False), ((31, 31), 8, False), ((20, 23), 4, False),
-    ((7, 7, 7), 4, False), ((15, 15, 15), 4, True), ((9, 6, 7), 4, False),
+@pytest.mark.parametrize("ns,leaf,edge_skel,precond", [
+    ((7, 7), 4, False, True), ((15, 15), 4, False, True), ((31, 31), 8, False, True),
+    ((20, 23), 4, False, True), ((7, 7, 7), 4, False, True), ((15, 15, 15), 4, True, True),
+    ((9, 6, 7), 4, False, True), ((20, 23), 4, False, "diag"), ((7, 7, 7), 4, True, "diag"),
 ])
-def test_tol_zero_is_exact(ns, leaf, edge_skel):
+def test_tol_zero_is_exact(ns, leaf, edge_skel, precond):
     """tol = 0: nothing is dropped, F = A and F^{-1} A = I to roundoff."""
     A = _problem(ns, b=0.01)
-    F = phif.factor(A, ns, leaf, 0.0, edge_skel=edge_skel)
+    F = phif.factor(A, ns, leaf, 0.0, edge_skel=edge_skel, precondition=precond)
     x = np.random.default_rng(1).standard_normal(A.shape[0])
     np.testing.assert_allclose(phif.matvec(F, x), A @ x, rtol=0, atol=1e-12 * np.abs(A @ x).max())
     y = phif.solve(F, A @ x)
@@ -237,6 +250,12 @@ def test_preconditioning_reduces_solve_error_on_high_contrast_field():
     _, it_p, _ = phif.pcg(A, np.ones(A.shape[0]), M=lambda r: phif.solve(Fp, r), rtol=1e-12)
     _, it_h, _ = phif.pcg(A, np.ones(A.shape[0]), M=lambda r: phif.solve(Fh, r), rtol=1e-12)
     assert it_p <= it_h
+    # the diagonal local preconditioner (concluding section) lies in between:
+    # it rescales every separator group to unit diagonal, which removes part of
+    # the coefficient contrast the IDs see (about 5x smaller e_s than HIF here)
+    Fd = phif.factor(A, ns, 8, 1e-6, precondition="diag")
+    es_d = phif.solve_error(A, Fd, seed=1)
+    assert es_d * 2 < es_h and es_p <= es_d
 
 
 def test_pcg_with_factor_on_small_benchmark_grid():

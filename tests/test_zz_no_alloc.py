@@ -43,6 +43,26 @@ def test_noalloc_apply_matches_apply_on_consecutive_calls(gpu_lib, precision):
     F.free()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_noalloc_apply_matches_apply_with_many_cta_fronts(gpu_lib, precision):
+    """3D factor with every front eliminated by the many-CTA schedule
+    (big_front = 1): its sweeps use the interior part of the scratch too."""
+    ns = (15, 15, 15)
+    a = W.log_uniform_pixels(ns, 1e-3, 1e3, seed=23)
+    csr = gpu_lib.rhif_assemble_fd(ns, torch.as_tensor(a, device="cuda"), 1e-2)
+    F = gpu_lib.rhif_factor(csr, ns, 4, 1e-3, precision=precision, edge_skel_3d=True, big_front=1)
+    for call in range(2):
+        x = torch.as_tensor(W.normal_rhs(ns, 50 + call, nrhs=3), device="cuda")
+        ref = F.apply(x)
+        out = torch.full_like(x, float("nan"))
+        assert _noalloc(gpu_lib, F, x, out) == 0
+        torch.cuda.synchronize()
+        r, o = ref.cpu().numpy(), out.cpu().numpy()
+        assert np.all(np.isfinite(o))
+        assert np.linalg.norm(o - r) <= 1e-12 * np.linalg.norm(r)
+    F.free()
+
+
 def test_noalloc_rejects_requests_beyond_the_static_scratch(gpu_lib):
     ns = (255, 255)
     a = W.log_uniform_pixels(ns, 1e-3, 1e3, seed=22)

@@ -541,6 +541,34 @@ def local_precond_compare(wl, timed) -> dict:
     return out
 
 
+def tensor_core_kinds(wl, timed, torch) -> dict:
+    """The headline step with each operand kind of the tensor-core Schur tiles
+    (TF32 split = FP32-accurate, one TF32 product, BF16) and with the FP64
+    factor, outside the headline's timed region: DOFs/s, PCG iterations, the
+    apply error ||F^{-1} A x - x|| / ||x|| on a seeded x, and the solution's
+    difference from the FP64 factor's.  Errors are reported, not raised."""
+    out = {}
+    p, r = wl.p, wl.rhif
+    x = torch.as_tensor(wl.W.normal_rhs(p.ns, 4242), device=wl.dev)
+    u_ref = None
+    for prec in ("fp64", "fp32", "tf32", "bf16"):
+        try:
+            sec, (u, its, rr), _ = timed(lambda: wl._solve_one(wl.a_d, wl.f_d, prec), 2, 1)
+            csr = r.rhif_assemble_fd(p.ns, wl.a_d, p.b)
+            F = r.rhif_factor(csr, p.ns, p.leaf, p.tol, precision=prec, edge_skel_3d=wl.edge)
+            ea = float(torch.linalg.norm(F.apply(F.spmv(x)) - x) / torch.linalg.norm(x))
+            F.free()
+            if prec == "fp64":
+                u_ref = u
+            out[prec] = {"value": wl.dofs * 2 / sec, "ms_per_step": 1e3 * sec / 2,
+                         "pcg_iters": its[0], "relres": rr[0], "apply_error": ea,
+                         "rel_diff_u_vs_fp64": float(torch.linalg.norm(u - u_ref) /
+                                                     torch.linalg.norm(u_ref))}
+        except Exception as e:   # noqa: BLE001 - reported in the line
+            out[prec] = {"error": str(e)[:200]}
+    return out
+
+
 def step_breakdown(wl, torch) -> dict:
     """Device time of each part of one headline step of a single-problem
     workload (assembly, factorization, one application of F^{-1}, PCG),
@@ -728,6 +756,8 @@ def gpu_arm(args):
         result["breakdown"] = step_breakdown(wl, torch)
     if args.workload == "c2":
         result["local_precond"] = local_precond_compare(wl, timed)
+    if args.workload == "c3":
+        result["tensor_core_kinds"] = tensor_core_kinds(wl, timed, torch)
     if args.workload == "c4":
         result["rhs_dofs_per_s"] = value * 32
     if args.workload == "c5":

@@ -43,7 +43,17 @@ enum {
   RHIF_ERR_CHECK = -7           /* a self-check found a violated invariant (detail says which) */
 };
 
-enum { RHIF_FP64 = 0, RHIF_MIXED_FP32 = 1 };  /* precision of the stored factor */
+/* Precision of the factor.  RHIF_FP64: every step in FP64.  The mixed
+ * precisions store and compute the factor in FP32 (the application of F^{-1}
+ * too; PCG's vectors, SpMV and dots stay FP64) and differ only in the
+ * operands of the tensor-core Schur tiles of fronts eliminated with the
+ * many-CTA schedule (Sec. 2.1 Schur update; in practice the 3D levels >= 1):
+ * RHIF_MIXED_FP32 splits each value into two TF32 parts (three products,
+ * about FP32 accuracy), RHIF_MIXED_TF32 uses one TF32 product, and
+ * RHIF_MIXED_BF16 one BF16 product, all accumulated in FP32. */
+enum { RHIF_FP64 = 0, RHIF_MIXED_FP32 = 1, RHIF_MIXED_TF32 = 2, RHIF_MIXED_BF16 = 3 };
+/* operand kinds of rhif_tc_gemm_check */
+enum { RHIF_TC_TF32X3 = 0, RHIF_TC_TF32 = 1, RHIF_TC_BF16 = 2 };
 enum { RHIF_PRECOND_NONE = 0, RHIF_PRECOND_BLOCK = 1, RHIF_PRECOND_DIAG = 2 };
 enum { RHIF_SOLVE = 0, RHIF_MATVEC = 1 };      /* apply F^{-1}; F (reserved, see rhif_apply) */
 
@@ -64,7 +74,7 @@ typedef struct {
 } rhif_csr;
 
 typedef struct {
-  int precision;      /* RHIF_FP64 (default) or RHIF_MIXED_FP32 */
+  int precision;      /* RHIF_FP64 (default), RHIF_MIXED_FP32, _TF32 or _BF16 */
   /* precondition: local preconditioner C_l applied to every separator group
    *   before skeletonization.  1 = block Jacobi by the Cholesky factor of the
    *   group's diagonal block (PHIF, Sec. 2.3; default); 0 = none (plain HIF,
@@ -221,13 +231,16 @@ int rhif_pcg(const rhif_handle* F, int nrhs, const double* f, int64_t ldf, doubl
 int rhif_estimate_es(const rhif_handle* F, const double* x0, int maxit, double rel, double* es,
                      int* iters, void* stream);
 
-/* C -= A B^T on the tensor cores (tcgen05, TF32 inputs split into a high
- * part and a remainder, FP32 accumulation: about FP32 accuracy), the product
+/* C -= A B^T on the tensor cores (tcgen05, FP32 accumulation), the product
  * used for the dense Schur updates of large fronts (Sec. 2.1), exported so
- * that it can be checked on a device.  A is M x K, B is N x K, C is M x N,
- * all FP32 DEVICE arrays in column-major order with leading dimensions lda,
- * ldb, ldc; M, N >= 1, K >= 0.  RHIF_ERR_TIMEOUT if a bounded wait gave up. */
-int rhif_tc_gemm_check(int M, int N, int K, const float* A, int64_t lda, const float* B,
+ * that it can be checked on a device.  kind: RHIF_TC_TF32X3 (TF32 inputs split
+ * into a high part and a remainder, three products: about FP32 accuracy),
+ * RHIF_TC_TF32 (one TF32 product) or RHIF_TC_BF16 (inputs rounded to BF16).
+ * A is M x K, B is N x K, C is M x N, all FP32 DEVICE arrays in column-major
+ * order with leading dimensions lda, ldb, ldc; M, N >= 1, K >= 0.
+ * RHIF_ERR_BAD_ARG for another kind or bad sizes, RHIF_ERR_TIMEOUT if a
+ * bounded wait gave up. */
+int rhif_tc_gemm_check(int kind, int M, int N, int K, const float* A, int64_t lda, const float* B,
                        int64_t ldb, float* C, int64_t ldc, void* stream);
 
 /* Per-pixel gradient of a loss with respect to log a, given the state u and

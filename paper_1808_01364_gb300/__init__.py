@@ -89,7 +89,7 @@ EXPORTS = {
                                 ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int,
                                 ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
                                 ctypes.c_void_p]),
-    "rhif_tc_gemm_check": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+    "rhif_tc_gemm_check": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                           ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
                                           ctypes.c_void_p]),
@@ -396,16 +396,22 @@ def rhif_autotune(csr, ns, leaf: int, tol: float, precision: str = "fp64", preco
     return kw, ms.value
 
 
-def rhif_tc_gemm_check(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor, stream=None):
-    """C -= A B^T on the tensor cores (3xTF32); A (M, K), B (N, K), C (M, N) FP32
-    tensors given in column-major order, i.e. as the transposes of row-major
-    tensors: pass A.t().contiguous().t() etc."""
+TC_KINDS = {"tf32x3": 0, "tf32": 1, "bf16": 2}
+
+
+def rhif_tc_gemm_check(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor, stream=None,
+                       kind: str = "tf32x3"):
+    """C -= A B^T on the tensor cores (operands: "tf32x3" split TF32, "tf32" or
+    "bf16"); A (M, K), B (N, K), C (M, N) FP32 tensors given in column-major
+    order, i.e. as the transposes of row-major tensors: pass
+    A.t().contiguous().t() etc."""
     load()
     M, K = A.shape
     N = B.shape[0]
     lda = max(int(A.stride(1)), M) if K > 0 else M
     ldb = max(int(B.stride(1)), N) if K > 0 else N
-    _check(_lib.rhif_tc_gemm_check(int(M), int(N), int(K), _colptr(A), lda, _colptr(B), ldb,
+    _check(_lib.rhif_tc_gemm_check(TC_KINDS[kind], int(M), int(N), int(K), _colptr(A), lda,
+                                   _colptr(B), ldb,
                                    _colptr(C), max(int(C.stride(1)), M), _stream(stream)))
     return C
 
@@ -526,7 +532,8 @@ def _opts(precision="fp64", precondition=True, edge_skel_3d=False, big_front=0,
           big_frame=0, skel_cluster=0, tensor_cores=0) -> Opts:
     o = Opts()
     _lib.rhif_default_opts(ctypes.byref(o))
-    o.precision = {"fp64": RHIF_FP64, "fp32": RHIF_MIXED_FP32, "mixed": RHIF_MIXED_FP32}[precision]
+    o.precision = {"fp64": RHIF_FP64, "fp32": RHIF_MIXED_FP32, "mixed": RHIF_MIXED_FP32,
+                   "tf32": 2, "bf16": 3}[precision]
     if isinstance(precondition, str):
         o.precondition = {"none": 0, "hif": 0, "block": 1, "phif": 1, "diag": 2}[precondition]
     else:

@@ -134,10 +134,13 @@ void launch_grad_logcoef(const GeoDev& G, const double* a_pix, const double* u, 
 // tensor-core tile products (tc_kernels.cu)
 size_t tc_tile_smem_bytes();
 int configure_tc_kernels();
-void launch_tc_gemm_check(int M, int N, int K, const float* A, int64_t lda, const float* B,
-                          int64_t ldb, float* C, int64_t ldc, int* status, cudaStream_t s);
+// kind: 0 = TF32 split in three products (about FP32), 1 = TF32, 2 = BF16
+void launch_tc_gemm_check(int kind, int M, int N, int K, const float* A, int64_t lda,
+                          const float* B, int64_t ldb, float* C, int64_t ldc, int* status,
+                          cudaStream_t s);
 // FP32 fronts: F[B,B] -= F[B,I] F[B,I]^T on the tensor cores, 128 x 64 tiles
 int64_t front_schur_tc_tiles(int nI, int nB);
-void launch_front_schur_tc(const LevelDev& Lv, int64_t tiles, int* status, cudaStream_t s);
+void launch_front_schur_tc(const LevelDev& Lv, int64_t tiles, int kind, int* status,
+                           cudaStream_t s);
 
 }  // namespace rhif

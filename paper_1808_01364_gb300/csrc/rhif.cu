@@ -679,7 +679,9 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
         int64_t tiles = 0;
         if (sizeof(T) == 4 && H->tensor_cores) {
           for (int c = 0; c < P.ncell(); ++c) tiles += front_schur_tc_tiles(P.nI[c], P.nB[c]);
-          launch_front_schur_tc(S.dev, tiles, H->status, s);
+          // operand kind of the Schur tiles: TF32 split (about FP32), TF32, BF16
+          const int kind = H->precision == RHIF_MIXED_BF16 ? 2 : H->precision == RHIF_MIXED_TF32 ? 1 : 0;
+          launch_front_schur_tc(S.dev, tiles, kind, H->status, s);
         } else {
           for (int c = 0; c < P.ncell(); ++c) tiles += front_schur_tiles(P.nI[c], P.nB[c]);
           launch_front_schur<T>(S.dev, tiles, s);
@@ -1149,7 +1151,7 @@ int rhif_factor(const rhif_csr* A, const rhif_grid* g, int leaf, double tol, con
   rhif_opts def;
   rhif_default_opts(&def);
   if (!o) o = &def;
-  if (o->precision != RHIF_FP64 && o->precision != RHIF_MIXED_FP32)
+  if (o->precision < RHIF_FP64 || o->precision > RHIF_MIXED_BF16)
     return fail(RHIF_ERR_BAD_ARG, "unknown precision");
   std::unique_ptr<rhif_handle> H(new rhif_handle());
   H->G = make_geometry(g->dim, g->n, leaf);
@@ -1267,7 +1269,7 @@ int rhif_autotune(const rhif_csr* A, const rhif_grid* g, int leaf, double tol, c
                         {&rhif_opts::skel_cluster, 3, {0, -1, 4}},
                         {&rhif_opts::tensor_cores, 2, {0, -1, 0}}};
   for (const Knob& k : knobs) {
-    if (k.field == &rhif_opts::tensor_cores && cur.precision != RHIF_MIXED_FP32) continue;
+    if (k.field == &rhif_opts::tensor_cores && cur.precision == RHIF_FP64) continue;
     const int start = cur.*(k.field);
     for (int i = 0; i < k.count; ++i) {
       const int v = k.values[i];
@@ -1499,8 +1501,9 @@ int rhif_estimate_es(const rhif_handle* Fc, const double* x0, int maxit, double 
   return RHIF_OK;
 }
 
-int rhif_tc_gemm_check(int M, int N, int K, const float* A, int64_t lda, const float* B,
+int rhif_tc_gemm_check(int kind, int M, int N, int K, const float* A, int64_t lda, const float* B,
                        int64_t ldb, float* C, int64_t ldc, void* stream) {
+  if (kind < RHIF_TC_TF32X3 || kind > RHIF_TC_BF16) return fail(RHIF_ERR_BAD_ARG, "unknown operand kind");
   if (M < 1 || N < 1 || K < 0 || !C || ldc < M || (K > 0 && (!A || !B || lda < M || ldb < N)))
     return fail(RHIF_ERR_BAD_ARG, "bad GEMM arguments");
   static std::once_flag once;
@@ -1511,7 +1514,7 @@ int rhif_tc_gemm_check(int M, int N, int K, const float* A, int64_t lda, const f
   int* st = nullptr;
   CK(cudaMallocAsync((void**)&st, 4 * sizeof(int), s));
   CK(cudaMemsetAsync(st, 0, 4 * sizeof(int), s));
-  launch_tc_gemm_check(M, N, K, A, lda, B, ldb, C, ldc, st, s);
+  launch_tc_gemm_check(kind, M, N, K, A, lda, B, ldb, C, ldc, st, s);
   int h[4] = {0, 0, 0, 0};
   CK(cudaMemcpyAsync(h, st, sizeof(h), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));

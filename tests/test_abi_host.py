@@ -139,9 +139,11 @@ def test_other_entry_points_check_their_arguments(rhif):
     assert lib.rhif_assemble_fd(_grid(rhif, (0, 3)), p, None, 0.0, p, p, p, None) == BAD_ARG
     assert lib.rhif_assemble_fd(_grid(rhif, (3, 3)), None, None, 0.0, p, p, p, None) == BAD_ARG
     assert lib.rhif_grad_logcoef(_grid(rhif, (3, 3)), p, p, None, p, None) == BAD_ARG
-    # tensor-core check: shapes
-    assert lib.rhif_tc_gemm_check(0, 4, 4, p, 4, p, 4, p, 4, None) == BAD_ARG
-    assert lib.rhif_tc_gemm_check(4, 4, 4, p, 3, p, 4, p, 4, None) == BAD_ARG
+    # tensor-core check: operand kind and shapes
+    assert lib.rhif_tc_gemm_check(0, 0, 4, 4, p, 4, p, 4, p, 4, None) == BAD_ARG
+    assert lib.rhif_tc_gemm_check(2, 4, 4, 4, p, 3, p, 4, p, 4, None) == BAD_ARG
+    assert lib.rhif_tc_gemm_check(3, 4, 4, 4, p, 4, p, 4, p, 4, None) == BAD_ARG
+    assert lib.rhif_tc_gemm_check(-1, 4, 4, 4, p, 4, p, 4, p, 4, None) == BAD_ARG
     # batches: negative counts and missing streams
     out = (ctypes.c_void_p * 1)()
     assert lib.rhif_factor_batched(-1, ctypes.byref(A), _grid(rhif, (15, 15)), 4, 1e-3, None,

@@ -159,6 +159,42 @@ int rhif_factor_batched(int count, const rhif_csr* A, const rhif_grid* g, int le
                         const rhif_opts* o, void* const* streams, int nstreams,
                         rhif_handle** out);
 
+/* Factor `count` independent problems (A[i] on grid g[i], the same
+ * dimension, leaf, tol and options) as ONE merged factorization: the cells,
+ * groups and units of every problem at a level form one work list, so each
+ * step of a level (Sec. 2.1 cell elimination, Sec. 2.3 block Jacobi scaling,
+ * Sec. 2.2 skeletonization) is one launch over the whole batch, and the host
+ * plans and synchronizes once per level for all problems.  Problems with
+ * fewer levels reach their root front earlier; it is eliminated as a cell of
+ * that merged level.  The DOFs of the problems are numbered consecutively
+ * (problem i's DOFs start at rhif_batch_info's dof_base[i]), and the handle
+ * works on the concatenated vectors: rhif_apply and rhif_apply_noalloc apply
+ * the block-diagonal F^{-1} of the batch, rhif_spmv the batch's A, rhif_pcg
+ * runs PCG for every (problem, right-hand side) pair on concatenated vectors
+ * (iters / relres then hold count x nrhs entries, problem-major), and
+ * rhif_skeletons reports the units of all problems (DOFs in the concatenated
+ * numbering).  rhif_estimate_es and rhif_autotune take single problems only.
+ * A, g: HOST arrays of count entries (the CSR pointers are device pointers,
+ * read during the call only).  Errors: those of rhif_factor; BAD_ARG for
+ * count < 1, mixed dimensions or more than 2^31 - 1 DOFs in total. */
+int rhif_factor_batch(int count, const rhif_csr* A, const rhif_grid* g, int leaf, double tol,
+                      const rhif_opts* o, void* stream, rhif_handle** out);
+
+/* Number of problems of a handle (1 for rhif_factor's) and, if dof_base is
+ * not NULL, the first DOF of each problem in the concatenated numbering plus
+ * the total (count + 1 HOST entries). */
+int rhif_batch_info(const rhif_handle* F, int* count, int64_t* dof_base);
+
+/* PCG for every problem of a merged batch handle with nrhs right-hand sides
+ * each: f[i] and u[i] (HOST arrays of count DEVICE pointers) hold problem i's
+ * N_i x nrhs right-hand sides and solutions (leading dimension N_i).  One
+ * iteration advances every (problem, right-hand side) pair with the same
+ * launches; each pair stops on its own relative residual (Sec. 4).  iters and
+ * relres: HOST arrays of count * nrhs entries, problem-major.  Errors as
+ * rhif_pcg; BAD_ARG for a handle of a single problem. */
+int rhif_pcg_batch(const rhif_handle* F, int nrhs, const double* const* f, double* const* u,
+                   double rtol, int maxit, int* iters, double* relres, void* stream);
+
 /* Autotuner of the scheduling options: one pass of coordinate descent over
  * big_front, big_frame, skel_cluster and (FP32 factors) tensor_cores, each
  * tried at its library default (0), forced on (1; skel_cluster: -1 and 4) and

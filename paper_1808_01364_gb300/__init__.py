@@ -102,6 +102,13 @@ EXPORTS = {
     "rhif_skeletons": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                       ctypes.POINTER(ctypes.c_int), ctypes.c_void_p,
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
+    "rhif_factor_batch": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                         ctypes.c_double, ctypes.POINTER(Opts), ctypes.c_void_p,
+                                         ctypes.POINTER(ctypes.c_void_p)]),
+    "rhif_batch_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]),
+    "rhif_pcg_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
     "rhif_factor_batched": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.c_int, ctypes.c_double, ctypes.POINTER(Opts),
                                            ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
@@ -375,6 +382,84 @@ def rhif_factor(csr, ns, leaf: int, tol: float, precision: str = "fp64", precond
     _check(_lib.rhif_factor(ctypes.byref(A), ctypes.byref(_grid(ns)), int(leaf), float(tol),
                             ctypes.byref(o), _stream(stream), ctypes.byref(h)))
     return Factor(h, ns, None)
+
+
+class BatchFactor(Factor):
+    """A merged factorization of several independent problems
+    (rhif_factor_batch): one handle, the problems' DOFs numbered consecutively
+    from ``dof_base[i]``; ``apply`` / ``spmv`` work on concatenated vectors of
+    length ``N`` (the total), ``pcg_batch`` on one right-hand-side block per
+    problem."""
+
+    def __init__(self, handle, grids):
+        super().__init__(handle, (1,), None)
+        self.grids = [tuple(int(v) for v in g) for g in grids]
+        cnt = ctypes.c_int()
+        base = (ctypes.c_int64 * (len(grids) + 1))()
+        _check(_lib.rhif_batch_info(self._h, ctypes.byref(cnt), base))
+        self.dof_base = list(base)
+        self.N = self.dof_base[-1]
+        self.ns = (self.N,)
+
+    def split(self, x: torch.Tensor):
+        """Views of a concatenated vector (N,) or (nrhs, N), one per problem."""
+        return [x[..., self.dof_base[i]:self.dof_base[i + 1]] for i in range(len(self.grids))]
+
+    def pcg(self, f: torch.Tensor, rtol=1e-10, maxit=1000, out=None, stream=None, check=True):
+        """PCG for every problem on concatenated vectors; iters / relres are
+        lists of per-problem lists."""
+        nrhs, ld = _cols(f, self.N)
+        u = torch.empty_like(f) if out is None else out
+        n = len(self.grids)
+        it = (ctypes.c_int * (n * nrhs))()
+        rr = (ctypes.c_double * (n * nrhs))()
+        rc = _lib.rhif_pcg(self._h, nrhs, _ptr(f), ld, _ptr(u), ld, float(rtol), int(maxit), it, rr,
+                           _stream(stream))
+        if rc != 0 and (check or rc != -3):
+            _check(rc)
+        return u, [list(it[i * nrhs:(i + 1) * nrhs]) for i in range(n)], \
+            [list(rr[i * nrhs:(i + 1) * nrhs]) for i in range(n)]
+
+    def pcg_batch(self, fs, rtol=1e-10, maxit=1000, stream=None, check=True):
+        """PCG with one right-hand-side block per problem: fs[i] of shape (N_i,)
+        or (nrhs, N_i); returns (us, iters, relres) as per-problem lists."""
+        n = len(self.grids)
+        if len(fs) != n:
+            raise ValueError("one right-hand-side block per problem")
+        nrhs = 1 if fs[0].dim() == 1 else fs[0].shape[0]
+        for i, f in enumerate(fs):
+            _need(f, "f", nrhs * (self.dof_base[i + 1] - self.dof_base[i]), torch.float64)
+            _on_device(f=f)
+            assert f.is_contiguous(), "right-hand sides must be contiguous"
+        us = [torch.empty_like(f) for f in fs]
+        Fp = (ctypes.c_void_p * n)(*[f.data_ptr() for f in fs])
+        Up = (ctypes.c_void_p * n)(*[u.data_ptr() for u in us])
+        it = (ctypes.c_int * (n * nrhs))()
+        rr = (ctypes.c_double * (n * nrhs))()
+        rc = _lib.rhif_pcg_batch(self._h, nrhs, Fp, Up, float(rtol), int(maxit), it, rr,
+                                 _stream(stream))
+        if rc != 0 and (check or rc != -3):
+            _check(rc)
+        return us, [list(it[i * nrhs:(i + 1) * nrhs]) for i in range(n)], \
+            [list(rr[i * nrhs:(i + 1) * nrhs]) for i in range(n)]
+
+
+def rhif_factor_batch(csrs, grids, leaf: int, tol: float, precision: str = "fp64",
+                      precondition=True, edge_skel_3d=False, stream=None, **sched) -> BatchFactor:
+    """One merged PHIF factorization of independent problems (one launch per
+    level step across all of them); csrs[i] = (rowptr, col, val) on grid grids[i]."""
+    load()
+    n = len(csrs)
+    A = (CSR * n)()
+    G = (Grid * n)()
+    for i, (csr, ns) in enumerate(zip(csrs, grids)):
+        A[i] = _csr(csr, ns)
+        G[i] = _grid(ns)
+    o = _opts(precision, precondition, edge_skel_3d, **sched)
+    h = ctypes.c_void_p()
+    _check(_lib.rhif_factor_batch(n, A, G, int(leaf), float(tol), ctypes.byref(o), _stream(stream),
+                                  ctypes.byref(h)))
+    return BatchFactor(h, grids)
 
 
 def rhif_autotune(csr, ns, leaf: int, tol: float, precision: str = "fp64", precondition=True,

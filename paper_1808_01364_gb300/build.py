@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "librhif.so")
-SOURCES = ["plan.cpp", "plan_check.cpp", "factor_kernels.cu", "apply_kernels.cu", "tc_kernels.cu", "rhif.cu"]
+SOURCES = ["plan.cpp", "plan_merge.cpp", "plan_check.cpp", "factor_kernels.cu", "apply_kernels.cu", "batch_kernels.cu", "tc_kernels.cu", "rhif.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC", "-Xcompiler", "-pthread",
          "-Xcompiler", "-O3"]

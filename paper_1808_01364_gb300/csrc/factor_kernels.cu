@@ -88,6 +88,19 @@ __global__ void k_expand_gids(LevelDev Lv) {
 // level 0: banded elimination of every leaf interior straight from the stencil
 // ---------------------------------------------------------------------------
 
+// Merged batches: point the kernel's grid and stencil at cell c's problem;
+// returns the first DOF of that problem in the concatenated numbering (0 for
+// a single problem, whose grid and stencil are the kernel's arguments).
+__device__ inline int64_t bind_cell_geo(const LevelDev& Lv, int c, GeoDev& G, const double*& diag,
+                                        const double*& off) {
+  if (!Lv.cell_prob) return 0;
+  const BatchGeo& b = Lv.bgeo[Lv.cell_prob[c]];
+  G = b.G;
+  diag = b.diag;
+  off = b.off;
+  return b.base;
+}
+
 __device__ inline void coords1(const GeoDev& G, int64_t gid, int x[3]) {
   int64_t rem = gid;
   x[0] = x[1] = x[2] = 1;
@@ -152,6 +165,7 @@ k_leaf_elim(GeoDev G, LevelDev Lv, const double* diag, const double* off, int* s
   const int nI = Lv.nI[c], nB = Lv.nB[c], n = nI + nB, w = Lv.band_w[c];
   const int w1 = w + 1;
   const int32_t* gid = Lv.gids + Lv.gid_off[c];
+  const int64_t dbase = bind_cell_geo(Lv, c, G, diag, off);
   T* sband = (T*)smraw;
   size_t band_bytes = ((size_t)Lv.max_nI * (Lv.max_w + 1) * sizeof(T) + 15) & ~size_t(15);
   int* postab = (int*)(smraw + band_bytes);
@@ -182,7 +196,7 @@ k_leaf_elim(GeoDev G, LevelDev Lv, const double* diag, const double* off, int* s
   __syncthreads();
   for (int p = threadIdx.x; p < n; p += blockDim.x) {
     int x[3];
-    coords1(G, gid[p], x);
+    coords1(G, gid[p] - dbase, x);
     int lin = 0, mul = 1;
     for (int a = 0; a < G.d; ++a) {
       lin += (x[a] - origin[a]) * mul;
@@ -193,7 +207,7 @@ k_leaf_elim(GeoDev G, LevelDev Lv, const double* diag, const double* off, int* s
   __syncthreads();
   // stencil entries: interior band, boundary couplings, this cell's share of A_BB
   for (int p = threadIdx.x; p < n; p += blockDim.x) {
-    const int64_t g = gid[p];
+    const int64_t g = gid[p] - dbase;
     int x[3];
     coords1(G, g, x);
     int lin = 0, mul = 1, lstride[3] = {1, 1, 1}, onplane = 0;
@@ -320,6 +334,7 @@ k_leaf_stream(GeoDev G, LevelDev Lv, const double* diag, const double* off, int*
   const int w1 = w + 1;
   const int tid = threadIdx.x;
   const int32_t* gid = Lv.gids + Lv.gid_off[c];
+  const int64_t dbase = bind_cell_geo(Lv, c, G, diag, off);
   unsigned char* p = smraw;
   T* sband = (T*)p;
   p += ((size_t)Lv.max_nI * (Lv.max_w + 1) * sizeof(T) + 15) & ~size_t(15);
@@ -362,7 +377,7 @@ k_leaf_stream(GeoDev G, LevelDev Lv, const double* diag, const double* off, int*
   __syncthreads();
   for (int q = tid; q < n; q += blockDim.x) {
     int x[3];
-    coords1(G, gid[q], x);
+    coords1(G, gid[q] - dbase, x);
     int lin = 0, mul = 1;
     for (int a = 0; a < G.d; ++a) {
       lin += (x[a] - origin[a]) * mul;
@@ -372,7 +387,7 @@ k_leaf_stream(GeoDev G, LevelDev Lv, const double* diag, const double* off, int*
   }
   __syncthreads();
   for (int q = tid; q < n; q += blockDim.x) {
-    const int64_t g = gid[q];
+    const int64_t g = gid[q] - dbase;
     int x[3];
     coords1(G, g, x);
     int lin = 0, mul = 1, lstride[3] = {1, 1, 1}, onplane = 0;
@@ -544,6 +559,7 @@ k_leaf_warp(GeoDev G, LevelDev Lv, const double* diag, const double* off, int* s
   T* bw = (T*)base;                 // band window: column k in slot k & 15, entry d = L[k+d, k]
   T* zw = bw + 256;                 // Z window: row k in slot k & 15 (NBT entries)
   const int32_t* gid = Lv.gids + Lv.gid_off[c];
+  const int64_t dbase = bind_cell_geo(Lv, c, G, diag, off);
   int ld;
   T* Fr = frame_of<T>(Lv, c, &ld);
   int* ci = Lv.cpl_i + Lv.b_off[c];
@@ -564,12 +580,12 @@ k_leaf_warp(GeoDev G, LevelDev Lv, const double* diag, const double* off, int* s
   __syncwarp();
   for (int q = lane; q < n; q += 32) {
     int x[3];
-    coords1(G, gid[q], x);
+    coords1(G, gid[q] - dbase, x);
     postab[(x[0] - origin[0]) + (x[1] - origin[1]) * m1] = q;
   }
   __syncwarp();
   for (int q = lane; q < n; q += 32) {
-    const int64_t g = gid[q];
+    const int64_t g = gid[q] - dbase;
     int x[3];
     coords1(G, g, x);
     const int lin = (x[0] - origin[0]) + (x[1] - origin[1]) * m1;

@@ -1,6 +1,7 @@
 // Host launchers of the CUDA kernels (factor_kernels.cu, apply_kernels.cu).
 #pragma once
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "tables.h"
@@ -130,6 +131,29 @@ void launch_assemble_fd(const GeoDev& G, const double* a_pix, const double* b_no
 void launch_exp(int64_t n, const double* x, double* y, cudaStream_t s);
 void launch_grad_logcoef(const GeoDev& G, const double* a_pix, const double* u, const double* lam,
                          double* grad, cudaStream_t s);
+
+// PCG vector kernels of a merged batch (batch_kernels.cu); S.prob etc. are
+// device arrays, scalars are 8 doubles per (right-hand side, problem),
+// right-hand side major
+constexpr int64_t kBatchRows = 4096;   // rows of one vector block
+void batch_vec_blocks(const std::vector<int64_t>& base, const std::vector<int64_t>& n,
+                      std::vector<int>& prob, std::vector<int64_t>& row0,
+                      std::vector<int64_t>& row1, std::vector<int>& pblk_off);
+void launch_bspmv(const VecSeg& S, const BatchGeo* bg, const double* x, int64_t ldx, double* y,
+                  int64_t ldy, int nrhs, double* partial, cudaStream_t s);
+void launch_bdot_partial(const VecSeg& S, const double* a, int64_t lda, const double* c,
+                         int64_t ldc, int nrhs, double* partial, cudaStream_t s);
+void launch_breduce(const VecSeg& S, const double* partial, int nrhs, double* sc, int mode,
+                    double rtol, cudaStream_t s);
+void launch_bupdate_xr(const VecSeg& S, int nrhs, const double* sc, double* x, int64_t ldx,
+                       double* r, int64_t ldr, const double* p, int64_t ldp, const double* q,
+                       int64_t ldq, double* partial, cudaStream_t s);
+void launch_bupdate_p(const VecSeg& S, int nrhs, const double* sc, const double* z, int64_t ldz,
+                      double* p, int64_t ldp, int first, cudaStream_t s);
+void launch_bgather(const VecSeg& S, const BatchGeo* bg, const double* const* src, double* y,
+                    int64_t ldy, int nrhs, cudaStream_t s);
+void launch_bscatter(const VecSeg& S, const BatchGeo* bg, const double* x, int64_t ldx,
+                     double* const* dst, int nrhs, cudaStream_t s);
 
 // tensor-core tile products (tc_kernels.cu)
 size_t tc_tile_smem_bytes();

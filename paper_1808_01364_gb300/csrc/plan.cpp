@@ -131,6 +131,7 @@ void LevelPlan::clear() {
   ea_off.clear();
   ea_child.clear();
   ea_map_off.clear();
+  cell_prob.clear();
   for (auto& ph : phases) phase_spare.push_back(std::move(ph));   // keeps their storage
   phases.clear();
 }

@@ -101,6 +101,8 @@ struct LevelPlan {
   std::vector<int> ea_child;
   std::vector<int64_t> ea_map_off;   // per child entry
   std::vector<int> ea_map;           // child B position -> parent front position, -1 = eliminated
+  // batches (merge_plans): problem of each cell; empty for a single problem
+  std::vector<int> cell_prob;
   // preconditioning + skeletonization passes (1, or 2 with 3D edge skeletonization)
   std::vector<PhasePlan> phases;
   std::vector<PhasePlan> phase_spare;   // storage of cleared phases, reused by build_level
@@ -125,6 +127,29 @@ void recycle_plan(LevelPlan&& P);
 LevelPlan build_level(const Geometry& G, int level, const std::vector<uint8_t>& keep,
                       const LevelPlan* prev,
                       bool precondition, bool edge_skel);
+
+// Offsets of one problem's part inside a merged plan (merge_plans).
+struct PartBase {
+  int64_t dof = 0;      // first DOF of the problem in the concatenated numbering
+  int64_t bucket = 0;   // first bucket position
+  int cell = 0, group = 0;
+  int unit[2] = {0, 0};   // first unit of each phase
+  int64_t perm[2] = {0, 0};
+};
+
+// Concatenate the plans of one level of several independent d-dimensional problems into
+// one plan whose cells, groups and units are those of every part, in part
+// order: every index is shifted by the part's base, DOF numbers by dof_base,
+// storage offsets by the running totals, and cell/group codes re-encoded
+// with the largest code base (codes are per-problem coordinates; only the
+// cells' codes are read on the device).  prev_cell_base[p] is the first cell
+// of part p in the merged plan of the previous level (extend-add children).
+// A part whose plan is its root front (no phases) contributes no units.
+// Writes each part's bases to `bases` and its problem index to cell_prob.
+void merge_plans(int d, const std::vector<const LevelPlan*>& parts,
+                 const std::vector<int>& part_prob, const std::vector<int64_t>& dof_base,
+                 const std::vector<int>& prev_cell_base, LevelPlan& out,
+                 std::vector<PartBase>& bases);
 
 // Row layout of A_{R,I} for a unit: the distinct separator groups other than
 // the unit itself, over the cells holding the unit in cell order, each cell's

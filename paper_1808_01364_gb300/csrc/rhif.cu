@@ -298,6 +298,16 @@ struct rhif_handle {
   int64_t work_elems = 0;
   double flops = 0.0, apply_bytes = 0.0, factor_ms = 0.0;
   int units = 0;
+  // Merged batch (rhif_factor_batch): the problems' grids and first DOFs in
+  // the concatenated numbering, their stencil views on the device, and per
+  // level the bases of the problems' parts in the merged plan (empty for a
+  // single problem).
+  std::vector<rhif::Geometry> pG;
+  std::vector<int64_t> pbase;
+  rhif::BatchGeo* bgeo = nullptr;
+  std::vector<std::vector<rhif::PartBase>> part_bases;
+  std::vector<std::vector<int>> part_prob;
+  rhif::VecSeg vseg{};   // PCG vector blocks of the batch (tables on the device, built on first use)
   // One F^{-1} application (the sweeps of apply_impl) as a CUDA graph, captured
   // for one (output, leading dimension, nrhs, scratch) and replayed by PCG;
   // the launch counts of one application are credited at every replay.
@@ -359,7 +369,8 @@ static int upload_level(rhif_handle* H, LevelStore& S, size_t elem) {
                o_gt = pk.add(P.group_t), o_gs = pk.add(P.group_start), o_gsz = pk.add(P.group_size),
                o_gco = pk.add(P.group_cell_off), o_gc = pk.add(P.group_cell),
                o_gp = pk.add(P.group_pos), o_eao = pk.add(P.ea_off), o_eac = pk.add(P.ea_child),
-               o_eamo = pk.add(P.ea_map_off), o_eam = pk.add(P.ea_map);
+               o_eamo = pk.add(P.ea_map_off), o_eam = pk.add(P.ea_map),
+               o_cprob = pk.add(P.cell_prob);
   struct PhOff {
     size_t pg, po, gp, ug, un, umo, uro, upo, gu;
   };
@@ -415,6 +426,8 @@ static int upload_level(rhif_handle* H, LevelStore& S, size_t elem) {
   L.ea_map_off = (const int64_t*)(b + o_eamo);
   L.ea_map = (const int*)(b + o_eam);
   L.status = H->status;
+  L.cell_prob = P.cell_prob.empty() ? nullptr : (const int*)(b + o_cprob);
+  L.bgeo = P.cell_prob.empty() ? nullptr : H->bgeo;
   if ((rc = H->mem.get((void**)&L.gids, P.gid_off.back() * sizeof(int32_t)))) return rc;
   if (P.level == 0) {
     if ((rc = H->mem.get(&L.frame_base, P.frame_total * elem))) return rc;
@@ -564,6 +577,53 @@ static int skeletonize(rhif_handle* H, const LevelPlan& P, const PhasePlan& ph, 
   }
 }
 
+// Plan of level `lvl` (Sec. 3.1 grouping).  A single problem: its level plan
+// from the previous one and the survivor flags.  A merged batch: the plan of
+// every problem that still has this level (its own previous plan and its
+// slice of the flags), concatenated by merge_plans; `pprev` holds the
+// problems' own plans of the previous level and receives those of this one.
+static LevelPlan plan_level(rhif_handle* H, int lvl, const std::vector<uint8_t>& keep,
+                            std::vector<LevelPlan>& pprev) {
+  if (H->pG.empty())
+    return build_level(H->G, lvl, keep, lvl ? &H->levels[lvl - 1].plan : nullptr, H->precondition,
+                       H->edge_skel);
+  const int np = (int)H->pG.size();
+  std::vector<LevelPlan> cur(np);
+  std::vector<const LevelPlan*> parts;
+  std::vector<int> prob, prev_cell;
+  std::vector<int64_t> base;
+  std::vector<uint8_t> kp;
+  int j = 0;   // part of problem p in the previous level
+  for (int p = 0; p < np; ++p) {
+    if (lvl > H->pG[p].L) continue;
+    const LevelPlan* pp = nullptr;
+    int pc = 0;
+    kp.clear();
+    if (lvl) {
+      const std::vector<int>& pr = H->part_prob[lvl - 1];
+      while (j < (int)pr.size() && pr[j] < p) ++j;
+      const PartBase& B = H->part_bases[lvl - 1][j];
+      pp = &pprev[p];
+      kp.assign(keep.begin() + B.bucket, keep.begin() + B.bucket + pp->bucket.size());
+      pc = B.cell;
+    }
+    cur[p] = build_level(H->pG[p], lvl, kp, pp, H->precondition, H->edge_skel);
+    parts.push_back(&cur[p]);
+    prob.push_back(p);
+    prev_cell.push_back(pc);
+    base.push_back(H->pbase[p]);
+  }
+  LevelPlan M;
+  if ((int)H->part_bases.size() <= lvl) {
+    H->part_bases.resize(lvl + 1);
+    H->part_prob.resize(lvl + 1);
+  }
+  merge_plans(H->G.d, parts, prob, base, prev_cell, M, H->part_bases[lvl]);
+  H->part_prob[lvl] = prob;
+  pprev.swap(cur);
+  return M;
+}
+
 template <typename T>
 static int factor_impl(rhif_handle* H, const rhif_csr* A) {
   const Geometry& G = H->G;
@@ -582,10 +642,23 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
   CK(cudaMemsetAsync(offb, 0, G.d * G.N * sizeof(double), s));
   CK(cudaMemsetAsync(H->status, 0, 8 * sizeof(int), s));
   CK(cudaMemsetAsync(alive_d, 1, G.N, s));
-  {
+  if (H->pG.empty()) {
     Launch t(kCatStencil, s, 0.0, double(A->nnz) * 12 + G.N * (8.0 + 24.0 * G.d), 2);
     launch_stencil_from_csr(H->gd, A->rowptr, A->col, A->val, A->nnz, H->diag, H->off, offb,
                             H->status, s);
+  } else {   // merged batch: each problem's stencil in its own block of diag / off
+    std::vector<BatchGeo> bg(H->pG.size());
+    for (size_t p = 0; p < H->pG.size(); ++p) {
+      const Geometry& Gp = H->pG[p];
+      const int64_t b = H->pbase[p];
+      bg[p] = BatchGeo{geo_dev(Gp), b, H->diag + b, H->off + G.d * b};
+      Launch t(kCatStencil, s, 0.0, double(A[p].nnz) * 12 + Gp.N * (8.0 + 24.0 * G.d), 2);
+      launch_stencil_from_csr(bg[p].G, A[p].rowptr, A[p].col, A[p].val, A[p].nnz, H->diag + b,
+                              H->off + G.d * b, offb + G.d * b, H->status, s);
+    }
+    if ((rc = H->mem.get((void**)&H->bgeo, bg.size() * sizeof(BatchGeo)))) return rc;
+    CK(cudaMemcpyAsync(H->bgeo, bg.data(), bg.size() * sizeof(BatchGeo), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));   // bg is a host local
   }
 
   // per position of the current level's bucket: the DOF survives into the
@@ -602,9 +675,10 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
   // queued for upload while the GPU converts the CSR matrix, before the
   // pattern check waits for that conversion.
   double t_plan = 0.0, t_up = 0.0;
+  std::vector<LevelPlan> pprev;   // merged batch: the problems' own plans of the last level
   {
     auto t0 = clk::now();
-    H->levels[0].plan = build_level(G, 0, keep, nullptr, H->precondition, H->edge_skel);
+    H->levels[0].plan = plan_level(H, 0, keep, pprev);
     t_plan = ms_since(t0);
     auto t1 = clk::now();
     if ((rc = upload_level(H, H->levels[0], elem))) return rc;
@@ -615,10 +689,9 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
 
   for (int lvl = 0; lvl <= G.L; ++lvl) {
     LevelStore& S = H->levels[lvl];
-    const LevelPlan* prev = lvl ? &H->levels[lvl - 1].plan : nullptr;
     if (lvl) {
       auto t0 = clk::now();
-      S.plan = build_level(G, lvl, keep, prev, H->precondition, H->edge_skel);
+      S.plan = plan_level(H, lvl, keep, pprev);
       t_plan = ms_since(t0);
       auto t1 = clk::now();
       if ((rc = upload_level(H, S, elem))) return rc;
@@ -1139,32 +1212,19 @@ int rhif_assemble_fd_log(const rhif_grid* g, const double* log_a_pix, double* a_
   return rhif_assemble_fd(g, a_pix_out, b_node, b_const, rowptr, col, val, stream);
 }
 
-int rhif_factor(const rhif_csr* A, const rhif_grid* g, int leaf, double tol, const rhif_opts* o,
-                void* stream, rhif_handle** out) {
-  if (!out) return fail(RHIF_ERR_BAD_ARG, "null output handle");
-  *out = nullptr;
-  int rc = check_grid(g);
-  if (rc) return rc;
-  if (!A || !A->rowptr || !A->col || !A->val) return fail(RHIF_ERR_BAD_ARG, "null CSR pointer");
-  if (leaf < 2) return fail(RHIF_ERR_BAD_ARG, "leaf must be >= 2");
-  if (!(tol >= 0.0) || !std::isfinite(tol)) return fail(RHIF_ERR_BAD_ARG, "tol must be finite and >= 0");
+// Options of a factorization (argument checks before any device work).
+static int set_options(rhif_handle* H, int dim, double tol, const rhif_opts* o) {
   rhif_opts def;
   rhif_default_opts(&def);
   if (!o) o = &def;
   if (o->precision < RHIF_FP64 || o->precision > RHIF_MIXED_BF16)
     return fail(RHIF_ERR_BAD_ARG, "unknown precision");
-  std::unique_ptr<rhif_handle> H(new rhif_handle());
-  H->G = make_geometry(g->dim, g->n, leaf);
-  if (A->nrows != H->G.N) return fail(RHIF_ERR_BAD_ARG, "CSR rows != number of grid DOFs");
-  if (A->nnz < H->G.N) return fail(RHIF_ERR_BAD_ARG, "CSR has fewer entries than rows");
-  if (H->G.L > 20) return fail(RHIF_ERR_BAD_ARG, "too many levels");
-  H->gd = geo_dev(H->G);
   H->precision = o->precision;
   if (o->precondition < 0 || o->precondition > 2)
     return fail(RHIF_ERR_BAD_ARG, "precondition must be 0 (HIF), 1 (block Jacobi) or 2 (diagonal)");
   H->precondition = o->precondition != 0;
   H->precond_diag = o->precondition == 2;
-  H->edge_skel = (g->dim == 3) && o->edge_skel_3d;
+  H->edge_skel = (dim == 3) && o->edge_skel_3d;
   H->big_front = o->big_front == 0 ? kBigFront : (o->big_front < 0 ? INT_MAX : o->big_front);
   H->big_frame = o->big_frame < 0 ? INT_MAX : o->big_frame;
   if (o->skel_cluster > 16 || (o->skel_cluster > 0 && (o->skel_cluster & (o->skel_cluster - 1))))
@@ -1172,6 +1232,13 @@ int rhif_factor(const rhif_csr* A, const rhif_grid* g, int leaf, double tol, con
   H->skel_cluster = o->skel_cluster;
   H->tensor_cores = o->tensor_cores >= 0;
   H->tol = tol;
+  return RHIF_OK;
+}
+
+// Run the factorization of a prepared handle (A: one CSR per problem).
+static int run_factor(std::unique_ptr<rhif_handle>& H, const rhif_csr* A, void* stream,
+                      rhif_handle** out) {
+  int rc = RHIF_OK;
   H->mem.s = (cudaStream_t)stream;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
@@ -1194,6 +1261,71 @@ int rhif_factor(const rhif_csr* A, const rhif_grid* g, int leaf, double tol, con
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   *out = H.release();
+  return RHIF_OK;
+}
+
+int rhif_factor(const rhif_csr* A, const rhif_grid* g, int leaf, double tol, const rhif_opts* o,
+                void* stream, rhif_handle** out) {
+  if (!out) return fail(RHIF_ERR_BAD_ARG, "null output handle");
+  *out = nullptr;
+  int rc = check_grid(g);
+  if (rc) return rc;
+  if (!A || !A->rowptr || !A->col || !A->val) return fail(RHIF_ERR_BAD_ARG, "null CSR pointer");
+  if (leaf < 2) return fail(RHIF_ERR_BAD_ARG, "leaf must be >= 2");
+  if (!(tol >= 0.0) || !std::isfinite(tol)) return fail(RHIF_ERR_BAD_ARG, "tol must be finite and >= 0");
+  std::unique_ptr<rhif_handle> H(new rhif_handle());
+  if ((rc = set_options(H.get(), g->dim, tol, o))) return rc;
+  H->G = make_geometry(g->dim, g->n, leaf);
+  if (A->nrows != H->G.N) return fail(RHIF_ERR_BAD_ARG, "CSR rows != number of grid DOFs");
+  if (A->nnz < H->G.N) return fail(RHIF_ERR_BAD_ARG, "CSR has fewer entries than rows");
+  if (H->G.L > 20) return fail(RHIF_ERR_BAD_ARG, "too many levels");
+  H->gd = geo_dev(H->G);
+  return run_factor(H, A, stream, out);
+}
+
+int rhif_factor_batch(int count, const rhif_csr* A, const rhif_grid* g, int leaf, double tol,
+                      const rhif_opts* o, void* stream, rhif_handle** out) {
+  if (!out) return fail(RHIF_ERR_BAD_ARG, "null output handle");
+  *out = nullptr;
+  if (count < 1 || !A || !g) return fail(RHIF_ERR_BAD_ARG, "need count >= 1 problems");
+  if (leaf < 2) return fail(RHIF_ERR_BAD_ARG, "leaf must be >= 2");
+  if (!(tol >= 0.0) || !std::isfinite(tol)) return fail(RHIF_ERR_BAD_ARG, "tol must be finite and >= 0");
+  int rc = RHIF_OK;
+  std::unique_ptr<rhif_handle> H(new rhif_handle());
+  if ((rc = set_options(H.get(), g[0].dim, tol, o))) return rc;
+  Geometry T{};
+  T.d = g[0].dim;
+  T.leaf = leaf;
+  for (int p = 0; p < count; ++p) {
+    if ((rc = check_grid(&g[p]))) return rc;
+    if (g[p].dim != T.d) return fail(RHIF_ERR_BAD_ARG, "every problem of a batch needs the same dimension");
+    if (!A[p].rowptr || !A[p].col || !A[p].val) return fail(RHIF_ERR_BAD_ARG, "null CSR pointer");
+    const Geometry Gp = make_geometry(g[p].dim, g[p].n, leaf);
+    if (A[p].nrows != Gp.N || A[p].nnz < Gp.N) return fail(RHIF_ERR_BAD_ARG, "CSR does not match its grid");
+    if (Gp.L > 20) return fail(RHIF_ERR_BAD_ARG, "too many levels");
+    H->pG.push_back(Gp);
+    H->pbase.push_back(T.N);
+    T.N += Gp.N;
+    T.L = std::max(T.L, Gp.L);
+  }
+  if (T.N > INT32_MAX) return fail(RHIF_ERR_BAD_ARG, "a batch holds at most 2^31 - 1 DOFs");
+  H->G = T;
+  H->gd = geo_dev(T);
+  return run_factor(H, A, stream, out);
+}
+
+int rhif_batch_info(const rhif_handle* F, int* count, int64_t* dof_base) {
+  if (!F || !count) return fail(RHIF_ERR_BAD_ARG, "null argument");
+  *count = F->pG.empty() ? 1 : (int)F->pG.size();
+  if (dof_base) {
+    if (F->pG.empty()) {
+      dof_base[0] = 0;
+      dof_base[1] = F->G.N;
+    } else {
+      for (size_t p = 0; p < F->pG.size(); ++p) dof_base[p] = F->pbase[p];
+      dof_base[F->pG.size()] = F->G.N;
+    }
+  }
   return RHIF_OK;
 }
 
@@ -1335,11 +1467,47 @@ int rhif_apply(const rhif_handle* F, int op, int nrhs, const double* x, int64_t 
   return apply_dispatch(F, y, ldy, nrhs, s);
 }
 
+// Vector blocks of a merged batch (uploaded once per handle).
+static int batch_segments(rhif_handle* H) {
+  if (H->vseg.nblk) return RHIF_OK;
+  std::vector<int64_t> n(H->pG.size());
+  for (size_t p = 0; p < n.size(); ++p) n[p] = H->pG[p].N;
+  std::vector<int> prob, pblk;
+  std::vector<int64_t> r0, r1;
+  batch_vec_blocks(H->pbase, n, prob, r0, r1, pblk);
+  Packer pk;
+  const size_t o_p = pk.add(prob), o_r0 = pk.add(r0), o_r1 = pk.add(r1), o_b = pk.add(pblk);
+  void* d = nullptr;
+  int rc = H->mem.get(&d, pk.total);
+  if (rc) return rc;
+  if ((rc = pk.upload(d, H->mem.s))) return rc;
+  CK(cudaStreamSynchronize(H->mem.s));
+  char* b = (char*)d;
+  H->vseg.nblk = (int)prob.size();
+  H->vseg.nprob = (int)n.size();
+  H->vseg.prob = (const int*)(b + o_p);
+  H->vseg.row0 = (const int64_t*)(b + o_r0);
+  H->vseg.row1 = (const int64_t*)(b + o_r1);
+  H->vseg.pblk_off = (const int*)(b + o_b);
+  return RHIF_OK;
+}
+
 int rhif_spmv(const rhif_handle* F, int nrhs, const double* x, int64_t ldx, double* y, int64_t ldy,
               void* stream) {
   if (!F || !x || !y || nrhs < 0) return fail(RHIF_ERR_BAD_ARG, "null argument");
   if (ldx < F->G.N || ldy < F->G.N) return fail(RHIF_ERR_BAD_ARG, "leading dimension < N");
   if (nrhs == 0) return RHIF_OK;
+  if (!F->pG.empty()) {   // merged batch: every problem's stencil on its block of the vectors
+    rhif_handle* H = const_cast<rhif_handle*>(F);
+    int rc = batch_segments(H);
+    if (rc) return rc;
+    const double N = double(F->G.N);
+    Launch t(kCatSpmv, (cudaStream_t)stream, 2.0 * (2 * F->G.d + 1) * N * nrhs,
+             (8.0 * (1 + F->G.d) + 16.0) * N * nrhs);
+    launch_bspmv(H->vseg, H->bgeo, x, ldx, y, ldy, nrhs, nullptr, (cudaStream_t)stream);
+    CK(cudaGetLastError());
+    return RHIF_OK;
+  }
   {
     const double N = double(F->G.N);
     Launch t(kCatSpmv, (cudaStream_t)stream, 2.0 * (2 * F->G.d + 1) * N * nrhs,
@@ -1350,6 +1518,131 @@ int rhif_spmv(const rhif_handle* F, int nrhs, const double* x, int64_t ldx, doub
   return RHIF_OK;
 }
 
+// PCG (Sec. 4) of every (problem, right-hand side) pair of a merged batch at
+// once, on concatenated vectors: the same iteration as rhif_pcg with
+// per-pair scalars, one F^{-1} application (the merged sweeps, replayed as a
+// CUDA graph) and one SpMV launch per iteration for the whole batch, and one
+// readback of the convergence flags.  iters / relres: count x nrhs, problem-major.
+static int pcg_batch_core(rhif_handle* F, int nrhs, const double* f, int64_t ldf, double* u,
+                          int64_t ldu, double rtol, int maxit, int* iters, double* relres,
+                          cudaStream_t s) {
+  int rc = batch_segments(F);
+  if (rc) return rc;
+  const VecSeg& S = F->vseg;
+  const int np = S.nprob, nblk = S.nblk;
+  const int64_t N = F->G.N, ld = N;
+  const double spmv_flops = 2.0 * (2 * F->G.d + 1) * N, spmv_bytes = (8.0 * (1 + F->G.d) + 16.0) * N;
+  const int64_t nsc = 8 * (int64_t)np * nrhs;
+  const int64_t need = 4 * N * nrhs + (int64_t)nblk * nrhs + 2 * nsc;
+  if ((rc = ensure_work(F, need))) return rc;
+  double* r = F->work;
+  double* z = r + N * nrhs;
+  double* p = z + N * nrhs;
+  double* q = p + N * nrhs;
+  double* part = q + N * nrhs;
+  double* sc = part + (int64_t)nblk * nrhs;
+  double* sc2 = sc + nsc;
+  auto vb = [&](double per_entry) { return per_entry * double(N) * nrhs; };
+  const double rb = 8.0 * nblk * nrhs;
+  CK(cudaMemsetAsync(sc, 0, 2 * nsc * sizeof(double), s));
+  for (int c = 0; c < nrhs; ++c) CK(cudaMemsetAsync(u + c * ldu, 0, N * sizeof(double), s));
+  { Launch t_(kCatVector, s, 0.0, vb(16)); launch_copy_cols(N, nrhs, f, ldf, r, ld, s); }
+  { Launch t_(kCatVector, s, 0.0, vb(8)); launch_bdot_partial(S, f, ldf, f, ldf, nrhs, part, s); }
+  { Launch t_(kCatVector, s, 0.0, rb); launch_breduce(S, part, nrhs, sc, 0, rtol, s); }
+  { Launch t_(kCatVector, s, 0.0, vb(16)); launch_copy_cols(N, nrhs, r, ld, z, ld, s); }
+  if ((rc = apply_dispatch(F, z, ld, nrhs, s, true))) return rc;
+  { Launch t_(kCatVector, s, 0.0, vb(16)); launch_bdot_partial(S, r, ld, z, ld, nrhs, part, s); }
+  { Launch t_(kCatVector, s, 0.0, rb); launch_breduce(S, part, nrhs, sc, 1, rtol, s); }
+  { Launch t_(kCatVector, s, 0.0, vb(24)); launch_bupdate_p(S, nrhs, sc, z, ld, p, ld, 1, s); }
+  std::vector<double> hsc(nsc);
+  const int npair = np * nrhs;
+  std::vector<int> it(npair, maxit);
+  std::vector<char> was_done(npair, 0);
+  int all_done = 0;
+  for (int k = 1; k <= maxit; ++k) {
+    { Launch t_(kCatSpmv, s, spmv_flops * nrhs, spmv_bytes * nrhs); launch_bspmv(S, F->bgeo, p, ld, q, ld, nrhs, part, s); }
+    { Launch t_(kCatVector, s, 0.0, rb); launch_breduce(S, part, nrhs, sc, 2, rtol, s); }
+    { Launch t_(kCatVector, s, 0.0, vb(48)); launch_bupdate_xr(S, nrhs, sc, u, ldu, r, ld, p, ld, q, ld, part, s); }
+    { Launch t_(kCatVector, s, 0.0, rb); launch_breduce(S, part, nrhs, sc, 3, rtol, s); }
+    CK(cudaMemcpyAsync(hsc.data(), sc, nsc * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    int nd = 0;
+    for (int c = 0; c < nrhs; ++c)
+      for (int pp = 0; pp < np; ++pp) {
+        const int pair = pp * nrhs + c;
+        if (hsc[8 * ((int64_t)c * np + pp) + kScDone] != 0.0) {
+          if (!was_done[pair]) { it[pair] = k; was_done[pair] = 1; }
+          ++nd;
+        }
+      }
+    if (nd == npair) { all_done = 1; break; }
+    { Launch t_(kCatVector, s, 0.0, vb(16)); launch_copy_cols(N, nrhs, r, ld, z, ld, s); }
+    if ((rc = apply_dispatch(F, z, ld, nrhs, s, true))) return rc;
+    { Launch t_(kCatVector, s, 0.0, vb(16)); launch_bdot_partial(S, r, ld, z, ld, nrhs, part, s); }
+    { Launch t_(kCatVector, s, 0.0, rb); launch_breduce(S, part, nrhs, sc, 4, rtol, s); }
+    { Launch t_(kCatVector, s, 0.0, vb(24)); launch_bupdate_p(S, nrhs, sc, z, ld, p, ld, 0, s); }
+  }
+  if (maxit == 0) {
+    CK(cudaMemcpyAsync(hsc.data(), sc, nsc * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  // true residuals
+  { Launch t_(kCatSpmv, s, spmv_flops * nrhs, spmv_bytes * nrhs); launch_bspmv(S, F->bgeo, u, ldu, q, ld, nrhs, nullptr, s); }
+  { Launch t_(kCatVector, s, 0.0, vb(24)); launch_sub(N, nrhs, f, ldf, q, ld, r, ld, s); }
+  { Launch t_(kCatVector, s, 0.0, vb(8)); launch_bdot_partial(S, r, ld, r, ld, nrhs, part, s); }
+  { Launch t_(kCatVector, s, 0.0, rb); launch_breduce(S, part, nrhs, sc2, 1, rtol, s); }
+  std::vector<double> h2(nsc);
+  CK(cudaMemcpyAsync(h2.data(), sc2, nsc * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  CK(cudaGetLastError());
+  for (int c = 0; c < nrhs; ++c)
+    for (int pp = 0; pp < np; ++pp) {
+      const int64_t o = 8 * ((int64_t)c * np + pp);
+      const double ff = hsc[o + kScFF];
+      if (iters) iters[pp * nrhs + c] = it[pp * nrhs + c];
+      if (relres) relres[pp * nrhs + c] = ff > 0 ? std::sqrt(h2[o + kScRZ] / ff) : 0.0;
+    }
+  if (!all_done) return fail(RHIF_ERR_NOT_CONVERGED, "PCG reached maxit before rtol");
+  return RHIF_OK;
+}
+
+int rhif_pcg_batch(const rhif_handle* Fc, int nrhs, const double* const* f, double* const* u,
+                   double rtol, int maxit, int* iters, double* relres, void* stream) {
+  rhif_handle* F = const_cast<rhif_handle*>(Fc);
+  if (!F || !f || !u || nrhs < 1 || maxit < 0 || !(rtol >= 0.0))
+    return fail(RHIF_ERR_BAD_ARG, "bad argument");
+  if (F->pG.empty()) return fail(RHIF_ERR_BAD_ARG, "not a batch handle (rhif_factor_batch)");
+  const int np = (int)F->pG.size();
+  for (int p = 0; p < np; ++p)
+    if (!f[p] || !u[p]) return fail(RHIF_ERR_BAD_ARG, "null right-hand side or solution");
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = batch_segments(F);
+  if (rc) return rc;
+  const int64_t N = F->G.N;
+  // concatenated right-hand sides and solutions, and the problems' pointer tables
+  void* buf = nullptr;
+  if ((rc = F->mem.get(&buf, 2 * N * nrhs * sizeof(double) + 2 * np * sizeof(double*) + 16))) return rc;
+  double* fc = (double*)buf;
+  double* uc = fc + N * nrhs;
+  const double** fp = (const double**)(uc + N * nrhs);
+  double** up = (double**)(fp + np);
+  std::vector<const double*> hp(2 * np);
+  for (int p = 0; p < np; ++p) {
+    hp[p] = f[p];
+    hp[np + p] = u[p];
+  }
+  CK(cudaMemcpyAsync((void*)fp, hp.data(), 2 * np * sizeof(double*), cudaMemcpyHostToDevice, s));
+  { Launch t_(kCatVector, s, 0.0, 16.0 * N * nrhs); launch_bgather(F->vseg, F->bgeo, fp, fc, N, nrhs, s); }
+  rc = pcg_batch_core(F, nrhs, fc, N, uc, N, rtol, maxit, iters, relres, s);
+  if (rc == RHIF_OK || rc == RHIF_ERR_NOT_CONVERGED) {
+    Launch t_(kCatVector, s, 0.0, 16.0 * N * nrhs);
+    launch_bscatter(F->vseg, F->bgeo, uc, N, up, nrhs, s);
+  }
+  CK(cudaStreamSynchronize(s));   // hp is a host local
+  F->mem.release(buf);
+  return rc;
+}
+
 int rhif_pcg(const rhif_handle* Fc, int nrhs, const double* f, int64_t ldf, double* u, int64_t ldu,
              double rtol, int maxit, int* iters, double* relres, void* stream) {
   rhif_handle* F = const_cast<rhif_handle*>(Fc);
@@ -1357,6 +1650,8 @@ int rhif_pcg(const rhif_handle* Fc, int nrhs, const double* f, int64_t ldf, doub
     return fail(RHIF_ERR_BAD_ARG, "bad argument");
   const int64_t N = F->G.N;
   if (ldf < N || ldu < N) return fail(RHIF_ERR_BAD_ARG, "leading dimension < N");
+  if (!F->pG.empty())
+    return pcg_batch_core(F, nrhs, f, ldf, u, ldu, rtol, maxit, iters, relres, (cudaStream_t)stream);
   cudaStream_t s = (cudaStream_t)stream;
   const int nblk = vec_blocks(N);
   const int64_t ld = N;
@@ -1436,6 +1731,7 @@ int rhif_estimate_es(const rhif_handle* Fc, const double* x0, int maxit, double 
                      int* iters, void* stream) {
   rhif_handle* F = const_cast<rhif_handle*>(Fc);
   if (!F || !x0 || !es || maxit < 1 || !(rel >= 0.0)) return fail(RHIF_ERR_BAD_ARG, "bad argument");
+  if (!F->pG.empty()) return fail(RHIF_ERR_BAD_ARG, "e_s of a batch: estimate each problem on its own");
   const int64_t N = F->G.N;
   cudaStream_t s = (cudaStream_t)stream;
   const int nblk = vec_blocks(N);

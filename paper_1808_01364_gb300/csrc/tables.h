@@ -18,6 +18,27 @@ struct GeoDev {
   int64_t stride[3];
 };
 
+// One problem of a merged batch: its grid, the first of its DOFs in the
+// concatenated numbering, and its stencil form (diagonal; forward-edge
+// weights, d x N_p, axis-major).
+struct BatchGeo {
+  GeoDev G;
+  int64_t base;
+  const double* diag;
+  const double* off;
+};
+
+// Vector blocks of a merged batch: block b covers rows [row0[b], row1[b]) of
+// problem prob[b] in the concatenated numbering; problem p owns blocks
+// pblk_off[p] .. pblk_off[p+1]-1.
+struct VecSeg {
+  int nblk, nprob;
+  const int* prob;
+  const int64_t* row0;
+  const int64_t* row1;
+  const int* pblk_off;
+};
+
 struct LevelDev {
   int level, ncell, ngroup;
   int width, code_base;      // cell width in grid intervals; base of the group code
@@ -60,6 +81,10 @@ struct LevelDev {
   const int64_t* ea_map_off;
   const int* ea_map;
   int* status;               // error word of the handle (timeouts of bulk copies)
+  // merged batches: problem of each cell and the problems' grids (null for a
+  // single problem: the kernels' GeoDev and stencil arguments apply)
+  const int* cell_prob;
+  const BatchGeo* bgeo;
 };
 
 struct PhaseDev {

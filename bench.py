@@ -14,14 +14,17 @@ factor is measured beside it under "fp64".
   c3  3D 7-point 63^3, log10 a ~ U[-3,3], b = 1e-2, leaf 8, faces + edges
       skeletonized, tol 1e-3, FP32 factor
   c4  64 independent 2D problems (sides uniform in 127..511, log10 a ~ U[-3,3],
-      leaf 8, tol 1e-3) with 32 right-hand sides each, FP32 factors, batched
-      factor and PCG over 8 streams; DOFs count each problem once
+      leaf 8, tol 1e-3) with 32 right-hand sides each, FP32 factors, one merged
+      factorization (one launch per level step for all problems) and PCG of
+      every (problem, rhs) pair with the same launches; DOFs count each
+      problem once
   c5  differentiable solve on 511^2: log a from a smooth seeded field, forward
       PHIF solve, loss 0.5 ||u - u_obs||^2, backward (adjoint PCG with the same
       factor + gradient kernel); leaf 16, tol 1e-6, FP32 factor, PCG to 1e-12
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                       [--workload c1|c2|c3|c4|c5]
+                       [--workload c1|c2|c3|c4|c5] [--tol T]
+       python bench.py --paper-tables | --skeleton-growth   (studies, one JSON line)
 Under torchrun every rank runs its own independent replica (the path does not
 shard); `value` sums the DOFs of all ranks over the slowest rank's time.
 """
@@ -431,7 +434,6 @@ class Workload:
             self.a_h = [t.as_tensor(q.a).pin_memory() for q in self.ps]
             self.f_h = [t.as_tensor(q.f).pin_memory() for q in self.ps]
             self.u_h = [t.empty(q.f.shape, dtype=t.float64).pin_memory() for q in self.ps]
-            self.streams = [t.cuda.Stream() for _ in range(8)]
             self.h2d = sum((q.a.size + q.f.size) * 8 for q in self.ps)
             self.d2h = sum(q.f.size * 8 for q in self.ps)
         else:   # c5
@@ -463,13 +465,13 @@ class Workload:
         return u, its, rr
 
     def _batch(self, a_list, f_list, precision):
+        # one merged factorization of all problems (one launch per level step)
+        # and PCG of every (problem, rhs) pair with the same launches
         r = self.rhif
         csrs = [r.rhif_assemble_fd(q.ns, a, q.b) for q, a in zip(self.ps, a_list)]
-        facs, _ = r.rhif_factor_batched(csrs, [q.ns for q in self.ps], 8, 1e-3, precision=precision,
-                                        streams=self.streams)
-        us, its, rr = r.rhif_pcg_batched(facs, f_list, rtol=self.rtol, streams=self.streams)
-        for F in facs:
-            F.free()
+        FB = r.rhif_factor_batch(csrs, [q.ns for q in self.ps], 8, 1e-3, precision=precision)
+        us, its, rr = FB.pcg_batch(f_list, rtol=self.rtol)
+        FB.free()
         return us, [max(i) for i in its], [max(x) for x in rr]
 
     def _grad(self, la, f, uo, precision):
@@ -516,7 +518,8 @@ class Workload:
         if self.key in ("c1", "c2", "c3"):
             c.update(N=self.p.n, leaf=self.p.leaf, tol=self.p.tol)
         elif self.key == "c4":
-            c.update(problems=len(self.ps), rhs_per_problem=32, leaf=8, tol=1e-3, streams=8)
+            c.update(problems=len(self.ps), rhs_per_problem=32, leaf=8, tol=1e-3,
+                     batching="merged levels: one launch per level step for all problems")
         else:
             c.update(N=self.dofs, leaf=16, tol=1e-6, step="forward PCG + adjoint PCG + gradient")
         return c

@@ -252,14 +252,14 @@ static bool leaf_staged(const LevelDev& Lv) {
 }
 
 template <typename T>
-static size_t leaf_warp_smem(const LevelDev& Lv) {
-  return 16 + (leaf_staged<T>(Lv) ? leaf_band_bytes<T>(Lv.max_nI, Lv.max_w) : 0) +
+static size_t leaf_warp_smem(const LevelDev& Lv, bool staged) {
+  return 16 + (staged ? leaf_band_bytes<T>(Lv.max_nI, Lv.max_w) : 0) +
          round16((2 * (Lv.max_nI + 1) + Lv.max_nB) * sizeof(T));
 }
 
 template <typename T>
-static int leaf_warps_per_cta(const LevelDev& Lv) {
-  const size_t per = leaf_warp_smem<T>(Lv);
+static int leaf_warps_per_cta(const LevelDev& Lv, bool staged) {
+  const size_t per = leaf_warp_smem<T>(Lv, staged);
   int w = (int)(kStageBudget / per);
   return w < 1 ? 1 : (w > kLeafWarps ? kLeafWarps : w);
 }
@@ -996,28 +996,39 @@ k_apply_group_down_warp(LevelDev Lv, PhaseDev Ph, double* x, int64_t ldx, int nr
   }
 }
 
-// Right-hand sides run as separate CTAs (grid.y): the per-RHS work of the
-// sweeps is independent, and the factor blocks they share come from L2.
-static inline unsigned rhs_grid(int nrhs) { return (unsigned)std::min(std::max(nrhs, 1), 65535); }
+// Right-hand sides over grid.y: the per-RHS work of the sweeps is
+// independent.  A launch gets as many CTAs per vector as keep it at about
+// 2432 CTAs (152 SMs x 16); the remaining right-hand sides loop inside each
+// CTA, which then reads its factor blocks once (staged in shared memory, or
+// from L1) for all of them instead of once per right-hand side.
+static inline unsigned rhs_grid(int nrhs, int64_t gridx) {
+  const int64_t target = 152 * 16;
+  int64_t gy = (target + std::max<int64_t>(gridx, 1) - 1) / std::max<int64_t>(gridx, 1);
+  gy = std::min<int64_t>(std::max<int64_t>(gy, 1), std::max(nrhs, 1));
+  return (unsigned)std::min<int64_t>(gy, 65535);
+}
 
 template <typename T>
 void launch_apply_cell_up(const LevelDev& Lv, double* x, int64_t ldx, int nrhs, double* ubuf,
                           int64_t ldu, cudaStream_t s) {
   if (!Lv.ncell) return;
   if (Lv.level == 0) {
-    const int wpc = leaf_warps_per_cta<T>(Lv);
-    const size_t per = leaf_warp_smem<T>(Lv);
+    const bool multi = nrhs > (int)rhs_grid(nrhs, Lv.ncell / kLeafWarps + 1);
+    const bool staged = leaf_staged<T>(Lv) || multi;
+    const int wpc = leaf_warps_per_cta<T>(Lv, staged);
+    const size_t per = leaf_warp_smem<T>(Lv, staged);
     const unsigned grid = (Lv.ncell + wpc - 1) / wpc;
-    if (leaf_staged<T>(Lv))
-      k_apply_leaf_up<T, true><<<dim3(grid, rhs_grid(nrhs)), 32 * wpc, wpc * per, s>>>(Lv, x, ldx, nrhs, ubuf, ldu, (int)per);
+    const unsigned gy = rhs_grid(nrhs, grid);
+    if (staged)
+      k_apply_leaf_up<T, true><<<dim3(grid, gy), 32 * wpc, wpc * per, s>>>(Lv, x, ldx, nrhs, ubuf, ldu, (int)per);
     else
-      k_apply_leaf_up<T, false><<<dim3(grid, rhs_grid(nrhs)), 32 * wpc, wpc * per, s>>>(Lv, x, ldx, nrhs, ubuf, ldu, (int)per);
+      k_apply_leaf_up<T, false><<<dim3(grid, gy), 32 * wpc, wpc * per, s>>>(Lv, x, ldx, nrhs, ubuf, ldu, (int)per);
     return;
   }
   const size_t base = round16(2 * (Lv.max_nI + 1) * sizeof(T));
   const size_t blk = round16((size_t)Lv.max_n * Lv.max_nI * sizeof(T));
   const int stage = blk <= kStageBudget;
-  k_apply_cell_up<T><<<dim3(Lv.ncell, rhs_grid(nrhs)), kApplyThreads, base + (stage ? blk : 0), s>>>(Lv, x, ldx, nrhs, ubuf,
+  k_apply_cell_up<T><<<dim3(Lv.ncell, rhs_grid(nrhs, Lv.ncell)), kApplyThreads, base + (stage ? blk : 0), s>>>(Lv, x, ldx, nrhs, ubuf,
                                                                             ldu, stage);
 }
 
@@ -1025,19 +1036,22 @@ template <typename T>
 void launch_apply_cell_down(const LevelDev& Lv, double* x, int64_t ldx, int nrhs, cudaStream_t s) {
   if (!Lv.ncell) return;
   if (Lv.level == 0) {
-    const int wpc = leaf_warps_per_cta<T>(Lv);
-    const size_t per = leaf_warp_smem<T>(Lv);
+    const bool multi = nrhs > (int)rhs_grid(nrhs, Lv.ncell / kLeafWarps + 1);
+    const bool staged = leaf_staged<T>(Lv) || multi;
+    const int wpc = leaf_warps_per_cta<T>(Lv, staged);
+    const size_t per = leaf_warp_smem<T>(Lv, staged);
     const unsigned grid = (Lv.ncell + wpc - 1) / wpc;
-    if (leaf_staged<T>(Lv))
-      k_apply_leaf_down<T, true><<<dim3(grid, rhs_grid(nrhs)), 32 * wpc, wpc * per, s>>>(Lv, x, ldx, nrhs, (int)per);
+    const unsigned gy = rhs_grid(nrhs, grid);
+    if (staged)
+      k_apply_leaf_down<T, true><<<dim3(grid, gy), 32 * wpc, wpc * per, s>>>(Lv, x, ldx, nrhs, (int)per);
     else
-      k_apply_leaf_down<T, false><<<dim3(grid, rhs_grid(nrhs)), 32 * wpc, wpc * per, s>>>(Lv, x, ldx, nrhs, (int)per);
+      k_apply_leaf_down<T, false><<<dim3(grid, gy), 32 * wpc, wpc * per, s>>>(Lv, x, ldx, nrhs, (int)per);
     return;
   }
   const size_t base = round16((2 * Lv.max_nI + Lv.max_nB + 1) * sizeof(T));
   const size_t blk = round16((size_t)Lv.max_n * Lv.max_nI * sizeof(T));
   const int stage = blk <= kStageBudget;
-  k_apply_cell_down<T><<<dim3(Lv.ncell, rhs_grid(nrhs)), kApplyThreads, base + (stage ? blk : 0), s>>>(Lv, x, ldx, nrhs,
+  k_apply_cell_down<T><<<dim3(Lv.ncell, rhs_grid(nrhs, Lv.ncell)), kApplyThreads, base + (stage ? blk : 0), s>>>(Lv, x, ldx, nrhs,
                                                                               stage);
 }
 
@@ -1085,14 +1099,14 @@ void launch_apply_group_up(const LevelDev& Lv, const PhaseDev& Ph, int gather, d
   if (Lv.max_group <= 32) {
     const size_t per = group_warp_smem<T>(Lv.max_group);
     const unsigned grid = (Lv.ngroup + kGroupWarps - 1) / kGroupWarps;
-    k_apply_group_up_warp<T><<<dim3(grid, rhs_grid(nrhs)), 32 * kGroupWarps, kGroupWarps * per, s>>>(
+    k_apply_group_up_warp<T><<<dim3(grid, rhs_grid(nrhs, grid)), 32 * kGroupWarps, kGroupWarps * per, s>>>(
         Lv, Ph, gather, x, ldx, nrhs, ubuf, ldu, (int)per);
     return;
   }
   const size_t base = round16(2 * (Lv.max_group + 1) * sizeof(T));
   const size_t blk = group_block_bytes<T>(Lv.max_group);
   const int stage = blk <= kStageBudget;
-  k_apply_group_up<T><<<dim3(Lv.ngroup, rhs_grid(nrhs)), kGroupThreads, base + (stage ? blk : 0), s>>>(
+  k_apply_group_up<T><<<dim3(Lv.ngroup, rhs_grid(nrhs, Lv.ngroup)), kGroupThreads, base + (stage ? blk : 0), s>>>(
       Lv, Ph, gather, x, ldx, nrhs, ubuf, ldu, stage);
 }
 
@@ -1103,14 +1117,14 @@ void launch_apply_group_down(const LevelDev& Lv, const PhaseDev& Ph, double* x, 
   if (Lv.max_group <= 32) {
     const size_t per = group_warp_smem<T>(Lv.max_group);
     const unsigned grid = (Lv.ngroup + kGroupWarps - 1) / kGroupWarps;
-    k_apply_group_down_warp<T><<<dim3(grid, rhs_grid(nrhs)), 32 * kGroupWarps, kGroupWarps * per, s>>>(
+    k_apply_group_down_warp<T><<<dim3(grid, rhs_grid(nrhs, grid)), 32 * kGroupWarps, kGroupWarps * per, s>>>(
         Lv, Ph, x, ldx, nrhs, (int)per);
     return;
   }
   const size_t base = round16(2 * (Lv.max_group + 1) * sizeof(T));
   const size_t blk = group_block_bytes<T>(Lv.max_group);
   const int stage = blk <= kStageBudget;
-  k_apply_group_down<T><<<dim3(Lv.ngroup, rhs_grid(nrhs)), kGroupThreads, base + (stage ? blk : 0), s>>>(
+  k_apply_group_down<T><<<dim3(Lv.ngroup, rhs_grid(nrhs, Lv.ngroup)), kGroupThreads, base + (stage ? blk : 0), s>>>(
       Lv, Ph, x, ldx, nrhs, stage);
 }
 

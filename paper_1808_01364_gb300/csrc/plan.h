@@ -151,6 +151,10 @@ void merge_plans(int d, const std::vector<const LevelPlan*>& parts,
                  const std::vector<int>& prev_cell_base, LevelPlan& out,
                  std::vector<PartBase>& bases);
 
+// Hands a merged plan that is no longer needed to the calling thread's pool
+// of merged plans (one per level), reused by the next merge_plans of that level.
+void recycle_merged_plan(LevelPlan&& P);
+
 // Row layout of A_{R,I} for a unit: the distinct separator groups other than
 // the unit itself, over the cells holding the unit in cell order, each cell's
 // segments in code order; a group met again in a later cell is not repeated

@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cstdlib>
 #include <cmath>
@@ -590,29 +591,41 @@ static LevelPlan plan_level(rhif_handle* H, int lvl, const std::vector<uint8_t>&
   const int np = (int)H->pG.size();
   std::vector<LevelPlan> cur(np);
   std::vector<const LevelPlan*> parts;
-  std::vector<int> prob, prev_cell;
+  std::vector<int> prob, prev_cell, prev_part;
   std::vector<int64_t> base;
-  std::vector<uint8_t> kp;
   int j = 0;   // part of problem p in the previous level
   for (int p = 0; p < np; ++p) {
     if (lvl > H->pG[p].L) continue;
-    const LevelPlan* pp = nullptr;
-    int pc = 0;
-    kp.clear();
+    int pc = 0, pj = -1;
     if (lvl) {
       const std::vector<int>& pr = H->part_prob[lvl - 1];
       while (j < (int)pr.size() && pr[j] < p) ++j;
-      const PartBase& B = H->part_bases[lvl - 1][j];
-      pp = &pprev[p];
-      kp.assign(keep.begin() + B.bucket, keep.begin() + B.bucket + pp->bucket.size());
-      pc = B.cell;
+      pj = j;
+      pc = H->part_bases[lvl - 1][j].cell;
     }
-    cur[p] = build_level(H->pG[p], lvl, kp, pp, H->precondition, H->edge_skel);
     parts.push_back(&cur[p]);
     prob.push_back(p);
     prev_cell.push_back(pc);
+    prev_part.push_back(pj);
     base.push_back(H->pbase[p]);
   }
+  // the problems' plans are independent: one per planner-pool thread (each
+  // build_level then runs its own loops on its thread; the pool's threads
+  // keep their planner storage between factorizations)
+  HostPool::get().parallel_for((int64_t)prob.size(), 1, [&](int64_t q0, int64_t q1) {
+    std::vector<uint8_t> kp;
+    for (int64_t q = q0; q < q1; ++q) {
+      const int p = prob[q];
+      const LevelPlan* pp = nullptr;
+      kp.clear();
+      if (lvl) {
+        const PartBase& B = H->part_bases[lvl - 1][prev_part[q]];
+        pp = &pprev[p];
+        kp.assign(keep.begin() + B.bucket, keep.begin() + B.bucket + pp->bucket.size());
+      }
+      cur[p] = build_level(H->pG[p], lvl, kp, pp, H->precondition, H->edge_skel);
+    }
+  });
   LevelPlan M;
   if ((int)H->part_bases.size() <= lvl) {
     H->part_bases.resize(lvl + 1);
@@ -1886,7 +1899,10 @@ void rhif_free(rhif_handle* F) {
   cudaStreamSynchronize(F->mem.s);
   if (F->apply_graph) cudaGraphExecDestroy(F->apply_graph);
   if (F->capture_stream) cudaStreamDestroy(F->capture_stream);
-  for (auto& S : F->levels) recycle_plan(std::move(S.plan));
+  for (auto& S : F->levels) {
+    if (S.plan.cell_prob.empty()) recycle_plan(std::move(S.plan));
+    else recycle_merged_plan(std::move(S.plan));
+  }
   delete F;
 }
 

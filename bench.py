@@ -793,8 +793,8 @@ def paper_tables(args):
     high-contrast field (Sec. 4) at 1023^2 (leaf 16; tol 1e-3, 1e-4, 1e-6,
     1e-8 as in Table 1) and 31^3 / 63^3 (leaf 8, faces + edges; tol 1e-3,
     1e-6), HIF, PHIF with the diagonal local preconditioner and PHIF (FP64
-    factors): factor time, root size, e_s (power iteration, 1e-2 relative
-    change) and PCG iterations to relres 1e-12.  One JSON line."""
+    factors): factor time, root size, e_a and e_s (power iterations, 1e-2
+    relative change) and PCG iterations to relres 1e-12.  One JSON line."""
     import numpy as np
     import torch
 
@@ -808,6 +808,8 @@ def paper_tables(args):
         n = int(np.prod(ns))
         f = torch.as_tensor(W.normal_rhs(ns, W.SEED_BASE + 6), device="cuda")
         x0 = torch.as_tensor(np.random.Generator(np.random.PCG64(7)).standard_normal(n),
+                             device="cuda")
+        x1 = torch.as_tensor(np.random.Generator(np.random.PCG64(8)).standard_normal(n),
                              device="cuda")
         csr = rhif.rhif_assemble_fd(ns, a, 0.0)
         for tol in tols[len(ns)]:
@@ -824,8 +826,9 @@ def paper_tables(args):
                     e1.synchronize()
                     st = F.stats()
                     es, _ = F.estimate_es(x0)
+                    ea, _ = F.estimate_ea(x0, x1)
                     _, its, rr = F.pcg(f, rtol=1e-12, maxit=1000, check=False)
-                    row.update(factor_ms=e0.elapsed_time(e1), root=st["root_size"], e_s=es,
+                    row.update(factor_ms=e0.elapsed_time(e1), root=st["root_size"], e_a=ea, e_s=es,
                                pcg_iters=its[0], relres=rr[0],
                                factor_gb=st["factor_bytes"] / 1e9)
                     F.free()

@@ -55,7 +55,8 @@ enum { RHIF_FP64 = 0, RHIF_MIXED_FP32 = 1, RHIF_MIXED_TF32 = 2, RHIF_MIXED_BF16 
 /* operand kinds of rhif_tc_gemm_check */
 enum { RHIF_TC_TF32X3 = 0, RHIF_TC_TF32 = 1, RHIF_TC_BF16 = 2 };
 enum { RHIF_PRECOND_NONE = 0, RHIF_PRECOND_BLOCK = 1, RHIF_PRECOND_DIAG = 2 };
-enum { RHIF_SOLVE = 0, RHIF_MATVEC = 1 };      /* apply F^{-1}; F (reserved, see rhif_apply) */
+/* operations of rhif_apply: F^{-1}, F, G^{-1}, G^{-T} with F = G G^T (Eq. 3.3) */
+enum { RHIF_SOLVE = 0, RHIF_MATVEC = 1, RHIF_HALF = 2, RHIF_HALF_T = 3 };
 
 typedef struct {
   int dim;      /* 2 or 3 */
@@ -219,11 +220,22 @@ int rhif_pcg_batched(int count, rhif_handle* const* F, int nrhs, const double* c
                      double* const* u, double rtol, int maxit, int* iters, double* relres,
                      void* const* streams, int nstreams);
 
-/* y = F^{-1} x (op = RHIF_SOLVE, Eq. 3.2) for nrhs column vectors of length N
- * stored with leading dimensions ldx/ldy (>= N).  x and y may alias only if
- * ldx == ldy and x == y.  op = RHIF_MATVEC (y = F x, Eq. 3.1) is reserved and
- * returns RHIF_ERR_BAD_ARG: the stored factor keeps the explicit inverses
- * (L^{-1} of fronts, L_g^{-1}, L_rr^{-1}) that F^{-1} needs, not the blocks of F. */
+/* y = op(F) x for nrhs column vectors of length N stored with leading
+ * dimensions ldx/ldy (>= N):
+ *  - RHIF_SOLVE:  y = F^{-1} x (Eq. 3.2), the upward and downward sweeps;
+ *  - RHIF_HALF:   y = G^{-1} x = B_L^{-1} R_{L-1}^T ... R_0^T x with F = G G^T
+ *                 (Eq. 3.3), the upward sweep and the forward root solve;
+ *  - RHIF_HALF_T: y = G^{-T} x, the backward root solve and the downward
+ *                 sweep (so RHIF_HALF_T after RHIF_HALF is RHIF_SOLVE);
+ *  - RHIF_MATVEC: y = F x (Eq. 3.1).  The stored factor keeps the explicit
+ *                 inverses F^{-1} needs, so F x is the solution of
+ *                 F^{-1} y = x by conjugate gradients preconditioned with A
+ *                 (a few iterations: A F^{-1} is the operator PCG sees),
+ *                 to ||x - F^{-1} y|| <= 1e-13 ||x|| for FP64 factors (1e-7
+ *                 for FP32 ones) or the precision of the application; it
+ *                 uses the handle's work space; single problems only.
+ * x and y may alias only if ldx == ldy and x == y (not for RHIF_MATVEC).
+ * Errors: BAD_ARG (unknown op, sizes, aliasing), CUDA. */
 int rhif_apply(const rhif_handle* F, int op, int nrhs, const double* x, int64_t ldx,
                double* y, int64_t ldy, void* stream);
 
@@ -256,6 +268,15 @@ int rhif_spmv(const rhif_handle* F, int nrhs, const double* x, int64_t ldx,
 int rhif_pcg(const rhif_handle* F, int nrhs, const double* f, int64_t ldf, double* u,
              int64_t ldu, double rtol, int maxit, int* iters, double* relres,
              void* stream);
+
+/* Error estimate e_a = ||A - F||_2 / ||A||_2 (Sec. 4) by two power
+ * iterations as in rhif_estimate_es: on (A - F)^2 from x0 (F x as in
+ * rhif_apply with RHIF_MATVEC) and on A^2 from x1 (NULL: x0), each stopped
+ * when two successive estimates differ by at most rel times the estimate or
+ * after maxit products.  ea, iters (products of the first iteration): HOST
+ * scalars.  Single problems only. */
+int rhif_estimate_ea(const rhif_handle* F, const double* x0, const double* x1, int maxit,
+                     double rel, double* ea, int* iters, void* stream);
 
 /* Error estimate e_s = ||I - A F^{-1}||_2 (Sec. 4) by power iteration on
  * M^T M with M = I - A F^{-1}, M^T = I - F^{-1} A (A and F^{-1} symmetric):

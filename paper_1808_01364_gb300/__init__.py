@@ -25,7 +25,7 @@ _lib = None
 _lock = threading.Lock()
 
 RHIF_FP64, RHIF_MIXED_FP32 = 0, 1
-RHIF_SOLVE, RHIF_MATVEC = 0, 1
+RHIF_SOLVE, RHIF_MATVEC, RHIF_HALF, RHIF_HALF_T = 0, 1, 2, 3
 ERRORS = {0: "OK", -1: "BAD_ARG", -2: "NOT_SPD", -3: "NOT_CONVERGED", -4: "TIMEOUT", -5: "OOM",
           -6: "CUDA"}
 
@@ -93,6 +93,9 @@ EXPORTS = {
                                           ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                           ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
                                           ctypes.c_void_p]),
+    "rhif_estimate_ea": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                        ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]),
     "rhif_estimate_es": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                         ctypes.c_double, ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]),
@@ -291,15 +294,39 @@ class Factor:
             _lib.rhif_free(self._h)
             self._h = None
 
-    def apply(self, x: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
-        """F^{-1} x (Eq. 3.2) for x of shape (N,) or (nrhs, N)."""
+    def apply(self, x: torch.Tensor, out: torch.Tensor | None = None, stream=None,
+              op: str = "solve") -> torch.Tensor:
+        """op(F) x for x of shape (N,) or (nrhs, N): "solve" F^{-1} (Eq. 3.2),
+        "matvec" F (Eq. 3.1), "half" G^{-1}, "half_t" G^{-T} (F = G G^T, Eq. 3.3)."""
         nrhs, ld = _cols(x, self.N)
         if out is not None:
             _need(out, "out", x.numel(), torch.float64)
             _on_device(out=out)
         y = torch.empty_like(x) if out is None else out
-        _check(_lib.rhif_apply(self._h, RHIF_SOLVE, nrhs, _ptr(x), ld, _ptr(y), ld, _stream(stream)))
+        code = {"solve": RHIF_SOLVE, "matvec": RHIF_MATVEC, "half": RHIF_HALF,
+                "half_t": RHIF_HALF_T}[op]
+        _check(_lib.rhif_apply(self._h, code, nrhs, _ptr(x), ld, _ptr(y), ld, _stream(stream)))
         return y
+
+    def matvec(self, x: torch.Tensor, stream=None) -> torch.Tensor:
+        """F x (Eq. 3.1)."""
+        return self.apply(x, stream=stream, op="matvec")
+
+    def estimate_ea(self, x0: torch.Tensor, x1: torch.Tensor | None = None, maxit: int = 100,
+                    rel: float = 1e-2, stream=None):
+        """e_a = ||A - F||_2 / ||A||_2 by power iteration from the device vectors
+        x0 (numerator) and x1 (denominator; default x0); returns (estimate, products)."""
+        _need(x0, "x0", self.N, torch.float64)
+        _on_device(x0=x0)
+        if x1 is not None:
+            _need(x1, "x1", self.N, torch.float64)
+            _on_device(x1=x1)
+        ea = ctypes.c_double()
+        it = ctypes.c_int()
+        _check(_lib.rhif_estimate_ea(self._h, _ptr(x0.contiguous()),
+                                     _ptr(x1.contiguous()) if x1 is not None else None, int(maxit),
+                                     float(rel), ctypes.byref(ea), ctypes.byref(it), _stream(stream)))
+        return ea.value, it.value
 
     def apply_noalloc(self, x: torch.Tensor, out: torch.Tensor, stream=None) -> torch.Tensor:
         """F^{-1} x into the caller's ``out`` without any device allocation

@@ -297,6 +297,9 @@ struct rhif_handle {
   std::vector<int64_t> xoff_host;   // per-cell offsets of the L^{-1} scratch (upload source)
   double* work = nullptr;
   int64_t work_elems = 0;
+  double* mv_work = nullptr;   // work space of y = F x (rhif_apply with RHIF_MATVEC)
+  int64_t mv_elems = 0;
+  int mv_iters = 0;            // CG iterations of the last y = F x
   double flops = 0.0, apply_bytes = 0.0, factor_ms = 0.0;
   int units = 0;
   // Merged batch (rhif_factor_batch): the problems' grids and first DOFs in
@@ -981,8 +984,12 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
   return RHIF_OK;
 }
 
+// part: 0 = F^{-1} (both sweeps), 1 = G^{-1} (upward sweep and the forward
+// root solve), 2 = G^{-T} (backward root solve and downward sweep), with
+// F = G G^T (Eq. 3.3: G = R_0^{-T} ... R_{L-1}^{-T} B_L).
 template <typename T>
-static int apply_impl(const rhif_handle* Hc, double* y, int64_t ldy, int nrhs, cudaStream_t s) {
+static int apply_impl(const rhif_handle* Hc, double* y, int64_t ldy, int nrhs, cudaStream_t s,
+                      int part = 0) {
   rhif_handle* H = const_cast<rhif_handle*>(Hc);
   const int L = H->G.L;
   const int64_t ldu = H->ub_len;
@@ -1001,15 +1008,21 @@ static int apply_impl(const rhif_handle* Hc, double* y, int64_t ldy, int nrhs, c
     else
       launch_apply_cell_down<T>(S.dev, y, ldy, nrhs, s);
   };
-  for (int l = 0; l < L; ++l) {
-    LevelStore& S = H->levels[l];
-    cell_up(S, l == 0 ? kCatApplyLeafUp : kCatApplyCellUp);
-    for (size_t p = 0; p < S.phases.size(); ++p) {
-      Launch t(kCatApplyGroupUp, s, S.grp_flops[p] * nrhs, S.grp_bytes[p] * nrhs);
-      launch_apply_group_up<T>(S.dev, S.phases[p].dev, p == 0, y, ldy, nrhs, H->ubuf, ldu, s);
+  if (part != 2) {
+    for (int l = 0; l < L; ++l) {
+      LevelStore& S = H->levels[l];
+      cell_up(S, l == 0 ? kCatApplyLeafUp : kCatApplyCellUp);
+      for (size_t p = 0; p < S.phases.size(); ++p) {
+        Launch t(kCatApplyGroupUp, s, S.grp_flops[p] * nrhs, S.grp_bytes[p] * nrhs);
+        launch_apply_group_up<T>(S.dev, S.phases[p].dev, p == 0, y, ldy, nrhs, H->ubuf, ldu, s);
+      }
     }
+    cell_up(H->levels[L], kCatApplyCellUp);
   }
-  cell_up(H->levels[L], kCatApplyCellUp);
+  if (part == 1) {
+    CK(cudaGetLastError());
+    return RHIF_OK;
+  }
   cell_down(H->levels[L], kCatApplyCellDown);
   for (int l = L - 1; l >= 0; --l) {
     LevelStore& S = H->levels[l];
@@ -1036,9 +1049,10 @@ static int apply_prepare(rhif_handle* H, int nrhs) {
   return RHIF_OK;
 }
 
-static int apply_launch(const rhif_handle* H, double* y, int64_t ldy, int nrhs, cudaStream_t s) {
-  return H->precision == RHIF_FP64 ? apply_impl<double>(H, y, ldy, nrhs, s)
-                                   : apply_impl<float>(H, y, ldy, nrhs, s);
+static int apply_launch(const rhif_handle* H, double* y, int64_t ldy, int nrhs, cudaStream_t s,
+                        int part = 0) {
+  return H->precision == RHIF_FP64 ? apply_impl<double>(H, y, ldy, nrhs, s, part)
+                                   : apply_impl<float>(H, y, ldy, nrhs, s, part);
 }
 
 static void credit_graph(const rhif_handle* H) {
@@ -1464,20 +1478,106 @@ int rhif_pcg_batched(int count, rhif_handle* const* F, int nrhs, const double* c
       &details);
 }
 
-int rhif_apply(const rhif_handle* F, int op, int nrhs, const double* x, int64_t ldx, double* y,
+// y = F x (Eq. 3.1) from the stored factor.  The stored blocks are those
+// F^{-1} needs (Eq. 3.2: explicit inverses of the triangular factors), so F x
+// is the solution of F^{-1} y = x, found by conjugate gradients on the SPD
+// operator F^{-1} preconditioned with A: A F^{-1} has the spectrum the outer
+// PCG sees (clustered at 1, spread e_s = ||I - A F^{-1}||), so a few
+// iterations reach the precision of the application of F^{-1} itself.  Stops
+// when every column's residual ||x - F^{-1} y|| is at most rtol ||x|| (rtol
+// 1e-13 for FP64 factors, 1e-7 for FP32 ones, whose F^{-1} is applied in FP32)
+// or has not decreased for 4 iterations (the precision of the application),
+// after at most 200 iterations.
+static int matvec_impl(rhif_handle* F, int nrhs, const double* x, int64_t ldx, double* y,
+                       int64_t ldy, cudaStream_t s) {
+  const int64_t N = F->G.N, ld = N;
+  const int nblk = vec_blocks(N);
+  const int64_t need = 4 * N * nrhs + (int64_t)nblk * nrhs + 8 * nrhs;
+  if (need > F->mv_elems) {
+    if (F->mv_work) F->mem.release(F->mv_work);
+    F->mv_work = nullptr;
+    int rc = F->mem.get((void**)&F->mv_work, need * sizeof(double));
+    if (rc) return rc;
+    F->mv_elems = need;
+  }
+  const bool batch = !F->pG.empty();
+  if (batch) return fail(RHIF_ERR_BAD_ARG, "F x of a batch: apply it to each problem's factor");
+  double* r = F->mv_work;
+  double* z = r + N * nrhs;
+  double* p = z + N * nrhs;
+  double* q = p + N * nrhs;
+  double* part = q + N * nrhs;
+  double* sc = part + (int64_t)nblk * nrhs;
+  const double rtol = F->precision == RHIF_FP64 ? 1e-13 : 1e-7;
+  int rc = RHIF_OK;
+  auto A = [&](const double* in, double* out) {
+    Launch t(kCatSpmv, s, 2.0 * (2 * F->G.d + 1) * N * nrhs, (8.0 * (1 + F->G.d) + 16.0) * N * nrhs);
+    launch_spmv(F->gd, F->diag, F->off, in, ld, out, ld, nrhs, nullptr, s);
+  };
+  auto dot = [&](const double* a, int64_t la, const double* b, int64_t lb, int mode) {
+    launch_dot_partial(N, a, la, b, lb, nrhs, part, s);
+    launch_reduce(part, nblk, nrhs, sc, mode, rtol, s);
+  };
+  CK(cudaMemsetAsync(sc, 0, 8 * nrhs * sizeof(double), s));
+  for (int c = 0; c < nrhs; ++c) CK(cudaMemsetAsync(y + c * ldy, 0, N * sizeof(double), s));
+  launch_copy_cols(N, nrhs, x, ldx, r, ld, s);
+  dot(x, ldx, x, ldx, 0);
+  A(r, z);
+  dot(r, ld, z, ld, 1);
+  launch_update_p(N, nrhs, sc, z, ld, p, ld, 1, s);
+  std::vector<double> hsc(8 * nrhs);
+  std::vector<double> best(nrhs, INFINITY);
+  std::vector<int> since(nrhs, 0);
+  int k = 0;
+  for (k = 1; k <= 200; ++k) {
+    launch_copy_cols(N, nrhs, p, ld, q, ld, s);
+    if ((rc = apply_dispatch(F, q, ld, nrhs, s, true))) return rc;   // q = F^{-1} p
+    dot(p, ld, q, ld, 2);                                            // alpha
+    launch_update_xr(N, nrhs, sc, y, ldy, r, ld, p, ld, q, ld, part, s);
+    launch_reduce(part, nblk, nrhs, sc, 3, rtol, s);                 // rr, done
+    CK(cudaMemcpyAsync(hsc.data(), sc, 8 * nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    bool all = true;
+    for (int c = 0; c < nrhs; ++c) {
+      const double rr = hsc[8 * c + kScRR];
+      if (rr < 0.99 * best[c]) {
+        best[c] = rr;
+        since[c] = 0;
+      } else {
+        ++since[c];
+      }
+      all = all && (hsc[8 * c + kScDone] != 0.0 || since[c] >= 4);
+    }
+    if (all) break;
+    A(r, z);                                                         // z = A r
+    dot(r, ld, z, ld, 4);                                            // beta
+    launch_update_p(N, nrhs, sc, z, ld, p, ld, 0, s);
+  }
+  F->mv_iters = std::min(k, 200);
+  CK(cudaGetLastError());
+  return RHIF_OK;
+}
+
+int rhif_apply(const rhif_handle* Fc, int op, int nrhs, const double* x, int64_t ldx, double* y,
                int64_t ldy, void* stream) {
+  rhif_handle* F = const_cast<rhif_handle*>(Fc);
   if (!F || !x || !y || nrhs < 0) return fail(RHIF_ERR_BAD_ARG, "null argument");
-  if (op != RHIF_SOLVE) return fail(RHIF_ERR_BAD_ARG, "only RHIF_SOLVE is available");
+  if (op < RHIF_SOLVE || op > RHIF_HALF_T) return fail(RHIF_ERR_BAD_ARG, "unknown operation");
   const int64_t N = F->G.N;
   if (ldx < N || ldy < N) return fail(RHIF_ERR_BAD_ARG, "leading dimension < N");
   if (x == y && ldx != ldy) return fail(RHIF_ERR_BAD_ARG, "aliased x and y need ldx == ldy");
+  if (op == RHIF_MATVEC && x == y) return fail(RHIF_ERR_BAD_ARG, "F x needs distinct x and y");
   if (nrhs == 0) return RHIF_OK;
   cudaStream_t s = (cudaStream_t)stream;
+  if (op == RHIF_MATVEC) return matvec_impl(F, nrhs, x, ldx, y, ldy, s);
   if (x != y) {
     Launch t(kCatVector, s, 0.0, 16.0 * N * nrhs);
     launch_copy_cols(N, nrhs, x, ldx, y, ldy, s);
   }
-  return apply_dispatch(F, y, ldy, nrhs, s);
+  if (op == RHIF_SOLVE) return apply_dispatch(F, y, ldy, nrhs, s);
+  int rc = apply_prepare(F, nrhs);
+  if (rc) return rc;
+  return apply_launch(F, y, ldy, nrhs, s, op == RHIF_HALF ? 1 : 2);
 }
 
 // Vector blocks of a merged batch (uploaded once per handle).
@@ -1806,6 +1906,90 @@ int rhif_estimate_es(const rhif_handle* Fc, const double* x0, int maxit, double 
   }
   *es = est;
   if (iters) *iters = std::min(it, maxit);
+  CK(cudaGetLastError());
+  return RHIF_OK;
+}
+
+int rhif_estimate_ea(const rhif_handle* Fc, const double* x0, const double* x1, int maxit,
+                     double rel, double* ea, int* iters, void* stream) {
+  rhif_handle* F = const_cast<rhif_handle*>(Fc);
+  if (!F || !x0 || !ea || maxit < 1 || !(rel >= 0.0)) return fail(RHIF_ERR_BAD_ARG, "bad argument");
+  if (!F->pG.empty()) return fail(RHIF_ERR_BAD_ARG, "e_a of a batch: estimate each problem on its own");
+  if (!x1) x1 = x0;
+  const int64_t N = F->G.N;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nblk = vec_blocks(N);
+  int rc = ensure_work(F, 4 * N + nblk + 16);
+  if (rc) return rc;
+  double* v = F->work;
+  double* w = v + N;
+  double* t = w + N;
+  double* u = t + N;
+  double* part = u + N;
+  double* sc = part + nblk;
+  double* inv = sc + 8;
+  std::vector<double> hsc(8);
+  auto norm = [&](const double* x, double* out) -> int {
+    launch_dot_partial(N, x, N, x, N, 1, part, s);
+    launch_reduce(part, nblk, 1, sc, 0, 0.0, s);
+    CK(cudaMemcpyAsync(hsc.data(), sc, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *out = std::sqrt(hsc[kScFF]);
+    return RHIF_OK;
+  };
+  auto scale_to_v = [&](const double* src, double nv) -> int {
+    const double a = 1.0 / nv;
+    launch_copy_cols(N, 1, src, N, v, N, s);
+    CK(cudaMemcpyAsync(inv, &a, sizeof(double), cudaMemcpyHostToDevice, s));
+    launch_scale(N, v, inv, s);
+    CK(cudaStreamSynchronize(s));   // `a` is a host local
+    return RHIF_OK;
+  };
+  // out = M in: M = A - F (with_f) or A
+  auto apply_m = [&](const double* in, double* out, bool with_f) -> int {
+    launch_spmv(F->gd, F->diag, F->off, in, N, out, N, 1, nullptr, s);
+    if (!with_f) return RHIF_OK;
+    int r2 = matvec_impl(F, 1, in, N, u, N, s);
+    if (r2) return r2;
+    launch_sub(N, 1, out, N, u, N, out, N, s);
+    return RHIF_OK;
+  };
+  // power iteration on M^T M = M^2 (M symmetric), Sec. 4 estimator
+  auto power = [&](const double* start, bool with_f, double* est_out, int* it_out) -> int {
+    double nv = 0.0;
+    int r2 = norm(start, &nv);
+    if (r2) return r2;
+    if (nv == 0.0) return fail(RHIF_ERR_BAD_ARG, "zero start vector");
+    if ((r2 = scale_to_v(start, nv))) return r2;
+    double est = 0.0;
+    int it = 1;
+    for (; it <= maxit; ++it) {
+      if ((r2 = apply_m(v, t, with_f))) return r2;
+      if ((r2 = apply_m(t, w, with_f))) return r2;
+      double nw = 0.0;
+      if ((r2 = norm(w, &nw))) return r2;
+      const double cur = std::sqrt(nw);
+      if (nw == 0.0) {
+        est = 0.0;
+        break;
+      }
+      if ((r2 = scale_to_v(w, nw))) return r2;
+      if (est > 0.0 && std::fabs(cur - est) <= rel * cur) {
+        est = cur;
+        break;
+      }
+      est = cur;
+    }
+    *est_out = est;
+    *it_out = std::min(it, maxit);
+    return RHIF_OK;
+  };
+  double num = 0.0, den = 0.0;
+  int it_num = 0, it_den = 0;
+  if ((rc = power(x0, true, &num, &it_num))) return rc;
+  if ((rc = power(x1, false, &den, &it_den))) return rc;
+  *ea = den > 0.0 ? num / den : 0.0;
+  if (iters) *iters = it_num;
   CK(cudaGetLastError());
   return RHIF_OK;
 }

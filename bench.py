@@ -68,6 +68,8 @@ def _args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--tol", type=float, default=None,
                    help="ID tolerance of the single-problem workloads (default: the workload's)")
+    p.add_argument("--tc-kernel", action="store_true",
+                   help="throughput of the tensor-core tile product per operand kind (4096 x 4096 x 1024)")
     p.add_argument("--skeleton-growth", action="store_true",
                    help="3D root-size study with and without edge skeletonization (Remark 3.1)")
     p.add_argument("--paper-tables", action="store_true",
@@ -838,6 +840,37 @@ def paper_tables(args):
     print(json.dumps({"paper_tables": rows}))
 
 
+def tc_kernel(args):
+    """C -= A B^T through rhif_tc_gemm_check on 4096 x 4096 x 1024 FP32 data,
+    each operand kind: CUDA-event time per call (2 warm-up, 5 timed calls)
+    and the useful rate 2MNK / t.  One JSON line."""
+    import torch
+
+    import paper_1808_01364_gb300 as rhif
+    rhif.load()
+    M = N = 4096
+    K = 1024
+    g = torch.Generator(device="cuda").manual_seed(7)
+    A = torch.randn(K, M, device="cuda", generator=g).t()
+    B = torch.randn(K, N, device="cuda", generator=g).t()
+    out = {}
+    for kind in ("tf32x3", "tf32", "bf16"):
+        C = torch.zeros(N, M, device="cuda").t()
+        for _ in range(2):
+            rhif.rhif_tc_gemm_check(A, B, C, kind=kind)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(5):
+            rhif.rhif_tc_gemm_check(A, B, C, kind=kind)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 5
+        out[kind] = {"ms": ms, "useful_tflops": 2 * M * N * K / ms / 1e9,
+                     "products": 3 if kind == "tf32x3" else 1}
+    print(json.dumps({"tc_kernel": out, "M": M, "N": N, "K": K}))
+
+
 def skeleton_growth(args):
     """Root size |S_L| of 3D factors with and without edge skeletonization
     (Remark 3.1) as the grid grows: i.i.d. log-uniform [1e-3, 1e3] field,
@@ -886,6 +919,9 @@ def main():
     args = _args()
     if args.steps is None:
         args.steps = 5 if args.impl == "reference" else DEFAULT_STEPS[args.workload]
+    if args.tc_kernel:
+        tc_kernel(args)
+        return
     if args.skeleton_growth:
         skeleton_growth(args)
         return

@@ -106,7 +106,14 @@ typedef struct {
    *   a high part and a remainder: about FP32 accuracy); 0 = on (default),
    *   < 0 = off (CUDA cores).  FP64 factors always use the CUDA cores. */
   int tensor_cores;
-  int reserved[1];
+  /* leaf_fp64: FP32 factors (precision pattern): every 2D leaf whose estimated
+   *   condition number kappa_1(D A_II D) (D = diag(A_II)^{-1/2}; Hager's
+   *   estimate of ||(D A_II D)^{-1}||_1 from the FP32 band factor) exceeds
+   *   10^leaf_fp64 is eliminated again in FP64 arithmetic, its band, couplings
+   *   and Schur complement stored rounded to FP32.  0 = default (10^6),
+   *   < 0 = never, at most 30.  FP64 factors and 3D leaves ignore it; a leaf
+   *   whose FP32 Cholesky broke down is still reported as NOT_SPD. */
+  int leaf_fp64;
 } rhif_opts;
 
 typedef struct rhif_handle rhif_handle;
@@ -318,6 +325,7 @@ typedef struct {
   int precision;
   int units;              /* skeletonized units, all levels */
   double factor_ms;       /* device time of the last rhif_factor */
+  int fp64_leaves;        /* leaves of an FP32 factor re-eliminated in FP64 (leaf_fp64) */
 } rhif_stats_t;
 
 /* Copy statistics of a factor to host memory. */

@@ -49,7 +49,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("precondition", ctypes.c_int),
                 ("edge_skel_3d", ctypes.c_int), ("big_front", ctypes.c_int),
                 ("big_frame", ctypes.c_int), ("skel_cluster", ctypes.c_int),
-                ("tensor_cores", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
+                ("tensor_cores", ctypes.c_int), ("leaf_fp64", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -57,7 +57,7 @@ class Stats(ctypes.Structure):
                 ("active", ctypes.c_int64 * 16), ("factor_bytes", ctypes.c_int64),
                 ("flops", ctypes.c_double), ("apply_bytes", ctypes.c_double),
                 ("precision", ctypes.c_int), ("units", ctypes.c_int),
-                ("factor_ms", ctypes.c_double)]
+                ("factor_ms", ctypes.c_double), ("fp64_leaves", ctypes.c_int)]
 
 
 class KernelStat(ctypes.Structure):
@@ -375,7 +375,7 @@ class Factor:
         return {"levels": st.levels, "n": st.n, "root_size": st.root_size,
                 "active": list(st.active)[:st.levels], "factor_bytes": st.factor_bytes,
                 "flops": st.flops, "apply_bytes": st.apply_bytes, "precision": st.precision,
-                "units": st.units, "factor_ms": st.factor_ms}
+                "units": st.units, "factor_ms": st.factor_ms, "fp64_leaves": st.fp64_leaves}
 
     def skeletons(self, level: int, phase: int = 0):
         """[(dofs in pivot order, rank)] for every unit of a level/phase."""
@@ -397,14 +397,14 @@ class Factor:
 
 def rhif_factor(csr, ns, leaf: int, tol: float, precision: str = "fp64", precondition=True,
                 edge_skel_3d=False, stream=None, big_front=0, big_frame=0,
-                skel_cluster=0, tensor_cores=0) -> Factor:
+                skel_cluster=0, tensor_cores=0, leaf_fp64=0) -> Factor:
     """PHIF factorization of the CSR matrix ``csr = (rowptr, col, val)`` on grid ``ns``.
     ``big_front`` / ``big_frame`` / ``skel_cluster`` are the scheduling options of
-    ``rhif_opts``."""
+    ``rhif_opts``; ``leaf_fp64`` the FP64 leaf fallback of FP32 factors."""
     load()
     A = _csr(csr, ns)
     o = _opts(precision, precondition, edge_skel_3d, big_front, big_frame, skel_cluster,
-              tensor_cores)
+              tensor_cores, leaf_fp64)
     h = ctypes.c_void_p()
     _check(_lib.rhif_factor(ctypes.byref(A), ctypes.byref(_grid(ns)), int(leaf), float(tol),
                             ctypes.byref(o), _stream(stream), ctypes.byref(h)))
@@ -641,7 +641,7 @@ def rhif_solve(log_a: torch.Tensor, f: torch.Tensor, ns, **opts) -> torch.Tensor
 
 
 def _opts(precision="fp64", precondition=True, edge_skel_3d=False, big_front=0,
-          big_frame=0, skel_cluster=0, tensor_cores=0) -> Opts:
+          big_frame=0, skel_cluster=0, tensor_cores=0, leaf_fp64=0) -> Opts:
     o = Opts()
     _lib.rhif_default_opts(ctypes.byref(o))
     o.precision = {"fp64": RHIF_FP64, "fp32": RHIF_MIXED_FP32, "mixed": RHIF_MIXED_FP32,
@@ -655,6 +655,7 @@ def _opts(precision="fp64", precondition=True, edge_skel_3d=False, big_front=0,
     o.big_frame = int(big_frame)
     o.skel_cluster = int(skel_cluster)
     o.tensor_cores = int(tensor_cores)
+    o.leaf_fp64 = int(leaf_fp64)
     return o
 
 

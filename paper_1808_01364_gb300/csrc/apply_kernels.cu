@@ -36,93 +36,6 @@ __device__ inline bool staged_ok(uint64_t* bar, int* status, int level, int kind
 // level 0: banded leaf factors, one warp per cell
 // ---------------------------------------------------------------------------
 
-// y <- L^{-1} y with L banded (column k of band holds 1/L[k,k], L[k+1..k+w, k]); one warp.
-template <typename T>
-__device__ inline void warp_band_fwd(const T* band, int n, int w, T* y) {
-  const int lane = threadIdx.x & 31;
-  const int w1 = w + 1;
-  for (int k = 0; k < n; ++k) {
-    const T yk = y[k] * band[k * w1];
-    __syncwarp();
-    if (lane == 0) y[k] = yk;
-    const int wk = min(w, n - 1 - k);
-    for (int d = 1 + lane; d <= wk; d += 32) y[k + d] -= band[k * w1 + d] * yk;
-    __syncwarp();
-  }
-}
-
-// y <- L^{-T} y with L banded; one warp.
-template <typename T>
-__device__ inline void warp_band_bwd(const T* band, int n, int w, T* y) {
-  const int lane = threadIdx.x & 31;
-  const int w1 = w + 1;
-  for (int k = n - 1; k >= 0; --k) {
-    const int wk = min(w, n - 1 - k);
-    T s = T(0);
-    for (int d = 1 + lane; d <= wk; d += 32) s += band[k * w1 + d] * y[k + d];
-    s = warp_sum(s);
-    if (lane == 0) y[k] = (y[k] - s) * band[k * w1];
-    __syncwarp();
-  }
-}
-
-// Blocked forms for w <= 31: blocks of w rows, lane r owns row s + r.  The
-// coupling of a block to the w rows before (after) it is one dot product per
-// lane; the triangle inside the block is solved in registers with shuffles.
-template <typename T>
-__device__ inline void warp_band_fwd_blk(const T* band, int n, int w, T* y) {
-  const int lane = threadIdx.x & 31;
-  const int w1 = w + 1;
-  for (int s0 = 0; s0 < n; s0 += w) {
-    const int B = min(w, n - s0);
-    const int i = s0 + lane;
-    T acc = T(0);
-    if (lane < B) {
-      acc = y[i];
-      for (int d = lane + 1; d <= w; ++d) {
-        const int j = i - d;
-        if (j < 0) break;
-        acc -= band[j * w1 + d] * y[j];
-      }
-    }
-    for (int c = 0; c < B; ++c) {
-      const T yc = __shfl_sync(0xffffffffu, acc, c) * band[(s0 + c) * w1];
-      if (lane == c) acc = yc;
-      else if (lane > c && lane < B) acc -= band[(s0 + c) * w1 + (lane - c)] * yc;
-    }
-    if (lane < B) y[i] = acc;
-    __syncwarp();
-  }
-}
-
-template <typename T>
-__device__ inline void warp_band_bwd_blk(const T* band, int n, int w, T* y) {
-  const int lane = threadIdx.x & 31;
-  const int w1 = w + 1;
-  const int nblk = (n + w - 1) / w;
-  for (int bi = nblk - 1; bi >= 0; --bi) {
-    const int s0 = bi * w;
-    const int B = min(w, n - s0);
-    const int i = s0 + lane;
-    T acc = T(0);
-    if (lane < B) {
-      acc = y[i];
-      for (int d = B - lane; d <= w; ++d) {
-        const int j = i + d;
-        if (j >= n) break;
-        acc -= band[i * w1 + d] * y[j];
-      }
-    }
-    for (int c = B - 1; c >= 0; --c) {
-      const T yc = __shfl_sync(0xffffffffu, acc, c) * band[(s0 + c) * w1];
-      if (lane == c) acc = yc;
-      else if (lane < c) acc -= band[(s0 + lane) * w1 + (c - lane)] * yc;
-    }
-    if (lane < B) y[i] = acc;
-    __syncwarp();
-  }
-}
-
 // Forms for w <= 15 (all 2D leaves up to leaf 16).  The factor stores, in
 // the in-block slots of every diagonal w x w block of the band, the explicit
 // inverse X of that block (k_band_block_inverse); the slots coupling a block

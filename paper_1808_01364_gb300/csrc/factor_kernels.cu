@@ -323,13 +323,19 @@ size_t leaf_stream_smem(int max_nI, int max_w, int leaf, int d) {
   return band + win + t + pairs + 64;
 }
 
-template <typename T>
+// T: arithmetic; S: storage of the band, the couplings and the frame (S = float
+// with T = double is the FP64 re-elimination of the FP32 factor's leaves whose
+// condition estimate is too large: computed in FP64, stored rounded to FP32).
+// only: when not null, the cells with only[c] == 0 return at once.
+template <typename T, typename S = T>
 __global__ void __launch_bounds__(kThreads)
-k_leaf_stream(GeoDev G, LevelDev Lv, const double* diag, const double* off, int* status) {
+k_leaf_stream(GeoDev G, LevelDev Lv, const double* diag, const double* off, int* status,
+              const int* only = nullptr) {
   extern __shared__ unsigned char smraw[];
   __shared__ int bad;
   __shared__ T s_piv;
   const int c = blockIdx.x;
+  if (only && !only[c]) return;
   const int nI = Lv.nI[c], nB = Lv.nB[c], n = nI + nB, w = Lv.band_w[c];
   const int w1 = w + 1;
   const int tid = threadIdx.x;
@@ -347,9 +353,9 @@ k_leaf_stream(GeoDev G, LevelDev Lv, const double* diag, const double* off, int*
   short* pairs = (short*)p;                              // (d1, d2) with 1 <= d2 <= d1 <= w
   const int npair = w * (w + 1) / 2;
   int ld;
-  T* Fr = frame_of<T>(Lv, c, &ld);
+  S* Fr = frame_of<S>(Lv, c, &ld);
   int* ci = Lv.cpl_i + Lv.b_off[c];
-  T* ca = (T*)Lv.cpl_a + Lv.b_off[c];
+  S* ca = (S*)Lv.cpl_a + Lv.b_off[c];
   const int m = G.leaf, m1 = m + 1;
   int origin[3] = {0, 0, 0};
   {
@@ -373,7 +379,7 @@ k_leaf_stream(GeoDev G, LevelDev Lv, const double* diag, const double* off, int*
   for (int i = tid; i < tab; i += blockDim.x) postab[i] = -1;
   for (int i = tid; i < nI * w1; i += blockDim.x) sband[i] = T(0);
   for (int i = tid; i < w1 * kStreamNB; i += blockDim.x) win[i] = T(0);
-  for (int64_t i = tid; i < (int64_t)nB * nB; i += blockDim.x) Fr[i] = T(0);
+  for (int64_t i = tid; i < (int64_t)nB * nB; i += blockDim.x) Fr[i] = S(0);
   __syncthreads();
   for (int q = tid; q < n; q += blockDim.x) {
     int x[3];
@@ -400,9 +406,9 @@ k_leaf_stream(GeoDev G, LevelDev Lv, const double* diag, const double* off, int*
     const int b = q - nI;
     if (q < nI) sband[q * w1] = T(diag[g]);
     else {
-      Fr[b + (int64_t)b * ld] = T(diag[g] / double(1 << onplane));
+      Fr[b + (int64_t)b * ld] = S(diag[g] / double(1 << onplane));
       ci[b] = -1;
-      ca[b] = T(0);
+      ca[b] = S(0);
     }
     for (int a = 0; a < G.d; ++a) {
       const double share = double(1 << (onplane - (x[a] % m == 0)));
@@ -417,9 +423,9 @@ k_leaf_stream(GeoDev G, LevelDev Lv, const double* diag, const double* off, int*
           if (r < nI && r > q) sband[q * w1 + (r - q)] = T(v);
         } else if (r < nI) {
           ci[b] = r;
-          ca[b] = T(v);
+          ca[b] = S(v);
         } else {
-          Fr[b + (int64_t)(r - nI) * ld] = T(v / share);
+          Fr[b + (int64_t)(r - nI) * ld] = S(v / share);
         }
       }
     }
@@ -427,11 +433,11 @@ k_leaf_stream(GeoDev G, LevelDev Lv, const double* diag, const double* off, int*
   __syncthreads();
   // initial rows 0..w of the Z window: the single entry a_b of column b sits in row ci[b]
   for (int b = tid; b < nB; b += blockDim.x)
-    if (ci[b] >= 0 && ci[b] <= w) win[(ci[b] % w1) * kStreamNB + b] = ca[b];
+    if (ci[b] >= 0 && ci[b] <= w) win[(ci[b] % w1) * kStreamNB + b] = T(ca[b]);
   // fixed work assignment: Z-window column zb, rows 1 + zr0 + 4j; band pairs tid and tid + 256
   const int zb = tid & (kStreamNB - 1), zr0 = tid >> 6;
   const int my_ci = (tid < nB) ? ci[tid] : -1;
-  const T my_ca = (tid < nB) ? ca[tid] : T(0);
+  const T my_ca = (tid < nB) ? T(ca[tid]) : T(0);
   int pd1[2] = {0, 0}, pd2[2] = {0, 0};
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
@@ -510,12 +516,12 @@ k_leaf_stream(GeoDev G, LevelDev Lv, const double* diag, const double* off, int*
 #pragma unroll
     for (int bq = 0; bq < 4; ++bq) {
       const int i = ti + a, j = tj + bq;
-      if (i < nB && j < nB && i >= j) Fr[i + (int64_t)j * ld] -= acc[a][bq];
+      if (i < nB && j < nB && i >= j) Fr[i + (int64_t)j * ld] = S(T(Fr[i + (int64_t)j * ld]) - acc[a][bq]);
     }
   // band with reciprocal diagonal for the application
-  T* band = (T*)Lv.band + Lv.band_off[c];
+  S* band = (S*)Lv.band + Lv.band_off[c];
   for (int i = tid; i < nI * w1; i += blockDim.x)
-    band[i] = (i % w1 == 0) ? T(1) / sband[i] : sband[i];
+    band[i] = S((i % w1 == 0) ? T(1) / sband[i] : sband[i]);
   __syncthreads();
   if (tid == 0 && bad) report(status, RHIF_ERR_NOT_SPD, 0, kKindCell, c);
 }
@@ -2071,6 +2077,107 @@ __global__ void __launch_bounds__(kThreads) k_skel_cluster(LevelDev Lv, PhaseDev
               status);
 }
 
+// ---------------------------------------------------------------------------
+// FP64 leaf fallback of the FP32 factor: condition estimate of every leaf
+// ---------------------------------------------------------------------------
+
+// kappa_1(B) = ||B||_1 ||B^{-1}||_1 of the Jacobi-scaled leaf block
+// B = D A_II D, D = diag(A_II)^{-1/2}, from the leaf's banded FP32 factor
+// (A_II = L L^T; band column k: 1/L_kk, L[k+1..k+w, k]).  The leaves this
+// runs on are 2D (at most 64 boundary DOFs): A_II is the five-point stencil
+// of the interior box in lexicographic order, nonzero at offsets 0, +-1 and
+// +-w only, so ||B||_1 is the largest row sum of |B| over those entries of
+// L L^T (the others vanish in exact arithmetic); ||B^{-1}||_1 comes from one
+// application of B^{-1} = S L^{-T} L^{-1} S (S = D^{-1}) to the vector of
+// ones, exact for these M-matrices (see below).  One warp per leaf; flag[c] = 1 when
+// the estimate exceeds `thresh` or is not finite, counted in *count.
+template <typename T>
+__global__ void __launch_bounds__(128) k_leaf_cond(LevelDev Lv, double thresh, int* flag,
+                                                   int* count, int per_warp) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (c >= Lv.ncell) return;
+  const int n = Lv.nI[c], w = Lv.band_w[c], w1 = w + 1;
+  const T* band = (const T*)Lv.band + Lv.band_off[c];
+  T* sd = (T*)(smraw + (size_t)warp * per_warp);   // S = sqrt(diag A_II)
+  T* x = sd + Lv.max_nI;
+  T* y = x + Lv.max_nI;
+  // x temporarily holds L_kk (the band keeps 1/L_kk for the solves)
+  for (int k = lane; k < n; k += 32) x[k] = T(1) / band[k * w1];
+  __syncwarp();
+  auto Lik = [&](int i, int k) -> T {   // L[i, k], k <= i <= k + w
+    return i == k ? x[k] : band[k * w1 + (i - k)];
+  };
+  auto aij = [&](int i, int j) -> T {   // (L L^T)_ij, |i - j| <= w
+    const int lo = max(0, max(i, j) - w), hi = min(i, j);
+    T a = T(0);
+    for (int k = lo; k <= hi; ++k) a += Lik(i, k) * Lik(j, k);
+    return a;
+  };
+  for (int i = lane; i < n; i += 32) sd[i] = my_sqrt(aij(i, i));
+  __syncwarp();
+  // ||B||_1: row sums of |d_i a_ij d_j| over the stencil offsets
+  T norm1 = T(0);
+  for (int i = lane; i < n; i += 32) {
+    T rs = T(1);
+    const int offs[4] = {-w, -1, 1, w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = i + offs[q];
+      if (j < 0 || j >= n || (q == 0 && w == 1) || (q == 3 && w == 1)) continue;
+      rs += fabs(aij(i, j)) / (sd[i] * sd[j]);
+    }
+    norm1 = fmax(norm1, rs);
+  }
+  for (int o = 16; o > 0; o >>= 1) norm1 = fmax(norm1, __shfl_xor_sync(0xffffffffu, norm1, o));
+  auto binv = [&](T* v) {   // v <- S L^{-T} L^{-1} S v
+    for (int i = lane; i < n; i += 32) v[i] *= sd[i];
+    __syncwarp();
+    if (w >= 1 && w <= 31) {
+      warp_band_fwd_blk(band, n, w, v);
+      warp_band_bwd_blk(band, n, w, v);
+    } else {
+      warp_band_fwd(band, n, w, v);
+      warp_band_bwd(band, n, w, v);
+    }
+    for (int i = lane; i < n; i += 32) v[i] *= sd[i];
+    __syncwarp();
+  };
+  // ||B^{-1}||_1 = max_i (B^{-1} 1)_i: B is an M-matrix (unit diagonal,
+  // nonpositive off-diagonal entries: the five-point stencil has positive
+  // edge weights), so B^{-1} >= 0 entrywise and its largest column sum is the
+  // largest entry of B^{-1} applied to the vector of ones (B = B^T).  A
+  // negative entry (not an M-matrix) leaves max |.|, a lower bound.
+  for (int i = lane; i < n; i += 32) y[i] = T(1);
+  __syncwarp();
+  binv(y);
+  T est = T(0);
+  for (int i = lane; i < n; i += 32) est = fmax(est, fabs(y[i]));
+  for (int o = 16; o > 0; o >>= 1) est = fmax(est, __shfl_xor_sync(0xffffffffu, est, o));
+  const double kappa = double(norm1) * double(est);
+  if (lane == 0) {
+    const int f = !(kappa <= thresh);   // above the threshold, or not finite
+    flag[c] = f;
+    if (f) atomicAdd(count, 1);
+  }
+}
+
+void launch_leaf_cond(const LevelDev& Lv, double thresh, int* flag, int* count, cudaStream_t s) {
+  if (!Lv.ncell) return;
+  const int per = (int)(((size_t)4 * Lv.max_nI * sizeof(float) + 15) & ~size_t(15));
+  k_leaf_cond<float><<<(Lv.ncell + 3) / 4, 128, 4 * per, s>>>(Lv, thresh, flag, count, per);
+}
+
+// The flagged leaves of an FP32 factor eliminated again in FP64 (streaming
+// leaf kernel, FP64 arithmetic, results rounded to the FP32 storage).
+void launch_leaf_fp64_redo(const GeoDev& G, const LevelDev& Lv, const double* diag,
+                           const double* off, int* status, const int* flag, cudaStream_t s) {
+  if (!Lv.ncell || Lv.max_nB > kStreamNB) return;
+  const size_t sm = leaf_stream_smem<double>(Lv.max_nI, Lv.max_w, G.leaf, G.d);
+  k_leaf_stream<double, float><<<Lv.ncell, kThreads, sm, s>>>(G, Lv, diag, off, status, flag);
+}
+
 // Redundant DOFs leave the active set only after every ID of the phase has
 // been taken (the IDs all read the same matrix, Sec. 2.2 parallel order).
 __global__ void k_mark_dead(LevelDev Lv, PhaseDev Ph, uint8_t* alive) {
@@ -2348,6 +2455,11 @@ int configure_factor_kernels() {
     e = cudaFuncSetAttribute(k_precond_scale<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_leaf_stream<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_leaf_stream<double, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             big);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_leaf_cond<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   return e == cudaSuccess ? 0 : -1;
 }
 

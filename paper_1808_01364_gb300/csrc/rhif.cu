@@ -161,13 +161,14 @@ int Packer::upload(void* dst, cudaStream_t s) const {
 enum Cat {
   kCatStencil, kCatLeafElim, kCatExpandGids, kCatExtendAdd, kCatPartialChol, kCatPrecondDiag, kCatPrecondScale,
   kCatSkel, kCatApplyCellUp, kCatApplyCellDown, kCatApplyGroupUp, kCatApplyGroupDown, kCatSpmv,
-  kCatVector, kCatAssemble, kCatGrad, kCatApplyLeafUp, kCatApplyLeafDown, kCatBandInverse, kNumCat
+  kCatVector, kCatAssemble, kCatGrad, kCatApplyLeafUp, kCatApplyLeafDown, kCatBandInverse,
+  kCatLeafCond, kCatLeafFp64, kNumCat
 };
 static const char* kCatName[kNumCat] = {
     "stencil_from_csr", "leaf_elim", "expand_gids", "extend_add", "partial_chol", "precond_diag",
     "precond_scale", "skel", "apply_cell_up", "apply_cell_down", "apply_group_up",
     "apply_group_down", "spmv", "pcg_vector", "assemble_fd", "grad_logcoef", "apply_leaf_up",
-    "apply_leaf_down", "band_inverse"};
+    "apply_leaf_down", "band_inverse", "leaf_cond", "leaf_fp64"};
 struct KStat {
   int64_t launches = 0;
   double ms = 0, flops = 0, bytes = 0;
@@ -278,6 +279,8 @@ struct rhif_handle {
   int precision = RHIF_FP64;
   bool precondition = true, edge_skel = false;
   bool precond_diag = false;   // diagonal local preconditioner in place of block Cholesky
+  double leaf_fp64 = 0.0;      // FP32 factors: FP64 re-elimination of leaves above this condition (0 = never)
+  int fp64_leaves = -1;        // leaves re-eliminated in FP64 (read back on request)
   int big_front = 0, big_frame = 0;   // many-CTA thresholds (see rhif_opts)
   int skel_cluster = 0;
   bool skel_warp = true;   // small units: one warp each
@@ -737,6 +740,23 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
       {
         Launch t(kCatLeafElim, s, lvl_flops, 0.0);
         launch_leaf_elim<T>(H->gd, S.dev, H->diag, H->off, H->status, s);
+      }
+      // precision pattern: leaves of an FP32 factor whose Jacobi-scaled
+      // condition estimate exceeds the threshold are eliminated again in FP64
+      // (their band, couplings and frame rounded to FP32) before any later
+      // step reads them
+      if (sizeof(T) == 4 && H->leaf_fp64 > 0.0 && P.max_nB <= 64) {
+        int* flag = nullptr;
+        if ((rc = H->mem.get((void**)&flag, P.ncell() * sizeof(int)))) return rc;
+        {
+          Launch t(kCatLeafCond, s, 0.0, 0.0);
+          launch_leaf_cond(S.dev, H->leaf_fp64, flag, H->status + 4, s);
+        }
+        {
+          Launch t(kCatLeafFp64, s, 0.0, 0.0);
+          launch_leaf_fp64_redo(H->gd, S.dev, H->diag, H->off, H->status, flag, s);
+        }
+        H->mem.release(flag);
       }
     } else {
       for (int c = 0; c < P.ncell(); ++c) {
@@ -1258,6 +1278,8 @@ static int set_options(rhif_handle* H, int dim, double tol, const rhif_opts* o) 
     return fail(RHIF_ERR_BAD_ARG, "skel_cluster must be a power of two <= 16");
   H->skel_cluster = o->skel_cluster;
   H->tensor_cores = o->tensor_cores >= 0;
+  if (o->leaf_fp64 > 30) return fail(RHIF_ERR_BAD_ARG, "leaf_fp64 must be <= 30");
+  H->leaf_fp64 = o->leaf_fp64 < 0 ? 0.0 : std::pow(10.0, o->leaf_fp64 == 0 ? 6 : o->leaf_fp64);
   H->tol = tol;
   return RHIF_OK;
 }
@@ -2047,6 +2069,16 @@ int rhif_stats(const rhif_handle* F, rhif_stats_t* st) {
   st->precision = F->precision;
   st->units = F->units;
   st->factor_ms = F->factor_ms;
+  st->fp64_leaves = 0;
+  if (F->precision != RHIF_FP64 && F->leaf_fp64 > 0.0 && F->status) {
+    rhif_handle* H = const_cast<rhif_handle*>(F);
+    if (H->fp64_leaves < 0) {   // the counter of the condition kernel (status word 4)
+      int v = 0;
+      CK(cudaMemcpy(&v, H->status + 4, sizeof(int), cudaMemcpyDeviceToHost));
+      H->fp64_leaves = v;
+    }
+    st->fp64_leaves = H->fp64_leaves;
+  }
   return RHIF_OK;
 }
 

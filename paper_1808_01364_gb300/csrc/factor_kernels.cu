@@ -2085,49 +2085,48 @@ __global__ void __launch_bounds__(kThreads) k_skel_cluster(LevelDev Lv, PhaseDev
 // B = D A_II D, D = diag(A_II)^{-1/2}, from the leaf's banded FP32 factor
 // (A_II = L L^T; band column k: 1/L_kk, L[k+1..k+w, k]).  The leaves this
 // runs on are 2D (at most 64 boundary DOFs): A_II is the five-point stencil
-// of the interior box in lexicographic order, nonzero at offsets 0, +-1 and
-// +-w only, so ||B||_1 is the largest row sum of |B| over those entries of
-// L L^T (the others vanish in exact arithmetic); ||B^{-1}||_1 comes from one
-// application of B^{-1} = S L^{-T} L^{-1} S (S = D^{-1}) to the vector of
-// ones, exact for these M-matrices (see below).  One warp per leaf; flag[c] = 1 when
+// of the interior box in lexicographic order (x-neighbours at +-1 within a
+// row of w, y-neighbours at +-w), so D and ||B||_1 come from the stencil form
+// itself; ||B^{-1}||_1 comes from one application of
+// B^{-1} = S L^{-T} L^{-1} S (S = D^{-1}) to the vector of ones, exact for
+// these M-matrices (see below).  One warp per leaf; flag[c] = 1 when
 // the estimate exceeds `thresh` or is not finite, counted in *count.
 template <typename T>
-__global__ void __launch_bounds__(128) k_leaf_cond(LevelDev Lv, double thresh, int* flag,
+__global__ void __launch_bounds__(128) k_leaf_cond(GeoDev G, LevelDev Lv, const double* diag,
+                                                   const double* off, double thresh, int* flag,
                                                    int* count, int per_warp) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c = blockIdx.x * (blockDim.x >> 5) + warp;
   if (c >= Lv.ncell) return;
   const int n = Lv.nI[c], w = Lv.band_w[c], w1 = w + 1;
-  const T* band = (const T*)Lv.band + Lv.band_off[c];
-  T* sd = (T*)(smraw + (size_t)warp * per_warp);   // S = sqrt(diag A_II)
+  const int32_t* gid = Lv.gids + Lv.gid_off[c];
+  const int64_t dbase = bind_cell_geo(Lv, c, G, diag, off);
+  T* band = (T*)(smraw + (size_t)warp * per_warp);   // the band, staged (coalesced copy)
+  T* sd = band + (size_t)Lv.max_nI * (Lv.max_w + 1);   // S = sqrt(diag A_II)
   T* x = sd + Lv.max_nI;
   T* y = x + Lv.max_nI;
-  // x temporarily holds L_kk (the band keeps 1/L_kk for the solves)
-  for (int k = lane; k < n; k += 32) x[k] = T(1) / band[k * w1];
+  {
+    const T* g = (const T*)Lv.band + Lv.band_off[c];
+    for (int i = lane; i < n * w1; i += 32) band[i] = g[i];
+    __syncwarp();
+  }
+  // entries of A_II from the stencil form (interior in lexicographic order:
+  // x-neighbours at +-1 inside a row of w, y-neighbours at +-w)
+  // (in T: FP64 arithmetic is scarce on this GPU and the estimate needs no more)
+  for (int i = lane; i < n; i += 32) sd[i] = my_sqrt(T(diag[gid[i] - dbase]));
   __syncwarp();
-  auto Lik = [&](int i, int k) -> T {   // L[i, k], k <= i <= k + w
-    return i == k ? x[k] : band[k * w1 + (i - k)];
-  };
-  auto aij = [&](int i, int j) -> T {   // (L L^T)_ij, |i - j| <= w
-    const int lo = max(0, max(i, j) - w), hi = min(i, j);
-    T a = T(0);
-    for (int k = lo; k <= hi; ++k) a += Lik(i, k) * Lik(j, k);
-    return a;
-  };
-  for (int i = lane; i < n; i += 32) sd[i] = my_sqrt(aij(i, i));
-  __syncwarp();
-  // ||B||_1: row sums of |d_i a_ij d_j| over the stencil offsets
+  // ||B||_1: row sums of |d_i a_ij d_j|
   T norm1 = T(0);
   for (int i = lane; i < n; i += 32) {
+    const int64_t g = gid[i] - dbase;
+    const int ix = i % w;
+    const T ri = T(1) / sd[i];
     T rs = T(1);
-    const int offs[4] = {-w, -1, 1, w};
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int j = i + offs[q];
-      if (j < 0 || j >= n || (q == 0 && w == 1) || (q == 3 && w == 1)) continue;
-      rs += fabs(aij(i, j)) / (sd[i] * sd[j]);
-    }
+    if (ix + 1 < w && i + 1 < n) rs += fabs(T(off[g])) * ri / sd[i + 1];
+    if (ix > 0) rs += fabs(T(off[g - 1])) * ri / sd[i - 1];
+    if (i + w < n) rs += fabs(T(off[G.N + g])) * ri / sd[i + w];
+    if (i >= w) rs += fabs(T(off[G.N + g - G.stride[1]])) * ri / sd[i - w];
     norm1 = fmax(norm1, rs);
   }
   for (int o = 16; o > 0; o >>= 1) norm1 = fmax(norm1, __shfl_xor_sync(0xffffffffu, norm1, o));
@@ -2163,10 +2162,12 @@ __global__ void __launch_bounds__(128) k_leaf_cond(LevelDev Lv, double thresh, i
   }
 }
 
-void launch_leaf_cond(const LevelDev& Lv, double thresh, int* flag, int* count, cudaStream_t s) {
+void launch_leaf_cond(const GeoDev& G, const LevelDev& Lv, const double* diag, const double* off,
+                      double thresh, int* flag, int* count, cudaStream_t s) {
   if (!Lv.ncell) return;
-  const int per = (int)(((size_t)4 * Lv.max_nI * sizeof(float) + 15) & ~size_t(15));
-  k_leaf_cond<float><<<(Lv.ncell + 3) / 4, 128, 4 * per, s>>>(Lv, thresh, flag, count, per);
+  const int per = (int)(((size_t)(Lv.max_w + 4) * Lv.max_nI * sizeof(float) + 15) & ~size_t(15));
+  k_leaf_cond<float><<<(Lv.ncell + 3) / 4, 128, 4 * per, s>>>(G, Lv, diag, off, thresh, flag,
+                                                             count, per);
 }
 
 // The flagged leaves of an FP32 factor eliminated again in FP64 (streaming

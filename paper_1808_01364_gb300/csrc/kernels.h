@@ -156,7 +156,8 @@ void launch_bscatter(const VecSeg& S, const BatchGeo* bg, const double* x, int64
                      double* const* dst, int nrhs, cudaStream_t s);
 
 // FP64 leaf fallback of FP32 factors (factor_kernels.cu)
-void launch_leaf_cond(const LevelDev& Lv, double thresh, int* flag, int* count, cudaStream_t s);
+void launch_leaf_cond(const GeoDev& G, const LevelDev& Lv, const double* diag, const double* off,
+                      double thresh, int* flag, int* count, cudaStream_t s);
 void launch_leaf_fp64_redo(const GeoDev& G, const LevelDev& Lv, const double* diag,
                            const double* off, int* status, const int* flag, cudaStream_t s);
 

@@ -750,7 +750,7 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
         if ((rc = H->mem.get((void**)&flag, P.ncell() * sizeof(int)))) return rc;
         {
           Launch t(kCatLeafCond, s, 0.0, 0.0);
-          launch_leaf_cond(S.dev, H->leaf_fp64, flag, H->status + 4, s);
+          launch_leaf_cond(H->gd, S.dev, H->diag, H->off, H->leaf_fp64, flag, H->status + 4, s);
         }
         {
           Launch t(kCatLeafFp64, s, 0.0, 0.0);

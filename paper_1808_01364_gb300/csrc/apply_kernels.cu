@@ -283,6 +283,190 @@ k_apply_leaf_down(LevelDev Lv, double* x, int64_t ldx, int nrhs, int per_warp_by
 }
 
 // ---------------------------------------------------------------------------
+// level 0, many right-hand sides: one warp per (leaf, 32 right-hand sides),
+// lane = right-hand side.  The band (inverted diagonal blocks, w <= 15) is
+// staged once in shared memory and read as broadcasts; each lane solves its
+// own vector with the operations of warp_band_{fwd,bwd}_inv in the same
+// order.  The vectors sit in shared memory with a row of 33 per DOF
+// (v[i * 33 + r]): gathers and scatters run one right-hand side at a time with
+// the lanes over DOFs (coalesced along the leaf's rows), the solves one lane
+// per right-hand side (conflict-free).
+// ---------------------------------------------------------------------------
+
+constexpr int kMrLd = 33;
+
+template <typename T>
+__device__ inline void lane_band_fwd_inv(const T* band, int n, int w, T* v) {
+  const int lane = threadIdx.x & 31;
+  const int w1 = w + 1;
+  for (int s0 = 0; s0 < n; s0 += w) {
+    const int B = min(w, n - s0);
+    T acc[kBandRegW];
+#pragma unroll
+    for (int r = 0; r < kBandRegW; ++r) {
+      if (r >= B) break;
+      const int i = s0 + r;
+      T a = v[i * kMrLd + lane];
+#pragma unroll
+      for (int d = 1; d <= kBandRegW; ++d) {
+        const int j = i - d;
+        const bool ok = d <= w && d > r && j >= 0;
+        const T cp = ok ? band[j * w1 + d] : T(0);
+        const T yp = ok ? v[j * kMrLd + lane] : T(0);
+        a -= cp * yp;
+      }
+      acc[r] = a;
+    }
+#pragma unroll
+    for (int r = 0; r < kBandRegW; ++r) {
+      if (r >= B) break;
+      T out = T(0);
+#pragma unroll
+      for (int c = 0; c < kBandRegW; ++c) {
+        const T xr = (c <= r && c < B) ? band[(s0 + c) * w1 + (r - c)] : T(0);
+        out += xr * (c < B ? acc[c] : T(0));
+      }
+      v[(s0 + r) * kMrLd + lane] = out;
+    }
+  }
+}
+
+template <typename T>
+__device__ inline void lane_band_bwd_inv(const T* band, int n, int w, T* v) {
+  const int lane = threadIdx.x & 31;
+  const int w1 = w + 1;
+  const int nblk = (n + w - 1) / w;
+  for (int bi = nblk - 1; bi >= 0; --bi) {
+    const int s0 = bi * w;
+    const int B = min(w, n - s0);
+    T acc[kBandRegW];
+#pragma unroll
+    for (int r = 0; r < kBandRegW; ++r) {
+      if (r >= B) break;
+      const int i = s0 + r;
+      T a = v[i * kMrLd + lane];
+#pragma unroll
+      for (int d = 1; d <= kBandRegW; ++d) {
+        const int j = i + d;
+        const bool ok = d <= w && d >= B - r && j < n;
+        const T cp = ok ? band[i * w1 + d] : T(0);
+        const T yn = ok ? v[j * kMrLd + lane] : T(0);
+        a -= cp * yn;
+      }
+      acc[r] = a;
+    }
+#pragma unroll
+    for (int r = 0; r < kBandRegW; ++r) {
+      if (r >= B) break;
+      T out = T(0);
+#pragma unroll
+      for (int c = 0; c < kBandRegW; ++c) {
+        const T xc = (c >= r && c < B) ? band[(s0 + r) * w1 + (c - r)] : T(0);
+        out += xc * (c < B ? acc[c] : T(0));
+      }
+      v[(s0 + r) * kMrLd + lane] = out;
+    }
+  }
+}
+
+// Per-warp shared memory of the many-right-hand-side leaf kernels: the band,
+// two vectors of max_nI rows and one of max_nB rows, kMrLd entries a row.
+template <typename T>
+__host__ __device__ inline size_t leaf_mr_bytes(int max_nI, int max_nB, int max_w) {
+  return round16((size_t)max_nI * (max_w + 1) * sizeof(T)) +
+         2 * round16((size_t)max_nI * kMrLd * sizeof(T)) + round16((size_t)max_nB * kMrLd * sizeof(T));
+}
+
+template <typename T>
+__device__ inline const T* leaf_mr_stage(const LevelDev& Lv, int c, unsigned char* base) {
+  const int lane = threadIdx.x & 31;
+  T* sb = (T*)base;
+  const T* g = (const T*)Lv.band + Lv.band_off[c];
+  const int cnt = Lv.nI[c] * (Lv.band_w[c] + 1);
+  for (int i = lane; i < cnt; i += 32) sb[i] = g[i];
+  __syncwarp();
+  return sb;
+}
+
+// E_0^T per leaf for right-hand sides 32 * blockIdx.y + lane: as k_apply_leaf_up.
+template <typename T>
+__global__ void __launch_bounds__(128)
+k_apply_leaf_up_mr(LevelDev Lv, double* x, int64_t ldx, int nrhs, double* ubuf, int64_t ldu,
+                   int per_warp_bytes) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (c >= Lv.ncell) return;
+  unsigned char* base = smraw + (size_t)warp * per_warp_bytes;
+  const T* band = leaf_mr_stage<T>(Lv, c, base);
+  T* y = (T*)(base + round16((size_t)Lv.max_nI * (Lv.max_w + 1) * sizeof(T)));
+  T* z = y + (round16((size_t)Lv.max_nI * kMrLd * sizeof(T)) / sizeof(T));
+  const int nI = Lv.nI[c], nB = Lv.nB[c], w = Lv.band_w[c];
+  const int32_t* gI = Lv.gids + Lv.gid_off[c];
+  const int* ci = Lv.cpl_i + Lv.b_off[c];
+  const T* ca = (const T*)Lv.cpl_a + Lv.b_off[c];
+  const int r0 = blockIdx.y * 32, R = min(32, nrhs - r0);
+  for (int r = 0; r < 32; ++r) {   // gather, one right-hand side at a time
+    const double* xr = x + (int64_t)(r0 + r) * ldx;
+    for (int i = lane; i < nI; i += 32) y[i * kMrLd + r] = r < R ? T(xr[gI[i]]) : T(0);
+  }
+  __syncwarp();
+  lane_band_fwd_inv(band, nI, w, y);
+  for (int i = 0; i < nI; ++i) z[i * kMrLd + lane] = y[i * kMrLd + lane];
+  __syncwarp();
+  for (int r = 0; r < R; ++r) {
+    double* xr = x + (int64_t)(r0 + r) * ldx;
+    for (int i = lane; i < nI; i += 32) xr[gI[i]] = double(y[i * kMrLd + r]);
+  }
+  lane_band_bwd_inv(band, nI, w, z);
+  __syncwarp();
+  for (int r = 0; r < R; ++r) {
+    double* u = ubuf + (int64_t)(r0 + r) * ldu + Lv.b_off[c];
+    for (int b = lane; b < nB; b += 32)
+      u[b] = ci[b] >= 0 ? double(ca[b] * z[ci[b] * kMrLd + r]) : 0.0;
+  }
+}
+
+// E_0 per leaf for right-hand sides 32 * blockIdx.y + lane: as k_apply_leaf_down.
+template <typename T>
+__global__ void __launch_bounds__(128)
+k_apply_leaf_down_mr(LevelDev Lv, double* x, int64_t ldx, int nrhs, int per_warp_bytes) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (c >= Lv.ncell) return;
+  unsigned char* base = smraw + (size_t)warp * per_warp_bytes;
+  const T* band = leaf_mr_stage<T>(Lv, c, base);
+  T* t = (T*)(base + round16((size_t)Lv.max_nI * (Lv.max_w + 1) * sizeof(T)));
+  T* v = t + (round16((size_t)Lv.max_nI * kMrLd * sizeof(T)) / sizeof(T));
+  T* xb = v + (round16((size_t)Lv.max_nI * kMrLd * sizeof(T)) / sizeof(T));
+  const int nI = Lv.nI[c], nB = Lv.nB[c], w = Lv.band_w[c];
+  const int32_t* gI = Lv.gids + Lv.gid_off[c];
+  const int32_t* gB = gI + nI;
+  const int* ci = Lv.cpl_i + Lv.b_off[c];
+  const T* ca = (const T*)Lv.cpl_a + Lv.b_off[c];
+  const int r0 = blockIdx.y * 32, R = min(32, nrhs - r0);
+  for (int r = 0; r < 32; ++r) {   // gather x_I and the coupled x_B, one right-hand side at a time
+    const double* xr = x + (int64_t)(r0 + r) * ldx;
+    for (int i = lane; i < nI; i += 32) t[i * kMrLd + r] = r < R ? T(xr[gI[i]]) : T(0);
+    for (int b = lane; b < nB; b += 32)
+      xb[b * kMrLd + r] = (r < R && ci[b] >= 0) ? ca[b] * T(xr[gB[b]]) : T(0);
+  }
+  for (int i = 0; i < nI; ++i) v[i * kMrLd + lane] = T(0);
+  __syncwarp();
+  for (int b = 0; b < nB; ++b)   // A_BI^T x_B in boundary order, as the one-vector kernel
+    if (ci[b] >= 0) v[ci[b] * kMrLd + lane] += xb[b * kMrLd + lane];
+  lane_band_fwd_inv(band, nI, w, v);
+  for (int i = 0; i < nI; ++i) t[i * kMrLd + lane] -= v[i * kMrLd + lane];
+  lane_band_bwd_inv(band, nI, w, t);
+  __syncwarp();
+  for (int r = 0; r < R; ++r) {
+    double* xr = x + (int64_t)(r0 + r) * ldx;
+    for (int i = lane; i < nI; i += 32) xr[gI[i]] = double(t[i * kMrLd + r]);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // dense fronts (levels >= 1 and the root)
 // ---------------------------------------------------------------------------
 
@@ -909,6 +1093,15 @@ k_apply_group_down_warp(LevelDev Lv, PhaseDev Ph, double* x, int64_t ldx, int nr
   }
 }
 
+// Lane-per-right-hand-side leaf kernels: from 8 right-hand sides, for leaf
+// levels whose bands all hold inverted diagonal blocks (w <= 15: 2D) and fit
+// the shared-memory budget.
+template <typename T>
+static bool leaf_lanes_per_rhs(const LevelDev& Lv, int nrhs) {
+  return nrhs >= 8 && Lv.max_w >= 1 && Lv.max_w <= kBandRegW &&
+         leaf_mr_bytes<T>(Lv.max_nI, Lv.max_nB, Lv.max_w) <= kStageBudget;
+}
+
 // Right-hand sides over grid.y: the per-RHS work of the sweeps is
 // independent.  A launch gets as many CTAs per vector as keep it at about
 // 2432 CTAs (152 SMs x 16); the remaining right-hand sides loop inside each
@@ -926,6 +1119,13 @@ void launch_apply_cell_up(const LevelDev& Lv, double* x, int64_t ldx, int nrhs, 
                           int64_t ldu, cudaStream_t s) {
   if (!Lv.ncell) return;
   if (Lv.level == 0) {
+    if (leaf_lanes_per_rhs<T>(Lv, nrhs)) {   // many right-hand sides: lane = right-hand side
+      const size_t per = leaf_mr_bytes<T>(Lv.max_nI, Lv.max_nB, Lv.max_w);
+      const int wpc = (int)std::max<size_t>(1, std::min<size_t>(4, kStageBudget / per));
+      const dim3 grid((Lv.ncell + wpc - 1) / wpc, (nrhs + 31) / 32);
+      k_apply_leaf_up_mr<T><<<grid, 32 * wpc, wpc * per, s>>>(Lv, x, ldx, nrhs, ubuf, ldu, (int)per);
+      return;
+    }
     const bool multi = nrhs > (int)rhs_grid(nrhs, Lv.ncell / kLeafWarps + 1);
     const bool staged = leaf_staged<T>(Lv) || multi;
     const int wpc = leaf_warps_per_cta<T>(Lv, staged);
@@ -949,6 +1149,13 @@ template <typename T>
 void launch_apply_cell_down(const LevelDev& Lv, double* x, int64_t ldx, int nrhs, cudaStream_t s) {
   if (!Lv.ncell) return;
   if (Lv.level == 0) {
+    if (leaf_lanes_per_rhs<T>(Lv, nrhs)) {   // many right-hand sides: lane = right-hand side
+      const size_t per = leaf_mr_bytes<T>(Lv.max_nI, Lv.max_nB, Lv.max_w);
+      const int wpc = (int)std::max<size_t>(1, std::min<size_t>(4, kStageBudget / per));
+      const dim3 grid((Lv.ncell + wpc - 1) / wpc, (nrhs + 31) / 32);
+      k_apply_leaf_down_mr<T><<<grid, 32 * wpc, wpc * per, s>>>(Lv, x, ldx, nrhs, (int)per);
+      return;
+    }
     const bool multi = nrhs > (int)rhs_grid(nrhs, Lv.ncell / kLeafWarps + 1);
     const bool staged = leaf_staged<T>(Lv) || multi;
     const int wpc = leaf_warps_per_cta<T>(Lv, staged);
@@ -1051,6 +1258,8 @@ int configure_apply_kernels() {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_group_down<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_leaf_up<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_leaf_down<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_leaf_up_mr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_leaf_down_mr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_group_up_warp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_group_down_warp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_big_up1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);

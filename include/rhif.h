@@ -326,6 +326,8 @@ typedef struct {
   int units;              /* skeletonized units, all levels */
   double factor_ms;       /* device time of the last rhif_factor */
   int fp64_leaves;        /* leaves of an FP32 factor re-eliminated in FP64 (leaf_fp64) */
+  int64_t unit_dofs[16];  /* DOFs of the skeletonized units of level l (all phases) */
+  int64_t skeletons[16];  /* of them kept as skeletons (sum of the ID ranks), l < min(L,16) */
 } rhif_stats_t;
 
 /* Copy statistics of a factor to host memory. */

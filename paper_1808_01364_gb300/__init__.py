@@ -57,7 +57,8 @@ class Stats(ctypes.Structure):
                 ("active", ctypes.c_int64 * 16), ("factor_bytes", ctypes.c_int64),
                 ("flops", ctypes.c_double), ("apply_bytes", ctypes.c_double),
                 ("precision", ctypes.c_int), ("units", ctypes.c_int),
-                ("factor_ms", ctypes.c_double), ("fp64_leaves", ctypes.c_int)]
+                ("factor_ms", ctypes.c_double), ("fp64_leaves", ctypes.c_int),
+                ("unit_dofs", ctypes.c_int64 * 16), ("skeletons", ctypes.c_int64 * 16)]
 
 
 class KernelStat(ctypes.Structure):
@@ -375,7 +376,9 @@ class Factor:
         return {"levels": st.levels, "n": st.n, "root_size": st.root_size,
                 "active": list(st.active)[:st.levels], "factor_bytes": st.factor_bytes,
                 "flops": st.flops, "apply_bytes": st.apply_bytes, "precision": st.precision,
-                "units": st.units, "factor_ms": st.factor_ms, "fp64_leaves": st.fp64_leaves}
+                "units": st.units, "factor_ms": st.factor_ms, "fp64_leaves": st.fp64_leaves,
+                "unit_dofs": list(st.unit_dofs)[:st.levels],
+                "skeletons": list(st.skeletons)[:st.levels]}
 
     def skeletons(self, level: int, phase: int = 0):
         """[(dofs in pivot order, rank)] for every unit of a level/phase."""

@@ -2069,6 +2069,16 @@ int rhif_stats(const rhif_handle* F, rhif_stats_t* st) {
   st->precision = F->precision;
   st->units = F->units;
   st->factor_ms = F->factor_ms;
+  for (int l = 0; l < F->G.L && l < 16; ++l) {
+    const LevelStore& S = F->levels[l];
+    for (size_t p = 0; p < S.phases.size(); ++p) {
+      const PhasePlan& ph = S.plan.phases[p];
+      for (size_t u = 0; u < S.phases[p].h_rank.size(); ++u) {
+        st->unit_dofs[l] += S.plan.group_size[ph.units.group[u]];
+        st->skeletons[l] += S.phases[p].h_rank[u];
+      }
+    }
+  }
   st->fp64_leaves = 0;
   if (F->precision != RHIF_FP64 && F->leaf_fp64 > 0.0 && F->status) {
     rhif_handle* H = const_cast<rhif_handle*>(F);

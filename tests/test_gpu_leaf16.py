@@ -121,6 +121,12 @@ def test_leaf16_fp64_matches_oracle(gpu_lib, ns, tol):
     assert leaf_launches >= 1 and leaf_apply >= 2
     if not diverged:
         assert diff <= FP64_APPLY_DIFF
+        # per-level statistics of the IDs: unit DOFs and kept skeletons
+        st = Fg.stats()
+        for lvl, lv in enumerate(Fo.levels):
+            units = [u for ph in lv.phases for u in ph.units]
+            assert st["unit_dofs"][lvl] == sum(u.e.size for u in units)
+            assert st["skeletons"][lvl] == sum(u.sk.size for u in units)
     assert eg <= 2 * eo + 1e-12
     Fg.free()
 

@@ -295,77 +295,114 @@ k_apply_leaf_down(LevelDev Lv, double* x, int64_t ldx, int nrhs, int per_warp_by
 
 constexpr int kMrLd = 33;
 
-template <typename T>
-__device__ inline void lane_band_fwd_inv(const T* band, int n, int w, T* v) {
+// Solves with the half bandwidth W a compile-time constant: the rows of the
+// previous (next) block that couple into the current one stay in registers,
+// so a block reads only its band entries (broadcasts) from shared memory.
+template <typename T, int W>
+__device__ inline void lane_band_fwd_w(const T* band, int n, T* v) {
   const int lane = threadIdx.x & 31;
-  const int w1 = w + 1;
-  for (int s0 = 0; s0 < n; s0 += w) {
-    const int B = min(w, n - s0);
-    T acc[kBandRegW];
+  constexpr int w1 = W + 1;
+  T prev[W];   // outputs of the previous block, row s0 - W + q in prev[q]
 #pragma unroll
-    for (int r = 0; r < kBandRegW; ++r) {
-      if (r >= B) break;
+  for (int q = 0; q < W; ++q) prev[q] = T(0);
+  for (int s0 = 0; s0 < n; s0 += W) {
+    const int B = min(W, n - s0);
+    T acc[W];
+#pragma unroll
+    for (int r = 0; r < W; ++r) {
       const int i = s0 + r;
-      T a = v[i * kMrLd + lane];
+      T a = r < B ? v[i * kMrLd + lane] : T(0);
 #pragma unroll
-      for (int d = 1; d <= kBandRegW; ++d) {
+      for (int d = 1; d <= kBandRegW; ++d) {   // the one-vector kernel's order: d ascending
+        if (d > W || d <= r) continue;
         const int j = i - d;
-        const bool ok = d <= w && d > r && j >= 0;
+        const bool ok = j >= 0 && r < B;
         const T cp = ok ? band[j * w1 + d] : T(0);
-        const T yp = ok ? v[j * kMrLd + lane] : T(0);
-        a -= cp * yp;
+        a -= cp * (ok ? prev[W + r - d] : T(0));
       }
       acc[r] = a;
     }
 #pragma unroll
-    for (int r = 0; r < kBandRegW; ++r) {
-      if (r >= B) break;
+    for (int r = 0; r < W; ++r) {
       T out = T(0);
 #pragma unroll
       for (int c = 0; c < kBandRegW; ++c) {
-        const T xr = (c <= r && c < B) ? band[(s0 + c) * w1 + (r - c)] : T(0);
+        if (c >= W) continue;
+        const T xr = (c <= r && r < B && c < B) ? band[(s0 + c) * w1 + (r - c)] : T(0);
         out += xr * (c < B ? acc[c] : T(0));
       }
-      v[(s0 + r) * kMrLd + lane] = out;
+      if (r < B) v[(s0 + r) * kMrLd + lane] = out;
+      prev[r] = out;
     }
+  }
+}
+
+template <typename T, int W>
+__device__ inline void lane_band_bwd_w(const T* band, int n, T* v) {
+  const int lane = threadIdx.x & 31;
+  constexpr int w1 = W + 1;
+  const int nblk = (n + W - 1) / W;
+  T next[W];   // outputs of the next block, row s0 + B + q in next[q]
+#pragma unroll
+  for (int q = 0; q < W; ++q) next[q] = T(0);
+  for (int bi = nblk - 1; bi >= 0; --bi) {
+    const int s0 = bi * W;
+    const int B = min(W, n - s0);
+    T acc[W];
+#pragma unroll
+    for (int r = 0; r < W; ++r) {
+      const int i = s0 + r;
+      T a = r < B ? v[i * kMrLd + lane] : T(0);
+      // couplings to the next block (only a full block has one: the last
+      // block is the only partial one)
+      if (B == W) {
+#pragma unroll
+        for (int d = 1; d <= kBandRegW; ++d) {
+          if (d > W || r + d - W < 0) continue;
+          const int j = i + d;
+          const bool ok = j < n;
+          const T cp = ok ? band[i * w1 + d] : T(0);
+          a -= cp * (ok ? next[r + d - W] : T(0));
+        }
+      }
+      acc[r] = a;
+    }
+#pragma unroll
+    for (int r = 0; r < W; ++r) {
+      T out = T(0);
+#pragma unroll
+      for (int c = 0; c < kBandRegW; ++c) {
+        if (c >= W) continue;
+        const T xc = (c >= r && c < B && r < B) ? band[(s0 + r) * w1 + (c - r)] : T(0);
+        out += xc * (c < B ? acc[c] : T(0));
+      }
+      if (r < B) v[(s0 + r) * kMrLd + lane] = out;
+      acc[r] = out;
+    }
+#pragma unroll
+    for (int r = 0; r < W; ++r) next[r] = acc[r];
+  }
+}
+
+template <typename T>
+__device__ inline void lane_band_fwd_inv(const T* band, int n, int w, T* v) {
+  switch (w) {
+#define RHIF_W(k) case k: lane_band_fwd_w<T, k>(band, n, v); break;
+    RHIF_W(1) RHIF_W(2) RHIF_W(3) RHIF_W(4) RHIF_W(5) RHIF_W(6) RHIF_W(7) RHIF_W(8)
+    RHIF_W(9) RHIF_W(10) RHIF_W(11) RHIF_W(12) RHIF_W(13) RHIF_W(14) RHIF_W(15)
+#undef RHIF_W
+    default: break;
   }
 }
 
 template <typename T>
 __device__ inline void lane_band_bwd_inv(const T* band, int n, int w, T* v) {
-  const int lane = threadIdx.x & 31;
-  const int w1 = w + 1;
-  const int nblk = (n + w - 1) / w;
-  for (int bi = nblk - 1; bi >= 0; --bi) {
-    const int s0 = bi * w;
-    const int B = min(w, n - s0);
-    T acc[kBandRegW];
-#pragma unroll
-    for (int r = 0; r < kBandRegW; ++r) {
-      if (r >= B) break;
-      const int i = s0 + r;
-      T a = v[i * kMrLd + lane];
-#pragma unroll
-      for (int d = 1; d <= kBandRegW; ++d) {
-        const int j = i + d;
-        const bool ok = d <= w && d >= B - r && j < n;
-        const T cp = ok ? band[i * w1 + d] : T(0);
-        const T yn = ok ? v[j * kMrLd + lane] : T(0);
-        a -= cp * yn;
-      }
-      acc[r] = a;
-    }
-#pragma unroll
-    for (int r = 0; r < kBandRegW; ++r) {
-      if (r >= B) break;
-      T out = T(0);
-#pragma unroll
-      for (int c = 0; c < kBandRegW; ++c) {
-        const T xc = (c >= r && c < B) ? band[(s0 + r) * w1 + (c - r)] : T(0);
-        out += xc * (c < B ? acc[c] : T(0));
-      }
-      v[(s0 + r) * kMrLd + lane] = out;
-    }
+  switch (w) {
+#define RHIF_W(k) case k: lane_band_bwd_w<T, k>(band, n, v); break;
+    RHIF_W(1) RHIF_W(2) RHIF_W(3) RHIF_W(4) RHIF_W(5) RHIF_W(6) RHIF_W(7) RHIF_W(8)
+    RHIF_W(9) RHIF_W(10) RHIF_W(11) RHIF_W(12) RHIF_W(13) RHIF_W(14) RHIF_W(15)
+#undef RHIF_W
+    default: break;
   }
 }
 
@@ -375,6 +412,40 @@ template <typename T>
 __host__ __device__ inline size_t leaf_mr_bytes(int max_nI, int max_nB, int max_w) {
   return round16((size_t)max_nI * (max_w + 1) * sizeof(T)) +
          2 * round16((size_t)max_nI * kMrLd * sizeof(T)) + round16((size_t)max_nB * kMrLd * sizeof(T));
+}
+
+// v[i * kMrLd + r] = T(x[g[i] + (r0 + r) ldx]) for i < n, r < 32 (0 for r >= R,
+// or where ci[i] < 0 when ci is given): lanes along i, eight right-hand sides'
+// loads in flight before their stores.
+template <typename T>
+__device__ inline void mr_gather(const double* x, int64_t ldx, int r0, int R, const int32_t* g,
+                                 int n, T* v, const int* ci = nullptr) {
+  const int lane = threadIdx.x & 31;
+  for (int i = lane; i < n; i += 32) {
+    const bool use = !ci || ci[i] >= 0;
+    const int64_t gi = g[i];
+    for (int rb = 0; rb < 32; rb += 8) {
+      double t[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        t[q] = (use && rb + q < R) ? x[gi + (int64_t)(r0 + rb + q) * ldx] : 0.0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v[i * kMrLd + rb + q] = T(t[q]);
+    }
+  }
+  __syncwarp();
+}
+
+// x[g[i] + (r0 + r) ldx] = double(v[i * kMrLd + r]) for i < n, r < R.
+template <typename T>
+__device__ inline void mr_scatter(double* x, int64_t ldx, int r0, int R, const int32_t* g, int n,
+                                  const T* v) {
+  const int lane = threadIdx.x & 31;
+  __syncwarp();
+  for (int i = lane; i < n; i += 32) {
+    const int64_t gi = g[i];
+    for (int r = 0; r < R; ++r) x[gi + (int64_t)(r0 + r) * ldx] = double(v[i * kMrLd + r]);
+  }
 }
 
 template <typename T>
@@ -406,18 +477,11 @@ k_apply_leaf_up_mr(LevelDev Lv, double* x, int64_t ldx, int nrhs, double* ubuf, 
   const int* ci = Lv.cpl_i + Lv.b_off[c];
   const T* ca = (const T*)Lv.cpl_a + Lv.b_off[c];
   const int r0 = blockIdx.y * 32, R = min(32, nrhs - r0);
-  for (int r = 0; r < 32; ++r) {   // gather, one right-hand side at a time
-    const double* xr = x + (int64_t)(r0 + r) * ldx;
-    for (int i = lane; i < nI; i += 32) y[i * kMrLd + r] = r < R ? T(xr[gI[i]]) : T(0);
-  }
-  __syncwarp();
+  mr_gather<T>(x, ldx, r0, R, gI, nI, y);
   lane_band_fwd_inv(band, nI, w, y);
   for (int i = 0; i < nI; ++i) z[i * kMrLd + lane] = y[i * kMrLd + lane];
   __syncwarp();
-  for (int r = 0; r < R; ++r) {
-    double* xr = x + (int64_t)(r0 + r) * ldx;
-    for (int i = lane; i < nI; i += 32) xr[gI[i]] = double(y[i * kMrLd + r]);
-  }
+  mr_scatter<T>(x, ldx, r0, R, gI, nI, y);
   lane_band_bwd_inv(band, nI, w, z);
   __syncwarp();
   for (int r = 0; r < R; ++r) {
@@ -446,12 +510,11 @@ k_apply_leaf_down_mr(LevelDev Lv, double* x, int64_t ldx, int nrhs, int per_warp
   const int* ci = Lv.cpl_i + Lv.b_off[c];
   const T* ca = (const T*)Lv.cpl_a + Lv.b_off[c];
   const int r0 = blockIdx.y * 32, R = min(32, nrhs - r0);
-  for (int r = 0; r < 32; ++r) {   // gather x_I and the coupled x_B, one right-hand side at a time
-    const double* xr = x + (int64_t)(r0 + r) * ldx;
-    for (int i = lane; i < nI; i += 32) t[i * kMrLd + r] = r < R ? T(xr[gI[i]]) : T(0);
-    for (int b = lane; b < nB; b += 32)
-      xb[b * kMrLd + r] = (r < R && ci[b] >= 0) ? ca[b] * T(xr[gB[b]]) : T(0);
-  }
+  mr_gather<T>(x, ldx, r0, R, gI, nI, t);
+  mr_gather<T>(x, ldx, r0, R, gB, nB, xb, ci);   // coupled boundary values only
+  for (int b = lane; b < nB; b += 32)
+    if (ci[b] >= 0)
+      for (int r = 0; r < 32; ++r) xb[b * kMrLd + r] *= ca[b];
   for (int i = 0; i < nI; ++i) v[i * kMrLd + lane] = T(0);
   __syncwarp();
   for (int b = 0; b < nB; ++b)   // A_BI^T x_B in boundary order, as the one-vector kernel
@@ -460,10 +523,7 @@ k_apply_leaf_down_mr(LevelDev Lv, double* x, int64_t ldx, int nrhs, int per_warp
   for (int i = 0; i < nI; ++i) t[i * kMrLd + lane] -= v[i * kMrLd + lane];
   lane_band_bwd_inv(band, nI, w, t);
   __syncwarp();
-  for (int r = 0; r < R; ++r) {
-    double* xr = x + (int64_t)(r0 + r) * ldx;
-    for (int i = lane; i < nI; i += 32) xr[gI[i]] = double(t[i * kMrLd + r]);
-  }
+  mr_scatter<T>(x, ldx, r0, R, gI, nI, t);
 }
 
 // ---------------------------------------------------------------------------

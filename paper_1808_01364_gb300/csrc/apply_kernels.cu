@@ -542,82 +542,142 @@ __device__ inline const T* front_stage(const T* F, int n, int nI, T* dst, uint64
   return dst;
 }
 
-template <typename T>
+// RC right-hand sides per pass (1, or 8 when there are many): each element of
+// the front read from shared memory serves RC products; every right-hand side
+// keeps the summation order of the one-vector pass.
+template <typename T, int RC>
 __global__ void __launch_bounds__(kApplyThreads)
 k_apply_cell_up(LevelDev Lv, double* x, int64_t ldx, int nrhs, double* ubuf, int64_t ldu,
                 int stage) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ __align__(8) uint64_t bar;
+  const int ld = Lv.max_nI + 1;
   T* x_in = (T*)smraw;
-  T* y = x_in + Lv.max_nI + 1;
+  T* y = x_in + RC * ld;
   const int c = blockIdx.x;
   const int nI = Lv.nI[c], nB = Lv.nB[c], n = nI + nB;
   const T* F = (const T*)Lv.front + Lv.front_off[c];
-  if (stage) F = front_stage(F, n, nI, (T*)(smraw + round16(2 * (Lv.max_nI + 1) * sizeof(T))), &bar);
+  if (stage) F = front_stage(F, n, nI, (T*)(smraw + round16(2 * RC * ld * sizeof(T))), &bar);
   const int32_t* gI = Lv.gids + Lv.gid_off[c];
   __syncthreads();
-  for (int r = blockIdx.y; r < nrhs; r += gridDim.y) {   // right-hand sides over grid.y
-    double* xr = x + r * ldx;
-    for (int i = threadIdx.x; i < nI; i += blockDim.x) x_in[i] = T(xr[gI[i]]);
-    if (stage && r == (int)blockIdx.y && !staged_ok(&bar, Lv.status, Lv.level, kKindCell, c)) return;
+  for (int r0 = blockIdx.y * RC; r0 < nrhs; r0 += gridDim.y * RC) {   // chunks over grid.y
+    const int rc = min(RC, nrhs - r0);
+    for (int idx = threadIdx.x; idx < rc * nI; idx += blockDim.x) {
+      const int q = idx / nI, i = idx % nI;
+      x_in[q * ld + i] = T(x[(int64_t)(r0 + q) * ldx + gI[i]]);
+    }
+    if (stage && r0 == (int)blockIdx.y * RC &&
+        !staged_ok(&bar, Lv.status, Lv.level, kKindCell, c))
+      return;
     __syncthreads();
     // y = L^{-1} x_I: the front's L block holds L^{-1} (one row per thread)
     for (int i = threadIdx.x; i < nI; i += blockDim.x) {
-      T s = T(0);
-      for (int k = 0; k <= i; ++k) s += F[i + (int64_t)k * n] * x_in[k];
-      y[i] = s;
+      T sq[RC];
+#pragma unroll
+      for (int q = 0; q < RC; ++q) sq[q] = T(0);
+      for (int k = 0; k <= i; ++k) {
+        const T f = F[i + (int64_t)k * n];
+#pragma unroll
+        for (int q = 0; q < RC; ++q)
+          if (q < rc) sq[q] += f * x_in[q * ld + k];
+      }
+#pragma unroll
+      for (int q = 0; q < RC; ++q)
+        if (q < rc) y[q * ld + i] = sq[q];
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < nI; i += blockDim.x) xr[gI[i]] = double(y[i]);
-    double* u = ubuf + r * ldu + Lv.b_off[c];
+    for (int idx = threadIdx.x; idx < rc * nI; idx += blockDim.x) {
+      const int q = idx / nI, i = idx % nI;
+      x[(int64_t)(r0 + q) * ldx + gI[i]] = double(y[q * ld + i]);
+    }
     for (int b = threadIdx.x; b < nB; b += blockDim.x) {
-      T s = T(0);
-      for (int k = 0; k < nI; ++k) s += F[(nI + b) + (int64_t)k * n] * y[k];
-      u[b] = double(s);
+      T sq[RC];
+#pragma unroll
+      for (int q = 0; q < RC; ++q) sq[q] = T(0);
+      for (int k = 0; k < nI; ++k) {
+        const T f = F[(nI + b) + (int64_t)k * n];
+#pragma unroll
+        for (int q = 0; q < RC; ++q)
+          if (q < rc) sq[q] += f * y[q * ld + k];
+      }
+#pragma unroll
+      for (int q = 0; q < RC; ++q)
+        if (q < rc) ubuf[(int64_t)(r0 + q) * ldu + Lv.b_off[c] + b] = double(sq[q]);
     }
     __syncthreads();
   }
 }
 
-template <typename T>
+template <typename T, int RC>
 __global__ void __launch_bounds__(kApplyThreads)
 k_apply_cell_down(LevelDev Lv, double* x, int64_t ldx, int nrhs, int stage) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ __align__(8) uint64_t bar;
+  const int ldi = Lv.max_nI, ldb = Lv.max_nB + 1;
   T* t = (T*)smraw;
-  T* xb = t + Lv.max_nI;
-  T* xo = xb + Lv.max_nB;
+  T* xb = t + RC * ldi;
+  T* xo = xb + RC * ldb;
   const int c = blockIdx.x;
   const int nI = Lv.nI[c], nB = Lv.nB[c], n = nI + nB;
   const T* F = (const T*)Lv.front + Lv.front_off[c];
   if (stage)
-    F = front_stage(F, n, nI, (T*)(smraw + round16((2 * Lv.max_nI + Lv.max_nB + 1) * sizeof(T))),
-                    &bar);
+    F = front_stage(F, n, nI,
+                    (T*)(smraw + round16(RC * (2 * Lv.max_nI + Lv.max_nB + 1) * sizeof(T))), &bar);
   const int32_t* gI = Lv.gids + Lv.gid_off[c];
   const int32_t* gB = gI + nI;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   __syncthreads();
-  for (int r = blockIdx.y; r < nrhs; r += gridDim.y) {   // right-hand sides over grid.y
-    double* xr = x + r * ldx;
-    for (int b = threadIdx.x; b < nB; b += blockDim.x) xb[b] = T(xr[gB[b]]);
-    if (stage && r == (int)blockIdx.y && !staged_ok(&bar, Lv.status, Lv.level, kKindCell, c)) return;
+  for (int r0 = blockIdx.y * RC; r0 < nrhs; r0 += gridDim.y * RC) {   // chunks over grid.y
+    const int rc = min(RC, nrhs - r0);
+    for (int idx = threadIdx.x; idx < rc * nB; idx += blockDim.x) {
+      const int q = idx / nB, b = idx % nB;
+      xb[q * ldb + b] = T(x[(int64_t)(r0 + q) * ldx + gB[b]]);
+    }
+    if (stage && r0 == (int)blockIdx.y * RC &&
+        !staged_ok(&bar, Lv.status, Lv.level, kKindCell, c))
+      return;
     __syncthreads();
     for (int k = warp; k < nI; k += nwarps) {
-      T s = T(0);
-      for (int b = lane; b < nB; b += 32) s += F[(nI + b) + (int64_t)k * n] * xb[b];
-      s = warp_sum(s);
-      if (lane == 0) t[k] = T(xr[gI[k]]) - s;
+      T sq[RC];
+#pragma unroll
+      for (int q = 0; q < RC; ++q) sq[q] = T(0);
+      for (int b = lane; b < nB; b += 32) {
+        const T f = F[(nI + b) + (int64_t)k * n];
+#pragma unroll
+        for (int q = 0; q < RC; ++q)
+          if (q < rc) sq[q] += f * xb[q * ldb + b];
+      }
+#pragma unroll
+      for (int q = 0; q < RC; ++q) {
+        if (q >= rc) break;
+        const T sr = warp_sum(sq[q]);
+        if (lane == 0) t[q * ldi + k] = T(x[(int64_t)(r0 + q) * ldx + gI[k]]) - sr;
+      }
     }
     __syncthreads();
     // x_I = L^{-T} t: the front's L block holds L^{-1}; one row per warp
     for (int i = warp; i < nI; i += nwarps) {
-      T s = T(0);
-      for (int k = i + lane; k < nI; k += 32) s += F[k + (int64_t)i * n] * t[k];
-      s = warp_sum(s);
-      if (lane == 0) xo[i] = s;
+      T sq[RC];
+#pragma unroll
+      for (int q = 0; q < RC; ++q) sq[q] = T(0);
+      for (int k = i + lane; k < nI; k += 32) {
+        const T f = F[k + (int64_t)i * n];
+#pragma unroll
+        for (int q = 0; q < RC; ++q)
+          if (q < rc) sq[q] += f * t[q * ldi + k];
+      }
+#pragma unroll
+      for (int q = 0; q < RC; ++q) {
+        if (q >= rc) break;
+        const T sr = warp_sum(sq[q]);
+        if (lane == 0) xo[q * ldi + i] = sr;
+      }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < nI; i += blockDim.x) xr[gI[i]] = double(xo[i]);
+    for (int idx = threadIdx.x; idx < rc * nI; idx += blockDim.x) {
+      const int q = idx / nI, i = idx % nI;
+      x[(int64_t)(r0 + q) * ldx + gI[i]] = double(xo[q * ldi + i]);
+    }
     __syncthreads();
   }
 }
@@ -1198,11 +1258,17 @@ void launch_apply_cell_up(const LevelDev& Lv, double* x, int64_t ldx, int nrhs, 
       k_apply_leaf_up<T, false><<<dim3(grid, gy), 32 * wpc, wpc * per, s>>>(Lv, x, ldx, nrhs, ubuf, ldu, (int)per);
     return;
   }
-  const size_t base = round16(2 * (Lv.max_nI + 1) * sizeof(T));
+  const int rcn = nrhs >= 8 ? 8 : 1;   // right-hand sides per pass
+  const size_t base = round16(2 * rcn * (Lv.max_nI + 1) * sizeof(T));
   const size_t blk = round16((size_t)Lv.max_n * Lv.max_nI * sizeof(T));
-  const int stage = blk <= kStageBudget;
-  k_apply_cell_up<T><<<dim3(Lv.ncell, rhs_grid(nrhs, Lv.ncell)), kApplyThreads, base + (stage ? blk : 0), s>>>(Lv, x, ldx, nrhs, ubuf,
-                                                                            ldu, stage);
+  const int stage = blk <= kStageBudget && base + blk <= 200 * 1024;
+  const dim3 grid(Lv.ncell, rhs_grid((nrhs + rcn - 1) / rcn, Lv.ncell));
+  if (rcn == 8)
+    k_apply_cell_up<T, 8><<<grid, kApplyThreads, base + (stage ? blk : 0), s>>>(Lv, x, ldx, nrhs,
+                                                                                ubuf, ldu, stage);
+  else
+    k_apply_cell_up<T, 1><<<grid, kApplyThreads, base + (stage ? blk : 0), s>>>(Lv, x, ldx, nrhs,
+                                                                                ubuf, ldu, stage);
 }
 
 template <typename T>
@@ -1228,11 +1294,17 @@ void launch_apply_cell_down(const LevelDev& Lv, double* x, int64_t ldx, int nrhs
       k_apply_leaf_down<T, false><<<dim3(grid, gy), 32 * wpc, wpc * per, s>>>(Lv, x, ldx, nrhs, (int)per);
     return;
   }
-  const size_t base = round16((2 * Lv.max_nI + Lv.max_nB + 1) * sizeof(T));
+  const int rcn = nrhs >= 8 ? 8 : 1;   // right-hand sides per pass
+  const size_t base = round16(rcn * (2 * Lv.max_nI + Lv.max_nB + 1) * sizeof(T));
   const size_t blk = round16((size_t)Lv.max_n * Lv.max_nI * sizeof(T));
-  const int stage = blk <= kStageBudget;
-  k_apply_cell_down<T><<<dim3(Lv.ncell, rhs_grid(nrhs, Lv.ncell)), kApplyThreads, base + (stage ? blk : 0), s>>>(Lv, x, ldx, nrhs,
-                                                                              stage);
+  const int stage = blk <= kStageBudget && base + blk <= 200 * 1024;
+  const dim3 grid(Lv.ncell, rhs_grid((nrhs + rcn - 1) / rcn, Lv.ncell));
+  if (rcn == 8)
+    k_apply_cell_down<T, 8><<<grid, kApplyThreads, base + (stage ? blk : 0), s>>>(Lv, x, ldx, nrhs,
+                                                                                  stage);
+  else
+    k_apply_cell_down<T, 1><<<grid, kApplyThreads, base + (stage ? blk : 0), s>>>(Lv, x, ldx, nrhs,
+                                                                                  stage);
 }
 
 // right-hand sides per chunk so that a chunk of an rows-long vector fits in
@@ -1312,8 +1384,10 @@ template <typename T>
 int configure_apply_kernels() {
   const int big = 200 * 1024;
   cudaError_t e = cudaSuccess;
-  e = cudaFuncSetAttribute(k_apply_cell_up<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_cell_down<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  e = cudaFuncSetAttribute(k_apply_cell_up<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_cell_up<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_cell_down<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_cell_down<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_group_up<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_group_down<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_leaf_up<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);

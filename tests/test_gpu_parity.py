@@ -243,12 +243,13 @@ def test_separator_breakdown_reported(gpu_lib, skel_cluster, precondition):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-@pytest.mark.parametrize("ns,leaf", [((63, 63), 8), ((127, 127), 16), ((20, 23), 4)])
+@pytest.mark.parametrize("ns,leaf", [((63, 63), 8), ((127, 127), 16), ((20, 23), 4), ((15, 15, 15), 4)])
 def test_many_rhs_apply_matches_one_rhs_apply(gpu_lib, precision, ns, leaf):
-    """From 8 right-hand sides the leaf sweeps run one lane per right-hand
-    side (the one-vector kernels' operations, compiled in another shape): 40
-    right-hand sides (a full and a partial chunk of 32) match the columns of
-    40 one-vector applications to rounding (FP64 1e-11, FP32 1e-5 relative)."""
+    """From 8 right-hand sides the 2D leaf sweeps run one lane per right-hand
+    side and the front sweeps eight right-hand sides per pass (the one-vector
+    kernels' operations, compiled in another shape): 40 right-hand sides (full
+    and partial chunks) match the columns of 40 one-vector applications to
+    rounding (FP64 1e-11, FP32 1e-5 relative)."""
     a = W.log_uniform_pixels(ns, 1e-3, 1e3, seed=sum(ns) + 2)
     Fg = gpu_lib.rhif_factor(_gpu_matrix(gpu_lib, ns, a, 0.0), ns, leaf, 1e-3, precision=precision)
     X = _dev(np.random.default_rng(14).standard_normal((40, Fg.N)))

@@ -459,7 +459,8 @@ __device__ inline const T* leaf_mr_stage(const LevelDev& Lv, int c, unsigned cha
   return sb;
 }
 
-// E_0^T per leaf for right-hand sides 32 * blockIdx.y + lane: as k_apply_leaf_up.
+// E_0^T per leaf for right-hand sides r0 + lane, r0 = 32 blockIdx.y, 32 (blockIdx.y +
+// gridDim.y), ...: as k_apply_leaf_up.
 template <typename T>
 __global__ void __launch_bounds__(128)
 k_apply_leaf_up_mr(LevelDev Lv, double* x, int64_t ldx, int nrhs, double* ubuf, int64_t ldu,
@@ -476,22 +477,25 @@ k_apply_leaf_up_mr(LevelDev Lv, double* x, int64_t ldx, int nrhs, double* ubuf, 
   const int32_t* gI = Lv.gids + Lv.gid_off[c];
   const int* ci = Lv.cpl_i + Lv.b_off[c];
   const T* ca = (const T*)Lv.cpl_a + Lv.b_off[c];
-  const int r0 = blockIdx.y * 32, R = min(32, nrhs - r0);
-  mr_gather<T>(x, ldx, r0, R, gI, nI, y);
-  lane_band_fwd_inv(band, nI, w, y);
-  for (int i = 0; i < nI; ++i) z[i * kMrLd + lane] = y[i * kMrLd + lane];
-  __syncwarp();
-  mr_scatter<T>(x, ldx, r0, R, gI, nI, y);
-  lane_band_bwd_inv(band, nI, w, z);
-  __syncwarp();
-  for (int r = 0; r < R; ++r) {
-    double* u = ubuf + (int64_t)(r0 + r) * ldu + Lv.b_off[c];
-    for (int b = lane; b < nB; b += 32)
-      u[b] = ci[b] >= 0 ? double(ca[b] * z[ci[b] * kMrLd + r]) : 0.0;
+  for (int r0 = blockIdx.y * 32; r0 < nrhs; r0 += gridDim.y * 32) {
+    const int R = min(32, nrhs - r0);
+    mr_gather<T>(x, ldx, r0, R, gI, nI, y);
+    lane_band_fwd_inv(band, nI, w, y);
+    for (int i = 0; i < nI; ++i) z[i * kMrLd + lane] = y[i * kMrLd + lane];
+    __syncwarp();
+    mr_scatter<T>(x, ldx, r0, R, gI, nI, y);
+    lane_band_bwd_inv(band, nI, w, z);
+    __syncwarp();
+    for (int r = 0; r < R; ++r) {
+      double* u = ubuf + (int64_t)(r0 + r) * ldu + Lv.b_off[c];
+      for (int b = lane; b < nB; b += 32)
+        u[b] = ci[b] >= 0 ? double(ca[b] * z[ci[b] * kMrLd + r]) : 0.0;
+    }
+    __syncwarp();
   }
 }
 
-// E_0 per leaf for right-hand sides 32 * blockIdx.y + lane: as k_apply_leaf_down.
+// E_0 per leaf for right-hand sides r0 + lane (as above): as k_apply_leaf_down.
 template <typename T>
 __global__ void __launch_bounds__(128)
 k_apply_leaf_down_mr(LevelDev Lv, double* x, int64_t ldx, int nrhs, int per_warp_bytes) {
@@ -509,21 +513,24 @@ k_apply_leaf_down_mr(LevelDev Lv, double* x, int64_t ldx, int nrhs, int per_warp
   const int32_t* gB = gI + nI;
   const int* ci = Lv.cpl_i + Lv.b_off[c];
   const T* ca = (const T*)Lv.cpl_a + Lv.b_off[c];
-  const int r0 = blockIdx.y * 32, R = min(32, nrhs - r0);
-  mr_gather<T>(x, ldx, r0, R, gI, nI, t);
-  mr_gather<T>(x, ldx, r0, R, gB, nB, xb, ci);   // coupled boundary values only
-  for (int b = lane; b < nB; b += 32)
-    if (ci[b] >= 0)
-      for (int r = 0; r < 32; ++r) xb[b * kMrLd + r] *= ca[b];
-  for (int i = 0; i < nI; ++i) v[i * kMrLd + lane] = T(0);
-  __syncwarp();
-  for (int b = 0; b < nB; ++b)   // A_BI^T x_B in boundary order, as the one-vector kernel
-    if (ci[b] >= 0) v[ci[b] * kMrLd + lane] += xb[b * kMrLd + lane];
-  lane_band_fwd_inv(band, nI, w, v);
-  for (int i = 0; i < nI; ++i) t[i * kMrLd + lane] -= v[i * kMrLd + lane];
-  lane_band_bwd_inv(band, nI, w, t);
-  __syncwarp();
-  mr_scatter<T>(x, ldx, r0, R, gI, nI, t);
+  for (int r0 = blockIdx.y * 32; r0 < nrhs; r0 += gridDim.y * 32) {
+    const int R = min(32, nrhs - r0);
+    mr_gather<T>(x, ldx, r0, R, gI, nI, t);
+    mr_gather<T>(x, ldx, r0, R, gB, nB, xb, ci);   // coupled boundary values only
+    for (int b = lane; b < nB; b += 32)
+      if (ci[b] >= 0)
+        for (int r = 0; r < 32; ++r) xb[b * kMrLd + r] *= ca[b];
+    for (int i = 0; i < nI; ++i) v[i * kMrLd + lane] = T(0);
+    __syncwarp();
+    for (int b = 0; b < nB; ++b)   // A_BI^T x_B in boundary order, as the one-vector kernel
+      if (ci[b] >= 0) v[ci[b] * kMrLd + lane] += xb[b * kMrLd + lane];
+    lane_band_fwd_inv(band, nI, w, v);
+    for (int i = 0; i < nI; ++i) t[i * kMrLd + lane] -= v[i * kMrLd + lane];
+    lane_band_bwd_inv(band, nI, w, t);
+    __syncwarp();
+    mr_scatter<T>(x, ldx, r0, R, gI, nI, t);
+    __syncwarp();
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1213,6 +1220,197 @@ k_apply_group_down_warp(LevelDev Lv, PhaseDev Ph, double* x, int64_t ldx, int nr
   }
 }
 
+// ---------------------------------------------------------------------------
+// separator groups with many right-hand sides: one warp per group and one lane
+// per right-hand side (32 a pass); the group's values are lane-strided in
+// shared memory, the factor blocks staged beside them and read as broadcasts.
+// Every lane does the one-vector warp kernels' products in their order, as
+// scalar loops, in place (the unit steps need no second vector).
+// ---------------------------------------------------------------------------
+
+// Per-warp bytes: barrier, staged blocks, the unit's permutation, the values.
+template <typename T>
+__host__ __device__ inline size_t group_mr_bytes(int max_group) {
+  return 16 + group_block_bytes<T>(max_group) + round16(max_group * sizeof(int)) +
+         round16((size_t)max_group * kMrLd * sizeof(T));
+}
+
+// v[i kMrLd + lane] = T(x[gid[i] + (r0 + lane) ldx] - the cells' updates
+// ubuf[(r0 + lane) ldu + b_off[cell] + pos + i] in the group's cell order)
+// for lanes < R (0 above), eight entries' loads in flight.
+template <typename T>
+__device__ inline void group_mr_gather(const LevelDev& Lv, int g, int n, const int32_t* gid,
+                                       const double* x, int64_t ldx, const double* ubuf,
+                                       int64_t ldu, int r0, int R, T* v) {
+  const int lane = threadIdx.x & 31;
+  const bool on = lane < R;
+  const double* xr = x + (int64_t)(r0 + (on ? lane : 0)) * ldx;
+  const double* ur = ubuf ? ubuf + (int64_t)(r0 + (on ? lane : 0)) * ldu : nullptr;
+  const int k0 = Lv.group_cell_off[g], k1 = Lv.group_cell_off[g + 1];
+  for (int i0 = 0; i0 < n; i0 += 8) {
+    double t[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) t[q] = (on && i0 + q < n) ? xr[gid[i0 + q]] : 0.0;
+    if (ur)
+      for (int k = k0; k < k1; ++k) {
+        const double* u = ur + Lv.b_off[Lv.group_cell[k]] + Lv.group_pos[k] + i0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if (on && i0 + q < n) t[q] -= u[q];
+      }
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      if (i0 + q < n) v[(i0 + q) * kMrLd + lane] = T(t[q]);
+  }
+  __syncwarp();
+}
+
+template <typename T>
+__device__ inline void group_mr_scatter(double* x, int64_t ldx, const int32_t* gid, int n, int r0,
+                                        int R, const T* v) {
+  const int lane = threadIdx.x & 31;
+  __syncwarp();
+  if (lane >= R) return;
+  double* xr = x + (int64_t)(r0 + lane) * ldx;
+  for (int i = 0; i < n; ++i) xr[gid[i]] = double(v[i * kMrLd + lane]);
+}
+
+// Shared setup of the two sweeps: stage the group's blocks, copy the unit's
+// permutation, return the warp's value rows (nullptr: group not in this phase).
+template <typename T>
+__device__ inline T* group_mr_setup(const LevelDev& Lv, const PhaseDev& Ph, int g, int per_warp_bytes,
+                                    const T** Lg, const T** Fu, const T** Tm, int** perm,
+                                    uint64_t** bar) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n = Lv.group_size[g];
+  const int pi = Ph.group_pre[g], u = Ph.group_unit[g];
+  unsigned char* base = smraw + (size_t)warp * per_warp_bytes;
+  *bar = (uint64_t*)base;
+  *perm = (int*)(base + 16 + group_block_bytes<T>(Lv.max_group));
+  group_stage(Ph, pi, u, n, base + 16, *bar, lane == 0, Lg, Fu, Tm);
+  if (u >= 0)
+    for (int i = lane; i < n; i += 32) (*perm)[i] = Ph.perm[Ph.u_perm_off[u] + i];
+  return (T*)((unsigned char*)*perm + round16(Lv.max_group * sizeof(int)));
+}
+
+// C_l^T then K_l^T of group blockIdx.x * warps + warp for right-hand sides
+// r0 + lane, r0 = 32 blockIdx.y, 32 (blockIdx.y + gridDim.y), ...: as
+// k_apply_group_up_warp.
+template <typename T>
+__global__ void __launch_bounds__(32 * kGroupWarps)
+k_apply_group_up_mr(LevelDev Lv, PhaseDev Ph, int gather, double* x, int64_t ldx, int nrhs,
+                    const double* ubuf, int64_t ldu, int per_warp_bytes) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (g >= Lv.ngroup || Lv.group_t[g] < Ph.pre_min_type) return;
+  const int n = Lv.group_size[g];
+  const int32_t* gid = Lv.bucket + Lv.group_start[g];
+  const int pi = Ph.group_pre[g], u = Ph.group_unit[g];
+  const T *Lg, *Fu, *Tm;
+  int* perm;
+  uint64_t* bar;
+  T* v = group_mr_setup<T>(Lv, Ph, g, per_warp_bytes, &Lg, &Fu, &Tm, &perm, &bar);
+  T* xv = v + lane;   // xv[i * kMrLd]: entry i of this lane's right-hand side
+  for (int r0 = blockIdx.y * 32; r0 < nrhs; r0 += gridDim.y * 32) {
+    const int R = min(32, nrhs - r0);
+    group_mr_gather<T>(Lv, g, n, gid, x, ldx, gather ? ubuf : nullptr, ldu, r0, R, v);
+    if ((pi >= 0 || u >= 0) && r0 == (int)blockIdx.y * 32 &&
+        !staged_ok(bar, Lv.status, Lv.level, kKindGroup, g))
+      return;
+    if (Lg)             // C^T: x_g = L_g^{-1} x_g, rows from the last (in place)
+      for (int i = n - 1; i >= 0; --i) {
+        T s = T(0);
+        for (int c = 0; c <= i; ++c) s += Lg[i + c * n] * xv[c * kMrLd];
+        xv[i * kMrLd] = s;
+      }
+    if (u >= 0) {   // K^T: x_rd -= T^T x_sk ; x_rd = L_rr^{-1} x_rd ; x_sk -= W x_rd
+      const int k = Ph.rank[u], r = n - k;
+      for (int a = 0; a < r; ++a) {
+        T s = xv[perm[k + a] * kMrLd];
+        for (int q = 0; q < k; ++q) s -= Tm[q + a * k] * xv[perm[q] * kMrLd];
+        xv[perm[k + a] * kMrLd] = s;
+      }
+      for (int a = r - 1; a >= 0; --a) {
+        T s = T(0);
+        for (int c = 0; c <= a; ++c) s += Fu[a + c * n] * xv[perm[k + c] * kMrLd];
+        xv[perm[k + a] * kMrLd] = s;
+      }
+      for (int q = 0; q < k; ++q) {
+        T s = xv[perm[q] * kMrLd];
+        for (int a = 0; a < r; ++a) s -= Fu[(r + q) + a * n] * xv[perm[k + a] * kMrLd];
+        xv[perm[q] * kMrLd] = s;
+      }
+    }
+    group_mr_scatter<T>(x, ldx, gid, n, r0, R, v);
+  }
+}
+
+// K_l then C_l: as k_apply_group_down_warp.
+template <typename T>
+__global__ void __launch_bounds__(32 * kGroupWarps)
+k_apply_group_down_mr(LevelDev Lv, PhaseDev Ph, double* x, int64_t ldx, int nrhs, int per_warp_bytes) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (g >= Lv.ngroup || Lv.group_t[g] < Ph.pre_min_type) return;
+  const int n = Lv.group_size[g];
+  const int32_t* gid = Lv.bucket + Lv.group_start[g];
+  const int pi = Ph.group_pre[g], u = Ph.group_unit[g];
+  const T *Lg, *Fu, *Tm;
+  int* perm;
+  uint64_t* bar;
+  T* v = group_mr_setup<T>(Lv, Ph, g, per_warp_bytes, &Lg, &Fu, &Tm, &perm, &bar);
+  T* xv = v + lane;
+  for (int r0 = blockIdx.y * 32; r0 < nrhs; r0 += gridDim.y * 32) {
+    const int R = min(32, nrhs - r0);
+    group_mr_gather<T>(Lv, g, n, gid, x, ldx, nullptr, 0, r0, R, v);
+    if ((pi >= 0 || u >= 0) && r0 == (int)blockIdx.y * 32 &&
+        !staged_ok(bar, Lv.status, Lv.level, kKindGroup, g))
+      return;
+    if (u >= 0) {   // K: x_rd = L_rr^{-T}(x_rd - W^T x_sk) ; x_sk -= T x_rd
+      const int k = Ph.rank[u], r = n - k;
+      for (int a = 0; a < r; ++a) {
+        T s = xv[perm[k + a] * kMrLd];
+        for (int q = 0; q < k; ++q) s -= Fu[(r + q) + a * n] * xv[perm[q] * kMrLd];
+        xv[perm[k + a] * kMrLd] = s;
+      }
+      for (int a = 0; a < r; ++a) {   // rows from the first (in place)
+        T s = T(0);
+        for (int c = a; c < r; ++c) s += Fu[c + a * n] * xv[perm[k + c] * kMrLd];
+        xv[perm[k + a] * kMrLd] = s;
+      }
+      for (int q = 0; q < k; ++q) {
+        T s = xv[perm[q] * kMrLd];
+        for (int a = 0; a < r; ++a) s -= Tm[q + a * k] * xv[perm[k + a] * kMrLd];
+        xv[perm[q] * kMrLd] = s;
+      }
+    }
+    if (Lg)   // C: x_g = L_g^{-T} x_g
+      for (int i = 0; i < n; ++i) {
+        T s = T(0);
+        for (int c = i; c < n; ++c) s += Lg[c + i * n] * xv[c * kMrLd];
+        xv[i * kMrLd] = s;
+      }
+    group_mr_scatter<T>(x, ldx, gid, n, r0, R, v);
+  }
+}
+
+// Lane-per-right-hand-side group kernels: from 8 right-hand sides, where a
+// warp's blocks and values fit the shared-memory budget.
+template <typename T>
+static int group_mr_warps(const LevelDev& Lv, int nrhs) {
+  if (nrhs < 8) return 0;
+  const size_t per = group_mr_bytes<T>(Lv.max_group);
+  if (per > kStageBudget) return 0;
+  return (int)std::min<size_t>(kGroupWarps, (200 * 1024) / per);
+}
+
+// grid.y of the lane-per-right-hand-side kernels: one 32-wide chunk of
+// right-hand sides each, looping beyond 65535 chunks.
+static inline unsigned mr_chunks(int nrhs) {
+  return (unsigned)std::min(std::max((nrhs + 31) / 32, 1), 65535);
+}
+
 // Lane-per-right-hand-side leaf kernels: from 8 right-hand sides, for leaf
 // levels whose bands all hold inverted diagonal blocks (w <= 15: 2D) and fit
 // the shared-memory budget.
@@ -1242,7 +1440,7 @@ void launch_apply_cell_up(const LevelDev& Lv, double* x, int64_t ldx, int nrhs, 
     if (leaf_lanes_per_rhs<T>(Lv, nrhs)) {   // many right-hand sides: lane = right-hand side
       const size_t per = leaf_mr_bytes<T>(Lv.max_nI, Lv.max_nB, Lv.max_w);
       const int wpc = (int)std::max<size_t>(1, std::min<size_t>(4, kStageBudget / per));
-      const dim3 grid((Lv.ncell + wpc - 1) / wpc, (nrhs + 31) / 32);
+      const dim3 grid((Lv.ncell + wpc - 1) / wpc, mr_chunks(nrhs));
       k_apply_leaf_up_mr<T><<<grid, 32 * wpc, wpc * per, s>>>(Lv, x, ldx, nrhs, ubuf, ldu, (int)per);
       return;
     }
@@ -1278,7 +1476,7 @@ void launch_apply_cell_down(const LevelDev& Lv, double* x, int64_t ldx, int nrhs
     if (leaf_lanes_per_rhs<T>(Lv, nrhs)) {   // many right-hand sides: lane = right-hand side
       const size_t per = leaf_mr_bytes<T>(Lv.max_nI, Lv.max_nB, Lv.max_w);
       const int wpc = (int)std::max<size_t>(1, std::min<size_t>(4, kStageBudget / per));
-      const dim3 grid((Lv.ncell + wpc - 1) / wpc, (nrhs + 31) / 32);
+      const dim3 grid((Lv.ncell + wpc - 1) / wpc, mr_chunks(nrhs));
       k_apply_leaf_down_mr<T><<<grid, 32 * wpc, wpc * per, s>>>(Lv, x, ldx, nrhs, (int)per);
       return;
     }
@@ -1348,6 +1546,13 @@ template <typename T>
 void launch_apply_group_up(const LevelDev& Lv, const PhaseDev& Ph, int gather, double* x,
                            int64_t ldx, int nrhs, const double* ubuf, int64_t ldu, cudaStream_t s) {
   if (!Lv.ngroup) return;
+  if (const int wpc = group_mr_warps<T>(Lv, nrhs)) {
+    const size_t per = group_mr_bytes<T>(Lv.max_group);
+    const unsigned grid = (Lv.ngroup + wpc - 1) / wpc;
+    k_apply_group_up_mr<T><<<dim3(grid, mr_chunks(nrhs)), 32 * wpc, wpc * per, s>>>(
+        Lv, Ph, gather, x, ldx, nrhs, ubuf, ldu, (int)per);
+    return;
+  }
   if (Lv.max_group <= 32) {
     const size_t per = group_warp_smem<T>(Lv.max_group);
     const unsigned grid = (Lv.ngroup + kGroupWarps - 1) / kGroupWarps;
@@ -1366,6 +1571,13 @@ template <typename T>
 void launch_apply_group_down(const LevelDev& Lv, const PhaseDev& Ph, double* x, int64_t ldx,
                              int nrhs, cudaStream_t s) {
   if (!Lv.ngroup) return;
+  if (const int wpc = group_mr_warps<T>(Lv, nrhs)) {
+    const size_t per = group_mr_bytes<T>(Lv.max_group);
+    const unsigned grid = (Lv.ngroup + wpc - 1) / wpc;
+    k_apply_group_down_mr<T><<<dim3(grid, mr_chunks(nrhs)), 32 * wpc, wpc * per, s>>>(
+        Lv, Ph, x, ldx, nrhs, (int)per);
+    return;
+  }
   if (Lv.max_group <= 32) {
     const size_t per = group_warp_smem<T>(Lv.max_group);
     const unsigned grid = (Lv.ngroup + kGroupWarps - 1) / kGroupWarps;
@@ -1395,6 +1607,8 @@ int configure_apply_kernels() {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_leaf_up_mr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_leaf_down_mr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_group_up_warp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_group_up_mr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_group_down_mr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_group_down_warp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_big_up1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_big_up2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);

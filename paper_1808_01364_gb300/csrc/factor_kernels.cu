@@ -323,19 +323,13 @@ size_t leaf_stream_smem(int max_nI, int max_w, int leaf, int d) {
   return band + win + t + pairs + 64;
 }
 
-// T: arithmetic; S: storage of the band, the couplings and the frame (S = float
-// with T = double is the FP64 re-elimination of the FP32 factor's leaves whose
-// condition estimate is too large: computed in FP64, stored rounded to FP32).
-// only: when not null, the cells with only[c] == 0 return at once.
-template <typename T, typename S = T>
+template <typename T>
 __global__ void __launch_bounds__(kThreads)
-k_leaf_stream(GeoDev G, LevelDev Lv, const double* diag, const double* off, int* status,
-              const int* only = nullptr) {
+k_leaf_stream(GeoDev G, LevelDev Lv, const double* diag, const double* off, int* status) {
   extern __shared__ unsigned char smraw[];
   __shared__ int bad;
   __shared__ T s_piv;
   const int c = blockIdx.x;
-  if (only && !only[c]) return;
   const int nI = Lv.nI[c], nB = Lv.nB[c], n = nI + nB, w = Lv.band_w[c];
   const int w1 = w + 1;
   const int tid = threadIdx.x;
@@ -353,9 +347,9 @@ k_leaf_stream(GeoDev G, LevelDev Lv, const double* diag, const double* off, int*
   short* pairs = (short*)p;                              // (d1, d2) with 1 <= d2 <= d1 <= w
   const int npair = w * (w + 1) / 2;
   int ld;
-  S* Fr = frame_of<S>(Lv, c, &ld);
+  T* Fr = frame_of<T>(Lv, c, &ld);
   int* ci = Lv.cpl_i + Lv.b_off[c];
-  S* ca = (S*)Lv.cpl_a + Lv.b_off[c];
+  T* ca = (T*)Lv.cpl_a + Lv.b_off[c];
   const int m = G.leaf, m1 = m + 1;
   int origin[3] = {0, 0, 0};
   {
@@ -379,7 +373,7 @@ k_leaf_stream(GeoDev G, LevelDev Lv, const double* diag, const double* off, int*
   for (int i = tid; i < tab; i += blockDim.x) postab[i] = -1;
   for (int i = tid; i < nI * w1; i += blockDim.x) sband[i] = T(0);
   for (int i = tid; i < w1 * kStreamNB; i += blockDim.x) win[i] = T(0);
-  for (int64_t i = tid; i < (int64_t)nB * nB; i += blockDim.x) Fr[i] = S(0);
+  for (int64_t i = tid; i < (int64_t)nB * nB; i += blockDim.x) Fr[i] = T(0);
   __syncthreads();
   for (int q = tid; q < n; q += blockDim.x) {
     int x[3];
@@ -406,9 +400,9 @@ k_leaf_stream(GeoDev G, LevelDev Lv, const double* diag, const double* off, int*
     const int b = q - nI;
     if (q < nI) sband[q * w1] = T(diag[g]);
     else {
-      Fr[b + (int64_t)b * ld] = S(diag[g] / double(1 << onplane));
+      Fr[b + (int64_t)b * ld] = T(diag[g] / double(1 << onplane));
       ci[b] = -1;
-      ca[b] = S(0);
+      ca[b] = T(0);
     }
     for (int a = 0; a < G.d; ++a) {
       const double share = double(1 << (onplane - (x[a] % m == 0)));
@@ -423,9 +417,9 @@ k_leaf_stream(GeoDev G, LevelDev Lv, const double* diag, const double* off, int*
           if (r < nI && r > q) sband[q * w1 + (r - q)] = T(v);
         } else if (r < nI) {
           ci[b] = r;
-          ca[b] = S(v);
+          ca[b] = T(v);
         } else {
-          Fr[b + (int64_t)(r - nI) * ld] = S(v / share);
+          Fr[b + (int64_t)(r - nI) * ld] = T(v / share);
         }
       }
     }
@@ -516,12 +510,12 @@ k_leaf_stream(GeoDev G, LevelDev Lv, const double* diag, const double* off, int*
 #pragma unroll
     for (int bq = 0; bq < 4; ++bq) {
       const int i = ti + a, j = tj + bq;
-      if (i < nB && j < nB && i >= j) Fr[i + (int64_t)j * ld] = S(T(Fr[i + (int64_t)j * ld]) - acc[a][bq]);
+      if (i < nB && j < nB && i >= j) Fr[i + (int64_t)j * ld] -= acc[a][bq];
     }
   // band with reciprocal diagonal for the application
-  S* band = (S*)Lv.band + Lv.band_off[c];
+  T* band = (T*)Lv.band + Lv.band_off[c];
   for (int i = tid; i < nI * w1; i += blockDim.x)
-    band[i] = S((i % w1 == 0) ? T(1) / sband[i] : sband[i]);
+    band[i] = T((i % w1 == 0) ? T(1) / sband[i] : sband[i]);
   __syncthreads();
   if (tid == 0 && bad) report(status, RHIF_ERR_NOT_SPD, 0, kKindCell, c);
 }
@@ -1151,9 +1145,14 @@ k_precond_diag_warp(LevelDev Lv, PhaseDev Ph, int* status) {
   }
 }
 
-// frame <- D^{-1} frame D^{-T}, D = block diag of the L_g of the frame's groups
+// frame <- D^{-1} frame D^{-T}, D = block diag of the L_g of the frame's groups.
+// stage: work on a symmetric copy in shared memory with an odd leading
+// dimension (the row pass walks along rows of the copy, one column per
+// thread: an even one puts a warp's accesses in one bank).  xstage: the
+// L_g^{-1} of the cell's segments are copied beside it, max_group^2 apart.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_precond_scale(LevelDev Lv, PhaseDev Ph, int stage) {
+__global__ void __launch_bounds__(kThreads)
+k_precond_scale(LevelDev Lv, PhaseDev Ph, int stage, int xstage) {
   extern __shared__ unsigned char smraw[];
   const int c = blockIdx.x;
   int gld;
@@ -1161,12 +1160,27 @@ __global__ void __launch_bounds__(kThreads) k_precond_scale(LevelDev Lv, PhaseDe
   const int nb = Lv.nB[c];
   T* Fr = Fg;
   int ld = gld;
+  const int s0 = Lv.seg_off[c], s1 = Lv.seg_off[c + 1];
+  const int64_t mg2 = (int64_t)Lv.max_group * Lv.max_group;
+  T* Xs = nullptr;
   if (stage) {   // work on a full symmetric copy in shared memory
     Fr = (T*)smraw;
-    ld = nb;
+    ld = nb | 1;
     for (int64_t idx = threadIdx.x; idx < (int64_t)nb * nb; idx += blockDim.x) {
       const int i = (int)(idx % nb), j = (int)(idx / nb);
-      Fr[idx] = sym_at(Fg, gld, i, j);
+      Fr[i + (int64_t)j * ld] = sym_at(Fg, gld, i, j);
+    }
+    if (xstage && Ph.Linv && !Ph.diag_only) {
+      Xs = (T*)(smraw + round16((size_t)Lv.max_nB * (Lv.max_nB | 1) * sizeof(T)));
+      for (int q = s0; q < s1; ++q) {
+        const int g = Lv.seg_group[q];
+        const int pi = Ph.group_pre[g];
+        if (pi < 0) continue;
+        const int sz = Lv.group_size[g];
+        const T* src = (const T*)Ph.Linv + Ph.pre_off[pi];
+        T* dst = Xs + (q - s0) * mg2;
+        for (int i = threadIdx.x; i < sz * sz; i += blockDim.x) dst[i] = src[i];
+      }
     }
   } else {
     for (int64_t idx = threadIdx.x; idx < (int64_t)nb * nb; idx += blockDim.x) {
@@ -1175,7 +1189,6 @@ __global__ void __launch_bounds__(kThreads) k_precond_scale(LevelDev Lv, PhaseDe
     }
   }
   __syncthreads();
-  const int s0 = Lv.seg_off[c], s1 = Lv.seg_off[c + 1];
   const int64_t work = (int64_t)(s1 - s0) * nb;
   // rows: F[g, :] <- L_g^{-1} F[g, :]
   for (int64_t t = threadIdx.x; t < work; t += blockDim.x) {
@@ -1193,7 +1206,7 @@ __global__ void __launch_bounds__(kThreads) k_precond_scale(LevelDev Lv, PhaseDe
       continue;
     }
     if (Ph.Linv) {   // col <- L_g^{-1} col as a product, bottom up in place
-      const T* Xg = (const T*)Ph.Linv + Ph.pre_off[pi];
+      const T* Xg = Xs ? Xs + (s - s0) * mg2 : (const T*)Ph.Linv + Ph.pre_off[pi];
       for (int a = sz - 1; a >= 0; --a) {
         T v = T(0);
         for (int q = 0; q <= a; ++q) v += Xg[a + (int64_t)q * sz] * col[q];
@@ -1226,7 +1239,7 @@ __global__ void __launch_bounds__(kThreads) k_precond_scale(LevelDev Lv, PhaseDe
       continue;
     }
     if (Ph.Linv) {   // row <- row L_g^{-T} as a product, right to left in place
-      const T* Xg = (const T*)Ph.Linv + Ph.pre_off[pi];
+      const T* Xg = Xs ? Xs + (s - s0) * mg2 : (const T*)Ph.Linv + Ph.pre_off[pi];
       for (int a = sz - 1; a >= 0; --a) {
         T v = T(0);
         for (int q = 0; q <= a; ++q) v += Xg[a + (int64_t)q * sz] * row[(int64_t)q * ld];
@@ -1245,7 +1258,7 @@ __global__ void __launch_bounds__(kThreads) k_precond_scale(LevelDev Lv, PhaseDe
     __syncthreads();
     for (int64_t idx = threadIdx.x; idx < (int64_t)nb * nb; idx += blockDim.x) {
       const int i = (int)(idx % nb), j = (int)(idx / nb);
-      Fg[i + (int64_t)j * gld] = Fr[idx];
+      Fg[i + (int64_t)j * gld] = Fr[i + (int64_t)j * ld];
     }
   }
 }
@@ -2089,11 +2102,11 @@ __global__ void __launch_bounds__(kThreads) k_skel_cluster(LevelDev Lv, PhaseDev
 // row of w, y-neighbours at +-w), so D and ||B||_1 come from the stencil form
 // itself; ||B^{-1}||_1 comes from one application of
 // B^{-1} = S L^{-T} L^{-1} S (S = D^{-1}) to the vector of ones, exact for
-// these M-matrices (see below).  One warp per leaf; flag[c] = 1 when
-// the estimate exceeds `thresh` or is not finite, counted in *count.
+// these M-matrices (see below).  One warp per leaf; a leaf whose estimate
+// exceeds `thresh` or is not finite is appended to list (*count entries).
 template <typename T>
 __global__ void __launch_bounds__(128) k_leaf_cond(GeoDev G, LevelDev Lv, const double* diag,
-                                                   const double* off, double thresh, int* flag,
+                                                   const double* off, double thresh, int* list,
                                                    int* count, int per_warp) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -2155,28 +2168,244 @@ __global__ void __launch_bounds__(128) k_leaf_cond(GeoDev G, LevelDev Lv, const 
   for (int i = lane; i < n; i += 32) est = fmax(est, fabs(y[i]));
   for (int o = 16; o > 0; o >>= 1) est = fmax(est, __shfl_xor_sync(0xffffffffu, est, o));
   const double kappa = double(norm1) * double(est);
-  if (lane == 0) {
-    const int f = !(kappa <= thresh);   // above the threshold, or not finite
-    flag[c] = f;
-    if (f) atomicAdd(count, 1);
-  }
+  if (lane == 0 && !(kappa <= thresh))   // above the threshold, or not finite
+    list[atomicAdd(count, 1)] = c;          // compact list of the flagged leaves
 }
 
 void launch_leaf_cond(const GeoDev& G, const LevelDev& Lv, const double* diag, const double* off,
-                      double thresh, int* flag, int* count, cudaStream_t s) {
+                      double thresh, int* list, int* count, cudaStream_t s) {
   if (!Lv.ncell) return;
   const int per = (int)(((size_t)(Lv.max_w + 4) * Lv.max_nI * sizeof(float) + 15) & ~size_t(15));
-  k_leaf_cond<float><<<(Lv.ncell + 3) / 4, 128, 4 * per, s>>>(G, Lv, diag, off, thresh, flag,
+  k_leaf_cond<float><<<(Lv.ncell + 3) / 4, 128, 4 * per, s>>>(G, Lv, diag, off, thresh, list,
                                                              count, per);
 }
 
-// The flagged leaves of an FP32 factor eliminated again in FP64 (streaming
-// leaf kernel, FP64 arithmetic, results rounded to the FP32 storage).
+// FP64 re-elimination of the flagged leaves of an FP32 factor, spread over
+// CTAs.  GB300 runs FP64 at a small fraction of its FP32 rate, so one CTA per
+// leaf spends most of its time in the FP64 accumulation of S = Z^T Z
+// (Z = L^{-1} A_IB, nB x nB).  Here CTA (leaf, t) takes the lower tile
+// t = (I, J), I >= J, of the 64 x 64 boundary block in 16 x 16 tiles: every
+// CTA of a leaf assembles and factors the band in FP64 (the column-by-column
+// pass of k_leaf_stream, the same operations in the same order), carries the
+// rows of Z only for the tile's 16 or 32 columns, and accumulates only its
+// tile of S.  It writes its tile of the frame's lower triangle, the FP32
+// A_BB share minus S rounded to FP32 (as k_leaf_stream<double, float>); tile
+// 0 writes the band.  The couplings and the frame's upper triangle are the
+// FP32 leaf kernel's, from the same stencil values.  The flagged leaves come
+// as a list of count[0] cells; the grid's x loops over it.
+constexpr int kRedoTile = 16;
+constexpr int kRedoTiles = 10;   // lower tiles of the 64 x 64 block
+
+__global__ void __launch_bounds__(kThreads)
+k_leaf_redo64(GeoDev G, LevelDev Lv, const double* diag, const double* off, int* status,
+              const int* list, const int* count) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ int bad;
+  __shared__ double s_piv;
+  __shared__ int sci[kStreamNB];
+  __shared__ double sca[kStreamNB];
+  __shared__ float abb[kRedoTile][kRedoTile + 1];
+  const int tid = threadIdx.x;
+  const int t = blockIdx.y;
+  int I = 0;
+  while ((I + 1) * (I + 2) / 2 <= t) ++I;
+  const int J = t - I * (I + 1) / 2;
+  const int ncol = I == J ? kRedoTile : 2 * kRedoTile;
+  const int zc = tid & 31, zr0 = tid >> 5;                 // Z column, first row phase
+  const int zb = zc < kRedoTile ? J * kRedoTile + zc : I * kRedoTile + (zc - kRedoTile);
+  const int si = tid >> 4, sj = tid & 15;                  // this thread's entry of the S tile
+  const int zi = I == J ? si : kRedoTile + si;             // their Z columns
+  const int zj = sj;
+  const int m = G.leaf, m1 = m + 1;
+  int tab = 1;
+  for (int a = 0; a < G.d; ++a) tab *= m1;
+  const int nlist = *count;
+  for (int li = blockIdx.x; li < nlist; li += gridDim.x) {
+    const int c = list[li];
+    const int nI = Lv.nI[c], nB = Lv.nB[c], n = nI + nB, w = Lv.band_w[c];
+    const int w1 = w + 1;
+    const int32_t* gid = Lv.gids + Lv.gid_off[c];
+    const int64_t dbase = bind_cell_geo(Lv, c, G, diag, off);
+    unsigned char* p = smraw;
+    double* sband = (double*)p;
+    p += round16((size_t)Lv.max_nI * (Lv.max_w + 1) * sizeof(double));
+    double* win = (double*)p;                              // win[(k % w1) * 32 + zc]
+    p += round16((size_t)(Lv.max_w + 1) * 32 * sizeof(double));
+    int* postab = (int*)p;
+    p += round16((size_t)tab * sizeof(int));
+    short* pairs = (short*)p;                              // (d1, d2), 1 <= d2 <= d1 <= w
+    const int npair = w * (w + 1) / 2;
+    int origin[3] = {0, 0, 0};
+    {
+      int64_t code = Lv.cell_code[c];
+      for (int a = 0; a < G.d; ++a) {
+        const int v = (int)(code % Lv.code_base);
+        code /= Lv.code_base;
+        origin[a] = ((v - 1) / 2) * m;
+      }
+    }
+    if (tid == 0) {
+      bad = 0;
+      int q = 0;
+      for (int d1 = 1; d1 <= w; ++d1)
+        for (int d2 = 1; d2 <= d1; ++d2) {
+          pairs[2 * q] = (short)d1;
+          pairs[2 * q + 1] = (short)d2;
+          ++q;
+        }
+    }
+    for (int i = tid; i < tab; i += blockDim.x) postab[i] = -1;
+    for (int i = tid; i < nI * w1; i += blockDim.x) sband[i] = 0.0;
+    for (int i = tid; i < w1 * 32; i += blockDim.x) win[i] = 0.0;
+    for (int i = tid; i < kStreamNB; i += blockDim.x) {
+      sci[i] = -1;
+      sca[i] = 0.0;
+    }
+    abb[si][sj] = 0.0f;
+    __syncthreads();
+    for (int q = tid; q < n; q += blockDim.x) {
+      int x[3];
+      coords1(G, gid[q] - dbase, x);
+      int lin = 0, mul = 1;
+      for (int a = 0; a < G.d; ++a) {
+        lin += (x[a] - origin[a]) * mul;
+        mul *= m1;
+      }
+      postab[lin] = q;
+    }
+    __syncthreads();
+    // the stencil of every DOF: band rows (interior), couplings and the
+    // A_BB share of the tile (boundary)
+    for (int q = tid; q < n; q += blockDim.x) {
+      const int64_t g = gid[q] - dbase;
+      int x[3];
+      coords1(G, g, x);
+      int lin = 0, mul = 1, lstride[3] = {1, 1, 1}, onplane = 0;
+      for (int a = 0; a < G.d; ++a) {
+        lin += (x[a] - origin[a]) * mul;
+        lstride[a] = mul;
+        mul *= m1;
+        onplane += (x[a] % m == 0);
+      }
+      const int b = q - nI;
+      const bool rowin = b >= I * kRedoTile && b < (I + 1) * kRedoTile;
+      if (q < nI) sband[q * w1] = diag[g];
+      else if (rowin && b >= J * kRedoTile && b < (J + 1) * kRedoTile)
+        abb[b - I * kRedoTile][b - J * kRedoTile] = float(diag[g] / double(1 << onplane));
+      for (int a = 0; a < G.d; ++a) {
+        const double share = double(1 << (onplane - (x[a] % m == 0)));
+        const int lx = x[a] - origin[a];
+        for (int dir = -1; dir <= 1; dir += 2) {
+          if (dir > 0 && !(x[a] + 1 <= G.ns[a] && lx + 1 <= m)) continue;
+          if (dir < 0 && !(x[a] - 1 >= 1 && lx - 1 >= 0)) continue;
+          const int r = postab[lin + dir * lstride[a]];
+          if (r < 0) continue;
+          const double v = dir > 0 ? off[a * G.N + g] : off[a * G.N + g - G.stride[a]];
+          if (q < nI) {
+            if (r < nI && r > q) sband[q * w1 + (r - q)] = v;
+          } else if (r < nI) {
+            sci[b] = r;
+            sca[b] = double(float(v));   // the coupling as the FP32 factor stores it
+          } else if (rowin) {
+            const int j = r - nI;
+            if (j >= J * kRedoTile && j < (J + 1) * kRedoTile && j <= b)
+              abb[b - I * kRedoTile][j - J * kRedoTile] = float(v / share);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    const int my_ci = (zc < ncol && zb < nB) ? sci[zb] : -1;
+    const double my_ca = (zc < ncol && zb < nB) ? sca[zb] : 0.0;
+    // initial rows 0..w of the Z window: the single entry of column zb in row ci
+    if (zr0 == 0 && my_ci >= 0 && my_ci <= w) win[(my_ci % w1) * 32 + zc] = my_ca;
+    int pd1[2] = {0, 0}, pd2[2] = {0, 0};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int q = tid + h * kThreads;
+      if (q < npair) {
+        pd1[h] = pairs[2 * q];
+        pd2[h] = pairs[2 * q + 1];
+      }
+    }
+    double acc = 0.0;
+    int slot = 0;   // k % (w + 1)
+    __syncthreads();
+    for (int k = 0; k < nI; ++k) {
+      const int wk = min(w, nI - 1 - k);
+      double* zk = win + slot * 32;
+      double* colk = sband + k * w1;
+      if (tid == 0) {   // 1. pivot of column k
+        double dkk = colk[0];
+        if (!(dkk > 0.0)) {
+          bad = 1;
+          dkk = 1.0;
+        }
+        s_piv = my_sqrt(dkk);
+        colk[0] = s_piv;
+      }
+      __syncthreads();
+      const double rpiv = 1.0 / s_piv;
+      // 2. scale column k of L and row k of Z
+      if (tid >= 1 && tid <= wk) colk[tid] *= rpiv;
+      if (tid < ncol) zk[tid] *= rpiv;
+      __syncthreads();
+      // 3. trailing band update, Z rows k+1..k+wk, the S tile
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int d1 = pd1[h], d2 = pd2[h];
+        if (d1 && d1 <= wk) sband[(k + d2) * w1 + (d1 - d2)] -= colk[d1] * colk[d2];
+      }
+      if (zc < ncol) {
+        const double zv = zk[zc];
+        int sl = slot + 1 + zr0;
+        while (sl >= w1) sl -= w1;
+        for (int dd = 1 + zr0; dd <= wk; dd += 8) {
+          win[sl * 32 + zc] -= colk[dd] * zv;
+          sl += 8;
+          while (sl >= w1) sl -= w1;
+        }
+      }
+      acc += zk[zi] * zk[zj];
+      __syncthreads();
+      // 4. recycle row k's slot for row k + w + 1
+      const int nr = k + w1;
+      if (tid < ncol) zk[tid] = (nr < nI && my_ci == nr) ? my_ca : 0.0;
+      slot = (slot + 1 == w1) ? 0 : slot + 1;
+      __syncthreads();
+    }
+    int ld;
+    float* Fr = frame_of<float>(Lv, c, &ld);
+    const int i = I * kRedoTile + si, j = J * kRedoTile + sj;
+    if (i < nB && j < nB && i >= j) Fr[i + (int64_t)j * ld] = float(double(abb[si][sj]) - acc);
+    if (t == 0) {   // band with reciprocal diagonal for the application
+      float* band = (float*)Lv.band + Lv.band_off[c];
+      for (int e = tid; e < nI * w1; e += blockDim.x)
+        band[e] = float((e % w1 == 0) ? 1.0 / sband[e] : sband[e]);
+      if (tid == 0 && bad) report(status, RHIF_ERR_NOT_SPD, 0, kKindCell, c);
+    }
+    __syncthreads();
+  }
+}
+
+static size_t leaf_redo_smem(int max_nI, int max_w, int leaf, int d) {
+  int tab = 1;
+  for (int a = 0; a < d; ++a) tab *= leaf + 1;
+  return round16((size_t)max_nI * (max_w + 1) * sizeof(double)) +
+         round16((size_t)(max_w + 1) * 32 * sizeof(double)) + round16((size_t)tab * sizeof(int)) +
+         round16((size_t)(max_w * (max_w + 1) / 2) * 2 * sizeof(short));
+}
+
+// The flagged leaves (list[0 .. count[0]) of an FP32 factor eliminated again
+// in FP64, results rounded to the FP32 storage.  The grid covers up to 64
+// flagged leaves at once; more are taken in turns.
 void launch_leaf_fp64_redo(const GeoDev& G, const LevelDev& Lv, const double* diag,
-                           const double* off, int* status, const int* flag, cudaStream_t s) {
-  if (!Lv.ncell || Lv.max_nB > kStreamNB) return;
-  const size_t sm = leaf_stream_smem<double>(Lv.max_nI, Lv.max_w, G.leaf, G.d);
-  k_leaf_stream<double, float><<<Lv.ncell, kThreads, sm, s>>>(G, Lv, diag, off, status, flag);
+                           const double* off, int* status, const int* list, const int* count,
+                           cudaStream_t s) {
+  if (!Lv.ncell || Lv.max_nB > kStreamNB || Lv.max_w >= 32) return;
+  const size_t sm = leaf_redo_smem(Lv.max_nI, Lv.max_w, G.leaf, G.d);
+  const unsigned gx = (unsigned)std::min(Lv.ncell, 64);
+  k_leaf_redo64<<<dim3(gx, kRedoTiles), kThreads, sm, s>>>(G, Lv, diag, off, status, list, count);
 }
 
 // Redundant DOFs leave the active set only after every ID of the phase has
@@ -2338,13 +2567,16 @@ int launch_unit_invert(const LevelDev& Lv, const PhaseDev& Ph, T* X, cudaStream_
 }
 
 template <typename T>
-void launch_precond_scale(const LevelDev& Lv, const PhaseDev& Ph, cudaStream_t s) {
+void launch_precond_scale(const LevelDev& Lv, const PhaseDev& Ph, int max_seg, cudaStream_t s) {
   if (!(Ph.npre && Lv.ncell)) return;
-  const size_t blk = (size_t)Lv.max_nB * Lv.max_nB * sizeof(T);
-  if (blk <= 200 * 1024) {
-    k_precond_scale<T><<<Lv.ncell, kThreads, blk, s>>>(Lv, Ph, 1);
+  const size_t blk = round16((size_t)Lv.max_nB * (Lv.max_nB | 1) * sizeof(T));
+  const size_t xb = (size_t)max_seg * Lv.max_group * Lv.max_group * sizeof(T);
+  if (blk + xb <= 96 * 1024) {
+    k_precond_scale<T><<<Lv.ncell, kThreads, blk + xb, s>>>(Lv, Ph, 1, 1);
+  } else if (blk <= 200 * 1024) {
+    k_precond_scale<T><<<Lv.ncell, kThreads, blk, s>>>(Lv, Ph, 1, 0);
   } else {
-    k_precond_scale<T><<<Lv.ncell, kThreads, 0, s>>>(Lv, Ph, 0);
+    k_precond_scale<T><<<Lv.ncell, kThreads, 0, s>>>(Lv, Ph, 0, 0);
   }
 }
 
@@ -2457,8 +2689,7 @@ int configure_factor_kernels() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_leaf_stream<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_leaf_stream<double, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             big);
+    e = cudaFuncSetAttribute(k_leaf_redo64, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_leaf_cond<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   return e == cudaSuccess ? 0 : -1;
@@ -2477,7 +2708,7 @@ int configure_factor_kernels() {
   template void launch_front_trailing<T>(const LevelDev&, int, int64_t, cudaStream_t);            \
   template void launch_front_schur<T>(const LevelDev&, int64_t, cudaStream_t);                    \
   template int launch_precond_diag<T>(const LevelDev&, const PhaseDev&, int*, cudaStream_t);     \
-  template void launch_precond_scale<T>(const LevelDev&, const PhaseDev&, cudaStream_t);          \
+  template void launch_precond_scale<T>(const LevelDev&, const PhaseDev&, int, cudaStream_t);          \
   template void launch_precond_scale_big<T>(const LevelDev&, const PhaseDev&, int64_t,            \
                                             cudaStream_t);                                        \
   template void launch_skel<T>(const LevelDev&, const PhaseDev&, uint8_t*, double, int*, int64_t, \

@@ -55,7 +55,7 @@ int launch_unit_invert(const LevelDev& Lv, const PhaseDev& Ph, T* X, cudaStream_
 template <typename T>
 int launch_precond_diag(const LevelDev& Lv, const PhaseDev& Ph, int* status, cudaStream_t s);   // launches
 template <typename T>
-void launch_precond_scale(const LevelDev& Lv, const PhaseDev& Ph, cudaStream_t s);
+void launch_precond_scale(const LevelDev& Lv, const PhaseDev& Ph, int max_seg, cudaStream_t s);
 // Tile-product scaling of large frames; needs Ph.Linv (filled by
 // launch_precond_diag when non-null) and the scale_task tables; `tasks` is
 // the total number of 64-wide blocks.
@@ -157,9 +157,10 @@ void launch_bscatter(const VecSeg& S, const BatchGeo* bg, const double* x, int64
 
 // FP64 leaf fallback of FP32 factors (factor_kernels.cu)
 void launch_leaf_cond(const GeoDev& G, const LevelDev& Lv, const double* diag, const double* off,
-                      double thresh, int* flag, int* count, cudaStream_t s);
+                      double thresh, int* list, int* count, cudaStream_t s);
 void launch_leaf_fp64_redo(const GeoDev& G, const LevelDev& Lv, const double* diag,
-                           const double* off, int* status, const int* flag, cudaStream_t s);
+                           const double* off, int* status, const int* list, const int* count,
+                           cudaStream_t s);
 
 // tensor-core tile products (tc_kernels.cu)
 size_t tc_tile_smem_bytes();

@@ -746,17 +746,17 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
       // (their band, couplings and frame rounded to FP32) before any later
       // step reads them
       if (sizeof(T) == 4 && H->leaf_fp64 > 0.0 && P.max_nB <= 64) {
-        int* flag = nullptr;
-        if ((rc = H->mem.get((void**)&flag, P.ncell() * sizeof(int)))) return rc;
+        int* list = nullptr;   // the flagged leaves; their count is status word 4
+        if ((rc = H->mem.get((void**)&list, P.ncell() * sizeof(int)))) return rc;
         {
           Launch t(kCatLeafCond, s, 0.0, 0.0);
-          launch_leaf_cond(H->gd, S.dev, H->diag, H->off, H->leaf_fp64, flag, H->status + 4, s);
+          launch_leaf_cond(H->gd, S.dev, H->diag, H->off, H->leaf_fp64, list, H->status + 4, s);
         }
         {
           Launch t(kCatLeafFp64, s, 0.0, 0.0);
-          launch_leaf_fp64_redo(H->gd, S.dev, H->diag, H->off, H->status, flag, s);
+          launch_leaf_fp64_redo(H->gd, S.dev, H->diag, H->off, H->status, list, H->status + 4, s);
         }
-        H->mem.release(flag);
+        H->mem.release(list);
       }
     } else {
       for (int c = 0; c < P.ncell(); ++c) {
@@ -858,7 +858,9 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
         {
           Launch t(kCatPrecondScale, s, sflops, 0.0);
           if (!big) {
-            launch_precond_scale<T>(S.dev, D, s);
+            int max_seg = 0;
+            for (int c = 0; c < P.ncell(); ++c) max_seg = std::max(max_seg, P.seg_off[c + 1] - P.seg_off[c]);
+            launch_precond_scale<T>(S.dev, D, max_seg, s);
           } else {
             launch_precond_scale_big<T>(S.dev, D, blocks, s);
             add_launches(kCatPrecondScale, blocks > 0 ? 2 : 0);

@@ -328,7 +328,7 @@ __global__ void __launch_bounds__(kThreads)
 k_leaf_stream(GeoDev G, LevelDev Lv, const double* diag, const double* off, int* status) {
   extern __shared__ unsigned char smraw[];
   __shared__ int bad;
-  __shared__ T s_piv;
+  __shared__ T s_piv, s_rpiv;
   const int c = blockIdx.x;
   const int nI = Lv.nI[c], nB = Lv.nB[c], n = nI + nB, w = Lv.band_w[c];
   const int w1 = w + 1;
@@ -461,10 +461,11 @@ k_leaf_stream(GeoDev G, LevelDev Lv, const double* diag, const double* off, int*
         dkk = T(1);
       }
       s_piv = my_sqrt(dkk);
+      s_rpiv = T(1) / s_piv;   // once, not per thread (FP64 divides are slow here)
       colk[0] = s_piv;
     }
     __syncthreads();
-    const T rpiv = T(1) / s_piv;
+    const T rpiv = s_rpiv;
     // 2. scale column k of L and row k of Z
     if (tid >= 1 && tid <= wk) colk[tid] *= rpiv;
     if (tid < kStreamNB) zk[tid] *= rpiv;
@@ -768,6 +769,37 @@ __global__ void k_extend_add(LevelDev cur, LevelDev prev, int slot, int chunk) {
     if (pi < 0 || pj < 0) continue;
     const int r = max(pi, pj), q = min(pi, pj);
     F[r + (int64_t)q * n] += Fc[i + (int64_t)j * ldc];
+  }
+}
+
+// One CTA per parent cell, for fronts whose children's frames are small: the
+// front is zeroed, then the children's frames are added in slot order (the
+// order of the per-slot launches above), with a barrier between children
+// (two children can share entries of the front).  One launch replaces the
+// memset and the per-slot launches.
+constexpr int kEaCellThreads = 512;
+
+template <typename T>
+__global__ void __launch_bounds__(kEaCellThreads) k_extend_add_cell(LevelDev cur, LevelDev prev) {
+  const int c = blockIdx.x;
+  const int n = cur.nI[c] + cur.nB[c];
+  T* F = (T*)cur.front + cur.front_off[c];
+  for (int64_t idx = threadIdx.x; idx < (int64_t)n * n; idx += blockDim.x) F[idx] = T(0);
+  for (int k = cur.ea_off[c]; k < cur.ea_off[c + 1]; ++k) {
+    __syncthreads();
+    const int pc = cur.ea_child[k];
+    const int* map = cur.ea_map + cur.ea_map_off[k];
+    const int nbc = prev.nB[pc];
+    int ldc;
+    const T* Fc = frame_of<T>(prev, pc, &ldc);
+    for (int64_t idx = threadIdx.x; idx < (int64_t)nbc * nbc; idx += blockDim.x) {
+      const int i = (int)(idx % nbc), j = (int)(idx / nbc);
+      if (i < j) continue;
+      const int pi = map[i], pj = map[j];
+      if (pi < 0 || pj < 0) continue;
+      const int r = max(pi, pj), q = min(pi, pj);
+      F[r + (int64_t)q * n] += Fc[i + (int64_t)j * ldc];
+    }
   }
 }
 
@@ -2201,7 +2233,7 @@ k_leaf_redo64(GeoDev G, LevelDev Lv, const double* diag, const double* off, int*
               const int* list, const int* count) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ int bad;
-  __shared__ double s_piv;
+  __shared__ double s_piv, s_rpiv;
   __shared__ int sci[kStreamNB];
   __shared__ double sca[kStreamNB];
   __shared__ float abb[kRedoTile][kRedoTile + 1];
@@ -2342,10 +2374,11 @@ k_leaf_redo64(GeoDev G, LevelDev Lv, const double* diag, const double* off, int*
           dkk = 1.0;
         }
         s_piv = my_sqrt(dkk);
+        s_rpiv = 1.0 / s_piv;   // once, not per thread
         colk[0] = s_piv;
       }
       __syncthreads();
-      const double rpiv = 1.0 / s_piv;
+      const double rpiv = s_rpiv;
       // 2. scale column k of L and row k of Z
       if (tid >= 1 && tid <= wk) colk[tid] *= rpiv;
       if (tid < ncol) zk[tid] *= rpiv;
@@ -2482,9 +2515,13 @@ template <typename T>
 int launch_extend_add(const LevelDev& cur, const LevelDev& prev, int64_t front_total, int slots,
                       cudaStream_t s) {
   if (!cur.ncell) return 0;
+  const int64_t nb = prev.max_nB;
+  if (nb * nb * slots <= 128 * 1024) {   // small frames: one CTA per parent, one launch
+    k_extend_add_cell<T><<<cur.ncell, kEaCellThreads, 0, s>>>(cur, prev);
+    return 1;
+  }
   cudaMemsetAsync(cur.front, 0, (size_t)front_total * sizeof(T), s);
   const int chunk = 16 * kThreads;
-  const int64_t nb = prev.max_nB;
   const unsigned chunks = (unsigned)((nb * nb + chunk - 1) / chunk);
   if (!chunks) return 0;
   for (int slot = 0; slot < slots; ++slot)

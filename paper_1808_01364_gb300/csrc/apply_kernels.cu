@@ -1721,6 +1721,48 @@ __global__ void k_reduce(const double* partial, int nblk, double* sc, int mode, 
   }
 }
 
+// Device-side PCG loop (the iterations as a conditional WHILE node of a CUDA
+// graph).  kit[0]: iterations done; kit[1 + c]: first iteration at which
+// right-hand side c met the tolerance (maxit until then).  After each
+// iteration's residual reduction the check records newly converged
+// right-hand sides and sets the loop condition: go on while some right-hand
+// side has not converged and fewer than maxit iterations ran, so the loop
+// always ends.
+__global__ void k_pcg_kit_init(int* kit, int nrhs, int maxit) {
+  for (int c = threadIdx.x; c <= nrhs; c += blockDim.x) kit[c] = c == 0 ? 0 : maxit;
+}
+
+__global__ void k_pcg_check(const double* sc, int nrhs, int* kit, int maxit,
+                            cudaGraphConditionalHandle h) {
+  __shared__ int live;
+  if (threadIdx.x == 0) live = 0;
+  __syncthreads();
+  const int k = kit[0] + 1;
+  int mine = 0;
+  for (int c = threadIdx.x; c < nrhs; c += blockDim.x) {
+    if (sc[8 * c + kScDone] != 0.0) {
+      if (kit[1 + c] > k) kit[1 + c] = k;
+    } else {
+      mine = 1;
+    }
+  }
+  if (mine) atomicOr(&live, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    kit[0] = k;
+    cudaGraphSetConditional(h, (live && k < maxit) ? 1u : 0u);
+  }
+}
+
+void launch_pcg_kit_init(int* kit, int nrhs, int maxit, cudaStream_t s) {
+  k_pcg_kit_init<<<1, 256, 0, s>>>(kit, nrhs, maxit);
+}
+
+void launch_pcg_check(const double* sc, int nrhs, int* kit, int maxit,
+                      cudaGraphConditionalHandle h, cudaStream_t s) {
+  k_pcg_check<<<1, 256, 0, s>>>(sc, nrhs, kit, maxit, h);
+}
+
 // x += alpha p ; r -= alpha q ; partial r.r
 __global__ void k_update_xr(int64_t N, const double* sc, double* x, int64_t ldx, double* rv,
                             int64_t ldr, const double* p, int64_t ldp, const double* q,

@@ -124,6 +124,9 @@ void launch_update_p(int64_t N, int nrhs, const double* sc, const double* z, int
 void launch_sub(int64_t N, int nrhs, const double* a, int64_t lda, const double* b, int64_t ldb,
                 double* y, int64_t ldy, cudaStream_t s);
 void launch_scale(int64_t N, double* x, const double* alpha, cudaStream_t s);
+void launch_pcg_kit_init(int* kit, int nrhs, int maxit, cudaStream_t s);
+void launch_pcg_check(const double* sc, int nrhs, int* kit, int maxit,
+                      cudaGraphConditionalHandle h, cudaStream_t s);
 void launch_copy_cols(int64_t N, int nrhs, const double* a, int64_t lda, double* y, int64_t ldy,
                       cudaStream_t s);
 void launch_assemble_fd(const GeoDev& G, const double* a_pix, const double* b_node, double b_const,

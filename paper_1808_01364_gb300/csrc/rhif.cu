@@ -326,6 +326,18 @@ struct rhif_handle {
   int ag_nrhs = 0;
   int64_t ag_launches[rhif::kNumCat] = {};
   double ag_flops[rhif::kNumCat] = {}, ag_bytes[rhif::kNumCat] = {};
+  // The iterations of rhif_pcg as one CUDA graph (iteration 1, then a
+  // conditional WHILE node over the others), for one (solution, work
+  // buffers, scratch, nrhs, rtol, maxit); the launch counts of the part
+  // before the loop and of one loop body, credited per run.
+  cudaGraphExec_t pcg_graph = nullptr;
+  const void* pg_u = nullptr;
+  const void* pg_work = nullptr;
+  const void* pg_ubuf = nullptr;
+  int64_t pg_ldu = 0;
+  int pg_nrhs = 0, pg_maxit = 0;
+  double pg_rtol = 0.0;
+  rhif::KStat pg_pre[rhif::kNumCat] = {}, pg_body[rhif::kNumCat] = {};
 };
 
 namespace rhif {
@@ -1168,6 +1180,159 @@ static int ensure_work(rhif_handle* H, int64_t elems) {
   return RHIF_OK;
 }
 
+// Launch counts of a graph part, credited `times` over.
+static void credit_counts(const KStat* c, double times) {
+  if (times <= 0) return;
+  std::lock_guard<std::mutex> lk(g_kmu);
+  for (int k = 0; k < kNumCat; ++k) {
+    g_kstat[k].launches += (int64_t)(c[k].launches * times);
+    g_kstat[k].flops += c[k].flops * times;
+    g_kstat[k].bytes += c[k].bytes * times;
+  }
+}
+
+// Buffers of rhif_pcg inside the handle's work array.
+struct PcgBufs {
+  double *r, *z, *p, *q, *part, *sc, *sc2;
+  int* kit;
+};
+
+static PcgBufs pcg_bufs(double* work, int64_t N, int nrhs, int nblk) {
+  PcgBufs b;
+  b.r = work;
+  b.z = b.r + N * nrhs;
+  b.p = b.z + N * nrhs;
+  b.q = b.p + N * nrhs;
+  b.part = b.q + N * nrhs;
+  b.sc = b.part + (int64_t)nblk * nrhs;
+  b.sc2 = b.sc + 8 * nrhs;
+  b.kit = (int*)(b.sc2 + 8 * nrhs);
+  return b;
+}
+
+// SpMV q = A p, step alpha, x += alpha p, r -= alpha q, residual test: the
+// part of a PCG iteration (Sec. 4) up to the convergence test.
+static void pcg_step(rhif_handle* F, int nrhs, double* u, int64_t ldu, const PcgBufs& b,
+                     double rtol, cudaStream_t s) {
+  const int64_t N = F->G.N, ld = N;
+  const int nblk = vec_blocks(N);
+  const double spmv_flops = 2.0 * (2 * F->G.d + 1) * N, spmv_bytes = (8.0 * (1 + F->G.d) + 16.0) * N;
+  const double rb = 8.0 * nblk * nrhs, vb48 = 48.0 * double(N) * nrhs;
+  { Launch t_(kCatSpmv, s, spmv_flops * nrhs, spmv_bytes * nrhs); launch_spmv(F->gd, F->diag, F->off, b.p, ld, b.q, ld, nrhs, b.part, s); }
+  { Launch t_(kCatVector, s, 0.0, rb); launch_reduce(b.part, nblk, nrhs, b.sc, 2, rtol, s); }
+  { Launch t_(kCatVector, s, 0.0, vb48); launch_update_xr(N, nrhs, b.sc, u, ldu, b.r, ld, b.p, ld, b.q, ld, b.part, s); }
+  { Launch t_(kCatVector, s, 0.0, rb); launch_reduce(b.part, nblk, nrhs, b.sc, 3, rtol, s); }
+}
+
+// z = F^{-1} r, beta, p = z + beta p: the rest of a PCG iteration.
+static int pcg_direction(rhif_handle* F, int nrhs, const PcgBufs& b, double rtol, cudaStream_t s,
+                         bool replay) {
+  const int64_t N = F->G.N, ld = N;
+  const int nblk = vec_blocks(N);
+  const double rb = 8.0 * nblk * nrhs;
+  { Launch t_(kCatVector, s, 0.0, 16.0 * double(N) * nrhs); launch_copy_cols(N, nrhs, b.r, ld, b.z, ld, s); }
+  int rc = replay ? apply_dispatch(F, b.z, ld, nrhs, s, true) : apply_launch(F, b.z, ld, nrhs, s);
+  if (rc) return rc;
+  { Launch t_(kCatVector, s, 0.0, 16.0 * double(N) * nrhs); launch_dot_partial(N, b.r, ld, b.z, ld, nrhs, b.part, s); }
+  { Launch t_(kCatVector, s, 0.0, rb); launch_reduce(b.part, nblk, nrhs, b.sc, 4, rtol, s); }
+  { Launch t_(kCatVector, s, 0.0, 24.0 * double(N) * nrhs); launch_update_p(N, nrhs, b.sc, b.z, ld, b.p, ld, 0, s); }
+  return RHIF_OK;
+}
+
+// The iterations of rhif_pcg (Sec. 4) as one CUDA graph: iteration 1 up to
+// its convergence test, then a conditional WHILE node whose body is one more
+// iteration (preconditioner application, search direction, SpMV, step,
+// test).  The test kernel sets the loop condition on the device, so the host
+// waits once, after the loop, instead of once per iteration.  Captured on the
+// handle's private stream (nothing runs); false when the graph cannot be made
+// (the caller then iterates from the host).
+static bool capture_pcg(rhif_handle* H, int nrhs, double* u, int64_t ldu, double rtol, int maxit) {
+  if (H->pcg_graph) {
+    cudaGraphExecDestroy(H->pcg_graph);
+    H->pcg_graph = nullptr;
+  }
+  if (!H->capture_stream &&
+      cudaStreamCreateWithFlags(&H->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    H->capture_stream = nullptr;
+    return false;
+  }
+  cudaStream_t cs = H->capture_stream;
+  const PcgBufs b = pcg_bufs(H->work, H->G.N, nrhs, vec_blocks(H->G.N));
+  KStat pre[kNumCat] = {}, body[kNumCat] = {};
+  cudaGraph_t g = nullptr;
+  if (cudaGraphCreate(&g, 0) != cudaSuccess) return false;
+  cudaGraphConditionalHandle h{};
+  bool ok = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault) == cudaSuccess;
+  cudaGraphNodeParams np{};
+  if (ok && cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+                cudaSuccess) {
+    t_capture_stats = pre;
+    launch_pcg_kit_init(b.kit, nrhs, maxit, cs);
+    pcg_step(H, nrhs, u, ldu, b, rtol, cs);
+    launch_pcg_check(b.sc, nrhs, b.kit, maxit, h, cs);
+    t_capture_stats = nullptr;
+    cudaStreamCaptureStatus st{};
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    ok = cudaStreamGetCaptureInfo(cs, &st, nullptr, &cg, &deps, nullptr, &nd) == cudaSuccess &&
+         st == cudaStreamCaptureStatusActive && cg;
+    cudaGraphNode_t w = nullptr;
+    if (ok) {
+      np.type = cudaGraphNodeTypeConditional;
+      np.conditional.handle = h;
+      np.conditional.type = cudaGraphCondTypeWhile;
+      np.conditional.size = 1;
+      ok = cudaGraphAddNode(&w, cg, deps, nullptr, nd, &np) == cudaSuccess;
+    }
+    if (ok)
+      ok = cudaStreamUpdateCaptureDependencies(cs, &w, nullptr, 1, cudaStreamSetCaptureDependencies) ==
+           cudaSuccess;
+    cudaGraph_t out = nullptr;
+    const bool ended = cudaStreamEndCapture(cs, &out) == cudaSuccess;
+    ok = ok && ended && out == g;
+  } else {
+    ok = false;
+  }
+  if (ok) {
+    cudaGraph_t bg = np.conditional.phGraph_out[0];
+    ok = bg && cudaStreamBeginCaptureToGraph(cs, bg, nullptr, nullptr, 0,
+                                             cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      t_capture_stats = body;
+      const int rc = pcg_direction(H, nrhs, b, rtol, cs, false);
+      pcg_step(H, nrhs, u, ldu, b, rtol, cs);
+      launch_pcg_check(b.sc, nrhs, b.kit, maxit, h, cs);
+      t_capture_stats = nullptr;
+      cudaGraph_t out = nullptr;
+      const bool ended = cudaStreamEndCapture(cs, &out) == cudaSuccess;
+      ok = ended && out == bg && rc == RHIF_OK;
+    }
+  }
+  cudaGraphExec_t exec = nullptr;
+  if (ok) ok = cudaGraphInstantiate(&exec, g, 0) == cudaSuccess;
+  cudaGraphDestroy(g);
+  cudaGetLastError();   // a failed capture leaves no sticky error
+  if (!ok) {
+    if (exec) cudaGraphExecDestroy(exec);
+    return false;
+  }
+  H->pcg_graph = exec;
+  H->pg_u = u;
+  H->pg_work = H->work;
+  H->pg_ubuf = H->ubuf;
+  H->pg_ldu = ldu;
+  H->pg_nrhs = nrhs;
+  H->pg_rtol = rtol;
+  H->pg_maxit = maxit;
+  for (int c = 0; c < kNumCat; ++c) {
+    H->pg_pre[c] = pre[c];
+    H->pg_body[c] = body[c];
+  }
+  return true;
+}
+
+
 // Runs job(i, stream) for i = 0..count-1 with one host worker per stream.
 template <typename Job>
 static int run_batched(int count, void* const* streams, int nstreams, Job job,
@@ -1793,68 +1958,83 @@ int rhif_pcg(const rhif_handle* Fc, int nrhs, const double* f, int64_t ldf, doub
   const int nblk = vec_blocks(N);
   const int64_t ld = N;
   const double spmv_flops = 2.0 * (2 * F->G.d + 1) * N, spmv_bytes = (8.0 * (1 + F->G.d) + 16.0) * N;
-  // r, z, p, q (N x nrhs each), partials, two scalar blocks
-  const int64_t need = 4 * N * nrhs + (int64_t)nblk * nrhs + 16 * nrhs;
+  // r, z, p, q (N x nrhs each), partials, two scalar blocks, iteration counters
+  const int64_t need = 4 * N * nrhs + (int64_t)nblk * nrhs + 16 * nrhs + (nrhs + 2) / 2 + 1;
   int rc = ensure_work(F, need);
   if (rc) return rc;
-  double* r = F->work;
-  double* z = r + N * nrhs;
-  double* p = z + N * nrhs;
-  double* q = p + N * nrhs;
-  double* part = q + N * nrhs;
-  double* sc = part + (int64_t)nblk * nrhs;
-  double* sc2 = sc + 8 * nrhs;
+  const PcgBufs b = pcg_bufs(F->work, N, nrhs, nblk);
   // algorithmic bytes of the vector launches (FP64 vectors read / written once)
   auto vb = [&](double per_entry) { return per_entry * double(N) * nrhs; };
   const double rb = 8.0 * nblk * nrhs;
-  CK(cudaMemsetAsync(sc, 0, 16 * nrhs * sizeof(double), s));
+  CK(cudaMemsetAsync(b.sc, 0, 16 * nrhs * sizeof(double), s));
   for (int c = 0; c < nrhs; ++c) CK(cudaMemsetAsync(u + c * ldu, 0, N * sizeof(double), s));
-  { Launch t_(kCatVector, s, 0.0, vb(16)); launch_copy_cols(N, nrhs, f, ldf, r, ld, s); }
-  { Launch t_(kCatVector, s, 0.0, vb(8)); launch_dot_partial(N, f, ldf, f, ldf, nrhs, part, s); }
-  { Launch t_(kCatVector, s, 0.0, rb); launch_reduce(part, nblk, nrhs, sc, 0, rtol, s); }
-  { Launch t_(kCatVector, s, 0.0, vb(16)); launch_copy_cols(N, nrhs, r, ld, z, ld, s); }
-  if ((rc = apply_dispatch(F, z, ld, nrhs, s, true))) return rc;
-  { Launch t_(kCatVector, s, 0.0, vb(16)); launch_dot_partial(N, r, ld, z, ld, nrhs, part, s); }
-  { Launch t_(kCatVector, s, 0.0, rb); launch_reduce(part, nblk, nrhs, sc, 1, rtol, s); }
-  { Launch t_(kCatVector, s, 0.0, vb(24)); launch_update_p(N, nrhs, sc, z, ld, p, ld, 1, s); }
+  { Launch t_(kCatVector, s, 0.0, vb(16)); launch_copy_cols(N, nrhs, f, ldf, b.r, ld, s); }
+  { Launch t_(kCatVector, s, 0.0, vb(8)); launch_dot_partial(N, f, ldf, f, ldf, nrhs, b.part, s); }
+  { Launch t_(kCatVector, s, 0.0, rb); launch_reduce(b.part, nblk, nrhs, b.sc, 0, rtol, s); }
+  { Launch t_(kCatVector, s, 0.0, vb(16)); launch_copy_cols(N, nrhs, b.r, ld, b.z, ld, s); }
+  if ((rc = apply_dispatch(F, b.z, ld, nrhs, s, true))) return rc;
+  { Launch t_(kCatVector, s, 0.0, vb(16)); launch_dot_partial(N, b.r, ld, b.z, ld, nrhs, b.part, s); }
+  { Launch t_(kCatVector, s, 0.0, rb); launch_reduce(b.part, nblk, nrhs, b.sc, 1, rtol, s); }
+  { Launch t_(kCatVector, s, 0.0, vb(24)); launch_update_p(N, nrhs, b.sc, b.z, ld, b.p, ld, 1, s); }
   std::vector<double> hsc(8 * nrhs);
-  std::vector<int> it(nrhs, maxit);
-  std::vector<char> was_done(nrhs, 0);
+  std::vector<int> it(nrhs, maxit), hkit(nrhs + 1, 0);
   int all_done = 0;
-  for (int k = 1; k <= maxit; ++k) {
-    { Launch t_(kCatSpmv, s, spmv_flops * nrhs, spmv_bytes * nrhs); launch_spmv(F->gd, F->diag, F->off, p, ld, q, ld, nrhs, part, s); }
-    { Launch t_(kCatVector, s, 0.0, rb); launch_reduce(part, nblk, nrhs, sc, 2, rtol, s); }
-    { Launch t_(kCatVector, s, 0.0, vb(48)); launch_update_xr(N, nrhs, sc, u, ldu, r, ld, p, ld, q, ld, part, s); }
-    { Launch t_(kCatVector, s, 0.0, rb); launch_reduce(part, nblk, nrhs, sc, 3, rtol, s); }
-    CK(cudaMemcpyAsync(hsc.data(), sc, 8 * nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    int nd = 0;
-    for (int c = 0; c < nrhs; ++c) {
-      if (hsc[8 * c + kScDone] != 0.0) {
-        if (!was_done[c]) { it[c] = k; was_done[c] = 1; }
-        ++nd;
-      }
-    }
-    if (nd == nrhs) { all_done = 1; break; }
-    { Launch t_(kCatVector, s, 0.0, vb(16)); launch_copy_cols(N, nrhs, r, ld, z, ld, s); }
-    if ((rc = apply_dispatch(F, z, ld, nrhs, s, true))) return rc;
-    { Launch t_(kCatVector, s, 0.0, vb(16)); launch_dot_partial(N, r, ld, z, ld, nrhs, part, s); }
-    { Launch t_(kCatVector, s, 0.0, rb); launch_reduce(part, nblk, nrhs, sc, 4, rtol, s); }
-    { Launch t_(kCatVector, s, 0.0, vb(24)); launch_update_p(N, nrhs, sc, z, ld, p, ld, 0, s); }
+  // the iterations: on the device as one graph with a conditional loop
+  // (unless per-launch timing is on), else from the host
+  bool timing;
+  {
+    std::lock_guard<std::mutex> lk(g_kmu);
+    timing = g_timing;
   }
-  if (maxit == 0) {
-    CK(cudaMemcpyAsync(hsc.data(), sc, 8 * nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
+  bool device_loop = false;
+  if (!timing && maxit > 0) {
+    const bool match = F->pcg_graph && F->pg_u == u && F->pg_work == F->work &&
+                       F->pg_ubuf == F->ubuf && F->pg_ldu == ldu && F->pg_nrhs == nrhs &&
+                       F->pg_rtol == rtol && F->pg_maxit == maxit;
+    if (match || capture_pcg(F, nrhs, u, ldu, rtol, maxit)) {
+      CK(cudaGraphLaunch(F->pcg_graph, s));
+      CK(cudaMemcpyAsync(hkit.data(), b.kit, (nrhs + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(hsc.data(), b.sc, 8 * nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
+      device_loop = true;
+    }
+  }
+  if (!device_loop) {
+    std::vector<char> was_done(nrhs, 0);
+    for (int k = 1; k <= maxit; ++k) {
+      pcg_step(F, nrhs, u, ldu, b, rtol, s);
+      CK(cudaMemcpyAsync(hsc.data(), b.sc, 8 * nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      int nd = 0;
+      for (int c = 0; c < nrhs; ++c) {
+        if (hsc[8 * c + kScDone] != 0.0) {
+          if (!was_done[c]) { it[c] = k; was_done[c] = 1; }
+          ++nd;
+        }
+      }
+      if (nd == nrhs) { all_done = 1; break; }
+      if ((rc = pcg_direction(F, nrhs, b, rtol, s, true))) return rc;
+    }
+    if (maxit == 0)
+      CK(cudaMemcpyAsync(hsc.data(), b.sc, 8 * nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
   }
   // true residual
-  { Launch t_(kCatSpmv, s, spmv_flops * nrhs, spmv_bytes * nrhs); launch_spmv(F->gd, F->diag, F->off, u, ldu, q, ld, nrhs, nullptr, s); }
-  { Launch t_(kCatVector, s, 0.0, vb(24)); launch_sub(N, nrhs, f, ldf, q, ld, r, ld, s); }
-  { Launch t_(kCatVector, s, 0.0, vb(8)); launch_dot_partial(N, r, ld, r, ld, nrhs, part, s); }
-  { Launch t_(kCatVector, s, 0.0, rb); launch_reduce(part, nblk, nrhs, sc2, 1, rtol, s); }
+  { Launch t_(kCatSpmv, s, spmv_flops * nrhs, spmv_bytes * nrhs); launch_spmv(F->gd, F->diag, F->off, u, ldu, b.q, ld, nrhs, nullptr, s); }
+  { Launch t_(kCatVector, s, 0.0, vb(24)); launch_sub(N, nrhs, f, ldf, b.q, ld, b.r, ld, s); }
+  { Launch t_(kCatVector, s, 0.0, vb(8)); launch_dot_partial(N, b.r, ld, b.r, ld, nrhs, b.part, s); }
+  { Launch t_(kCatVector, s, 0.0, rb); launch_reduce(b.part, nblk, nrhs, b.sc2, 1, rtol, s); }
   std::vector<double> h2(8 * nrhs);
-  CK(cudaMemcpyAsync(h2.data(), sc2, 8 * nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(h2.data(), b.sc2, 8 * nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   CK(cudaGetLastError());
+  if (device_loop) {
+    credit_counts(F->pg_pre, 1.0);
+    credit_counts(F->pg_body, double(hkit[0] - 1));
+    all_done = 1;
+    for (int c = 0; c < nrhs; ++c) {
+      it[c] = hkit[1 + c];
+      if (hsc[8 * c + kScDone] == 0.0) all_done = 0;
+    }
+  }
   for (int c = 0; c < nrhs; ++c) {
     const double ff = hsc[8 * c + kScFF];
     if (iters) iters[c] = it[c];
@@ -2126,6 +2306,7 @@ void rhif_free(rhif_handle* F) {
   F->mem.release_all();
   cudaStreamSynchronize(F->mem.s);
   if (F->apply_graph) cudaGraphExecDestroy(F->apply_graph);
+  if (F->pcg_graph) cudaGraphExecDestroy(F->pcg_graph);
   if (F->capture_stream) cudaStreamDestroy(F->capture_stream);
   for (auto& S : F->levels) {
     if (S.plan.cell_prob.empty()) recycle_plan(std::move(S.plan));

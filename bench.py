@@ -334,12 +334,16 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def alu_peak_nominal(precision: str):
-    """Plain-ALU peak of GB300 from its unit counts and clock (TFLOP/s): FP32 =
-    152 SMs x 128 FMA lanes x 2 flops x 2.07 GHz; FP64 = the chip's nominal
-    1.25 TFLOP/s.  The cuBLAS GEMM rates measured live are reported beside it."""
+def alu_peak_nominal(precision: str, torch=None, sm_max_mhz=None):
+    """Plain-ALU peak from the unit counts and clock (TFLOP/s): FP32 = SMs (read
+    from the device) x 128 FMA lanes x 2 flops x the maximum SM clock (sampled
+    by nvidia-smi during the run, else 2070 MHz); FP64 = GB300's nominal 1.25
+    TFLOP/s.  The cuBLAS GEMM rates measured live are reported beside it."""
     if precision == "fp32":
-        return 152 * 128 * 2 * 2.07e9 / 1e12, "nominal: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz"
+        sms = torch.cuda.get_device_properties(0).multi_processor_count if torch is not None else 152
+        mhz = float(sm_max_mhz) if sm_max_mhz else 2070.0
+        return (sms * 128 * 2 * mhz * 1e6 / 1e12,
+                f"derived: {sms} SMs (device) x 128 FP32 lanes x 2 flops x {mhz:.0f} MHz (max SM clock)")
     return 1.25, "nominal GB300 FP64 rate"
 
 
@@ -727,7 +731,7 @@ def gpu_arm(args):
                 "peak_kind": hbm_kind}
     else:
         achieved = st["flops"] / max(st["launches"], 1) / (per_launch_ms / 1e3) / 1e12
-        peak, kind = alu_peak_nominal(wl.headline)
+        peak, kind = alu_peak_nominal(wl.headline, torch, (clk or {}).get("sm_max_mhz"))
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "peak_kind": kind}
     roof["frac"] = roof["achieved"] / roof["peak"]

@@ -271,7 +271,12 @@ int rhif_spmv(const rhif_handle* F, int nrhs, const double* x, int64_t ldx,
  * x0 = 0, stopped when ||f - A u|| / ||f|| <= rtol (recursive residual) for
  * every right-hand side or after maxit iterations.  iters and relres are HOST
  * arrays of nrhs entries receiving the iteration count and the true relative
- * residual.  Returns NOT_CONVERGED if some system missed rtol. */
+ * residual.  Returns NOT_CONVERGED if some system missed rtol.  The iterations
+ * run on the device as one CUDA graph (captured once per u, nrhs, rtol and
+ * maxit, on a private stream, and launched on `stream`) whose conditional
+ * loop tests convergence on the device; the call returns after one wait for
+ * the results.  While kernel timing is on (rhif_set_timing) the iterations
+ * are issued from the host instead, one wait per iteration. */
 int rhif_pcg(const rhif_handle* F, int nrhs, const double* f, int64_t ldf, double* u,
              int64_t ldu, double rtol, int maxit, int* iters, double* relres,
              void* stream);

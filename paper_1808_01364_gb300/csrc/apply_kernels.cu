@@ -1893,66 +1893,71 @@ __device__ double edge_weight(const GeoDev& G, const double* a_pix, const int x[
     s += a_pix[p[0] + (int64_t)nx * (p[1] + (int64_t)ny * p[2])];
     ++cnt;
   }
-  return s / cnt;
+  return s * (1.0 / cnt);   // cnt = 2^(d-1): the same value as s / cnt, without a divide
 }
 
+// One thread per row.  I: index type of the row arithmetic (32-bit while the
+// entry count fits: GB300 has no fast 64-bit divide, and its FP64 divide is
+// slow too, so the 1/h^2 factor is applied as the exact integer (n + 1)^2).
+template <typename I>
 __global__ void k_assemble_fd(GeoDev G, const double* a_pix, const double* b_node, double b_const,
                               int64_t* rowptr, int32_t* col, double* val) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= G.N) return;
+  const int64_t i64 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i64 >= G.N) return;
+  const I i = (I)i64;
   int x[3] = {0, 0, 0};   // 0-based
-  int64_t rem = i;
+  I rem = i;
   for (int a = 0; a < G.d; ++a) {
-    x[a] = (int)(rem % G.ns[a]);
-    rem /= G.ns[a];
+    x[a] = (int)(rem % (I)G.ns[a]);
+    rem /= (I)G.ns[a];
   }
-  // rows before i, counted slab by slab from the last axis
-  int64_t before = 0, rows_before = 0;
+  // entries before row i, counted slab by slab from the last axis
+  I before = 0;
   {
-    int64_t inner = 1;   // rows in one slab of the lower axes
-    for (int a = 0; a < G.d; ++a) inner *= G.ns[a];
+    I inner = 1;   // rows in one slab of the lower axes
+    for (int a = 0; a < G.d; ++a) inner *= (I)G.ns[a];
     for (int a = G.d - 1; a >= 0; --a) {
-      inner /= G.ns[a];
+      inner /= (I)G.ns[a];
       // rows with coordinate a in [0, x[a]) and equal higher coordinates: box [0,n_0)x..x[0,x[a])x{x_{a+1}}..
-      const int64_t cnt = inner * x[a];
-      rows_before += cnt;
-      int64_t nbs = cnt;   // diagonal entries
+      const I cnt = inner * (I)x[a];
+      I nbs = cnt;   // diagonal entries
       for (int b = 0; b < G.d; ++b) {
-        int64_t sb;
-        if (b < a) sb = nb_sum(G.ns[b], G.ns[b]) * (cnt / G.ns[b]);
-        else if (b == a) sb = nb_sum(x[a], G.ns[a]) * inner;
-        else sb = (int64_t)nb_one(x[b], G.ns[b]) * cnt;
+        I sb;
+        if (b < a) sb = (I)nb_sum(G.ns[b], G.ns[b]) * (cnt / (I)G.ns[b]);
+        else if (b == a) sb = (I)nb_sum(x[a], G.ns[a]) * inner;
+        else sb = (I)nb_one(x[b], G.ns[b]) * cnt;
         nbs += sb;
       }
       before += nbs;
     }
   }
-  rowptr[i] = before;
-  if (i == G.N - 1) {
+  rowptr[i64] = (int64_t)before;
+  if (i64 == G.N - 1) {
     int64_t own = 1;
     for (int a = 0; a < G.d; ++a) own += nb_one(x[a], G.ns[a]);
-    rowptr[G.N] = before + own;
+    rowptr[G.N] = (int64_t)before + own;
   }
   int x1[3] = {1, 1, 1};
   for (int a = 0; a < G.d; ++a) x1[a] = x[a] + 1;
-  double diag = b_node ? b_node[i] : b_const;
+  double diag = b_node ? b_node[i64] : b_const;
   double offv[3][2];
   for (int a = 0; a < G.d; ++a) {
-    const double h = 1.0 / (G.ns[a] + 1);
+    const double q = (double)(G.ns[a] + 1);   // 1/h^2 = (n + 1)^2, exact
+    const double ih2 = q * q;
     int xl[3] = {x1[0], x1[1], x1[2]};
     xl[a] = x1[a] - 1;
-    const double wl = edge_weight(G, a_pix, xl, a) / (h * h);   // edge from x-1 to x
-    const double wr = edge_weight(G, a_pix, x1, a) / (h * h);   // edge from x to x+1
+    const double wl = edge_weight(G, a_pix, xl, a) * ih2;   // edge from x-1 to x
+    const double wr = edge_weight(G, a_pix, x1, a) * ih2;   // edge from x to x+1
     diag += wl + wr;
     offv[a][0] = -wl;
     offv[a][1] = -wr;
   }
-  int64_t k = before;
+  int64_t k = (int64_t)before;
   for (int a = G.d - 1; a >= 0; --a)
-    if (x[a] >= 1) { col[k] = (int32_t)(i - G.stride[a]); val[k] = offv[a][0]; ++k; }
-  col[k] = (int32_t)i; val[k] = diag; ++k;
+    if (x[a] >= 1) { col[k] = (int32_t)(i64 - G.stride[a]); val[k] = offv[a][0]; ++k; }
+  col[k] = (int32_t)i64; val[k] = diag; ++k;
   for (int a = 0; a < G.d; ++a)
-    if (x[a] + 1 < G.ns[a]) { col[k] = (int32_t)(i + G.stride[a]); val[k] = offv[a][1]; ++k; }
+    if (x[a] + 1 < G.ns[a]) { col[k] = (int32_t)(i64 + G.stride[a]); val[k] = offv[a][1]; ++k; }
 }
 
 __global__ void k_exp(int64_t n, const double* x, double* y) {
@@ -1967,7 +1972,11 @@ void launch_exp(int64_t n, const double* x, double* y, cudaStream_t s) {
 void launch_assemble_fd(const GeoDev& G, const double* a_pix, const double* b_node, double b_const,
                         int64_t* rowptr, int32_t* col, double* val, cudaStream_t s) {
   if (!G.N) return;
-  k_assemble_fd<<<(unsigned)((G.N + 255) / 256), 256, 0, s>>>(G, a_pix, b_node, b_const, rowptr, col, val);
+  const unsigned grid = (unsigned)((G.N + 255) / 256);
+  if (G.N * (2 * G.d + 1) < (int64_t(1) << 31))   // every entry offset fits 32 bits
+    k_assemble_fd<int32_t><<<grid, 256, 0, s>>>(G, a_pix, b_node, b_const, rowptr, col, val);
+  else
+    k_assemble_fd<int64_t><<<grid, 256, 0, s>>>(G, a_pix, b_node, b_const, rowptr, col, val);
 }
 
 // one thread per pixel: -a_p / 2^(d-1) * sum over the 2^(d-1)*d grid edges of
@@ -1993,7 +2002,8 @@ __global__ void k_grad_logcoef(GeoDev G, const double* a_pix, const double* u, c
   };
   double acc = 0.0;
   for (int ax = 0; ax < G.d; ++ax) {
-    const double h = 1.0 / (G.ns[ax] + 1);
+    const double q = (double)(G.ns[ax] + 1);   // 1/h^2 = (n + 1)^2, exact (as the assembly)
+    const double ih2 = q * q;
     for (int m = 0; m < (1 << (G.d - 1)); ++m) {
       int c0[3] = {0, 0, 0};
       int bit = 0;
@@ -2003,10 +2013,10 @@ __global__ void k_grad_logcoef(GeoDev G, const double* a_pix, const double* u, c
       }
       int c1[3] = {c0[0], c0[1], c0[2]};
       c1[ax] += 1;
-      acc += (node(c1, u) - node(c0, u)) * (node(c1, lam) - node(c0, lam)) / (h * h);
+      acc += (node(c1, u) - node(c0, u)) * (node(c1, lam) - node(c0, lam)) * ih2;
     }
   }
-  grad[p] = -a_pix[p] * acc / double(1 << (G.d - 1));
+  grad[p] = -a_pix[p] * acc * (1.0 / double(1 << (G.d - 1)));   // exact: a power of two
 }
 
 void launch_grad_logcoef(const GeoDev& G, const double* a_pix, const double* u, const double* lam,

@@ -211,6 +211,7 @@ template <typename T, bool STAGE>
 __global__ void __launch_bounds__(32 * kLeafWarps)
 k_apply_leaf_up(LevelDev Lv, double* x, int64_t ldx, int nrhs, double* ubuf, int64_t ldu,
                 int per_warp_bytes) {
+  pdl_trigger();
   extern __shared__ __align__(16) unsigned char smraw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c = blockIdx.x * (blockDim.x >> 5) + warp;
@@ -224,6 +225,7 @@ k_apply_leaf_up(LevelDev Lv, double* x, int64_t ldx, int nrhs, double* ubuf, int
   const int32_t* gI = Lv.gids + Lv.gid_off[c];
   const int* ci = Lv.cpl_i + Lv.b_off[c];
   const T* ca = (const T*)Lv.cpl_a + Lv.b_off[c];
+  pdl_wait();   // the vectors come from the previous kernel of the sweep
   for (int r = blockIdx.y; r < nrhs; r += gridDim.y) {   // right-hand sides over grid.y
     double* xr = x + r * ldx;
     warp_gather(xr, gI, nI, y);
@@ -246,6 +248,7 @@ k_apply_leaf_up(LevelDev Lv, double* x, int64_t ldx, int nrhs, double* ubuf, int
 template <typename T, bool STAGE>
 __global__ void __launch_bounds__(32 * kLeafWarps)
 k_apply_leaf_down(LevelDev Lv, double* x, int64_t ldx, int nrhs, int per_warp_bytes) {
+  pdl_trigger();
   extern __shared__ __align__(16) unsigned char smraw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c = blockIdx.x * (blockDim.x >> 5) + warp;
@@ -261,6 +264,7 @@ k_apply_leaf_down(LevelDev Lv, double* x, int64_t ldx, int nrhs, int per_warp_by
   const int* ci = Lv.cpl_i + Lv.b_off[c];
   const T* ca = (const T*)Lv.cpl_a + Lv.b_off[c];
   T* xb = v + Lv.max_nI + 1;   // boundary values
+  pdl_wait();   // the vectors come from the previous kernel of the sweep
   for (int r = blockIdx.y; r < nrhs; r += gridDim.y) {   // right-hand sides over grid.y
     double* xr = x + r * ldx;
     for (int i = lane; i < nI; i += 32) v[i] = T(0);
@@ -465,6 +469,7 @@ template <typename T>
 __global__ void __launch_bounds__(128)
 k_apply_leaf_up_mr(LevelDev Lv, double* x, int64_t ldx, int nrhs, double* ubuf, int64_t ldu,
                    int per_warp_bytes) {
+  pdl_trigger();
   extern __shared__ __align__(16) unsigned char smraw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c = blockIdx.x * (blockDim.x >> 5) + warp;
@@ -477,6 +482,7 @@ k_apply_leaf_up_mr(LevelDev Lv, double* x, int64_t ldx, int nrhs, double* ubuf, 
   const int32_t* gI = Lv.gids + Lv.gid_off[c];
   const int* ci = Lv.cpl_i + Lv.b_off[c];
   const T* ca = (const T*)Lv.cpl_a + Lv.b_off[c];
+  pdl_wait();   // the vectors come from the previous kernel of the sweep
   for (int r0 = blockIdx.y * 32; r0 < nrhs; r0 += gridDim.y * 32) {
     const int R = min(32, nrhs - r0);
     mr_gather<T>(x, ldx, r0, R, gI, nI, y);
@@ -499,6 +505,7 @@ k_apply_leaf_up_mr(LevelDev Lv, double* x, int64_t ldx, int nrhs, double* ubuf, 
 template <typename T>
 __global__ void __launch_bounds__(128)
 k_apply_leaf_down_mr(LevelDev Lv, double* x, int64_t ldx, int nrhs, int per_warp_bytes) {
+  pdl_trigger();
   extern __shared__ __align__(16) unsigned char smraw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c = blockIdx.x * (blockDim.x >> 5) + warp;
@@ -513,6 +520,7 @@ k_apply_leaf_down_mr(LevelDev Lv, double* x, int64_t ldx, int nrhs, int per_warp
   const int32_t* gB = gI + nI;
   const int* ci = Lv.cpl_i + Lv.b_off[c];
   const T* ca = (const T*)Lv.cpl_a + Lv.b_off[c];
+  pdl_wait();   // the vectors come from the previous kernel of the sweep
   for (int r0 = blockIdx.y * 32; r0 < nrhs; r0 += gridDim.y * 32) {
     const int R = min(32, nrhs - r0);
     mr_gather<T>(x, ldx, r0, R, gI, nI, t);
@@ -556,6 +564,7 @@ template <typename T, int RC>
 __global__ void __launch_bounds__(kApplyThreads)
 k_apply_cell_up(LevelDev Lv, double* x, int64_t ldx, int nrhs, double* ubuf, int64_t ldu,
                 int stage) {
+  pdl_trigger();
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ __align__(8) uint64_t bar;
   const int ld = Lv.max_nI + 1;
@@ -567,6 +576,7 @@ k_apply_cell_up(LevelDev Lv, double* x, int64_t ldx, int nrhs, double* ubuf, int
   if (stage) F = front_stage(F, n, nI, (T*)(smraw + round16(2 * RC * ld * sizeof(T))), &bar);
   const int32_t* gI = Lv.gids + Lv.gid_off[c];
   __syncthreads();
+  pdl_wait();   // the vectors come from the previous kernel of the sweep
   for (int r0 = blockIdx.y * RC; r0 < nrhs; r0 += gridDim.y * RC) {   // chunks over grid.y
     const int rc = min(RC, nrhs - r0);
     for (int idx = threadIdx.x; idx < rc * nI; idx += blockDim.x) {
@@ -618,6 +628,7 @@ k_apply_cell_up(LevelDev Lv, double* x, int64_t ldx, int nrhs, double* ubuf, int
 template <typename T, int RC>
 __global__ void __launch_bounds__(kApplyThreads)
 k_apply_cell_down(LevelDev Lv, double* x, int64_t ldx, int nrhs, int stage) {
+  pdl_trigger();
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ __align__(8) uint64_t bar;
   const int ldi = Lv.max_nI, ldb = Lv.max_nB + 1;
@@ -634,6 +645,7 @@ k_apply_cell_down(LevelDev Lv, double* x, int64_t ldx, int nrhs, int stage) {
   const int32_t* gB = gI + nI;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   __syncthreads();
+  pdl_wait();   // the vectors come from the previous kernel of the sweep
   for (int r0 = blockIdx.y * RC; r0 < nrhs; r0 += gridDim.y * RC) {   // chunks over grid.y
     const int rc = min(RC, nrhs - r0);
     for (int idx = threadIdx.x; idx < rc * nB; idx += blockDim.x) {
@@ -706,6 +718,7 @@ template <typename T>
 __global__ void __launch_bounds__(kBigRows)
 k_apply_big_up1(LevelDev Lv, const double* x, int64_t ldx, int nrhs, int rc, double* tmp,
                 int64_t ldt) {
+  pdl_trigger();
   extern __shared__ __align__(16) unsigned char smraw[];
   T* xs = (T*)smraw;   // [kend][rc]
   const int c = blockIdx.y;
@@ -718,6 +731,7 @@ k_apply_big_up1(LevelDev Lv, const double* x, int64_t ldx, int nrhs, int rc, dou
   const T* F = (const T*)Lv.front + Lv.front_off[c];
   const int32_t* gI = Lv.gids + Lv.gid_off[c];
   double* tc = tmp + Lv.gid_off[c];
+  pdl_wait();   // the vectors come from the previous kernel of the sweep
   for (int q0 = 0; q0 < nrhs; q0 += rc) {
     const int nr = min(rc, nrhs - q0);
     __syncthreads();
@@ -744,6 +758,7 @@ template <typename T>
 __global__ void __launch_bounds__(kBigRows)
 k_apply_big_up2(LevelDev Lv, double* x, int64_t ldx, int nrhs, int rc, double* ubuf, int64_t ldu,
                 const double* tmp, int64_t ldt) {
+  pdl_trigger();
   extern __shared__ __align__(16) unsigned char smraw[];
   T* ys = (T*)smraw;   // [nI][rc]
   const int c = blockIdx.y;
@@ -754,6 +769,7 @@ k_apply_big_up2(LevelDev Lv, double* x, int64_t ldx, int nrhs, int rc, double* u
   const T* F = (const T*)Lv.front + Lv.front_off[c];
   const int32_t* gI = Lv.gids + Lv.gid_off[c];
   const double* tc = tmp + Lv.gid_off[c];
+  pdl_wait();   // the vectors come from the previous kernel of the sweep
   for (int q0 = 0; q0 < nrhs; q0 += rc) {
     const int nr = min(rc, nrhs - q0);
     if (row < nI)
@@ -785,6 +801,7 @@ template <typename T>
 __global__ void __launch_bounds__(32 * kBigWarps)
 k_apply_big_down1(LevelDev Lv, const double* x, int64_t ldx, int nrhs, int rc, double* tmp,
                   int64_t ldt) {
+  pdl_trigger();
   extern __shared__ __align__(16) unsigned char smraw[];
   T* xb = (T*)smraw;   // [nB][rc]
   const int c = blockIdx.y;
@@ -796,6 +813,7 @@ k_apply_big_down1(LevelDev Lv, const double* x, int64_t ldx, int nrhs, int rc, d
   const int32_t* gI = Lv.gids + Lv.gid_off[c];
   const int32_t* gB = gI + nI;
   double* tc = tmp + Lv.gid_off[c];
+  pdl_wait();   // the vectors come from the previous kernel of the sweep
   for (int q0 = 0; q0 < nrhs; q0 += rc) {
     const int nr = min(rc, nrhs - q0);
     __syncthreads();
@@ -828,6 +846,7 @@ template <typename T>
 __global__ void __launch_bounds__(32 * kBigWarps)
 k_apply_big_down2(LevelDev Lv, double* x, int64_t ldx, int nrhs, int rc, const double* tmp,
                   int64_t ldt) {
+  pdl_trigger();
   extern __shared__ __align__(16) unsigned char smraw[];
   T* ts = (T*)smraw;   // [nI][rc]
   const int c = blockIdx.y;
@@ -838,6 +857,7 @@ k_apply_big_down2(LevelDev Lv, double* x, int64_t ldx, int nrhs, int rc, const d
   const T* F = (const T*)Lv.front + Lv.front_off[c];
   const int32_t* gI = Lv.gids + Lv.gid_off[c];
   const double* tc = tmp + Lv.gid_off[c];
+  pdl_wait();   // the vectors come from the previous kernel of the sweep
   for (int q0 = 0; q0 < nrhs; q0 += rc) {
     const int nr = min(rc, nrhs - q0);
     __syncthreads();
@@ -1000,6 +1020,7 @@ template <typename T>
 __global__ void __launch_bounds__(kGroupThreads)
 k_apply_group_up(LevelDev Lv, PhaseDev Ph, int gather, double* x, int64_t ldx, int nrhs,
                  const double* ubuf, int64_t ldu, int stage) {
+  pdl_trigger();
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ __align__(8) uint64_t bar;
   T* xg = (T*)smraw;
@@ -1016,6 +1037,7 @@ k_apply_group_up(LevelDev Lv, PhaseDev Ph, int gather, double* x, int64_t ldx, i
   else
     group_global(Ph, pi, u, n, &Lg, &Fu, &Tm);
   __syncthreads();
+  pdl_wait();   // the vectors come from the previous kernel of the sweep
   for (int r = blockIdx.y; r < nrhs; r += gridDim.y) {   // right-hand sides over grid.y
     double* xr = x + r * ldx;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -1043,6 +1065,7 @@ k_apply_group_up(LevelDev Lv, PhaseDev Ph, int gather, double* x, int64_t ldx, i
 template <typename T>
 __global__ void __launch_bounds__(kGroupThreads)
 k_apply_group_down(LevelDev Lv, PhaseDev Ph, double* x, int64_t ldx, int nrhs, int stage) {
+  pdl_trigger();
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ __align__(8) uint64_t bar;
   T* xg = (T*)smraw;
@@ -1059,6 +1082,7 @@ k_apply_group_down(LevelDev Lv, PhaseDev Ph, double* x, int64_t ldx, int nrhs, i
   else
     group_global(Ph, pi, u, n, &Lg, &Fu, &Tm);
   __syncthreads();
+  pdl_wait();   // the vectors come from the previous kernel of the sweep
   for (int r = blockIdx.y; r < nrhs; r += gridDim.y) {   // right-hand sides over grid.y
     double* xr = x + r * ldx;
     for (int i = threadIdx.x; i < n; i += blockDim.x) xg[i] = T(xr[gid[i]]);
@@ -1089,6 +1113,7 @@ template <typename T>
 __global__ void __launch_bounds__(32 * kGroupWarps)
 k_apply_group_up_warp(LevelDev Lv, PhaseDev Ph, int gather, double* x, int64_t ldx, int nrhs,
                       const double* ubuf, int64_t ldu, int per_warp_bytes) {
+  pdl_trigger();
   extern __shared__ __align__(16) unsigned char smraw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = blockIdx.x * kGroupWarps + warp;
@@ -1110,6 +1135,7 @@ k_apply_group_up_warp(LevelDev Lv, PhaseDev Ph, int gather, double* x, int64_t l
   const int p_sk = (u >= 0 && lane < k) ? perm[lane] : 0;
   const int p_rd = (u >= 0 && lane < r) ? perm[k + lane] : 0;
   const int my_idx = (u >= 0 && lane < n) ? invp[lane] : 0;
+  pdl_wait();   // the vectors come from the previous kernel of the sweep
   for (int rr = blockIdx.y; rr < nrhs; rr += gridDim.y) {   // right-hand sides over grid.y
     double* xr = x + rr * ldx;
     T xv = T(0);
@@ -1160,6 +1186,7 @@ template <typename T>
 __global__ void __launch_bounds__(32 * kGroupWarps)
 k_apply_group_down_warp(LevelDev Lv, PhaseDev Ph, double* x, int64_t ldx, int nrhs,
                         int per_warp_bytes) {
+  pdl_trigger();
   extern __shared__ __align__(16) unsigned char smraw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = blockIdx.x * kGroupWarps + warp;
@@ -1181,6 +1208,7 @@ k_apply_group_down_warp(LevelDev Lv, PhaseDev Ph, double* x, int64_t ldx, int nr
   const int p_sk = (u >= 0 && lane < k) ? perm[lane] : 0;
   const int p_rd = (u >= 0 && lane < r) ? perm[k + lane] : 0;
   const int my_idx = (u >= 0 && lane < n) ? invp[lane] : 0;
+  pdl_wait();   // the vectors come from the previous kernel of the sweep
   for (int rr = blockIdx.y; rr < nrhs; rr += gridDim.y) {   // right-hand sides over grid.y
     double* xr = x + rr * ldx;
     T xv = lane < n ? T(xr[gid[lane]]) : T(0);
@@ -1301,6 +1329,7 @@ template <typename T>
 __global__ void __launch_bounds__(32 * kGroupWarps)
 k_apply_group_up_mr(LevelDev Lv, PhaseDev Ph, int gather, double* x, int64_t ldx, int nrhs,
                     const double* ubuf, int64_t ldu, int per_warp_bytes) {
+  pdl_trigger();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = blockIdx.x * (blockDim.x >> 5) + warp;
   if (g >= Lv.ngroup || Lv.group_t[g] < Ph.pre_min_type) return;
@@ -1312,6 +1341,7 @@ k_apply_group_up_mr(LevelDev Lv, PhaseDev Ph, int gather, double* x, int64_t ldx
   uint64_t* bar;
   T* v = group_mr_setup<T>(Lv, Ph, g, per_warp_bytes, &Lg, &Fu, &Tm, &perm, &bar);
   T* xv = v + lane;   // xv[i * kMrLd]: entry i of this lane's right-hand side
+  pdl_wait();   // the vectors come from the previous kernel of the sweep
   for (int r0 = blockIdx.y * 32; r0 < nrhs; r0 += gridDim.y * 32) {
     const int R = min(32, nrhs - r0);
     group_mr_gather<T>(Lv, g, n, gid, x, ldx, gather ? ubuf : nullptr, ldu, r0, R, v);
@@ -1350,6 +1380,7 @@ k_apply_group_up_mr(LevelDev Lv, PhaseDev Ph, int gather, double* x, int64_t ldx
 template <typename T>
 __global__ void __launch_bounds__(32 * kGroupWarps)
 k_apply_group_down_mr(LevelDev Lv, PhaseDev Ph, double* x, int64_t ldx, int nrhs, int per_warp_bytes) {
+  pdl_trigger();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = blockIdx.x * (blockDim.x >> 5) + warp;
   if (g >= Lv.ngroup || Lv.group_t[g] < Ph.pre_min_type) return;
@@ -1361,6 +1392,7 @@ k_apply_group_down_mr(LevelDev Lv, PhaseDev Ph, double* x, int64_t ldx, int nrhs
   uint64_t* bar;
   T* v = group_mr_setup<T>(Lv, Ph, g, per_warp_bytes, &Lg, &Fu, &Tm, &perm, &bar);
   T* xv = v + lane;
+  pdl_wait();   // the vectors come from the previous kernel of the sweep
   for (int r0 = blockIdx.y * 32; r0 < nrhs; r0 += gridDim.y * 32) {
     const int R = min(32, nrhs - r0);
     group_mr_gather<T>(Lv, g, n, gid, x, ldx, nullptr, 0, r0, R, v);
@@ -1432,6 +1464,30 @@ static inline unsigned rhs_grid(int nrhs, int64_t gridx) {
   return (unsigned)std::min<int64_t>(gy, 65535);
 }
 
+// Launches a kernel of an F^{-1} sweep.  Small grids (at most kPdlMaxCtas
+// CTAs: the upper levels, whose kernels are latency-bound) get programmatic
+// stream serialization: the kernel may begin while the previous one on the
+// stream finishes (its factor blocks staged early, pdl_wait before the
+// vectors).  Large grids are launched in plain stream order: there the
+// waiting CTAs and their early staging slowed the running kernel down.
+constexpr int64_t kPdlMaxCtas = 8 * 152;
+
+template <typename... KArgs, typename... Args>
+static void launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = (int64_t)grid.x * grid.y * grid.z <= kPdlMaxCtas ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
+}
+
 template <typename T>
 void launch_apply_cell_up(const LevelDev& Lv, double* x, int64_t ldx, int nrhs, double* ubuf,
                           int64_t ldu, cudaStream_t s) {
@@ -1441,7 +1497,7 @@ void launch_apply_cell_up(const LevelDev& Lv, double* x, int64_t ldx, int nrhs, 
       const size_t per = leaf_mr_bytes<T>(Lv.max_nI, Lv.max_nB, Lv.max_w);
       const int wpc = (int)std::max<size_t>(1, std::min<size_t>(4, kStageBudget / per));
       const dim3 grid((Lv.ncell + wpc - 1) / wpc, mr_chunks(nrhs));
-      k_apply_leaf_up_mr<T><<<grid, 32 * wpc, wpc * per, s>>>(Lv, x, ldx, nrhs, ubuf, ldu, (int)per);
+      launch_pdl(k_apply_leaf_up_mr<T>, grid, 32 * wpc, wpc * per, s, Lv, x, ldx, nrhs, ubuf, ldu, (int)per);
       return;
     }
     const bool multi = nrhs > (int)rhs_grid(nrhs, Lv.ncell / kLeafWarps + 1);
@@ -1451,9 +1507,9 @@ void launch_apply_cell_up(const LevelDev& Lv, double* x, int64_t ldx, int nrhs, 
     const unsigned grid = (Lv.ncell + wpc - 1) / wpc;
     const unsigned gy = rhs_grid(nrhs, grid);
     if (staged)
-      k_apply_leaf_up<T, true><<<dim3(grid, gy), 32 * wpc, wpc * per, s>>>(Lv, x, ldx, nrhs, ubuf, ldu, (int)per);
+      launch_pdl(k_apply_leaf_up<T, true>, dim3(grid, gy), 32 * wpc, wpc * per, s, Lv, x, ldx, nrhs, ubuf, ldu, (int)per);
     else
-      k_apply_leaf_up<T, false><<<dim3(grid, gy), 32 * wpc, wpc * per, s>>>(Lv, x, ldx, nrhs, ubuf, ldu, (int)per);
+      launch_pdl(k_apply_leaf_up<T, false>, dim3(grid, gy), 32 * wpc, wpc * per, s, Lv, x, ldx, nrhs, ubuf, ldu, (int)per);
     return;
   }
   const int rcn = nrhs >= 8 ? 8 : 1;   // right-hand sides per pass
@@ -1462,10 +1518,10 @@ void launch_apply_cell_up(const LevelDev& Lv, double* x, int64_t ldx, int nrhs, 
   const int stage = blk <= kStageBudget && base + blk <= 200 * 1024;
   const dim3 grid(Lv.ncell, rhs_grid((nrhs + rcn - 1) / rcn, Lv.ncell));
   if (rcn == 8)
-    k_apply_cell_up<T, 8><<<grid, kApplyThreads, base + (stage ? blk : 0), s>>>(Lv, x, ldx, nrhs,
+    launch_pdl(k_apply_cell_up<T, 8>, grid, kApplyThreads, base + (stage ? blk : 0), s, Lv, x, ldx, nrhs,
                                                                                 ubuf, ldu, stage);
   else
-    k_apply_cell_up<T, 1><<<grid, kApplyThreads, base + (stage ? blk : 0), s>>>(Lv, x, ldx, nrhs,
+    launch_pdl(k_apply_cell_up<T, 1>, grid, kApplyThreads, base + (stage ? blk : 0), s, Lv, x, ldx, nrhs,
                                                                                 ubuf, ldu, stage);
 }
 
@@ -1477,7 +1533,7 @@ void launch_apply_cell_down(const LevelDev& Lv, double* x, int64_t ldx, int nrhs
       const size_t per = leaf_mr_bytes<T>(Lv.max_nI, Lv.max_nB, Lv.max_w);
       const int wpc = (int)std::max<size_t>(1, std::min<size_t>(4, kStageBudget / per));
       const dim3 grid((Lv.ncell + wpc - 1) / wpc, mr_chunks(nrhs));
-      k_apply_leaf_down_mr<T><<<grid, 32 * wpc, wpc * per, s>>>(Lv, x, ldx, nrhs, (int)per);
+      launch_pdl(k_apply_leaf_down_mr<T>, grid, 32 * wpc, wpc * per, s, Lv, x, ldx, nrhs, (int)per);
       return;
     }
     const bool multi = nrhs > (int)rhs_grid(nrhs, Lv.ncell / kLeafWarps + 1);
@@ -1487,9 +1543,9 @@ void launch_apply_cell_down(const LevelDev& Lv, double* x, int64_t ldx, int nrhs
     const unsigned grid = (Lv.ncell + wpc - 1) / wpc;
     const unsigned gy = rhs_grid(nrhs, grid);
     if (staged)
-      k_apply_leaf_down<T, true><<<dim3(grid, gy), 32 * wpc, wpc * per, s>>>(Lv, x, ldx, nrhs, (int)per);
+      launch_pdl(k_apply_leaf_down<T, true>, dim3(grid, gy), 32 * wpc, wpc * per, s, Lv, x, ldx, nrhs, (int)per);
     else
-      k_apply_leaf_down<T, false><<<dim3(grid, gy), 32 * wpc, wpc * per, s>>>(Lv, x, ldx, nrhs, (int)per);
+      launch_pdl(k_apply_leaf_down<T, false>, dim3(grid, gy), 32 * wpc, wpc * per, s, Lv, x, ldx, nrhs, (int)per);
     return;
   }
   const int rcn = nrhs >= 8 ? 8 : 1;   // right-hand sides per pass
@@ -1498,10 +1554,10 @@ void launch_apply_cell_down(const LevelDev& Lv, double* x, int64_t ldx, int nrhs
   const int stage = blk <= kStageBudget && base + blk <= 200 * 1024;
   const dim3 grid(Lv.ncell, rhs_grid((nrhs + rcn - 1) / rcn, Lv.ncell));
   if (rcn == 8)
-    k_apply_cell_down<T, 8><<<grid, kApplyThreads, base + (stage ? blk : 0), s>>>(Lv, x, ldx, nrhs,
+    launch_pdl(k_apply_cell_down<T, 8>, grid, kApplyThreads, base + (stage ? blk : 0), s, Lv, x, ldx, nrhs,
                                                                                   stage);
   else
-    k_apply_cell_down<T, 1><<<grid, kApplyThreads, base + (stage ? blk : 0), s>>>(Lv, x, ldx, nrhs,
+    launch_pdl(k_apply_cell_down<T, 1>, grid, kApplyThreads, base + (stage ? blk : 0), s, Lv, x, ldx, nrhs,
                                                                                   stage);
 }
 
@@ -1519,10 +1575,10 @@ int launch_apply_big_up(const LevelDev& Lv, double* x, int64_t ldx, int nrhs, do
   if (!Lv.ncell || !Lv.max_nI) return 0;
   const int rc = big_rhs_chunk<T>(Lv.max_nI);
   const size_t sm = (size_t)Lv.max_nI * rc * sizeof(T);
-  k_apply_big_up1<T><<<dim3((Lv.max_nI + kBigRows - 1) / kBigRows, Lv.ncell), kBigRows, sm, s>>>(
+  launch_pdl(k_apply_big_up1<T>, dim3((Lv.max_nI + kBigRows - 1) / kBigRows, Lv.ncell), kBigRows, sm, s,
       Lv, x, ldx, nrhs, rc, tmp, ldu);
   const int rows = std::max(Lv.max_nI, Lv.max_nB);
-  k_apply_big_up2<T><<<dim3((rows + kBigRows - 1) / kBigRows, Lv.ncell), kBigRows, sm, s>>>(
+  launch_pdl(k_apply_big_up2<T>, dim3((rows + kBigRows - 1) / kBigRows, Lv.ncell), kBigRows, sm, s,
       Lv, x, ldx, nrhs, rc, ubuf, ldu, tmp, ldu);
   return 2;
 }
@@ -1533,12 +1589,11 @@ int launch_apply_big_down(const LevelDev& Lv, double* x, int64_t ldx, int nrhs, 
   if (!Lv.ncell || !Lv.max_nI) return 0;
   const unsigned gx = (Lv.max_nI + kBigWarps - 1) / kBigWarps;
   const int rcb = big_rhs_chunk<T>(Lv.max_nB);
-  k_apply_big_down1<T><<<dim3(gx, Lv.ncell), 32 * kBigWarps,
-                         (size_t)std::max(Lv.max_nB, 1) * rcb * sizeof(T), s>>>(Lv, x, ldx, nrhs,
-                                                                                rcb, tmp, ldt);
+  launch_pdl(k_apply_big_down1<T>, dim3(gx, Lv.ncell), 32 * kBigWarps,
+             (size_t)std::max(Lv.max_nB, 1) * rcb * sizeof(T), s, Lv, x, ldx, nrhs, rcb, tmp, ldt);
   const int rci = big_rhs_chunk<T>(Lv.max_nI);
-  k_apply_big_down2<T><<<dim3(gx, Lv.ncell), 32 * kBigWarps, (size_t)Lv.max_nI * rci * sizeof(T),
-                         s>>>(Lv, x, ldx, nrhs, rci, tmp, ldt);
+  launch_pdl(k_apply_big_down2<T>, dim3(gx, Lv.ncell), 32 * kBigWarps,
+             (size_t)Lv.max_nI * rci * sizeof(T), s, Lv, x, ldx, nrhs, rci, tmp, ldt);
   return 2;
 }
 
@@ -1549,21 +1604,21 @@ void launch_apply_group_up(const LevelDev& Lv, const PhaseDev& Ph, int gather, d
   if (const int wpc = group_mr_warps<T>(Lv, nrhs)) {
     const size_t per = group_mr_bytes<T>(Lv.max_group);
     const unsigned grid = (Lv.ngroup + wpc - 1) / wpc;
-    k_apply_group_up_mr<T><<<dim3(grid, mr_chunks(nrhs)), 32 * wpc, wpc * per, s>>>(
+    launch_pdl(k_apply_group_up_mr<T>, dim3(grid, mr_chunks(nrhs)), 32 * wpc, wpc * per, s,
         Lv, Ph, gather, x, ldx, nrhs, ubuf, ldu, (int)per);
     return;
   }
   if (Lv.max_group <= 32) {
     const size_t per = group_warp_smem<T>(Lv.max_group);
     const unsigned grid = (Lv.ngroup + kGroupWarps - 1) / kGroupWarps;
-    k_apply_group_up_warp<T><<<dim3(grid, rhs_grid(nrhs, grid)), 32 * kGroupWarps, kGroupWarps * per, s>>>(
+    launch_pdl(k_apply_group_up_warp<T>, dim3(grid, rhs_grid(nrhs, grid)), 32 * kGroupWarps, kGroupWarps * per, s,
         Lv, Ph, gather, x, ldx, nrhs, ubuf, ldu, (int)per);
     return;
   }
   const size_t base = round16(2 * (Lv.max_group + 1) * sizeof(T));
   const size_t blk = group_block_bytes<T>(Lv.max_group);
   const int stage = blk <= kStageBudget;
-  k_apply_group_up<T><<<dim3(Lv.ngroup, rhs_grid(nrhs, Lv.ngroup)), kGroupThreads, base + (stage ? blk : 0), s>>>(
+  launch_pdl(k_apply_group_up<T>, dim3(Lv.ngroup, rhs_grid(nrhs, Lv.ngroup)), kGroupThreads, base + (stage ? blk : 0), s,
       Lv, Ph, gather, x, ldx, nrhs, ubuf, ldu, stage);
 }
 
@@ -1574,21 +1629,21 @@ void launch_apply_group_down(const LevelDev& Lv, const PhaseDev& Ph, double* x, 
   if (const int wpc = group_mr_warps<T>(Lv, nrhs)) {
     const size_t per = group_mr_bytes<T>(Lv.max_group);
     const unsigned grid = (Lv.ngroup + wpc - 1) / wpc;
-    k_apply_group_down_mr<T><<<dim3(grid, mr_chunks(nrhs)), 32 * wpc, wpc * per, s>>>(
+    launch_pdl(k_apply_group_down_mr<T>, dim3(grid, mr_chunks(nrhs)), 32 * wpc, wpc * per, s,
         Lv, Ph, x, ldx, nrhs, (int)per);
     return;
   }
   if (Lv.max_group <= 32) {
     const size_t per = group_warp_smem<T>(Lv.max_group);
     const unsigned grid = (Lv.ngroup + kGroupWarps - 1) / kGroupWarps;
-    k_apply_group_down_warp<T><<<dim3(grid, rhs_grid(nrhs, grid)), 32 * kGroupWarps, kGroupWarps * per, s>>>(
+    launch_pdl(k_apply_group_down_warp<T>, dim3(grid, rhs_grid(nrhs, grid)), 32 * kGroupWarps, kGroupWarps * per, s,
         Lv, Ph, x, ldx, nrhs, (int)per);
     return;
   }
   const size_t base = round16(2 * (Lv.max_group + 1) * sizeof(T));
   const size_t blk = group_block_bytes<T>(Lv.max_group);
   const int stage = blk <= kStageBudget;
-  k_apply_group_down<T><<<dim3(Lv.ngroup, rhs_grid(nrhs, Lv.ngroup)), kGroupThreads, base + (stage ? blk : 0), s>>>(
+  launch_pdl(k_apply_group_down<T>, dim3(Lv.ngroup, rhs_grid(nrhs, Lv.ngroup)), kGroupThreads, base + (stage ? blk : 0), s,
       Lv, Ph, x, ldx, nrhs, stage);
 }
 

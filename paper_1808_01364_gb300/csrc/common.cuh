@@ -56,6 +56,15 @@ __device__ inline void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint
       : "memory");
 }
 
+// Programmatic dependent launch (the sweeps of one F^{-1} application): a
+// kernel lets the next one start as soon as all of its CTAs run
+// (pdl_trigger), and the next one stages its factor blocks, which no sweep
+// writes, before it waits for the previous kernel's completion and memory
+// (pdl_wait) and only then reads the vectors.  Both are no-ops for a launch
+// without the programmatic-serialization attribute.
+__device__ inline void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ inline void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ inline bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(

@@ -260,8 +260,22 @@ struct PhaseStore {
   std::vector<int> h_rank, h_perm;
 };
 
-struct LevelStore {
+// The level-0 plan of a single problem depends on the grid, the leaf size
+// and the options only (the leaves and the level-0 separators are fixed by
+// the geometry, Sec. 3.1): the last one built is kept with a device copy of
+// its tables and shared, read-only, by later factorizations of the same kind.
+struct Plan0 {
   LevelPlan plan;
+  void* tables = nullptr;   // upload_level's layout of the plan's tables
+  ~Plan0() {
+    if (tables) cudaFree(tables);
+  }
+};
+
+struct LevelStore {
+  LevelPlan own;                       // this factorization's plan of the level
+  std::shared_ptr<const Plan0> p0;     // or the shared level-0 plan
+  const LevelPlan& plan() const { return p0 ? p0->plan : own; }
   LevelDev dev{};
   std::vector<PhaseStore> phases;
   void* tables = nullptr;
@@ -376,36 +390,69 @@ static int configure_once() {
 }
 
 // Upload the index tables of a level and fill the device views.
-static int upload_level(rhif_handle* H, LevelStore& S, size_t elem) {
-  const LevelPlan& P = S.plan;
-  Packer pk;
-  const size_t o_bucket = pk.add(P.bucket), o_code = pk.add(P.cell_code),
-               o_cstart = pk.add(P.cell_start), o_nI = pk.add(P.nI), o_nB = pk.add(P.nB),
-               o_goff = pk.add(P.gid_off), o_boff = pk.add(P.b_off), o_foff = pk.add(P.front_off),
-               o_froff = pk.add(P.frame_off), o_frld = pk.add(P.frame_ld),
-               o_bw = pk.add(P.band_w), o_boff2 = pk.add(P.band_off), o_zoff = pk.add(P.z_off),
-               o_soff = pk.add(P.seg_off), o_sg = pk.add(P.seg_group), o_sp = pk.add(P.seg_pos),
-               o_gt = pk.add(P.group_t), o_gs = pk.add(P.group_start), o_gsz = pk.add(P.group_size),
-               o_gco = pk.add(P.group_cell_off), o_gc = pk.add(P.group_cell),
-               o_gp = pk.add(P.group_pos), o_eao = pk.add(P.ea_off), o_eac = pk.add(P.ea_child),
-               o_eamo = pk.add(P.ea_map_off), o_eam = pk.add(P.ea_map),
-               o_cprob = pk.add(P.cell_prob);
+// Offsets of a plan's tables in one device buffer (upload_level's layout).
+struct TableLayout {
+  size_t bucket, code, cstart, nI, nB, goff, boff, foff, froff, frld, bw, boff2, zoff, soff, sg,
+      sp, gt, gs, gsz, gco, gc, gp, eao, eac, eamo, eam, cprob;
   struct PhOff {
     size_t pg, po, gp, ug, un, umo, uro, upo, gu;
   };
-  std::vector<PhOff> po(P.phases.size());
+  std::vector<PhOff> po;
+};
+
+static TableLayout table_layout(const LevelPlan& P, Packer& pk) {
+  TableLayout t;
+  t.bucket = pk.add(P.bucket);
+  t.code = pk.add(P.cell_code);
+  t.cstart = pk.add(P.cell_start);
+  t.nI = pk.add(P.nI);
+  t.nB = pk.add(P.nB);
+  t.goff = pk.add(P.gid_off);
+  t.boff = pk.add(P.b_off);
+  t.foff = pk.add(P.front_off);
+  t.froff = pk.add(P.frame_off);
+  t.frld = pk.add(P.frame_ld);
+  t.bw = pk.add(P.band_w);
+  t.boff2 = pk.add(P.band_off);
+  t.zoff = pk.add(P.z_off);
+  t.soff = pk.add(P.seg_off);
+  t.sg = pk.add(P.seg_group);
+  t.sp = pk.add(P.seg_pos);
+  t.gt = pk.add(P.group_t);
+  t.gs = pk.add(P.group_start);
+  t.gsz = pk.add(P.group_size);
+  t.gco = pk.add(P.group_cell_off);
+  t.gc = pk.add(P.group_cell);
+  t.gp = pk.add(P.group_pos);
+  t.eao = pk.add(P.ea_off);
+  t.eac = pk.add(P.ea_child);
+  t.eamo = pk.add(P.ea_map_off);
+  t.eam = pk.add(P.ea_map);
+  t.cprob = pk.add(P.cell_prob);
+  t.po.resize(P.phases.size());
   for (size_t i = 0; i < P.phases.size(); ++i) {
     const PhasePlan& ph = P.phases[i];
     const UnitTable& U = ph.units;
-    po[i] = {pk.add(ph.pre_group), pk.add(ph.pre_off), pk.add(ph.group_pre), pk.add(U.group),
-             pk.add(U.nrow), pk.add(U.m_off), pk.add(U.rec_off), pk.add(U.perm_off),
-             pk.add(ph.group_unit)};
+    t.po[i] = {pk.add(ph.pre_group), pk.add(ph.pre_off), pk.add(ph.group_pre), pk.add(U.group),
+               pk.add(U.nrow), pk.add(U.m_off), pk.add(U.rec_off), pk.add(U.perm_off),
+               pk.add(ph.group_unit)};
   }
+  return t;
+}
+
+static int upload_level(rhif_handle* H, LevelStore& S, size_t elem) {
+  const LevelPlan& P = S.plan();
+  Packer pk;
+  const TableLayout t = table_layout(P, pk);
   void* d = nullptr;
-  int rc = H->mem.get(&d, pk.total);
-  if (rc) return rc;
-  S.tables = d;
-  if ((rc = pk.upload(d, H->mem.s))) return rc;
+  int rc = RHIF_OK;
+  if (S.p0) {   // the shared level-0 tables, already on the device
+    d = S.p0->tables;
+  } else {
+    if ((rc = H->mem.get(&d, pk.total))) return rc;
+    S.tables = d;
+    if ((rc = pk.upload(d, H->mem.s))) return rc;
+  }
   char* b = (char*)d;
   LevelDev& L = S.dev;
   L.level = P.level;
@@ -418,34 +465,34 @@ static int upload_level(rhif_handle* H, LevelStore& S, size_t elem) {
   L.max_n = P.max_n;
   L.max_group = P.max_group;
   L.max_w = P.max_w;
-  L.bucket = (const int32_t*)(b + o_bucket);
-  L.cell_code = (const int64_t*)(b + o_code);
-  L.cell_start = (const int32_t*)(b + o_cstart);
-  L.nI = (const int*)(b + o_nI);
-  L.nB = (const int*)(b + o_nB);
-  L.gid_off = (const int64_t*)(b + o_goff);
-  L.b_off = (const int64_t*)(b + o_boff);
-  L.front_off = (const int64_t*)(b + o_foff);
-  L.frame_off = (const int64_t*)(b + o_froff);
-  L.frame_ld = (const int*)(b + o_frld);
-  L.band_w = (const int*)(b + o_bw);
-  L.band_off = (const int64_t*)(b + o_boff2);
-  L.z_off = (const int64_t*)(b + o_zoff);
-  L.seg_off = (const int*)(b + o_soff);
-  L.seg_group = (const int*)(b + o_sg);
-  L.seg_pos = (const int*)(b + o_sp);
-  L.group_t = (const int*)(b + o_gt);
-  L.group_start = (const int32_t*)(b + o_gs);
-  L.group_size = (const int*)(b + o_gsz);
-  L.group_cell_off = (const int*)(b + o_gco);
-  L.group_cell = (const int*)(b + o_gc);
-  L.group_pos = (const int*)(b + o_gp);
-  L.ea_off = (const int*)(b + o_eao);
-  L.ea_child = (const int*)(b + o_eac);
-  L.ea_map_off = (const int64_t*)(b + o_eamo);
-  L.ea_map = (const int*)(b + o_eam);
+  L.bucket = (const int32_t*)(b + t.bucket);
+  L.cell_code = (const int64_t*)(b + t.code);
+  L.cell_start = (const int32_t*)(b + t.cstart);
+  L.nI = (const int*)(b + t.nI);
+  L.nB = (const int*)(b + t.nB);
+  L.gid_off = (const int64_t*)(b + t.goff);
+  L.b_off = (const int64_t*)(b + t.boff);
+  L.front_off = (const int64_t*)(b + t.foff);
+  L.frame_off = (const int64_t*)(b + t.froff);
+  L.frame_ld = (const int*)(b + t.frld);
+  L.band_w = (const int*)(b + t.bw);
+  L.band_off = (const int64_t*)(b + t.boff2);
+  L.z_off = (const int64_t*)(b + t.zoff);
+  L.seg_off = (const int*)(b + t.soff);
+  L.seg_group = (const int*)(b + t.sg);
+  L.seg_pos = (const int*)(b + t.sp);
+  L.group_t = (const int*)(b + t.gt);
+  L.group_start = (const int32_t*)(b + t.gs);
+  L.group_size = (const int*)(b + t.gsz);
+  L.group_cell_off = (const int*)(b + t.gco);
+  L.group_cell = (const int*)(b + t.gc);
+  L.group_pos = (const int*)(b + t.gp);
+  L.ea_off = (const int*)(b + t.eao);
+  L.ea_child = (const int*)(b + t.eac);
+  L.ea_map_off = (const int64_t*)(b + t.eamo);
+  L.ea_map = (const int*)(b + t.eam);
   L.status = H->status;
-  L.cell_prob = P.cell_prob.empty() ? nullptr : (const int*)(b + o_cprob);
+  L.cell_prob = P.cell_prob.empty() ? nullptr : (const int*)(b + t.cprob);
   L.bgeo = P.cell_prob.empty() ? nullptr : H->bgeo;
   if ((rc = H->mem.get((void**)&L.gids, P.gid_off.back() * sizeof(int32_t)))) return rc;
   if (P.level == 0) {
@@ -467,17 +514,17 @@ static int upload_level(rhif_handle* H, LevelStore& S, size_t elem) {
     D.pre_min_type = ph.pre_min_type;
     D.npre = (int)ph.pre_group.size();
     D.diag_only = H->precond_diag ? 1 : 0;
-    D.pre_group = (const int*)(b + po[i].pg);
-    D.pre_off = (const int64_t*)(b + po[i].po);
-    D.group_pre = (const int*)(b + po[i].gp);
+    D.pre_group = (const int*)(b + t.po[i].pg);
+    D.pre_off = (const int64_t*)(b + t.po[i].po);
+    D.group_pre = (const int*)(b + t.po[i].gp);
     D.nunit = (int)U.group.size();
     D.max_n = U.max_n;
-    D.u_group = (const int*)(b + po[i].ug);
-    D.u_nrow = (const int*)(b + po[i].un);
-    D.u_m_off = (const int64_t*)(b + po[i].umo);
-    D.u_rec_off = (const int64_t*)(b + po[i].uro);
-    D.u_perm_off = (const int64_t*)(b + po[i].upo);
-    D.group_unit = (const int*)(b + po[i].gu);
+    D.u_group = (const int*)(b + t.po[i].ug);
+    D.u_nrow = (const int*)(b + t.po[i].un);
+    D.u_m_off = (const int64_t*)(b + t.po[i].umo);
+    D.u_rec_off = (const int64_t*)(b + t.po[i].uro);
+    D.u_perm_off = (const int64_t*)(b + t.po[i].upo);
+    D.group_unit = (const int*)(b + t.po[i].gu);
     if ((rc = H->mem.get(&D.Lbuf, ph.pre_total * elem))) return rc;
     if ((rc = H->mem.get(&D.rec, U.rec_total * elem))) return rc;
     if ((rc = H->mem.get((void**)&D.perm, U.perm_total * sizeof(int)))) return rc;
@@ -604,7 +651,7 @@ static int skeletonize(rhif_handle* H, const LevelPlan& P, const PhasePlan& ph, 
 static LevelPlan plan_level(rhif_handle* H, int lvl, const std::vector<uint8_t>& keep,
                             std::vector<LevelPlan>& pprev) {
   if (H->pG.empty())
-    return build_level(H->G, lvl, keep, lvl ? &H->levels[lvl - 1].plan : nullptr, H->precondition,
+    return build_level(H->G, lvl, keep, lvl ? &H->levels[lvl - 1].plan() : nullptr, H->precondition,
                        H->edge_skel);
   const int np = (int)H->pG.size();
   std::vector<LevelPlan> cur(np);
@@ -653,6 +700,52 @@ static LevelPlan plan_level(rhif_handle* H, int lvl, const std::vector<uint8_t>&
   H->part_prob[lvl] = prob;
   pprev.swap(cur);
   return M;
+}
+
+// Level-0 plan of a single problem: the shared one when the last one built
+// matches (device, grid, leaf size, local preconditioner, edge
+// skeletonization), else a new one, uploaded once (synchronously, so that
+// other streams may use it) and published for later factorizations.
+struct Plan0Key {
+  int device, d, ns[3], leaf, precondition, edge;
+  bool operator==(const Plan0Key& o) const {
+    return device == o.device && d == o.d && ns[0] == o.ns[0] && ns[1] == o.ns[1] &&
+           ns[2] == o.ns[2] && leaf == o.leaf && precondition == o.precondition && edge == o.edge;
+  }
+};
+static std::mutex g_p0_mu;
+static Plan0Key g_p0_key{};
+static std::shared_ptr<const Plan0>* g_p0 = new std::shared_ptr<const Plan0>();   // never destroyed
+
+static int plan0_get(rhif_handle* H, LevelStore& S) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  const Geometry& G = H->G;
+  const Plan0Key key{dev, G.d, {G.ns[0], G.ns[1], G.ns[2]}, G.leaf,
+                     H->precondition, H->edge_skel ? 1 : 0};
+  {
+    std::lock_guard<std::mutex> lk(g_p0_mu);
+    if (*g_p0 && g_p0_key == key) {
+      S.p0 = *g_p0;
+      return RHIF_OK;
+    }
+  }
+  auto e = std::make_shared<Plan0>();
+  static const std::vector<uint8_t> none;
+  e->plan = build_level(G, 0, none, nullptr, H->precondition, H->edge_skel);
+  Packer pk;
+  table_layout(e->plan, pk);
+  CK(cudaMalloc(&e->tables, std::max<size_t>(pk.total, 16)));
+  int rc = pk.upload(e->tables, H->mem.s);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(H->mem.s));
+  {
+    std::lock_guard<std::mutex> lk(g_p0_mu);
+    *g_p0 = e;
+    g_p0_key = key;
+  }
+  S.p0 = e;
+  return RHIF_OK;
 }
 
 template <typename T>
@@ -709,7 +802,11 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
   std::vector<LevelPlan> pprev;   // merged batch: the problems' own plans of the last level
   {
     auto t0 = clk::now();
-    H->levels[0].plan = plan_level(H, 0, keep, pprev);
+    if (H->pG.empty()) {
+      if ((rc = plan0_get(H, H->levels[0]))) return rc;
+    } else {
+      H->levels[0].own = plan_level(H, 0, keep, pprev);
+    }
     t_plan = ms_since(t0);
     auto t1 = clk::now();
     if ((rc = upload_level(H, H->levels[0], elem))) return rc;
@@ -722,15 +819,15 @@ static int factor_impl(rhif_handle* H, const rhif_csr* A) {
     LevelStore& S = H->levels[lvl];
     if (lvl) {
       auto t0 = clk::now();
-      S.plan = plan_level(H, lvl, keep, pprev);
+      S.own = plan_level(H, lvl, keep, pprev);
       t_plan = ms_since(t0);
       auto t1 = clk::now();
       if ((rc = upload_level(H, S, elem))) return rc;
       t_up = ms_since(t1);
     }
-    keep.assign(S.plan.bucket.size(), 1);
+    keep.assign(S.plan().bucket.size(), 1);
     auto t2 = clk::now();
-    const LevelPlan& P = S.plan;
+    const LevelPlan& P = S.plan();
     H->ub_len = std::max<int64_t>(H->ub_len, P.b_off.back());
     {
       Launch t(kCatExpandGids, s, 0.0, 8.0 * P.gid_off.back());
@@ -2240,10 +2337,10 @@ int rhif_stats(const rhif_handle* F, rhif_stats_t* st) {
   std::memset(st, 0, sizeof(*st));
   st->levels = F->G.L;
   st->n = F->G.N;
-  st->root_size = F->levels.empty() ? 0 : F->levels.back().plan.nI.empty() ? 0 : F->levels.back().plan.nI[0];
+  st->root_size = F->levels.empty() ? 0 : F->levels.back().plan().nI.empty() ? 0 : F->levels.back().plan().nI[0];
   for (int l = 0; l < F->G.L && l < 16; ++l) {
     // active DOFs after level l = DOFs present at level l+1
-    st->active[l] = (int64_t)F->levels[l + 1].plan.bucket.size();
+    st->active[l] = (int64_t)F->levels[l + 1].plan().bucket.size();
   }
   st->factor_bytes = (int64_t)F->mem.bytes;
   st->flops = F->flops;
@@ -2254,9 +2351,9 @@ int rhif_stats(const rhif_handle* F, rhif_stats_t* st) {
   for (int l = 0; l < F->G.L && l < 16; ++l) {
     const LevelStore& S = F->levels[l];
     for (size_t p = 0; p < S.phases.size(); ++p) {
-      const PhasePlan& ph = S.plan.phases[p];
+      const PhasePlan& ph = S.plan().phases[p];
       for (size_t u = 0; u < S.phases[p].h_rank.size(); ++u) {
-        st->unit_dofs[l] += S.plan.group_size[ph.units.group[u]];
+        st->unit_dofs[l] += S.plan().group_size[ph.units.group[u]];
         st->skeletons[l] += S.phases[p].h_rank[u];
       }
     }
@@ -2280,21 +2377,21 @@ int rhif_skeletons(const rhif_handle* F, int level, int phase, int* count, int* 
   if (level < 0 || level >= F->G.L) return fail(RHIF_ERR_BAD_ARG, "level out of range");
   const LevelStore& S = F->levels[level];
   if (phase < 0 || phase >= (int)S.phases.size()) return fail(RHIF_ERR_BAD_ARG, "phase out of range");
-  const PhasePlan& ph = S.plan.phases[phase];
+  const PhasePlan& ph = S.plan().phases[phase];
   const PhaseStore& PS = S.phases[phase];
   const int nu = (int)ph.units.group.size();
   *count = nu;
   int64_t pos = 0;
   for (int u = 0; u < nu; ++u) {
     const int gi = ph.units.group[u];
-    const int64_t g0 = S.plan.group_start[gi];
-    const int n = S.plan.group_size[gi];
+    const int64_t g0 = S.plan().group_start[gi];
+    const int n = S.plan().group_size[gi];
     if (sizes) sizes[u] = n;
     if (ranks) ranks[u] = PS.h_rank[u];
     if (gids) {
       if (pos + n > capacity) return fail(RHIF_ERR_BAD_ARG, "gids capacity too small");
       const int* pm = PS.h_perm.data() + ph.units.perm_off[u];
-      for (int i = 0; i < n; ++i) gids[pos + i] = S.plan.bucket[g0 + pm[i]];
+      for (int i = 0; i < n; ++i) gids[pos + i] = S.plan().bucket[g0 + pm[i]];
     }
     pos += n;
   }
@@ -2309,8 +2406,9 @@ void rhif_free(rhif_handle* F) {
   if (F->pcg_graph) cudaGraphExecDestroy(F->pcg_graph);
   if (F->capture_stream) cudaStreamDestroy(F->capture_stream);
   for (auto& S : F->levels) {
-    if (S.plan.cell_prob.empty()) recycle_plan(std::move(S.plan));
-    else recycle_merged_plan(std::move(S.plan));
+    if (S.p0) continue;   // the shared level-0 plan stays with its other holders
+    if (S.own.cell_prob.empty()) recycle_plan(std::move(S.own));
+    else recycle_merged_plan(std::move(S.own));
   }
   delete F;
 }

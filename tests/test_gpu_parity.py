@@ -259,3 +259,37 @@ def test_many_rhs_apply_matches_one_rhs_apply(gpu_lib, precision, ns, leaf):
         y1 = Fg.apply(X[r].contiguous()).cpu().numpy()
         assert np.linalg.norm(Y[r] - y1) <= tol * np.linalg.norm(y1)
     Fg.free()
+
+
+def test_shared_level0_plan_gives_the_factor_of_a_fresh_plan(gpu_lib):
+    """The level-0 plan (fixed by the grid, the leaf size and the options) is
+    kept and shared by later factorizations of the same kind: factors made
+    after other grids and other options evicted it, and factors made while it
+    is shared, apply exactly as the first one did."""
+    ns_a, ns_b = (31, 33), (47, 47)
+    x = _dev(np.random.default_rng(11).standard_normal(ns_a[0] * ns_a[1]))
+
+    def apply_a(**kw):
+        a = W.log_uniform_pixels(ns_a, 1e-3, 1e3, seed=3)
+        Fa = gpu_lib.rhif_factor(gpu_lib.rhif_assemble_fd(ns_a, _dev(a), 0.0), ns_a, 4, 1e-3,
+                                 precision="fp64", **kw)
+        y = Fa.apply(x).cpu().numpy()
+        return Fa, y
+
+    F1, y1 = apply_a()                      # builds the shared plan
+    F2, y2 = apply_a()                      # shares it while F1 holds it too
+    np.testing.assert_array_equal(y1, y2)
+    F1.free()
+    b = W.log_uniform_pixels(ns_b, 1e-3, 1e3, seed=4)
+    Fb = gpu_lib.rhif_factor(gpu_lib.rhif_assemble_fd(ns_b, _dev(b), 0.0), ns_b, 4, 1e-3,
+                             precision="fp64")   # another grid: a new plan replaces it
+    F3, y3 = apply_a()                      # rebuilt for the first grid
+    np.testing.assert_array_equal(y1, y3)
+    F4, y4 = apply_a(precondition="diag")   # other options: another plan
+    F5, y5 = apply_a()
+    np.testing.assert_array_equal(y1, y5)
+    assert not np.array_equal(y1, y4)
+    y2b = F2.apply(x).cpu().numpy()         # the handle that shared the first plan still works
+    np.testing.assert_array_equal(y1, y2b)
+    for F in (F2, Fb, F3, F4, F5):
+        F.free()

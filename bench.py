@@ -334,6 +334,14 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def hbm_bound(kernel: str) -> bool:
+    """Kernel categories bounded by memory traffic (the F^-1 sweeps, SpMV,
+    vector updates, assembly, extend-add); the others count flops."""
+    return kernel.startswith("apply") or kernel in (
+        "spmv", "pcg_vector", "extend_add", "expand_gids", "assemble_fd", "stencil_from_csr",
+        "band_inverse")
+
+
 def alu_peak_nominal(precision: str, torch=None, sm_max_mhz=None):
     """Plain-ALU peak from the unit counts and clock (TFLOP/s): FP32 = SMs (read
     from the device) x 128 FMA lanes x 2 flops x the maximum SM clock (sampled
@@ -725,7 +733,7 @@ def gpu_arm(args):
     hbm, hbm_kind = measured_peaks()
     name, st = max(ks.items(), key=lambda kv: kv[1]["total_ms"])
     per_launch_ms = st["total_ms"] / max(st["launches"], 1)
-    if name.startswith("apply") or name in ("spmv", "pcg_vector", "extend_add", "expand_gids"):
+    if hbm_bound(name):
         achieved = st["bytes"] / max(st["launches"], 1) / (per_launch_ms / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "peak_kind": hbm_kind}
@@ -736,6 +744,27 @@ def gpu_arm(args):
                 "peak_kind": kind}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["kernel"] = name
+    # every kernel category against its roofline: counted work over its
+    # CUDA-event time in the instrumented steps
+    alu_pk, _ = alu_peak_nominal(wl.headline, torch, (clk or {}).get("sm_max_mhz"))
+    gemm_pk = peaks.get(wl.headline, peaks.get("fp32"))
+    by_kernel = {}
+    for k, v in sorted(ks.items(), key=lambda kv: -kv[1]["total_ms"]):
+        if not v["launches"] or v["total_ms"] <= 0:
+            continue
+        t = v["total_ms"] / 1e3
+        row = {"ms_per_step": round(v["total_ms"] / args.steps, 4),
+               "launches_per_step": round(v["launches"] / args.steps, 2)}
+        if hbm_bound(k) and v["bytes"] > 0:
+            a = v["bytes"] / t / 1e9
+            row.update(bound="hbm", achieved=round(a, 2), unit="GB/s", frac=round(a / hbm, 5))
+        elif v["flops"] > 0:
+            a = v["flops"] / t / 1e12
+            row.update(bound="alu", achieved=round(a, 5), unit="TFLOP/s", frac=round(a / alu_pk, 6),
+                       frac_of_gemm=round(a / gemm_pk, 6))
+        else:
+            row.update(bound="latency", note="no counted work (condition estimate, FP64 re-elimination)")
+        by_kernel[k] = row
     roof["launch_ms"] = per_launch_ms
     roof["traffic"] = profile_traffic(name, wl.headline, args.workload)
 
@@ -751,6 +780,7 @@ def gpu_arm(args):
         other: {"value": value_o, "ms_per_step": 1e3 * sec_o / args.fp64_steps,
                 "pcg_iters": its_o[0], "relres": rr_o[0], "rel_diff_vs_headline": du},
         "roofline": roof,
+        "roofline_by_kernel": by_kernel,
         "alu_peaks_tflops": peaks,
         "kernels": {k: {"launches": v["launches"], "ms": round(v["total_ms"], 3)}
                     for k, v in ks.items() if v["launches"]},

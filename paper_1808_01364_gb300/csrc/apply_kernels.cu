@@ -1464,30 +1464,6 @@ static inline unsigned rhs_grid(int nrhs, int64_t gridx) {
   return (unsigned)std::min<int64_t>(gy, 65535);
 }
 
-// Launches a kernel of an F^{-1} sweep.  Small grids (at most kPdlMaxCtas
-// CTAs: the upper levels, whose kernels are latency-bound) get programmatic
-// stream serialization: the kernel may begin while the previous one on the
-// stream finishes (its factor blocks staged early, pdl_wait before the
-// vectors).  Large grids are launched in plain stream order: there the
-// waiting CTAs and their early staging slowed the running kernel down.
-constexpr int64_t kPdlMaxCtas = 8 * 152;
-
-template <typename... KArgs, typename... Args>
-static void launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
-                       Args... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = block;
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = (int64_t)grid.x * grid.y * grid.z <= kPdlMaxCtas ? 1 : 0;
-  cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
-}
-
 template <typename T>
 void launch_apply_cell_up(const LevelDev& Lv, double* x, int64_t ldx, int nrhs, double* ubuf,
                           int64_t ldu, cudaStream_t s) {

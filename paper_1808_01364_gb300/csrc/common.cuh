@@ -65,6 +65,32 @@ __device__ inline void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint
 __device__ inline void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ inline void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+// Launches a kernel of the factorization or of an F^{-1} sweep.  Small grids
+// (at most kPdlMaxCtas CTAs: the upper levels, whose kernels are
+// latency-bound) get programmatic stream serialization: the kernel may begin
+// while the previous one on the stream finishes, and waits for it with
+// pdl_wait before it reads what that kernel wrote (factorization kernels:
+// first thing; sweeps: after staging their factor blocks).  Large grids are
+// launched in plain stream order: there the waiting CTAs and their early
+// staging slowed the running kernel down.
+constexpr int64_t kPdlMaxCtas = 8 * 152;
+
+template <typename... KArgs, typename... Args>
+static void launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = (int64_t)grid.x * grid.y * grid.z <= kPdlMaxCtas ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
+}
+
 __device__ inline bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(

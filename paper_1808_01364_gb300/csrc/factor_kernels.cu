@@ -24,6 +24,8 @@ namespace rhif {
 __global__ void k_stencil_from_csr(GeoDev G, const int64_t* rowptr, const int32_t* col,
                                    const double* val, int64_t nnz, double* diag, double* off,
                                    double* offb, int* status) {
+  pdl_trigger();
+  pdl_wait();   // what the previous kernel of the stream wrote
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= G.N) return;
   const int64_t b = rowptr[i], e = rowptr[i + 1];
@@ -62,6 +64,8 @@ __global__ void k_stencil_from_csr(GeoDev G, const int64_t* rowptr, const int32_
 }
 
 __global__ void k_stencil_check(int64_t n, const double* off, const double* offb, int* status) {
+  pdl_trigger();
+  pdl_wait();   // what the previous kernel of the stream wrote
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n && off[i] != offb[i]) report(status, RHIF_ERR_BAD_ARG, -1, kKindArg, (int)(i % 2147483647));
 }
@@ -71,6 +75,8 @@ __global__ void k_stencil_check(int64_t n, const double* off, const double* offb
 // ---------------------------------------------------------------------------
 
 __global__ void k_expand_gids(LevelDev Lv) {
+  pdl_trigger();
+  pdl_wait();   // what the previous kernel of the stream wrote
   const int c = blockIdx.x;
   const int nI = Lv.nI[c];
   int32_t* out = Lv.gids + Lv.gid_off[c];
@@ -159,6 +165,8 @@ size_t leaf_smem_bytes(int max_nI, int max_nB, int max_w, int leaf, int d) {
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_leaf_elim(GeoDev G, LevelDev Lv, const double* diag, const double* off, int* status) {
+  pdl_trigger();
+  pdl_wait();   // what the previous kernel of the stream wrote
   extern __shared__ unsigned char smraw[];
   __shared__ int bad;
   const int c = blockIdx.x;
@@ -326,6 +334,8 @@ size_t leaf_stream_smem(int max_nI, int max_w, int leaf, int d) {
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_leaf_stream(GeoDev G, LevelDev Lv, const double* diag, const double* off, int* status) {
+  pdl_trigger();
+  pdl_wait();   // what the previous kernel of the stream wrote
   extern __shared__ unsigned char smraw[];
   __shared__ int bad;
   __shared__ T s_piv, s_rpiv;
@@ -543,6 +553,8 @@ __host__ __device__ inline size_t leaf_warp_bytes(int max_nI, int leaf, int nbt)
 template <typename T, int NBT>
 __global__ void __launch_bounds__(32 * kLeafWarpCta)
 k_leaf_warp(GeoDev G, LevelDev Lv, const double* diag, const double* off, int* status) {
+  pdl_trigger();
+  pdl_wait();   // what the previous kernel of the stream wrote
   constexpr int CPL = NBT / 32;   // boundary columns per lane
   extern __shared__ __align__(16) unsigned char smraw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -751,6 +763,8 @@ k_leaf_warp(GeoDev G, LevelDev Lv, const double* diag, const double* off, int* s
 // the children of a parent is taken in slot order, as a fixed-order gather.
 template <typename T>
 __global__ void k_extend_add(LevelDev cur, LevelDev prev, int slot, int chunk) {
+  pdl_trigger();
+  pdl_wait();   // what the previous kernel of the stream wrote
   const int c = blockIdx.y;
   const int k = cur.ea_off[c] + slot;
   if (k >= cur.ea_off[c + 1]) return;
@@ -781,6 +795,8 @@ constexpr int kEaCellThreads = 512;
 
 template <typename T>
 __global__ void __launch_bounds__(kEaCellThreads) k_extend_add_cell(LevelDev cur, LevelDev prev) {
+  pdl_trigger();
+  pdl_wait();   // what the previous kernel of the stream wrote
   const int c = blockIdx.x;
   const int n = cur.nI[c] + cur.nB[c];
   T* F = (T*)cur.front + cur.front_off[c];
@@ -810,6 +826,8 @@ __global__ void __launch_bounds__(kEaCellThreads) k_extend_add_cell(LevelDev cur
 // forward substitution, X[r,c] = -(1/L_rr) sum_{k=c}^{r-1} L[r,k] X[k,c].
 template <typename T>
 __global__ void k_band_block_inverse(LevelDev Lv) {
+  pdl_trigger();
+  pdl_wait();   // what the previous kernel of the stream wrote
   const int lane = threadIdx.x & 31;
   const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (c >= Lv.ncell) return;
@@ -841,6 +859,8 @@ __global__ void k_band_block_inverse(LevelDev Lv) {
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_partial_chol(LevelDev Lv, int* status) {
+  pdl_trigger();
+  pdl_wait();   // what the previous kernel of the stream wrote
   extern __shared__ unsigned char smraw[];
   T* sm = (T*)smraw;
   const int c = blockIdx.x;
@@ -863,6 +883,8 @@ __global__ void __launch_bounds__(kThreads) k_partial_chol(LevelDev Lv, int* sta
 // the factored block staged in shared memory).
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_front_pdiag(LevelDev Lv, int p0, int* status) {
+  pdl_trigger();
+  pdl_wait();   // what the previous kernel of the stream wrote
   extern __shared__ unsigned char smraw[];
   const int c = blockIdx.x;
   const int nI = Lv.nI[c], n = nI + Lv.nB[c];
@@ -875,6 +897,8 @@ __global__ void __launch_bounds__(kThreads) k_front_pdiag(LevelDev Lv, int p0, i
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_front_prows(LevelDev Lv, int p0) {
+  pdl_trigger();
+  pdl_wait();   // what the previous kernel of the stream wrote
   extern __shared__ unsigned char smraw[];
   T* D = (T*)smraw;
   const int c = blockIdx.y;
@@ -901,6 +925,8 @@ __host__ __device__ inline int64_t trail_tiles(int nI, int n, int p0) {
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_front_trailing(LevelDev Lv, int p0) {
+  pdl_trigger();
+  pdl_wait();   // what the previous kernel of the stream wrote
   extern __shared__ unsigned char smraw[];
   int64_t bid = blockIdx.x;
   int c = 0;
@@ -927,6 +953,8 @@ __host__ __device__ inline int64_t schur_tiles(int nI, int nB) {
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_front_schur(LevelDev Lv) {
+  pdl_trigger();
+  pdl_wait();   // what the previous kernel of the stream wrote
   extern __shared__ unsigned char smraw[];
   int64_t bid = blockIdx.x;
   int c = 0;
@@ -953,6 +981,8 @@ __global__ void __launch_bounds__(kThreads) k_front_schur(LevelDev Lv) {
 // lower triangle of L with X.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_front_trinv(LevelDev Lv, T* X, const int64_t* xoff) {
+  pdl_trigger();
+  pdl_wait();   // what the previous kernel of the stream wrote
   extern __shared__ unsigned char smraw[];
   const int c = blockIdx.y;
   const int nI = Lv.nI[c], n = nI + Lv.nB[c];
@@ -965,6 +995,8 @@ __global__ void __launch_bounds__(kThreads) k_front_trinv(LevelDev Lv, T* X, con
 // block), into Ph.Linv (same layout as Lbuf, upper triangle zero).
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_group_trinv(LevelDev Lv, PhaseDev Ph) {
+  pdl_trigger();
+  pdl_wait();   // what the previous kernel of the stream wrote
   extern __shared__ unsigned char smraw[];
   const int b = blockIdx.y;
   const int sz = Lv.group_size[Ph.pre_group[b]];
@@ -983,6 +1015,8 @@ __global__ void __launch_bounds__(kThreads) k_group_trinv(LevelDev Lv, PhaseDev 
 // like the records.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_unit_trinv(LevelDev Lv, PhaseDev Ph, T* X) {
+  pdl_trigger();
+  pdl_wait();   // what the previous kernel of the stream wrote
   extern __shared__ unsigned char smraw[];
   const int u = blockIdx.y;
   const int n = Lv.group_size[Ph.u_group[u]];
@@ -996,6 +1030,8 @@ __global__ void __launch_bounds__(kThreads) k_unit_trinv(LevelDev Lv, PhaseDev P
 // Lower triangle of every unit's L_rr^{-1} from X back into its record.
 template <typename T>
 __global__ void k_unit_inv_store(LevelDev Lv, PhaseDev Ph, const T* X) {
+  pdl_trigger();
+  pdl_wait();   // what the previous kernel of the stream wrote
   const int u = blockIdx.y;
   const int n = Lv.group_size[Ph.u_group[u]];
   const int r = n - Ph.rank[u];
@@ -1017,6 +1053,8 @@ constexpr int trinv_warps() { return sizeof(T) == 4 ? 4 : 2; }   // 33.8 KB of s
 
 template <typename T, bool UNIT>
 __global__ void __launch_bounds__(32 * trinv_warps<T>()) k_trinv_warp(LevelDev Lv, PhaseDev Ph, int count) {
+  pdl_trigger();
+  pdl_wait();   // what the previous kernel of the stream wrote
   constexpr int W = trinv_warps<T>();
   __shared__ T Ls[W][32][33];
   __shared__ T Xs[W][32][33];
@@ -1063,6 +1101,8 @@ __global__ void __launch_bounds__(32 * trinv_warps<T>()) k_trinv_warp(LevelDev L
 
 template <typename T>
 __global__ void k_front_inv_store(LevelDev Lv, const T* X, const int64_t* xoff) {
+  pdl_trigger();
+  pdl_wait();   // what the previous kernel of the stream wrote
   const int c = blockIdx.y;
   const int nI = Lv.nI[c], n = nI + Lv.nB[c];
   T* F = (T*)Lv.front + Lv.front_off[c];
@@ -1084,6 +1124,8 @@ __global__ void k_front_inv_store(LevelDev Lv, const T* X, const int64_t* xoff) 
 // L_g = diag(A_gg)^{1/2} and every later step sees a diagonal L_g.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_precond_diag(LevelDev Lv, PhaseDev Ph, int* status) {
+  pdl_trigger();
+  pdl_wait();   // what the previous kernel of the stream wrote
   extern __shared__ unsigned char smraw[];
   T* sm = (T*)smraw;
   const int b = blockIdx.x;
@@ -1117,6 +1159,8 @@ constexpr int pdiag_warps() { return sizeof(T) == 4 ? 4 : 2; }   // 33.8 KB of s
 template <typename T>
 __global__ void __launch_bounds__(32 * pdiag_warps<T>())
 k_precond_diag_warp(LevelDev Lv, PhaseDev Ph, int* status) {
+  pdl_trigger();
+  pdl_wait();   // what the previous kernel of the stream wrote
   constexpr int W = pdiag_warps<T>();
   __shared__ T Ls[W][32][33];
   __shared__ T Xs[W][32][33];
@@ -1185,6 +1229,8 @@ k_precond_diag_warp(LevelDev Lv, PhaseDev Ph, int* status) {
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_precond_scale(LevelDev Lv, PhaseDev Ph, int stage, int xstage) {
+  pdl_trigger();
+  pdl_wait();   // what the previous kernel of the stream wrote
   extern __shared__ unsigned char smraw[];
   const int c = blockIdx.x;
   int gld;
@@ -1303,6 +1349,8 @@ k_precond_scale(LevelDev Lv, PhaseDev Ph, int stage, int xstage) {
 
 template <typename T>
 __global__ void k_frame_symmetrize(LevelDev Lv) {
+  pdl_trigger();
+  pdl_wait();   // what the previous kernel of the stream wrote
   for (int c = blockIdx.y; c < Lv.ncell; c += gridDim.y) {
     int ld;
     T* Fr = frame_of<T>(Lv, c, &ld);
@@ -1336,6 +1384,8 @@ __device__ inline void scale_task_of(const PhaseDev& Ph, int64_t bid, int* cell,
 // is in place (a row tile depends only on the rows above and at it).
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_frame_rows_tp(LevelDev Lv, PhaseDev Ph) {
+  pdl_trigger();
+  pdl_wait();   // what the previous kernel of the stream wrote
   extern __shared__ unsigned char smraw[];
   T* sm = (T*)smraw;
   int c, q, blk;
@@ -1366,6 +1416,8 @@ __global__ void __launch_bounds__(kThreads) k_frame_rows_tp(LevelDev Lv, PhaseDe
 // tiles right to left so the update is in place.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_frame_cols_tp(LevelDev Lv, PhaseDev Ph) {
+  pdl_trigger();
+  pdl_wait();   // what the previous kernel of the stream wrote
   extern __shared__ unsigned char smraw[];
   T* sm = (T*)smraw;
   int c, q, blk;
@@ -1659,6 +1711,8 @@ __device__ void skel_finish(const LevelDev& Lv, const PhaseDev& Ph, int u, int g
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_skel(LevelDev Lv, PhaseDev Ph, uint8_t* alive,
                                                    double tol, int* status, int mstage) {
+  pdl_trigger();
+  pdl_wait();   // what the previous kernel of the stream wrote
   extern __shared__ unsigned char smraw[];
   T* sm = (T*)smraw;                                   // partial-Cholesky / tile workspace
   T* nrm = sm + partial_chol_smem_elems();             // [max_n]
@@ -1759,6 +1813,8 @@ __host__ __device__ inline size_t skel_warp_bytes(int max_n, int64_t max_m, size
 template <typename T>
 __global__ void __launch_bounds__(256) k_skel_warp(LevelDev Lv, PhaseDev Ph, uint8_t* alive,
                                                    double tol, int* status, int per_warp) {
+  pdl_trigger();
+  pdl_wait();   // what the previous kernel of the stream wrote
   extern __shared__ __align__(16) unsigned char smraw[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int u = blockIdx.x * (blockDim.x >> 5) + wid;
@@ -1958,6 +2014,8 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads) k_skel_cluster(LevelDev Lv, PhaseDev Ph, uint8_t* alive,
                                                            double tol, int* status,
                                                            int64_t slice_cap) {
+  pdl_trigger();
+  pdl_wait();   // what the previous kernel of the stream wrote
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks(), cr = (int)cl.block_rank();
@@ -2140,6 +2198,8 @@ template <typename T>
 __global__ void __launch_bounds__(128) k_leaf_cond(GeoDev G, LevelDev Lv, const double* diag,
                                                    const double* off, double thresh, int* list,
                                                    int* count, int per_warp) {
+  pdl_trigger();
+  pdl_wait();   // what the previous kernel of the stream wrote
   extern __shared__ __align__(16) unsigned char smraw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c = blockIdx.x * (blockDim.x >> 5) + warp;
@@ -2208,7 +2268,7 @@ void launch_leaf_cond(const GeoDev& G, const LevelDev& Lv, const double* diag, c
                       double thresh, int* list, int* count, cudaStream_t s) {
   if (!Lv.ncell) return;
   const int per = (int)(((size_t)(Lv.max_w + 4) * Lv.max_nI * sizeof(float) + 15) & ~size_t(15));
-  k_leaf_cond<float><<<(Lv.ncell + 3) / 4, 128, 4 * per, s>>>(G, Lv, diag, off, thresh, list,
+  launch_pdl(k_leaf_cond<float>, (Lv.ncell + 3) / 4, 128, 4 * per, s, G, Lv, diag, off, thresh, list,
                                                              count, per);
 }
 
@@ -2231,6 +2291,8 @@ constexpr int kRedoTiles = 10;   // lower tiles of the 64 x 64 block
 __global__ void __launch_bounds__(kThreads)
 k_leaf_redo64(GeoDev G, LevelDev Lv, const double* diag, const double* off, int* status,
               const int* list, const int* count) {
+  pdl_trigger();
+  pdl_wait();   // what the previous kernel of the stream wrote
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ int bad;
   __shared__ double s_piv, s_rpiv;
@@ -2438,12 +2500,14 @@ void launch_leaf_fp64_redo(const GeoDev& G, const LevelDev& Lv, const double* di
   if (!Lv.ncell || Lv.max_nB > kStreamNB || Lv.max_w >= 32) return;
   const size_t sm = leaf_redo_smem(Lv.max_nI, Lv.max_w, G.leaf, G.d);
   const unsigned gx = (unsigned)std::min(Lv.ncell, 64);
-  k_leaf_redo64<<<dim3(gx, kRedoTiles), kThreads, sm, s>>>(G, Lv, diag, off, status, list, count);
+  launch_pdl(k_leaf_redo64, dim3(gx, kRedoTiles), kThreads, sm, s, G, Lv, diag, off, status, list, count);
 }
 
 // Redundant DOFs leave the active set only after every ID of the phase has
 // been taken (the IDs all read the same matrix, Sec. 2.2 parallel order).
 __global__ void k_mark_dead(LevelDev Lv, PhaseDev Ph, uint8_t* alive) {
+  pdl_trigger();
+  pdl_wait();   // what the previous kernel of the stream wrote
   const int u = blockIdx.x;
   const int g = Ph.u_group[u];
   const int n = Lv.group_size[g], k = Ph.rank[u];
@@ -2462,13 +2526,13 @@ void launch_stencil_from_csr(const GeoDev& G, const int64_t* rowptr, const int32
                              const double* val, int64_t nnz, double* diag, double* off,
                              double* offb, int* status, cudaStream_t s) {
   if (G.N == 0) return;
-  k_stencil_from_csr<<<blocks_for(G.N, 256), 256, 0, s>>>(G, rowptr, col, val, nnz, diag, off,
+  launch_pdl(k_stencil_from_csr, blocks_for(G.N, 256), 256, 0, s, G, rowptr, col, val, nnz, diag, off,
                                                            offb, status);
-  k_stencil_check<<<blocks_for(G.d * G.N, 256), 256, 0, s>>>(G.d * G.N, off, offb, status);
+  launch_pdl(k_stencil_check, blocks_for(G.d * G.N, 256), 256, 0, s, G.d * G.N, off, offb, status);
 }
 
 void launch_expand_gids(const LevelDev& Lv, cudaStream_t s) {
-  if (Lv.ncell) k_expand_gids<<<Lv.ncell, 128, 0, s>>>(Lv);
+  if (Lv.ncell) launch_pdl(k_expand_gids, Lv.ncell, 128, 0, s, Lv);
 }
 
 template <typename T>
@@ -2490,25 +2554,25 @@ void launch_leaf_elim(const GeoDev& G, const LevelDev& Lv, const double* diag, c
   if (!Lv.ncell) return;
   if (leaf_warp_fits<T>(G, Lv, 32)) {
     const size_t sm = kLeafWarpCta * leaf_warp_bytes<T>(Lv.max_nI, G.leaf, 32);
-    k_leaf_warp<T, 32><<<(Lv.ncell + kLeafWarpCta - 1) / kLeafWarpCta, 32 * kLeafWarpCta, sm, s>>>(
+    launch_pdl(k_leaf_warp<T, 32>, (Lv.ncell + kLeafWarpCta - 1) / kLeafWarpCta, 32 * kLeafWarpCta, sm, s,
         G, Lv, diag, off, status);
     return;
   }
   if constexpr (sizeof(T) == 4) {   // no FP64 instance of the 64-column kernel
     if (leaf_warp_fits<T>(G, Lv, 64)) {
       const size_t sm = kLeafWarpCta * leaf_warp_bytes<T>(Lv.max_nI, G.leaf, 64);
-      k_leaf_warp<T, 64><<<(Lv.ncell + kLeafWarpCta - 1) / kLeafWarpCta, 32 * kLeafWarpCta, sm, s>>>(
+      launch_pdl(k_leaf_warp<T, 64>, (Lv.ncell + kLeafWarpCta - 1) / kLeafWarpCta, 32 * kLeafWarpCta, sm, s,
           G, Lv, diag, off, status);
       return;
     }
   }
   if (Lv.max_nB <= kStreamNB) {
     const size_t sm = leaf_stream_smem<T>(Lv.max_nI, Lv.max_w, G.leaf, G.d);
-    k_leaf_stream<T><<<Lv.ncell, kThreads, sm, s>>>(G, Lv, diag, off, status);
+    launch_pdl(k_leaf_stream<T>, Lv.ncell, kThreads, sm, s, G, Lv, diag, off, status);
     return;
   }
   const size_t sm = leaf_smem_bytes<T>(Lv.max_nI, Lv.max_nB, Lv.max_w, G.leaf, G.d);
-  k_leaf_elim<T><<<Lv.ncell, kThreads, sm, s>>>(G, Lv, diag, off, status);
+  launch_pdl(k_leaf_elim<T>, Lv.ncell, kThreads, sm, s, G, Lv, diag, off, status);
 }
 
 template <typename T>
@@ -2517,7 +2581,7 @@ int launch_extend_add(const LevelDev& cur, const LevelDev& prev, int64_t front_t
   if (!cur.ncell) return 0;
   const int64_t nb = prev.max_nB;
   if (nb * nb * slots <= 128 * 1024) {   // small frames: one CTA per parent, one launch
-    k_extend_add_cell<T><<<cur.ncell, kEaCellThreads, 0, s>>>(cur, prev);
+    launch_pdl(k_extend_add_cell<T>, cur.ncell, kEaCellThreads, 0, s, cur, prev);
     return 1;
   }
   cudaMemsetAsync(cur.front, 0, (size_t)front_total * sizeof(T), s);
@@ -2525,7 +2589,7 @@ int launch_extend_add(const LevelDev& cur, const LevelDev& prev, int64_t front_t
   const unsigned chunks = (unsigned)((nb * nb + chunk - 1) / chunk);
   if (!chunks) return 0;
   for (int slot = 0; slot < slots; ++slot)
-    k_extend_add<T><<<dim3(chunks, cur.ncell), kThreads, 0, s>>>(cur, prev, slot, chunk);
+    launch_pdl(k_extend_add<T>, dim3(chunks, cur.ncell), kThreads, 0, s, cur, prev, slot, chunk);
   return slots;
 }
 
@@ -2533,41 +2597,41 @@ template <typename T>
 void launch_front_invert(const LevelDev& Lv, T* X, const int64_t* xoff, cudaStream_t s) {
   if (!Lv.ncell || !Lv.max_nI) return;
   const unsigned nb = (unsigned)((Lv.max_nI + kTile - 1) / kTile);
-  k_front_trinv<T><<<dim3(nb, Lv.ncell), kThreads, kTile * (kTile + 1) * sizeof(T), s>>>(Lv, X, xoff);
-  k_front_inv_store<T><<<dim3(64, Lv.ncell), 256, 0, s>>>(Lv, X, xoff);
+  launch_pdl(k_front_trinv<T>, dim3(nb, Lv.ncell), kThreads, kTile * (kTile + 1) * sizeof(T), s, Lv, X, xoff);
+  launch_pdl(k_front_inv_store<T>, dim3(64, Lv.ncell), 256, 0, s, Lv, X, xoff);
 }
 
 template <typename T>
 void launch_band_block_inverse(const LevelDev& Lv, cudaStream_t s) {
   if (!Lv.ncell) return;   // per-cell test inside: the apply decides per cell too
-  k_band_block_inverse<T><<<(Lv.ncell + 7) / 8, 256, 0, s>>>(Lv);
+  launch_pdl(k_band_block_inverse<T>, (Lv.ncell + 7) / 8, 256, 0, s, Lv);
 }
 
 template <typename T>
 void launch_partial_chol(const LevelDev& Lv, int* status, cudaStream_t s) {
   if (!Lv.ncell) return;
-  k_partial_chol<T><<<Lv.ncell, kThreads, partial_chol_smem_elems() * sizeof(T), s>>>(Lv, status);
+  launch_pdl(k_partial_chol<T>, Lv.ncell, kThreads, partial_chol_smem_elems() * sizeof(T), s, Lv, status);
 }
 
 template <typename T>
 void launch_front_panel(const LevelDev& Lv, int p0, int* status, cudaStream_t s) {
   const size_t sm = kNB * (kNB + 1) * sizeof(T);
-  k_front_pdiag<T><<<Lv.ncell, kThreads, sm, s>>>(Lv, p0, status);
+  launch_pdl(k_front_pdiag<T>, Lv.ncell, kThreads, sm, s, Lv, p0, status);
   const int rows = Lv.max_n - p0;
   if (rows > 0)
-    k_front_prows<T><<<dim3((rows + kThreads - 1) / kThreads, Lv.ncell), kThreads, sm, s>>>(Lv, p0);
+    launch_pdl(k_front_prows<T>, dim3((rows + kThreads - 1) / kThreads, Lv.ncell), kThreads, sm, s, Lv, p0);
 }
 
 template <typename T>
 void launch_front_trailing(const LevelDev& Lv, int p0, int64_t tiles, cudaStream_t s) {
   if (tiles > 0)
-    k_front_trailing<T><<<(unsigned)tiles, kThreads, 2 * kKC * (kTile + 1) * sizeof(T), s>>>(Lv, p0);
+    launch_pdl(k_front_trailing<T>, (unsigned)tiles, kThreads, 2 * kKC * (kTile + 1) * sizeof(T), s, Lv, p0);
 }
 
 template <typename T>
 void launch_front_schur(const LevelDev& Lv, int64_t tiles, cudaStream_t s) {
   if (tiles > 0)
-    k_front_schur<T><<<(unsigned)tiles, kThreads, 2 * kKC * (kTile + 1) * sizeof(T), s>>>(Lv);
+    launch_pdl(k_front_schur<T>, (unsigned)tiles, kThreads, 2 * kKC * (kTile + 1) * sizeof(T), s, Lv);
 }
 
 int64_t front_trailing_tiles(int nI, int n, int p0) { return trail_tiles(nI, n, p0); }
@@ -2578,13 +2642,13 @@ int launch_precond_diag(const LevelDev& Lv, const PhaseDev& Ph, int* status, cud
   if (!Ph.npre) return 0;
   if (Ph.Linv && Lv.max_group <= 32) {   // factor and inverse, one warp per group
     constexpr int W = pdiag_warps<T>();
-    k_precond_diag_warp<T><<<(Ph.npre + W - 1) / W, 32 * W, 0, s>>>(Lv, Ph, status);
+    launch_pdl(k_precond_diag_warp<T>, (Ph.npre + W - 1) / W, 32 * W, 0, s, Lv, Ph, status);
     return 1;
   }
-  k_precond_diag<T><<<Ph.npre, kThreads, partial_chol_smem_elems() * sizeof(T), s>>>(Lv, Ph, status);
+  launch_pdl(k_precond_diag<T>, Ph.npre, kThreads, partial_chol_smem_elems() * sizeof(T), s, Lv, Ph, status);
   if (!Ph.Linv) return 1;
   const unsigned nb = (unsigned)((Lv.max_group + kTile - 1) / kTile);
-  k_group_trinv<T><<<dim3(nb, Ph.npre), kThreads, kTile * (kTile + 1) * sizeof(T), s>>>(Lv, Ph);
+  launch_pdl(k_group_trinv<T>, dim3(nb, Ph.npre), kThreads, kTile * (kTile + 1) * sizeof(T), s, Lv, Ph);
   return 2;
 }
 
@@ -2593,13 +2657,13 @@ int launch_unit_invert(const LevelDev& Lv, const PhaseDev& Ph, T* X, cudaStream_
   if (!Ph.nunit) return 0;
   if (Ph.max_n <= 32) {
     constexpr int W = trinv_warps<T>();
-    k_trinv_warp<T, true><<<(Ph.nunit + W - 1) / W, 32 * W, 0, s>>>(Lv, Ph, Ph.nunit);
+    launch_pdl(k_trinv_warp<T, true>, (Ph.nunit + W - 1) / W, 32 * W, 0, s, Lv, Ph, Ph.nunit);
     return 1;
   }
   const unsigned nb = (unsigned)((Ph.max_n + kTile - 1) / kTile);
-  k_unit_trinv<T><<<dim3(nb, Ph.nunit), kThreads, kTile * (kTile + 1) * sizeof(T), s>>>(Lv, Ph, X);
+  launch_pdl(k_unit_trinv<T>, dim3(nb, Ph.nunit), kThreads, kTile * (kTile + 1) * sizeof(T), s, Lv, Ph, X);
   const unsigned chunks = (unsigned)((Ph.max_n * Ph.max_n + 255) / 256);
-  k_unit_inv_store<T><<<dim3(chunks, Ph.nunit), 256, 0, s>>>(Lv, Ph, X);
+  launch_pdl(k_unit_inv_store<T>, dim3(chunks, Ph.nunit), 256, 0, s, Lv, Ph, X);
   return 2;
 }
 
@@ -2609,22 +2673,22 @@ void launch_precond_scale(const LevelDev& Lv, const PhaseDev& Ph, int max_seg, c
   const size_t blk = round16((size_t)Lv.max_nB * (Lv.max_nB | 1) * sizeof(T));
   const size_t xb = (size_t)max_seg * Lv.max_group * Lv.max_group * sizeof(T);
   if (blk + xb <= 96 * 1024) {
-    k_precond_scale<T><<<Lv.ncell, kThreads, blk + xb, s>>>(Lv, Ph, 1, 1);
+    launch_pdl(k_precond_scale<T>, Lv.ncell, kThreads, blk + xb, s, Lv, Ph, 1, 1);
   } else if (blk <= 200 * 1024) {
-    k_precond_scale<T><<<Lv.ncell, kThreads, blk, s>>>(Lv, Ph, 1, 0);
+    launch_pdl(k_precond_scale<T>, Lv.ncell, kThreads, blk, s, Lv, Ph, 1, 0);
   } else {
-    k_precond_scale<T><<<Lv.ncell, kThreads, 0, s>>>(Lv, Ph, 0, 0);
+    launch_pdl(k_precond_scale<T>, Lv.ncell, kThreads, 0, s, Lv, Ph, 0, 0);
   }
 }
 
 template <typename T>
 void launch_precond_scale_big(const LevelDev& Lv, const PhaseDev& Ph, int64_t tasks,
                               cudaStream_t s) {
-  k_frame_symmetrize<T><<<dim3(64, min(Lv.ncell, 65535)), 256, 0, s>>>(Lv);
+  launch_pdl(k_frame_symmetrize<T>, dim3(64, min(Lv.ncell, 65535)), 256, 0, s, Lv);
   if (tasks <= 0) return;
   const size_t sm = 2 * kKC * (kTile + 1) * sizeof(T);
-  k_frame_rows_tp<T><<<(unsigned)tasks, kThreads, sm, s>>>(Lv, Ph);
-  k_frame_cols_tp<T><<<(unsigned)tasks, kThreads, sm, s>>>(Lv, Ph);
+  launch_pdl(k_frame_rows_tp<T>, (unsigned)tasks, kThreads, sm, s, Lv, Ph);
+  launch_pdl(k_frame_cols_tp<T>, (unsigned)tasks, kThreads, sm, s, Lv, Ph);
 }
 
 template <typename T>
@@ -2640,8 +2704,8 @@ void launch_skel(const LevelDev& Lv, const PhaseDev& Ph, uint8_t* alive, double 
   const size_t mb = (size_t)max_m_elems * sizeof(T);
   const int mstage = sm + mb <= 200 * 1024;
   if (mstage) sm += mb;
-  k_skel<T><<<Ph.nunit, kThreads, sm, s>>>(Lv, Ph, alive, tol, status, mstage);
-  k_mark_dead<<<Ph.nunit, 32, 0, s>>>(Lv, Ph, alive);
+  launch_pdl(k_skel<T>, Ph.nunit, kThreads, sm, s, Lv, Ph, alive, tol, status, mstage);
+  launch_pdl(k_mark_dead, Ph.nunit, 32, 0, s, Lv, Ph, alive);
 }
 
 template <typename T>
@@ -2653,8 +2717,8 @@ bool launch_skel_warp(const LevelDev& Lv, const PhaseDev& Ph, uint8_t* alive, do
   int wpc = (int)std::min<size_t>(8, (200 * 1024) / per);
   if (wpc < 1) return false;
   const unsigned grid = (unsigned)((Ph.nunit + wpc - 1) / wpc);
-  k_skel_warp<T><<<grid, 32 * wpc, wpc * per, s>>>(Lv, Ph, alive, tol, status, (int)per);
-  k_mark_dead<<<Ph.nunit, 32, 0, s>>>(Lv, Ph, alive);
+  launch_pdl(k_skel_warp<T>, grid, 32 * wpc, wpc * per, s, Lv, Ph, alive, tol, status, (int)per);
+  launch_pdl(k_mark_dead, Ph.nunit, 32, 0, s, Lv, Ph, alive);
   return true;
 }
 
@@ -2705,7 +2769,7 @@ cudaError_t launch_skel_cluster(const LevelDev& Lv, const PhaseDev& Ph, uint8_t*
   cfg.numAttrs = 1;
   cudaError_t e = cudaLaunchKernelEx(&cfg, k_skel_cluster<T>, Lv, Ph, alive, tol, status, slice_cap);
   if (e != cudaSuccess) return e;
-  k_mark_dead<<<Ph.nunit, 32, 0, s>>>(Lv, Ph, alive);
+  launch_pdl(k_mark_dead, Ph.nunit, 32, 0, s, Lv, Ph, alive);
   return cudaGetLastError();
 }
 

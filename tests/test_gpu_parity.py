@@ -293,3 +293,35 @@ def test_shared_level0_plan_gives_the_factor_of_a_fresh_plan(gpu_lib):
     np.testing.assert_array_equal(y1, y2b)
     for F in (F2, Fb, F3, F4, F5):
         F.free()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_device_pcg_loop_matches_host_loop(gpu_lib, precision):
+    """rhif_pcg runs its iterations on the device (a CUDA graph whose
+    conditional loop tests convergence there); with per-launch timing on it
+    runs the same iterations from the host.  Both give the same solution, bit
+    for bit, and the same per-right-hand-side iteration counts, also when
+    maxit stops them before rtol (NOT_CONVERGED, counts = maxit)."""
+    ns = (63, 63)
+    a = W.log_uniform_pixels(ns, 1e-3, 1e3, seed=17)
+    Fg = gpu_lib.rhif_factor(gpu_lib.rhif_assemble_fd(ns, _dev(a), 0.0), ns, 8, 1e-3,
+                             precision=precision)
+    f = _dev(np.random.default_rng(5).standard_normal((3, Fg.N)))
+    try:
+        u_d, it_d, rr_d = Fg.pcg(f, rtol=1e-11)
+        gpu_lib.rhif_set_timing(True)
+        u_h, it_h, rr_h = Fg.pcg(f, rtol=1e-11)
+    finally:
+        gpu_lib.rhif_set_timing(False)
+    np.testing.assert_array_equal(u_d.cpu().numpy(), u_h.cpu().numpy())
+    assert it_d == it_h and rr_d == rr_h
+    assert max(rr_d) <= 1.5e-11
+    u_d, it_d, _ = Fg.pcg(f, rtol=1e-14, maxit=2, check=False)
+    try:
+        gpu_lib.rhif_set_timing(True)
+        u_h, it_h, _ = Fg.pcg(f, rtol=1e-14, maxit=2, check=False)
+    finally:
+        gpu_lib.rhif_set_timing(False)
+    assert it_d == it_h == [2, 2, 2]
+    np.testing.assert_array_equal(u_d.cpu().numpy(), u_h.cpu().numpy())
+    Fg.free()

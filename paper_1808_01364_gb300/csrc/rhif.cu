@@ -1336,14 +1336,18 @@ static int pcg_direction(rhif_handle* F, int nrhs, const PcgBufs& b, double rtol
   return RHIF_OK;
 }
 
-// The iterations of rhif_pcg (Sec. 4) as one CUDA graph: iteration 1 up to
-// its convergence test, then a conditional WHILE node whose body is one more
-// iteration (preconditioner application, search direction, SpMV, step,
-// test).  The test kernel sets the loop condition on the device, so the host
-// waits once, after the loop, instead of once per iteration.  Captured on the
-// handle's private stream (nothing runs); false when the graph cannot be made
-// (the caller then iterates from the host).
-static bool capture_pcg(rhif_handle* H, int nrhs, double* u, int64_t ldu, double rtol, int maxit) {
+// PCG iterations (Sec. 4) as one CUDA graph: iteration 1 up to its
+// convergence test (`step`), then a conditional WHILE node whose body is one
+// more iteration (`direction`: preconditioner application and search
+// direction; `step`: SpMV, step, residual test).  k_pcg_check sets the loop
+// condition on the device from the ncheck done flags in sc (stride 8) and
+// counts iterations in kit, so the host waits once, after the loop, instead
+// of once per iteration.  Captured on the handle's private stream (nothing
+// runs) into H->pcg_graph; false when the graph cannot be made (the caller
+// then iterates from the host).
+template <typename Step, typename Dir>
+static bool capture_pcg_loop(rhif_handle* H, int ncheck, int* kit, const double* sc, int maxit,
+                             Step step, Dir direction) {
   if (H->pcg_graph) {
     cudaGraphExecDestroy(H->pcg_graph);
     H->pcg_graph = nullptr;
@@ -1354,7 +1358,6 @@ static bool capture_pcg(rhif_handle* H, int nrhs, double* u, int64_t ldu, double
     return false;
   }
   cudaStream_t cs = H->capture_stream;
-  const PcgBufs b = pcg_bufs(H->work, H->G.N, nrhs, vec_blocks(H->G.N));
   KStat pre[kNumCat] = {}, body[kNumCat] = {};
   cudaGraph_t g = nullptr;
   if (cudaGraphCreate(&g, 0) != cudaSuccess) return false;
@@ -1364,9 +1367,9 @@ static bool capture_pcg(rhif_handle* H, int nrhs, double* u, int64_t ldu, double
   if (ok && cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
                 cudaSuccess) {
     t_capture_stats = pre;
-    launch_pcg_kit_init(b.kit, nrhs, maxit, cs);
-    pcg_step(H, nrhs, u, ldu, b, rtol, cs);
-    launch_pcg_check(b.sc, nrhs, b.kit, maxit, h, cs);
+    launch_pcg_kit_init(kit, ncheck, maxit, cs);
+    step(cs);
+    launch_pcg_check(sc, ncheck, kit, maxit, h, cs);
     t_capture_stats = nullptr;
     cudaStreamCaptureStatus st{};
     cudaGraph_t cg = nullptr;
@@ -1397,9 +1400,9 @@ static bool capture_pcg(rhif_handle* H, int nrhs, double* u, int64_t ldu, double
                                              cudaStreamCaptureModeThreadLocal) == cudaSuccess;
     if (ok) {
       t_capture_stats = body;
-      const int rc = pcg_direction(H, nrhs, b, rtol, cs, false);
-      pcg_step(H, nrhs, u, ldu, b, rtol, cs);
-      launch_pcg_check(b.sc, nrhs, b.kit, maxit, h, cs);
+      const int rc = direction(cs);
+      step(cs);
+      launch_pcg_check(sc, ncheck, kit, maxit, h, cs);
       t_capture_stats = nullptr;
       cudaGraph_t out = nullptr;
       const bool ended = cudaStreamEndCapture(cs, &out) == cudaSuccess;
@@ -1415,6 +1418,21 @@ static bool capture_pcg(rhif_handle* H, int nrhs, double* u, int64_t ldu, double
     return false;
   }
   H->pcg_graph = exec;
+  for (int c = 0; c < kNumCat; ++c) {
+    H->pg_pre[c] = pre[c];
+    H->pg_body[c] = body[c];
+  }
+  return true;
+}
+
+// Whether H->pcg_graph was captured for these buffers and parameters.
+static bool pcg_graph_matches(const rhif_handle* H, const double* u, int64_t ldu, int nrhs,
+                              double rtol, int maxit) {
+  return H->pcg_graph && H->pg_u == u && H->pg_work == H->work && H->pg_ubuf == H->ubuf &&
+         H->pg_ldu == ldu && H->pg_nrhs == nrhs && H->pg_rtol == rtol && H->pg_maxit == maxit;
+}
+
+static void pcg_graph_key(rhif_handle* H, double* u, int64_t ldu, int nrhs, double rtol, int maxit) {
   H->pg_u = u;
   H->pg_work = H->work;
   H->pg_ubuf = H->ubuf;
@@ -1422,11 +1440,16 @@ static bool capture_pcg(rhif_handle* H, int nrhs, double* u, int64_t ldu, double
   H->pg_nrhs = nrhs;
   H->pg_rtol = rtol;
   H->pg_maxit = maxit;
-  for (int c = 0; c < kNumCat; ++c) {
-    H->pg_pre[c] = pre[c];
-    H->pg_body[c] = body[c];
-  }
-  return true;
+}
+
+// The iterations of rhif_pcg as one graph (capture_pcg_loop).
+static bool capture_pcg(rhif_handle* H, int nrhs, double* u, int64_t ldu, double rtol, int maxit) {
+  const PcgBufs b = pcg_bufs(H->work, H->G.N, nrhs, vec_blocks(H->G.N));
+  const bool ok = capture_pcg_loop(
+      H, nrhs, b.kit, b.sc, maxit, [&](cudaStream_t cs) { pcg_step(H, nrhs, u, ldu, b, rtol, cs); },
+      [&](cudaStream_t cs) { return pcg_direction(H, nrhs, b, rtol, cs, false); });
+  if (ok) pcg_graph_key(H, u, ldu, nrhs, rtol, maxit);
+  return ok;
 }
 
 
@@ -1932,7 +1955,8 @@ static int pcg_batch_core(rhif_handle* F, int nrhs, const double* f, int64_t ldf
   const int64_t N = F->G.N, ld = N;
   const double spmv_flops = 2.0 * (2 * F->G.d + 1) * N, spmv_bytes = (8.0 * (1 + F->G.d) + 16.0) * N;
   const int64_t nsc = 8 * (int64_t)np * nrhs;
-  const int64_t need = 4 * N * nrhs + (int64_t)nblk * nrhs + 2 * nsc;
+  const int npair = np * nrhs;
+  const int64_t need = 4 * N * nrhs + (int64_t)nblk * nrhs + 2 * nsc + (npair + 2) / 2 + 1;
   if ((rc = ensure_work(F, need))) return rc;
   double* r = F->work;
   double* z = r + N * nrhs;
@@ -1941,8 +1965,26 @@ static int pcg_batch_core(rhif_handle* F, int nrhs, const double* f, int64_t ldf
   double* part = q + N * nrhs;
   double* sc = part + (int64_t)nblk * nrhs;
   double* sc2 = sc + nsc;
+  int* kit = (int*)(sc2 + nsc);   // device loop: iterations, then one count per (rhs, problem)
   auto vb = [&](double per_entry) { return per_entry * double(N) * nrhs; };
   const double rb = 8.0 * nblk * nrhs;
+  // the two halves of an iteration: SpMV, step and residual test; then
+  // preconditioner application and search direction
+  auto step = [&](cudaStream_t st) {
+    { Launch t_(kCatSpmv, st, spmv_flops * nrhs, spmv_bytes * nrhs); launch_bspmv(S, F->bgeo, p, ld, q, ld, nrhs, part, st); }
+    { Launch t_(kCatVector, st, 0.0, rb); launch_breduce(S, part, nrhs, sc, 2, rtol, st); }
+    { Launch t_(kCatVector, st, 0.0, vb(48)); launch_bupdate_xr(S, nrhs, sc, u, ldu, r, ld, p, ld, q, ld, part, st); }
+    { Launch t_(kCatVector, st, 0.0, rb); launch_breduce(S, part, nrhs, sc, 3, rtol, st); }
+  };
+  auto direction = [&](cudaStream_t st, bool replay) -> int {
+    { Launch t_(kCatVector, st, 0.0, vb(16)); launch_copy_cols(N, nrhs, r, ld, z, ld, st); }
+    const int e = replay ? apply_dispatch(F, z, ld, nrhs, st, true) : apply_launch(F, z, ld, nrhs, st);
+    if (e) return e;
+    { Launch t_(kCatVector, st, 0.0, vb(16)); launch_bdot_partial(S, r, ld, z, ld, nrhs, part, st); }
+    { Launch t_(kCatVector, st, 0.0, rb); launch_breduce(S, part, nrhs, sc, 4, rtol, st); }
+    { Launch t_(kCatVector, st, 0.0, vb(24)); launch_bupdate_p(S, nrhs, sc, z, ld, p, ld, 0, st); }
+    return RHIF_OK;
+  };
   CK(cudaMemsetAsync(sc, 0, 2 * nsc * sizeof(double), s));
   for (int c = 0; c < nrhs; ++c) CK(cudaMemsetAsync(u + c * ldu, 0, N * sizeof(double), s));
   { Launch t_(kCatVector, s, 0.0, vb(16)); launch_copy_cols(N, nrhs, f, ldf, r, ld, s); }
@@ -1954,15 +1996,33 @@ static int pcg_batch_core(rhif_handle* F, int nrhs, const double* f, int64_t ldf
   { Launch t_(kCatVector, s, 0.0, rb); launch_breduce(S, part, nrhs, sc, 1, rtol, s); }
   { Launch t_(kCatVector, s, 0.0, vb(24)); launch_bupdate_p(S, nrhs, sc, z, ld, p, ld, 1, s); }
   std::vector<double> hsc(nsc);
-  const int npair = np * nrhs;
-  std::vector<int> it(npair, maxit);
+  std::vector<int> it(npair, maxit), hkit(npair + 1, 0);
   std::vector<char> was_done(npair, 0);
   int all_done = 0;
-  for (int k = 1; k <= maxit; ++k) {
-    { Launch t_(kCatSpmv, s, spmv_flops * nrhs, spmv_bytes * nrhs); launch_bspmv(S, F->bgeo, p, ld, q, ld, nrhs, part, s); }
-    { Launch t_(kCatVector, s, 0.0, rb); launch_breduce(S, part, nrhs, sc, 2, rtol, s); }
-    { Launch t_(kCatVector, s, 0.0, vb(48)); launch_bupdate_xr(S, nrhs, sc, u, ldu, r, ld, p, ld, q, ld, part, s); }
-    { Launch t_(kCatVector, s, 0.0, rb); launch_breduce(S, part, nrhs, sc, 3, rtol, s); }
+  // the iterations on the device as one graph with a conditional loop
+  // (unless per-launch timing is on), else from the host
+  bool timing;
+  {
+    std::lock_guard<std::mutex> lk(g_kmu);
+    timing = g_timing;
+  }
+  bool device_loop = false;
+  if (!timing && maxit > 0) {
+    bool ok = pcg_graph_matches(F, u, ldu, nrhs, rtol, maxit);
+    if (!ok) {
+      ok = capture_pcg_loop(F, npair, kit, sc, maxit, step,
+                            [&](cudaStream_t st) { return direction(st, false); });
+      if (ok) pcg_graph_key(F, u, ldu, nrhs, rtol, maxit);
+    }
+    if (ok) {
+      CK(cudaGraphLaunch(F->pcg_graph, s));
+      CK(cudaMemcpyAsync(hkit.data(), kit, (npair + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(hsc.data(), sc, nsc * sizeof(double), cudaMemcpyDeviceToHost, s));
+      device_loop = true;
+    }
+  }
+  for (int k = 1; !device_loop && k <= maxit; ++k) {
+    step(s);
     CK(cudaMemcpyAsync(hsc.data(), sc, nsc * sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     int nd = 0;
@@ -1975,11 +2035,7 @@ static int pcg_batch_core(rhif_handle* F, int nrhs, const double* f, int64_t ldf
         }
       }
     if (nd == npair) { all_done = 1; break; }
-    { Launch t_(kCatVector, s, 0.0, vb(16)); launch_copy_cols(N, nrhs, r, ld, z, ld, s); }
-    if ((rc = apply_dispatch(F, z, ld, nrhs, s, true))) return rc;
-    { Launch t_(kCatVector, s, 0.0, vb(16)); launch_bdot_partial(S, r, ld, z, ld, nrhs, part, s); }
-    { Launch t_(kCatVector, s, 0.0, rb); launch_breduce(S, part, nrhs, sc, 4, rtol, s); }
-    { Launch t_(kCatVector, s, 0.0, vb(24)); launch_bupdate_p(S, nrhs, sc, z, ld, p, ld, 0, s); }
+    if ((rc = direction(s, true))) return rc;
   }
   if (maxit == 0) {
     CK(cudaMemcpyAsync(hsc.data(), sc, nsc * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -1994,6 +2050,17 @@ static int pcg_batch_core(rhif_handle* F, int nrhs, const double* f, int64_t ldf
   CK(cudaMemcpyAsync(h2.data(), sc2, nsc * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   CK(cudaGetLastError());
+  if (device_loop) {   // counts per (rhs, problem) in the check's order, c * np + pp
+    credit_counts(F->pg_pre, 1.0);
+    credit_counts(F->pg_body, double(hkit[0] - 1));
+    all_done = 1;
+    for (int c = 0; c < nrhs; ++c)
+      for (int pp = 0; pp < np; ++pp) {
+        const int64_t j = (int64_t)c * np + pp;
+        it[pp * nrhs + c] = hkit[1 + j];
+        if (hsc[8 * j + kScDone] == 0.0) all_done = 0;
+      }
+  }
   for (int c = 0; c < nrhs; ++c)
     for (int pp = 0; pp < np; ++pp) {
       const int64_t o = 8 * ((int64_t)c * np + pp);
@@ -2085,10 +2152,7 @@ int rhif_pcg(const rhif_handle* Fc, int nrhs, const double* f, int64_t ldf, doub
   }
   bool device_loop = false;
   if (!timing && maxit > 0) {
-    const bool match = F->pcg_graph && F->pg_u == u && F->pg_work == F->work &&
-                       F->pg_ubuf == F->ubuf && F->pg_ldu == ldu && F->pg_nrhs == nrhs &&
-                       F->pg_rtol == rtol && F->pg_maxit == maxit;
-    if (match || capture_pcg(F, nrhs, u, ldu, rtol, maxit)) {
+    if (pcg_graph_matches(F, u, ldu, nrhs, rtol, maxit) || capture_pcg(F, nrhs, u, ldu, rtol, maxit)) {
       CK(cudaGraphLaunch(F->pcg_graph, s));
       CK(cudaMemcpyAsync(hkit.data(), b.kit, (nrhs + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
       CK(cudaMemcpyAsync(hsc.data(), b.sc, 8 * nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));

@@ -141,3 +141,29 @@ def test_merged_batch_rejects_mixed_dimensions(gpu_lib):
     with pytest.raises(gpu_lib.RhifError) as e:
         gpu_lib.rhif_factor_batch(csrs, [p2[0], p3[0]], 4, 1e-3)
     assert e.value.code == -1
+
+
+def test_batch_device_pcg_loop_matches_host_loop(gpu_lib):
+    """rhif_pcg_batch runs its iterations on the device (one CUDA graph whose
+    conditional loop tests every (problem, right-hand side) pair there); with
+    per-launch timing on it runs them from the host.  Both give the same
+    solutions bit for bit and the same per-pair iteration counts, also when
+    maxit stops them (NOT_CONVERGED)."""
+    probs = _problems([23, 31, (17, 29)], seed=410)
+    csrs = [gpu_lib.rhif_assemble_fd(ns, _dev(a), 0.0) for ns, a in probs]
+    FB = gpu_lib.rhif_factor_batch(csrs, [ns for ns, _ in probs], 4, 1e-3, precision="fp32")
+    rng = np.random.default_rng(23)
+    fs = [_dev(rng.standard_normal((2, int(np.prod(ns))))) for ns, _ in probs]
+    for rtol, maxit, check in ((1e-11, 1000, True), (1e-14, 2, False)):
+        ud, itd, _ = FB.pcg_batch(fs, rtol=rtol, maxit=maxit, check=check)
+        try:
+            gpu_lib.rhif_set_timing(True)
+            uh, ith, _ = FB.pcg_batch(fs, rtol=rtol, maxit=maxit, check=check)
+        finally:
+            gpu_lib.rhif_set_timing(False)
+        assert itd == ith
+        for a, b in zip(ud, uh):
+            np.testing.assert_array_equal(a.cpu().numpy(), b.cpu().numpy())
+        if maxit == 2:
+            assert all(i == [2, 2] for i in itd)
+    FB.free()

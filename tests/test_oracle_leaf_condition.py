@@ -1,12 +1,15 @@
-"""Why the FP32 factor has no per-leaf FP64 fallback (the decision recorded in
-the design notes), checked on the oracle's assembly of the 1023^2 recipe
-(log10 a ~ U[-4, 4] per pixel, leaf 16).
+"""Which condition estimate the FP64 leaf fallback of FP32 factors uses,
+checked on the oracle's assembly of the 1023^2 recipe (log10 a ~ U[-4, 4] per
+pixel, leaf 16).
 
 The cheap lower bound kappa_hat = (max L_ii / min L_ii)^2 of a leaf block's
 condition number grows with the coefficient contrast, so at contrast 1e8 a
-large share of the leaves would exceed the 1e6 threshold; the Jacobi-scaled
-condition number kappa(D A_II D) (D = diag(A_II)^{-1/2}), which bounds the
-accuracy of a Cholesky factorization, exceeds it on almost none.
+large share of the leaves would exceed the 1e6 threshold and be eliminated
+again in FP64; the Jacobi-scaled condition number kappa(D A_II D)
+(D = diag(A_II)^{-1/2}), which bounds the accuracy of a Cholesky
+factorization, exceeds it on almost none.  The fallback therefore tests the
+scaled condition number (its 1-norm form, computed on the GPU from the FP32
+band factor).
 """
 import numpy as np
 

@@ -2281,7 +2281,7 @@ void launch_leaf_cond(const GeoDev& G, const LevelDev& Lv, const double* diag, c
 // pass of k_leaf_stream, the same operations in the same order), carries the
 // rows of Z only for the tile's 16 or 32 columns, and accumulates only its
 // tile of S.  It writes its tile of the frame's lower triangle, the FP32
-// A_BB share minus S rounded to FP32 (as k_leaf_stream<double, float>); tile
+// A_BB share minus S, the difference taken in FP64 and rounded to FP32; tile
 // 0 writes the band.  The couplings and the frame's upper triangle are the
 // FP32 leaf kernel's, from the same stencil values.  The flagged leaves come
 // as a list of count[0] cells; the grid's x loops over it.

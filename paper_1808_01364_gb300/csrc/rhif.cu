@@ -1942,9 +1942,11 @@ int rhif_spmv(const rhif_handle* F, int nrhs, const double* x, int64_t ldx, doub
 
 // PCG (Sec. 4) of every (problem, right-hand side) pair of a merged batch at
 // once, on concatenated vectors: the same iteration as rhif_pcg with
-// per-pair scalars, one F^{-1} application (the merged sweeps, replayed as a
-// CUDA graph) and one SpMV launch per iteration for the whole batch, and one
-// readback of the convergence flags.  iters / relres: count x nrhs, problem-major.
+// per-pair scalars, one F^{-1} application (the merged sweeps) and one SpMV
+// launch per iteration for the whole batch.  The iterations run on the device
+// as one graph with a conditional loop over all pairs' convergence flags
+// (capture_pcg_loop), from the host while per-launch timing is on.
+// iters / relres: count x nrhs, problem-major.
 static int pcg_batch_core(rhif_handle* F, int nrhs, const double* f, int64_t ldf, double* u,
                           int64_t ldu, double rtol, int maxit, int* iters, double* relres,
                           cudaStream_t s) {

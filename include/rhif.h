@@ -199,7 +199,9 @@ int rhif_batch_info(const rhif_handle* F, int* count, int64_t* dof_base);
  * iteration advances every (problem, right-hand side) pair with the same
  * launches; each pair stops on its own relative residual (Sec. 4).  iters and
  * relres: HOST arrays of count * nrhs entries, problem-major.  Errors as
- * rhif_pcg; BAD_ARG for a handle of a single problem. */
+ * rhif_pcg; BAD_ARG for a handle of a single problem.  As in rhif_pcg, the
+ * iterations run on the device as one CUDA graph whose conditional loop tests
+ * every pair's convergence there (from the host while kernel timing is on). */
 int rhif_pcg_batch(const rhif_handle* F, int nrhs, const double* const* f, double* const* u,
                    double rtol, int maxit, int* iters, double* relres, void* stream);
 

@@ -2204,18 +2204,14 @@ __global__ void __launch_bounds__(128) k_leaf_cond(GeoDev G, LevelDev Lv, const 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c = blockIdx.x * (blockDim.x >> 5) + warp;
   if (c >= Lv.ncell) return;
-  const int n = Lv.nI[c], w = Lv.band_w[c], w1 = w + 1;
+  const int n = Lv.nI[c], w = Lv.band_w[c];
   const int32_t* gid = Lv.gids + Lv.gid_off[c];
   const int64_t dbase = bind_cell_geo(Lv, c, G, diag, off);
-  T* band = (T*)(smraw + (size_t)warp * per_warp);   // the band, staged (coalesced copy)
-  T* sd = band + (size_t)Lv.max_nI * (Lv.max_w + 1);   // S = sqrt(diag A_II)
-  T* x = sd + Lv.max_nI;
-  T* y = x + Lv.max_nI;
-  {
-    const T* g = (const T*)Lv.band + Lv.band_off[c];
-    for (int i = lane; i < n * w1; i += 32) band[i] = g[i];
-    __syncwarp();
-  }
+  // the band is read where the leaf elimination left it (staging it in shared
+  // memory limited the resident leaves to about half of them)
+  const T* band = (const T*)Lv.band + Lv.band_off[c];
+  T* sd = (T*)(smraw + (size_t)warp * per_warp);   // S = sqrt(diag A_II)
+  T* y = sd + Lv.max_nI;
   // entries of A_II from the stencil form (interior in lexicographic order:
   // x-neighbours at +-1 inside a row of w, y-neighbours at +-w)
   // (in T: FP64 arithmetic is scarce on this GPU and the estimate needs no more)
@@ -2267,7 +2263,7 @@ __global__ void __launch_bounds__(128) k_leaf_cond(GeoDev G, LevelDev Lv, const 
 void launch_leaf_cond(const GeoDev& G, const LevelDev& Lv, const double* diag, const double* off,
                       double thresh, int* list, int* count, cudaStream_t s) {
   if (!Lv.ncell) return;
-  const int per = (int)(((size_t)(Lv.max_w + 4) * Lv.max_nI * sizeof(float) + 15) & ~size_t(15));
+  const int per = (int)(((size_t)2 * Lv.max_nI * sizeof(float) + 15) & ~size_t(15));
   launch_pdl(k_leaf_cond<float>, (Lv.ncell + 3) / 4, 128, 4 * per, s, G, Lv, diag, off, thresh, list,
                                                              count, per);
 }
